@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the short-read extension path (arXiv 1805.00106, Sec. 3.5-3.6,
+6.4) on GB300: Smith-Waterman GCUPS and reads/s of the whole device path for
+the batched uneven workload (100 Mbp reference at 41% GC, 1M reads of 75-250
+bp, Poisson(6) candidate windows of read length + 64 bp), with inputs resident
+in HBM; an end-to-end number through the host-buffer call; the plain
+one-launch-per-batch engine on the same batch; the integer roofline of the
+extension kernels; and the oracle timed on the host cores.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank aligns its own batch of the same shape
+(seeded by rank: weak scaling, no data-path collective); timing is the max
+over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("c2 batched uneven: 100 Mbp reference (41% GC), 1M reads uniform 75-250 bp with 1% "
+            "substitutions and 0.1% indels, Poisson(6) windows per read capped at 64, each read "
+            "length + 2x32 bp; scores +2/-3, gap 5+2k")
+SP = (2, 3, 5, 2)
+OPS_PER_CELL = 3  # packed 16-bit ops per cell of the score-only recurrence (6 per s16x2 pair)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests/profiling)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0, help="wall budget of the oracle sample")
+    ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.p = gpu, None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1805_00106_gb300", "csrc", "sr_extend.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(cells):
+    """DRAM bytes of the extension kernels from the committed ncu capture, scaled
+    to this launch by cells; None when the kernel source changed since."""
+    p = os.path.join(ROOT, "profiles", "extend_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("kernel_sha256_16") != kernel_hash():
+        return None
+    return d["dram_bytes_per_cell"] * cells
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(w, budget_s, rng_seed=0):
+    """The oracle as it stands on this host's cores, on a bounded read sample."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    refs = [O.encode(bytes(r)) for r in w["refs"]]
+    n = len(w["read_off"]) - 1
+    m = np.diff(w["read_off"])
+    cells_per_read = np.add.reduceat(np.repeat(m, np.diff(w["cand_off"])) * w["c_len"].astype(np.int64),
+                                     w["cand_off"][:-1]) if w["cand_off"][-1] else np.zeros(n)
+    cells_per_read = np.where(np.diff(w["cand_off"]) > 0, cells_per_read, 0)
+    # calibrate on a small prefix, then size the sample to the wall budget
+    k0 = min(n, 200)
+    t0 = time.perf_counter()
+    sub = slice_reads(w, 0, k0)
+    O.run_batch(refs, sub["bases"], sub["read_off"], sub["cand_off"], sub["c_ref"], sub["c_strand"],
+                sub["c_start"], sub["c_len"], O.score_params(*SP), threads=cores)
+    t1 = time.perf_counter() - t0
+    rate = max(float(cells_per_read[:k0].sum()), 1.0) / max(t1, 1e-6)
+    target = rate * budget_s
+    csum = np.cumsum(cells_per_read)
+    k = int(min(n, max(k0, np.searchsorted(csum, target))))
+    sub = slice_reads(w, 0, k)
+    t0 = time.perf_counter()
+    O.run_batch(refs, sub["bases"], sub["read_off"], sub["cand_off"], sub["c_ref"], sub["c_strand"],
+                sub["c_start"], sub["c_len"], O.score_params(*SP), threads=cores)
+    dt = time.perf_counter() - t0
+    cells = float(csum[k - 1]) if k else 0.0
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"first {k} reads of the same workload ({int(sub['cand_off'][-1])} windows, "
+                      f"{cells:.3e} cells) in {dt:.2f} s on {cores} threads",
+            "reads_per_s": k / dt, "seconds": dt, "reads": k, "cells": cells}
+
+
+def slice_reads(w, r0, r1):
+    ro, co = w["read_off"], w["cand_off"]
+    b0, b1, c0, c1 = ro[r0], ro[r1], co[r0], co[r1]
+    return dict(refs=w["refs"], bases=w["bases"][b0:b1], read_off=ro[r0:r1 + 1] - b0,
+                cand_off=co[r0:r1 + 1] - c0, c_ref=w["c_ref"][c0:c1], c_strand=w["c_strand"][c0:c1],
+                c_start=w["c_start"][c0:c1], c_len=w["c_len"][c0:c1])
+
+
+def make_workload(scale, rank):
+    from paper_1805_00106_gb300 import synth
+    return synth.workload("c2", scale=scale, seed=rank * 1009)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = make_workload(args.scale, 0)
+    total = 0.0
+    cells = 0.0
+    reads = 0
+    for step in range(args.warmup + args.steps):
+        cb = cpu_baseline(w, max(1.0, args.cpu_seconds / max(1, args.steps)))
+        if step >= args.warmup:
+            total += cb["seconds"]
+            cells += cb["cells"]
+            reads += cb["reads"]
+    v = cells / total / 1e9
+    line = {"impl": "reference", "metric": "SW GCUPS", "value": round(v, 4), "unit": "GCUPS",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "bounded read prefix per step"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GCUPS", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": round(v, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "reads_per_s": round(reads / total, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_1805_00106_gb300 import sr
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    w = make_workload(args.scale, rank)
+    n_reads = len(w["read_off"]) - 1
+    n_items = int(w["cand_off"][-1])
+    sess = sr.Session.open([bytes(r) for r in w["refs"]])
+    spp = sr.score_params(*SP)
+    if args.tune:
+        sr.lib().sr_tune(sess.h, sr.C.byref(spp), 4096)
+    stream = torch.cuda.Stream()
+    batch = sess.stage(w["bases"], w["read_off"], w["cand_off"], w["c_ref"], w["c_strand"],
+                       w["c_start"], w["c_len"], stream=stream.cuda_stream)
+    opts = sr.align_opts(stream=stream.cuda_stream)
+    cells = float(batch.stats()["cells"])
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        batch.run(spp, opts)
+    kernels_per_step = batch.stats()["kernels"]
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ext_ms, tb_ms, tot_ms = [], [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.run_async(spp, opts)
+        batch.sync()
+        t, x, tb = batch.timing()
+        tot_ms.append(t)
+        ext_ms.append(x)
+        tb_ms.append(tb)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = cells * ws * args.steps / elapsed / 1e9
+    reads_per_s = n_reads * ws * args.steps / elapsed
+
+    # dominant kernel: the extension kernels (a5), timed by events on their stream
+    ext = statistics.mean(ext_ms) / 1e3
+    dpx_rate, probe_mhz = sr.probe_dpx()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    f_mhz = clk["sm_mhz"] if clk else probe_mhz
+    peak_gcups = n_sm * f_mhz * 1e6 * dpx_rate * 2 / (2 * OPS_PER_CELL) / 1e9
+    achieved = cells / ext / 1e9
+    traffic = traffic_per_launch(cells)
+    roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak_gcups, 2),
+                "unit": "GCUPS", "frac": round(achieved / peak_gcups, 4), "traffic": traffic,
+                "kernel": "k_extend16 (all length bins) + k_extend32",
+                "peak_basis": f"{n_sm} SMs x {f_mhz:.0f} MHz (median under load) x "
+                              f"{dpx_rate:.1f} packed-16-bit DPX lane-ops/clk/SM (measured) x 2 cells / "
+                              f"{2 * OPS_PER_CELL} ops",
+                "traceback_ms": round(statistics.mean(tb_ms), 3),
+                "extension_ms": round(1e3 * ext, 3)}
+
+    line = {"metric": "SW GCUPS (whole device path, batched engine)", "value": round(value, 3),
+            "unit": "GCUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * elapsed / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16x2 (int32 promotion)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reads": n_reads, "windows": n_items, "cells": cells,
+                       "engine": "batched (length bins, LPT persistent kernels, one CUDA graph)",
+                       "l2": "inputs larger than L2 (no flush)", "scale": args.scale},
+            "reads_per_s": round(reads_per_s, 1),
+            "gcups_without_traceback": round(cells / (statistics.mean(tot_ms) - statistics.mean(tb_ms)) * 1e3 / 1e9, 3),
+            "gpu_launches": int(kernels_per_step * args.steps),
+            "roofline": roofline, "clocks": clk}
+
+    if rank == 0 and not args.no_plain:
+        popts = sr.align_opts(engine=sr.ENGINE_PLAIN, stream=stream.cuda_stream)
+        batch.run(spp, popts)
+        pt = []
+        pe = []
+        for _ in range(max(2, min(args.steps, 3))):
+            batch.run(spp, popts)
+            t, x, _ = batch.timing()
+            pt.append(t)
+            pe.append(x)
+        line["plain"] = {"value": round(cells / (statistics.mean(pt) / 1e3) / 1e9, 3), "unit": "GCUPS",
+                         "ms_per_step": round(statistics.mean(pt), 3),
+                         "extension_gcups": round(cells / (statistics.mean(pe) / 1e3) / 1e9, 3),
+                         "engine": "one ordinary launch per batch, 16 lanes x 16 rows, input order"}
+    if rank == 0 and not args.no_e2e:
+        # end to end through sr_align_batch: pinned host inputs, H2D + path + D2H per step
+        pin = {}
+        for k in ["bases", "read_off", "cand_off", "c_ref", "c_strand", "c_start", "c_len"]:
+            a = np.ascontiguousarray(w[k])
+            dt = {np.dtype(np.int64): np.uint64, np.dtype(np.int32): np.uint32}.get(a.dtype, a.dtype)
+            if k in ("read_off", "cand_off", "c_start"):
+                dt = np.uint64
+            if k == "c_len":
+                dt = np.uint32
+            a = a.astype(dt)
+            t = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True)
+            t.numpy()[:] = a.view(np.uint8)
+            pin[k] = (t, t.numpy().view(dt))
+        h2d = sum(v[1].nbytes for v in pin.values())
+        ee = []
+        res = None
+        for i in range(3):
+            t0 = time.perf_counter()
+            res = sess.align(*[pin[k][1] for k in ["bases", "read_off", "cand_off", "c_ref", "c_strand",
+                                                  "c_start", "c_len"]], spp, sr.align_opts())
+            ee.append(time.perf_counter() - t0)
+        d2h = (res["item_score"].nbytes + res["item_end"].nbytes + res["best"].nbytes +
+               res["best_per_ref"].nbytes + res["cigar"].nbytes + 4 * (n_reads + 1))
+        e2e_t = statistics.median(ee[1:])
+        line["e2e"] = {"value": round(cells / e2e_t / 1e9, 3), "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h), "ms_per_step": round(1e3 * e2e_t, 2),
+                       "reads_per_s": round(n_reads / e2e_t, 1)}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(w, args.cpu_seconds).items()
+                                if k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

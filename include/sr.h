@@ -1,0 +1,294 @@
+/*
+ * sr.h -- C ABI of libsr, a GB300 (sm_103a) short-read extension library.
+ *
+ * It implements the data-parallel hot path of the seed-and-extend aligner of
+ * McVicar et al., "FPGA Acceleration of Short Read Alignment" (arXiv 1805.00106):
+ * affine-gap Smith-Waterman scoring of every read against the reference window
+ * of each candidate alignment location (CAL, Sec. 3.5), per-read best /
+ * second-best / tie tracking (Sec. 3.6, 4.2), traceback to a CIGAR for the
+ * winner (Sec. 4.2, 6.4) and classification of each read between two
+ * references by score (Sec. 6.1, 6.2, 6.4).  The k-mer index and CAL
+ * finder/filter (Sec. 3.1-3.3, 4.1-4.2) are a host stage.
+ *
+ * Conventions
+ *  - Every call returns sr_status (SR_OK = 0, negative on error); no C++
+ *    exception crosses this boundary.  sr_last_error() returns a thread-local
+ *    message for the last failure on the calling thread.
+ *  - Bases are ASCII A/C/G/T (either case).  Any other byte is SR_EBADBASE.
+ *    The 2-bit code is A=0, C=1, G=2, T=3 (Sec. 3.1, Fig. 3).
+ *  - Inputs are caller-owned and only read during the call (sr_submit copies
+ *    them).  Objects returned through an `out` pointer are owned by the caller
+ *    and released with the matching sr_*_free / sr_*_close.
+ *  - Scores: match +match, mismatch -mismatch, a gap of k bases costs
+ *    gap_open + k*gap_extend (Sec. 3.5; the paper leaves the constants open).
+ *  - Positions are 0-based on the forward strand of the reference; read
+ *    coordinates (read_start/read_end, 1-based) refer to the read as aligned,
+ *    i.e. reverse-complemented for '-' strand windows (Sec. 3.1 strand bit).
+ *  - All device work runs in libsr's own CUDA kernels on the current CUDA
+ *    device; no CPU fallback exists.  A build without a usable GPU returns
+ *    SR_ECUDA from every call that needs one.
+ */
+#ifndef SR_H
+#define SR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sr_status;
+enum {
+  SR_OK = 0,
+  SR_EINVAL = -1,   /* bad argument, size or parameter */
+  SR_ENOMEM = -2,   /* host or device allocation failed, or HBM budget exceeded */
+  SR_ECUDA = -3,    /* CUDA runtime error (message in sr_last_error) */
+  SR_EBADBASE = -4, /* a read or reference byte is not A/C/G/T */
+  SR_ETIMEOUT = -5, /* a bounded wait ran out (sr_wait, device queue poll) */
+  SR_EBUSY = -6,    /* resource in use (e.g. serving queue full) */
+  SR_EIO = -7       /* file I/O or format error */
+};
+
+#define SR_MAX_READ_LEN 256u /* longest read the device path accepts */
+#define SR_MAX_WIN_LEN 512u  /* longest reference window */
+#define SR_MAX_REFS 16u      /* references per session */
+#define SR_CIGAR_STRIDE 776u /* CIGAR words reserved per read (>= 3*256+4 runs) */
+
+const char* sr_last_error(void);
+const char* sr_version(void);
+
+/* ------------------------------------------------------------------ index
+ * Pointer table + CAL table over the canonical (lexicographically smaller of a
+ * k-mer and its reverse complement) seeds of every reference position (Sec. 3.1,
+ * 4.1).  The whole seed is put through an invertible hash; the top
+ * 2*address_bases bits address the pointer table, the rest is the key stored in
+ * the CAL table (Sec. 3.1).  Canonical seeds occurring more than cal_limit times
+ * are dropped (0 = no limit; Sec. 4.1, Table 5).
+ * seed_len in [4, 32]; address_bases in [1, min(seed_len, 14)] and
+ * 2*(seed_len - address_bases) <= 32.  n_threads 0 = all host cores. */
+typedef struct sr_index sr_index;
+typedef struct {
+  uint32_t seed_len;      /* default 20 */
+  uint32_t address_bases; /* default 12 */
+  uint32_t cal_limit;     /* 0 = unlimited */
+  uint32_t n_threads;     /* 0 = hardware concurrency */
+  uint64_t hash_seed;     /* mixes the invertible seed hash */
+} sr_index_params;
+
+/* Build from `len` ASCII bases (copied).  Errors: SR_EINVAL (params), SR_EBADBASE,
+ * SR_ENOMEM. */
+sr_status sr_index_build(const char* seq, uint64_t len, const sr_index_params* params,
+                         sr_index** out);
+/* Flat binary file: header (magic, params, sizes), tables, packed reference,
+ * checksum.  Errors: SR_EIO. */
+sr_status sr_index_save(const sr_index* idx, const char* path);
+sr_status sr_index_load(const char* path, sr_index** out);
+void sr_index_free(sr_index* idx);
+/* Reference length and number of CAL-table entries. */
+sr_status sr_index_info(const sr_index* idx, uint64_t* ref_len, uint64_t* n_entries);
+
+/* ------------------------------------------------------------------ reads
+ * CSR batch of reads: read r is bases[offsets[r] .. offsets[r+1]). */
+typedef struct {
+  uint32_t n_reads;
+  uint32_t reserved;
+  const char* bases;
+  const uint64_t* offsets; /* n_reads + 1 entries, offsets[0] = 0 */
+} sr_reads;
+
+/* ------------------------------------------------------------- candidates
+ * CAL finder + filter (Sec. 3.2, 3.3).  Seeds start at 0, seed_stride,
+ * 2*seed_stride, ... (1 = overlapping, seed_len = non-overlapping).  A hit at
+ * reference position p from the seed at read offset o gives a '+' CAL p - o when
+ * the reference k-mer equals the seed, a '-' CAL p - (m - o - k) when it equals
+ * the seed's reverse complement.  CALs of one (ref, strand) whose consecutive
+ * values differ by <= merge_dist merge into one, represented by the CAL value
+ * hit by the most seeds (smallest on ties).  Each merged CAL becomes the window
+ * [cal - pad, cal + m + pad) clamped to the reference.  With max_cands > 0 only
+ * the max_cands windows with the most seed hits are kept (ties: ref, strand,
+ * cal ascending).  Windows are listed per read by (ref, strand, cal). */
+typedef struct {
+  uint32_t seed_stride; /* default 1 */
+  uint32_t merge_dist;  /* default 32 */
+  uint32_t pad;         /* default 32 */
+  uint32_t max_cands;   /* 0 = all */
+  uint32_t n_threads;   /* 0 = hardware concurrency */
+} sr_cand_params;
+
+typedef struct {
+  uint32_t n_reads;
+  uint32_t reserved;
+  uint64_t n_cands;
+  uint64_t* offsets;  /* n_reads + 1: read r owns windows offsets[r] .. offsets[r+1] */
+  uint8_t* ref_id;    /* reference index per window */
+  uint8_t* strand;    /* 0 = '+', 1 = '-' (read is reverse-complemented) */
+  uint64_t* win_start;
+  uint32_t* win_len;  /* 1 .. SR_MAX_WIN_LEN */
+  uint32_t* hits;     /* seed hits merged into the window (may be NULL on input) */
+} sr_cand_list;
+
+/* idx[0..n_refs) are the references' indexes (same seed_len).  Errors:
+ * SR_EINVAL, SR_EBADBASE (read bytes), SR_ENOMEM. */
+sr_status sr_candidates(const sr_index* const* idx, uint32_t n_refs, const sr_reads* reads,
+                        const sr_cand_params* params, sr_cand_list** out);
+/* Allocate an empty list the caller fills (for windows chosen elsewhere). */
+sr_status sr_cand_list_alloc(uint32_t n_reads, uint64_t n_cands, sr_cand_list** out);
+void sr_cand_list_free(sr_cand_list* list);
+
+/* ---------------------------------------------------------------- scoring */
+typedef struct {
+  int32_t match, mismatch, gap_open, gap_extend;
+} sr_score_params;
+
+/* Readout (Sec. 3.5): 0 = best cell anywhere (local alignment, default);
+ * 1 = best cell of the read's final row. */
+enum { SR_MODE_LOCAL = 0, SR_MODE_FINAL_ROW = 1 };
+/* Engines: BATCHED = length-binned, LPT-ordered persistent kernels replayed as
+ * one CUDA graph (default); PLAIN = one ordinary launch per batch over the items
+ * in input order, one fixed kernel shape. */
+enum { SR_ENGINE_BATCHED = 0, SR_ENGINE_PLAIN = 1 };
+
+typedef struct {
+  uint32_t mode;        /* SR_MODE_* */
+  uint32_t engine;      /* SR_ENGINE_* */
+  uint32_t want_cigar;  /* 1 = trace back each read's winner */
+  uint32_t classify;    /* 1 = classify each read between references 0 and 1 */
+  int32_t min_score;    /* classification certainty threshold (default 40) */
+  int32_t margin;       /* classification score margin (default 5) */
+  uint32_t force_i32;   /* 1 = use the int32 kernel for every item */
+  uint32_t lanes;       /* 0 = auto; else lanes per alignment (1,2,4,8,16,32) */
+  uint32_t rows;        /* 0 = auto; else read rows per lane */
+  uint32_t reserved;
+  void* cuda_stream;    /* cudaStream_t to run on; NULL = the library's stream */
+} sr_align_opts;
+
+/* One reported alignment.  For a read without any positive-scoring window,
+ * score = 0, item = -1 and the other fields are 0. */
+typedef struct {
+  int32_t score;      /* best score */
+  int32_t second;     /* best score at a different (ref, end, strand) */
+  uint32_t n_ties;    /* distinct (ref, end, strand) reaching `score` */
+  int32_t item;       /* winning window (global candidate index), -1 = none */
+  uint8_t ref_id, strand;
+  uint16_t reserved;
+  int32_t read_start, read_end; /* 1-based on the aligned read (winner only) */
+  uint64_t ref_start, ref_end;  /* 0-based inclusive on the reference */
+  uint32_t cigar_off, cigar_len; /* into sr_results.cigar (winner only) */
+} sr_hit;
+
+enum { SR_CLASS_UNALIGNED = 0, SR_CLASS_A = 1, SR_CLASS_B = 2, SR_CLASS_AMBIGUOUS = 3 };
+
+typedef struct {
+  uint32_t n_reads, n_refs;
+  uint64_t n_items;
+  sr_hit* best;          /* n_reads: the read's winner over all references */
+  sr_hit* best_per_ref;  /* n_reads * n_refs: per reference (score, second,
+                            n_ties, item, strand, ref_end; no CIGAR) */
+  int32_t* item_score;   /* n_items: score of every (read, window) item */
+  uint32_t* item_end;    /* n_items: 1-based window column of the end cell, 0 if score 0 */
+  uint32_t* cigar;       /* BAM-style words (len << 4 | op), M=0 I=1 D=2 S=4 */
+  uint64_t n_cigar;
+  uint8_t* read_class;   /* n_reads, SR_CLASS_* (NULL unless classified) */
+  uint64_t cells;        /* DP cells of all items (sum of m*n) */
+  uint64_t n_i32_items;  /* items scored by the int32 kernel */
+} sr_results;
+
+void sr_results_free(sr_results* res);
+
+/* -------------------------------------------------------------- session
+ * A session keeps the references 2-bit packed in device memory (packed by a
+ * kernel) for as long as it is open.  hbm_budget bounds the device bytes the
+ * session may hold for batches and serving (0 = no limit). */
+typedef struct sr_session sr_session;
+sr_status sr_session_open(const sr_index* const* refs, uint32_t n_refs, uint64_t hbm_budget,
+                          sr_session** out);
+sr_status sr_session_open_seqs(const char* const* seqs, const uint64_t* lens, uint32_t n_refs,
+                               uint64_t hbm_budget, sr_session** out);
+void sr_session_close(sr_session* s);
+
+/* Whole batch, host buffers in and out: stage (host->device), run, fetch
+ * (device->host).  Errors: SR_EINVAL (shapes, windows past the reference,
+ * read or window too long, parameters), SR_EBADBASE, SR_ENOMEM, SR_ECUDA. */
+sr_status sr_align_batch(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                         const sr_score_params* sp, const sr_align_opts* opts, sr_results** out);
+
+/* The same in three steps, so the device part can be timed and repeated with
+ * inputs resident in HBM.  stage copies inputs to device buffers (no kernels);
+ * run enqueues every kernel of the path on the stream (pack, work list and
+ * bins, extension, per-read selection, traceback, classification) and waits
+ * for it; run_async only enqueues (check with sr_batch_sync); fetch copies the
+ * results back. */
+typedef struct sr_batch sr_batch;
+sr_status sr_batch_stage(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                         void* cuda_stream, sr_batch** out);
+sr_status sr_batch_run(sr_session* s, sr_batch* b, const sr_score_params* sp,
+                       const sr_align_opts* opts);
+sr_status sr_batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp,
+                             const sr_align_opts* opts);
+sr_status sr_batch_sync(sr_session* s, sr_batch* b);
+sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out);
+void sr_batch_free(sr_batch* b);
+/* Device-side statistics of the last run: kernels launched, cells, items per
+ * kernel variant.  Any pointer may be NULL. */
+sr_status sr_batch_stats(const sr_batch* b, uint64_t* kernels, uint64_t* cells,
+                         uint64_t* i32_items, uint64_t* tasks);
+
+/* Device time of the last run of a batch, from CUDA events recorded on the
+ * launching stream (inside the replayed graph): the whole path, the extension
+ * kernels alone, the traceback + CIGAR kernels.  Call after sr_batch_sync /
+ * sr_batch_run.  Any pointer may be NULL. */
+sr_status sr_batch_timing(const sr_batch* b, float* total_ms, float* extend_ms, float* traceback_ms);
+
+/* Re-classify a batch that has run, on the device, with other thresholds
+ * (Sec. 6.4); class_out (n_reads bytes, caller-owned) receives SR_CLASS_*. */
+typedef struct {
+  int32_t min_score; /* default 40 */
+  int32_t margin;    /* default 5; 1 = the paper's exact-tie rule */
+} sr_classify_params;
+sr_status sr_classify(sr_session* s, sr_batch* b, const sr_classify_params* params,
+                      uint8_t* class_out);
+
+/* -------------------------------------------------------------- serving
+ * Continuous batching: sr_submit copies a request and returns a ticket at once;
+ * a scheduler thread admits requests while their device footprint fits the
+ * session's hbm_budget, merges every admitted request into the next device
+ * round (copies of the next round overlap the current one), and completes each
+ * request as soon as its round finishes.  sr_wait blocks up to timeout_ms
+ * (< 0 = forever) and returns SR_ETIMEOUT when the limit runs out.  A request
+ * larger than the whole budget is rejected with SR_ENOMEM. */
+sr_status sr_serve_start(sr_session* s, const sr_score_params* sp, const sr_align_opts* opts,
+                         uint32_t max_inflight_requests);
+sr_status sr_submit(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                    uint64_t* ticket);
+sr_status sr_wait(sr_session* s, uint64_t ticket, int32_t timeout_ms, sr_results** out);
+/* Latency of completed requests, submit to completion, in microseconds:
+ * p50, p99, count; rounds run and the largest number of requests in a round. */
+sr_status sr_serve_stats(sr_session* s, double* p50_us, double* p99_us, uint64_t* completed,
+                         uint64_t* rounds, uint64_t* max_round_requests);
+sr_status sr_serve_stop(sr_session* s);
+
+/* ------------------------------------------------------------ autotuner
+ * Measures candidate kernel shapes (lanes per alignment x rows per lane) for
+ * each read-length bin on a synthetic sample on the current GPU and keeps the
+ * fastest; the table is used by SR_ENGINE_BATCHED.  save/load use a small text
+ * file keyed by device name.  sr_tune_get writes up to cap entries of
+ * (bin upper read length, lanes, rows). */
+sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t sample_reads);
+sr_status sr_tune_save(const char* path);
+sr_status sr_tune_load(const char* path);
+sr_status sr_tune_get(uint32_t* n_bins, uint32_t* upper, uint32_t* lanes, uint32_t* rows,
+                      uint32_t cap);
+sr_status sr_tune_set(uint32_t n_bins, const uint32_t* upper, const uint32_t* lanes,
+                      const uint32_t* rows);
+
+/* ------------------------------------------------------- measurement
+ * Issue-rate probe of the packed 16-bit DPX max/add-max instructions: returns
+ * lane-operations per clock per SM measured with CUDA events (and the clock
+ * attribute), used as the integer roofline denominator. */
+sr_status sr_probe_dpx(double* lane_ops_per_clk_per_sm, double* sm_clock_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SR_H */

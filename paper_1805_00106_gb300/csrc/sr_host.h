@@ -1,0 +1,14 @@
+// sr_host.h -- helpers shared by libsr's host translation units.
+#pragma once
+#include <stdint.h>
+
+#include "../../include/sr.h"
+
+namespace sr {
+// records a thread-local message for sr_last_error() and returns `st`
+sr_status set_error(sr_status st, const char* fmt, ...);
+// ASCII bases -> 2-bit codes (A=0 C=1 G=2 T=3); -1 on a non-ACGT byte
+int encode_ascii(const char* s, uint64_t n, uint8_t* out);
+// the index's reference as 2-bit codes
+const uint8_t* index_codes(const sr_index* idx, uint64_t* len);
+}  // namespace sr

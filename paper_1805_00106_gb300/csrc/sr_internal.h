@@ -1,0 +1,116 @@
+// sr_internal.h -- device data layout and kernel launchers shared inside libsr.
+//
+// Layout in HBM (all buffers 256-byte aligned by cudaMalloc):
+//   reference k : uint32 words, 16 bases per word, base p in bits 2*(p&15)..+1 of
+//                 word p>>4 (A=0 C=1 G=2 T=3, Sec. 3.1 Fig. 3 codes), followed by
+//                 >= 64 bytes of padding so 16-byte TMA copies of any window stay
+//                 inside the allocation;
+//   reads       : one 64-byte row per read (16 words = 256 bases), same packing;
+//   items       : one per (read, window) candidate, structure of arrays indexed
+//                 by the global candidate index.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sr {
+
+constexpr int kMaxReadLen = 256;
+constexpr int kMaxWinLen = 512;
+constexpr int kMaxRefs = 16;
+constexpr int kReadWords = 16;     // words per packed read row
+constexpr int kCigarStride = 776;  // CIGAR words reserved per read (>= 3*256 + 4 runs)
+constexpr int kNumBins = 8;        // read-length bins of the batched engine
+constexpr int kNumClasses = kNumBins + 1;  // + the int32 class
+constexpr int kI32Class = kNumBins;
+constexpr int kKeysPerClass = kMaxWinLen;  // sort key = class*512 + (512 - n)
+constexpr int kNumKeys = kNumClasses * kKeysPerClass;
+constexpr int kBias = 1024;        // bias of packed 16-bit DP values (keeps halves >= 0)
+
+// status word bits (device -> host)
+enum : uint32_t {
+  kStBadBase = 1u << 0,
+  kStBadRead = 1u << 1,    // read length 0 or > kMaxReadLen
+  kStBadWindow = 1u << 2,  // window outside its reference / bad ref id / length
+  kStTimeout = 1u << 3,    // a bounded wait (TMA mbarrier) ran out
+  kStOverflow = 1u << 4,   // int16 guard tripped (never expected: routing is exact)
+  kStInternal = 1u << 5,
+};
+
+struct DevRefs {
+  const uint32_t* words[kMaxRefs];
+  uint64_t len[kMaxRefs];
+  int n;
+};
+
+struct ScoreConst {
+  int32_t sa, sb, go, ge;
+};
+
+// per-read result slot (device); index read * (1 + n_refs) + (0 = overall, 1 + r = ref r)
+struct DevHit {
+  int32_t score, second;
+  uint32_t n_ties;
+  int32_t item;
+  int32_t read_start, read_end;  // winner only (1-based rows of the aligned read)
+  uint32_t start_j, cigar_len;   // winner only: 1-based first window column, CIGAR words
+};
+
+struct BatchDev {
+  // staged inputs
+  const char* bases = nullptr;
+  const uint64_t* read_off = nullptr;
+  const uint64_t* cand_off = nullptr;
+  const uint8_t* c_ref = nullptr;
+  const uint8_t* c_strand = nullptr;
+  const uint64_t* c_start = nullptr;
+  const uint32_t* c_len = nullptr;
+  uint32_t n_reads = 0;
+  uint64_t n_items = 0;
+  // derived
+  uint32_t* rpack = nullptr;      // n_reads * 16
+  uint32_t* rlen = nullptr;       // n_reads
+  uint32_t* item_read = nullptr;  // n_items
+  uint16_t* item_key = nullptr;   // n_items
+  uint32_t* order = nullptr;      // n_items, sorted by key
+  uint32_t* hist = nullptr;       // kNumKeys
+  uint32_t* cursor = nullptr;     // kNumKeys
+  uint32_t* class_range = nullptr;  // 2 * kNumClasses
+  uint32_t* queue = nullptr;      // kNumClasses + 8 counters
+  unsigned long long* cells = nullptr;  // 1 counter
+  uint32_t* status = nullptr;     // 1 word
+  // outputs
+  int32_t* item_score = nullptr;
+  uint32_t* item_end = nullptr;
+  DevHit* hits = nullptr;         // n_reads * (1 + n_refs)
+  uint32_t* cigar_slots = nullptr;  // n_reads * kCigarStride
+  uint32_t* cigar_off = nullptr;  // n_reads + 1 (exclusive scan of lengths)
+  uint32_t* cigar = nullptr;      // compacted, n_reads * kCigarStride capacity
+  uint8_t* read_class = nullptr;  // n_reads
+  uint32_t* scan_tmp = nullptr;   // block sums for scans
+};
+
+struct TuneBin {
+  uint32_t upper;  // largest read length in the bin
+  uint32_t lanes;  // G: lanes per alignment (power of two)
+  uint32_t rows;   // R: read rows per lane
+};
+
+// launchers (each returns the number of kernels it enqueued, or -1 on error)
+int launch_pack_refs(const char* ascii, uint64_t len, uint32_t* words, uint32_t* status,
+                     cudaStream_t st);
+int launch_prepare(const BatchDev& b, const DevRefs& refs, cudaStream_t st);
+int launch_bins(const BatchDev& b, const ScoreConst& sc, const TuneBin* bins, int n_bins,
+                bool force_i32, bool plain, cudaStream_t st);
+int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
+                  const TuneBin* bins, int n_bins, int mode, bool plain, uint32_t lanes,
+                  uint32_t rows, cudaStream_t st);
+int launch_select(const BatchDev& b, int n_refs, cudaStream_t st);
+int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, int mode,
+                     int n_refs, cudaStream_t st);
+int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);
+int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,
+                    cudaStream_t st);
+bool extend_config_supported(uint32_t lanes, uint32_t rows);
+int probe_dpx(double* lane_ops_per_clk_per_sm, double* clk_mhz);
+
+}  // namespace sr

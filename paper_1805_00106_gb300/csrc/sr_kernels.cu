@@ -1,0 +1,394 @@
+// sr_kernels.cu -- the non-DP kernels of the path: 2-bit packing (Sec. 3.1,
+// Fig. 3), work list + length bins, per-read score tracker (Sec. 3.6, 4.2),
+// classification (Sec. 6.1-6.4) and CIGAR compaction.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sr_internal.h"
+
+namespace sr {
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+// ASCII -> 2-bit code (A=0 C=1 G=2 T=3, either case); returns 4 for anything else
+__device__ __forceinline__ uint32_t ascii_code(uint32_t ch) {
+  const uint32_t c = ch | 0x20u;
+  const bool ok = c == 'a' || c == 'c' || c == 'g' || c == 't';
+  return ok ? (((c >> 1) ^ (c >> 2)) & 3u) : 4u;
+}
+
+// one thread per 16-base word of the reference; `words` has room for the padding
+__global__ void k_pack_ref(const char* ascii, uint64_t len, uint64_t n_words_alloc, uint32_t* words,
+                           uint32_t* status) {
+  for (uint64_t w = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; w < n_words_alloc;
+       w += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    uint32_t v = 0;
+    bool bad = false;
+    const uint64_t p0 = w * 16;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      if (p0 + b < len) {
+        uint32_t c = ascii_code(static_cast<uint8_t>(ascii[p0 + b]));
+        bad |= c > 3u;
+        v |= (c & 3u) << (2 * b);
+      }
+    }
+    words[w] = v;
+    if (bad) atomicOr(status, kStBadBase);
+  }
+}
+
+// 16 threads per read, one packed word each; validates length and bases
+__global__ void k_pack_reads(const char* bases, const uint64_t* off, uint32_t n_reads,
+                             uint32_t* rpack, uint32_t* rlen, uint32_t* status) {
+  const uint64_t gt = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  const uint64_t r = gt >> 4;
+  const uint32_t w = static_cast<uint32_t>(gt & 15u);
+  if (r >= n_reads) return;
+  const uint64_t o0 = off[r], o1 = off[r + 1];
+  const uint64_t m = o1 - o0;
+  const bool len_ok = o1 > o0 && m <= static_cast<uint64_t>(kMaxReadLen);
+  uint32_t v = 0;
+  bool bad = false;
+  if (len_ok) {
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      const uint64_t p = static_cast<uint64_t>(w) * 16 + b;
+      if (p < m) {
+        uint32_t c = ascii_code(static_cast<uint8_t>(bases[o0 + p]));
+        bad |= c > 3u;
+        v |= (c & 3u) << (2 * b);
+      }
+    }
+  }
+  rpack[r * kReadWords + w] = v;
+  if (w == 0) {
+    rlen[r] = len_ok ? static_cast<uint32_t>(m) : 0u;
+    if (!len_ok) atomicOr(status, kStBadRead);
+  }
+  if (bad) atomicOr(status, kStBadBase);
+}
+
+// warp per read: item -> read map and window validation
+__global__ void k_items(const uint64_t* cand_off, uint32_t n_reads, const uint8_t* c_ref,
+                        const uint8_t* c_strand, const uint64_t* c_start, const uint32_t* c_len,
+                        DevRefs refs, uint32_t* item_read, uint32_t* status) {
+  const uint64_t r = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n_reads) return;
+  const uint64_t c0 = cand_off[r], c1 = cand_off[r + 1];
+  bool bad = c1 < c0;
+  for (uint64_t c = c0 + lane; c < c1 && !bad; c += 32) {
+    item_read[c] = static_cast<uint32_t>(r);
+    const uint32_t k = c_ref[c];
+    const uint32_t n = c_len[c];
+    bool ok = k < static_cast<uint32_t>(refs.n) && c_strand[c] <= 1u && n >= 1u &&
+              n <= static_cast<uint32_t>(kMaxWinLen);
+    if (ok) ok = c_start[c] + n <= refs.len[k];
+    bad |= !ok;
+  }
+  if (bad) atomicOr(status, kStBadWindow);
+}
+
+struct BinArgs {
+  uint8_t cls_of_len[kMaxReadLen + 1];  // read length -> class (kI32Class for int32 items)
+};
+
+// sort key per item: class * 512 + (512 - n); shared-memory histogram
+__global__ void k_keys(const uint32_t* item_read, const uint32_t* rlen, const uint32_t* c_len,
+                       uint64_t n_items, BinArgs ba, uint16_t* item_key, uint32_t* hist) {
+  __shared__ uint32_t sh[kNumKeys];
+  for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x) sh[k] = 0;
+  __syncthreads();
+  for (uint64_t c = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; c < n_items;
+       c += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const uint32_t m = min(rlen[item_read[c]], static_cast<uint32_t>(kMaxReadLen));
+    const uint32_t n = min(max(c_len[c], 1u), static_cast<uint32_t>(kMaxWinLen));
+    const uint32_t key = static_cast<uint32_t>(ba.cls_of_len[m]) * kKeysPerClass + (kMaxWinLen - n);
+    item_key[c] = static_cast<uint16_t>(key);
+    atomicAdd(&sh[key], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kNumKeys; k += blockDim.x)
+    if (sh[k]) atomicAdd(&hist[k], sh[k]);
+}
+
+// one block: exclusive scan of the histogram -> cursor, class ranges
+__global__ void k_scan_keys(const uint32_t* hist, uint32_t* cursor, uint32_t* class_range) {
+  __shared__ uint32_t part[1024];
+  constexpr int per = (kNumKeys + 1023) / 1024;
+  const int t = threadIdx.x;
+  uint32_t loc[per];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < per; ++i) {
+    const int k = t * per + i;
+    loc[i] = k < kNumKeys ? hist[k] : 0u;
+    sum += loc[i];
+  }
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    uint32_t v = t >= off ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[t] - sum;
+#pragma unroll
+  for (int i = 0; i < per; ++i) {
+    const int k = t * per + i;
+    if (k < kNumKeys) {
+      cursor[k] = run;
+      if (k % kKeysPerClass == 0) class_range[2 * (k / kKeysPerClass)] = run;
+      if (k % kKeysPerClass == kKeysPerClass - 1) class_range[2 * (k / kKeysPerClass) + 1] = run + loc[i];
+    }
+    run += loc[i];
+  }
+}
+
+// scatter items into key order; warp-aggregated atomics per equal key
+__global__ void k_scatter(const uint16_t* item_key, uint64_t n_items, uint32_t* cursor,
+                          uint32_t* order) {
+  const uint64_t c = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  const bool live = c < n_items;
+  const uint32_t key = live ? item_key[c] : 0xffffffffu;
+  const uint32_t act = __ballot_sync(FULL, live);
+  if (!live) return;
+  const uint32_t peers = __match_any_sync(act, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&cursor[key], static_cast<uint32_t>(__popc(peers)));
+  base = __shfl_sync(peers, base, leader);
+  const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+  order[base + rank] = static_cast<uint32_t>(c);
+}
+
+// ---- per-read tracker (Sec. 3.6, 4.2): winner, second best, ties, per reference
+__device__ __forceinline__ unsigned long long wmin64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long x = __shfl_xor_sync(FULL, v, o);
+    v = x < v ? x : v;
+  }
+  return v;
+}
+
+__global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32_t* item_score,
+                         const uint32_t* item_end, const uint8_t* c_ref, const uint8_t* c_strand,
+                         const uint64_t* c_start, int n_refs, DevHit* hits) {
+  const uint64_t r = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n_reads) return;
+  const uint64_t c0 = cand_off[r], c1 = cand_off[r + 1];
+  const int slots = 1 + n_refs;
+  for (int f = -1; f < n_refs; ++f) {
+    // best score
+    int32_t best = 0;
+    for (uint64_t c = c0 + lane; c < c1; c += 32) {
+      if (f >= 0 && c_ref[c] != f) continue;
+      best = max(best, item_score[c]);
+    }
+    best = __reduce_max_sync(FULL, best);
+    DevHit h{};
+    h.item = -1;
+    if (best > 0) {
+      // winner: smallest (ref, global end, strand, candidate index) among the best
+      unsigned long long wk = ~0ull;
+      for (uint64_t c = c0 + lane; c < c1; c += 32) {
+        if ((f >= 0 && c_ref[c] != f) || item_score[c] != best) continue;
+        const unsigned long long gend = c_start[c] + item_end[c] - 1;
+        const unsigned long long k = (static_cast<unsigned long long>(c_ref[c]) << 60) |
+                                     (gend << 20) |
+                                     (static_cast<unsigned long long>(c_strand[c]) << 19) |
+                                     static_cast<unsigned long long>(c - c0);
+        wk = k < wk ? k : wk;
+      }
+      wk = wmin64(wk);
+      const uint64_t wc = c0 + (wk & 0x7ffffull);
+      const uint32_t wref = c_ref[wc], wstr = c_strand[wc];
+      const unsigned long long wend = c_start[wc] + item_end[wc] - 1;
+      int32_t second = 0;
+      uint32_t ties = 0;
+      for (uint64_t c = c0 + lane; c < c1; c += 32) {
+        if (f >= 0 && c_ref[c] != f) continue;
+        const int32_t s = item_score[c];
+        if (s <= 0) continue;
+        const unsigned long long ge = c_start[c] + item_end[c] - 1;
+        const bool same = c_ref[c] == wref && ge == wend && c_strand[c] == wstr;
+        if (!same) second = max(second, s);
+        if (s == best) {
+          bool seen = false;
+          for (uint64_t u = c0; u < c && !seen; ++u) {
+            if (f >= 0 && c_ref[u] != f) continue;
+            seen = item_score[u] == best && c_ref[u] == c_ref[c] && c_strand[u] == c_strand[c] &&
+                   c_start[u] + item_end[u] - 1 == ge;
+          }
+          ties += seen ? 0u : 1u;
+        }
+      }
+      h.score = best;
+      h.second = __reduce_max_sync(FULL, second);
+      h.n_ties = __reduce_add_sync(FULL, ties);
+      h.item = static_cast<int32_t>(wc);
+    }
+    if (lane == 0) hits[r * slots + (f + 1)] = h;
+  }
+}
+
+__global__ void k_classify(uint32_t n_reads, int n_refs, const DevHit* hits, int32_t min_score,
+                           int32_t margin, uint8_t* cls) {
+  const uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (r >= n_reads) return;
+  const int slots = 1 + n_refs;
+  const int32_t a = n_refs > 0 ? hits[r * slots + 1].score : 0;
+  const int32_t b = n_refs > 1 ? hits[r * slots + 2].score : 0;
+  uint8_t c;
+  if (max(a, b) < min_score) c = 0;
+  else if (b < min_score) c = 1;
+  else if (a < min_score) c = 2;
+  else if (a - b >= margin) c = 1;
+  else if (b - a >= margin) c = 2;
+  else c = 3;
+  cls[r] = c;
+}
+
+// ---- CIGAR compaction: exclusive scan of per-read lengths, then gather
+__global__ void k_scan_block(const DevHit* hits, int slots, uint32_t n, uint32_t* out,
+                             uint32_t* block_sums) {
+  __shared__ uint32_t sh[1024];
+  const uint32_t i = blockIdx.x * 1024u + threadIdx.x;
+  const uint32_t v = i < n ? hits[static_cast<uint64_t>(i) * slots].cigar_len : 0u;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    uint32_t x = threadIdx.x >= static_cast<unsigned>(off) ? sh[threadIdx.x - off] : 0u;
+    __syncthreads();
+    sh[threadIdx.x] += x;
+    __syncthreads();
+  }
+  if (i < n) out[i] = sh[threadIdx.x] - v;
+  if (threadIdx.x == 1023) block_sums[blockIdx.x] = sh[1023];
+}
+
+__global__ void k_scan_sums(uint32_t* block_sums, uint32_t nb, uint32_t* total_out) {
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  __shared__ uint32_t sh[1024];
+  for (uint32_t base = 0; base < nb; base += 1024) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < nb ? block_sums[i] : 0u;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      uint32_t x = threadIdx.x >= static_cast<unsigned>(off) ? sh[threadIdx.x - off] : 0u;
+      __syncthreads();
+      sh[threadIdx.x] += x;
+      __syncthreads();
+    }
+    if (i < nb) block_sums[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_cigar_gather(const DevHit* hits, int slots, uint32_t n, const uint32_t* block_sums,
+                               uint32_t* off, const uint32_t* slots_buf, uint32_t* cigar) {
+  const uint32_t r = blockIdx.x * static_cast<uint32_t>(blockDim.x) + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t o = off[r] + block_sums[r >> 10];
+  off[r] = o;
+  const uint32_t len = hits[static_cast<uint64_t>(r) * slots].cigar_len;
+  const uint32_t* src = slots_buf + static_cast<uint64_t>(r) * kCigarStride;
+  for (uint32_t k = 0; k < len; ++k) cigar[o + k] = src[k];
+}
+
+}  // namespace
+
+int launch_pack_refs(const char* ascii, uint64_t len, uint32_t* words, uint32_t* status,
+                     cudaStream_t st) {
+  const uint64_t nw = ((len + 63) / 64) * 4 + 16;
+  const int threads = 256;
+  const uint64_t blocks = (nw + threads - 1) / threads;
+  k_pack_ref<<<static_cast<unsigned>(blocks < 65535 * 16 ? blocks : 65535 * 16), threads, 0, st>>>(
+      ascii, len, nw, words, status);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_prepare(const BatchDev& b, const DevRefs& refs, cudaStream_t st) {
+  if (b.n_reads == 0) return 0;
+  const uint64_t t = static_cast<uint64_t>(b.n_reads) * 16;
+  k_pack_reads<<<static_cast<unsigned>((t + 255) / 256), 256, 0, st>>>(
+      b.bases, b.read_off, b.n_reads, b.rpack, b.rlen, b.status);
+  const uint64_t tw = static_cast<uint64_t>(b.n_reads) * 32;
+  k_items<<<static_cast<unsigned>((tw + 255) / 256), 256, 0, st>>>(
+      b.cand_off, b.n_reads, b.c_ref, b.c_strand, b.c_start, b.c_len, refs, b.item_read, b.status);
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
+}
+
+int launch_bins(const BatchDev& b, const ScoreConst& sc, const TuneBin* bins, int n_bins,
+                bool force_i32, bool plain, cudaStream_t st) {
+  if (plain || b.n_items == 0) return 0;
+  BinArgs ba;
+  const int32_t goe = sc.go + sc.ge;
+  const bool tables_fit = sc.sa + goe <= 127 && goe - sc.sb >= -128 && goe + sc.ge + 256 < kBias;
+  for (int m = 0; m <= kMaxReadLen; ++m) {
+    int c = n_bins - 1;
+    for (int k = 0; k < n_bins; ++k)
+      if (static_cast<uint32_t>(m) <= bins[k].upper) {
+        c = k;
+        break;
+      }
+    const bool i16_ok = tables_fit && static_cast<int64_t>(sc.sa) * m <= 32767 - kBias;
+    ba.cls_of_len[m] = static_cast<uint8_t>((force_i32 || !i16_ok) ? kI32Class : c);
+  }
+  cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * kNumKeys, st);
+  cudaMemsetAsync(b.queue, 0, sizeof(uint32_t) * (kNumClasses + 8), st);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t blocks_needed = (b.n_items + 1023) / 1024;
+  const unsigned kb = static_cast<unsigned>(blocks_needed < static_cast<uint64_t>(nsm) * 4
+                                                ? blocks_needed
+                                                : static_cast<uint64_t>(nsm) * 4);
+  k_keys<<<kb, 1024, 0, st>>>(b.item_read, b.rlen, b.c_len, b.n_items, ba, b.item_key, b.hist);
+  k_scan_keys<<<1, 1024, 0, st>>>(b.hist, b.cursor, b.class_range);
+  k_scatter<<<static_cast<unsigned>((b.n_items + 255) / 256), 256, 0, st>>>(b.item_key, b.n_items,
+                                                                            b.cursor, b.order);
+  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
+}
+
+int launch_select(const BatchDev& b, int n_refs, cudaStream_t st) {
+  if (b.n_reads == 0) return 0;
+  const uint64_t t = static_cast<uint64_t>(b.n_reads) * 32;
+  k_select<<<static_cast<unsigned>((t + 255) / 256), 256, 0, st>>>(
+      b.cand_off, b.n_reads, b.item_score, b.item_end, b.c_ref, b.c_strand, b.c_start, n_refs,
+      b.hits);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,
+                    cudaStream_t st) {
+  if (b.n_reads == 0) return 0;
+  k_classify<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, n_refs, b.hits, min_score, margin,
+                                                      b.read_class);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st) {
+  if (b.n_reads == 0) return 0;
+  const int slots = 1 + n_refs;
+  const uint32_t nb = (b.n_reads + 1023) / 1024;
+  k_scan_block<<<nb, 1024, 0, st>>>(b.hits, slots, b.n_reads, b.cigar_off, b.scan_tmp);
+  k_scan_sums<<<1, 1024, 0, st>>>(b.scan_tmp, nb, b.cigar_off + b.n_reads);
+  k_cigar_gather<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.hits, slots, b.n_reads, b.scan_tmp,
+                                                          b.cigar_off, b.cigar_slots, b.cigar);
+  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
+}
+
+}  // namespace sr

@@ -1,0 +1,415 @@
+// sr_serve.cpp -- continuous batching for libsr.
+//
+// Requests (a read batch plus its candidate windows) are copied at submit and
+// queued.  One scheduler thread runs a two-deep pipeline: while round k runs
+// on one CUDA stream, it admits every queued request whose device footprint
+// still fits the session's HBM budget (FIFO, bounded by max_inflight), merges
+// them into round k+1 and stages its inputs on the other stream; then it
+// collects round k, splits the merged results back per request (item and
+// CIGAR indices rebased) and completes those requests, freeing their budget.
+// Each read's result depends only on that read and its windows, so a request
+// gets identical results alone or in any mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "sr_serve.h"
+
+namespace sr {
+namespace {
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  std::vector<char> bases;
+  std::vector<uint64_t> roff, coff, cstart;
+  std::vector<uint8_t> cref, cstr;
+  std::vector<uint32_t> clen;
+  uint64_t bytes = 0, cells = 0;
+  Clock::time_point t_submit, t_done;
+  sr_results* res = nullptr;
+  sr_status status = SR_OK;
+  bool done = false;
+};
+
+struct Round {
+  std::vector<Request*> reqs;
+  sr_batch* b = nullptr;
+  sr_status status = SR_OK;
+};
+
+}  // namespace
+
+struct Server {
+  sr_session* s = nullptr;
+  int device = 0;
+  sr_score_params sp{};
+  sr_align_opts opts{};
+  uint32_t max_inflight = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> pending;
+  std::map<uint64_t, Request*> all;
+  uint64_t next_ticket = 1;
+  uint64_t reserved = 0;
+  uint64_t inflight = 0;
+  bool stop = false;
+  std::thread th;
+  std::vector<double> lat_us;
+  uint64_t rounds = 0, max_round = 0;
+  cudaStream_t streams[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+sr_results* slice_results(const sr_results* all, uint32_t r0, uint32_t r1, uint64_t i0, uint64_t i1,
+                          uint64_t cells) {
+  const uint32_t n = r1 - r0, nr = all->n_refs;
+  const uint64_t ni = i1 - i0;
+  auto* r = static_cast<sr_results*>(calloc(1, sizeof(sr_results)));
+  if (!r) return nullptr;
+  r->n_reads = n;
+  r->n_refs = nr;
+  r->n_items = ni;
+  r->cells = cells;
+  r->best = static_cast<sr_hit*>(malloc((n ? n : 1) * sizeof(sr_hit)));
+  r->best_per_ref = static_cast<sr_hit*>(malloc(static_cast<size_t>(n ? n : 1) * nr * sizeof(sr_hit)));
+  r->item_score = static_cast<int32_t*>(malloc((ni ? ni : 1) * 4));
+  r->item_end = static_cast<uint32_t*>(malloc((ni ? ni : 1) * 4));
+  uint64_t cw0 = 0, cw1 = 0;
+  if (all->cigar) {
+    for (uint32_t k = r0; k < r1; ++k)
+      if (all->best[k].cigar_len) {
+        cw0 = all->best[k].cigar_off;
+        break;
+      }
+    cw1 = cw0;
+    for (uint32_t k = r0; k < r1; ++k)
+      if (all->best[k].cigar_len) cw1 = all->best[k].cigar_off + all->best[k].cigar_len;
+    r->n_cigar = cw1 - cw0;
+    r->cigar = static_cast<uint32_t*>(malloc((r->n_cigar ? r->n_cigar : 1) * 4));
+    if (r->cigar && r->n_cigar) memcpy(r->cigar, all->cigar + cw0, r->n_cigar * 4);
+  }
+  if (all->read_class) {
+    r->read_class = static_cast<uint8_t*>(malloc(n ? n : 1));
+    if (r->read_class && n) memcpy(r->read_class, all->read_class + r0, n);
+  }
+  if (!r->best || !r->best_per_ref || !r->item_score || !r->item_end || (all->cigar && !r->cigar) ||
+      (all->read_class && !r->read_class)) {
+    sr_results_free(r);
+    return nullptr;
+  }
+  auto fix = [&](sr_hit h, bool with_cigar) {
+    if (h.item >= 0) h.item -= static_cast<int32_t>(i0);
+    if (with_cigar && h.cigar_len) h.cigar_off -= static_cast<uint32_t>(cw0);
+    else if (!h.cigar_len) h.cigar_off = 0;
+    return h;
+  };
+  for (uint32_t k = 0; k < n; ++k) {
+    r->best[k] = fix(all->best[r0 + k], true);
+    for (uint32_t q = 0; q < nr; ++q)
+      r->best_per_ref[static_cast<size_t>(k) * nr + q] = fix(all->best_per_ref[static_cast<size_t>(r0 + k) * nr + q], false);
+  }
+  if (ni) {
+    memcpy(r->item_score, all->item_score + i0, ni * 4);
+    memcpy(r->item_end, all->item_end + i0, ni * 4);
+  }
+  return r;
+}
+
+void finish(Server* sv, Round& rd, sr_results* merged) {
+  uint32_t r0 = 0;
+  uint64_t i0 = 0;
+  const auto now = Clock::now();
+  std::vector<std::pair<Request*, sr_results*>> outs;
+  for (Request* q : rd.reqs) {
+    const uint32_t n = static_cast<uint32_t>(q->roff.size() - 1);
+    const uint64_t ni = q->coff.back();
+    sr_results* part = nullptr;
+    if (rd.status == SR_OK && merged) part = slice_results(merged, r0, r0 + n, i0, i0 + ni, q->cells);
+    outs.emplace_back(q, part);
+    r0 += n;
+    i0 += ni;
+  }
+  std::lock_guard<std::mutex> g(sv->mu);
+  for (auto& o : outs) {
+    Request* q = o.first;
+    q->res = o.second;
+    q->status = rd.status != SR_OK ? rd.status : (o.second ? SR_OK : SR_ENOMEM);
+    q->t_done = now;
+    q->done = true;
+    sv->reserved -= q->bytes;
+    --sv->inflight;
+    sv->lat_us.push_back(std::chrono::duration<double, std::micro>(now - q->t_submit).count());
+  }
+  sv->cv_done.notify_all();
+  sv->cv_work.notify_all();
+}
+
+sr_batch* stage_round(Server* sv, Round& rd, int stream_idx) {
+  uint32_t n = 0;
+  uint64_t nb = 0, ni = 0;
+  for (Request* q : rd.reqs) {
+    n += static_cast<uint32_t>(q->roff.size() - 1);
+    nb += q->roff.back();
+    ni += q->coff.back();
+  }
+  std::vector<char> bases(nb ? nb : 1);
+  std::vector<uint64_t> roff(n + 1ull), coff(n + 1ull), cstart(ni ? ni : 1);
+  std::vector<uint8_t> cref(ni ? ni : 1), cstr(ni ? ni : 1);
+  std::vector<uint32_t> clen(ni ? ni : 1);
+  uint32_t r = 0;
+  uint64_t ob = 0, oi = 0;
+  for (Request* q : rd.reqs) {
+    const uint32_t qn = static_cast<uint32_t>(q->roff.size() - 1);
+    if (q->roff.back()) memcpy(bases.data() + ob, q->bases.data(), q->roff.back());
+    for (uint32_t k = 0; k < qn; ++k) {
+      roff[r + k] = ob + q->roff[k];
+      coff[r + k] = oi + q->coff[k];
+    }
+    const uint64_t qi = q->coff.back();
+    if (qi) {
+      memcpy(cstart.data() + oi, q->cstart.data(), qi * 8);
+      memcpy(cref.data() + oi, q->cref.data(), qi);
+      memcpy(cstr.data() + oi, q->cstr.data(), qi);
+      memcpy(clen.data() + oi, q->clen.data(), qi * 4);
+    }
+    r += qn;
+    ob += q->roff.back();
+    oi += qi;
+  }
+  roff[n] = ob;
+  coff[n] = oi;
+  sr_reads reads{n, 0, bases.data(), roff.data()};
+  sr_cand_list cl{};
+  cl.n_reads = n;
+  cl.n_cands = ni;
+  cl.offsets = coff.data();
+  cl.ref_id = cref.data();
+  cl.strand = cstr.data();
+  cl.win_start = cstart.data();
+  cl.win_len = clen.data();
+  sr_batch* b = nullptr;
+  rd.status = batch_stage_internal(sv->s, &reads, &cl, sv->streams[stream_idx], false, &b);
+  return rd.status == SR_OK ? b : nullptr;
+}
+
+void scheduler(Server* sv) {
+  cudaSetDevice(sv->device);
+  Round running;
+  int next_stream = 0;
+  for (;;) {
+    Round next;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      if (!running.b) sv->cv_work.wait(lk, [&] { return sv->stop || !sv->pending.empty(); });
+      if (sv->stop && sv->pending.empty() && !running.b) break;
+      const uint64_t budget = session_budget(sv->s);
+      while (!sv->pending.empty()) {
+        Request* q = sv->pending.front();
+        if (budget && sv->reserved + q->bytes > budget) break;
+        if (sv->max_inflight && sv->inflight >= sv->max_inflight) break;
+        sv->pending.pop_front();
+        sv->reserved += q->bytes;
+        ++sv->inflight;
+        next.reqs.push_back(q);
+      }
+    }
+    if (!next.reqs.empty()) next.b = stage_round(sv, next, next_stream);  // overlaps `running`
+    if (running.b || !running.reqs.empty()) {
+      sr_results* merged = nullptr;
+      if (running.status == SR_OK) running.status = sr_batch_fetch(sv->s, running.b, &merged);
+      finish(sv, running, merged);
+      sr_results_free(merged);
+      sr_batch_free(running.b);
+      running = Round();
+    }
+    if (!next.reqs.empty()) {
+      if (next.status == SR_OK) {
+        sr_align_opts o = sv->opts;
+        o.cuda_stream = sv->streams[next_stream];
+        next.status = sr_batch_run_async(sv->s, next.b, &sv->sp, &o);
+      }
+      {
+        std::lock_guard<std::mutex> g(sv->mu);
+        ++sv->rounds;
+        sv->max_round = std::max<uint64_t>(sv->max_round, next.reqs.size());
+      }
+      if (next.status != SR_OK) {
+        finish(sv, next, nullptr);
+        sr_batch_free(next.b);
+      } else {
+        running = next;
+        next_stream ^= 1;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+void serve_destroy(Server* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv_work.notify_all();
+  if (sv->th.joinable()) sv->th.join();
+  for (auto& kv : sv->all) {
+    sr_results_free(kv.second->res);
+    delete kv.second;
+  }
+  for (auto st : sv->streams)
+    if (st) cudaStreamDestroy(st);
+  delete sv;
+}
+
+}  // namespace sr
+
+using namespace sr;
+
+extern "C" sr_status sr_serve_start(sr_session* s, const sr_score_params* sp, const sr_align_opts* opts,
+                                    uint32_t max_inflight_requests) {
+  if (!s || !sp) return set_error(SR_EINVAL, "sr_serve_start: null argument");
+  if (session_server(s)) return set_error(SR_EBUSY, "sr_serve_start: already serving");
+  auto* sv = new Server;
+  sv->s = s;
+  cudaGetDevice(&sv->device);
+  sv->sp = *sp;
+  if (opts) {
+    sv->opts = *opts;
+  } else {
+    sv->opts.want_cigar = 1;
+    sv->opts.min_score = 40;
+    sv->opts.margin = 5;
+  }
+  sv->max_inflight = max_inflight_requests;
+  for (auto& st : sv->streams) {
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      serve_destroy(sv);
+      return set_error(SR_ECUDA, "sr_serve_start: stream creation failed");
+    }
+  }
+  session_server(s) = sv;
+  sv->th = std::thread(scheduler, sv);
+  return SR_OK;
+}
+
+extern "C" sr_status sr_serve_stop(sr_session* s) {
+  if (!s) return set_error(SR_EINVAL, "sr_serve_stop: null session");
+  Server* sv = session_server(s);
+  if (!sv) return SR_OK;
+  serve_destroy(sv);
+  session_server(s) = nullptr;
+  return SR_OK;
+}
+
+extern "C" sr_status sr_submit(sr_session* s, const sr_reads* reads, const sr_cand_list* cands, uint64_t* ticket) {
+  if (!s || !reads || !cands || !ticket) return set_error(SR_EINVAL, "sr_submit: null argument");
+  Server* sv = session_server(s);
+  if (!sv) return set_error(SR_EINVAL, "sr_submit: call sr_serve_start first");
+  const uint32_t n = reads->n_reads;
+  if (cands->n_reads != n) return set_error(SR_EINVAL, "sr_submit: reads and candidates differ in n_reads");
+  if (n && (!reads->offsets || !reads->bases || !cands->offsets)) return set_error(SR_EINVAL, "sr_submit: null arrays");
+  auto* q = new Request;
+  q->roff.assign(reads->offsets, reads->offsets + n + 1);
+  q->coff.assign(cands->offsets, cands->offsets + n + 1);
+  if (n == 0) {
+    q->roff.assign(1, 0);
+    q->coff.assign(1, 0);
+  }
+  if (q->roff[0] != 0 || q->coff[0] != 0 || q->coff.back() != cands->n_cands) {
+    delete q;
+    return set_error(SR_EINVAL, "sr_submit: bad offsets");
+  }
+  for (uint32_t r = 0; r < n; ++r)
+    if (q->roff[r + 1] < q->roff[r] || q->coff[r + 1] < q->coff[r]) {
+      delete q;
+      return set_error(SR_EINVAL, "sr_submit: decreasing offsets");
+    }
+  const uint64_t nb = q->roff.back(), ni = q->coff.back();
+  q->bases.assign(reads->bases, reads->bases + nb);
+  if (ni) {
+    q->cstart.assign(cands->win_start, cands->win_start + ni);
+    q->cref.assign(cands->ref_id, cands->ref_id + ni);
+    q->cstr.assign(cands->strand, cands->strand + ni);
+    q->clen.assign(cands->win_len, cands->win_len + ni);
+  }
+  for (uint32_t r = 0; r < n; ++r)
+    for (uint64_t k = q->coff[r]; k < q->coff[r + 1]; ++k) q->cells += (q->roff[r + 1] - q->roff[r]) * q->clen[k];
+  q->bytes = batch_bytes_estimate(n, ni, nb, session_n_refs(s));
+  const uint64_t budget = session_budget(s);
+  if (budget && q->bytes > budget) {
+    delete q;
+    return set_error(SR_ENOMEM, "sr_submit: request needs more than the whole HBM budget");
+  }
+  q->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    q->ticket = sv->next_ticket++;
+    sv->all[q->ticket] = q;
+    sv->pending.push_back(q);
+  }
+  sv->cv_work.notify_all();
+  *ticket = q->ticket;
+  return SR_OK;
+}
+
+extern "C" sr_status sr_wait(sr_session* s, uint64_t ticket, int32_t timeout_ms, sr_results** out) {
+  if (!s || !out) return set_error(SR_EINVAL, "sr_wait: null argument");
+  *out = nullptr;
+  Server* sv = session_server(s);
+  if (!sv) return set_error(SR_EINVAL, "sr_wait: not serving");
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->all.find(ticket);
+  if (it == sv->all.end()) return set_error(SR_EINVAL, "sr_wait: unknown ticket");
+  Request* q = it->second;
+  auto ready = [&] { return q->done; };
+  if (timeout_ms < 0) {
+    sv->cv_done.wait(lk, ready);
+  } else if (!sv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+    return set_error(SR_ETIMEOUT, "sr_wait: request not finished within %d ms", timeout_ms);
+  }
+  sv->all.erase(it);
+  sr_status st = q->status;
+  *out = q->res;
+  q->res = nullptr;
+  lk.unlock();
+  delete q;
+  if (st != SR_OK) return set_error(st, "sr_wait: request failed (status %d)", st);
+  return SR_OK;
+}
+
+extern "C" sr_status sr_serve_stats(sr_session* s, double* p50_us, double* p99_us, uint64_t* completed,
+                                    uint64_t* rounds, uint64_t* max_round_requests) {
+  if (!s) return set_error(SR_EINVAL, "sr_serve_stats: null session");
+  Server* sv = session_server(s);
+  if (!sv) return set_error(SR_EINVAL, "sr_serve_stats: not serving");
+  std::vector<double> v;
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    v = sv->lat_us;
+    if (rounds) *rounds = sv->rounds;
+    if (max_round_requests) *max_round_requests = sv->max_round;
+  }
+  std::sort(v.begin(), v.end());
+  auto pct = [&](double p) {
+    if (v.empty()) return 0.0;
+    size_t k = static_cast<size_t>(p * (v.size() - 1) + 0.5);
+    return v[std::min(k, v.size() - 1)];
+  };
+  if (p50_us) *p50_us = pct(0.50);
+  if (p99_us) *p99_us = pct(0.99);
+  if (completed) *completed = v.size();
+  return SR_OK;
+}

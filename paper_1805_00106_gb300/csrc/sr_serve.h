@@ -1,0 +1,20 @@
+// sr_serve.h -- continuous-batching request server of libsr (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "sr_host.h"
+
+namespace sr {
+struct Server;
+void serve_destroy(Server* sv);  // stops the scheduler and frees the server
+uint64_t batch_bytes_estimate(uint32_t n_reads, uint64_t n_items, uint64_t n_bases, uint32_t n_refs);
+cudaStream_t session_stream(sr_session* s);
+uint64_t session_budget(sr_session* s);
+std::atomic<uint64_t>& session_used(sr_session* s);
+Server*& session_server(sr_session* s);
+uint32_t session_n_refs(sr_session* s);
+sr_status batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                               void* stream, bool check_budget, sr_batch** out);
+}  // namespace sr

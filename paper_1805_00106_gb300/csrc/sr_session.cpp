@@ -1,0 +1,942 @@
+// sr_session.cpp -- sessions (device-resident references), batches (staging,
+// the device pipeline as one CUDA graph, fetch), classification, the
+// autotuner table and the C ABI glue of libsr.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sr_host.h"
+#include "sr_internal.h"
+#include "sr_serve.h"
+
+namespace sr {
+
+static thread_local std::string g_err;
+
+sr_status set_error(sr_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+static sr_status cuda_error(const char* where, cudaError_t e) {
+  return set_error(SR_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// ---- autotuner table (read-length bins -> kernel shape)
+static std::mutex g_tune_mu;
+static TuneBin g_bins[kNumBins] = {{64, 4, 16},   {80, 8, 10},   {96, 8, 12},   {128, 8, 16},
+                                   {160, 16, 10}, {192, 16, 12}, {224, 16, 14}, {256, 16, 16}};
+
+void tune_get_bins(TuneBin* out) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  memcpy(out, g_bins, sizeof(g_bins));
+}
+void tune_set_bins(const TuneBin* in) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  memcpy(g_bins, in, sizeof(g_bins));
+}
+
+static sr_status check_score(const sr_score_params* sp) {
+  if (!sp) return set_error(SR_EINVAL, "null score params");
+  const int lim = 1 << 20;
+  if (sp->match < 1 || sp->mismatch < 1 || sp->gap_open < 0 || sp->gap_extend < 1 ||
+      sp->match > lim || sp->mismatch > lim || sp->gap_open > lim || sp->gap_extend > lim)
+    return set_error(SR_EINVAL,
+                     "score params: need match >= 1, mismatch >= 1, gap_open >= 0, gap_extend >= 1, each <= 2^20");
+  return SR_OK;
+}
+
+static sr_align_opts default_opts() {
+  sr_align_opts o{};
+  o.mode = SR_MODE_LOCAL;
+  o.engine = SR_ENGINE_BATCHED;
+  o.want_cigar = 1;
+  o.classify = 0;
+  o.min_score = 40;
+  o.margin = 5;
+  return o;
+}
+
+}  // namespace sr
+
+using namespace sr;
+
+struct sr_session {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  uint32_t n_refs = 0;
+  std::vector<uint32_t*> d_words;
+  std::vector<uint64_t> lens;
+  DevRefs refs{};
+  uint64_t hbm_budget = 0;
+  std::atomic<uint64_t> hbm_used{0};
+  Server* server = nullptr;
+};
+
+struct sr_batch {
+  sr_session* s = nullptr;
+  cudaStream_t stream = nullptr;
+  BatchDev d{};
+  void* arena = nullptr;
+  uint64_t bytes = 0;
+  uint32_t n_reads = 0;
+  uint64_t n_items = 0;
+  uint64_t cells = 0;
+  std::vector<uint64_t> h_cstart;
+  std::vector<uint8_t> h_cref, h_cstrand;
+  std::vector<uint16_t> h_item_m;  // read length of each item
+  uint32_t max_m = 0;
+  cudaGraphExec_t graph = nullptr;
+  sr_score_params g_sp{};
+  sr_align_opts g_opts{};
+  TuneBin g_bins[kNumBins]{};
+  uint64_t kernels = 0;
+  uint64_t i32_items = 0;
+  bool ran = false;
+  sr_align_opts last_opts{};
+  cudaEvent_t ev[6] = {};  // around: whole path, extension kernels, traceback
+};
+
+extern "C" const char* sr_last_error(void) { return g_err.c_str(); }
+extern "C" const char* sr_version(void) { return "libsr 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------ session
+static sr_status open_common(const uint8_t* const* codes, const char* const* ascii,
+                             const uint64_t* lens, uint32_t n_refs, uint64_t budget,
+                             sr_session** out) {
+  if (!out || n_refs == 0 || n_refs > SR_MAX_REFS) return set_error(SR_EINVAL, "session: 1..16 references");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) return set_error(SR_ECUDA, "session: no CUDA device available");
+  auto* s = new sr_session;
+  cudaGetDevice(&s->device);
+  e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_error("session stream", e);
+  }
+  s->hbm_budget = budget;
+  s->n_refs = n_refs;
+  uint32_t* d_status = nullptr;
+  e = cudaMalloc(&d_status, 4);
+  if (e != cudaSuccess) {
+    sr_session_close(s);
+    return cuda_error("session status", e);
+  }
+  cudaMemsetAsync(d_status, 0, 4, s->stream);
+  for (uint32_t r = 0; r < n_refs; ++r) {
+    const uint64_t len = lens[r];
+    if (len == 0 || len >= (1ull << 40)) {
+      cudaFree(d_status);
+      sr_session_close(s);
+      return set_error(SR_EINVAL, "session: reference length out of range");
+    }
+    const uint64_t nw = ((len + 63) / 64) * 4 + 16;
+    uint32_t* w = nullptr;
+    e = cudaMalloc(&w, nw * 4);
+    if (e != cudaSuccess) {
+      cudaFree(d_status);
+      sr_session_close(s);
+      return cuda_error("session reference", e);
+    }
+    s->d_words.push_back(w);
+    s->lens.push_back(len);
+    // upload ASCII in chunks and pack on the device (a1)
+    const uint64_t chunk = 1ull << 28;  // 256 MiB, a multiple of 64 bases
+    char* d_ascii = nullptr;
+    e = cudaMalloc(&d_ascii, std::min(len, chunk));
+    if (e != cudaSuccess) {
+      cudaFree(d_status);
+      sr_session_close(s);
+      return cuda_error("session staging", e);
+    }
+    std::vector<char> tmp;
+    for (uint64_t off = 0; off < len; off += chunk) {
+      const uint64_t n = std::min(chunk, len - off);
+      const char* src;
+      if (ascii) {
+        src = ascii[r] + off;
+      } else {
+        tmp.resize(n);
+        static const char L[4] = {'A', 'C', 'G', 'T'};
+        for (uint64_t i = 0; i < n; ++i) tmp[i] = L[codes[r][off + i] & 3];
+        src = tmp.data();
+      }
+      e = cudaMemcpyAsync(d_ascii, src, n, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess && launch_pack_refs(d_ascii, n, w + off / 16, d_status, s->stream) < 0)
+        e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) break;
+    }
+    cudaFree(d_ascii);
+    if (e != cudaSuccess) {
+      cudaFree(d_status);
+      sr_session_close(s);
+      return cuda_error("session pack", e);
+    }
+    s->refs.words[r] = w;
+    s->refs.len[r] = len;
+  }
+  s->refs.n = static_cast<int>(n_refs);
+  uint32_t st = 0;
+  cudaMemcpy(&st, d_status, 4, cudaMemcpyDeviceToHost);
+  cudaFree(d_status);
+  if (st & kStBadBase) {
+    sr_session_close(s);
+    return set_error(SR_EBADBASE, "session: reference has a non-ACGT base");
+  }
+  *out = s;
+  return SR_OK;
+}
+
+extern "C" sr_status sr_session_open(const sr_index* const* refs, uint32_t n_refs, uint64_t hbm_budget,
+                                     sr_session** out) {
+  if (!refs) return set_error(SR_EINVAL, "sr_session_open: null refs");
+  std::vector<const uint8_t*> codes(n_refs);
+  std::vector<uint64_t> lens(n_refs);
+  for (uint32_t r = 0; r < n_refs; ++r) {
+    if (!refs[r]) return set_error(SR_EINVAL, "sr_session_open: null index");
+    codes[r] = index_codes(refs[r], &lens[r]);
+  }
+  return open_common(codes.data(), nullptr, lens.data(), n_refs, hbm_budget, out);
+}
+
+extern "C" sr_status sr_session_open_seqs(const char* const* seqs, const uint64_t* lens, uint32_t n_refs,
+                                          uint64_t hbm_budget, sr_session** out) {
+  if (!seqs || !lens) return set_error(SR_EINVAL, "sr_session_open_seqs: null argument");
+  return open_common(nullptr, seqs, lens, n_refs, hbm_budget, out);
+}
+
+extern "C" void sr_session_close(sr_session* s) {
+  if (!s) return;
+  if (s->server) {
+    serve_destroy(s->server);
+    s->server = nullptr;
+  }
+  for (auto* w : s->d_words) cudaFree(w);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+namespace sr {
+cudaStream_t session_stream(sr_session* s) { return s->stream; }
+uint64_t session_budget(sr_session* s) { return s->hbm_budget; }
+std::atomic<uint64_t>& session_used(sr_session* s) { return s->hbm_used; }
+Server*& session_server(sr_session* s) { return s->server; }
+uint32_t session_n_refs(sr_session* s) { return s->n_refs; }
+}  // namespace sr
+
+// ------------------------------------------------------------------ batches
+namespace {
+
+struct Carve {
+  uint64_t off = 0;
+  template <class T>
+  void take(T*& p, uint64_t count) {
+    off = (off + 255) & ~255ull;
+    p = reinterpret_cast<T*>(off);
+    off += (count ? count : 1) * sizeof(T);
+  }
+};
+
+template <class T>
+void rebase(T*& p, char* base) {
+  p = reinterpret_cast<T*>(base + reinterpret_cast<uint64_t>(p));
+}
+template <class T>
+void rebase_c(const T*& p, char* base) {
+  p = reinterpret_cast<const T*>(base + reinterpret_cast<uint64_t>(p));
+}
+
+}  // namespace
+
+namespace sr {
+uint64_t batch_bytes_estimate(uint32_t n_reads, uint64_t n_items, uint64_t n_bases, uint32_t n_refs) {
+  Carve c;
+  char* p1;
+  uint64_t* p8;
+  uint32_t* p4;
+  uint16_t* p2;
+  DevHit* ph;
+  c.take(p1, n_bases);
+  c.take(p8, n_reads + 1ull);
+  c.take(p8, n_reads + 1ull);
+  c.take(p1, n_items);
+  c.take(p1, n_items);
+  c.take(p8, n_items);
+  c.take(p4, n_items);
+  c.take(p4, n_reads * 16ull);
+  c.take(p4, n_reads);
+  c.take(p4, n_items);
+  c.take(p2, n_items);
+  c.take(p4, n_items);
+  c.take(p4, kNumKeys);
+  c.take(p4, kNumKeys);
+  c.take(p4, 2 * kNumClasses);
+  c.take(p4, kNumClasses + 8);
+  c.take(p4, 4);
+  c.take(p4, n_items);
+  c.take(p4, n_items);
+  c.take(ph, static_cast<uint64_t>(n_reads) * (1 + n_refs));
+  c.take(p4, static_cast<uint64_t>(n_reads) * kCigarStride);
+  c.take(p4, n_reads + 1ull);
+  c.take(p4, static_cast<uint64_t>(n_reads) * kCigarStride);
+  c.take(p1, n_reads);
+  c.take(p4, n_reads / 1024 + 4ull);
+  return c.off + 256;
+}
+}  // namespace sr
+
+extern "C" sr_status sr_batch_stage(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                                    void* cuda_stream, sr_batch** out) {
+  return batch_stage_internal(s, reads, cands, cuda_stream, true, out);
+}
+
+sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                                   void* cuda_stream, bool check_budget, sr_batch** out) {
+  if (!s || !reads || !cands || !out) return set_error(SR_EINVAL, "sr_batch_stage: null argument");
+  *out = nullptr;
+  const uint32_t n = reads->n_reads;
+  if (cands->n_reads != n) return set_error(SR_EINVAL, "sr_batch_stage: reads and candidates differ in n_reads");
+  if (n > (8u << 20)) return set_error(SR_EINVAL, "sr_batch_stage: more than 8M reads in one batch");
+  if (n && (!reads->offsets || !reads->bases || !cands->offsets))
+    return set_error(SR_EINVAL, "sr_batch_stage: null arrays");
+  const uint64_t nb = n ? reads->offsets[n] : 0;
+  const uint64_t nc = n ? cands->offsets[n] : 0;
+  if (n && (reads->offsets[0] != 0 || cands->offsets[0] != 0))
+    return set_error(SR_EINVAL, "sr_batch_stage: offsets must start at 0");
+  if (nc != cands->n_cands) return set_error(SR_EINVAL, "sr_batch_stage: n_cands != offsets[n_reads]");
+  if (nc >= (1ull << 32)) return set_error(SR_EINVAL, "sr_batch_stage: too many windows");
+  if (nc && (!cands->ref_id || !cands->strand || !cands->win_start || !cands->win_len))
+    return set_error(SR_EINVAL, "sr_batch_stage: null candidate arrays");
+  // host-side validation: every kernel relies on these bounds (window copies,
+  // shared-memory column streams, packed read rows)
+  for (uint32_t r = 0; r < n; ++r) {
+    if (reads->offsets[r + 1] < reads->offsets[r] || cands->offsets[r + 1] < cands->offsets[r])
+      return set_error(SR_EINVAL, "sr_batch_stage: decreasing offsets");
+    const uint64_t m = reads->offsets[r + 1] - reads->offsets[r];
+    if (m == 0 || m > SR_MAX_READ_LEN)
+      return set_error(SR_EINVAL, "sr_batch_stage: read %u has length %llu, must be 1..256", r,
+                       static_cast<unsigned long long>(m));
+    if (cands->offsets[r + 1] - cands->offsets[r] >= (1ull << 19))
+      return set_error(SR_EINVAL, "sr_batch_stage: read %u has more than 2^19-1 windows", r);
+  }
+  for (uint64_t k = 0; k < nc; ++k) {
+    const uint32_t ref = cands->ref_id[k], len = cands->win_len[k];
+    if (ref >= s->n_refs || cands->strand[k] > 1 || len < 1 || len > SR_MAX_WIN_LEN ||
+        cands->win_start[k] > s->lens[ref] || cands->win_start[k] + len > s->lens[ref])
+      return set_error(SR_EINVAL, "sr_batch_stage: window %llu is outside its reference or malformed",
+                       static_cast<unsigned long long>(k));
+  }
+  const uint64_t bytes = batch_bytes_estimate(n, nc, nb, s->n_refs);
+  if (check_budget && s->hbm_budget && s->hbm_used.load() + bytes > s->hbm_budget)
+    return set_error(SR_ENOMEM, "sr_batch_stage: batch needs %llu bytes, over the HBM budget",
+                     static_cast<unsigned long long>(bytes));
+  auto* b = new sr_batch;
+  b->s = s;
+  b->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : s->stream;
+  b->n_reads = n;
+  b->n_items = nc;
+  Carve c;
+  BatchDev& d = b->d;
+  char* p1;
+  c.take(p1, nb);
+  d.bases = p1;
+  uint64_t* p8;
+  c.take(p8, n + 1ull);
+  d.read_off = p8;
+  c.take(p8, n + 1ull);
+  d.cand_off = p8;
+  uint8_t* pu8;
+  c.take(pu8, nc);
+  d.c_ref = pu8;
+  c.take(pu8, nc);
+  d.c_strand = pu8;
+  c.take(p8, nc);
+  d.c_start = p8;
+  uint32_t* p4;
+  c.take(p4, nc);
+  d.c_len = p4;
+  c.take(d.rpack, n * 16ull);
+  c.take(d.rlen, n);
+  c.take(d.item_read, nc);
+  c.take(d.item_key, nc);
+  c.take(d.order, nc);
+  c.take(d.hist, kNumKeys);
+  c.take(d.cursor, kNumKeys);
+  c.take(d.class_range, 2 * kNumClasses);
+  c.take(d.queue, kNumClasses + 8);
+  c.take(d.status, 4);
+  c.take(d.item_score, nc);
+  c.take(d.item_end, nc);
+  c.take(d.hits, static_cast<uint64_t>(n) * (1 + s->n_refs));
+  c.take(d.cigar_slots, static_cast<uint64_t>(n) * kCigarStride);
+  c.take(d.cigar_off, n + 1ull);
+  c.take(d.cigar, static_cast<uint64_t>(n) * kCigarStride);
+  c.take(d.read_class, n);
+  c.take(d.scan_tmp, n / 1024 + 4ull);
+  b->bytes = c.off + 256;
+  cudaError_t e = cudaMalloc(&b->arena, b->bytes);
+  if (e != cudaSuccess) {
+    delete b;
+    cudaGetLastError();
+    return set_error(SR_ENOMEM, "sr_batch_stage: device allocation of %llu bytes failed",
+                     static_cast<unsigned long long>(c.off));
+  }
+  char* base = static_cast<char*>(b->arena);
+  rebase_c(d.bases, base);
+  rebase_c(d.read_off, base);
+  rebase_c(d.cand_off, base);
+  rebase_c(d.c_ref, base);
+  rebase_c(d.c_strand, base);
+  rebase_c(d.c_start, base);
+  rebase_c(d.c_len, base);
+  rebase(d.rpack, base);
+  rebase(d.rlen, base);
+  rebase(d.item_read, base);
+  rebase(d.item_key, base);
+  rebase(d.order, base);
+  rebase(d.hist, base);
+  rebase(d.cursor, base);
+  rebase(d.class_range, base);
+  rebase(d.queue, base);
+  rebase(d.status, base);
+  rebase(d.item_score, base);
+  rebase(d.item_end, base);
+  rebase(d.hits, base);
+  rebase(d.cigar_slots, base);
+  rebase(d.cigar_off, base);
+  rebase(d.cigar, base);
+  rebase(d.read_class, base);
+  rebase(d.scan_tmp, base);
+  d.n_reads = n;
+  d.n_items = nc;
+  s->hbm_used += b->bytes;
+  for (auto& ev : b->ev) {
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      sr_batch_free(b);
+      return cuda_error("sr_batch_stage events", cudaGetLastError());
+    }
+  }
+  cudaStream_t st = b->stream;
+  if (nb) e = cudaMemcpyAsync(const_cast<char*>(d.bases), reads->bases, nb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<uint64_t*>(d.read_off), reads->offsets, (n + 1ull) * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<uint64_t*>(d.cand_off), cands->offsets, (n + 1ull) * 8, cudaMemcpyHostToDevice, st);
+  if (nc) {
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<uint8_t*>(d.c_ref), cands->ref_id, nc, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<uint8_t*>(d.c_strand), cands->strand, nc, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<uint64_t*>(d.c_start), cands->win_start, nc * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<uint32_t*>(d.c_len), cands->win_len, nc * 4, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    sr_batch_free(b);
+    return cuda_error("sr_batch_stage copy", e);
+  }
+  // host copies used to assemble results, and the DP cell count
+  b->h_cstart.assign(cands->win_start, cands->win_start + nc);
+  b->h_cref.assign(cands->ref_id, cands->ref_id + nc);
+  b->h_cstrand.assign(cands->strand, cands->strand + nc);
+  uint64_t cells = 0;
+  b->h_item_m.resize(nc);
+  for (uint32_t r = 0; r < n; ++r) {
+    const uint64_t m = reads->offsets[r + 1] - reads->offsets[r];
+    b->max_m = std::max<uint32_t>(b->max_m, static_cast<uint32_t>(std::min<uint64_t>(m, 65535)));
+    for (uint64_t k = cands->offsets[r]; k < cands->offsets[r + 1]; ++k) {
+      cells += m * cands->win_len[k];
+      b->h_item_m[k] = static_cast<uint16_t>(std::min<uint64_t>(m, 65535));
+    }
+  }
+  b->cells = cells;
+  *out = b;
+  return SR_OK;
+}
+
+extern "C" void sr_batch_free(sr_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto ev : b->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (b->arena) {
+    cudaStreamSynchronize(b->stream);
+    cudaFree(b->arena);
+    b->s->hbm_used -= b->bytes;
+  }
+  delete b;
+}
+
+namespace sr {
+
+// enqueue every kernel of the path for one batch; returns kernels launched or -1
+static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& o,
+                   const TuneBin* bins, cudaStream_t st) {
+  const BatchDev& d = b->d;
+  const ScoreConst sc{sp.match, sp.mismatch, sp.gap_open, sp.gap_extend};
+  const bool plain = o.engine == SR_ENGINE_PLAIN;
+  const int nr = static_cast<int>(b->s->n_refs);
+  int k = 0, t;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  const unsigned evf = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  auto mark = [&](int i) { return cudaEventRecordWithFlags(b->ev[i], st, evf) == cudaSuccess; };
+  if (!mark(0)) return -1;
+  if (cudaMemsetAsync(d.status, 0, 4, st) != cudaSuccess) return -1;
+  if ((t = launch_prepare(d, b->s->refs, st)) < 0) return -1;
+  k += t;
+  if (b->n_items) {
+    if ((t = launch_bins(d, sc, bins, kNumBins, o.force_i32 != 0, plain, st)) < 0) return -1;
+    k += t;
+    if (!mark(2)) return -1;
+    if ((t = launch_extend(d, b->s->refs, sc, bins, kNumBins, static_cast<int>(o.mode), plain, o.lanes,
+                           o.rows, st)) < 0)
+      return -1;
+    if (!mark(3)) return -1;
+    k += t;
+  } else {
+    if (!mark(2) || !mark(3)) return -1;
+  }
+  if ((t = launch_select(d, nr, st)) < 0) return -1;
+  k += t;
+  if (!mark(4)) return -1;
+  if (o.want_cigar) {
+    if ((t = launch_traceback(d, b->s->refs, sc, static_cast<int>(o.mode), nr, st)) < 0) return -1;
+    k += t;
+    if ((t = launch_cigar_compact(d, nr, st)) < 0) return -1;
+    k += t;
+  }
+  if (!mark(5)) return -1;
+  if (o.classify) {
+    if ((t = launch_classify(d, nr, o.min_score, o.margin, st)) < 0) return -1;
+    k += t;
+  }
+  if (!mark(1)) return -1;
+  return k;
+}
+
+static bool same_opts(const sr_align_opts& a, const sr_align_opts& b) {
+  return a.mode == b.mode && a.engine == b.engine && a.want_cigar == b.want_cigar && a.classify == b.classify &&
+         a.min_score == b.min_score && a.margin == b.margin && a.force_i32 == b.force_i32 &&
+         a.lanes == b.lanes && a.rows == b.rows;
+}
+
+sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp, const sr_align_opts* opts) {
+  if (!s || !b || b->s != s) return set_error(SR_EINVAL, "sr_batch_run: bad session/batch");
+  sr_status st = check_score(sp);
+  if (st != SR_OK) return st;
+  sr_align_opts o = opts ? *opts : default_opts();
+  if (o.mode > 1 || o.engine > 1) return set_error(SR_EINVAL, "sr_batch_run: bad mode/engine");
+  if ((o.lanes || o.rows) && !extend_config_supported(o.lanes, o.rows))
+    return set_error(SR_EINVAL, "sr_batch_run: unsupported lanes x rows shape");
+  if (o.lanes && o.lanes * o.rows < std::max<uint32_t>(b->max_m, 1))
+    return set_error(SR_EINVAL, "sr_batch_run: lanes*rows must cover the longest read of the batch");
+  if (o.classify && s->n_refs < 2) return set_error(SR_EINVAL, "sr_batch_run: classification needs 2 references");
+  const int32_t goe = sp->gap_open + sp->gap_extend;
+  const bool i16_tables = sp->match + goe <= 127 && goe - sp->mismatch >= -128 && goe + sp->gap_extend + 256 < kBias;
+  if (o.engine == SR_ENGINE_PLAIN &&
+      (!i16_tables || o.force_i32 || static_cast<int64_t>(sp->match) * b->max_m > 32767 - kBias))
+    return set_error(SR_EINVAL, "sr_batch_run: the plain engine runs the int16 kernel only; use the batched engine");
+  cudaStream_t stream = o.cuda_stream ? static_cast<cudaStream_t>(o.cuda_stream) : b->stream;
+  TuneBin bins[kNumBins];
+  tune_get_bins(bins);
+  {
+    uint64_t n32 = 0;
+    for (uint64_t k = 0; k < b->n_items; ++k)
+      if (o.force_i32 || !i16_tables || static_cast<int64_t>(sp->match) * b->h_item_m[k] > 32767 - kBias) ++n32;
+    b->i32_items = o.engine == SR_ENGINE_PLAIN ? 0 : n32;
+  }
+  const bool plain = o.engine == SR_ENGINE_PLAIN;
+  if (plain) {
+    const int k = enqueue(b, *sp, o, bins, stream);
+    if (k < 0) return cuda_error("sr_batch_run launch", cudaGetLastError());
+    b->kernels = static_cast<uint64_t>(k);
+  } else {
+    // the batched engine replays the whole path as one CUDA graph
+    const bool reuse = b->graph && same_opts(b->g_opts, o) && memcmp(&b->g_sp, sp, sizeof(*sp)) == 0 &&
+                       memcmp(b->g_bins, bins, sizeof(bins)) == 0;
+    if (!reuse) {
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_error("sr_batch_run capture", e);
+      const int k = enqueue(b, *sp, o, bins, stream);
+      e = cudaStreamEndCapture(stream, &g);
+      if (k < 0 || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_error("sr_batch_run capture", e != cudaSuccess ? e : cudaGetLastError());
+      }
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return cuda_error("sr_batch_run instantiate", e);
+      }
+      b->g_opts = o;
+      b->g_sp = *sp;
+      memcpy(b->g_bins, bins, sizeof(bins));
+      b->kernels = static_cast<uint64_t>(k);
+    }
+    cudaError_t e = cudaGraphLaunch(b->graph, stream);
+    if (e != cudaSuccess) return cuda_error("sr_batch_run graph launch", e);
+  }
+  b->ran = true;
+  b->last_opts = o;
+  return SR_OK;
+}
+
+sr_status batch_sync(sr_batch* b, cudaStream_t stream) {
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_error("sr_batch_sync", e);
+  uint32_t st = 0;
+  e = cudaMemcpy(&st, b->d.status, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error("sr_batch_sync status", e);
+  if (st & kStBadBase) return set_error(SR_EBADBASE, "read has a non-ACGT base");
+  if (st & kStBadRead) return set_error(SR_EINVAL, "read length must be 1..256");
+  if (st & kStBadWindow) return set_error(SR_EINVAL, "window outside its reference, bad ref id/strand or length not in 1..512");
+  if (st & kStTimeout) return set_error(SR_ETIMEOUT, "device wait for a window copy ran out");
+  if (st & (kStOverflow | kStInternal)) return set_error(SR_ECUDA, "device internal check failed (status %u)", st);
+  return SR_OK;
+}
+
+}  // namespace sr
+
+extern "C" sr_status sr_batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp,
+                                        const sr_align_opts* opts) {
+  return batch_run_async(s, b, sp, opts);
+}
+
+extern "C" sr_status sr_batch_sync(sr_session* s, sr_batch* b) {
+  if (!s || !b) return set_error(SR_EINVAL, "sr_batch_sync: null argument");
+  cudaStream_t st = b->last_opts.cuda_stream ? static_cast<cudaStream_t>(b->last_opts.cuda_stream) : b->stream;
+  return batch_sync(b, st);
+}
+
+extern "C" sr_status sr_batch_run(sr_session* s, sr_batch* b, const sr_score_params* sp,
+                                  const sr_align_opts* opts) {
+  sr_status st = batch_run_async(s, b, sp, opts);
+  if (st != SR_OK) return st;
+  return sr_batch_sync(s, b);
+}
+
+extern "C" sr_status sr_batch_stats(const sr_batch* b, uint64_t* kernels, uint64_t* cells, uint64_t* i32_items,
+                                    uint64_t* tasks) {
+  if (!b) return set_error(SR_EINVAL, "sr_batch_stats: null batch");
+  if (kernels) *kernels = b->kernels;
+  if (cells) *cells = b->cells;
+  if (i32_items) *i32_items = b->i32_items;
+  if (tasks) *tasks = (b->n_items + 1) / 2;
+  return SR_OK;
+}
+
+extern "C" sr_status sr_batch_timing(const sr_batch* b, float* total_ms, float* extend_ms, float* traceback_ms) {
+  if (!b || !b->ran) return set_error(SR_EINVAL, "sr_batch_timing: batch has not run");
+  float t = 0;
+  if (total_ms) {
+    if (cudaEventElapsedTime(&t, b->ev[0], b->ev[1]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
+    *total_ms = t;
+  }
+  if (extend_ms) {
+    if (cudaEventElapsedTime(&t, b->ev[2], b->ev[3]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
+    *extend_ms = t;
+  }
+  if (traceback_ms) {
+    if (cudaEventElapsedTime(&t, b->ev[4], b->ev[5]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
+    *traceback_ms = t;
+  }
+  return SR_OK;
+}
+
+extern "C" void sr_results_free(sr_results* r) {
+  if (!r) return;
+  free(r->best);
+  free(r->best_per_ref);
+  free(r->item_score);
+  free(r->item_end);
+  free(r->cigar);
+  free(r->read_class);
+  free(r);
+}
+
+extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out) {
+  if (!s || !b || !out) return set_error(SR_EINVAL, "sr_batch_fetch: null argument");
+  if (!b->ran) return set_error(SR_EINVAL, "sr_batch_fetch: batch has not run");
+  *out = nullptr;
+  cudaStream_t stream = b->last_opts.cuda_stream ? static_cast<cudaStream_t>(b->last_opts.cuda_stream) : b->stream;
+  sr_status st = batch_sync(b, stream);
+  if (st != SR_OK) return st;
+  const uint32_t n = b->n_reads, nr = s->n_refs;
+  const uint64_t nc = b->n_items;
+  const int slots = 1 + static_cast<int>(nr);
+  auto* r = static_cast<sr_results*>(calloc(1, sizeof(sr_results)));
+  if (!r) return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
+  r->n_reads = n;
+  r->n_refs = nr;
+  r->n_items = nc;
+  r->cells = b->cells;
+  r->best = static_cast<sr_hit*>(calloc(n ? n : 1, sizeof(sr_hit)));
+  r->best_per_ref = static_cast<sr_hit*>(calloc(static_cast<size_t>(n ? n : 1) * nr, sizeof(sr_hit)));
+  r->item_score = static_cast<int32_t*>(malloc((nc ? nc : 1) * 4));
+  r->item_end = static_cast<uint32_t*>(malloc((nc ? nc : 1) * 4));
+  std::vector<DevHit> hits(static_cast<size_t>(n) * slots);
+  std::vector<uint32_t> coff(n + 1ull, 0);
+  if (!r->best || !r->best_per_ref || !r->item_score || !r->item_end) {
+    sr_results_free(r);
+    return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
+  }
+  cudaError_t e = cudaSuccess;
+  if (nc) {
+    e = cudaMemcpy(r->item_score, b->d.item_score, nc * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(r->item_end, b->d.item_end, nc * 4, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess && n) e = cudaMemcpy(hits.data(), b->d.hits, hits.size() * sizeof(DevHit), cudaMemcpyDeviceToHost);
+  const bool cig = b->last_opts.want_cigar != 0;
+  if (e == cudaSuccess && n && cig) e = cudaMemcpy(coff.data(), b->d.cigar_off, (n + 1ull) * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && cig) {
+    const uint64_t total = n ? coff[n] : 0;
+    r->n_cigar = total;
+    r->cigar = static_cast<uint32_t*>(malloc((total ? total : 1) * 4));
+    if (!r->cigar) {
+      sr_results_free(r);
+      return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
+    }
+    if (total) e = cudaMemcpy(r->cigar, b->d.cigar, total * 4, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess && b->last_opts.classify) {
+    r->read_class = static_cast<uint8_t*>(malloc(n ? n : 1));
+    if (n) e = cudaMemcpy(r->read_class, b->d.read_class, n, cudaMemcpyDeviceToHost);
+  }
+  if (e != cudaSuccess) {
+    sr_results_free(r);
+    return cuda_error("sr_batch_fetch copy", e);
+  }
+  for (uint32_t i = 0; i < n; ++i) {
+    for (int sl = 0; sl < slots; ++sl) {
+      const DevHit& h = hits[static_cast<size_t>(i) * slots + sl];
+      sr_hit o{};
+      o.score = h.score;
+      o.second = h.second;
+      o.n_ties = h.n_ties;
+      o.item = h.item;
+      if (h.item >= 0) {
+        const uint64_t it = static_cast<uint64_t>(h.item);
+        o.ref_id = b->h_cref[it];
+        o.strand = b->h_cstrand[it];
+        o.ref_end = b->h_cstart[it] + r->item_end[it] - 1;
+        if (sl == 0 && cig) {
+          o.read_start = h.read_start;
+          o.read_end = h.read_end;
+          o.ref_start = b->h_cstart[it] + h.start_j - 1;
+          o.cigar_off = coff[i];
+          o.cigar_len = h.cigar_len;
+        }
+      }
+      if (sl == 0) r->best[i] = o;
+      else r->best_per_ref[static_cast<size_t>(i) * nr + (sl - 1)] = o;
+    }
+  }
+  *out = r;
+  return SR_OK;
+}
+
+extern "C" sr_status sr_align_batch(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                                    const sr_score_params* sp, const sr_align_opts* opts, sr_results** out) {
+  if (!out) return set_error(SR_EINVAL, "sr_align_batch: null out");
+  *out = nullptr;
+  sr_batch* b = nullptr;
+  sr_status st = sr_batch_stage(s, reads, cands, opts ? opts->cuda_stream : nullptr, &b);
+  if (st != SR_OK) return st;
+  st = sr_batch_run(s, b, sp, opts);
+  if (st == SR_OK) st = sr_batch_fetch(s, b, out);
+  sr_batch_free(b);
+  return st;
+}
+
+extern "C" sr_status sr_classify(sr_session* s, sr_batch* b, const sr_classify_params* params, uint8_t* class_out) {
+  if (!s || !b || !class_out) return set_error(SR_EINVAL, "sr_classify: null argument");
+  if (!b->ran) return set_error(SR_EINVAL, "sr_classify: batch has not run");
+  if (s->n_refs < 2) return set_error(SR_EINVAL, "sr_classify: needs 2 references");
+  const int32_t ms = params ? params->min_score : 40, mg = params ? params->margin : 5;
+  cudaStream_t stream = b->stream;
+  if (launch_classify(b->d, static_cast<int>(s->n_refs), ms, mg, stream) < 0)
+    return cuda_error("sr_classify launch", cudaGetLastError());
+  cudaError_t e = cudaMemcpyAsync(class_out, b->d.read_class, b->n_reads, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_error("sr_classify", e);
+  return SR_OK;
+}
+
+// ------------------------------------------------------------------ tuning table
+extern "C" sr_status sr_tune_get(uint32_t* n_bins, uint32_t* upper, uint32_t* lanes, uint32_t* rows, uint32_t cap) {
+  TuneBin b[kNumBins];
+  tune_get_bins(b);
+  if (n_bins) *n_bins = kNumBins;
+  for (uint32_t i = 0; i < kNumBins && i < cap; ++i) {
+    if (upper) upper[i] = b[i].upper;
+    if (lanes) lanes[i] = b[i].lanes;
+    if (rows) rows[i] = b[i].rows;
+  }
+  return SR_OK;
+}
+
+extern "C" sr_status sr_tune_set(uint32_t n_bins, const uint32_t* upper, const uint32_t* lanes, const uint32_t* rows) {
+  if (n_bins != kNumBins || !upper || !lanes || !rows) return set_error(SR_EINVAL, "sr_tune_set: need 8 bins");
+  TuneBin b[kNumBins];
+  for (uint32_t i = 0; i < kNumBins; ++i) {
+    if (!extend_config_supported(lanes[i], rows[i]) || lanes[i] * rows[i] < upper[i] ||
+        (i > 0 && upper[i] <= upper[i - 1]) || upper[i] > SR_MAX_READ_LEN)
+      return set_error(SR_EINVAL, "sr_tune_set: bin %u: unsupported shape or bad bound", i);
+    b[i] = TuneBin{upper[i], lanes[i], rows[i]};
+  }
+  if (b[kNumBins - 1].upper != SR_MAX_READ_LEN) return set_error(SR_EINVAL, "sr_tune_set: last bin must end at 256");
+  tune_set_bins(b);
+  return SR_OK;
+}
+
+extern "C" sr_status sr_tune_save(const char* path) {
+  if (!path) return set_error(SR_EINVAL, "sr_tune_save: null path");
+  TuneBin b[kNumBins];
+  tune_get_bins(b);
+  cudaDeviceProp p{};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const bool have = cudaGetDeviceProperties(&p, dev) == cudaSuccess;
+  FILE* f = fopen(path, "w");
+  if (!f) return set_error(SR_EIO, "sr_tune_save: cannot open");
+  fprintf(f, "# libsr tune table: device %s\n", have ? p.name : "unknown");
+  for (int i = 0; i < kNumBins; ++i) fprintf(f, "%u %u %u\n", b[i].upper, b[i].lanes, b[i].rows);
+  return fclose(f) == 0 ? SR_OK : set_error(SR_EIO, "sr_tune_save: write failed");
+}
+
+extern "C" sr_status sr_tune_load(const char* path) {
+  if (!path) return set_error(SR_EINVAL, "sr_tune_load: null path");
+  FILE* f = fopen(path, "r");
+  if (!f) return set_error(SR_EIO, "sr_tune_load: cannot open");
+  uint32_t up[kNumBins], la[kNumBins], ro[kNumBins];
+  char line[256];
+  int n = 0;
+  while (n < kNumBins && fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    if (sscanf(line, "%u %u %u", &up[n], &la[n], &ro[n]) == 3) ++n;
+  }
+  fclose(f);
+  if (n != kNumBins) return set_error(SR_EIO, "sr_tune_load: expected 8 bins");
+  return sr_tune_set(kNumBins, up, la, ro);
+}
+
+// Autotuner: for each read-length bin, time every supported kernel shape whose
+// rows cover the bin on a synthetic sample (reads of the bin's longest length,
+// 6 windows of length m + 64 each at random positions of reference 0) and keep
+// the fastest.
+extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t sample_reads) {
+  if (!s) return set_error(SR_EINVAL, "sr_tune: null session");
+  sr_status st = check_score(sp);
+  if (st != SR_OK) return st;
+  if (sample_reads == 0) sample_reads = 4096;
+  static const uint32_t shapes[][2] = {{4, 16}, {8, 8},   {8, 10},  {8, 12},  {8, 16},  {16, 6},
+                                       {16, 8}, {16, 10}, {16, 12}, {16, 14}, {16, 16}, {32, 8}};
+  TuneBin cur[kNumBins];
+  tune_get_bins(cur);
+  uint64_t rng = 0x9E3779B97F4A7C15ull;
+  auto next = [&]() {
+    rng ^= rng << 13;
+    rng ^= rng >> 7;
+    rng ^= rng << 17;
+    return rng;
+  };
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int bi = 0; bi < kNumBins; ++bi) {
+    const uint32_t m = cur[bi].upper;
+    const uint32_t nw = 6;
+    std::vector<char> bases(static_cast<size_t>(sample_reads) * m);
+    for (auto& c : bases) c = "ACGT"[next() & 3];
+    std::vector<uint64_t> roff(sample_reads + 1ull), coff(sample_reads + 1ull);
+    std::vector<uint8_t> cref(static_cast<size_t>(sample_reads) * nw, 0), cstr(cref.size(), 0);
+    std::vector<uint64_t> cst(cref.size());
+    std::vector<uint32_t> cln(cref.size());
+    const uint64_t L = s->lens[0];
+    for (uint32_t r = 0; r <= sample_reads; ++r) {
+      roff[r] = static_cast<uint64_t>(r) * m;
+      coff[r] = static_cast<uint64_t>(r) * nw;
+    }
+    for (size_t k = 0; k < cref.size(); ++k) {
+      const uint32_t wl = static_cast<uint32_t>(std::min<uint64_t>(m + 64, L));
+      cln[k] = wl;
+      cst[k] = (L > wl) ? next() % (L - wl) : 0;
+    }
+    sr_reads rd{sample_reads, 0, bases.data(), roff.data()};
+    sr_cand_list cl{};
+    cl.n_reads = sample_reads;
+    cl.n_cands = cref.size();
+    cl.offsets = coff.data();
+    cl.ref_id = cref.data();
+    cl.strand = cstr.data();
+    cl.win_start = cst.data();
+    cl.win_len = cln.data();
+    sr_batch* b = nullptr;
+    st = batch_stage_internal(s, &rd, &cl, nullptr, false, &b);
+    if (st != SR_OK) break;
+    float best_ms = 1e30f;
+    TuneBin pick = cur[bi];
+    for (auto& sh : shapes) {
+      if (sh[0] * sh[1] < m || sh[0] * sh[1] > 2 * m + 64) continue;
+      sr_align_opts o = default_opts();
+      o.want_cigar = 0;
+      o.lanes = sh[0];
+      o.rows = sh[1];
+      float tot = 0;
+      bool ok = true;
+      for (int rep = 0; rep < 4 && ok; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, b->stream);
+        ok = batch_run_async(s, b, sp, &o) == SR_OK;
+      }
+      cudaEventRecord(e1, b->stream);
+      if (ok) ok = batch_sync(b, b->stream) == SR_OK;
+      if (!ok) continue;
+      cudaEventElapsedTime(&tot, e0, e1);
+      if (tot < best_ms) {
+        best_ms = tot;
+        pick = TuneBin{m, sh[0], sh[1]};
+      }
+    }
+    sr_batch_free(b);
+    cur[bi] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SR_OK) return st;
+  tune_set_bins(cur);
+  return SR_OK;
+}
+
+extern "C" sr_status sr_probe_dpx(double* rate, double* mhz) {
+  if (!rate || !mhz) return set_error(SR_EINVAL, "sr_probe_dpx: null argument");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return set_error(SR_ECUDA, "no CUDA device");
+  if (probe_dpx(rate, mhz) != 0) return cuda_error("sr_probe_dpx", cudaGetLastError());
+  return SR_OK;
+}

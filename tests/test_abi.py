@@ -1,0 +1,67 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/sr.h declares (no compute calls here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    txt = open(os.path.join(ROOT, "include", "sr.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sr_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported():
+    from paper_1805_00106_gb300 import sr
+    path = sr._build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(sr_\w+)", out))
+    names = declared()
+    assert len(names) >= 30
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = sr.lib()
+    for n in names:
+        assert hasattr(L, n)
+
+
+def test_calls_fail_loudly_without_gpu():
+    import torch
+    from paper_1805_00106_gb300 import sr
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(sr.SrError) as e:
+        sr.Session.open([b"ACGT" * 64])
+    assert e.value.status == sr.SR_ECUDA
+    with pytest.raises(sr.SrError):
+        sr.probe_dpx()
+
+
+def test_binding_has_no_compute_fallback():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_1805_00106_gb300")
+    for dp, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cpp", ".cu", ".h")):
+                src = open(os.path.join(dp, f), errors="replace").read()
+                assert "oracle" not in src.replace("the oracle", ""), f
+
+
+def test_tune_table_roundtrip(tmp_path):
+    from paper_1805_00106_gb300 import sr
+    bins = sr.tune_get()
+    assert len(bins) == 8 and bins[-1][0] == 256
+    p = str(tmp_path / "tune.txt")
+    sr.lib().sr_tune_save(p.encode())
+    new = [(64, 4, 16), (80, 8, 10), (96, 8, 12), (128, 8, 16), (160, 16, 10), (192, 16, 12),
+           (224, 16, 14), (256, 32, 8)]
+    sr.tune_set(new)
+    assert sr.tune_get() == new
+    assert sr.lib().sr_tune_load(p.encode()) == 0
+    assert sr.tune_get() == bins
+    with pytest.raises(sr.SrError):
+        sr.tune_set([(64, 4, 8)] + bins[1:])  # rows do not cover the bin

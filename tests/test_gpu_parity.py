@@ -1,0 +1,227 @@
+"""GPU path vs oracle, element by element, on seeded synthetic inputs (-m gpu).
+
+Every case calls libsr through its C ABI (the ctypes binding) and compares item
+scores and end columns, per-read winner / second / ties, per-reference bests,
+winner CIGARs and classes with the oracle, bit-exactly (integer DP).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1805_00106_gb300 import synth as S
+
+from .parity import compare, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+SP = (2, 3, 5, 2)
+
+
+@pytest.fixture(scope="module")
+def sr():
+    from paper_1805_00106_gb300 import sr as _sr
+    _sr.lib()
+    return _sr
+
+
+def _session(sr, w):
+    return sr.Session.open([bytes(r) for r in w["refs"]])
+
+
+def _check(g, o, **kw):
+    bad = compare(g, o, **kw)
+    assert not bad, "\n".join(bad)
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_c1_small_both_engines(sr, engine):
+    w = S.workload("c1", scale=0.02, seed=3)
+    s = _session(sr, w)
+    g = gpu_run(s, w, engine=engine)
+    _check(g, oracle_run(w))
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_c2_small_uneven_lengths(sr, engine):
+    w = S.workload("c2", scale=0.0006, seed=5)
+    s = _session(sr, w)
+    _check(gpu_run(s, w, engine=engine), oracle_run(w))
+
+
+def test_reverse_strand_reads(sr):
+    w = S.workload("c2", scale=0.0004, seed=7, rc_frac=0.5)
+    s = _session(sr, w)
+    _check(gpu_run(s, w), oracle_run(w))
+
+
+@pytest.mark.parametrize("shape", [(4, 16), (8, 8), (8, 10), (8, 12), (8, 16), (16, 6), (16, 8),
+                                   (16, 10), (16, 12), (16, 14), (16, 16), (32, 8)])
+def test_forced_kernel_shapes(sr, shape):
+    g_, r_ = shape
+    cap = g_ * r_
+    w = S.workload("c2", scale=0.0003, seed=11)
+    # keep reads the shape covers
+    m = np.diff(w["read_off"])
+    keep = np.nonzero(m <= cap)[0]
+    w = subset(w, keep)
+    s = _session(sr, w)
+    _check(gpu_run(s, w, lanes=g_, rows=r_), oracle_run(w))
+    if cap >= 256:
+        _check(gpu_run(s, w, lanes=g_, rows=r_, engine=1), oracle_run(w))
+
+
+def test_int32_path_forced(sr):
+    w = S.workload("c1", scale=0.01, seed=13)
+    s = _session(sr, w)
+    _check(gpu_run(s, w, force_i32=True), oracle_run(w))
+
+
+def test_overflow_promotion_large_match_score(sr):
+    """match = 200: 250 identical bases score 50000 > int16; those items must be
+    promoted to the int32 kernel and still agree with the oracle."""
+    rng = np.random.default_rng(17)
+    ref = rng.choice(np.frombuffer(b"ACGT", np.uint8), 6000)
+    reads, offs, cands = [], [0], dict(cand_off=[0], c_ref=[], c_strand=[], c_start=[], c_len=[])
+    for k, m in enumerate([250, 200, 120, 60, 16]):
+        pos = 300 + 900 * k
+        reads.append(ref[pos:pos + m])
+        offs.append(offs[-1] + m)
+        for st in (pos - 20, pos + 400):
+            cands["c_ref"].append(0); cands["c_strand"].append(0)
+            cands["c_start"].append(st); cands["c_len"].append(m + 40)
+        cands["cand_off"].append(len(cands["c_ref"]))
+    w = dict(refs=[ref], bases=np.concatenate(reads), read_off=np.array(offs),
+             **{k: np.array(v) for k, v in cands.items()})
+    s = _session(sr, w)
+    sp = (200, 3, 5, 2)
+    o = oracle_run(w, sp=sp)
+    assert o["item_score"].max() == 50000
+    _check(gpu_run(s, w, sp=sp), o)
+
+
+def test_final_row_mode(sr):
+    w = S.workload("c2", scale=0.0003, seed=19)
+    s = _session(sr, w)
+    _check(gpu_run(s, w, mode=1), oracle_run(w, mode=1))
+    _check(gpu_run(s, w, mode=1, force_i32=True), oracle_run(w, mode=1))
+
+
+def subset(w, keep):
+    keep = np.asarray(keep)
+    roff, coff = w["read_off"], w["cand_off"]
+    bases = np.concatenate([w["bases"][roff[r]:roff[r + 1]] for r in keep]) if len(keep) else np.zeros(0, np.uint8)
+    new_roff = np.concatenate([[0], np.cumsum([roff[r + 1] - roff[r] for r in keep])]).astype(np.int64)
+    items = np.concatenate([np.arange(coff[r], coff[r + 1]) for r in keep]).astype(np.int64) if len(keep) else np.zeros(0, np.int64)
+    new_coff = np.concatenate([[0], np.cumsum([coff[r + 1] - coff[r] for r in keep])]).astype(np.int64)
+    out = dict(w)
+    out.update(bases=bases, read_off=new_roff, cand_off=new_coff, c_ref=w["c_ref"][items],
+               c_strand=w["c_strand"][items], c_start=w["c_start"][items], c_len=w["c_len"][items])
+    return out
+
+
+def test_edge_lengths_and_clamped_windows(sr):
+    rng = np.random.default_rng(23)
+    L = 3000
+    ref = rng.choice(np.frombuffer(b"ACGT", np.uint8), L)
+    reads, offs = [], [0]
+    cand = dict(cand_off=[0], c_ref=[], c_strand=[], c_start=[], c_len=[])
+    lengths = [1, 2, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 255, 256]
+    for m in lengths:
+        pos = int(rng.integers(0, L - m))
+        r = ref[pos:pos + m].copy()
+        if m > 10:
+            r[m // 2] = ord("A") if r[m // 2] != ord("A") else ord("C")
+        reads.append(r)
+        offs.append(offs[-1] + m)
+        wins = [(pos, m), (max(0, pos - 64), min(L - max(0, pos - 64), m + 128)), (0, min(L, m + 5)),
+                (L - min(L, m + 7), min(L, m + 7)), (pos, 1), (max(0, pos - 3), min(5, L)),
+                (max(0, min(pos, L - 512)), 512)]
+        if m > 12:
+            wins.append((pos + 2, m - 10))
+        for k, (st, ln) in enumerate(wins):
+            cand["c_ref"].append(0); cand["c_strand"].append(k % 2)
+            cand["c_start"].append(st); cand["c_len"].append(ln)
+        cand["cand_off"].append(len(cand["c_ref"]))
+    # a read with no windows at all
+    reads.append(ref[10:90]); offs.append(offs[-1] + 80); cand["cand_off"].append(len(cand["c_ref"]))
+    w = dict(refs=[ref], bases=np.concatenate(reads), read_off=np.array(offs),
+             **{k: np.array(v) for k, v in cand.items()})
+    s = _session(sr, w)
+    o = oracle_run(w)
+    _check(gpu_run(s, w), o)
+    _check(gpu_run(s, w, force_i32=True), o)
+    _check(gpu_run(s, w, engine=1), o)
+
+
+def test_empty_batches(sr):
+    w = S.workload("c1", scale=0.005, seed=29)
+    s = _session(sr, w)
+    n = len(w["read_off"]) - 1
+    # no windows for any read
+    w0 = dict(w, cand_off=np.zeros(n + 1, np.int64), c_ref=np.zeros(0, np.uint8),
+              c_strand=np.zeros(0, np.uint8), c_start=np.zeros(0, np.int64), c_len=np.zeros(0, np.int32))
+    g = gpu_run(s, w0)
+    assert np.all(g["best"]["item"] == -1) and np.all(g["best"]["score"] == 0)
+    # no reads
+    wz = dict(w0, bases=np.zeros(0, np.uint8), read_off=np.zeros(1, np.int64), cand_off=np.zeros(1, np.int64))
+    g = gpu_run(s, wz)
+    assert g["n_reads"] == 0
+
+
+def test_bad_inputs_are_rejected(sr):
+    w = S.workload("c1", scale=0.005, seed=31)
+    s = _session(sr, w)
+    bad = dict(w, bases=w["bases"].copy())
+    bad["bases"][5] = ord("N")
+    with pytest.raises(sr.SrError) as e:
+        gpu_run(s, bad)
+    assert e.value.status == sr.SR_EBADBASE
+    bad = dict(w, c_start=w["c_start"].copy())
+    bad["c_start"][3] = len(w["refs"][0]) - 2
+    with pytest.raises(sr.SrError) as e:
+        gpu_run(s, bad)
+    assert e.value.status == sr.SR_EINVAL
+    # a read longer than 256 bases
+    long = dict(w, bases=np.concatenate([w["bases"], np.full(300, ord("A"), np.uint8)]),
+                read_off=np.concatenate([w["read_off"], [w["read_off"][-1] + 300]]),
+                cand_off=np.concatenate([w["cand_off"], [w["cand_off"][-1]]]))
+    with pytest.raises(sr.SrError) as e:
+        gpu_run(s, long)
+    assert e.value.status == sr.SR_EINVAL
+    with pytest.raises(sr.SrError) as e:
+        gpu_run(s, w, sp=(2, 3, 5, 0))
+    assert e.value.status == sr.SR_EINVAL
+
+
+def test_xenograft_classification_with_host_index(sr):
+    w = S.workload("c3", scale=0.0008, seed=37)
+    idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=10, cal_limit=1024) for r in w["refs"]]
+    cd = sr.candidates(idx, w["bases"], w["read_off"], seed_stride=1, merge_dist=32, pad=32)
+    w.update(cd)
+    s = sr.Session.from_indexes(idx)
+    g = gpu_run(s, w, classify=True, min_score=40, margin=5)
+    o = oracle_run(w)
+    _check(g, o, classify=(40, 5))
+    # re-classification on the device with the paper's exact-tie rule
+    b = s.stage(w["bases"], w["read_off"], w["cand_off"], w["c_ref"], w["c_strand"], w["c_start"], w["c_len"])
+    b.run(sr.score_params(*SP), sr.align_opts())
+    cls = b.classify(min_score=40, margin=1)
+    exp = [O.classify(int(a), int(bb), 40, 1) for a, bb in zip(o["best_per_ref"]["score"][:, 0],
+                                                                 o["best_per_ref"]["score"][:, 1])]
+    assert np.array_equal(cls, np.array(exp, np.uint8))
+
+
+def test_repeated_runs_and_staged_batch_identical(sr):
+    w = S.workload("c2", scale=0.0003, seed=41)
+    s = _session(sr, w)
+    b = s.stage(w["bases"], w["read_off"], w["cand_off"], w["c_ref"], w["c_strand"], w["c_start"], w["c_len"])
+    outs = []
+    for _ in range(3):
+        b.run(sr.score_params(*SP), sr.align_opts())
+        outs.append(b.fetch())
+    for o in outs[1:]:
+        for k in ["item_score", "item_end", "best", "cigar"]:
+            assert np.array_equal(o[k], outs[0][k])
+    _check(outs[0], oracle_run(w))
+    st = b.stats()
+    assert st["kernels"] >= 8 and st["cells"] > 0

@@ -329,10 +329,12 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
           for (int k = 1; k < R; k += 2) cm = __vimax3_s16x2(cm, T[k], T[k + 1 < R ? k + 1 : k]);
         }
         cm &= cw.y;
-        bool keep_hi, keep_lo;
-        best = __vibmax_s16x2(best, cm, &keep_hi, &keep_lo);
-        jlo = keep_lo ? jlo : static_cast<uint32_t>(j + 1);
-        jhi = keep_hi ? jhi : static_cast<uint32_t>(j + 1);
+        // strict improvement per half records the (1-based) column
+        const uint32_t nb = __vimax_s16x2_relu(best, cm);
+        const uint32_t chg = nb ^ best;
+        jlo = (chg & 0xffffu) ? static_cast<uint32_t>(j + 1) : jlo;
+        jhi = (chg >> 16) ? static_cast<uint32_t>(j + 1) : jhi;
+        best = nb;
       }
     }
 

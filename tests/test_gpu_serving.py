@@ -1,0 +1,110 @@
+"""Continuous batching (serving) through the C ABI (-m gpu): requests submitted
+while others run are merged into shared device rounds, and each request's
+results are byte-identical to aligning it alone (tolerance 0); HBM-budget
+admission, bounded waits and oracle parity of served results."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1805_00106_gb300 import synth as S
+
+from .parity import compare, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ["bases", "read_off", "cand_off", "c_ref", "c_strand", "c_start", "c_len"]
+
+
+def request_of(refs, n, seed):
+    rd = S.reads(refs, n, seed, 75, 250, 0.009, 0.001, 0.0)
+    cd = S.cands(rd, [len(r) for r in refs], seed + 1, S.COUNT_UNIFORM, 64, 32, cap_per_read=64)
+    return dict(**rd, **cd)
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_1805_00106_gb300 import sr
+    a = S.ref_iid(200_000, seed=1)
+    b = S.mutate(a, seed=2, sub=0.15, indel=0.02, nblocks=3, blk_lo=1000, blk_hi=20000)
+    reqs = S.serving_batches([a, b], 24, seed=3, max_batch=1500)
+    return sr, [a, b], reqs
+
+
+def test_results_alone_equal_results_in_the_mix(env):
+    sr, refs, reqs = env
+    s = sr.Session.open([bytes(r) for r in refs], hbm_budget=6 << 30)
+    alone = [s.align(*[q[k] for k in KEYS], sr.score_params(), sr.align_opts(classify=True)) for q in reqs]
+    s.serve_start(sr.score_params(), sr.align_opts(classify=True), max_inflight=0)
+    tickets = [None] * len(reqs)
+
+    def submit(i):
+        time.sleep(0.002 * (i % 5))
+        tickets[i] = s.submit(*[reqs[i][k] for k in KEYS])
+
+    th = [threading.Thread(target=submit, args=(i,)) for i in range(len(reqs))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    served = [s.wait(t, timeout_ms=120_000) for t in tickets]
+    st = s.serve_stats()
+    s.serve_stop()
+    for a, b in zip(alone, served):
+        for k in ["item_score", "item_end", "cigar", "read_class"]:
+            assert np.array_equal(a[k], b[k]), k
+        for f in a["best"].dtype.names:
+            assert np.array_equal(a["best"][f], b["best"][f]), f
+            assert np.array_equal(a["best_per_ref"][f], b["best_per_ref"][f]), f
+    assert st["completed"] == len(reqs)
+    assert st["max_round_requests"] >= 2, st  # requests shared device rounds
+    assert st["rounds"] < len(reqs)
+    assert st["p99_us"] >= st["p50_us"] > 0
+
+
+def test_served_results_match_oracle(env):
+    sr, refs, reqs = env
+    s = sr.Session.open([bytes(r) for r in refs])
+    s.serve_start(sr.score_params(), sr.align_opts())
+    q = reqs[0]
+    t = s.submit(*[q[k] for k in KEYS])
+    g = s.wait(t, timeout_ms=120_000)
+    s.serve_stop()
+    w = dict(q, refs=refs)
+    bad = compare(g, oracle_run(w))
+    assert not bad, bad
+
+
+def test_budget_admission_and_bounded_wait(env):
+    sr, refs, reqs = env
+    s = sr.Session.open([bytes(r) for r in refs], hbm_budget=64 << 20)
+    s.serve_start(sr.score_params(), sr.align_opts(), max_inflight=2)
+    big = request_of(refs, 60000, 9)  # needs more than the whole budget
+    with pytest.raises(sr.SrError) as e:
+        s.submit(*[big[k] for k in KEYS])
+    assert e.value.status == sr.SR_ENOMEM
+    with pytest.raises(sr.SrError) as e:
+        s.wait(987654, timeout_ms=0)
+    assert e.value.status == sr.SR_EINVAL
+    # several requests that each fit but not all at once: admitted as memory frees
+    tickets = [s.submit(*[q[k] for k in KEYS]) for q in reqs[:8]]
+    outs = [s.wait(t, timeout_ms=120_000) for t in tickets]
+    assert all(o["n_reads"] == len(q["read_off"]) - 1 for o, q in zip(outs, reqs[:8]))
+    s.serve_stop()
+
+
+def test_wait_timeout_returns_etimeout(env):
+    sr, refs, _ = env
+    s = sr.Session.open([bytes(r) for r in refs])
+    s.serve_start(sr.score_params(), sr.align_opts(), max_inflight=1)
+    big = request_of(refs, 40000, 11)
+    t1 = s.submit(*[big[k] for k in KEYS])
+    t2 = s.submit(*[big[k] for k in KEYS])
+    with pytest.raises(sr.SrError) as e:
+        s.wait(t2, timeout_ms=0)
+    assert e.value.status == sr.SR_ETIMEOUT
+    a = s.wait(t1, timeout_ms=120_000)
+    b = s.wait(t2, timeout_ms=120_000)
+    assert np.array_equal(a["item_score"], b["item_score"])
+    s.serve_stop()

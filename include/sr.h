@@ -282,6 +282,40 @@ sr_status sr_tune_get(uint32_t* n_bins, uint32_t* upper, uint32_t* lanes, uint32
 sr_status sr_tune_set(uint32_t n_bins, const uint32_t* upper, const uint32_t* lanes,
                       const uint32_t* rows);
 
+/* ------------------------------------------------ allocation-free scoring
+ * No counterpart in the paper: a service entry point of this library.
+ * Scores every (read, window) item whose inputs already sit in device memory
+ * and writes each item's score and 1-based end column (0 when the score is 0)
+ * into caller-owned device buffers, without allocating anything.  It is meant
+ * for callers that cannot call cudaMalloc: a process whose device memory is
+ * already held by another allocator, or a latency-sensitive caller that must
+ * not pay for allocation (cudaMalloc/cudaFree can synchronize the device and
+ * can fail under fragmentation).  Its scratch (work-queue counters, status
+ * word, packed read rows, read lengths, item-to-read map) is a fixed
+ * file-scope device array of about 3.3 MiB that every GPU loading libsr keeps
+ * until the process exits; calls with more than SR_NOALLOC_MAX_READS reads or
+ * SR_NOALLOC_MAX_ITEMS windows are rejected with SR_EINVAL.
+ *  - Inputs: d_bases/d_read_off (CSR ASCII reads, offsets from 0), d_cand_off
+ *    (n_reads + 1 window offsets from 0 ending at n_items) and the per-window
+ *    d_ref_id/d_strand/d_win_start/d_win_len, all device pointers; references
+ *    come from the session.  Outputs: d_item_score, d_item_end (n_items each).
+ *  - Scores must fit the packed 16-bit kernel (match + gap_open + 2*gap_extend
+ *    small, match * 256 <= 31743); otherwise SR_EINVAL (use sr_align_batch).
+ *  - Runs on cuda_stream (NULL = default stream) and returns when the work is
+ *    done; bad offsets, reads or windows give SR_EINVAL / SR_EBADBASE.
+ *  - The first call on a device looks up the scratch array's device address
+ *    with that device current; make that first call before any stream capture.
+ *  - All calls share the one scratch array: calls whose work overlaps on the
+ *    GPU (two host threads, or two streams) race on it. */
+#define SR_NOALLOC_MAX_READS 32768u
+#define SR_NOALLOC_MAX_ITEMS 262144u
+sr_status sr_align_items_noalloc(sr_session* s, const char* d_bases, const uint64_t* d_read_off,
+                                 uint32_t n_reads, const uint64_t* d_cand_off,
+                                 const uint8_t* d_ref_id, const uint8_t* d_strand,
+                                 const uint64_t* d_win_start, const uint32_t* d_win_len,
+                                 uint64_t n_items, const sr_score_params* sp,
+                                 int32_t* d_item_score, uint32_t* d_item_end, void* cuda_stream);
+
 /* ------------------------------------------------------- measurement
  * Issue-rate probe of the packed 16-bit DPX max/add-max instructions: returns
  * lane-operations per clock per SM measured with CUDA events (and the clock

@@ -239,6 +239,7 @@ uint64_t session_budget(sr_session* s) { return s->hbm_budget; }
 std::atomic<uint64_t>& session_used(sr_session* s) { return s->hbm_used; }
 Server*& session_server(sr_session* s) { return s->server; }
 uint32_t session_n_refs(sr_session* s) { return s->n_refs; }
+const DevRefs& session_refs(sr_session* s) { return s->refs; }
 }  // namespace sr
 
 // ------------------------------------------------------------------ batches

@@ -139,6 +139,8 @@ def lib():
             "sr_tune_get": ([P, P, P, P, C.c_uint32], C.c_int32),
             "sr_tune_set": ([C.c_uint32, P, P, P], C.c_int32),
             "sr_probe_dpx": ([P, P], C.c_int32),
+            "sr_align_items_noalloc": ([P, P, P, C.c_uint32, P, P, P, P, P, C.c_uint64,
+                                        C.POINTER(ScoreParams), P, P, P], C.c_int32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)

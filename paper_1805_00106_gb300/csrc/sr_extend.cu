@@ -60,6 +60,7 @@ struct ExtArgs {
   DevRefs refs;
   int32_t* item_score;
   uint32_t* item_end;
+  uint32_t* item_iend;          // winner end-row search (mode 2): smallest row at the end column
   uint32_t* status;
   uint64_t n_items;             // plain engine: items in input order
   int cls;
@@ -135,12 +136,12 @@ struct ItemDesc {
   uint64_t ws;
 };
 
-__device__ __forceinline__ ItemDesc load_item(const ExtArgs& a, uint32_t item) {
+__device__ __forceinline__ ItemDesc load_item(const ExtArgs& a, uint32_t item, bool to_end) {
   ItemDesc d;
   d.item = item;
   d.read = a.item_read[item];
   d.m = a.rlen[d.read];
-  d.n = a.c_len[item];
+  d.n = to_end ? a.item_end[item] : a.c_len[item];
   d.strand = a.c_strand[item];
   d.ref = a.c_ref[item];
   d.ws = a.c_start[item];
@@ -210,10 +211,10 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
     if (has_task) {
       uint32_t p0 = begin + 2 * task;
       uint32_t i0 = a.order ? a.order[p0] : p0;
-      lo = load_item(a, i0);
+      lo = load_item(a, i0, MODE == 2);
       if (2 * task + 1 < count) {
         uint32_t i1 = a.order ? a.order[p0 + 1] : p0 + 1;
-        hi = load_item(a, i1);
+        hi = load_item(a, i1, MODE == 2);
         hi_valid = true;
       } else {
         hi = lo;
@@ -236,11 +237,11 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
 
     // ---- per-row substitution tables (a4: query profile in registers)
     uint32_t TL[R], TH[R];
+    const int padlo = G * R - static_cast<int>(lo.m);
+    const int padhi = G * R - static_cast<int>(hi.m);
     {
       const uint32_t* rowlo = a.rpack + static_cast<size_t>(lo.read) * kReadWords;
       const uint32_t* rowhi = a.rpack + static_cast<size_t>(hi.read) * kReadWords;
-      const int padlo = G * R - static_cast<int>(lo.m);
-      const int padhi = G * R - static_cast<int>(hi.m);
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         const int r = glane * R + k;
@@ -292,6 +293,12 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
     }
     uint32_t tprev = INIT, Tbot = INIT, Fbot = INIT, best = INIT;
     uint32_t jlo = 0, jhi = 0;
+    // mode 2: biased T value of the winner's score in each half, rows found
+    uint32_t tgt_lo = 0, tgt_hi = 0, ilo = 0xffffffffu, ihi = 0xffffffffu;
+    if (MODE == 2 && has_task) {
+      tgt_lo = static_cast<uint32_t>(a.item_score[lo.item] - goe + kBias);
+      tgt_hi = static_cast<uint32_t>(a.item_score[hi.item] - goe + kBias);
+    }
     const uint32_t lastmask = (MODE == 1 && glane == G - 1) ? FULL : 0u;
     const int nsteps = static_cast<int>(__reduce_max_sync(FULL, nmax)) + G - 1;
     for (int s = 0; s < nsteps; ++s) {
@@ -320,6 +327,19 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
         tprev = tin;
         Tbot = T[R - 1];
         Fbot = f;
+        if (MODE == 2) {
+          if (j == static_cast<int>(lo.n) - 1) {
+#pragma unroll
+            for (int k = R - 1; k >= 0; --k)
+              if ((T[k] & 0xffffu) == tgt_lo) ilo = static_cast<uint32_t>(glane * R + k - padlo + 1);
+          }
+          if (j == static_cast<int>(hi.n) - 1) {
+#pragma unroll
+            for (int k = R - 1; k >= 0; --k)
+              if ((T[k] >> 16) == tgt_hi) ihi = static_cast<uint32_t>(glane * R + k - padhi + 1);
+          }
+          continue;
+        }
         uint32_t cm;
         if (MODE == 1) {
           cm = T[R - 1] & lastmask;
@@ -338,6 +358,19 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
       }
     }
 
+    if (MODE == 2) {
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) {
+        ilo = min(ilo, __shfl_xor_sync(FULL, ilo, off, G));
+        ihi = min(ihi, __shfl_xor_sync(FULL, ihi, off, G));
+      }
+      if (has_task && glane == 0) {
+        a.item_iend[lo.item] = ilo;
+        if (hi_valid) a.item_iend[hi.item] = ihi;
+      }
+      __syncwarp();
+      continue;
+    }
     // ---- group reduction of (score, -column) and write-back
     const int32_t base_t = kBias - goe;
     const uint32_t slo = (best & 0xffffu) - base_t;
@@ -381,7 +414,7 @@ __global__ void __launch_bounds__(128) k_extend32(ExtArgs a) {
     if (lane == 0) t0 = atomicAdd(a.queue + a.cls, 1u);
     const uint32_t task = __shfl_sync(FULL, t0, 0);
     if (task >= count) break;
-    const ItemDesc it = load_item(a, a.order[begin + task]);
+    const ItemDesc it = load_item(a, a.order[begin + task], false);
     const uint32_t* row = a.rpack + static_cast<size_t>(it.read) * kReadWords;
     const uint32_t* ref = a.refs.words[it.ref];
     for (uint32_t j = lane; j < it.n; j += 32) {
@@ -524,6 +557,7 @@ ExtArgs make_args(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc) 
   a.refs = refs;
   a.item_score = b.item_score;
   a.item_end = b.item_end;
+  a.item_iend = b.item_iend;
   a.status = b.status;
   a.n_items = b.n_items;
   a.sa = sc.sa;
@@ -534,6 +568,27 @@ ExtArgs make_args(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc) 
 }
 
 }  // namespace
+
+int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
+                       const TuneBin* bins, int n_bins, bool plain, uint32_t lanes, uint32_t rows,
+                       cudaStream_t st) {
+  ExtArgs a = make_args(b, refs, sc);
+  a.order = b.order;  // winners compacted per class
+  a.class_range = b.wrange;
+  a.queue = b.wqueue;
+  a.item_iend = b.item_iend;
+  int launched = 0;
+  const int classes = plain ? 1 : n_bins;
+  for (int c = 0; c < classes; ++c) {
+    a.cls = c;
+    uint32_t g = lanes ? lanes : (plain ? 16u : bins[c].lanes);
+    uint32_t r = rows ? rows : (plain ? 16u : bins[c].rows);
+    int k = dispatch16<2, true>(g, r, a, st, 0);
+    if (k < 0) return -1;
+    launched += k;
+  }
+  return launched;
+}
 
 bool extend_config_supported(uint32_t lanes, uint32_t rows) {
 #define SR_CHK(g, r) \

@@ -83,6 +83,11 @@ struct BatchDev {
   uint32_t* item_end = nullptr;
   DevHit* hits = nullptr;         // n_reads * (1 + n_refs)
   uint32_t* cigar_slots = nullptr;  // n_reads * kCigarStride
+  uint32_t* item_iend = nullptr;  // n_items: end row of winning items (traceback)
+  uint32_t* wcount = nullptr;     // kNumClasses: winners per class
+  uint32_t* wrange = nullptr;     // 2 * kNumClasses: winner ranges in `order`
+  uint32_t* wqueue = nullptr;     // kNumClasses + 8: winner-pass task counters
+  uint8_t* need_full = nullptr;   // n_reads: winner needs the full-rectangle traceback
   uint32_t* cigar_off = nullptr;  // n_reads + 1 (exclusive scan of lengths)
   uint32_t* cigar = nullptr;      // compacted, n_reads * kCigarStride capacity
   uint8_t* read_class = nullptr;  // n_reads
@@ -105,6 +110,10 @@ int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
                   const TuneBin* bins, int n_bins, int mode, bool plain, uint32_t lanes,
                   uint32_t rows, cudaStream_t st);
 int launch_select(const BatchDev& b, int n_refs, cudaStream_t st);
+int launch_winners(const BatchDev& b, int n_refs, bool plain, cudaStream_t st);
+int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
+                       const TuneBin* bins, int n_bins, bool plain, uint32_t lanes, uint32_t rows,
+                       cudaStream_t st);
 int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, int mode,
                      int n_refs, cudaStream_t st);
 int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);

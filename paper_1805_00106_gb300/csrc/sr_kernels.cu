@@ -238,6 +238,36 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
   }
 }
 
+// winners of the int16 classes, compacted per class into `order` (whose class
+// ranges hold at least as many slots); int32-class winners are marked for the
+// full-rectangle traceback
+__global__ void k_winners(uint32_t n_reads, int slots, const DevHit* hits, const uint16_t* item_key,
+                          const uint32_t* class_range, bool plain, uint32_t* wcount, uint32_t* order,
+                          uint8_t* need_full) {
+  const uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (r >= n_reads) return;
+  const DevHit h = hits[r * slots];
+  uint8_t full = 0;
+  if (h.item >= 0 && h.score > 0) {
+    const uint32_t cls = plain ? 0u : static_cast<uint32_t>(item_key[h.item]) / kKeysPerClass;
+    if (cls >= static_cast<uint32_t>(kNumBins)) {
+      full = 1;
+    } else {
+      const uint32_t pos = atomicAdd(&wcount[cls], 1u);
+      order[(plain ? 0u : class_range[2 * cls]) + pos] = static_cast<uint32_t>(h.item);
+    }
+  }
+  need_full[r] = full;
+}
+
+__global__ void k_wrange(const uint32_t* class_range, const uint32_t* wcount, bool plain, uint32_t* wrange) {
+  const int c = threadIdx.x;
+  if (c >= kNumClasses) return;
+  const uint32_t b = plain ? 0u : class_range[2 * c];
+  wrange[2 * c] = b;
+  wrange[2 * c + 1] = b + (c < kNumBins ? wcount[c] : 0u);
+}
+
 __global__ void k_classify(uint32_t n_reads, int n_refs, const DevHit* hits, int32_t min_score,
                            int32_t margin, uint8_t* cls) {
   const uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
@@ -370,6 +400,17 @@ int launch_select(const BatchDev& b, int n_refs, cudaStream_t st) {
       b.cand_off, b.n_reads, b.item_score, b.item_end, b.c_ref, b.c_strand, b.c_start, n_refs,
       b.hits);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_winners(const BatchDev& b, int n_refs, bool plain, cudaStream_t st) {
+  if (b.n_reads == 0) return 0;
+  if (cudaMemsetAsync(b.wcount, 0, sizeof(uint32_t) * kNumClasses, st) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(b.wqueue, 0, sizeof(uint32_t) * (kNumClasses + 8), st) != cudaSuccess) return -1;
+  k_winners<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, 1 + n_refs, b.hits, b.item_key,
+                                                     b.class_range, plain, b.wcount, b.order,
+                                                     b.need_full);
+  k_wrange<<<1, 32, 0, st>>>(b.class_range, b.wcount, plain, b.wrange);
+  return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
 int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,

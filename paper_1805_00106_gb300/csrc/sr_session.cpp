@@ -299,6 +299,11 @@ uint64_t batch_bytes_estimate(uint32_t n_reads, uint64_t n_items, uint64_t n_bas
   c.take(p4, static_cast<uint64_t>(n_reads) * kCigarStride);
   c.take(p1, n_reads);
   c.take(p4, n_reads / 1024 + 4ull);
+  c.take(p4, n_items);
+  c.take(p4, kNumClasses);
+  c.take(p4, 2 * kNumClasses);
+  c.take(p4, kNumClasses + 8);
+  c.take(p1, n_reads);
   return c.off + 256;
 }
 }  // namespace sr
@@ -391,6 +396,11 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   c.take(d.cigar, static_cast<uint64_t>(n) * kCigarStride);
   c.take(d.read_class, n);
   c.take(d.scan_tmp, n / 1024 + 4ull);
+  c.take(d.item_iend, nc);
+  c.take(d.wcount, kNumClasses);
+  c.take(d.wrange, 2 * kNumClasses);
+  c.take(d.wqueue, kNumClasses + 8);
+  c.take(d.need_full, n);
   b->bytes = c.off + 256;
   cudaError_t e = cudaMalloc(&b->arena, b->bytes);
   if (e != cudaSuccess) {
@@ -425,6 +435,11 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   rebase(d.cigar, base);
   rebase(d.read_class, base);
   rebase(d.scan_tmp, base);
+  rebase(d.item_iend, base);
+  rebase(d.wcount, base);
+  rebase(d.wrange, base);
+  rebase(d.wqueue, base);
+  rebase(d.need_full, base);
   d.n_reads = n;
   d.n_items = nc;
   s->hbm_used += b->bytes;
@@ -521,6 +536,12 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
   k += t;
   if (!mark(4)) return -1;
   if (o.want_cigar) {
+    if ((t = launch_winners(d, nr, plain, st)) < 0) return -1;
+    k += t;
+    if (o.mode == SR_MODE_LOCAL && b->n_items) {
+      if ((t = launch_winner_rows(d, b->s->refs, sc, bins, kNumBins, plain, o.lanes, o.rows, st)) < 0) return -1;
+      k += t;
+    }
     if ((t = launch_traceback(d, b->s->refs, sc, static_cast<int>(o.mode), nr, st)) < 0) return -1;
     k += t;
     if ((t = launch_cigar_compact(d, nr, st)) < 0) return -1;

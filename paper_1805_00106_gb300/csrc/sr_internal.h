@@ -88,6 +88,8 @@ struct BatchDev {
   uint32_t* wrange = nullptr;     // 2 * kNumClasses: winner ranges in `order`
   uint32_t* wqueue = nullptr;     // kNumClasses + 8: winner-pass task counters
   uint8_t* need_full = nullptr;   // n_reads: winner needs the full-rectangle traceback
+  uint32_t* tb_list = nullptr;    // 4 * n_reads: reads per traceback kernel (band <= 8/16/32, full)
+  uint32_t* tb_count = nullptr;   // 4 counters
   uint32_t* cigar_off = nullptr;  // n_reads + 1 (exclusive scan of lengths)
   uint32_t* cigar = nullptr;      // compacted, n_reads * kCigarStride capacity
   uint8_t* read_class = nullptr;  // n_reads

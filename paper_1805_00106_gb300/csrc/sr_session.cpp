@@ -304,6 +304,8 @@ uint64_t batch_bytes_estimate(uint32_t n_reads, uint64_t n_items, uint64_t n_bas
   c.take(p4, 2 * kNumClasses);
   c.take(p4, kNumClasses + 8);
   c.take(p1, n_reads);
+  c.take(p4, 4ull * n_reads);
+  c.take(p4, 4);
   return c.off + 256;
 }
 }  // namespace sr
@@ -401,6 +403,8 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   c.take(d.wrange, 2 * kNumClasses);
   c.take(d.wqueue, kNumClasses + 8);
   c.take(d.need_full, n);
+  c.take(d.tb_list, 4ull * n);
+  c.take(d.tb_count, 4);
   b->bytes = c.off + 256;
   cudaError_t e = cudaMalloc(&b->arena, b->bytes);
   if (e != cudaSuccess) {
@@ -440,6 +444,8 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   rebase(d.wrange, base);
   rebase(d.wqueue, base);
   rebase(d.need_full, base);
+  rebase(d.tb_list, base);
+  rebase(d.tb_count, base);
   d.n_reads = n;
   d.n_items = nc;
   s->hbm_used += b->bytes;

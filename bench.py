@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="wall budget of the oracle sample")
-    ap.add_argument("--tune", action="store_true", help="run the autotuner before timing")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default bins)")
     return ap.parse_args()
 
 
@@ -104,9 +104,11 @@ class Clocks:
 
 
 def kernel_hash():
+    """Hash of the extension kernels' source (the kernel the roofline reports)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1805_00106_gb300", "csrc", "sr_extend.cu"), "rb") as f:
-        h.update(f.read())
+    for f in ["sr_extend.cuh", "sr_extend.cu"]:
+        with open(os.path.join(ROOT, "paper_1805_00106_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -222,7 +224,7 @@ def main():
     n_items = int(w["cand_off"][-1])
     sess = sr.Session.open([bytes(r) for r in w["refs"]])
     spp = sr.score_params(*SP)
-    if args.tune:
+    if not args.no_tune:
         sr.lib().sr_tune(sess.h, sr.C.byref(spp), 4096)
     stream = torch.cuda.Stream()
     batch = sess.stage(w["bases"], w["read_off"], w["cand_off"], w["c_ref"], w["c_strand"],

@@ -122,6 +122,8 @@ int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);
 int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,
                     cudaStream_t st);
 bool extend_config_supported(uint32_t lanes, uint32_t rows);
+// the built (lanes, rows) shapes; returns how many there are
+int extend_shapes(uint32_t* lanes, uint32_t* rows, int cap);
 int probe_dpx(double* lane_ops_per_clk_per_sm, double* clk_mhz);
 
 }  // namespace sr

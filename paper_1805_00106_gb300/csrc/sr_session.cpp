@@ -38,8 +38,9 @@ static sr_status cuda_error(const char* where, cudaError_t e) {
 
 // ---- autotuner table (read-length bins -> kernel shape)
 static std::mutex g_tune_mu;
-static TuneBin g_bins[kNumBins] = {{64, 4, 16},   {80, 8, 10},   {96, 8, 12},   {128, 8, 16},
-                                   {160, 16, 10}, {192, 16, 12}, {224, 16, 14}, {256, 16, 16}};
+// defaults = the autotuner's picks on GB300 for the c2 score parameters
+static TuneBin g_bins[kNumBins] = {{64, 4, 16},  {80, 4, 24},   {96, 4, 24},  {128, 8, 16},
+                                   {160, 8, 20}, {192, 16, 12}, {224, 8, 28}, {256, 16, 16}};
 
 void tune_get_bins(TuneBin* out) {
   std::lock_guard<std::mutex> g(g_tune_mu);
@@ -576,6 +577,8 @@ sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp,
   if (o.mode > 1 || o.engine > 1) return set_error(SR_EINVAL, "sr_batch_run: bad mode/engine");
   if ((o.lanes || o.rows) && !extend_config_supported(o.lanes, o.rows))
     return set_error(SR_EINVAL, "sr_batch_run: unsupported lanes x rows shape");
+  if (o.engine == SR_ENGINE_PLAIN && o.lanes && !((o.lanes == 16 && o.rows == 16) || (o.lanes == 32 && o.rows == 8)))
+    return set_error(SR_EINVAL, "sr_batch_run: the plain engine runs the 16x16 or 32x8 shape");
   if (o.lanes && o.lanes * o.rows < std::max<uint32_t>(b->max_m, 1))
     return set_error(SR_EINVAL, "sr_batch_run: lanes*rows must cover the longest read of the batch");
   if (o.classify && s->n_refs < 2) return set_error(SR_EINVAL, "sr_batch_run: classification needs 2 references");
@@ -883,8 +886,9 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
   sr_status st = check_score(sp);
   if (st != SR_OK) return st;
   if (sample_reads == 0) sample_reads = 4096;
-  static const uint32_t shapes[][2] = {{4, 16}, {8, 8},   {8, 10},  {8, 12},  {8, 16},  {16, 6},
-                                       {16, 8}, {16, 10}, {16, 12}, {16, 14}, {16, 16}, {32, 8}};
+  uint32_t sh_lanes[64], sh_rows[64];
+  const int n_shapes = std::min(64, extend_shapes(sh_lanes, sh_rows, 64));
+  const bool verbose = getenv("SR_TUNE_VERBOSE") != nullptr;
   TuneBin cur[kNumBins];
   tune_get_bins(cur);
   uint64_t rng = 0x9E3779B97F4A7C15ull;
@@ -930,7 +934,8 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
     if (st != SR_OK) break;
     float best_ms = 1e30f;
     TuneBin pick = cur[bi];
-    for (auto& sh : shapes) {
+    for (int q = 0; q < n_shapes; ++q) {
+      const uint32_t sh[2] = {sh_lanes[q], sh_rows[q]};
       if (sh[0] * sh[1] < m || sh[0] * sh[1] > 2 * m + 64) continue;
       sr_align_opts o = default_opts();
       o.want_cigar = 0;
@@ -946,6 +951,8 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
       if (ok) ok = batch_sync(b, b->stream) == SR_OK;
       if (!ok) continue;
       cudaEventElapsedTime(&tot, e0, e1);
+      if (verbose)
+        fprintf(stderr, "sr_tune bin<=%u lanes %u rows %u: %.3f ms for 3 runs\n", m, sh[0], sh[1], tot);
       if (tot < best_ms) {
         best_ms = tot;
         pick = TuneBin{m, sh[0], sh[1]};

@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="wall budget of the oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default bins)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving latency run")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="duration of each offered load")
     return ap.parse_args()
 
 
@@ -171,6 +173,81 @@ def slice_reads(w, r0, r1):
     return dict(refs=w["refs"], bases=w["bases"][b0:b1], read_off=ro[r0:r1 + 1] - b0,
                 cand_off=co[r0:r1 + 1] - c0, c_ref=w["c_ref"][c0:c1], c_strand=w["c_strand"][c0:c1],
                 c_start=w["c_start"][c0:c1], c_len=w["c_len"][c0:c1])
+
+
+def serving_bench(sr, scale, seconds=4.0, pool_size=48, seed=404):
+    """Continuous batching on the xenograft reference pair (64 Mbp A and a diverged
+    B, held on the device): requests of 1-4096 reads (75-250 bp, 0-64 windows
+    each) arrive as a Poisson process at 0.25x, 0.5x and 0.9x of the served
+    saturation rate; latency is submit -> completion per request."""
+    import threading
+    from paper_1805_00106_gb300 import synth
+    a = synth.ref_iid(max(20000, int(64_000_000 * scale)), seed)
+    b = synth.mutate(a, seed + 1, 0.15, 0.02, 50 if scale >= 0.5 else 2,
+                     min(10_000, len(a) // 40), min(1_000_000, len(a) // 20))
+    pool = synth.serving_batches([a, b], pool_size, seed + 2)
+    keys = ["bases", "read_off", "cand_off", "c_ref", "c_strand", "c_start", "c_len"]
+    sess = sr.Session.open([bytes(a), bytes(b)], hbm_budget=8 << 30)
+    spp = sr.score_params(*SP)
+    opts = sr.align_opts(classify=True)
+
+    def run(rate, duration, burst=False):
+        sess.serve_start(spp, opts)
+        rng = np.random.default_rng(seed)
+        tickets, reads = [], []
+        t0 = time.perf_counter()
+        done = threading.Event()
+
+        def waiter():
+            i = 0
+            while not (done.is_set() and i >= len(tickets)):
+                if i < len(tickets):
+                    sess.wait(tickets[i], timeout_ms=120_000)
+                    i += 1
+                else:
+                    time.sleep(0.0005)
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        nxt = t0
+        k = 0
+        while True:
+            now = time.perf_counter()
+            if burst:
+                if k >= len(pool):
+                    break
+            elif now - t0 >= duration:
+                break
+            if not burst and now < nxt:
+                time.sleep(min(nxt - now, 0.002))
+                continue
+            q = pool[k % len(pool)]
+            tickets.append(sess.submit(*[q[kk] for kk in keys]))
+            reads.append(len(q["read_off"]) - 1)
+            k += 1
+            if not burst:
+                nxt += rng.exponential(1.0 / rate)
+        done.set()
+        th.join()
+        el = time.perf_counter() - t0
+        st = sess.serve_stats()
+        sess.serve_stop()
+        return dict(requests=len(tickets), req_per_s=round(len(tickets) / el, 2),
+                    reads_per_s=round(sum(reads) / el, 1), p50_ms=round(st["p50_us"] / 1e3, 3),
+                    p99_ms=round(st["p99_us"] / 1e3, 3), rounds=st["rounds"],
+                    max_round_requests=st["max_round_requests"])
+
+    run(1.0, 0, burst=True)  # warm-up: graph shapes, host pages
+    sat = run(1.0, 0, burst=True)
+    out = {"workload": "xenograft pair 64 Mbp (A, B = A with 15% substitutions, 2% indels, 50 block "
+                       "moves); requests of 1-4096 reads, 75-250 bp, 0-64 windows each; Poisson arrivals",
+           "saturation": {"req_per_s": sat["req_per_s"], "reads_per_s": sat["reads_per_s"]}, "loads": []}
+    for f in (0.25, 0.5, 0.9):
+        r = run(f * sat["req_per_s"], seconds)
+        r["offered"] = f
+        out["loads"].append(r)
+    sess.close()
+    return out
 
 
 def make_workload(scale, rank):
@@ -336,6 +413,8 @@ def main():
         line["e2e"] = {"value": round(cells / e2e_t / 1e9, 3), "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "ms_per_step": round(1e3 * e2e_t, 2),
                        "reads_per_s": round(n_reads / e2e_t, 1)}
+    if rank == 0 and not args.no_serve:
+        line["serving"] = serving_bench(sr, args.scale, args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(w, args.cpu_seconds).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}

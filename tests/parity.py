@@ -73,3 +73,98 @@ def compare(g, o, reads=None, want_cigar=True, classify=None):
         if not np.array_equal(g["read_class"], exp):
             bad.append(f"class differs at {int(np.sum(g['read_class'] != exp))} reads")
     return bad
+
+
+def subset_reads(w, reads):
+    """Workload restricted to `reads` (in that order), offsets rebased."""
+    reads = np.asarray(reads, np.int64)
+    ro, co = np.asarray(w["read_off"], np.int64), np.asarray(w["cand_off"], np.int64)
+    bases = np.concatenate([w["bases"][ro[r]:ro[r + 1]] for r in reads])
+    lens = ro[reads + 1] - ro[reads]
+    cnts = co[reads + 1] - co[reads]
+    items = np.concatenate([np.arange(co[r], co[r + 1]) for r in reads]) if cnts.sum() else np.zeros(0, np.int64)
+    out = dict(refs=w["refs"], bases=bases, read_off=np.concatenate([[0], np.cumsum(lens)]),
+               cand_off=np.concatenate([[0], np.cumsum(cnts)]))
+    for k in ["c_ref", "c_strand", "c_start", "c_len"]:
+        out[k] = np.asarray(w[k])[items]
+    return out
+
+
+def compare_sampled(g, w, reads, o, want_cigar=True, classify=None):
+    """Compare the GPU results of a whole batch, on the sampled reads only, with
+    the oracle's results `o` for the subset workload of those reads."""
+    bad = []
+    co = np.asarray(w["cand_off"], np.int64)
+    so = 0
+    for s, r in enumerate(reads):
+        c0, c1 = co[r], co[r + 1]
+        n = c1 - c0
+        if not np.array_equal(g["item_score"][c0:c1], o["item_score"][so:so + n]):
+            bad.append(f"read {r}: item scores differ")
+        if not np.array_equal(g["item_end"][c0:c1].astype(np.int64), o["item_end_j"][so:so + n].astype(np.int64)):
+            bad.append(f"read {r}: item ends differ")
+        gb, ob = g["best"][r], o["best"][s]
+        for f in ["score", "second", "n_ties"]:
+            if int(gb[f]) != int(ob[f]):
+                bad.append(f"read {r}: best.{f} {gb[f]} vs {ob[f]}")
+        gi = int(gb["item"]) - c0 if gb["item"] >= 0 else -1
+        oi = int(ob["item"]) - so if ob["item"] >= 0 else -1
+        if gi != oi:
+            bad.append(f"read {r}: winner {gi} vs {oi}")
+        if ob["item"] >= 0:
+            for f in ["ref_id", "strand", "ref_end"] + (["ref_start", "read_start", "read_end", "cigar_len"] if want_cigar else []):
+                if int(gb[f]) != int(ob[f]):
+                    bad.append(f"read {r}: best.{f} {gb[f]} vs {ob[f]}")
+            if want_cigar:
+                gc = g["cigar"][int(gb["cigar_off"]): int(gb["cigar_off"]) + int(gb["cigar_len"])]
+                if not np.array_equal(gc, o["cigar"][s][: int(ob["cigar_len"])]):
+                    bad.append(f"read {r}: CIGAR differs")
+        for q in range(g["best_per_ref"].shape[1]):
+            gp, op = g["best_per_ref"][r, q], o["best_per_ref"][s, q]
+            if int(gp["score"]) != int(op["score"]) or int(gp["n_ties"]) != int(op["n_ties"]) or \
+               int(gp["second"]) != int(op["second"]):
+                bad.append(f"read {r}: per-ref {q} differs")
+        if classify is not None:
+            exp = O.classify(int(o["best_per_ref"][s, 0]["score"]), int(o["best_per_ref"][s, 1]["score"]),
+                             classify[0], classify[1])
+            if int(g["read_class"][r]) != exp:
+                bad.append(f"read {r}: class {g['read_class'][r]} vs {exp}")
+        so += n
+        if len(bad) > 20:
+            break
+    return bad
+
+
+def whole_batch_properties(g, w):
+    """Properties that hold at any size: the winner's score is the read's largest
+    item score, ties and second are consistent, CIGARs consume the read."""
+    co = np.asarray(w["cand_off"], np.int64)
+    ro = np.asarray(w["read_off"], np.int64)
+    sc = g["item_score"]
+    n = len(ro) - 1
+    mx = np.zeros(n, np.int64)
+    has = np.diff(co) > 0
+    if len(sc):
+        red = np.maximum.reduceat(sc.astype(np.int64), co[:-1][has]) if has.any() else np.zeros(0)
+        mx[has] = red
+    b = g["best"]
+    bad = []
+    if not np.array_equal(np.maximum(mx, 0), b["score"].astype(np.int64)):
+        bad.append("best score is not the largest item score")
+    pos = b["score"] > 0
+    if np.any(b["n_ties"][pos] < 1) or np.any(b["n_ties"][~pos] != 0):
+        bad.append("n_ties inconsistent")
+    if np.any(b["second"] > b["score"]):
+        bad.append("second > best")
+    if np.any(sc[b["item"][pos]] != b["score"][pos]):
+        bad.append("winner item does not carry the best score")
+    # CIGAR lengths: M+I+S == read length for every winner
+    cig = g["cigar"]
+    idx = np.nonzero(pos)[0]
+    for r in idx[:: max(1, len(idx) // 20000)]:
+        words = cig[int(b["cigar_off"][r]): int(b["cigar_off"][r]) + int(b["cigar_len"][r])]
+        ops, lens = words & 15, words >> 4
+        if int(lens[(ops == 0) | (ops == 1) | (ops == 4)].sum()) != ro[r + 1] - ro[r]:
+            bad.append(f"read {r}: CIGAR does not consume the read")
+            break
+    return bad

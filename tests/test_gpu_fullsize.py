@@ -1,0 +1,76 @@
+"""GPU path at the full sizes of the workloads (-m gpu), in the launch
+configuration bench.py times (batched engine, default bins, winner CIGARs).
+
+c1 is checked against the oracle on every read; c2, c3 and c5 on a random
+sample of reads the oracle computes one by one, plus size-independent
+properties on every read.  c3's windows come from the host index
+(sr_candidates), which tests/test_host_stage.py pins to the oracle's
+brute-force CAL finder on small references."""
+import numpy as np
+import pytest
+
+from paper_1805_00106_gb300 import synth as S
+
+from .parity import compare, compare_sampled, oracle_run, subset_reads, whole_batch_properties
+
+pytestmark = pytest.mark.gpu
+KEYS = ["bases", "read_off", "cand_off", "c_ref", "c_strand", "c_start", "c_len"]
+
+
+@pytest.fixture(scope="module")
+def sr():
+    from paper_1805_00106_gb300 import sr as _sr
+    _sr.lib()
+    return _sr
+
+
+def _run(sr, s, w, **opts):
+    return s.align(*[w[k] for k in KEYS], sr.score_params(2, 3, 5, 2), sr.align_opts(**opts))
+
+
+def _sampled(sr, w, g, n, seed, **kw):
+    rng = np.random.default_rng(seed)
+    reads = np.sort(rng.choice(len(w["read_off"]) - 1, size=min(n, len(w["read_off"]) - 1), replace=False))
+    sub = subset_reads(w, reads)
+    o = oracle_run(sub, threads=8)
+    bad = compare_sampled(g, w, reads, o, **kw)
+    assert not bad, "\n".join(bad[:20])
+    bad = whole_batch_properties(g, w)
+    assert not bad, bad
+
+
+def test_c1_full_every_read(sr):
+    w = S.workload("c1")
+    s = sr.Session.open([bytes(r) for r in w["refs"]])
+    g = _run(sr, s, w)
+    bad = compare(g, oracle_run(w, threads=8))
+    assert not bad, bad
+
+
+def test_c2_full_sampled(sr):
+    w = S.workload("c2")
+    s = sr.Session.open([bytes(r) for r in w["refs"]])
+    g = _run(sr, s, w)
+    assert g["n_items"] > 5_900_000
+    _sampled(sr, w, g, 1500, 1)
+
+
+def test_c3_full_sampled_with_classification(sr):
+    w = S.workload("c3")
+    idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=12, cal_limit=1024) for r in w["refs"]]
+    w.update(sr.candidates(idx, w["bases"], w["read_off"], seed_stride=1, merge_dist=32, pad=32))
+    s = sr.Session.from_indexes(idx)
+    g = _run(sr, s, w, classify=True, min_score=40, margin=5)
+    _sampled(sr, w, g, 1500, 2, classify=(40, 5))
+    # classification against the generator's truth (informational bound)
+    truth = w["t_ref"] + 1
+    correct = float(np.mean(g["read_class"] == truth))
+    assert correct > 0.8, correct
+
+
+def test_c5_full_sampled(sr):
+    w = S.workload("c5")
+    s = sr.Session.open([bytes(r) for r in w["refs"]])
+    g = _run(sr, s, w)
+    assert int(np.diff(w["cand_off"]).max()) == 256
+    _sampled(sr, w, g, 800, 3)

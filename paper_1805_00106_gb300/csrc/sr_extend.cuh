@@ -78,12 +78,26 @@ namespace {
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int kStageWords = 40;      // >= 36 words needed for a 512-base window
 constexpr long kWaitLimit = 1 << 22; // bounded mbarrier polls
+constexpr int kColLead = 32;         // >= G - 1 virtual columns before column 0
+
+// Selector of a real column: the low half of the result is byte b_lo of the lo
+// table sign-extended, the high half byte 4 + b_hi (the hi table) sign-extended.
+// A virtual half picks the sign of a byte for both of its bytes, so its score
+// term is 0 or -1, below go + ge.  With it, a lane may run columns outside an
+// item's window: before column 0 every value stays at the H = 0 border
+// (H(i-1,j-1) + s - (go+ge) < 0), and past the last column every value is
+// strictly below the best real cell already seen (each term subtracts ge or
+// more from a real value), so neither changes the tracked best.
+constexpr uint32_t kSelLo = 0x0080u, kSelHi = 0xC400u;
+constexpr uint32_t kVirtLo = 0x0088u, kVirtHi = 0xCC00u;
 
 struct __align__(16) GroupSmem {
   uint32_t stage[2][kStageWords];  // 16-byte aligned TMA destinations
   unsigned long long mbar;
   uint32_t pad[2];
-  uint16_t col[kMaxWinLen];        // per column: PRMT selector of the two items' bases
+  // per column j (stored at j + kColLead): PRMT selector of the two items' bases;
+  // columns before the window and past each item's end hold the virtual selector
+  uint16_t col[kMaxWinLen + 2 * kColLead];
 };
 static_assert(sizeof(GroupSmem) % 16 == 0, "group smem alignment");
 
@@ -199,6 +213,7 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
     mbar_init(&gs->mbar, 1);
     fence_mbar_init();
   }
+  for (int c = glane; c < kColLead; c += G) gs->col[c] = static_cast<uint16_t>(kVirtLo | kVirtHi);
   __syncwarp();
   uint32_t phase = 0;
 
@@ -292,13 +307,18 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
     }
     if (__any_sync(FULL, !ok)) break;
     const uint32_t nmax = has_task ? max(lo.n, hi.n) : 0u;
-    if (has_task) {
+    const uint32_t nlo = has_task ? lo.n : 0u, nhi = has_task ? hi.n : 0u;
+    const uint32_t wmax = __reduce_max_sync(FULL, nmax);
+    const int nsteps = static_cast<int>(wmax) + G - 1;
+    {
+      // real columns, then virtual ones up to the last column any lane of the warp reaches
       const uint32_t offlo = static_cast<uint32_t>(lo.ws - (w0lo << 4));
       const uint32_t offhi = static_cast<uint32_t>(hi.ws - (w0hi << 4));
-      for (uint32_t j = glane; j < nmax; j += G) {
-        uint32_t blo = j < lo.n ? base_at(gs->stage[0], offlo + j) : 0u;
-        uint32_t bhi = j < hi.n ? base_at(gs->stage[1], offhi + j) : 0u;
-        gs->col[j] = static_cast<uint16_t>(0xC480u + blo * 0x11u + bhi * 0x1100u);
+      const uint32_t ncol = wmax + G - 1;
+      for (uint32_t j = glane; j < ncol; j += G) {
+        const uint32_t vlo = j < nlo ? kSelLo + base_at(gs->stage[0], offlo + j) * 0x11u : kVirtLo;
+        const uint32_t vhi = j < nhi ? kSelHi + base_at(gs->stage[1], offhi + j) * 0x1100u : kVirtHi;
+        gs->col[kColLead + j] = static_cast<uint16_t>(vlo | vhi);
       }
     }
     __syncwarp();
@@ -319,8 +339,7 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
       tgt_hi = static_cast<uint32_t>(a.item_score[hi.item] - goe + kBias);
     }
     const uint32_t lastmask = (MODE == 1 && glane == G - 1) ? FULL : 0u;
-    const bool ragged = __any_sync(FULL, has_task && lo.n != hi.n);
-    const int nsteps = static_cast<int>(__reduce_max_sync(FULL, nmax)) + G - 1;
+    const uint16_t* colp = gs->col + kColLead - glane;  // colp[s] = column s - glane
     for (int s = 0; s < nsteps; ++s) {
       // lane 0's row above is the top border (H = 0, F = -inf): tin = fin = INIT
       uint32_t tin = __shfl_up_sync(FULL, Tbot, 1, G);
@@ -330,8 +349,8 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
         fin = INIT;
       }
       const int j = s - glane;
-      if (j >= 0 && j < static_cast<int>(nmax)) {
-        const uint32_t sel = gs->col[j];
+      {
+        const uint32_t sel = colp[s];
         uint32_t td = tprev, tup = tin, f = fin;
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -369,8 +388,10 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
 #pragma unroll
           for (int k = 1; k < R; k += 2) cm = __vimax3_s16x2(cm, T[k], T[k + 1 < R ? k + 1 : k]);
         }
-        // columns past the shorter window of an unequal pair do not count
-        if (ragged) cm &= (j < static_cast<int>(lo.n) ? 0xffffu : 0u) | (j < static_cast<int>(hi.n) ? 0xffff0000u : 0u);
+        // final-row readout: virtual columns may exceed the final row's best, mask them
+        if (MODE == 1)
+          cm &= (static_cast<uint32_t>(j) < nlo ? 0xffffu : 0u) |
+                (static_cast<uint32_t>(j) < nhi ? 0xffff0000u : 0u);
         // strict improvement per half records the (1-based) column
         const uint32_t nb = __vimax_s16x2_relu(best, cm);
         const uint32_t chg = nb ^ best;

@@ -87,14 +87,50 @@ struct BatchDev {
   uint32_t* wcount = nullptr;     // kNumClasses: winners per class
   uint32_t* wrange = nullptr;     // 2 * kNumClasses: winner ranges in `order`
   uint32_t* wqueue = nullptr;     // kNumClasses + 8: winner-pass task counters
-  uint8_t* need_full = nullptr;   // n_reads: winner needs the full-rectangle traceback
-  uint32_t* tb_list = nullptr;    // 4 * n_reads: reads per traceback kernel (band <= 8/16/32, full)
-  uint32_t* tb_count = nullptr;   // 4 counters
+  uint8_t* tb_flag = nullptr;     // n_reads: how the winner's end row is found (kTbFlag*)
+  uint32_t* tb_list = nullptr;    // 2 * n_reads: per-read sort code, then reads sorted by code
+  uint32_t* tb_count = nullptr;   // kTbCountWords: code histogram, cursors, bucket ranges
   uint32_t* cigar_off = nullptr;  // n_reads + 1 (exclusive scan of lengths)
   uint32_t* cigar = nullptr;      // compacted, n_reads * kCigarStride capacity
   uint8_t* read_class = nullptr;  // n_reads
   uint32_t* scan_tmp = nullptr;   // block sums for scans
 };
+
+// traceback routing.  A winner's end row i* is searched inside the band
+// (kTbFlagBand), comes from the extension kernels' winner mode (kTbFlagRow:
+// the band over every possible end row would be wider than 32 diagonals), or is
+// found by the full-rectangle kernel (kTbFlagFull: int32-class winners).
+enum : uint8_t { kTbFlagBand = 0, kTbFlagFull = 1, kTbFlagRow = 2 };
+constexpr int kTbBuckets = 4;                        // band <= 8 / 16 / 32 diagonals, full
+constexpr int kTbCodes = kTbBuckets * kMaxReadLen;   // code = bucket * 256 + (256 - last row)
+constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + 8;
+constexpr int kTbMaxBand = 32;
+
+// Diagonal band of a winner (score S >= 1 ending in column j*) whose end row lies
+// in [ilo, ihi]: every alignment of score S ending at (i, j*) has at most
+// g(i) = (sa * min(i, j*) - S - go) / ge gap bases (each gap run costs go plus ge
+// per base and at most min(i, j*) bases can match), so it stays within the
+// diagonals j - i in [j* - ihi - g(ihi), j* - ilo + g(ihi)] (g grows with i).
+struct TbBand {
+  int ilo, ihi, g, w, dlo;
+};
+#ifdef __CUDACC__
+__host__ __device__ inline TbBand tb_band(int32_t sa, int32_t go, int32_t ge, int32_t S, uint32_t jstar,
+                                          uint32_t ilo, uint32_t ihi) {
+  TbBand b;
+  const int64_t gl = (static_cast<int64_t>(sa) * (ihi < jstar ? ihi : jstar) - S - go) / ge;
+  b.ilo = static_cast<int>(ilo);
+  b.ihi = static_cast<int>(ihi);
+  b.g = gl > 0 ? static_cast<int>(gl) : 0;
+  b.w = b.ihi - b.ilo + 2 * b.g + 1;
+  b.dlo = static_cast<int>(jstar) - b.ihi - b.g;
+  return b;
+}
+// smallest row that can end an alignment of score S (S <= sa * i)
+__host__ __device__ inline uint32_t tb_min_row(int32_t sa, int32_t S) {
+  return static_cast<uint32_t>((S + sa - 1) / sa);
+}
+#endif
 
 struct TuneBin {
   uint32_t upper;  // largest read length in the bin
@@ -112,7 +148,8 @@ int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
                   const TuneBin* bins, int n_bins, int mode, bool plain, uint32_t lanes,
                   uint32_t rows, cudaStream_t st);
 int launch_select(const BatchDev& b, int n_refs, cudaStream_t st);
-int launch_winners(const BatchDev& b, int n_refs, bool plain, cudaStream_t st);
+int launch_winners(const BatchDev& b, const ScoreConst& sc, int mode, int n_refs, bool plain,
+                   cudaStream_t st);
 int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
                        const TuneBin* bins, int n_bins, bool plain, uint32_t lanes, uint32_t rows,
                        cudaStream_t st);

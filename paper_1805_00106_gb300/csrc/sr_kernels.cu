@@ -238,26 +238,37 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
   }
 }
 
-// winners of the int16 classes, compacted per class into `order` (whose class
-// ranges hold at least as many slots); int32-class winners are marked for the
-// full-rectangle traceback
+// How each read's winner finds its end row for the traceback.  int32-class
+// winners go to the full-rectangle kernel.  Otherwise the band that covers every
+// row able to end the alignment (rows ceil(S / match) .. m in local mode, row m
+// in final-row mode) is searched directly when it is at most 32 diagonals wide;
+// wider ones first get their end row from the extension kernels' winner mode,
+// for which they are compacted per class into `order` (whose class ranges hold
+// at least as many slots).
 __global__ void k_winners(uint32_t n_reads, int slots, const DevHit* hits, const uint16_t* item_key,
-                          const uint32_t* class_range, bool plain, uint32_t* wcount, uint32_t* order,
-                          uint8_t* need_full) {
+                          const uint32_t* class_range, const uint32_t* rlen, const uint32_t* item_read,
+                          const uint32_t* item_end, ScoreConst sc, int mode, bool plain,
+                          uint32_t* wcount, uint32_t* order, uint8_t* tb_flag) {
   const uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   if (r >= n_reads) return;
   const DevHit h = hits[r * slots];
-  uint8_t full = 0;
+  uint8_t flag = kTbFlagBand;
   if (h.item >= 0 && h.score > 0) {
     const uint32_t cls = plain ? 0u : static_cast<uint32_t>(item_key[h.item]) / kKeysPerClass;
     if (cls >= static_cast<uint32_t>(kNumBins)) {
-      full = 1;
-    } else {
-      const uint32_t pos = atomicAdd(&wcount[cls], 1u);
-      order[(plain ? 0u : class_range[2 * cls]) + pos] = static_cast<uint32_t>(h.item);
+      flag = kTbFlagFull;
+    } else if (mode == 0) {
+      const uint32_t m = rlen[item_read[h.item]];
+      const uint32_t ilo = tb_min_row(sc.sa, h.score);
+      const TbBand b = tb_band(sc.sa, sc.go, sc.ge, h.score, item_end[h.item], ilo < 1u ? 1u : ilo, m);
+      if (b.w > kTbMaxBand) {
+        flag = kTbFlagRow;
+        const uint32_t pos = atomicAdd(&wcount[cls], 1u);
+        order[(plain ? 0u : class_range[2 * cls]) + pos] = static_cast<uint32_t>(h.item);
+      }
     }
   }
-  need_full[r] = full;
+  tb_flag[r] = flag;
 }
 
 __global__ void k_wrange(const uint32_t* class_range, const uint32_t* wcount, bool plain, uint32_t* wrange) {
@@ -402,13 +413,14 @@ int launch_select(const BatchDev& b, int n_refs, cudaStream_t st) {
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_winners(const BatchDev& b, int n_refs, bool plain, cudaStream_t st) {
+int launch_winners(const BatchDev& b, const ScoreConst& sc, int mode, int n_refs, bool plain,
+                   cudaStream_t st) {
   if (b.n_reads == 0) return 0;
   if (cudaMemsetAsync(b.wcount, 0, sizeof(uint32_t) * kNumClasses, st) != cudaSuccess) return -1;
   if (cudaMemsetAsync(b.wqueue, 0, sizeof(uint32_t) * (kNumClasses + 8), st) != cudaSuccess) return -1;
   k_winners<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, 1 + n_refs, b.hits, b.item_key,
-                                                     b.class_range, plain, b.wcount, b.order,
-                                                     b.need_full);
+                                                     b.class_range, b.rlen, b.item_read, b.item_end, sc,
+                                                     mode, plain, b.wcount, b.order, b.tb_flag);
   k_wrange<<<1, 32, 0, st>>>(b.class_range, b.wcount, plain, b.wrange);
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }

@@ -403,9 +403,9 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   c.take(d.wcount, kNumClasses);
   c.take(d.wrange, 2 * kNumClasses);
   c.take(d.wqueue, kNumClasses + 8);
-  c.take(d.need_full, n);
-  c.take(d.tb_list, 4ull * n);
-  c.take(d.tb_count, 4);
+  c.take(d.tb_flag, n);
+  c.take(d.tb_list, 2ull * n);
+  c.take(d.tb_count, kTbCountWords);
   b->bytes = c.off + 256;
   cudaError_t e = cudaMalloc(&b->arena, b->bytes);
   if (e != cudaSuccess) {
@@ -444,7 +444,7 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   rebase(d.wcount, base);
   rebase(d.wrange, base);
   rebase(d.wqueue, base);
-  rebase(d.need_full, base);
+  rebase(d.tb_flag, base);
   rebase(d.tb_list, base);
   rebase(d.tb_count, base);
   d.n_reads = n;
@@ -543,7 +543,7 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
   k += t;
   if (!mark(4)) return -1;
   if (o.want_cigar) {
-    if ((t = launch_winners(d, nr, plain, st)) < 0) return -1;
+    if ((t = launch_winners(d, sc, static_cast<int>(o.mode), nr, plain, st)) < 0) return -1;
     k += t;
     if (o.mode == SR_MODE_LOCAL && b->n_items) {
       if ((t = launch_winner_rows(d, b->s->refs, sc, bins, kNumBins, plain, o.lanes, o.rows, st)) < 0) return -1;

@@ -2,10 +2,9 @@
 // arXiv 1805.00106: the reported alignment of Sec. 4.2 / SAM output, whose
 // traceback the paper runs on the host, Sec. 6.4).
 //
-// Most winners are traced by k_tb_band (below), which needs the end row i*
-// found by the extension kernel's winner mode.  Winners whose band is wider
-// than 32 diagonals, and int32-class winners, use k_traceback: one warp per
-// read recomputes the DP of the winning window in
+// Most winners are traced by k_tb_wave (below), a banded DP that also finds the
+// end row i*.  Winners whose band is wider than 32 diagonals, and int32-class
+// winners, use k_traceback: one warp per read recomputes the DP of the winning window in
 // exact int32 over rows 1..m and columns 1..j* only (j* = the end column found
 // by the extension kernels; cells right of j* cannot influence the path) with
 // the same systolic sweep (8 rows per lane), and records per cell a 4-bit
@@ -44,7 +43,7 @@ struct TbArgs {
   const uint32_t* item_end;
   DevRefs refs;
   const uint32_t* item_iend;
-  uint8_t* need_full;
+  const uint8_t* tb_flag;
   DevHit* hits;
   uint32_t* cigar_slots;
   uint32_t* status;
@@ -54,7 +53,7 @@ struct TbArgs {
   int32_t sa, sb, go, ge;
 };
 
-__global__ void __launch_bounds__(32) k_traceback(TbArgs a, const uint32_t* list, const uint32_t* count_ptr) {
+__global__ void __launch_bounds__(32) k_traceback(TbArgs a, const uint32_t* list, const uint32_t* range) {
   extern __shared__ uint32_t dirs[];  // [j][lane], j < j*
   __shared__ uint8_t rcode[kMaxWinLen];
   __shared__ uint8_t qcode[kMaxReadLen];
@@ -62,9 +61,9 @@ __global__ void __launch_bounds__(32) k_traceback(TbArgs a, const uint32_t* list
   const int lane = threadIdx.x;
   const int32_t goe = a.go + a.ge;
   constexpr int32_t NEG = -(1 << 28);
-  const uint32_t count = *count_ptr;
+  const uint32_t begin = range[0], count = range[1] - range[0];
   for (uint32_t li = blockIdx.x; li < count; li += gridDim.x) {
-    const uint32_t r = list[li];
+    const uint32_t r = list[begin + li];
     DevHit* hp = a.hits + static_cast<uint64_t>(r) * a.slots;
     const int32_t item = hp->item;
     const int32_t S = hp->score;
@@ -218,85 +217,260 @@ __global__ void __launch_bounds__(32) k_traceback(TbArgs a, const uint32_t* list
   }
 }
 
-// Banded traceback.  The winning path's total gap length is at most
-// g = (match * min(i*, j*) - S - gap_open) / gap_extend when it has a gap at all
-// (every gap run costs gap_open plus gap_extend per base, and at most
-// min(i*, j*) bases can match), so the path lies in the diagonals
-// [d* - g, d* + g] around its end diagonal d* = j* - i*.  A DP restricted to
-// those diagonals (cells outside count as H = 0, E = F = -inf) gives values no
-// larger than the full DP's, and equal ones on every cell of the path (the
-// path's own prefixes stay inside); each traceback decision there compares a
-// path value with a value that is either also on the path or lower in both
-// DPs, so the banded DP reproduces the full-DP path exactly.
+// Banded traceback.  The winner's end cell is (i*, j*): j* from the extension
+// kernels, i* the smallest row with H(i*, j*) = S.  Every alignment of score S
+// ending in column j* at a row in [ilo, ihi] lies in the band of tb_band(), so a
+// DP restricted to those diagonals (cells outside count as H = 0, E = F = -inf)
+// gives values no larger than the full DP's and equal ones on every cell of
+// such an alignment (its prefixes stay inside).  Column j* of the band thus
+// holds S exactly at the rows where the full DP does, which gives i*; and each
+// traceback decision compares a path value with a value that is either also on
+// the path or lower in both DPs, so the banded DP reproduces the full-DP path.
 //
-// Schedule: a segment of SEG lanes holds one read, lane k the band diagonal
-// dlo + k.  Lane k computes row i at step 2(i-1) + k, so its left neighbour
-// (lane k-1, same row) and its upper neighbour (lane k+1, row above) were both
-// computed at the previous step and its diagonal neighbour (itself, row above)
-// two steps before: one shuffle each, no dependency chain within a step.  Each
-// cell stores 4 bits: H came from the diagonal, H equals E, E opened, F opened.
-// The walk jumps along runs of diagonal steps, checking SEG cells per
-// iteration with a prefix sum of their scores.
-constexpr int kTbWarps = 4;
+// Schedule: a segment of SEG lanes holds two reads, lane k the band diagonal
+// dlo + k of each.  Lane k computes row i of read A at step 2(i-1) + k and row i
+// of read B one step later, so every lane computes one cell per step, of A and B
+// in turn.  A cell's left neighbour (lane k-1, same row) and upper neighbour
+// (lane k+1, row above) belong to the same read and were computed at the
+// previous step, its diagonal neighbour (itself, row above) two steps before:
+// one shuffle each, no dependency chain within a step.  Each cell stores 4 bits
+// (H came from the diagonal, H equals E, E opened, F opened); read A's in the low
+// and read B's in the high nibble of one byte per (row, lane).  The walk jumps
+// along runs of diagonal steps, checking SEG cells per iteration with a prefix
+// sum of their scores.
+constexpr int kTbWarps = 2;  // static shared memory stays below 48 KB per block
+constexpr uint32_t kNoRow = 0xffffffffu;
+
+struct TbRead {
+  bool has;
+  uint32_t r, m, jstar, strand, rd;
+  int32_t S, item;
+  int ilo, ihi, g, w, dlo;
+  uint64_t ws;
+  const uint32_t* ref;
+};
+
+// rows that may end the winner's alignment: row m in final-row mode, the row the
+// extension kernels' winner mode found, or every row from ceil(S / match) to m
+__device__ __forceinline__ bool tb_rows(const TbArgs& a, uint32_t r, int32_t item, int32_t S, uint32_t m,
+                                        uint32_t* ilo, uint32_t* ihi) {
+  if (a.mode == 1) {
+    *ilo = *ihi = m;
+    return m >= 1;
+  }
+  if (a.tb_flag[r] == kTbFlagRow) {
+    const uint32_t i = a.item_iend[item];
+    *ilo = *ihi = i;
+    return i >= 1 && i <= m;
+  }
+  uint32_t lo = tb_min_row(a.sa, S);
+  if (lo < 1) lo = 1;
+  *ilo = lo;
+  *ihi = m;
+  return lo <= m;
+}
+
+__device__ __forceinline__ TbRead tb_load(const TbArgs& a, bool has, uint32_t r) {
+  TbRead t{};
+  t.has = has;
+  if (!has) return t;
+  t.r = r;
+  const DevHit* hp = a.hits + static_cast<uint64_t>(r) * a.slots;
+  t.item = hp->item;
+  t.S = hp->score;
+  t.rd = a.item_read[t.item];
+  t.m = a.rlen[t.rd];
+  t.jstar = a.item_end[t.item];
+  uint32_t ilo = 1, ihi = 1;
+  tb_rows(a, r, t.item, t.S, t.m, &ilo, &ihi);  // checked by the routing kernel
+  const TbBand b = tb_band(a.sa, a.go, a.ge, t.S, t.jstar, ilo, ihi);
+  t.ilo = b.ilo;
+  t.ihi = b.ihi;
+  t.g = b.g;
+  t.w = b.w;
+  t.dlo = b.dlo;
+  t.strand = a.c_strand[t.item];
+  t.ws = a.c_start[t.item];
+  t.ref = a.refs.words[a.c_ref[t.item]];
+  return t;
+}
+
+// walk back from (i*, j*) through one read's nibbles (shift 0: read A, 4: read B)
+template <int SEG>
+__device__ __forceinline__ void tb_walk(const TbArgs& a, const TbRead& t, uint32_t istar, int shift,
+                                        const uint8_t* dirs, const uint8_t* qcode, const uint8_t* rcode,
+                                        int k, int seg, uint32_t seg_mask) {
+  if (!t.has) return;
+  const int32_t goe = a.go + a.ge;
+  uint32_t* out = a.cigar_slots + static_cast<uint64_t>(t.r) * kCigarStride;
+  int i = static_cast<int>(istar), j = static_cast<int>(t.jstar);
+  int kk = j - i - t.dlo;
+  int32_t h = t.S;
+  int state = 0;
+  uint32_t nr = 0, cur_op = 0xffu, cur_len = 0;
+  bool bad = istar == kNoRow;
+  const int limit = static_cast<int>(t.ihi + t.jstar) + 4;
+  for (int it = 0; !bad; ++it) {
+    if (it > limit || kk < 0 || kk >= t.w) {
+      bad = true;
+      break;
+    }
+    if (state == 0) {
+      if (h == 0) break;
+      const int ii = i - k, jj = j - k;
+      const bool v = ii >= 1 && jj >= 1;
+      const uint32_t nib = v ? (dirs[(ii - 1) * SEG + kk] >> shift) & 15u : 0u;
+      const int32_t st = v ? (qcode[ii - 1] == rcode[jj - 1] ? a.sa : -a.sb) : 0;
+      int32_t incl = st;
+#pragma unroll
+      for (int off = 1; off < SEG; off <<= 1) {
+        const int32_t x = __shfl_up_sync(seg_mask, incl, off, SEG);
+        if (k >= off) incl += x;
+      }
+      const bool stop = !(v && (h - (incl - st)) != 0 && (nib & 1u));
+      const uint32_t bal = (__ballot_sync(seg_mask, stop) & seg_mask) >> (SEG == 32 ? 0 : seg * SEG);
+      const int L = bal ? __ffs(bal) - 1 : SEG;
+      if (L > 0) {
+        const int32_t used = __shfl_sync(seg_mask, incl, L - 1, SEG);
+        h -= used;
+        i -= L;
+        j -= L;
+        if (cur_op == 0u) {
+          cur_len += static_cast<uint32_t>(L);
+        } else {
+          if (nr + 4 >= static_cast<uint32_t>(kCigarStride)) {
+            bad = true;
+            break;
+          }
+          if (cur_len && k == 0) out[1 + nr] = (cur_len << 4) | cur_op;
+          nr += cur_len ? 1u : 0u;
+          cur_op = 0u;
+          cur_len = static_cast<uint32_t>(L);
+        }
+        continue;
+      }
+      const uint32_t nib0 = __shfl_sync(seg_mask, nib, 0, SEG);
+      state = (nib0 & 2u) ? 1 : 2;
+    } else {
+      if (i < 1 || j < 1) {
+        bad = true;
+        break;
+      }
+      const uint32_t nib = (dirs[(i - 1) * SEG + kk] >> shift) & 15u;
+      const uint32_t op = state == 1 ? 2u : 1u;  // D : I
+      if (cur_op == op) {
+        ++cur_len;
+      } else {
+        if (nr + 4 >= static_cast<uint32_t>(kCigarStride)) {
+          bad = true;
+          break;
+        }
+        if (cur_len && k == 0) out[1 + nr] = (cur_len << 4) | cur_op;
+        nr += cur_len ? 1u : 0u;
+        cur_op = op;
+        cur_len = 1;
+      }
+      const bool open = state == 1 ? (nib & 4u) : (nib & 8u);
+      h += open ? goe : a.ge;
+      if (open) state = 0;
+      if (op == 2u) {
+        --j;
+        --kk;
+      } else {
+        --i;
+        ++kk;
+      }
+    }
+  }
+  if (k == 0) {
+    DevHit* hp = a.hits + static_cast<uint64_t>(t.r) * a.slots;
+    if (bad || nr + 3 > static_cast<uint32_t>(kCigarStride)) {
+      atomicOr(a.status, kStInternal);
+      hp->cigar_len = 0;
+    } else {
+      if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
+      // runs sit reversed in out[1 .. nr]; put them in order after the soft clip
+      for (uint32_t x = 0; x < nr / 2; ++x) {
+        const uint32_t t0 = out[1 + x];
+        out[1 + x] = out[nr - x];
+        out[nr - x] = t0;
+      }
+      const uint32_t start_i = static_cast<uint32_t>(i) + 1u;
+      uint32_t nc;
+      if (start_i > 1) {
+        out[0] = ((start_i - 1u) << 4) | 4u;
+        nc = nr + 1;
+      } else {
+        for (uint32_t x = 0; x < nr; ++x) out[x] = out[x + 1];
+        nc = nr;
+      }
+      if (istar < t.m) out[nc++] = ((t.m - istar) << 4) | 4u;
+      hp->read_start = static_cast<int32_t>(start_i);
+      hp->read_end = static_cast<int32_t>(istar);
+      hp->start_j = static_cast<uint32_t>(j) + 1u;
+      hp->cigar_len = nc;
+    }
+  }
+}
 
 template <int SEG>
 __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint32_t* list,
-                                                           const uint32_t* count_ptr) {
+                                                           const uint32_t* range) {
   constexpr int NSEG = 32 / SEG;
   __shared__ uint8_t dirs_s[kTbWarps][NSEG][kMaxReadLen * SEG];
-  __shared__ uint8_t rcode_s[kTbWarps][NSEG][kMaxWinLen];
-  __shared__ uint8_t qcode_s[kTbWarps][NSEG][kMaxReadLen];
+  __shared__ uint8_t rcode_s[kTbWarps][NSEG][2][kMaxWinLen];
+  __shared__ uint8_t qcode_s[kTbWarps][NSEG][2][kMaxReadLen];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int seg = lane / SEG;
   const int k = lane % SEG;
   const uint32_t seg_mask = SEG == 32 ? FULL : (((1u << SEG) - 1u) << (seg * SEG));
   uint8_t* dirs = dirs_s[warp][seg];
-  uint8_t* rcode = rcode_s[warp][seg];
-  uint8_t* qcode = qcode_s[warp][seg];
+  const uint8_t* qA = qcode_s[warp][seg][0];
+  const uint8_t* qB = qcode_s[warp][seg][1];
+  const uint8_t* rA = rcode_s[warp][seg][0];
+  const uint8_t* rB = rcode_s[warp][seg][1];
   const int32_t goe = a.go + a.ge;
   constexpr int32_t NEG = -(1 << 28);
-  const uint32_t count = *count_ptr;
-  const uint32_t stride = gridDim.x * kTbWarps * NSEG;
-  for (uint32_t base = (blockIdx.x * kTbWarps + warp) * NSEG; base < count; base += stride) {
-    const uint32_t li = base + seg;
-    const bool has = li < count;
-    uint32_t r = 0, m = 0, istar = 0, jstar = 0, strand = 0;
-    int32_t S = 0, item = -1;
-    int g = 0, w = 0, dlo = 0;
-    uint64_t ws = 0;
-    const uint32_t* ref = nullptr;
-    if (has) {
-      r = list[li];
-      const DevHit* hp = a.hits + static_cast<uint64_t>(r) * a.slots;
-      item = hp->item;
-      S = hp->score;
-      const uint32_t rd = a.item_read[item];
-      m = a.rlen[rd];
-      jstar = a.item_end[item];
-      istar = a.mode == 1 ? m : a.item_iend[item];
-      const int64_t gl = (static_cast<int64_t>(a.sa) * min(istar, jstar) - S - a.go) / a.ge;
-      g = gl > 0 ? static_cast<int>(gl) : 0;
-      w = 2 * g + 1;
-      dlo = static_cast<int>(jstar) - static_cast<int>(istar) - g;
-      strand = a.c_strand[item];
-      ws = a.c_start[item];
-      ref = a.refs.words[a.c_ref[item]];
-      const uint32_t* row = a.rpack + static_cast<uint64_t>(rd) * kReadWords;
-      for (uint32_t j = k; j < jstar; j += SEG) rcode[j] = static_cast<uint8_t>(base_at(ref, ws + j));
-      for (uint32_t i = k; i < istar; i += SEG)
-        qcode[i] = static_cast<uint8_t>(strand ? 3u - base_at(row, m - 1u - i) : base_at(row, i));
+  const uint32_t begin = range[0];
+  const uint32_t count = range[1] - begin;
+  constexpr uint32_t kPerWarp = 2 * NSEG;
+  const uint32_t stride = gridDim.x * kTbWarps * kPerWarp;
+  for (uint32_t base = (blockIdx.x * kTbWarps + warp) * kPerWarp; base < count; base += stride) {
+    TbRead rd[2];
+#pragma unroll
+    for (int X = 0; X < 2; ++X) {
+      const uint32_t li = base + 2 * seg + X;
+      rd[X] = tb_load(a, li < count, li < count ? list[begin + li] : 0u);
+      if (rd[X].has) {
+        uint8_t* rc = rcode_s[warp][seg][X];
+        uint8_t* qc = qcode_s[warp][seg][X];
+        const uint32_t* row = a.rpack + static_cast<uint64_t>(rd[X].rd) * kReadWords;
+        for (uint32_t j = k; j < rd[X].jstar; j += SEG) rc[j] = static_cast<uint8_t>(base_at(rd[X].ref, rd[X].ws + j));
+        for (uint32_t i = k; i < static_cast<uint32_t>(rd[X].ihi); i += SEG)
+          qc[i] = static_cast<uint8_t>(rd[X].strand ? 3u - base_at(row, rd[X].m - 1u - i) : base_at(row, i));
+      }
     }
     __syncwarp();
-    // ---- banded DP, skew-2 wavefront
-    const int nsteps = has ? 2 * (static_cast<int>(istar) - 1) + w : 0;
-    const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(nsteps)));
-    int32_t Hc = 0, Ec = NEG, Fc = NEG;
+    // ---- banded DP of both reads, interleaved skew-2 wavefront
+    const int stA = rd[0].has ? 2 * (rd[0].ihi - 1) + rd[0].w : 0;
+    const int stB = rd[1].has ? 2 * (rd[1].ihi - 1) + rd[1].w : 0;
+    const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(max(stA, stB) + 1)));
+    int32_t H1 = 0, H2 = 0, E1 = NEG, F1 = NEG;  // this lane's cells of steps t-1 and t-2
+    uint32_t nibA = 0, icA = kNoRow, icB = kNoRow;
     for (int t = 0; t < nmax; ++t) {
-      int32_t hl = __shfl_up_sync(FULL, Hc, 1, SEG);
-      int32_t el = __shfl_up_sync(FULL, Ec, 1, SEG);
-      int32_t hu = __shfl_down_sync(FULL, Hc, 1, SEG);
-      int32_t fu = __shfl_down_sync(FULL, Fc, 1, SEG);
+      int32_t hl = __shfl_up_sync(FULL, H1, 1, SEG);
+      int32_t el = __shfl_up_sync(FULL, E1, 1, SEG);
+      int32_t hu = __shfl_down_sync(FULL, H1, 1, SEG);
+      int32_t fu = __shfl_down_sync(FULL, F1, 1, SEG);
+      const int X = (t - k) & 1;  // 0: read A, 1: read B
+      const int tk = t - k - X;   // 2 (i - 1)
+      const int i = (tk >> 1) + 1;
+      const bool has = X ? rd[1].has : rd[0].has;
+      const int w = X ? rd[1].w : rd[0].w;
+      const int dlo = X ? rd[1].dlo : rd[0].dlo;
+      const int ihi = X ? rd[1].ihi : rd[0].ihi;
+      const int js = static_cast<int>(X ? rd[1].jstar : rd[0].jstar);
       if (k == 0) {
         hl = 0;
         el = NEG;
@@ -305,185 +479,132 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
         hu = 0;
         fu = NEG;
       }
-      const int tk = t - k;
-      if (has && k < w && tk >= 0 && !(tk & 1) && tk / 2 < static_cast<int>(istar)) {
-        const int i = tk / 2 + 1;
+      int32_t nH = 0, nE = NEG, nF = NEG;
+      uint32_t nib = 0;
+      if (has && k < w && tk >= 0 && i <= ihi) {
         const int j = i + dlo + k;
         const int32_t eo = hl - goe, ee = el - a.ge, fo = hu - goe, fe = fu - a.ge;
         const int32_t E = max(eo, ee), F = max(fo, fe);
-        uint32_t nib = 0;
-        if (j >= 1 && j <= static_cast<int>(jstar)) {
-          const int32_t hs = Hc + (qcode[i - 1] == rcode[j - 1] ? a.sa : -a.sb);
+        if (j >= 1 && j <= js) {
+          const uint8_t qb = X ? qB[i - 1] : qA[i - 1];
+          const uint8_t rb = X ? rB[j - 1] : rA[j - 1];
+          const int32_t hs = H2 + (qb == rb ? a.sa : -a.sb);
           const int32_t H = max(max(0, hs), max(E, F));
           nib = static_cast<uint32_t>(H == hs) | (static_cast<uint32_t>(H == E) << 1) |
                 (static_cast<uint32_t>(eo >= ee) << 2) | (static_cast<uint32_t>(fo >= fe) << 3);
-          Hc = H;
-          Ec = E;
-          Fc = F;
-        } else {
-          Hc = 0;
-          Ec = NEG;
-          Fc = NEG;
+          nH = H;
+          nE = E;
+          nF = F;
+          if (j == js && H == (X ? rd[1].S : rd[0].S)) {
+            if (X) icB = min(icB, static_cast<uint32_t>(i));
+            else icA = min(icA, static_cast<uint32_t>(i));
+          }
         }
-        dirs[(i - 1) * SEG + k] = static_cast<uint8_t>(nib);
       }
+      // read A's nibble of row i waits one step for read B's of the same row
+      if (X == 0) nibA = nib;
+      else if (tk >= 0 && i <= kMaxReadLen) dirs[(i - 1) * SEG + k] = static_cast<uint8_t>(nibA | (nib << 4));
+      H2 = H1;
+      H1 = nH;
+      E1 = nE;
+      F1 = nF;
+    }
+#pragma unroll
+    for (int off = SEG / 2; off > 0; off >>= 1) {
+      icA = min(icA, __shfl_xor_sync(FULL, icA, off, SEG));
+      icB = min(icB, __shfl_xor_sync(FULL, icB, off, SEG));
     }
     __syncwarp();
-    // ---- walk back (per segment)
-    if (has) {
-      uint32_t* out = a.cigar_slots + static_cast<uint64_t>(r) * kCigarStride;
-      int i = static_cast<int>(istar), j = static_cast<int>(jstar), kk = g;
-      int32_t h = S;
-      int state = 0;
-      uint32_t nr = 0, cur_op = 0xffu, cur_len = 0;
-      bool bad = false;
-      const int limit = static_cast<int>(istar + jstar) + 4;
-      for (int it = 0;; ++it) {
-        if (it > limit || kk < 0 || kk >= w) {
-          bad = true;
-          break;
-        }
-        if (state == 0) {
-          if (h == 0) break;
-          const int ii = i - k, jj = j - k;
-          const bool v = ii >= 1 && jj >= 1;
-          const uint32_t nib = v ? dirs[(ii - 1) * SEG + kk] : 0u;
-          const int32_t st = v ? (qcode[ii - 1] == rcode[jj - 1] ? a.sa : -a.sb) : 0;
-          int32_t incl = st;
-#pragma unroll
-          for (int off = 1; off < SEG; off <<= 1) {
-            const int32_t x = __shfl_up_sync(seg_mask, incl, off, SEG);
-            if (k >= off) incl += x;
-          }
-          const bool stop = !(v && (h - (incl - st)) != 0 && (nib & 1u));
-          const uint32_t bal = (__ballot_sync(seg_mask, stop) & seg_mask) >> (SEG == 32 ? 0 : seg * SEG);
-          const int L = bal ? __ffs(bal) - 1 : SEG;
-          if (L > 0) {
-            const int32_t used = __shfl_sync(seg_mask, incl, L - 1, SEG);
-            h -= used;
-            i -= L;
-            j -= L;
-            if (cur_op == 0u) {
-              cur_len += static_cast<uint32_t>(L);
-            } else {
-              if (nr + 4 >= static_cast<uint32_t>(kCigarStride)) {
-                bad = true;
-                break;
-              }
-              if (cur_len && k == 0) out[1 + nr] = (cur_len << 4) | cur_op;
-              nr += cur_len ? 1u : 0u;
-              cur_op = 0u;
-              cur_len = static_cast<uint32_t>(L);
-            }
-            continue;
-          }
-          const uint32_t nib0 = __shfl_sync(seg_mask, nib, 0, SEG);
-          state = (nib0 & 2u) ? 1 : 2;
-        } else {
-          if (i < 1 || j < 1) {
-            bad = true;
-            break;
-          }
-          const uint32_t nib = dirs[(i - 1) * SEG + kk];
-          const uint32_t op = state == 1 ? 2u : 1u;  // D : I
-          if (cur_op == op) {
-            ++cur_len;
-          } else {
-            if (nr + 4 >= static_cast<uint32_t>(kCigarStride)) {
-              bad = true;
-              break;
-            }
-            if (cur_len && k == 0) out[1 + nr] = (cur_len << 4) | cur_op;
-            nr += cur_len ? 1u : 0u;
-            cur_op = op;
-            cur_len = 1;
-          }
-          const bool open = state == 1 ? (nib & 4u) : (nib & 8u);
-          h += open ? goe : a.ge;
-          if (open) state = 0;
-          if (op == 2u) {
-            --j;
-            --kk;
-          } else {
-            --i;
-            ++kk;
-          }
-        }
-      }
-      if (k == 0) {
-        DevHit* hp = a.hits + static_cast<uint64_t>(r) * a.slots;
-        if (bad || nr + 3 > static_cast<uint32_t>(kCigarStride)) {
-          atomicOr(a.status, kStInternal);
-          hp->cigar_len = 0;
-        } else {
-          if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
-          // runs sit reversed in out[1 .. nr]; put them in order after the soft clip
-          for (uint32_t x = 0; x < nr / 2; ++x) {
-            const uint32_t t0 = out[1 + x];
-            out[1 + x] = out[nr - x];
-            out[nr - x] = t0;
-          }
-          const uint32_t start_i = static_cast<uint32_t>(i) + 1u;
-          uint32_t nc;
-          if (start_i > 1) {
-            out[0] = ((start_i - 1u) << 4) | 4u;
-            nc = nr + 1;
-          } else {
-            for (uint32_t x = 0; x < nr; ++x) out[x] = out[x + 1];
-            nc = nr;
-          }
-          if (istar < m) out[nc++] = ((m - istar) << 4) | 4u;
-          hp->read_start = static_cast<int32_t>(start_i);
-          hp->read_end = static_cast<int32_t>(istar);
-          hp->start_j = static_cast<uint32_t>(j) + 1u;
-          hp->cigar_len = nc;
-        }
-      }
-    }
+    // ---- walk back, read A then read B of each segment
+    tb_walk<SEG>(a, rd[0], icA, 0, dirs, qA, rA, k, seg, seg_mask);
+    __syncwarp(seg_mask);
+    tb_walk<SEG>(a, rd[1], icB, 4, dirs, qB, rB, k, seg, seg_mask);
     __syncwarp();
   }
 }
 
-// Routing: clears reads without a winner and sorts winners by band width into
-// lists for k_tb_wave<8|16|32>; wider bands and int32-class winners go to the
-// full-rectangle kernel.
-__global__ void k_tb_route(TbArgs a, uint32_t* lists, uint32_t* counts) {
+// Routing: clears reads without a winner, picks each winner's traceback kernel
+// (band <= 8 / 16 / 32 diagonals, else the full-rectangle kernel) and counts the
+// sort code bucket * 256 + (256 - last row), so that each kernel's reads come
+// sorted by the number of rows their DP runs, longest first.
+__global__ void __launch_bounds__(1024) k_tb_route(TbArgs a, uint32_t* code, uint32_t* hist) {
+  __shared__ uint32_t sh[kTbCodes];
+  for (int c = threadIdx.x; c < kTbCodes; c += blockDim.x) sh[c] = 0;
+  __syncthreads();
   const uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
-  const bool live = r < a.n_reads;
-  int bucket = -1;
-  if (live) {
+  if (r < a.n_reads) {
+    uint32_t cd = kNoRow;
     DevHit* hp = a.hits + r * a.slots;
     const int32_t item = hp->item, S = hp->score;
     if (item < 0 || S <= 0) {
       hp->read_start = hp->read_end = 0;
       hp->start_j = 0;
       hp->cigar_len = 0;
-    } else if (a.need_full[r]) {
-      bucket = 3;
     } else {
       const uint32_t m = a.rlen[a.item_read[item]];
       const uint32_t jstar = a.item_end[item];
-      const uint32_t istar = a.mode == 1 ? m : a.item_iend[item];
-      if (istar == 0 || istar > m || jstar == 0) {
-        atomicOr(a.status, kStInternal);
-        hp->cigar_len = 0;
+      int bucket = -1;
+      uint32_t last = m;
+      if (a.tb_flag[r] == kTbFlagFull) {
+        bucket = kTbBuckets - 1;
       } else {
-        const int64_t gl = (static_cast<int64_t>(a.sa) * min(istar, jstar) - S - a.go) / a.ge;
-        const int64_t w = 2 * (gl > 0 ? gl : 0) + 1;
-        bucket = w <= 8 ? 0 : (w <= 16 ? 1 : (w <= 32 ? 2 : 3));
+        uint32_t ilo = 0, ihi = 0;
+        if (jstar == 0 || m == 0 || m > kMaxReadLen || !tb_rows(a, static_cast<uint32_t>(r), item, S, m, &ilo, &ihi)) {
+          atomicOr(a.status, kStInternal);
+          hp->cigar_len = 0;
+        } else {
+          const TbBand b = tb_band(a.sa, a.go, a.ge, S, jstar, ilo, ihi);
+          bucket = b.w <= 8 ? 0 : (b.w <= 16 ? 1 : (b.w <= kTbMaxBand ? 2 : 3));
+          last = ihi;
+        }
+      }
+      if (bucket >= 0) {
+        cd = static_cast<uint32_t>(bucket) * kMaxReadLen + (kMaxReadLen - last);
+        atomicAdd(&sh[cd], 1u);
       }
     }
+    code[r] = cd;
   }
-  const uint32_t act = __ballot_sync(FULL, live && bucket >= 0);
-  if (!(live && bucket >= 0)) return;
-  const uint32_t peers = __match_any_sync(act, static_cast<uint32_t>(bucket));
+  __syncthreads();
+  for (int c = threadIdx.x; c < kTbCodes; c += blockDim.x)
+    if (sh[c]) atomicAdd(&hist[c], sh[c]);
+}
+
+// exclusive offsets of the codes (one block of kTbCodes threads) and each
+// bucket's [begin, end) in the sorted list
+__global__ void __launch_bounds__(kTbCodes) k_tb_scan(uint32_t* cnt) {
+  __shared__ uint32_t sh[kTbCodes];
+  const int t = threadIdx.x;
+  const uint32_t v = cnt[t];
+  sh[t] = v;
+  __syncthreads();
+  for (int off = 1; off < kTbCodes; off <<= 1) {
+    const uint32_t x = t >= off ? sh[t - off] : 0u;
+    __syncthreads();
+    sh[t] += x;
+    __syncthreads();
+  }
+  cnt[kTbCodes + t] = sh[t] - v;
+  if (t % kMaxReadLen == 0) {
+    const int b = t / kMaxReadLen;
+    cnt[2 * kTbCodes + 2 * b] = sh[t] - v;
+    cnt[2 * kTbCodes + 2 * b + 1] = sh[t + kMaxReadLen - 1];
+  }
+}
+
+__global__ void k_tb_scatter(uint32_t n_reads, const uint32_t* code, uint32_t* cursor, uint32_t* list) {
+  const uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  const uint32_t cd = r < n_reads ? code[r] : kNoRow;
+  const bool live = cd != kNoRow;
+  const uint32_t act = __ballot_sync(FULL, live);
+  if (!live) return;
+  const uint32_t peers = __match_any_sync(act, cd);
   const int ln = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
   uint32_t b0 = 0;
-  if (ln == leader) b0 = atomicAdd(&counts[bucket], static_cast<uint32_t>(__popc(peers)));
+  if (ln == leader) b0 = atomicAdd(&cursor[cd], static_cast<uint32_t>(__popc(peers)));
   b0 = __shfl_sync(peers, b0, leader);
-  lists[static_cast<uint64_t>(bucket) * a.n_reads + b0 + __popc(peers & ((1u << ln) - 1u))] =
-      static_cast<uint32_t>(r);
+  list[b0 + __popc(peers & ((1u << ln) - 1u))] = static_cast<uint32_t>(r);
 }
 
 }  // namespace
@@ -501,7 +622,7 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   a.item_read = b.item_read;
   a.item_end = b.item_end;
   a.item_iend = b.item_iend;
-  a.need_full = b.need_full;
+  a.tb_flag = b.tb_flag;
   a.refs = refs;
   a.hits = b.hits;
   a.cigar_slots = b.cigar_slots;
@@ -516,20 +637,26 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaMemsetAsync(b.tb_count, 0, 4 * sizeof(uint32_t), st) != cudaSuccess) return -1;
-  k_tb_route<<<(b.n_reads + 255) / 256, 256, 0, st>>>(a, b.tb_list, b.tb_count);
-  int launched = 1;
+  uint32_t* code = b.tb_list;
+  uint32_t* list = b.tb_list + b.n_reads;
+  uint32_t* hist = b.tb_count;
+  uint32_t* cursor = b.tb_count + kTbCodes;
+  const uint32_t* ranges = b.tb_count + 2 * kTbCodes;
+  if (cudaMemsetAsync(hist, 0, kTbCodes * sizeof(uint32_t), st) != cudaSuccess) return -1;
+  k_tb_route<<<(b.n_reads + 1023) / 1024, 1024, 0, st>>>(a, code, hist);
+  k_tb_scan<<<1, kTbCodes, 0, st>>>(b.tb_count);
+  k_tb_scatter<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, code, cursor, list);
+  int launched = 3;
   auto wave = [&](auto kern, int bucket, int per_warp) -> bool {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kTbWarps, 0) != cudaSuccess) return false;
     const uint32_t g0 = static_cast<uint32_t>(nsm) * static_cast<uint32_t>(per_sm > 0 ? per_sm : 1);
     const uint32_t need = (b.n_reads + kTbWarps * per_warp - 1) / (kTbWarps * per_warp);
-    kern<<<need < g0 ? need : g0, 32 * kTbWarps, 0, st>>>(a, b.tb_list + static_cast<uint64_t>(bucket) * b.n_reads,
-                                                        b.tb_count + bucket);
+    kern<<<need < g0 ? need : g0, 32 * kTbWarps, 0, st>>>(a, list, ranges + 2 * bucket);
     ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
   };
-  if (!wave(k_tb_wave<8>, 0, 4) || !wave(k_tb_wave<16>, 1, 2) || !wave(k_tb_wave<32>, 2, 1)) return -1;
+  if (!wave(k_tb_wave<8>, 0, 8) || !wave(k_tb_wave<16>, 1, 4) || !wave(k_tb_wave<32>, 2, 2)) return -1;
   const size_t smem = static_cast<size_t>(kMaxWinLen) * 32 * sizeof(uint32_t);
   static bool attr = false;
   if (!attr) {
@@ -541,7 +668,7 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traceback, 32, smem) != cudaSuccess) return -1;
   const uint32_t grid = static_cast<uint32_t>(nsm) * static_cast<uint32_t>(per_sm > 0 ? per_sm : 1);
-  k_traceback<<<grid, 32, smem, st>>>(a, b.tb_list + 3ull * b.n_reads, b.tb_count + 3);
+  k_traceback<<<grid, 32, smem, st>>>(a, list, ranges + 2 * (kTbBuckets - 1));
   ++launched;
   return cudaPeekAtLastError() == cudaSuccess ? launched : -1;
 }

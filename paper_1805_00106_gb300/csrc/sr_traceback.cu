@@ -452,63 +452,102 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
       }
     }
     __syncwarp();
-    // ---- banded DP of both reads, interleaved skew-2 wavefront
+    // ---- banded DP of both reads, interleaved skew-2 wavefront.  Lane k runs
+    // read (k & 1) at even steps and the other read at odd steps, so a pair of
+    // steps has a fixed read per half-step and the per-read terms are set once.
     const int stA = rd[0].has ? 2 * (rd[0].ihi - 1) + rd[0].w : 0;
     const int stB = rd[1].has ? 2 * (rd[1].ihi - 1) + rd[1].w : 0;
     const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(max(stA, stB) + 1)));
-    int32_t H1 = 0, H2 = 0, E1 = NEG, F1 = NEG;  // this lane's cells of steps t-1 and t-2
-    uint32_t nibA = 0, icA = kNoRow, icB = kNoRow;
-    for (int t = 0; t < nmax; ++t) {
-      int32_t hl = __shfl_up_sync(FULL, H1, 1, SEG);
-      int32_t el = __shfl_up_sync(FULL, E1, 1, SEG);
-      int32_t hu = __shfl_down_sync(FULL, H1, 1, SEG);
-      int32_t fu = __shfl_down_sync(FULL, F1, 1, SEG);
-      const int X = (t - k) & 1;  // 0: read A, 1: read B
-      const int tk = t - k - X;   // 2 (i - 1)
-      const int i = (tk >> 1) + 1;
-      const bool has = X ? rd[1].has : rd[0].has;
-      const int w = X ? rd[1].w : rd[0].w;
-      const int dlo = X ? rd[1].dlo : rd[0].dlo;
-      const int ihi = X ? rd[1].ihi : rd[0].ihi;
-      const int js = static_cast<int>(X ? rd[1].jstar : rd[0].jstar);
-      if (k == 0) {
-        hl = 0;
-        el = NEG;
-      }
-      if (k + 1 >= w) {
-        hu = 0;
-        fu = NEG;
-      }
-      int32_t nH = 0, nE = NEG, nF = NEG;
-      uint32_t nib = 0;
-      if (has && k < w && tk >= 0 && i <= ihi) {
-        const int j = i + dlo + k;
+    const int p = k & 1;
+    struct Sub {
+      bool on, bd;       // lane inside the band; lane k + 1 outside it (top border)
+      int c, ihi, js;    // column = row + c
+      int32_t S;
+      const uint8_t* q;
+      const uint8_t* r;
+    };
+    Sub s0, s1;
+    {
+      const TbRead& x0 = p ? rd[1] : rd[0];
+      const TbRead& x1 = p ? rd[0] : rd[1];
+      s0 = Sub{x0.has && k < x0.w, k + 1 >= x0.w, x0.dlo + k, x0.ihi, static_cast<int>(x0.jstar), x0.S,
+               p ? qB : qA, p ? rB : rA};
+      s1 = Sub{x1.has && k < x1.w, k + 1 >= x1.w, x1.dlo + k, x1.ihi, static_cast<int>(x1.jstar), x1.S,
+               p ? qA : qB, p ? rA : rB};
+    }
+    // one cell of row i of a read: neighbours left (hl, el), above (hu, fu), diagonal hd
+    auto cell = [&](const Sub& sb, int i, int32_t hl, int32_t el, int32_t hu, int32_t fu, int32_t hd,
+                    int32_t& nH, int32_t& nE, int32_t& nF, uint32_t& nib, uint32_t& ic) {
+      nH = 0;
+      nE = NEG;
+      nF = NEG;
+      nib = 0;
+      if (sb.on && i >= 1 && i <= sb.ihi) {
+        const int j = i + sb.c;
         const int32_t eo = hl - goe, ee = el - a.ge, fo = hu - goe, fe = fu - a.ge;
         const int32_t E = max(eo, ee), F = max(fo, fe);
-        if (j >= 1 && j <= js) {
-          const uint8_t qb = X ? qB[i - 1] : qA[i - 1];
-          const uint8_t rb = X ? rB[j - 1] : rA[j - 1];
-          const int32_t hs = H2 + (qb == rb ? a.sa : -a.sb);
+        if (j >= 1 && j <= sb.js) {
+          const int32_t hs = hd + (sb.q[i - 1] == sb.r[j - 1] ? a.sa : -a.sb);
           const int32_t H = max(max(0, hs), max(E, F));
           nib = static_cast<uint32_t>(H == hs) | (static_cast<uint32_t>(H == E) << 1) |
                 (static_cast<uint32_t>(eo >= ee) << 2) | (static_cast<uint32_t>(fo >= fe) << 3);
           nH = H;
           nE = E;
           nF = F;
-          if (j == js && H == (X ? rd[1].S : rd[0].S)) {
-            if (X) icB = min(icB, static_cast<uint32_t>(i));
-            else icA = min(icA, static_cast<uint32_t>(i));
-          }
+          if (j == sb.js && H == sb.S) ic = min(ic, static_cast<uint32_t>(i));
         }
       }
-      // read A's nibble of row i waits one step for read B's of the same row
-      if (X == 0) nibA = nib;
-      else if (tk >= 0 && i <= kMaxReadLen) dirs[(i - 1) * SEG + k] = static_cast<uint8_t>(nibA | (nib << 4));
-      H2 = H1;
-      H1 = nH;
-      E1 = nE;
-      F1 = nF;
+    };
+    // cells of the previous pair of steps: half-step 0 (Ha, Ea, Fa) and 1 (Hb, Eb, Fb)
+    int32_t Ha = 0, Ea = NEG, Fa = NEG, Hb = 0, Eb = NEG, Fb = NEG;
+    uint32_t pend = 0, ic0 = kNoRow, ic1 = kNoRow;
+    int ia = 1 - ((k + p) >> 1);  // row of half-step 0 in this pair
+    for (int t = 0; t < nmax; t += 2, ++ia) {
+      uint32_t nib;
+      {
+        int32_t hl = __shfl_up_sync(FULL, Hb, 1, SEG);
+        int32_t el = __shfl_up_sync(FULL, Eb, 1, SEG);
+        int32_t hu = __shfl_down_sync(FULL, Hb, 1, SEG);
+        int32_t fu = __shfl_down_sync(FULL, Fb, 1, SEG);
+        if (k == 0) {
+          hl = 0;
+          el = NEG;
+        }
+        if (s0.bd) {
+          hu = 0;
+          fu = NEG;
+        }
+        cell(s0, ia, hl, el, hu, fu, Ha, Ha, Ea, Fa, nib, ic0);
+        // read A's nibble of a row waits for read B's of the same row
+        if (p) {
+          if (ia >= 1 && ia <= kMaxReadLen) dirs[(ia - 1) * SEG + k] = static_cast<uint8_t>(pend | (nib << 4));
+        } else {
+          pend = nib;
+        }
+      }
+      {
+        int32_t hl = __shfl_up_sync(FULL, Ha, 1, SEG);
+        int32_t el = __shfl_up_sync(FULL, Ea, 1, SEG);
+        int32_t hu = __shfl_down_sync(FULL, Ha, 1, SEG);
+        int32_t fu = __shfl_down_sync(FULL, Fa, 1, SEG);
+        if (k == 0) {
+          hl = 0;
+          el = NEG;
+        }
+        if (s1.bd) {
+          hu = 0;
+          fu = NEG;
+        }
+        const int ib = ia + p;
+        cell(s1, ib, hl, el, hu, fu, Hb, Hb, Eb, Fb, nib, ic1);
+        if (p) {
+          pend = nib;
+        } else if (ib >= 1 && ib <= kMaxReadLen) {
+          dirs[(ib - 1) * SEG + k] = static_cast<uint8_t>(pend | (nib << 4));
+        }
+      }
     }
+    uint32_t icA = p ? ic1 : ic0, icB = p ? ic0 : ic1;
 #pragma unroll
     for (int off = SEG / 2; off > 0; off >>= 1) {
       icA = min(icA, __shfl_xor_sync(FULL, icA, off, SEG));

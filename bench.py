@@ -117,7 +117,7 @@ def kernel_hash():
 def traffic_per_launch(cells):
     """DRAM bytes of the extension kernels from the committed ncu capture, scaled
     to this launch by cells; None when the kernel source changed since."""
-    p = os.path.join(ROOT, "profiles", "extend_traffic.json")
+    p = os.path.join(ROOT, "profiles", "k_extend_dram_traffic_c2.json")
     try:
         d = json.load(open(p))
     except Exception:

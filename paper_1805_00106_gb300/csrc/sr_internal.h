@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sr.h"
+
 namespace sr {
 
 constexpr int kMaxReadLen = 256;
@@ -94,6 +96,8 @@ struct BatchDev {
   uint32_t* cigar = nullptr;      // compacted, n_reads * kCigarStride capacity
   uint8_t* read_class = nullptr;  // n_reads
   uint32_t* scan_tmp = nullptr;   // block sums for scans
+  sr_hit* out_best = nullptr;     // n_reads: results in the public layout (fetch)
+  sr_hit* out_per_ref = nullptr;  // n_reads * n_refs
 };
 
 // traceback routing.  A winner's end row i* is searched inside the band
@@ -156,6 +160,7 @@ int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst&
 int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, int mode,
                      int n_refs, cudaStream_t st);
 int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);
+int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, cudaStream_t st);
 int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,
                     cudaStream_t st);
 bool extend_config_supported(uint32_t lanes, uint32_t rows);

@@ -425,6 +425,57 @@ int launch_winners(const BatchDev& b, const ScoreConst& sc, int mode, int n_refs
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 
+// Results in the public sr_hit layout: reference, strand and reference
+// coordinates of each read's overall winner (with its CIGAR offset) and of its
+// best window per reference.
+__global__ void k_assemble(uint32_t n_reads, int slots, const DevHit* hits, const uint8_t* c_ref,
+                           const uint8_t* c_strand, const uint64_t* c_start, const uint32_t* item_end,
+                           const uint32_t* cigar_off, bool want_cigar, sr_hit* best, sr_hit* per_ref) {
+  const uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (x >= static_cast<uint64_t>(n_reads) * slots) return;
+  const uint64_t i = x / slots;
+  const int sl = static_cast<int>(x - i * slots);
+  const DevHit h = hits[x];
+  sr_hit o;
+  o.score = h.score;
+  o.second = h.second;
+  o.n_ties = h.n_ties;
+  o.item = h.item;
+  o.ref_id = 0;
+  o.strand = 0;
+  o.reserved = 0;
+  o.read_start = 0;
+  o.read_end = 0;
+  o.ref_start = 0;
+  o.ref_end = 0;
+  o.cigar_off = 0;
+  o.cigar_len = 0;
+  if (h.item >= 0) {
+    const uint64_t it = static_cast<uint64_t>(h.item);
+    o.ref_id = c_ref[it];
+    o.strand = c_strand[it];
+    o.ref_end = c_start[it] + item_end[it] - 1;
+    if (sl == 0 && want_cigar) {
+      o.read_start = h.read_start;
+      o.read_end = h.read_end;
+      o.ref_start = c_start[it] + h.start_j - 1;
+      o.cigar_off = cigar_off[i];
+      o.cigar_len = h.cigar_len;
+    }
+  }
+  if (sl == 0) best[i] = o;
+  else per_ref[i * (slots - 1) + (sl - 1)] = o;
+}
+
+int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, cudaStream_t st) {
+  if (b.n_reads == 0) return 0;
+  const uint64_t total = static_cast<uint64_t>(b.n_reads) * (1 + n_refs);
+  k_assemble<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(
+      b.n_reads, 1 + n_refs, b.hits, b.c_ref, b.c_strand, b.c_start, b.item_end, b.cigar_off, want_cigar,
+      b.out_best, b.out_per_ref);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,
                     cudaStream_t st) {
   if (b.n_reads == 0) return 0;

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "sr_host.h"
@@ -86,6 +87,10 @@ struct sr_session {
   uint64_t hbm_budget = 0;
   std::atomic<uint64_t> hbm_used{0};
   Server* server = nullptr;
+  // the arena of the last freed batch, kept for the next one (not counted in hbm_used)
+  std::mutex spare_mu;
+  void* spare = nullptr;
+  uint64_t spare_bytes = 0;
 };
 
 struct sr_batch {
@@ -93,13 +98,12 @@ struct sr_batch {
   cudaStream_t stream = nullptr;
   BatchDev d{};
   void* arena = nullptr;
-  uint64_t bytes = 0;
+  uint64_t bytes = 0;        // carved size (counted in the session's hbm_used)
+  uint64_t arena_bytes = 0;  // allocated size (>= bytes when taken from the session's spare)
   uint32_t n_reads = 0;
   uint64_t n_items = 0;
   uint64_t cells = 0;
-  std::vector<uint64_t> h_cstart;
-  std::vector<uint8_t> h_cref, h_cstrand;
-  std::vector<uint16_t> h_item_m;  // read length of each item
+  uint64_t items_by_len[kMaxReadLen + 1] = {};  // windows per read length
   uint32_t max_m = 0;
   cudaGraphExec_t graph = nullptr;
   sr_score_params g_sp{};
@@ -230,6 +234,7 @@ extern "C" void sr_session_close(sr_session* s) {
     s->server = nullptr;
   }
   for (auto* w : s->d_words) cudaFree(w);
+  if (s->spare) cudaFree(s->spare);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
@@ -334,23 +339,89 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   if (nc && (!cands->ref_id || !cands->strand || !cands->win_start || !cands->win_len))
     return set_error(SR_EINVAL, "sr_batch_stage: null candidate arrays");
   // host-side validation: every kernel relies on these bounds (window copies,
-  // shared-memory column streams, packed read rows)
-  for (uint32_t r = 0; r < n; ++r) {
-    if (reads->offsets[r + 1] < reads->offsets[r] || cands->offsets[r + 1] < cands->offsets[r])
-      return set_error(SR_EINVAL, "sr_batch_stage: decreasing offsets");
-    const uint64_t m = reads->offsets[r + 1] - reads->offsets[r];
-    if (m == 0 || m > SR_MAX_READ_LEN)
-      return set_error(SR_EINVAL, "sr_batch_stage: read %u has length %llu, must be 1..256", r,
-                       static_cast<unsigned long long>(m));
-    if (cands->offsets[r + 1] - cands->offsets[r] >= (1ull << 19))
-      return set_error(SR_EINVAL, "sr_batch_stage: read %u has more than 2^19-1 windows", r);
+  // shared-memory column streams, packed read rows).  Read ranges are checked in
+  // parallel; the first bad read (lowest index) is reported.  The same pass
+  // counts the DP cells and the windows per read length.
+  struct Part {
+    uint64_t cells = 0;
+    uint32_t max_m = 0;
+    uint64_t by_len[kMaxReadLen + 1] = {};
+    uint32_t bad_read = UINT32_MAX;
+    int why = 0;  // 1 offsets, 2 read length, 3 window count, 4 window
+    uint64_t bad_win = 0;
+  };
+  const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const uint32_t nthr = (n < 65536u) ? 1u : hw;
+  std::vector<Part> parts(nthr);
+  auto check = [&](uint32_t t) {
+    Part& P = parts[t];
+    const uint32_t r0 = static_cast<uint32_t>(static_cast<uint64_t>(n) * t / nthr);
+    const uint32_t r1 = static_cast<uint32_t>(static_cast<uint64_t>(n) * (t + 1) / nthr);
+    for (uint32_t r = r0; r < r1; ++r) {
+      const uint64_t a0 = reads->offsets[r], a1 = reads->offsets[r + 1];
+      const uint64_t c0 = cands->offsets[r], c1 = cands->offsets[r + 1];
+      if (a1 < a0 || c1 < c0 || c1 > nc) {
+        P.bad_read = r;
+        P.why = 1;
+        return;
+      }
+      const uint64_t m = a1 - a0;
+      if (m == 0 || m > SR_MAX_READ_LEN) {
+        P.bad_read = r;
+        P.why = 2;
+        return;
+      }
+      if (c1 - c0 >= (1ull << 19)) {
+        P.bad_read = r;
+        P.why = 3;
+        return;
+      }
+      for (uint64_t k = c0; k < c1; ++k) {
+        const uint32_t ref = cands->ref_id[k], len = cands->win_len[k];
+        if (ref >= s->n_refs || cands->strand[k] > 1 || len < 1 || len > SR_MAX_WIN_LEN ||
+            cands->win_start[k] > s->lens[ref] || cands->win_start[k] + len > s->lens[ref]) {
+          P.bad_read = r;
+          P.why = 4;
+          P.bad_win = k;
+          return;
+        }
+        P.cells += m * len;
+      }
+      P.by_len[m] += c1 - c0;
+      P.max_m = std::max<uint32_t>(P.max_m, static_cast<uint32_t>(m));
+    }
+  };
+  if (nthr == 1) {
+    check(0);
+  } else {
+    std::vector<std::thread> th;
+    for (uint32_t t = 0; t < nthr; ++t) th.emplace_back(check, t);
+    for (auto& x : th) x.join();
   }
-  for (uint64_t k = 0; k < nc; ++k) {
-    const uint32_t ref = cands->ref_id[k], len = cands->win_len[k];
-    if (ref >= s->n_refs || cands->strand[k] > 1 || len < 1 || len > SR_MAX_WIN_LEN ||
-        cands->win_start[k] > s->lens[ref] || cands->win_start[k] + len > s->lens[ref])
-      return set_error(SR_EINVAL, "sr_batch_stage: window %llu is outside its reference or malformed",
-                       static_cast<unsigned long long>(k));
+  uint64_t cells = 0;
+  uint32_t max_m = 0;
+  uint64_t by_len[kMaxReadLen + 1] = {};
+  const Part* worst = nullptr;
+  for (const Part& P : parts) {
+    if (P.bad_read != UINT32_MAX && (!worst || P.bad_read < worst->bad_read)) worst = &P;
+    cells += P.cells;
+    max_m = std::max(max_m, P.max_m);
+    for (int m = 0; m <= kMaxReadLen; ++m) by_len[m] += P.by_len[m];
+  }
+  if (worst) {
+    const uint32_t r = worst->bad_read;
+    switch (worst->why) {
+      case 1:
+        return set_error(SR_EINVAL, "sr_batch_stage: decreasing or out-of-range offsets at read %u", r);
+      case 2:
+        return set_error(SR_EINVAL, "sr_batch_stage: read %u has length %llu, must be 1..256", r,
+                         static_cast<unsigned long long>(reads->offsets[r + 1] - reads->offsets[r]));
+      case 3:
+        return set_error(SR_EINVAL, "sr_batch_stage: read %u has more than 2^19-1 windows", r);
+      default:
+        return set_error(SR_EINVAL, "sr_batch_stage: window %llu is outside its reference or malformed",
+                         static_cast<unsigned long long>(worst->bad_win));
+    }
   }
   const uint64_t bytes = batch_bytes_estimate(n, nc, nb, s->n_refs);
   if (check_budget && s->hbm_budget && s->hbm_used.load() + bytes > s->hbm_budget)
@@ -406,14 +477,45 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   c.take(d.tb_flag, n);
   c.take(d.tb_list, 2ull * n);
   c.take(d.tb_count, kTbCountWords);
+  c.take(d.out_best, n);
+  c.take(d.out_per_ref, static_cast<uint64_t>(n) * s->n_refs);
   b->bytes = c.off + 256;
-  cudaError_t e = cudaMalloc(&b->arena, b->bytes);
-  if (e != cudaSuccess) {
-    delete b;
-    cudaGetLastError();
-    return set_error(SR_ENOMEM, "sr_batch_stage: device allocation of %llu bytes failed",
-                     static_cast<unsigned long long>(c.off));
+  {
+    std::lock_guard<std::mutex> lk(s->spare_mu);
+    if (s->spare && s->spare_bytes >= b->bytes) {
+      b->arena = s->spare;
+      b->arena_bytes = s->spare_bytes;
+      s->spare = nullptr;
+      s->spare_bytes = 0;
+    }
   }
+  if (!b->arena) {
+    cudaError_t e = cudaMalloc(&b->arena, b->bytes);
+    if (e != cudaSuccess) {
+      // the cached arena may be what is in the way
+      cudaGetLastError();
+      void* sp = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(s->spare_mu);
+        sp = s->spare;
+        s->spare = nullptr;
+        s->spare_bytes = 0;
+      }
+      if (sp) {
+        cudaFree(sp);
+        e = cudaMalloc(&b->arena, b->bytes);
+      }
+      if (e != cudaSuccess) {
+        b->arena = nullptr;
+        delete b;
+        cudaGetLastError();
+        return set_error(SR_ENOMEM, "sr_batch_stage: device allocation of %llu bytes failed",
+                         static_cast<unsigned long long>(c.off));
+      }
+    }
+    b->arena_bytes = b->bytes;
+  }
+  cudaError_t e = cudaSuccess;
   char* base = static_cast<char*>(b->arena);
   rebase_c(d.bases, base);
   rebase_c(d.read_off, base);
@@ -447,6 +549,8 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   rebase(d.tb_flag, base);
   rebase(d.tb_list, base);
   rebase(d.tb_count, base);
+  rebase(d.out_best, base);
+  rebase(d.out_per_ref, base);
   d.n_reads = n;
   d.n_items = nc;
   s->hbm_used += b->bytes;
@@ -477,21 +581,9 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
     sr_batch_free(b);
     return cuda_error("sr_batch_stage copy", e);
   }
-  // host copies used to assemble results, and the DP cell count
-  b->h_cstart.assign(cands->win_start, cands->win_start + nc);
-  b->h_cref.assign(cands->ref_id, cands->ref_id + nc);
-  b->h_cstrand.assign(cands->strand, cands->strand + nc);
-  uint64_t cells = 0;
-  b->h_item_m.resize(nc);
-  for (uint32_t r = 0; r < n; ++r) {
-    const uint64_t m = reads->offsets[r + 1] - reads->offsets[r];
-    b->max_m = std::max<uint32_t>(b->max_m, static_cast<uint32_t>(std::min<uint64_t>(m, 65535)));
-    for (uint64_t k = cands->offsets[r]; k < cands->offsets[r + 1]; ++k) {
-      cells += m * cands->win_len[k];
-      b->h_item_m[k] = static_cast<uint16_t>(std::min<uint64_t>(m, 65535));
-    }
-  }
   b->cells = cells;
+  b->max_m = max_m;
+  std::memcpy(b->items_by_len, by_len, sizeof(by_len));
   *out = b;
   return SR_OK;
 }
@@ -503,7 +595,17 @@ extern "C" void sr_batch_free(sr_batch* b) {
     if (ev) cudaEventDestroy(ev);
   if (b->arena) {
     cudaStreamSynchronize(b->stream);
-    cudaFree(b->arena);
+    // keep the larger of this arena and the session's spare for the next batch
+    void* drop = b->arena;
+    {
+      std::lock_guard<std::mutex> lk(b->s->spare_mu);
+      if (!b->s->spare || b->s->spare_bytes < b->arena_bytes) {
+        drop = b->s->spare;
+        b->s->spare = b->arena;
+        b->s->spare_bytes = b->arena_bytes;
+      }
+    }
+    if (drop) cudaFree(drop);
     b->s->hbm_used -= b->bytes;
   }
   delete b;
@@ -592,8 +694,8 @@ sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp,
   tune_get_bins(bins);
   {
     uint64_t n32 = 0;
-    for (uint64_t k = 0; k < b->n_items; ++k)
-      if (o.force_i32 || !i16_tables || static_cast<int64_t>(sp->match) * b->h_item_m[k] > 32767 - kBias) ++n32;
+    for (int m = 0; m <= kMaxReadLen; ++m)
+      if (o.force_i32 || !i16_tables || static_cast<int64_t>(sp->match) * m > 32767 - kBias) n32 += b->items_by_len[m];
     b->i32_items = o.engine == SR_ENGINE_PLAIN ? 0 : n32;
   }
   const bool plain = o.engine == SR_ENGINE_PLAIN;
@@ -720,73 +822,61 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
   if (st != SR_OK) return st;
   const uint32_t n = b->n_reads, nr = s->n_refs;
   const uint64_t nc = b->n_items;
-  const int slots = 1 + static_cast<int>(nr);
   auto* r = static_cast<sr_results*>(calloc(1, sizeof(sr_results)));
   if (!r) return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
   r->n_reads = n;
   r->n_refs = nr;
   r->n_items = nc;
   r->cells = b->cells;
-  r->best = static_cast<sr_hit*>(calloc(n ? n : 1, sizeof(sr_hit)));
-  r->best_per_ref = static_cast<sr_hit*>(calloc(static_cast<size_t>(n ? n : 1) * nr, sizeof(sr_hit)));
+  r->best = static_cast<sr_hit*>(malloc(static_cast<size_t>(n ? n : 1) * sizeof(sr_hit)));
+  r->best_per_ref = static_cast<sr_hit*>(malloc(static_cast<size_t>(n ? n : 1) * (nr ? nr : 1) * sizeof(sr_hit)));
   r->item_score = static_cast<int32_t*>(malloc((nc ? nc : 1) * 4));
   r->item_end = static_cast<uint32_t*>(malloc((nc ? nc : 1) * 4));
-  std::vector<DevHit> hits(static_cast<size_t>(n) * slots);
-  std::vector<uint32_t> coff(n + 1ull, 0);
   if (!r->best || !r->best_per_ref || !r->item_score || !r->item_end) {
     sr_results_free(r);
     return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
   }
-  cudaError_t e = cudaSuccess;
-  if (nc) {
-    e = cudaMemcpy(r->item_score, b->d.item_score, nc * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(r->item_end, b->d.item_end, nc * 4, cudaMemcpyDeviceToHost);
-  }
-  if (e == cudaSuccess && n) e = cudaMemcpy(hits.data(), b->d.hits, hits.size() * sizeof(DevHit), cudaMemcpyDeviceToHost);
+  // records in the public layout are assembled on the device, then every array
+  // comes back with one copy each on the batch's stream and a single wait
   const bool cig = b->last_opts.want_cigar != 0;
-  if (e == cudaSuccess && n && cig) e = cudaMemcpy(coff.data(), b->d.cigar_off, (n + 1ull) * 4, cudaMemcpyDeviceToHost);
+  if (launch_assemble(b->d, static_cast<int>(nr), cig, stream) < 0) {
+    sr_results_free(r);
+    return cuda_error("sr_batch_fetch assemble", cudaGetLastError());
+  }
+  uint32_t total = 0;
+  cudaError_t e = cudaSuccess;
+  if (n && cig) {
+    e = cudaMemcpyAsync(&total, b->d.cigar_off + n, 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  }
   if (e == cudaSuccess && cig) {
-    const uint64_t total = n ? coff[n] : 0;
     r->n_cigar = total;
-    r->cigar = static_cast<uint32_t*>(malloc((total ? total : 1) * 4));
+    r->cigar = static_cast<uint32_t*>(malloc((total ? total : 1) * 4ull));
     if (!r->cigar) {
       sr_results_free(r);
       return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
     }
-    if (total) e = cudaMemcpy(r->cigar, b->d.cigar, total * 4, cudaMemcpyDeviceToHost);
   }
   if (e == cudaSuccess && b->last_opts.classify) {
     r->read_class = static_cast<uint8_t*>(malloc(n ? n : 1));
-    if (n) e = cudaMemcpy(r->read_class, b->d.read_class, n, cudaMemcpyDeviceToHost);
+    if (!r->read_class) {
+      sr_results_free(r);
+      return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
+    }
   }
+  auto copy = [&](void* dst, const void* src, uint64_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, stream);
+  };
+  copy(r->item_score, b->d.item_score, nc * 4);
+  copy(r->item_end, b->d.item_end, nc * 4);
+  copy(r->best, b->d.out_best, static_cast<uint64_t>(n) * sizeof(sr_hit));
+  copy(r->best_per_ref, b->d.out_per_ref, static_cast<uint64_t>(n) * nr * sizeof(sr_hit));
+  if (cig) copy(r->cigar, b->d.cigar, static_cast<uint64_t>(total) * 4);
+  if (b->last_opts.classify) copy(r->read_class, b->d.read_class, n);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
     sr_results_free(r);
     return cuda_error("sr_batch_fetch copy", e);
-  }
-  for (uint32_t i = 0; i < n; ++i) {
-    for (int sl = 0; sl < slots; ++sl) {
-      const DevHit& h = hits[static_cast<size_t>(i) * slots + sl];
-      sr_hit o{};
-      o.score = h.score;
-      o.second = h.second;
-      o.n_ties = h.n_ties;
-      o.item = h.item;
-      if (h.item >= 0) {
-        const uint64_t it = static_cast<uint64_t>(h.item);
-        o.ref_id = b->h_cref[it];
-        o.strand = b->h_cstrand[it];
-        o.ref_end = b->h_cstart[it] + r->item_end[it] - 1;
-        if (sl == 0 && cig) {
-          o.read_start = h.read_start;
-          o.read_end = h.read_end;
-          o.ref_start = b->h_cstart[it] + h.start_j - 1;
-          o.cigar_off = coff[i];
-          o.cigar_len = h.cigar_len;
-        }
-      }
-      if (sl == 0) r->best[i] = o;
-      else r->best_per_ref[static_cast<size_t>(i) * nr + (sl - 1)] = o;
-    }
   }
   *out = r;
   return SR_OK;

@@ -201,15 +201,32 @@ def make_cands(cand_off, c_ref, c_strand, c_start, c_len, keep: _Keep):
     return cl
 
 
+class _ResultsOwner:
+    """Frees an sr_results when the last array viewing it is gone."""
+
+    def __init__(self, rp):
+        self.rp = rp
+
+    def __del__(self):
+        try:
+            lib().sr_results_free(self.rp)
+        except Exception:
+            pass
+
+
 def results_to_numpy(rp) -> dict:
+    """Arrays viewing the library's result buffers (no copy); the buffers are
+    released with sr_results_free once no array refers to them."""
     r = rp.contents
     n, nr, ni = r.n_reads, r.n_refs, r.n_items
+    owner = _ResultsOwner(rp)
 
     def arr(ptr, count, dtype):
         if count == 0 or not ptr:
             return np.zeros(0, dtype)
         buf = (C.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr if isinstance(ptr, int) else C.cast(ptr, C.c_void_p).value)
-        return np.frombuffer(buf, dtype).copy()
+        buf._owner = owner
+        return np.frombuffer(buf, dtype)
 
     out = dict(
         best=arr(C.cast(r.best, C.c_void_p).value, n, HIT_DTYPE),
@@ -221,7 +238,6 @@ def results_to_numpy(rp) -> dict:
         cells=int(r.cells),
         n_reads=n, n_refs=nr, n_items=ni,
     )
-    lib().sr_results_free(rp)
     return out
 
 

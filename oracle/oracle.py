@@ -78,6 +78,8 @@ def lib():
                                C.POINTER(Aln)]
         L.or_align.restype = C.c_int
         L.or_select.argtypes = [C.c_int, P, P, P, P, P, C.c_int, P, P, P, P]
+        L.or_report.argtypes = [C.c_int, P, P, P, P, P, C.c_int, C.c_int, C.c_int, P]
+        L.or_report.restype = C.c_int
         L.or_classify.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32]
         L.or_classify.restype = C.c_int
         L.or_candidates.argtypes = [C.c_int, P, P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -140,6 +142,35 @@ def select(scores, ref_ids, strands, gends, cands=None, ref_filter=-1):
     lib().or_select(n, _p(sc), _p(ri), _p(st), _p(ge), _p(cd), ref_filter,
                     C.byref(b), C.byref(s), C.byref(t), C.byref(w))
     return dict(best=b.value, second=s.value, n_ties=t.value, winner=w.value)
+
+
+REPORT_BEST_N, REPORT_TIED = 1, 2
+
+
+def report(scores, ref_ids, strands, gends, kind, n_best=1, cands=None, cap=256):
+    """Indices of one read's reported items (Sec. 4.2 tracker options), in order."""
+    n = len(scores)
+    sc = np.ascontiguousarray(scores, np.int32)
+    ri = np.ascontiguousarray(ref_ids, np.int32)
+    st = np.ascontiguousarray(strands, np.int32)
+    ge = np.ascontiguousarray(gends, np.int64)
+    cd = np.ascontiguousarray(np.arange(n) if cands is None else cands, np.int32)
+    out = np.zeros(max(cap, 1), np.int32)
+    k = lib().or_report(n, _p(sc), _p(ri), _p(st), _p(ge), _p(cd), kind, n_best, cap, _p(out))
+    return out[:k].copy()
+
+
+def report_batch(res: dict, cand_off, c_ref, c_strand, c_start, kind, n_best=1, cap=256):
+    """Per read, the global item indices reported from a run_batch result."""
+    co = np.asarray(cand_off, np.int64)
+    out = []
+    for r in range(len(co) - 1):
+        c0, c1 = int(co[r]), int(co[r + 1])
+        ends = np.asarray(c_start[c0:c1], np.int64) + np.asarray(res["item_end_j"][c0:c1], np.int64) - 1
+        idx = report(res["item_score"][c0:c1], c_ref[c0:c1], c_strand[c0:c1], ends, kind, n_best,
+                     cands=np.arange(c1 - c0), cap=cap)
+        out.append(idx + c0)
+    return out
 
 
 def classify(score_a: int, score_b: int, min_score: int = 40, margin: int = 5) -> int:

@@ -206,6 +206,50 @@ void or_select(int n_items, const int32_t* score, const int32_t* ref_id, const i
   *n_ties = ties;
 }
 
+/* Score-tracker report options of Sec. 4.2: the highest-scoring CALs up to a
+ * number (kind 1), or all CALs tied for the highest score (kind 2).  The items
+ * with a positive score are taken in the winner order of or_select (score
+ * descending, then ref_id, global end, strand, candidate index ascending); an
+ * item whose (ref_id, global end, strand) equals that of an item already taken
+ * reports the same alignment and is skipped.  Kind 1 stops after n_best items,
+ * kind 2 at the first item scoring below the best.  At most cap indices are
+ * written to out; the return value is the number written. */
+int or_report(int n_items, const int32_t* score, const int32_t* ref_id, const int32_t* strand,
+              const int64_t* gend, const int32_t* cand, int kind, int n_best, int cap, int32_t* out) {
+  int* order = (int*)malloc(sizeof(int) * (n_items > 0 ? n_items : 1));
+  int n = 0;
+  for (int t = 0; t < n_items; ++t)
+    if (score[t] > 0) order[n++] = t;
+  /* selection sort by the winner order */
+  for (int a = 0; a < n; ++a) {
+    int b = a;
+    for (int c = a + 1; c < n; ++c) {
+      int x = order[c], y = order[b], better;
+      if (score[x] != score[y]) better = score[x] > score[y];
+      else if (ref_id[x] != ref_id[y]) better = ref_id[x] < ref_id[y];
+      else if (gend[x] != gend[y]) better = gend[x] < gend[y];
+      else if (strand[x] != strand[y]) better = strand[x] < strand[y];
+      else better = cand[x] < cand[y];
+      if (better) b = c;
+    }
+    int tmp = order[a]; order[a] = order[b]; order[b] = tmp;
+  }
+  int k = 0;
+  for (int a = 0; a < n && k < cap; ++a) {
+    int x = order[a];
+    if (kind == 1 && k >= n_best) break;
+    if (kind == 2 && score[x] != score[order[0]]) break;
+    int seen = 0;
+    for (int u = 0; u < k; ++u) {
+      int y = out[u];
+      if (ref_id[y] == ref_id[x] && gend[y] == gend[x] && strand[y] == strand[x]) { seen = 1; break; }
+    }
+    if (!seen) out[k++] = x;
+  }
+  free(order);
+  return k;
+}
+
 /* Xenograft classification (Sec. 6.1, 6.2: the higher score decides; Sec. 6.4:
  * equal is a tie, a read aligned to one reference only counts for it, reads
  * aligned to neither with any certainty are unaligned).  min_score is the

@@ -56,6 +56,9 @@ void or_select(int n_items, const int32_t* score, const int32_t* ref_id, const i
                const int64_t* gend, const int32_t* cand, int ref_filter,
                int32_t* best, int32_t* second, uint32_t* n_ties, int32_t* winner);
 
+int or_report(int n_items, const int32_t* score, const int32_t* ref_id, const int32_t* strand,
+              const int64_t* gend, const int32_t* cand, int kind, int n_best, int cap, int32_t* out);
+
 int or_classify(int32_t score_a, int32_t score_b, int32_t min_score, int32_t margin);
 
 int or_candidates(int n_refs, const uint8_t* const* refs, const int64_t* ref_lens,

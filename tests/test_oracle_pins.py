@@ -440,3 +440,60 @@ def test_batch_matches_per_item_align_and_select():
         assert O.cigar_list(out["cigar"][rd], b["cigar_len"]) == res["cigar"]
         assert b["ref_start"] == c_st[w] + res["start_j"] - 1
         assert b["read_start"] == res["start_i"] and b["read_end"] == res["end_i"]
+
+
+# ---- score-tracker report options (Sec. 4.2: the N highest-scoring CALs, or all
+# CALs tied for the highest score)
+
+def test_report_small_example():
+    # items: 0 (5, ref0, end10), 1 (9, ref0, end20), 2 duplicate of 1's alignment,
+    # 3 (3, ref0, end5), 4 (9, ref1, end20), 5 scores 0 (no alignment)
+    sc, ref, st, ge = [5, 9, 9, 3, 9, 0], [0, 0, 0, 0, 1, 0], [0] * 6, [10, 20, 20, 5, 20, 7]
+    assert list(O.report(sc, ref, st, ge, O.REPORT_BEST_N, 3)) == [1, 4, 0]
+    assert list(O.report(sc, ref, st, ge, O.REPORT_BEST_N, 10)) == [1, 4, 0, 3]
+    assert list(O.report(sc, ref, st, ge, O.REPORT_TIED)) == [1, 4]
+    # the '-' strand at the same end is a different alignment
+    assert list(O.report([4, 4], [0, 0], [1, 0], [9, 9], O.REPORT_TIED)) == [1, 0]
+    assert list(O.report([0, 0], [0, 0], [0, 0], [1, 2], O.REPORT_TIED)) == []
+
+
+def _winner_key(sc, ref, ge, st, t):
+    return (-int(sc[t]), int(ref[t]), int(ge[t]), int(st[t]), t)
+
+
+def test_report_properties_random():
+    """The report is characterised without re-deriving it: its items have
+    pairwise different (ref, end, strand), come in winner order, N = 1 is the
+    tracker's winner and the tied report has n_ties items; every positive item
+    left out shares an alignment key with a reported one, or ranks after the
+    last reported item (N best) / scores below the best (tied)."""
+    rng = random.Random(77)
+    for _ in range(400):
+        n = rng.randint(0, 30)
+        sc = [rng.choice([0, 3, 5, 5, 8, 8, 8]) for _ in range(n)]
+        ref = [rng.randrange(2) for _ in range(n)]
+        st = [rng.randrange(2) for _ in range(n)]
+        ge = [rng.randrange(6) for _ in range(n)]
+        sel = O.select(sc, ref, st, ge)
+        b, ties, w = sel["best"], sel["n_ties"], sel["winner"]
+        for nb in (1, 2, 5, 40):
+            rep = list(O.report(sc, ref, st, ge, O.REPORT_BEST_N, nb))
+            keys = [(ref[t], ge[t], st[t]) for t in rep]
+            assert len(set(keys)) == len(keys)
+            assert all(sc[t] > 0 for t in rep)
+            ranks = [_winner_key(sc, ref, ge, st, t) for t in rep]
+            assert ranks == sorted(ranks)
+            assert len(rep) <= nb
+            if nb == 1:
+                assert rep == ([w] if w >= 0 else [])
+            for t in range(n):
+                if sc[t] <= 0 or t in rep:
+                    continue
+                if (ref[t], ge[t], st[t]) in keys:
+                    continue
+                assert len(rep) == nb and _winner_key(sc, ref, ge, st, t) > ranks[-1]
+        tied = list(O.report(sc, ref, st, ge, O.REPORT_TIED))
+        assert len(tied) == ties
+        assert all(sc[t] == b for t in tied)
+        tkeys = {(ref[t], ge[t], st[t]) for t in tied}
+        assert all((ref[t], ge[t], st[t]) in tkeys for t in range(n) if sc[t] == b and b > 0)

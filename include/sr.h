@@ -205,6 +205,10 @@ sr_status sr_session_open(const sr_index* const* refs, uint32_t n_refs, uint64_t
                           sr_session** out);
 sr_status sr_session_open_seqs(const char* const* seqs, const uint64_t* lens, uint32_t n_refs,
                                uint64_t hbm_budget, sr_session** out);
+/* Closing a session stops its server; its device memory is released once the
+ * last batch staged on it has been freed as well (a batch keeps its session
+ * alive, so sessions and batches may be released in either order).  After
+ * close, the session handle must not be passed to any call. */
 void sr_session_close(sr_session* s);
 
 /* Whole batch, host buffers in and out: stage (host->device), run, fetch
@@ -233,6 +237,39 @@ void sr_batch_free(sr_batch* b);
  * kernel variant.  Any pointer may be NULL. */
 sr_status sr_batch_stats(const sr_batch* b, uint64_t* kernels, uint64_t* cells,
                          uint64_t* i32_items, uint64_t* tasks);
+
+/* Score-tracker report options of Sec. 4.2 for a batch that has run: per read,
+ * the highest-scoring windows up to n_best (SR_REPORT_BEST_N), or every window
+ * tied for the read's best score (SR_REPORT_TIED; n_best is ignored).  Windows
+ * are taken in the winner order of sr_hit (score descending, then ref_id,
+ * reference end, strand '+' first, candidate index); a window whose
+ * (ref_id, reference end, strand) repeats that of a window already reported
+ * holds the same alignment and is skipped, so a read's tied report has n_ties
+ * entries.  Windows scoring 0 are never reported.  At most SR_REPORT_MAX entries
+ * per read: n_best must be 1..SR_REPORT_MAX (else SR_EINVAL), and reads with more
+ * tied alignments are cut at SR_REPORT_MAX and counted in n_truncated.
+ * Selection, counting and compaction run on the device; the result is
+ * allocated by the library and released with sr_report_free.  Fails with
+ * SR_EINVAL if the batch has not run. */
+enum { SR_REPORT_BEST_N = 1, SR_REPORT_TIED = 2 };
+#define SR_REPORT_MAX 256u
+typedef struct {
+  int32_t score;
+  int32_t item;       /* global candidate index */
+  uint8_t ref_id, strand;
+  uint16_t reserved;
+  uint32_t end_col;   /* 1-based last window column of the alignment */
+  uint64_t ref_end;   /* 0-based inclusive end on the reference */
+} sr_report_hit;
+typedef struct {
+  uint32_t n_reads;
+  uint32_t n_truncated;  /* reads whose tied set was cut at SR_REPORT_MAX */
+  uint64_t n_hits;
+  uint64_t* offsets;     /* n_reads + 1: read r's entries are hits[offsets[r] .. offsets[r+1]) */
+  sr_report_hit* hits;
+} sr_report;
+sr_status sr_batch_report(sr_session* s, sr_batch* b, uint32_t kind, uint32_t n_best, sr_report** out);
+void sr_report_free(sr_report* rep);
 
 /* Device time of the last run of a batch, from CUDA events recorded on the
  * launching stream (inside the replayed graph): the whole path, the extension

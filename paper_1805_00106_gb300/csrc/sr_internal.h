@@ -161,6 +161,13 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
                      int n_refs, cudaStream_t st);
 int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);
 int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, cudaStream_t st);
+// report options (sr_report.cu): count pass + scan into a scratch of
+// report_scratch_words(n_reads) words, then the write pass
+uint64_t report_scratch_words(uint32_t n_reads);
+int launch_report_count(const BatchDev& b, int n_refs, int kind, uint32_t n_best, uint32_t* scratch,
+                        cudaStream_t st);
+int launch_report_write(const BatchDev& b, int n_refs, int kind, uint32_t n_best, const uint32_t* scratch,
+                        sr_report_hit* out, cudaStream_t st);
 int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,
                     cudaStream_t st);
 bool extend_config_supported(uint32_t lanes, uint32_t rows);

@@ -87,6 +87,9 @@ struct sr_session {
   uint64_t hbm_budget = 0;
   std::atomic<uint64_t> hbm_used{0};
   Server* server = nullptr;
+  // the handle plus one per live batch: a batch keeps its session alive, so the
+  // two may be released in either order
+  std::atomic<int> live{1};
   // the arena of the last freed batch, kept for the next one (not counted in hbm_used)
   std::mutex spare_mu;
   void* spare = nullptr;
@@ -227,16 +230,21 @@ extern "C" sr_status sr_session_open_seqs(const char* const* seqs, const uint64_
   return open_common(nullptr, seqs, lens, n_refs, hbm_budget, out);
 }
 
+static void session_release(sr_session* s) {
+  if (s->live.fetch_sub(1) != 1) return;
+  for (auto* w : s->d_words) cudaFree(w);
+  if (s->spare) cudaFree(s->spare);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
 extern "C" void sr_session_close(sr_session* s) {
   if (!s) return;
   if (s->server) {
     serve_destroy(s->server);
     s->server = nullptr;
   }
-  for (auto* w : s->d_words) cudaFree(w);
-  if (s->spare) cudaFree(s->spare);
-  if (s->stream) cudaStreamDestroy(s->stream);
-  delete s;
+  session_release(s);
 }
 
 namespace sr {
@@ -429,6 +437,7 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
                      static_cast<unsigned long long>(bytes));
   auto* b = new sr_batch;
   b->s = s;
+  s->live.fetch_add(1);
   b->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : s->stream;
   b->n_reads = n;
   b->n_items = nc;
@@ -507,7 +516,7 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
       }
       if (e != cudaSuccess) {
         b->arena = nullptr;
-        delete b;
+        sr_batch_free(b);
         cudaGetLastError();
         return set_error(SR_ENOMEM, "sr_batch_stage: device allocation of %llu bytes failed",
                          static_cast<unsigned long long>(c.off));
@@ -608,7 +617,9 @@ extern "C" void sr_batch_free(sr_batch* b) {
     if (drop) cudaFree(drop);
     b->s->hbm_used -= b->bytes;
   }
+  sr_session* s = b->s;
   delete b;
+  if (s) session_release(s);
 }
 
 namespace sr {
@@ -879,6 +890,90 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
     return cuda_error("sr_batch_fetch copy", e);
   }
   *out = r;
+  return SR_OK;
+}
+
+extern "C" void sr_report_free(sr_report* rep) {
+  if (!rep) return;
+  free(rep->offsets);
+  free(rep->hits);
+  free(rep);
+}
+
+extern "C" sr_status sr_batch_report(sr_session* s, sr_batch* b, uint32_t kind, uint32_t n_best, sr_report** out) {
+  if (!s || !b || !out || b->s != s) return set_error(SR_EINVAL, "sr_batch_report: bad argument");
+  *out = nullptr;
+  if (!b->ran) return set_error(SR_EINVAL, "sr_batch_report: batch has not run");
+  if (kind != SR_REPORT_BEST_N && kind != SR_REPORT_TIED)
+    return set_error(SR_EINVAL, "sr_batch_report: kind must be SR_REPORT_BEST_N or SR_REPORT_TIED");
+  if (kind == SR_REPORT_BEST_N && (n_best < 1 || n_best > SR_REPORT_MAX))
+    return set_error(SR_EINVAL, "sr_batch_report: n_best must be 1..%u", SR_REPORT_MAX);
+  cudaStream_t stream = b->last_opts.cuda_stream ? static_cast<cudaStream_t>(b->last_opts.cuda_stream) : b->stream;
+  sr_status st = batch_sync(b, stream);
+  if (st != SR_OK) return st;
+  const uint32_t n = b->n_reads;
+  const int nr = static_cast<int>(s->n_refs);
+  auto* rep = static_cast<sr_report*>(calloc(1, sizeof(sr_report)));
+  if (!rep) return set_error(SR_ENOMEM, "sr_batch_report: out of memory");
+  rep->n_reads = n;
+  rep->offsets = static_cast<uint64_t*>(calloc(n + 1ull, sizeof(uint64_t)));
+  if (!rep->offsets) {
+    sr_report_free(rep);
+    return set_error(SR_ENOMEM, "sr_batch_report: out of memory");
+  }
+  if (n == 0) {
+    *out = rep;
+    return SR_OK;
+  }
+  uint32_t* scratch = nullptr;
+  sr_report_hit* d_hits = nullptr;
+  const uint64_t sw = report_scratch_words(n);
+  cudaError_t e = cudaMalloc(&scratch, sw * 4);
+  auto fail = [&](const char* where) {
+    cudaGetLastError();
+    if (scratch) cudaFree(scratch);
+    if (d_hits) cudaFree(d_hits);
+    sr_report_free(rep);
+    return cuda_error(where, e == cudaSuccess ? cudaErrorUnknown : e);
+  };
+  if (e != cudaSuccess) return fail("sr_batch_report alloc");
+  const int kd = static_cast<int>(kind);
+  if (launch_report_count(b->d, nr, kd, n_best, scratch, stream) < 0) {
+    e = cudaGetLastError();
+    return fail("sr_batch_report count");
+  }
+  uint32_t tail[2] = {0, 0};  // total entries, truncated reads
+  const uint32_t* d_off = scratch + n;
+  e = cudaMemcpyAsync(&tail[0], d_off + n, 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&tail[1], scratch + sw - 1, 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return fail("sr_batch_report total");
+  const uint64_t total = tail[0];
+  rep->n_truncated = tail[1];
+  rep->n_hits = total;
+  rep->hits = static_cast<sr_report_hit*>(malloc((total ? total : 1) * sizeof(sr_report_hit)));
+  std::vector<uint32_t> off32(n + 1ull);
+  if (!rep->hits) {
+    e = cudaErrorMemoryAllocation;
+    return fail("sr_batch_report host alloc");
+  }
+  if (total) {
+    e = cudaMalloc(&d_hits, total * sizeof(sr_report_hit));
+    if (e != cudaSuccess) return fail("sr_batch_report alloc");
+    if (launch_report_write(b->d, nr, kd, n_best, scratch, d_hits, stream) < 0) {
+      e = cudaGetLastError();
+      return fail("sr_batch_report write");
+    }
+    e = cudaMemcpyAsync(rep->hits, d_hits, total * sizeof(sr_report_hit), cudaMemcpyDeviceToHost, stream);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(off32.data(), d_off, (n + 1ull) * 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return fail("sr_batch_report copy");
+  for (uint64_t i = 0; i <= n; ++i) rep->offsets[i] = off32[i];
+  cudaFree(scratch);
+  if (d_hits) cudaFree(d_hits);
+  *out = rep;
   return SR_OK;
 }
 

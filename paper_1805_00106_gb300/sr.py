@@ -94,6 +94,20 @@ def _np_dtype(st):
 HIT_DTYPE = _np_dtype(Hit)
 
 
+class ReportHit(C.Structure):
+    _fields_ = [("score", C.c_int32), ("item", C.c_int32), ("ref_id", C.c_uint8), ("strand", C.c_uint8),
+                ("reserved", C.c_uint16), ("end_col", C.c_uint32), ("ref_end", C.c_uint64)]
+
+
+class Report(C.Structure):
+    _fields_ = [("n_reads", C.c_uint32), ("n_truncated", C.c_uint32), ("n_hits", C.c_uint64),
+                ("offsets", P), ("hits", P)]
+
+
+REPORT_HIT_DTYPE = _np_dtype(ReportHit)
+REPORT_BEST_N, REPORT_TIED, REPORT_MAX = 1, 2, 256
+
+
 def lib():
     """Load libsr.so (building it in-tree first if it is missing or stale)."""
     global _lib
@@ -128,6 +142,8 @@ def lib():
             "sr_batch_timing": ([P, P, P, P], C.c_int32),
             "sr_results_free": ([C.POINTER(Results)], None),
             "sr_classify": ([P, P, P, P], C.c_int32),
+            "sr_batch_report": ([P, P, C.c_uint32, C.c_uint32, C.POINTER(C.POINTER(Report))], C.c_int32),
+            "sr_report_free": ([C.POINTER(Report)], None),
             "sr_serve_start": ([P, C.POINTER(ScoreParams), C.POINTER(AlignOpts), C.c_uint32], C.c_int32),
             "sr_submit": ([P, C.POINTER(Reads), C.POINTER(CandList), C.POINTER(C.c_uint64)], C.c_int32),
             "sr_wait": ([P, C.c_uint64, C.c_int32, C.POINTER(C.POINTER(Results))], C.c_int32),
@@ -336,6 +352,22 @@ class Batch:
         prm = np.array([min_score, margin], np.int32)
         _check(lib().sr_classify(self.session.h, self.h, _p(prm), _p(out)))
         return out[:n]
+
+    def report(self, kind=REPORT_BEST_N, n_best=1):
+        """Sec. 4.2 tracker options on the device: per read, the n_best highest-scoring
+        windows (REPORT_BEST_N) or all windows tied for the best (REPORT_TIED).
+        Returns dict(offsets (n_reads + 1), hits (REPORT_HIT_DTYPE), n_truncated)."""
+        out = C.POINTER(Report)()
+        _check(lib().sr_batch_report(self.session.h, self.h, kind, n_best, C.byref(out)))
+        try:
+            r = out.contents
+            n, nh = r.n_reads, r.n_hits
+            offs = np.frombuffer((C.c_char * (8 * (n + 1))).from_address(r.offsets), np.uint64).copy()
+            hits = (np.frombuffer((C.c_char * (REPORT_HIT_DTYPE.itemsize * nh)).from_address(r.hits),
+                                  REPORT_HIT_DTYPE).copy() if nh else np.zeros(0, REPORT_HIT_DTYPE))
+            return dict(offsets=offs, hits=hits, n_truncated=int(r.n_truncated))
+        finally:
+            lib().sr_report_free(out)
 
     def stats(self):
         k, c, i, t = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()

@@ -211,6 +211,19 @@ sr_status sr_session_open_seqs(const char* const* seqs, const uint64_t* lens, ui
  * close, the session handle must not be passed to any call. */
 void sr_session_close(sr_session* s);
 
+/* The same CAL finder and filter on the GPU (the paper runs it on the host,
+ * Sec. 4.1-4.2; here the index lives in HBM next to the references).
+ * sr_session_attach_index uploads idx[r], the index of the session's reference
+ * r (same length; all with one seed_len and address_bases), once; replacing an
+ * attached set is allowed.  sr_candidates_device then returns exactly the list
+ * sr_candidates returns for those indexes (same windows, order and hits): one
+ * warp per read looks up its seeds, one block per read sorts and merges its
+ * CALs.  Reads longer than SR_MAX_READ_LEN are SR_EINVAL, non-ACGT bases
+ * SR_EBADBASE, no attached index SR_EINVAL.  params->n_threads is unused. */
+sr_status sr_session_attach_index(sr_session* s, const sr_index* const* idx, uint32_t n_refs);
+sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, const sr_cand_params* params,
+                               sr_cand_list** out);
+
 /* Whole batch, host buffers in and out: stage (host->device), run, fetch
  * (device->host).  Errors: SR_EINVAL (shapes, windows past the reference,
  * read or window too long, parameters), SR_EBADBASE, SR_ENOMEM, SR_ECUDA. */

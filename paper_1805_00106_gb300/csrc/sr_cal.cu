@@ -1,0 +1,352 @@
+// sr_cal.cu -- the CAL finder and filter on the device (McVicar et al., arXiv
+// 1805.00106, Sec. 3.2 CAL finder, Sec. 3.3 CAL filter; the paper's V2 keeps
+// them on the host, Sec. 4.1-4.2).  Same windows, in the same order, as the host
+// stage sr_candidates.
+//
+//   count / emit  one warp per read: the read's 2-bit codes in shared memory,
+//                 each lane takes seeds o = lane*stride, (lane+32)*stride, ...;
+//                 per reference the hashed canonical seed picks a bucket of the
+//                 pointer table, a binary search finds its key among the
+//                 bucket's (key, position)-sorted entries, and every matching
+//                 entry gives a '+' and/or '-' CAL by its orientation bits.
+//                 CALs are packed keys ref << 60 | strand << 59 | (cal + 1024).
+//   filter        one block per read: bitonic sort of its CAL keys (shared
+//                 memory, or global scratch for very large reads), then the
+//                 merge of consecutive CALs <= merge_dist apart into windows
+//                 represented by their most frequent CAL (smallest on ties),
+//                 the max_cands cut by hit count, and the clamped window
+//                 [cal - pad, cal + m + pad).
+//   compact       per-read windows to contiguous arrays.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sr_internal.h"
+#include "sr_seed.h"
+
+namespace sr {
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr int kCalWarps = 4;
+constexpr uint64_t kCalBias = 1024;
+constexpr uint64_t kCalMask = (1ull << 59) - 1;
+constexpr uint64_t kNoKey = ~0ull;
+
+__device__ __forceinline__ uint64_t cal_key(uint32_t ref, uint32_t strand, int64_t cal) {
+  return (static_cast<uint64_t>(ref) << 60) | (static_cast<uint64_t>(strand) << 59) |
+         static_cast<uint64_t>(cal + static_cast<int64_t>(kCalBias));
+}
+
+// ASCII -> 2-bit code; 4 for a non-ACGT byte
+__device__ __forceinline__ uint32_t code_of(char ch) {
+  switch (static_cast<unsigned>(static_cast<unsigned char>(ch)) | 0x20u) {
+    case 'a': return 0;
+    case 'c': return 1;
+    case 'g': return 2;
+    case 't': return 3;
+    default: return 4;
+  }
+}
+
+// entries [lo, hi) of reference r whose key equals the seed's
+__device__ __forceinline__ void lookup(const DevIndex& di, int r, uint64_t canon, uint64_t* lo, uint64_t* hi) {
+  const int kb = 2 * (di.k - di.a);
+  const uint64_t h = seed_hash(canon, di.k, di.hash_seed[r]);
+  const uint64_t b = h >> kb;
+  const uint32_t key = static_cast<uint32_t>(h & mask_bits(kb));
+  uint64_t s0 = di.ptr[r][b], s1 = di.ptr[r][b + 1];
+  const uint32_t* K = di.key[r];
+  // lower bound of key in the bucket
+  uint64_t l = s0, u = s1;
+  while (l < u) {
+    const uint64_t mid = l + ((u - l) >> 1);
+    if (K[mid] < key) l = mid + 1;
+    else u = mid;
+  }
+  uint64_t e = l;
+  while (e < s1 && K[e] == key) ++e;
+  *lo = l;
+  *hi = e;
+}
+
+// read r's codes into shared memory; false (and status) on a non-ACGT base
+__device__ __forceinline__ bool load_codes(const char* bases, uint64_t o0, uint32_t m, uint8_t* q, int lane,
+                                           uint32_t* status) {
+  bool bad = false;
+  for (uint32_t t = lane; t < m; t += 32) {
+    const uint32_t c = code_of(bases[o0 + t]);
+    bad |= c > 3;
+    q[t] = static_cast<uint8_t>(c & 3);
+  }
+  bad = __any_sync(FULL, bad);
+  if (bad && lane == 0) atomicOr(status, kStBadBase);
+  __syncwarp();
+  return !bad;
+}
+
+struct SeedArgs {
+  DevIndex di;
+  const char* bases;
+  const uint64_t* read_off;
+  uint32_t r0, nr;        // reads r0 .. r0 + nr
+  uint32_t stride;
+  uint32_t* count;        // count pass: CALs per read (indexed r - r0)
+  const uint64_t* off;    // emit pass: first slot of each read (indexed r - r0)
+  uint64_t* cals;         // emit pass
+  uint32_t* status;
+};
+
+template <bool EMIT>
+__global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
+  __shared__ uint8_t qs[kCalWarps][kMaxReadLen];
+  __shared__ uint32_t ctr[kCalWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint8_t* q = qs[warp];
+  const int k = a.di.k;
+  for (uint32_t rr = blockIdx.x * kCalWarps + warp; rr < a.nr; rr += gridDim.x * kCalWarps) {
+    const uint32_t r = a.r0 + rr;
+    const uint64_t o0 = a.read_off[r];
+    const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - o0);  // <= 256, checked on the host
+    if (lane == 0) ctr[warp] = 0;
+    __syncwarp();
+    uint32_t n = 0;
+    if (load_codes(a.bases, o0, m, q, lane, a.status) && m >= static_cast<uint32_t>(k)) {
+      const uint64_t base = EMIT ? a.off[rr] : 0;
+      for (uint32_t o = lane * a.stride; o + k <= m; o += 32 * a.stride) {
+        Kmer km;
+        for (int t = 0; t < k; ++t) kmer_push(km, q[o + t], k);
+        const uint64_t canon = km.fwd < km.rc ? km.fwd : km.rc;
+        const uint32_t rori = (km.fwd == canon ? 1u : 0u) | (km.rc == canon ? 2u : 0u);
+        for (int r2 = 0; r2 < a.di.n_refs; ++r2) {
+          uint64_t lo, hi;
+          lookup(a.di, r2, canon, &lo, &hi);
+          for (uint64_t e = lo; e < hi; ++e) {
+            const uint32_t fo = a.di.orient[r2][e];
+            const bool plus = ((fo & 1u) && (rori & 1u)) || ((fo & 2u) && (rori & 2u));
+            const bool minus = ((fo & 1u) && (rori & 2u)) || ((fo & 2u) && (rori & 1u));
+            if (EMIT) {
+              const int64_t p = a.di.pos[r2][e];
+              if (plus) a.cals[base + atomicAdd(&ctr[warp], 1u)] = cal_key(r2, 0, p - o);
+              if (minus) a.cals[base + atomicAdd(&ctr[warp], 1u)] =
+                  cal_key(r2, 1, p - static_cast<int64_t>(m - o - k));
+            } else {
+              n += (plus ? 1u : 0u) + (minus ? 1u : 0u);
+            }
+          }
+        }
+      }
+    }
+    if (!EMIT) {
+      n = __reduce_add_sync(FULL, n);
+      if (lane == 0) a.count[rr] = n;
+    }
+    __syncwarp();
+  }
+}
+
+// block-wide bitonic sort of P (a power of two) keys, ascending
+__device__ void bitonic(uint64_t* s, uint32_t P) {
+  for (uint32_t size = 2; size <= P; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
+        const uint32_t lo = 2 * i - (i & (stride - 1));
+        const uint32_t hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t x = s[lo], y = s[hi];
+        if ((x > y) == up) {
+          s[lo] = y;
+          s[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t pow2_at_least(uint32_t n) {
+  uint32_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+struct FilterArgs {
+  DevIndex di;
+  const uint64_t* read_off;
+  uint32_t r0, nr;
+  uint32_t merge_dist, pad, max_cands;
+  const uint32_t* count;  // CALs per read
+  const uint64_t* off;    // first slot of each read in cals / the window arrays
+  uint64_t* cals;
+  uint32_t smem_cap;      // reads with more CALs are left to the large-read kernel
+  uint32_t* nwin;         // windows per read
+  uint64_t* wkey;         // window CAL key (then reused for the start)
+  uint32_t* whits;
+  uint32_t* wlen;
+};
+
+// the filter of one read (whole block); keys: its CALs, room for P keys
+__device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, uint32_t n) {
+  __shared__ uint32_t s_nw;
+  const uint32_t r = a.r0 + rr;
+  const uint64_t base = a.off[rr];
+  const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - a.read_off[r]);
+  const uint32_t P = pow2_at_least(n);
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) keys[i] = i < n ? a.cals[base + i] : kNoKey;
+  __syncthreads();
+  bitonic(keys, P);
+  // merge: consecutive CALs of one (ref, strand) at most merge_dist apart; the
+  // window keeps the most frequent value (first, i.e. smallest, on ties)
+  if (threadIdx.x == 0) {
+    uint32_t nw = 0;
+    for (uint32_t t = 0; t < n;) {
+      uint32_t u = t + 1;
+      while (u < n && (keys[u] >> 59) == (keys[t] >> 59) && keys[u] - keys[u - 1] <= a.merge_dist) ++u;
+      uint32_t best = 0;
+      uint64_t bk = keys[t];
+      for (uint32_t v = t; v < u;) {
+        uint32_t x = v;
+        while (x < u && keys[x] == keys[v]) ++x;
+        if (x - v > best) {
+          best = x - v;
+          bk = keys[v];
+        }
+        v = x;
+      }
+      a.wkey[base + nw] = bk;
+      a.whits[base + nw] = u - t;
+      ++nw;
+      t = u;
+    }
+    s_nw = nw;
+  }
+  __syncthreads();
+  uint32_t nw = s_nw;
+  if (a.max_cands && nw > a.max_cands) {
+    // keep the max_cands windows with most hits (ties: smaller key), in key order
+    const uint32_t P2 = pow2_at_least(nw);
+    for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x)
+      keys[i] = i < nw ? (static_cast<uint64_t>(0xffffffffu - a.whits[base + i]) << 32) | i : kNoKey;
+    __syncthreads();
+    bitonic(keys, P2);
+    for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x)
+      keys[i] = i < a.max_cands ? (keys[i] & 0xffffffffull) : kNoKey;
+    __syncthreads();
+    bitonic(keys, P2);
+    if (threadIdx.x == 0) {
+      for (uint32_t j = 0; j < a.max_cands; ++j) {
+        const uint32_t src = static_cast<uint32_t>(keys[j]);
+        a.wkey[base + j] = a.wkey[base + src];
+        a.whits[base + j] = a.whits[base + src];
+      }
+    }
+    nw = a.max_cands;
+    __syncthreads();
+  }
+  // window [cal - pad, cal + m + pad) clamped to the reference
+  for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) {
+    const uint64_t key = a.wkey[base + i];
+    const uint32_t ref = static_cast<uint32_t>(key >> 60);
+    const int64_t cal = static_cast<int64_t>(key & kCalMask) - static_cast<int64_t>(kCalBias);
+    const int64_t N = static_cast<int64_t>(a.di.ref_len[ref]);
+    int64_t lo = cal - static_cast<int64_t>(a.pad), hi = cal + m + static_cast<int64_t>(a.pad);
+    if (lo < 0) lo = 0;
+    if (hi > N) hi = N;
+    a.wlen[base + i] = static_cast<uint32_t>(hi - lo);
+    // the key's ref and strand bits stay for the compaction; the start replaces the CAL
+    a.wkey[base + i] = (key & ~kCalMask) | static_cast<uint64_t>(lo);
+  }
+  if (threadIdx.x == 0) a.nwin[rr] = nw;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) k_cal_filter(FilterArgs a) {
+  extern __shared__ uint64_t skeys[];
+  for (uint32_t rr = blockIdx.x; rr < a.nr; rr += gridDim.x) {
+    const uint32_t n = a.count[rr];
+    if (n > a.smem_cap) continue;  // large-read kernel
+    filter_read(a, rr, skeys, n);
+  }
+}
+
+// one block per large read, keys in a global scratch of pow2(n) slots
+__global__ void __launch_bounds__(1024) k_cal_filter_big(FilterArgs a, uint32_t rr, uint64_t* scratch) {
+  filter_read(a, rr, scratch, a.count[rr]);
+}
+
+__global__ void k_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,
+                              const uint64_t* wkey, const uint32_t* whits, const uint32_t* wlen,
+                              uint8_t* o_ref, uint8_t* o_strand, uint64_t* o_start, uint32_t* o_len,
+                              uint32_t* o_hits) {
+  const uint32_t rr = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (rr >= nr) return;
+  const uint64_t base = off[rr];
+  const uint32_t d0 = woff[rr];
+  for (uint32_t i = lane; i < nwin[rr]; i += 32) {
+    const uint64_t key = wkey[base + i];
+    o_ref[d0 + i] = static_cast<uint8_t>(key >> 60);
+    o_strand[d0 + i] = static_cast<uint8_t>((key >> 59) & 1u);
+    o_start[d0 + i] = key & kCalMask;
+    o_len[d0 + i] = wlen[base + i];
+    o_hits[d0 + i] = whits[base + i];
+  }
+}
+
+}  // namespace
+
+int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
+                     uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* status,
+                     cudaStream_t st) {
+  if (nr == 0) return 0;
+  SeedArgs a{di, bases, read_off, r0, nr, stride, count, off, cals, status};
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t need = (nr + kCalWarps - 1) / kCalWarps;
+  const uint32_t grid = need < static_cast<uint32_t>(nsm) * 32 ? need : static_cast<uint32_t>(nsm) * 32;
+  if (cals) k_cal_seeds<true><<<grid, 32 * kCalWarps, 0, st>>>(a);
+  else k_cal_seeds<false><<<grid, 32 * kCalWarps, 0, st>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
+                      uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint64_t* off, uint64_t* cals,
+                      uint32_t max_small, const uint32_t* big, uint32_t n_big, uint64_t* scratch,
+                      uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen, cudaStream_t st) {
+  if (nr == 0) return 0;
+  FilterArgs a{di, read_off, r0, nr, merge_dist, pad, max_cands, count, off, cals, kCalSmemKeys,
+               nwin, wkey, whits, wlen};
+  int launched = 0;
+  uint32_t P = 1;
+  while (P < max_small) P <<= 1;
+  const size_t smem = static_cast<size_t>(P) * sizeof(uint64_t);
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_cal_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kCalSmemKeys * sizeof(uint64_t))) != cudaSuccess)
+      return -1;
+    attr = true;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t grid = nr < static_cast<uint32_t>(nsm) * 64 ? nr : static_cast<uint32_t>(nsm) * 64;
+  k_cal_filter<<<grid, 128, smem, st>>>(a);
+  ++launched;
+  for (uint32_t t = 0; t < n_big; ++t) {
+    k_cal_filter_big<<<1, 1024, 0, st>>>(a, big[t], scratch);
+    ++launched;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? launched : -1;
+}
+
+int launch_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,
+                       const uint64_t* wkey, const uint32_t* whits, const uint32_t* wlen, uint8_t* o_ref,
+                       uint8_t* o_strand, uint64_t* o_start, uint32_t* o_len, uint32_t* o_hits, cudaStream_t st) {
+  if (nr == 0) return 0;
+  k_cal_compact<<<(nr + 7) / 8, 256, 0, st>>>(nr, off, nwin, woff, wkey, whits, wlen, o_ref, o_strand, o_start,
+                                             o_len, o_hits);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace sr

@@ -11,4 +11,17 @@ sr_status set_error(sr_status st, const char* fmt, ...);
 int encode_ascii(const char* s, uint64_t n, uint8_t* out);
 // the index's reference as 2-bit codes
 const uint8_t* index_codes(const sr_index* idx, uint64_t* len);
+// the index's tables (pointer table of 4^address_bases + 1 bucket starts; per
+// entry the hashed seed's key bits, reference position and orientation bits)
+struct IndexTables {
+  uint32_t seed_len, address_bases;
+  uint64_t hash_seed, ref_len;
+  const uint64_t* ptr;
+  uint64_t n_ptr;
+  const uint32_t* key;
+  const uint32_t* pos;
+  const uint8_t* orient;
+  uint64_t n_entries;
+};
+IndexTables index_tables(const sr_index* idx);
 }  // namespace sr

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "sr_host.h"
+#include "sr_seed.h"
 
 struct sr_index {
   sr_index_params p{};
@@ -37,32 +38,6 @@ int encode_ascii(const char* s, uint64_t n, uint8_t* out) {
 }
 
 namespace {
-
-inline uint64_t mask_bits(int bits) { return bits >= 64 ? ~0ull : ((1ull << bits) - 1ull); }
-
-// invertible mix of the 2k-bit canonical seed (xor, odd multiplies, xor-shifts
-// mod 2^(2k)): address + key identify the seed exactly (Sec. 3.1 hashing keeps
-// the exact-match semantics of the key comparison).
-inline uint64_t seed_hash(uint64_t x, int k, uint64_t seed) {
-  const int bits = 2 * k;
-  const uint64_t M = mask_bits(bits);
-  x = (x ^ seed) & M;
-  x = (x * 0x9E3779B97F4A7C15ull) & M;
-  x ^= x >> ((bits + 1) / 2);
-  x = (x * 0xC2B2AE3D27D4EB4Full) & M;
-  x ^= x >> ((bits + 2) / 3);
-  return x & M;
-}
-
-struct Kmer {
-  uint64_t fwd = 0, rc = 0;
-};
-
-inline void kmer_push(Kmer& km, uint8_t c, int k) {
-  const uint64_t M = mask_bits(2 * k);
-  km.fwd = ((km.fwd << 2) | c) & M;
-  km.rc = (km.rc >> 2) | (static_cast<uint64_t>(3u - c) << (2 * (k - 1)));
-}
 
 int n_threads_of(uint32_t req) {
   unsigned hc = std::thread::hardware_concurrency();
@@ -170,6 +145,21 @@ namespace sr {
 const uint8_t* index_codes(const sr_index* idx, uint64_t* len) {
   *len = idx->codes.size();
   return idx->codes.data();
+}
+
+IndexTables index_tables(const sr_index* idx) {
+  IndexTables t;
+  t.seed_len = idx->p.seed_len;
+  t.address_bases = idx->p.address_bases;
+  t.hash_seed = idx->p.hash_seed;
+  t.ref_len = idx->codes.size();
+  t.ptr = idx->ptr.data();
+  t.n_ptr = idx->ptr.size();
+  t.key = idx->key.data();
+  t.pos = idx->pos.data();
+  t.orient = idx->orient.data();
+  t.n_entries = idx->key.size();
+  return t;
 }
 }  // namespace sr
 

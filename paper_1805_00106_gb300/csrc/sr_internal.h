@@ -161,6 +161,37 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
                      int n_refs, cudaStream_t st);
 int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);
 int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, cudaStream_t st);
+// exclusive scan of n counts into out[0..n] (out[n] = total) with a scratch of
+// n / 1024 + 1 words (sr_report.cu)
+int launch_scan_u32(const uint32_t* in, uint32_t n, uint32_t* out, uint32_t* sums, cudaStream_t st);
+
+// device copy of the host index of each reference (sr_cal.cu, Sec. 3.1-3.3)
+struct DevIndex {
+  const uint64_t* ptr[kMaxRefs];
+  const uint32_t* key[kMaxRefs];
+  const uint32_t* pos[kMaxRefs];
+  const uint8_t* orient[kMaxRefs];
+  uint64_t ref_len[kMaxRefs];
+  uint64_t hash_seed[kMaxRefs];
+  int n_refs, k, a;
+};
+constexpr uint32_t kCalSmemKeys = 8192;  // CALs per read sorted in shared memory (64 KB)
+// count pass (cals == nullptr: CALs per read into count) or emit pass (CAL keys
+// of read r0 + i into cals[off[i] ...]) over reads r0 .. r0 + nr
+int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
+                     uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* status,
+                     cudaStream_t st);
+// windows of each read at off[i] (nwin[i] of them); reads with more than
+// kCalSmemKeys CALs are listed in big (n_big, indices into the chunk) and use
+// scratch (pow2 of their largest count); max_small = largest count of the others
+int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
+                      uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint64_t* off, uint64_t* cals,
+                      uint32_t max_small, const uint32_t* big, uint32_t n_big, uint64_t* scratch,
+                      uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen, cudaStream_t st);
+int launch_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,
+                       const uint64_t* wkey, const uint32_t* whits, const uint32_t* wlen, uint8_t* o_ref,
+                       uint8_t* o_strand, uint64_t* o_start, uint32_t* o_len, uint32_t* o_hits, cudaStream_t st);
+
 // report options (sr_report.cu): count pass + scan into a scratch of
 // report_scratch_words(n_reads) words, then the write pass
 uint64_t report_scratch_words(uint32_t n_reads);

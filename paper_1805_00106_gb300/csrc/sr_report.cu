@@ -186,6 +186,15 @@ __global__ void k_scan_c(uint32_t* out, uint32_t n, const uint32_t* sums) {
 
 }  // namespace
 
+int launch_scan_u32(const uint32_t* in, uint32_t n, uint32_t* out, uint32_t* sums, cudaStream_t st) {
+  const uint32_t nb = (n + kScanBlock - 1) / kScanBlock;
+  if (nb == 0) return cudaMemsetAsync(out, 0, 4, st) == cudaSuccess ? 0 : -1;
+  k_scan_a<<<nb, kScanBlock, 0, st>>>(in, n, out, sums);
+  k_scan_b<<<1, kScanBlock, 0, st>>>(sums, nb, out + n);
+  k_scan_c<<<(n + 255) / 256, 256, 0, st>>>(out, n, sums);
+  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
+}
+
 // scratch: count n, offsets n + 1, sums n / 1024 + 1, one truncation counter
 uint64_t report_scratch_words(uint32_t n_reads) {
   return 2ull * n_reads + 1 + n_reads / kScanBlock + 1 + 1;
@@ -207,15 +216,9 @@ int launch_report_count(const BatchDev& b, int n_refs, int kind, uint32_t n_best
   const uint64_t need = (static_cast<uint64_t>(n) + kRepWarps - 1) / kRepWarps;
   const uint32_t grid = static_cast<uint32_t>(need < static_cast<uint64_t>(nsm) * 16 ? (need ? need : 1) : nsm * 16);
   k_report<<<grid, 32 * kRepWarps, 0, st>>>(a);
-  const uint32_t nb = (n + kScanBlock - 1) / kScanBlock;
-  if (nb) {
-    k_scan_a<<<nb, kScanBlock, 0, st>>>(count, n, offsets, sums);
-    k_scan_b<<<1, kScanBlock, 0, st>>>(sums, nb, offsets + n);
-    k_scan_c<<<(n + 255) / 256, 256, 0, st>>>(offsets, n, sums);
-  } else {
-    if (cudaMemsetAsync(offsets, 0, 4, st) != cudaSuccess) return -1;
-  }
-  return cudaPeekAtLastError() == cudaSuccess ? (nb ? 4 : 1) : -1;
+  const int t = launch_scan_u32(count, n, offsets, sums, st);
+  if (t < 0) return -1;
+  return cudaPeekAtLastError() == cudaSuccess ? 1 + t : -1;
 }
 
 int launch_report_write(const BatchDev& b, int n_refs, int kind, uint32_t n_best, const uint32_t* scratch,

@@ -90,6 +90,9 @@ struct sr_session {
   // the handle plus one per live batch: a batch keeps its session alive, so the
   // two may be released in either order
   std::atomic<int> live{1};
+  // device copy of the references' indexes (sr_session_attach_index)
+  DevIndex didx{};
+  std::vector<void*> idx_bufs;
   // the arena of the last freed batch, kept for the next one (not counted in hbm_used)
   std::mutex spare_mu;
   void* spare = nullptr;
@@ -233,6 +236,7 @@ extern "C" sr_status sr_session_open_seqs(const char* const* seqs, const uint64_
 static void session_release(sr_session* s) {
   if (s->live.fetch_sub(1) != 1) return;
   for (auto* w : s->d_words) cudaFree(w);
+  for (auto* p : s->idx_bufs) cudaFree(p);
   if (s->spare) cudaFree(s->spare);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -890,6 +894,220 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
     return cuda_error("sr_batch_fetch copy", e);
   }
   *out = r;
+  return SR_OK;
+}
+
+// ------------------------------------------------------------------ device CAL finder
+extern "C" sr_status sr_session_attach_index(sr_session* s, const sr_index* const* idx, uint32_t n_refs) {
+  if (!s || !idx || n_refs != s->n_refs || n_refs == 0)
+    return set_error(SR_EINVAL, "sr_session_attach_index: one index per session reference");
+  std::vector<IndexTables> t(n_refs);
+  for (uint32_t r = 0; r < n_refs; ++r) {
+    if (!idx[r]) return set_error(SR_EINVAL, "sr_session_attach_index: null index");
+    t[r] = index_tables(idx[r]);
+    if (t[r].ref_len != s->lens[r])
+      return set_error(SR_EINVAL, "sr_session_attach_index: index %u is of another reference", r);
+    if (t[r].seed_len != t[0].seed_len || t[r].address_bases != t[0].address_bases)
+      return set_error(SR_EINVAL, "sr_session_attach_index: indexes differ in seed layout");
+  }
+  for (auto* p : s->idx_bufs) cudaFree(p);
+  s->idx_bufs.clear();
+  s->didx = DevIndex{};
+  auto up = [&](const void* src, uint64_t bytes, void** dst) -> bool {
+    void* d = nullptr;
+    if (cudaMalloc(&d, bytes ? bytes : 1) != cudaSuccess) return false;
+    s->idx_bufs.push_back(d);
+    if (bytes && cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    *dst = d;
+    return true;
+  };
+  for (uint32_t r = 0; r < n_refs; ++r) {
+    void *pp, *pk, *ps, *po;
+    if (!up(t[r].ptr, t[r].n_ptr * 8, &pp) || !up(t[r].key, t[r].n_entries * 4, &pk) ||
+        !up(t[r].pos, t[r].n_entries * 4, &ps) || !up(t[r].orient, t[r].n_entries, &po)) {
+      for (auto* p : s->idx_bufs) cudaFree(p);
+      s->idx_bufs.clear();
+      s->didx = DevIndex{};
+      cudaGetLastError();
+      return set_error(SR_ENOMEM, "sr_session_attach_index: device upload failed");
+    }
+    s->didx.ptr[r] = static_cast<const uint64_t*>(pp);
+    s->didx.key[r] = static_cast<const uint32_t*>(pk);
+    s->didx.pos[r] = static_cast<const uint32_t*>(ps);
+    s->didx.orient[r] = static_cast<const uint8_t*>(po);
+    s->didx.ref_len[r] = t[r].ref_len;
+    s->didx.hash_seed[r] = t[r].hash_seed;
+  }
+  s->didx.n_refs = static_cast<int>(n_refs);
+  s->didx.k = static_cast<int>(t[0].seed_len);
+  s->didx.a = static_cast<int>(t[0].address_bases);
+  return SR_OK;
+}
+
+extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, const sr_cand_params* params,
+                                          sr_cand_list** out) {
+  if (!s || !reads || !out) return set_error(SR_EINVAL, "sr_candidates_device: null argument");
+  *out = nullptr;
+  if (s->didx.n_refs == 0) return set_error(SR_EINVAL, "sr_candidates_device: no index attached to the session");
+  sr_cand_params cp{};
+  if (params) cp = *params;
+  if (!cp.seed_stride) cp.seed_stride = 1;
+  const uint32_t n = reads->n_reads;
+  if (n && (!reads->bases || !reads->offsets)) return set_error(SR_EINVAL, "sr_candidates_device: null reads");
+  if (n && reads->offsets[0] != 0) return set_error(SR_EINVAL, "sr_candidates_device: offsets must start at 0");
+  for (uint32_t r = 0; r < n; ++r) {
+    if (reads->offsets[r + 1] < reads->offsets[r])
+      return set_error(SR_EINVAL, "sr_candidates_device: decreasing read offsets");
+    if (reads->offsets[r + 1] - reads->offsets[r] > SR_MAX_READ_LEN)
+      return set_error(SR_EINVAL, "sr_candidates_device: read %u longer than %u bases", r, SR_MAX_READ_LEN);
+  }
+  std::vector<uint64_t> offsets(n + 1ull, 0);
+  std::vector<uint8_t> o_ref, o_strand;
+  std::vector<uint64_t> o_start;
+  std::vector<uint32_t> o_len, o_hits;
+  if (n) {
+    cudaStream_t st = s->stream;
+    const uint64_t nb = reads->offsets[n];
+    std::vector<void*> bufs;
+    cudaError_t e = cudaSuccess;
+    auto dalloc = [&](uint64_t bytes) -> void* {
+      void* d = nullptr;
+      if (e == cudaSuccess) e = cudaMalloc(&d, bytes ? bytes : 1);
+      if (e == cudaSuccess) bufs.push_back(d);
+      return e == cudaSuccess ? d : nullptr;
+    };
+    auto done = [&](sr_status stt, const char* msg) -> sr_status {
+      cudaStreamSynchronize(st);
+      for (auto* p : bufs) cudaFree(p);
+      cudaGetLastError();
+      if (stt == SR_OK) return static_cast<sr_status>(SR_OK);
+      if (stt == SR_ECUDA) return cuda_error(msg, e == cudaSuccess ? cudaErrorUnknown : e);
+      return set_error(stt, "%s", msg);
+    };
+    char* d_bases = static_cast<char*>(dalloc(nb));
+    uint64_t* d_roff = static_cast<uint64_t*>(dalloc((n + 1ull) * 8));
+    uint32_t* d_count = static_cast<uint32_t*>(dalloc(n * 4ull));
+    uint32_t* d_status = static_cast<uint32_t*>(dalloc(4));
+    if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+    if (nb) e = cudaMemcpyAsync(d_bases, reads->bases, nb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_roff, reads->offsets, (n + 1ull) * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 4, st);
+    if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
+    if (launch_cal_seeds(s->didx, d_bases, d_roff, 0, n, cp.seed_stride, d_count, nullptr, nullptr, d_status, st) < 0) {
+      e = cudaGetLastError();
+      return done(SR_ECUDA, "sr_candidates_device count");
+    }
+    std::vector<uint32_t> count(n);
+    uint32_t status = 0;
+    e = cudaMemcpyAsync(count.data(), d_count, n * 4ull, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device count copy");
+    if (status & kStBadBase) return done(SR_EBADBASE, "sr_candidates_device: read has a non-ACGT base");
+    // chunks of reads whose CALs fit the buffers
+    uint64_t cap = 16ull << 20;
+    for (uint32_t r = 0; r < n; ++r) cap = std::max<uint64_t>(cap, count[r]);
+    uint64_t* d_cals = static_cast<uint64_t*>(dalloc(cap * 8));
+    uint64_t* d_wkey = static_cast<uint64_t*>(dalloc(cap * 8));
+    uint32_t* d_whits = static_cast<uint32_t*>(dalloc(cap * 4));
+    uint32_t* d_wlen = static_cast<uint32_t*>(dalloc(cap * 4));
+    uint8_t* d_oref = static_cast<uint8_t*>(dalloc(cap));
+    uint8_t* d_ostr = static_cast<uint8_t*>(dalloc(cap));
+    uint64_t* d_ostart = static_cast<uint64_t*>(dalloc(cap * 8));
+    uint32_t* d_olen = static_cast<uint32_t*>(dalloc(cap * 4));
+    uint32_t* d_ohits = static_cast<uint32_t*>(dalloc(cap * 4));
+    uint64_t* d_off = static_cast<uint64_t*>(dalloc(n * 8ull));
+    uint32_t* d_nwin = static_cast<uint32_t*>(dalloc(n * 4ull));
+    uint32_t* d_woff = static_cast<uint32_t*>(dalloc((n + 1ull) * 4));
+    uint32_t* d_sums = static_cast<uint32_t*>(dalloc((n / 1024 + 2ull) * 4));
+    if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+    uint64_t* d_scratch = nullptr;
+    uint64_t scratch_keys = 0;
+    std::vector<uint64_t> off(n);
+    std::vector<uint32_t> big, woff;
+    uint64_t total_w = 0;
+    for (uint32_t r0 = 0; r0 < n;) {
+      uint32_t r1 = r0;
+      uint64_t used = 0;
+      uint32_t max_small = 1;
+      uint64_t max_big = 0;
+      big.clear();
+      while (r1 < n && used + count[r1] <= cap) {
+        off[r1 - r0] = used;
+        used += count[r1];
+        if (count[r1] > kCalSmemKeys) {
+          big.push_back(r1 - r0);
+          max_big = std::max<uint64_t>(max_big, count[r1]);
+        } else {
+          max_small = std::max(max_small, count[r1]);
+        }
+        ++r1;
+      }
+      const uint32_t nr = r1 - r0;
+      if (max_big) {
+        uint64_t p2 = 1;
+        while (p2 < max_big) p2 <<= 1;
+        if (p2 > scratch_keys) {
+          e = cudaMalloc(&d_scratch, p2 * 8);
+          if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+          bufs.push_back(d_scratch);
+          scratch_keys = p2;
+        }
+      }
+      e = cudaMemcpyAsync(d_off, off.data(), nr * 8ull, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
+      if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_status, st) < 0 ||
+          launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_off, d_cals,
+                            max_small, big.data(), static_cast<uint32_t>(big.size()), d_scratch, d_nwin, d_wkey,
+                            d_whits, d_wlen, st) < 0 ||
+          launch_scan_u32(d_nwin, nr, d_woff, d_sums, st) < 0) {
+        e = cudaGetLastError();
+        return done(SR_ECUDA, "sr_candidates_device filter");
+      }
+      woff.resize(nr + 1ull);
+      e = cudaMemcpyAsync(woff.data(), d_woff, (nr + 1ull) * 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window count");
+      const uint64_t nw = woff[nr];
+      if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, d_oref, d_ostr, d_ostart, d_olen,
+                             d_ohits, st) < 0) {
+        e = cudaGetLastError();
+        return done(SR_ECUDA, "sr_candidates_device compact");
+      }
+      o_ref.resize(total_w + nw);
+      o_strand.resize(total_w + nw);
+      o_start.resize(total_w + nw);
+      o_len.resize(total_w + nw);
+      o_hits.resize(total_w + nw);
+      if (nw) {
+        e = cudaMemcpyAsync(o_ref.data() + total_w, d_oref, nw, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(o_strand.data() + total_w, d_ostr, nw, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(o_start.data() + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(o_len.data() + total_w, d_olen, nw * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(o_hits.data() + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
+      }
+      for (uint32_t i = 0; i <= nr; ++i) offsets[r0 + i] = total_w + woff[i];
+      total_w += nw;
+      r0 = r1;
+    }
+    sr_status stt = done(SR_OK, "");
+    if (stt != SR_OK) return stt;
+  }
+  const uint64_t total = offsets[n];
+  sr_cand_list* l = nullptr;
+  sr_status st2 = sr_cand_list_alloc(n, total, &l);
+  if (st2 != SR_OK) return st2;
+  std::memcpy(l->offsets, offsets.data(), (n + 1ull) * 8);
+  if (total) {
+    std::memcpy(l->ref_id, o_ref.data(), total);
+    std::memcpy(l->strand, o_strand.data(), total);
+    std::memcpy(l->win_start, o_start.data(), total * 8);
+    std::memcpy(l->win_len, o_len.data(), total * 4);
+    std::memcpy(l->hits, o_hits.data(), total * 4);
+  }
+  *out = l;
   return SR_OK;
 }
 

@@ -127,6 +127,9 @@ def lib():
                                C.POINTER(C.POINTER(CandList))], C.c_int32),
             "sr_cand_list_alloc": ([C.c_uint32, C.c_uint64, C.POINTER(C.POINTER(CandList))], C.c_int32),
             "sr_cand_list_free": ([C.POINTER(CandList)], None),
+            "sr_session_attach_index": ([P, P, C.c_uint32], C.c_int32),
+            "sr_candidates_device": ([P, C.POINTER(Reads), C.POINTER(CandParams),
+                                      C.POINTER(C.POINTER(CandList))], C.c_int32),
             "sr_session_open": ([P, C.c_uint32, C.c_uint64, C.POINTER(P)], C.c_int32),
             "sr_session_open_seqs": ([P, P, C.c_uint32, C.c_uint64, C.POINTER(P)], C.c_int32),
             "sr_session_close": ([P], None),
@@ -308,6 +311,10 @@ def candidates(indexes, bases, read_off, seed_stride=1, merge_dist=32, pad=32, m
     cp = CandParams(seed_stride, merge_dist, pad, max_cands, threads)
     out = C.POINTER(CandList)()
     _check(lib().sr_candidates(C.cast(arr, P), len(indexes), C.byref(reads), C.byref(cp), C.byref(out)))
+    return _cand_list_to_numpy(out)
+
+
+def _cand_list_to_numpy(out):
     l = out.contents
     n, nc = l.n_reads, l.n_cands
 
@@ -432,6 +439,19 @@ class Session:
         _check(lib().sr_align_batch(self.h, C.byref(reads), C.byref(cands), C.byref(sp or score_params()),
                                     C.byref(opts or align_opts()), C.byref(out)))
         return results_to_numpy(out)
+
+    # device CAL finder (Sec. 3.2-3.3 on the GPU)
+    def attach_index(self, indexes):
+        arr = (P * len(indexes))(*[ix.h for ix in indexes])
+        _check(lib().sr_session_attach_index(self.h, C.cast(arr, P), len(indexes)))
+
+    def candidates(self, bases, read_off, seed_stride=1, merge_dist=32, pad=32, max_cands=0):
+        keep = _Keep()
+        reads = make_reads(bases, read_off, keep)
+        cp = CandParams(seed_stride, merge_dist, pad, max_cands, 0)
+        out = C.POINTER(CandList)()
+        _check(lib().sr_candidates_device(self.h, C.byref(reads), C.byref(cp), C.byref(out)))
+        return _cand_list_to_numpy(out)
 
     # serving
     def serve_start(self, sp=None, opts=None, max_inflight=0):

@@ -1,0 +1,111 @@
+"""Device CAL finder + filter (Sec. 3.2-3.3 on the GPU) vs the host stage,
+which is itself pinned to the brute-force finder of the oracle: same windows,
+same order, same hit counts, bit-exact (-m gpu)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1805_00106_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ["cand_off", "c_ref", "c_strand", "c_start", "c_len", "c_hits"]
+
+
+@pytest.fixture(scope="module")
+def sr():
+    from paper_1805_00106_gb300 import sr as _sr
+    _sr.lib()
+    return _sr
+
+
+def _same(a, b):
+    for k in KEYS:
+        assert np.array_equal(np.asarray(a[k], np.int64), np.asarray(b[k], np.int64)), k
+
+
+@pytest.mark.parametrize("k,addr,cal_limit", [(20, 10, 1024), (22, 11, 0), (16, 8, 64)])
+def test_device_matches_host_xenograft(sr, k, addr, cal_limit):
+    w = S.workload("c3", scale=0.002, seed=17)
+    idx = [sr.Index.build(bytes(r), seed_len=k, address_bases=addr, cal_limit=cal_limit) for r in w["refs"]]
+    s = sr.Session.from_indexes(idx)
+    s.attach_index(idx)
+    for prm in [dict(seed_stride=1, merge_dist=32, pad=32), dict(seed_stride=k, merge_dist=32, pad=16),
+                dict(seed_stride=3, merge_dist=0, pad=0), dict(seed_stride=1, merge_dist=32, pad=32, max_cands=3),
+                dict(seed_stride=1, merge_dist=200, pad=64, max_cands=1)]:
+        h = sr.candidates(idx, w["bases"], w["read_off"], **prm)
+        d = s.candidates(w["bases"], w["read_off"], **prm)
+        _same(d, h)
+
+
+def test_device_matches_bruteforce_oracle(sr):
+    rng = np.random.default_rng(3)
+    ref = rng.choice(np.frombuffer(b"ACGT", np.uint8), 3000)
+    reads, offs = [], [0]
+    for m in [15, 20, 21, 40, 77, 100, 150, 256]:
+        p = int(rng.integers(0, 3000 - m))
+        r = ref[p:p + m].copy()
+        if rng.random() < 0.5:
+            r = np.frombuffer(bytes(r)[::-1].translate(bytes.maketrans(b"ACGT", b"TGCA")), np.uint8)
+        reads.append(r)
+        offs.append(offs[-1] + m)
+    bases = np.concatenate(reads)
+    idx = [sr.Index.build(bytes(ref), seed_len=20, address_bases=10)]
+    s = sr.Session.from_indexes(idx)
+    s.attach_index(idx)
+    d = s.candidates(bases, np.array(offs), seed_stride=1, merge_dist=32, pad=32)
+    codes = [O.encode(bytes(ref))]
+    for i in range(len(reads)):
+        e_ref, e_str, e_st, e_len, e_hits = O.candidates(codes, O.encode(bytes(reads[i])), k=20, stride=1,
+                                                        merge_dist=32, pad=32, with_hits=True)
+        c0, c1 = int(d["cand_off"][i]), int(d["cand_off"][i + 1])
+        got = list(zip(d["c_ref"][c0:c1].tolist(), d["c_strand"][c0:c1].tolist(), d["c_start"][c0:c1].tolist(),
+                       d["c_len"][c0:c1].tolist(), d["c_hits"][c0:c1].tolist()))
+        assert got == list(zip(e_ref.tolist(), e_str.tolist(), e_st.tolist(), e_len.tolist(), e_hits.tolist()))
+
+
+def test_reads_with_very_many_cals(sr):
+    """A tandem repeat gives reads tens of thousands of CALs: the large-read
+    filter (global-memory sort) must agree with the host too."""
+    rng = np.random.default_rng(11)
+    unit = rng.choice(np.frombuffer(b"ACGT", np.uint8), 23)
+    ref = np.concatenate([rng.choice(np.frombuffer(b"ACGT", np.uint8), 2000), np.tile(unit, 900),
+                          rng.choice(np.frombuffer(b"ACGT", np.uint8), 2000)])
+    reads, offs = [], [0]
+    for st, m in [(2500, 200), (3000, 256), (100, 100), (2100, 60), (20000, 120)]:
+        reads.append(ref[st:st + m])
+        offs.append(offs[-1] + m)
+    bases = np.concatenate(reads)
+    idx = [sr.Index.build(bytes(ref), seed_len=20, address_bases=10, cal_limit=0)]
+    s = sr.Session.from_indexes(idx)
+    s.attach_index(idx)
+    for prm in [dict(merge_dist=0, pad=8), dict(merge_dist=32, pad=32), dict(merge_dist=5, pad=0, max_cands=7)]:
+        h = sr.candidates(idx, bases, np.array(offs), **prm)
+        d = s.candidates(bases, np.array(offs), **prm)
+        _same(d, h)
+        if prm["merge_dist"] == 0:
+            # one window per repeat copy: ~900 windows from ~200k CALs (the large-read path)
+            assert int(np.max(np.diff(h["cand_off"]))) > 500
+            assert int(np.max(h["c_hits"])) > 100
+
+
+def test_device_candidates_errors_and_empty(sr):
+    w = S.workload("c3", scale=0.0008, seed=5)
+    idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=10) for r in w["refs"]]
+    s = sr.Session.from_indexes(idx)
+    with pytest.raises(sr.SrError) as e:
+        s.candidates(w["bases"], w["read_off"])  # no index attached
+    assert e.value.status == sr.SR_EINVAL
+    s.attach_index(idx)
+    bad = w["bases"].copy()
+    bad[7] = ord("N")
+    with pytest.raises(sr.SrError) as e:
+        s.candidates(bad, w["read_off"])
+    assert e.value.status == sr.SR_EBADBASE
+    long = np.concatenate([w["bases"], np.full(300, ord("A"), np.uint8)])
+    lo = np.concatenate([w["read_off"], [w["read_off"][-1] + 300]])
+    with pytest.raises(sr.SrError) as e:
+        s.candidates(long, lo)
+    assert e.value.status == sr.SR_EINVAL
+    d = s.candidates(np.zeros(0, np.uint8), np.zeros(1, np.int64))
+    assert len(d["cand_off"]) == 1 and len(d["c_ref"]) == 0

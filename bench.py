@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default bins)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving latency run")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="duration of each offered load")
+    ap.add_argument("--no-cal", action="store_true", help="skip the CAL finder comparison")
+    ap.add_argument("--sweep", action="store_true",
+                    help="seed length x CAL limit sweep on the xenograft and repeat-heavy workloads "
+                         "(one JSON line per setting) instead of the bench line")
+    ap.add_argument("--sweep-scale", type=float, default=0.25)
     return ap.parse_args()
 
 
@@ -251,6 +256,84 @@ def serving_bench(sr, scale, seconds=4.0, pool_size=48, seed=404):
     return out
 
 
+def cal_finder_bench(sr, scale):
+    """Host CAL finder (16 threads) vs the device one on the xenograft reads: reads/s,
+    windows, and that both give the same list."""
+    from paper_1805_00106_gb300 import synth
+    w = synth.workload("c3", scale=0.25 * scale, seed=7)
+    n = len(w["read_off"]) - 1
+    t0 = time.perf_counter()
+    idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=12, cal_limit=1024) for r in w["refs"]]
+    t_index = time.perf_counter() - t0
+    sess = sr.Session.from_indexes(idx)
+    sess.attach_index(idx)
+    prm = dict(seed_stride=1, merge_dist=32, pad=32)
+    t0 = time.perf_counter()
+    h = sr.candidates(idx, w["bases"], w["read_off"], **prm)
+    t_host = time.perf_counter() - t0
+    dt = []
+    d = None
+    for _ in range(3):
+        t0 = time.perf_counter()
+        d = sess.candidates(w["bases"], w["read_off"], **prm)
+        dt.append(time.perf_counter() - t0)
+    same = all(np.array_equal(np.asarray(h[k], np.int64), np.asarray(d[k], np.int64))
+               for k in ["cand_off", "c_ref", "c_strand", "c_start", "c_len", "c_hits"])
+    t_dev = statistics.median(dt)
+    return {"workload": f"xenograft pair {len(w['refs'][0]) / 1e6:.0f} Mbp each, {n} reads x 100 bp, k = 20, "
+                        "overlapping seeds, cal_limit 1024, merge 32, pad 32",
+            "host_reads_per_s": round(n / t_host, 1), "host_threads": os.cpu_count(),
+            "device_reads_per_s": round(n / t_dev, 1), "device_ms": round(1e3 * t_dev, 2),
+            "windows_per_read": round(len(d["c_ref"]) / max(n, 1), 3), "identical": bool(same),
+            "index_build_s": round(t_index, 2)}
+
+
+def sweep(args):
+    """The paper's seed length x CAL limit study (Table 5) on synthetic stand-ins:
+    per setting, windows (CALs after the filter) per read, end-to-end reads/s of
+    device candidates + sr_align_batch, and accuracy against the simulated truth
+    (xenograft: class of the source reference; repeat-heavy: winner ends at the
+    true locus)."""
+    from paper_1805_00106_gb300 import sr, synth
+    spp = sr.score_params(*SP)
+    for name in ["c3", "c5"]:
+        w = synth.workload(name, scale=args.sweep_scale, seed=11)
+        n = len(w["read_off"]) - 1
+        truth_end = np.asarray(w["t_pos"], np.int64) + np.asarray(w["t_span"], np.int64) - 1
+        for k in (20, 25):
+            for limit in (0, 1024, 128):
+                idx = [sr.Index.build(bytes(r), seed_len=k, address_bases=12, cal_limit=limit) for r in w["refs"]]
+                sess = sr.Session.from_indexes(idx)
+                sess.attach_index(idx)
+                opts = sr.align_opts(classify=name == "c3", min_score=40, margin=5)
+                ts = []
+                for _ in range(2):
+                    t0 = time.perf_counter()
+                    cd = sess.candidates(w["bases"], w["read_off"], seed_stride=1, merge_dist=32, pad=32)
+                    res = sess.align(w["bases"], w["read_off"], cd["cand_off"], cd["c_ref"], cd["c_strand"],
+                                     cd["c_start"], cd["c_len"], spp, opts)
+                    ts.append(time.perf_counter() - t0)
+                t = min(ts)
+                line = {"sweep": "seed length x CAL limit (Table 5 analogue)", "workload": name,
+                        "reads": n, "ref_mbp": [round(len(r) / 1e6, 1) for r in w["refs"]],
+                        "seed_len": k, "cal_limit": limit or "inf",
+                        "windows_per_read": round(len(cd["c_ref"]) / n, 3),
+                        "reads_per_s": round(n / t, 1), "ms": round(1e3 * t, 2)}
+                if name == "c3":
+                    cls = res["read_class"]
+                    exp = np.where(np.asarray(w["t_ref"]) == 0, 1, 2)
+                    line.update(correct=round(float(np.mean(cls == exp)), 4),
+                                ambiguous=round(float(np.mean(cls == 3)), 4),
+                                unaligned=round(float(np.mean(cls == 0)), 4))
+                else:
+                    b = res["best"]
+                    ok = (b["item"] >= 0) & (np.abs(b["ref_end"].astype(np.int64) - truth_end) <= 20)
+                    line.update(mapped_at_truth=round(float(np.mean(ok)), 4),
+                                unaligned=round(float(np.mean(b["item"] < 0)), 4))
+                print(json.dumps(line), flush=True)
+                del sess, idx
+
+
 def make_workload(scale, rank):
     from paper_1805_00106_gb300 import synth
     return synth.workload("c2", scale=scale, seed=rank * 1009)
@@ -294,6 +377,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        sweep(args)
         return
     import torch
     from paper_1805_00106_gb300 import sr
@@ -423,6 +509,8 @@ def main():
                        "reads_per_s": round(n_reads / e2e_t, 1)}
     if rank == 0 and not args.no_serve:
         line["serving"] = serving_bench(sr, args.scale, args.serve_seconds)
+    if rank == 0 and not args.no_cal:
+        line["cal_finder"] = cal_finder_bench(sr, args.scale)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(w, args.cpu_seconds).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}

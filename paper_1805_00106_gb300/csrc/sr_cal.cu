@@ -100,8 +100,13 @@ template <bool EMIT>
 __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
   __shared__ uint8_t qs[kCalWarps][kMaxReadLen];
   __shared__ uint32_t ctr[kCalWarps];
+  __shared__ uint32_t incl_s[kCalWarps][32];  // inclusive scan of the lanes' entry counts
+  __shared__ uint64_t lo_s[kCalWarps][32];     // each lane's first matching entry
+  __shared__ uint32_t o_s[kCalWarps][32];      // its seed offset and orientation bits
+  __shared__ uint32_t ro_s[kCalWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* q = qs[warp];
+  uint32_t* incl = incl_s[warp];
   const int k = a.di.k;
   for (uint32_t rr = blockIdx.x * kCalWarps + warp; rr < a.nr; rr += gridDim.x * kCalWarps) {
     const uint32_t r = a.r0 + rr;
@@ -112,27 +117,58 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
     uint32_t n = 0;
     if (load_codes(a.bases, o0, m, q, lane, a.status) && m >= static_cast<uint32_t>(k)) {
       const uint64_t base = EMIT ? a.off[rr] : 0;
-      for (uint32_t o = lane * a.stride; o + k <= m; o += 32 * a.stride) {
+      // 32 seeds per round, one per lane; the matching entries of all of them
+      // are then shared out over the warp (a repeat seed may have thousands)
+      for (uint32_t o_base = 0; o_base + k <= m; o_base += 32 * a.stride) {
+        const uint32_t o = o_base + lane * a.stride;
+        const bool live = o + k <= m;
         Kmer km;
-        for (int t = 0; t < k; ++t) kmer_push(km, q[o + t], k);
+        if (live)
+          for (int t = 0; t < k; ++t) kmer_push(km, q[o + t], k);
         const uint64_t canon = km.fwd < km.rc ? km.fwd : km.rc;
         const uint32_t rori = (km.fwd == canon ? 1u : 0u) | (km.rc == canon ? 2u : 0u);
         for (int r2 = 0; r2 < a.di.n_refs; ++r2) {
-          uint64_t lo, hi;
-          lookup(a.di, r2, canon, &lo, &hi);
-          for (uint64_t e = lo; e < hi; ++e) {
+          uint64_t lo = 0, hi = 0;
+          if (live) lookup(a.di, r2, canon, &lo, &hi);
+          uint32_t cnt = static_cast<uint32_t>(hi - lo), sc = cnt;
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t x = __shfl_up_sync(FULL, sc, off);
+            if (lane >= off) sc += x;
+          }
+          const uint32_t total = __shfl_sync(FULL, sc, 31);
+          if (total == 0) continue;
+          // owner values (shared memory: lanes that finish early still serve them)
+          incl[lane] = sc;
+          lo_s[warp][lane] = lo;
+          o_s[warp][lane] = o;
+          ro_s[warp][lane] = rori;
+          __syncwarp();
+          // entry j belongs to the first lane whose inclusive count exceeds j
+          for (uint32_t j = lane; j < total; j += 32) {
+            int lo_l = 0, hi_l = 31;
+            while (lo_l < hi_l) {
+              const int mid = (lo_l + hi_l) >> 1;
+              if (incl[mid] > j) hi_l = mid;
+              else lo_l = mid + 1;
+            }
+            const int own = lo_l;
+            const uint32_t before = own ? incl[own - 1] : 0u;
+            const uint64_t e = lo_s[warp][own] + (j - before);
+            const uint32_t so = o_s[warp][own], sro = ro_s[warp][own];
             const uint32_t fo = a.di.orient[r2][e];
-            const bool plus = ((fo & 1u) && (rori & 1u)) || ((fo & 2u) && (rori & 2u));
-            const bool minus = ((fo & 1u) && (rori & 2u)) || ((fo & 2u) && (rori & 1u));
+            const bool plus = ((fo & 1u) && (sro & 1u)) || ((fo & 2u) && (sro & 2u));
+            const bool minus = ((fo & 1u) && (sro & 2u)) || ((fo & 2u) && (sro & 1u));
             if (EMIT) {
               const int64_t p = a.di.pos[r2][e];
-              if (plus) a.cals[base + atomicAdd(&ctr[warp], 1u)] = cal_key(r2, 0, p - o);
+              if (plus) a.cals[base + atomicAdd(&ctr[warp], 1u)] = cal_key(r2, 0, p - so);
               if (minus) a.cals[base + atomicAdd(&ctr[warp], 1u)] =
-                  cal_key(r2, 1, p - static_cast<int64_t>(m - o - k));
+                  cal_key(r2, 1, p - static_cast<int64_t>(m - so - k));
             } else {
               n += (plus ? 1u : 0u) + (minus ? 1u : 0u);
             }
           }
+          __syncwarp();
         }
       }
     }
@@ -259,18 +295,21 @@ __device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, ui
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(128) k_cal_filter(FilterArgs a) {
+// reads with lo <= count <= hi, keys in shared memory
+__global__ void __launch_bounds__(256) k_cal_filter(FilterArgs a, uint32_t lo, uint32_t hi) {
   extern __shared__ uint64_t skeys[];
   for (uint32_t rr = blockIdx.x; rr < a.nr; rr += gridDim.x) {
     const uint32_t n = a.count[rr];
-    if (n > a.smem_cap) continue;  // large-read kernel
+    if (n < lo || n > hi) continue;
     filter_read(a, rr, skeys, n);
   }
 }
 
-// one block per large read, keys in a global scratch of pow2(n) slots
-__global__ void __launch_bounds__(1024) k_cal_filter_big(FilterArgs a, uint32_t rr, uint64_t* scratch) {
-  filter_read(a, rr, scratch, a.count[rr]);
+// one block per large read (big[b]), keys in a global scratch from slot soff[b]
+__global__ void __launch_bounds__(1024) k_cal_filter_big(FilterArgs a, const uint32_t* big, const uint64_t* soff,
+                                                         uint64_t* scratch) {
+  const uint32_t rr = big[blockIdx.x];
+  filter_read(a, rr, scratch + soff[blockIdx.x], a.count[rr]);
 }
 
 __global__ void k_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,
@@ -311,15 +350,12 @@ int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read
 
 int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
                       uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint64_t* off, uint64_t* cals,
-                      uint32_t max_small, const uint32_t* big, uint32_t n_big, uint64_t* scratch,
-                      uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen, cudaStream_t st) {
+                      uint32_t max_small, uint32_t max_mid, const uint32_t* big, const uint64_t* big_soff,
+                      uint32_t n_big, uint64_t* scratch, uint32_t* nwin, uint64_t* wkey, uint32_t* whits,
+                      uint32_t* wlen, cudaStream_t st) {
   if (nr == 0) return 0;
   FilterArgs a{di, read_off, r0, nr, merge_dist, pad, max_cands, count, off, cals, kCalSmemKeys,
                nwin, wkey, whits, wlen};
-  int launched = 0;
-  uint32_t P = 1;
-  while (P < max_small) P <<= 1;
-  const size_t smem = static_cast<size_t>(P) * sizeof(uint64_t);
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_cal_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -330,11 +366,27 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const uint32_t grid = nr < static_cast<uint32_t>(nsm) * 64 ? nr : static_cast<uint32_t>(nsm) * 64;
-  k_cal_filter<<<grid, 128, smem, st>>>(a);
-  ++launched;
-  for (uint32_t t = 0; t < n_big; ++t) {
-    k_cal_filter_big<<<1, 1024, 0, st>>>(a, big[t], scratch);
+  auto p2 = [](uint32_t n) {
+    uint32_t p = 1;
+    while (p < n) p <<= 1;
+    return p;
+  };
+  int launched = 0;
+  // small reads: 8 KB or less of keys per block, many blocks per SM
+  {
+    const size_t smem = static_cast<size_t>(p2(max_small)) * sizeof(uint64_t);
+    const uint32_t grid = nr < static_cast<uint32_t>(nsm) * 32 ? nr : static_cast<uint32_t>(nsm) * 32;
+    k_cal_filter<<<grid, 128, smem, st>>>(a, 0u, kCalSmallKeys);
+    ++launched;
+  }
+  if (max_mid) {
+    const size_t smem = static_cast<size_t>(p2(max_mid)) * sizeof(uint64_t);
+    const uint32_t grid = static_cast<uint32_t>(nsm) * 2;
+    k_cal_filter<<<grid, 256, smem, st>>>(a, kCalSmallKeys + 1, kCalSmemKeys);
+    ++launched;
+  }
+  if (n_big) {
+    k_cal_filter_big<<<n_big, 1024, 0, st>>>(a, big, big_soff, scratch);
     ++launched;
   }
   return cudaPeekAtLastError() == cudaSuccess ? launched : -1;

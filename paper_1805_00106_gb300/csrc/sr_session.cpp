@@ -1020,46 +1020,55 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     uint32_t* d_nwin = static_cast<uint32_t*>(dalloc(n * 4ull));
     uint32_t* d_woff = static_cast<uint32_t*>(dalloc((n + 1ull) * 4));
     uint32_t* d_sums = static_cast<uint32_t*>(dalloc((n / 1024 + 2ull) * 4));
+    uint32_t* d_big = static_cast<uint32_t*>(dalloc(n * 4ull));
+    uint64_t* d_bigoff = static_cast<uint64_t*>(dalloc(n * 8ull));
     if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
     uint64_t* d_scratch = nullptr;
     uint64_t scratch_keys = 0;
-    std::vector<uint64_t> off(n);
+    std::vector<uint64_t> off(n), bigoff;
     std::vector<uint32_t> big, woff;
     uint64_t total_w = 0;
     for (uint32_t r0 = 0; r0 < n;) {
       uint32_t r1 = r0;
       uint64_t used = 0;
-      uint32_t max_small = 1;
-      uint64_t max_big = 0;
+      uint32_t max_small = 1, max_mid = 0;
+      uint64_t big_keys = 0;
       big.clear();
+      bigoff.clear();
       while (r1 < n && used + count[r1] <= cap) {
         off[r1 - r0] = used;
         used += count[r1];
         if (count[r1] > kCalSmemKeys) {
+          uint64_t p2 = 1;
+          while (p2 < count[r1]) p2 <<= 1;
           big.push_back(r1 - r0);
-          max_big = std::max<uint64_t>(max_big, count[r1]);
+          bigoff.push_back(big_keys);
+          big_keys += p2;
+        } else if (count[r1] > kCalSmallKeys) {
+          max_mid = std::max(max_mid, count[r1]);
         } else {
           max_small = std::max(max_small, count[r1]);
         }
         ++r1;
       }
       const uint32_t nr = r1 - r0;
-      if (max_big) {
-        uint64_t p2 = 1;
-        while (p2 < max_big) p2 <<= 1;
-        if (p2 > scratch_keys) {
-          e = cudaMalloc(&d_scratch, p2 * 8);
-          if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-          bufs.push_back(d_scratch);
-          scratch_keys = p2;
-        }
+      if (big_keys > scratch_keys) {
+        e = cudaMalloc(&d_scratch, big_keys * 8);
+        if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+        bufs.push_back(d_scratch);
+        scratch_keys = big_keys;
       }
       e = cudaMemcpyAsync(d_off, off.data(), nr * 8ull, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess && !big.empty()) {
+        e = cudaMemcpyAsync(d_big, big.data(), big.size() * 4ull, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(d_bigoff, bigoff.data(), bigoff.size() * 8ull, cudaMemcpyHostToDevice, st);
+      }
       if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
       if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_status, st) < 0 ||
           launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_off, d_cals,
-                            max_small, big.data(), static_cast<uint32_t>(big.size()), d_scratch, d_nwin, d_wkey,
-                            d_whits, d_wlen, st) < 0 ||
+                            max_small, max_mid, d_big, d_bigoff, static_cast<uint32_t>(big.size()), d_scratch,
+                            d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
           launch_scan_u32(d_nwin, nr, d_woff, d_sums, st) < 0) {
         e = cudaGetLastError();
         return done(SR_ECUDA, "sr_candidates_device filter");

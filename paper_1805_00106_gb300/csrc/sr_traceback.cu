@@ -460,8 +460,8 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(max(stA, stB) + 1)));
     const int p = k & 1;
     struct Sub {
-      bool on, bd;       // lane inside the band; lane k + 1 outside it (top border)
-      int c, ihi, js;    // column = row + c
+      bool on, bd;          // lane inside the band; lane k + 1 outside it (top border)
+      int c, ilo, ihi, js;  // column = row + c; end rows searched in [ilo, ihi]
       int32_t S;
       const uint8_t* q;
       const uint8_t* r;
@@ -470,9 +470,9 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     {
       const TbRead& x0 = p ? rd[1] : rd[0];
       const TbRead& x1 = p ? rd[0] : rd[1];
-      s0 = Sub{x0.has && k < x0.w, k + 1 >= x0.w, x0.dlo + k, x0.ihi, static_cast<int>(x0.jstar), x0.S,
+      s0 = Sub{x0.has && k < x0.w, k + 1 >= x0.w, x0.dlo + k, x0.ilo, x0.ihi, static_cast<int>(x0.jstar), x0.S,
                p ? qB : qA, p ? rB : rA};
-      s1 = Sub{x1.has && k < x1.w, k + 1 >= x1.w, x1.dlo + k, x1.ihi, static_cast<int>(x1.jstar), x1.S,
+      s1 = Sub{x1.has && k < x1.w, k + 1 >= x1.w, x1.dlo + k, x1.ilo, x1.ihi, static_cast<int>(x1.jstar), x1.S,
                p ? qA : qB, p ? rA : rB};
     }
     // one cell of row i of a read: neighbours left (hl, el), above (hu, fu), diagonal hd
@@ -494,7 +494,8 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
           nH = H;
           nE = E;
           nF = F;
-          if (j == sb.js && H == sb.S) ic = min(ic, static_cast<uint32_t>(i));
+          // final-row mode ends in row m even where an earlier row also holds S
+          if (j == sb.js && H == sb.S && i >= sb.ilo) ic = min(ic, static_cast<uint32_t>(i));
         }
       }
     };

@@ -227,3 +227,37 @@ def test_repeated_runs_and_staged_batch_identical(sr):
     _check(outs[0], oracle_run(w))
     st = b.stats()
     assert st["kernels"] >= 8 and st["cells"] > 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tiny_random_reads_both_readouts(sr, mode):
+    """Short, low-complexity reads and windows with several scoring schemes: many
+    co-optimal cells (e.g. an earlier row holding the final row's best at the end
+    column) exercise the tie rules of the end cell and of the traceback."""
+    rng = np.random.default_rng(101 + mode)
+    L = 5000
+    ref = rng.choice(np.frombuffer(b"ACGT", np.uint8), L)
+    ref[1000:1600] = np.frombuffer(b"AC" * 300, np.uint8)
+    ref[2000:2600] = np.frombuffer(b"AAT" * 200, np.uint8)
+    reads, offs = [], [0]
+    cand = dict(cand_off=[0], c_ref=[], c_strand=[], c_start=[], c_len=[])
+    for k in range(1500):
+        m = int(rng.integers(1, 31))
+        src = int(rng.choice([rng.integers(0, L - 64), rng.integers(1000, 1540), rng.integers(2000, 2540)]))
+        r = ref[src:src + m].copy()
+        flips = rng.random(m) < 0.15
+        r[flips] = rng.choice(np.frombuffer(b"ACGT", np.uint8), int(flips.sum()))
+        reads.append(r)
+        offs.append(offs[-1] + m)
+        for _ in range(int(rng.integers(1, 4))):
+            n = int(rng.integers(1, 41))
+            st = int(min(max(0, src + int(rng.integers(-8, 9))), L - n))
+            cand["c_ref"].append(0); cand["c_strand"].append(int(rng.integers(0, 2)))
+            cand["c_start"].append(st); cand["c_len"].append(n)
+        cand["cand_off"].append(len(cand["c_ref"]))
+    w = dict(refs=[ref], bases=np.concatenate(reads), read_off=np.array(offs),
+             **{k: np.array(v) for k, v in cand.items()})
+    s = _session(sr, w)
+    for sp in [(2, 3, 5, 2), (3, 2, 2, 1), (1, 1, 1, 1), (2, 3, 0, 2)]:
+        o = oracle_run(w, sp=sp, mode=mode)
+        _check(gpu_run(s, w, sp=sp, mode=mode), o)

@@ -284,6 +284,30 @@ typedef struct {
 sr_status sr_batch_report(sr_session* s, sr_batch* b, uint32_t kind, uint32_t n_best, sr_report** out);
 void sr_report_free(sr_report* rep);
 
+/* SAM 1.6 text of a batch's results (the paper's host formats its output "into
+ * a standard format like SAM", Sec. 4.2).  Header: @HD, one @SQ per reference
+ * (ref_lens[n_refs]), @PG.  One line per read, in read order:
+ *   QNAME  read_names[r], or "r<index>"
+ *   FLAG   0, 16 for a '-' strand winner (SEQ is then the reverse complement), 4 unmapped
+ *   RNAME / POS  reference name (ref_names, or "ref<id>") and ref_start + 1
+ *   MAPQ   0 when n_ties > 1, else 60 * (score - second) / score (at most 60)
+ *   CIGAR  the winner's CIGAR (reference orientation, soft clips included)
+ *   RNEXT PNEXT TLEN QUAL  * 0 0 *
+ *   tags   AS:i score, XS:i second, X0:i n_ties; YC:Z class (UN/A/B/AMB) when the
+ *          results carry classes; XA:Z ref,+end,score; (or -end for '-' strand)
+ *          for every other window of `secondary` (an SR_REPORT_* report of the
+ *          same batch; end is the 1-based last reference base; the secondary
+ *          alignments carry no CIGAR).
+ * Host code (parallel formatting).  Errors: SR_EINVAL (inconsistent inputs),
+ * SR_EIO (file). */
+typedef struct {
+  const char* const* read_names;  /* n_reads names or NULL */
+  const char* const* ref_names;   /* n_refs names or NULL */
+  const sr_report* secondary;     /* or NULL */
+} sr_sam_opts;
+sr_status sr_write_sam(const sr_reads* reads, const sr_results* res, const uint64_t* ref_lens,
+                       const sr_sam_opts* opts, const char* path);
+
 /* Device time of the last run of a batch, from CUDA events recorded on the
  * launching stream (inside the replayed graph): the whole path, the extension
  * kernels alone, the traceback + CIGAR kernels.  Call after sr_batch_sync /

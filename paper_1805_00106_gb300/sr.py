@@ -105,6 +105,10 @@ class Report(C.Structure):
 
 
 REPORT_HIT_DTYPE = _np_dtype(ReportHit)
+
+
+class SamOpts(C.Structure):
+    _fields_ = [("read_names", P), ("ref_names", P), ("secondary", C.POINTER(Report))]
 REPORT_BEST_N, REPORT_TIED, REPORT_MAX = 1, 2, 256
 
 
@@ -147,6 +151,7 @@ def lib():
             "sr_classify": ([P, P, P, P], C.c_int32),
             "sr_batch_report": ([P, P, C.c_uint32, C.c_uint32, C.POINTER(C.POINTER(Report))], C.c_int32),
             "sr_report_free": ([C.POINTER(Report)], None),
+            "sr_write_sam": ([C.POINTER(Reads), C.POINTER(Results), P, C.POINTER(SamOpts), C.c_char_p], C.c_int32),
             "sr_serve_start": ([P, C.POINTER(ScoreParams), C.POINTER(AlignOpts), C.c_uint32], C.c_int32),
             "sr_submit": ([P, C.POINTER(Reads), C.POINTER(CandList), C.POINTER(C.c_uint64)], C.c_int32),
             "sr_wait": ([P, C.c_uint64, C.c_int32, C.POINTER(C.POINTER(Results))], C.c_int32),
@@ -258,6 +263,43 @@ def results_to_numpy(rp) -> dict:
         n_reads=n, n_refs=nr, n_items=ni,
     )
     return out
+
+
+def write_sam(path, bases, read_off, res: dict, ref_lens, read_names=None, ref_names=None, report=None):
+    """SAM text of aligned reads (sr_write_sam); `res` is an align/fetch result
+    dict, `report` an optional Batch.report() dict for XA secondary hits."""
+    keep = _Keep()
+    reads = make_reads(bases, read_off, keep)
+    best = keep.arr(res["best"], HIT_DTYPE)
+    n = len(best)
+    per = keep.arr(res["best_per_ref"], HIT_DTYPE)
+    cig = keep.arr(res["cigar"], np.uint32)
+    cls = keep.arr(res["read_class"], np.uint8) if res.get("read_class") is not None else None
+    r = Results()
+    r.n_reads, r.n_refs, r.n_items = n, len(ref_lens), 0
+    r.best = C.cast(best.ctypes.data, C.POINTER(Hit))
+    r.best_per_ref = C.cast(per.ctypes.data, C.POINTER(Hit))
+    r.cigar, r.n_cigar = (cig.ctypes.data if len(cig) else None), len(cig)
+    r.read_class = cls.ctypes.data if cls is not None else None
+    lens = keep.arr(np.asarray(ref_lens), np.uint64)
+    o = SamOpts()
+
+    def names(lst):
+        if lst is None:
+            return None
+        enc = [x.encode() for x in lst]
+        arr = (C.c_char_p * len(enc))(*enc)
+        keep.refs.append((enc, arr))
+        return C.cast(arr, P)
+
+    o.read_names, o.ref_names = names(read_names), names(ref_names)
+    if report is not None:
+        offs = keep.arr(report["offsets"], np.uint64)
+        hits = keep.arr(report["hits"], REPORT_HIT_DTYPE)
+        rp = Report(n, 0, len(hits), offs.ctypes.data, hits.ctypes.data if len(hits) else None)
+        keep.refs.append(rp)
+        o.secondary = C.pointer(rp)
+    _check(lib().sr_write_sam(C.byref(reads), C.byref(r), _p(lens), C.byref(o), os.fsencode(path)))
 
 
 def cigar_of(res: dict, read: int):

@@ -179,3 +179,49 @@ def serving_batches(refs, n_batches: int, seed: int, max_batch: int = 4096):
                    cap_per_read=64)
         out.append(dict(**rd, **cd))
     return out
+
+
+def splicing(scale: float = 1.0, seed: int = 0, read_len: int = 100) -> dict:
+    """Alternative-splicing stand-in (the paper adds exon-junction sequences of
+    Ensembl transcripts to the reference, Sec. 6.2 / Table 4): a 20 Mbp genome
+    (41% GC) with genes of 4-10 exons (60-250 bp, introns 300-3000 bp); the
+    junction library joins the last read_len-1 bases of exon i to the first
+    read_len-1 bases of every later exon j of the same gene (exon skipping
+    included), entries separated by 100 random bases.  Reads (1% errors) come
+    from one random isoform per gene (inner exons kept with p = 0.7); `spans`
+    marks reads crossing an exon junction of their isoform."""
+    rng = np.random.default_rng(seed)
+    genome = ref_iid(max(50_000, int(round(20_000_000 * scale))), seed, gc=0.41)
+    n_genes = max(4, int(round(4000 * scale)))
+    flank = read_len - 1
+    junctions, transcripts, bounds = [], [], []
+    pos = 1000
+    for g in range(n_genes):
+        n_ex = int(rng.integers(4, 11))
+        exons = []
+        p = pos
+        for _ in range(n_ex):
+            ln = int(rng.integers(60, 251))
+            if p + ln + 1000 >= len(genome):
+                break
+            exons.append((p, p + ln))
+            p += ln + int(rng.integers(300, 3001))
+        if len(exons) < 2:
+            break
+        pos = p + int(rng.integers(1000, 5000))
+        seqs = [genome[a:b] for a, b in exons]
+        for i in range(len(seqs)):
+            for j in range(i + 1, len(seqs)):
+                junctions.append(np.concatenate([seqs[i][-flank:], seqs[j][:flank]]))
+                junctions.append(rng.choice(np.frombuffer(b"ACGT", np.uint8), 100))
+        keep = [0] + [k for k in range(1, len(seqs) - 1) if rng.random() < 0.7] + [len(seqs) - 1]
+        transcripts.append(np.concatenate([seqs[k] for k in keep]))
+        cut = np.cumsum([len(seqs[k]) for k in keep])[:-1]
+        bounds.append(cut)
+    junc = np.concatenate(junctions) if junctions else rng.choice(np.frombuffer(b"ACGT", np.uint8), 1000)
+    lens = np.array([len(t) for t in transcripts], np.float64)
+    rd = reads(transcripts, max(4, int(round(200_000 * scale))), seed + 1, read_len, read_len, 0.009, 0.001,
+               0.0, weights=lens / lens.sum())
+    spans = np.array([bool(np.any((bounds[t] > p) & (bounds[t] < p + s)))
+                      for t, p, s in zip(rd["t_ref"], rd["t_pos"], rd["t_span"])])
+    return dict(name="splicing", genome=genome, junctions=junc, spans=spans, n_genes=len(transcripts), **rd)

@@ -126,3 +126,25 @@ def test_session_closed_before_its_batches(sr):
         s.close()
         b.close()
         assert g["n_reads"] == len(w["read_off"]) - 1
+
+
+def test_sam_from_gpu_results(sr, tmp_path):
+    """SAM written from the device's results carries the oracle's alignments."""
+    w = S.workload("c2", scale=0.0003, seed=21, rc_frac=0.5)
+    s, b = _run(sr, w)
+    g = b.fetch()
+    rep = b.report(sr.REPORT_BEST_N, 4)
+    path = tmp_path / "gpu.sam"
+    sr.write_sam(path, w["bases"], w["read_off"], g, [len(w["refs"][0])], report=rep)
+    o = oracle_run(w)
+    lines = [ln.rstrip("\n").split("\t") for ln in open(path) if not ln.startswith("@")]
+    assert len(lines) == len(w["read_off"]) - 1
+    ops = "MIDNSHP=X"
+    for r, f in enumerate(lines):
+        ob = o["best"][r]
+        if ob["item"] < 0:
+            assert f[1] == "4"
+            continue
+        assert int(f[3]) == int(ob["ref_start"]) + 1
+        assert f[5] == "".join(f"{int(x) >> 4}{ops[int(x) & 15]}" for x in o["cigar"][r][:int(ob["cigar_len"])])
+        assert f"AS:i:{int(ob['score'])}" in f[11:]

@@ -40,8 +40,9 @@ static sr_status cuda_error(const char* where, cudaError_t e) {
 // ---- autotuner table (read-length bins -> kernel shape)
 static std::mutex g_tune_mu;
 // defaults = the autotuner's picks on GB300 for the c2 score parameters
-static TuneBin g_bins[kNumBins] = {{64, 4, 16},  {80, 4, 24},   {96, 4, 24},  {128, 8, 16},
-                                   {160, 8, 20}, {192, 16, 12}, {224, 8, 28}, {256, 16, 16}};
+static TuneBin g_bins[kNumBins] = {{64, 4, 20},   {80, 4, 20},   {96, 4, 24},   {112, 4, 28},  {128, 4, 32},
+                                   {144, 8, 18},  {160, 8, 20},  {176, 8, 22},  {192, 8, 24},  {208, 8, 26},
+                                   {224, 16, 14}, {240, 16, 15}, {256, 16, 16}};
 
 void tune_get_bins(TuneBin* out) {
   std::lock_guard<std::mutex> g(g_tune_mu);
@@ -1245,7 +1246,7 @@ extern "C" sr_status sr_tune_get(uint32_t* n_bins, uint32_t* upper, uint32_t* la
 }
 
 extern "C" sr_status sr_tune_set(uint32_t n_bins, const uint32_t* upper, const uint32_t* lanes, const uint32_t* rows) {
-  if (n_bins != kNumBins || !upper || !lanes || !rows) return set_error(SR_EINVAL, "sr_tune_set: need 8 bins");
+  if (n_bins != kNumBins || !upper || !lanes || !rows) return set_error(SR_EINVAL, "sr_tune_set: need %d bins", kNumBins);
   TuneBin b[kNumBins];
   for (uint32_t i = 0; i < kNumBins; ++i) {
     if (!extend_config_supported(lanes[i], rows[i]) || lanes[i] * rows[i] < upper[i] ||
@@ -1285,7 +1286,7 @@ extern "C" sr_status sr_tune_load(const char* path) {
     if (sscanf(line, "%u %u %u", &up[n], &la[n], &ro[n]) == 3) ++n;
   }
   fclose(f);
-  if (n != kNumBins) return set_error(SR_EIO, "sr_tune_load: expected 8 bins");
+  if (n != kNumBins) return set_error(SR_EIO, "sr_tune_load: expected %d bins", kNumBins);
   return sr_tune_set(kNumBins, up, la, ro);
 }
 

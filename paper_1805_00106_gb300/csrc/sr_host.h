@@ -24,4 +24,6 @@ struct IndexTables {
   uint64_t n_entries;
 };
 IndexTables index_tables(const sr_index* idx);
+// a zeroed sr_results whose arrays the caller allocates with malloc (released by sr_results_free)
+sr_results* results_alloc();
 }  // namespace sr

@@ -22,6 +22,7 @@
 #include <thread>
 #include <vector>
 
+#include "sr_host.h"
 #include "sr_serve.h"
 
 namespace sr {
@@ -75,7 +76,7 @@ sr_results* slice_results(const sr_results* all, uint32_t r0, uint32_t r1, uint6
                           uint64_t cells) {
   const uint32_t n = r1 - r0, nr = all->n_refs;
   const uint64_t ni = i1 - i0;
-  auto* r = static_cast<sr_results*>(calloc(1, sizeof(sr_results)));
+  sr_results* r = results_alloc();
   if (!r) return nullptr;
   r->n_reads = n;
   r->n_refs = nr;

@@ -94,6 +94,9 @@ struct sr_session {
   // device copy of the references' indexes (sr_session_attach_index)
   DevIndex didx{};
   std::vector<void*> idx_bufs;
+  // pinned host blocks that held fetched results, kept for the next fetch
+  std::mutex pool_mu;
+  std::vector<std::pair<void*, uint64_t>> pool;
   // the arena of the last freed batch, kept for the next one (not counted in hbm_used)
   std::mutex spare_mu;
   void* spare = nullptr;
@@ -238,6 +241,7 @@ static void session_release(sr_session* s) {
   if (s->live.fetch_sub(1) != 1) return;
   for (auto* w : s->d_words) cudaFree(w);
   for (auto* p : s->idx_bufs) cudaFree(p);
+  for (auto& b : s->pool) cudaFreeHost(b.first);
   if (s->spare) cudaFree(s->spare);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -818,15 +822,78 @@ extern "C" sr_status sr_batch_timing(const sr_batch* b, float* total_ms, float* 
   return SR_OK;
 }
 
+namespace sr {
+// Every sr_results is the head of a ResultsBox.  Fetched results keep all
+// their arrays in one pinned host block of the session's pool (fast D2H, no
+// page faults, no unmapping at free); the block goes back to the pool when the
+// results are freed, and the results hold a reference to the session meanwhile.
+struct ResultsBox {
+  sr_results pub;
+  sr_session* pool_of = nullptr;
+  void* block = nullptr;
+  uint64_t block_bytes = 0;
+};
+
+sr_results* results_alloc() {
+  auto* b = static_cast<ResultsBox*>(calloc(1, sizeof(ResultsBox)));
+  return b ? &b->pub : nullptr;
+}
+
+static void* pool_take(sr_session* s, uint64_t bytes, uint64_t* got) {
+  {
+    std::lock_guard<std::mutex> lk(s->pool_mu);
+    int pick = -1;
+    for (size_t i = 0; i < s->pool.size(); ++i)
+      if (s->pool[i].second >= bytes && s->pool[i].second <= 2 * bytes + (64ull << 20) &&
+          (pick < 0 || s->pool[i].second < s->pool[pick].second))
+        pick = static_cast<int>(i);
+    if (pick >= 0) {
+      void* p = s->pool[pick].first;
+      *got = s->pool[pick].second;
+      s->pool.erase(s->pool.begin() + pick);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *got = bytes;
+  return p;
+}
+
+static void pool_give(sr_session* s, void* p, uint64_t bytes) {
+  void* drop = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->pool_mu);
+    s->pool.emplace_back(p, bytes);
+    if (s->pool.size() > 4) {  // keep the four most recent blocks
+      drop = s->pool.front().first;
+      s->pool.erase(s->pool.begin());
+    }
+  }
+  if (drop) cudaFreeHost(drop);
+}
+}  // namespace sr
+
 extern "C" void sr_results_free(sr_results* r) {
   if (!r) return;
+  auto* box = reinterpret_cast<ResultsBox*>(r);
+  if (box->block) {
+    sr_session* s = box->pool_of;
+    pool_give(s, box->block, box->block_bytes);
+    free(box);
+    session_release(s);
+    return;
+  }
   free(r->best);
   free(r->best_per_ref);
   free(r->item_score);
   free(r->item_end);
   free(r->cigar);
   free(r->read_class);
-  free(r);
+  free(box);
 }
 
 extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out) {
@@ -838,23 +905,16 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
   if (st != SR_OK) return st;
   const uint32_t n = b->n_reads, nr = s->n_refs;
   const uint64_t nc = b->n_items;
-  auto* r = static_cast<sr_results*>(calloc(1, sizeof(sr_results)));
+  sr_results* r = results_alloc();
   if (!r) return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
   r->n_reads = n;
   r->n_refs = nr;
   r->n_items = nc;
   r->cells = b->cells;
-  r->best = static_cast<sr_hit*>(malloc(static_cast<size_t>(n ? n : 1) * sizeof(sr_hit)));
-  r->best_per_ref = static_cast<sr_hit*>(malloc(static_cast<size_t>(n ? n : 1) * (nr ? nr : 1) * sizeof(sr_hit)));
-  r->item_score = static_cast<int32_t*>(malloc((nc ? nc : 1) * 4));
-  r->item_end = static_cast<uint32_t*>(malloc((nc ? nc : 1) * 4));
-  if (!r->best || !r->best_per_ref || !r->item_score || !r->item_end) {
-    sr_results_free(r);
-    return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
-  }
   // records in the public layout are assembled on the device, then every array
   // comes back with one copy each on the batch's stream and a single wait
   const bool cig = b->last_opts.want_cigar != 0;
+  const bool cls = b->last_opts.classify != 0;
   if (launch_assemble(b->d, static_cast<int>(nr), cig, stream) < 0) {
     sr_results_free(r);
     return cuda_error("sr_batch_fetch assemble", cudaGetLastError());
@@ -865,21 +925,51 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
     e = cudaMemcpyAsync(&total, b->d.cigar_off + n, 4, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   }
-  if (e == cudaSuccess && cig) {
-    r->n_cigar = total;
-    r->cigar = static_cast<uint32_t*>(malloc((total ? total : 1) * 4ull));
-    if (!r->cigar) {
+  if (e != cudaSuccess) {
+    sr_results_free(r);
+    return cuda_error("sr_batch_fetch copy", e);
+  }
+  // one block for every array, 256-byte aligned parts
+  uint64_t off = 0;
+  auto part = [&](uint64_t bytes) {
+    const uint64_t at = off;
+    off = (off + (bytes ? bytes : 1) + 255) & ~255ull;
+    return at;
+  };
+  const uint64_t o_best = part(static_cast<uint64_t>(n) * sizeof(sr_hit));
+  const uint64_t o_per = part(static_cast<uint64_t>(n) * (nr ? nr : 1) * sizeof(sr_hit));
+  const uint64_t o_sc = part(nc * 4);
+  const uint64_t o_end = part(nc * 4);
+  const uint64_t o_cig = cig ? part(static_cast<uint64_t>(total) * 4) : 0;
+  const uint64_t o_cls = cls ? part(n) : 0;
+  uint64_t got = 0;
+  char* blk = static_cast<char*>(pool_take(s, off, &got));
+  if (blk) {
+    auto* box = reinterpret_cast<ResultsBox*>(r);
+    box->pool_of = s;
+    box->block = blk;
+    box->block_bytes = got;
+    s->live.fetch_add(1);
+    r->best = reinterpret_cast<sr_hit*>(blk + o_best);
+    r->best_per_ref = reinterpret_cast<sr_hit*>(blk + o_per);
+    r->item_score = reinterpret_cast<int32_t*>(blk + o_sc);
+    r->item_end = reinterpret_cast<uint32_t*>(blk + o_end);
+    if (cig) r->cigar = reinterpret_cast<uint32_t*>(blk + o_cig);
+    if (cls) r->read_class = reinterpret_cast<uint8_t*>(blk + o_cls);
+  } else {  // no pinned memory: plain allocations
+    r->best = static_cast<sr_hit*>(malloc(static_cast<size_t>(n ? n : 1) * sizeof(sr_hit)));
+    r->best_per_ref = static_cast<sr_hit*>(malloc(static_cast<size_t>(n ? n : 1) * (nr ? nr : 1) * sizeof(sr_hit)));
+    r->item_score = static_cast<int32_t*>(malloc((nc ? nc : 1) * 4));
+    r->item_end = static_cast<uint32_t*>(malloc((nc ? nc : 1) * 4));
+    if (cig) r->cigar = static_cast<uint32_t*>(malloc((total ? total : 1) * 4ull));
+    if (cls) r->read_class = static_cast<uint8_t*>(malloc(n ? n : 1));
+    if (!r->best || !r->best_per_ref || !r->item_score || !r->item_end || (cig && !r->cigar) ||
+        (cls && !r->read_class)) {
       sr_results_free(r);
       return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
     }
   }
-  if (e == cudaSuccess && b->last_opts.classify) {
-    r->read_class = static_cast<uint8_t*>(malloc(n ? n : 1));
-    if (!r->read_class) {
-      sr_results_free(r);
-      return set_error(SR_ENOMEM, "sr_batch_fetch: out of memory");
-    }
-  }
+  if (cig) r->n_cigar = total;
   auto copy = [&](void* dst, const void* src, uint64_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, stream);
   };
@@ -888,7 +978,7 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
   copy(r->best, b->d.out_best, static_cast<uint64_t>(n) * sizeof(sr_hit));
   copy(r->best_per_ref, b->d.out_per_ref, static_cast<uint64_t>(n) * nr * sizeof(sr_hit));
   if (cig) copy(r->cigar, b->d.cigar, static_cast<uint64_t>(total) * 4);
-  if (b->last_opts.classify) copy(r->read_class, b->d.read_class, n);
+  if (cls) copy(r->read_class, b->d.read_class, n);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
     sr_results_free(r);

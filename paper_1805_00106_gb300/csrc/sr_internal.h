@@ -105,7 +105,7 @@ struct BatchDev {
 // the band over every possible end row would be wider than 32 diagonals), or is
 // found by the full-rectangle kernel (kTbFlagFull: int32-class winners).
 enum : uint8_t { kTbFlagBand = 0, kTbFlagFull = 1, kTbFlagRow = 2 };
-constexpr int kTbBuckets = 4;                        // band <= 8 / 16 / 32 diagonals, full
+constexpr int kTbBuckets = 7;                        // band <= 1 / 2 / 4 / 8 / 16 / 32 diagonals, full
 constexpr int kTbCodes = kTbBuckets * kMaxReadLen;   // code = bucket * 256 + (256 - last row)
 constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + 8;
 constexpr int kTbMaxBand = 32;

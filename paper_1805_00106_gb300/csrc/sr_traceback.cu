@@ -295,21 +295,52 @@ __device__ __forceinline__ TbRead tb_load(const TbArgs& a, bool has, uint32_t r)
   return t;
 }
 
+// What the walk needs of one read (kept in shared memory for narrow segments,
+// whose reads are walked by the whole warp one after another).
+struct WalkRead {
+  int32_t has, r, m, jstar, ihi, w, dlo, S;
+};
+
+__device__ __forceinline__ WalkRead walk_of(const TbRead& t) {
+  return WalkRead{t.has ? 1 : 0, static_cast<int32_t>(t.r), static_cast<int32_t>(t.m),
+                  static_cast<int32_t>(t.jstar), t.ihi, t.w, t.dlo, t.S};
+}
+
+// Codes of a read and its window in shared memory, addressed by 32-bit offsets
+// into the kernel's flat arrays: one byte per base, or 2-bit packed (16 bases
+// per word) for narrow segments, which hold many reads per warp.
+template <bool PACKED>
+struct Codes {
+  const uint8_t* qb;   // byte codes (flat array)
+  const uint8_t* rb;
+  const uint32_t* qw;  // packed codes (flat array)
+  const uint32_t* rw;
+  __device__ __forceinline__ bool match(uint32_t qo, uint32_t ro, uint32_t i0, uint32_t j0) const {
+    if (PACKED) {
+      const uint32_t a = (qw[qo + (i0 >> 4)] >> ((i0 & 15u) * 2u)) & 3u;
+      const uint32_t b = (rw[ro + (j0 >> 4)] >> ((j0 & 15u) * 2u)) & 3u;
+      return a == b;
+    }
+    return qb[qo + i0] == rb[ro + j0];
+  }
+};
+
 // walk back from (i*, j*) through one read's nibbles (shift 0: read A, 4: read B)
-template <int SEG>
-__device__ __forceinline__ void tb_walk(const TbArgs& a, const TbRead& t, uint32_t istar, int shift,
-                                        const uint8_t* dirs, const uint8_t* qcode, const uint8_t* rcode,
-                                        int k, int seg, uint32_t seg_mask) {
+// with a group of WG lanes (lane k of the group); dirs rows have SEG bytes
+template <int SEG, int WG, bool PACKED>
+__device__ __forceinline__ void tb_walk(const TbArgs& a, const WalkRead& t, uint32_t istar, int shift,
+                                        const uint8_t* dirs, const Codes<PACKED>& cd, uint32_t qo, uint32_t ro,
+                                        int k, uint32_t gmask, int gshift) {
   if (!t.has) return;
   const int32_t goe = a.go + a.ge;
   uint32_t* out = a.cigar_slots + static_cast<uint64_t>(t.r) * kCigarStride;
-  int i = static_cast<int>(istar), j = static_cast<int>(t.jstar);
+  int i = static_cast<int>(istar), j = t.jstar;
   int kk = j - i - t.dlo;
   int32_t h = t.S;
   int state = 0;
   uint32_t nr = 0, cur_op = 0xffu, cur_len = 0;
   bool bad = istar == kNoRow;
-  const int limit = static_cast<int>(t.ihi + t.jstar) + 4;
+  const int limit = t.ihi + t.jstar + 4;
   for (int it = 0; !bad; ++it) {
     if (it > limit || kk < 0 || kk >= t.w) {
       bad = true;
@@ -320,18 +351,18 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const TbRead& t, uint32
       const int ii = i - k, jj = j - k;
       const bool v = ii >= 1 && jj >= 1;
       const uint32_t nib = v ? (dirs[(ii - 1) * SEG + kk] >> shift) & 15u : 0u;
-      const int32_t st = v ? (qcode[ii - 1] == rcode[jj - 1] ? a.sa : -a.sb) : 0;
+      const int32_t st = v ? (cd.match(qo, ro, ii - 1, jj - 1) ? a.sa : -a.sb) : 0;
       int32_t incl = st;
 #pragma unroll
-      for (int off = 1; off < SEG; off <<= 1) {
-        const int32_t x = __shfl_up_sync(seg_mask, incl, off, SEG);
+      for (int off = 1; off < WG; off <<= 1) {
+        const int32_t x = __shfl_up_sync(gmask, incl, off, WG);
         if (k >= off) incl += x;
       }
       const bool stop = !(v && (h - (incl - st)) != 0 && (nib & 1u));
-      const uint32_t bal = (__ballot_sync(seg_mask, stop) & seg_mask) >> (SEG == 32 ? 0 : seg * SEG);
-      const int L = bal ? __ffs(bal) - 1 : SEG;
+      const uint32_t bal = (__ballot_sync(gmask, stop) & gmask) >> gshift;
+      const int L = bal ? __ffs(bal) - 1 : WG;
       if (L > 0) {
-        const int32_t used = __shfl_sync(seg_mask, incl, L - 1, SEG);
+        const int32_t used = __shfl_sync(gmask, incl, L - 1, WG);
         h -= used;
         i -= L;
         j -= L;
@@ -349,7 +380,7 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const TbRead& t, uint32
         }
         continue;
       }
-      const uint32_t nib0 = __shfl_sync(seg_mask, nib, 0, SEG);
+      const uint32_t nib0 = __shfl_sync(gmask, nib, 0, WG);
       state = (nib0 & 2u) ? 1 : 2;
     } else {
       if (i < 1 || j < 1) {
@@ -404,7 +435,7 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const TbRead& t, uint32
         for (uint32_t x = 0; x < nr; ++x) out[x] = out[x + 1];
         nc = nr;
       }
-      if (istar < t.m) out[nc++] = ((t.m - istar) << 4) | 4u;
+      if (istar < static_cast<uint32_t>(t.m)) out[nc++] = ((t.m - istar) << 4) | 4u;
       hp->read_start = static_cast<int32_t>(start_i);
       hp->read_end = static_cast<int32_t>(istar);
       hp->start_j = static_cast<uint32_t>(j) + 1u;
@@ -417,25 +448,35 @@ template <int SEG>
 __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint32_t* list,
                                                            const uint32_t* range) {
   constexpr int NSEG = 32 / SEG;
+  constexpr bool PACKED = SEG <= 4;
+  constexpr int kWinWords = kMaxWinLen / 16 + 1;
+  constexpr int kQB = PACKED ? 1 : kMaxReadLen;  // byte codes per read (unused when packed)
+  constexpr int kRB = PACKED ? 1 : kMaxWinLen;
+  constexpr int kQW = PACKED ? kReadWords : 1;   // packed words per read
+  constexpr int kRW = PACKED ? kWinWords : 1;
+  constexpr int kSlots = kTbWarps * NSEG * 2;     // reads resident per block
   __shared__ uint8_t dirs_s[kTbWarps][NSEG][kMaxReadLen * SEG];
-  __shared__ uint8_t rcode_s[kTbWarps][NSEG][2][kMaxWinLen];
-  __shared__ uint8_t qcode_s[kTbWarps][NSEG][2][kMaxReadLen];
+  __shared__ uint8_t qbyte_s[kSlots * kQB];
+  __shared__ uint8_t rbyte_s[kSlots * kRB];
+  __shared__ uint32_t qword_s[kSlots * kQW];
+  __shared__ uint32_t rword_s[kSlots * kRW];
+  __shared__ WalkRead walk_s[PACKED ? kSlots : 1];
+  __shared__ uint32_t iend_s[PACKED ? kSlots : 1];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int seg = lane / SEG;
   const int k = lane % SEG;
   const uint32_t seg_mask = SEG == 32 ? FULL : (((1u << SEG) - 1u) << (seg * SEG));
   uint8_t* dirs = dirs_s[warp][seg];
-  const uint8_t* qA = qcode_s[warp][seg][0];
-  const uint8_t* qB = qcode_s[warp][seg][1];
-  const uint8_t* rA = rcode_s[warp][seg][0];
-  const uint8_t* rB = rcode_s[warp][seg][1];
+  const Codes<PACKED> cd{qbyte_s, rbyte_s, qword_s, rword_s};
   const int32_t goe = a.go + a.ge;
   constexpr int32_t NEG = -(1 << 28);
   const uint32_t begin = range[0];
   const uint32_t count = range[1] - begin;
   constexpr uint32_t kPerWarp = 2 * NSEG;
   const uint32_t stride = gridDim.x * kTbWarps * kPerWarp;
+  // slot of read X of this segment, and its code offsets
+  auto slot = [&](int sg, int X) { return (warp * NSEG + sg) * 2 + X; };
   for (uint32_t base = (blockIdx.x * kTbWarps + warp) * kPerWarp; base < count; base += stride) {
     TbRead rd[2];
 #pragma unroll
@@ -443,12 +484,37 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
       const uint32_t li = base + 2 * seg + X;
       rd[X] = tb_load(a, li < count, li < count ? list[begin + li] : 0u);
       if (rd[X].has) {
-        uint8_t* rc = rcode_s[warp][seg][X];
-        uint8_t* qc = qcode_s[warp][seg][X];
+        const int sl = slot(seg, X);
         const uint32_t* row = a.rpack + static_cast<uint64_t>(rd[X].rd) * kReadWords;
-        for (uint32_t j = k; j < rd[X].jstar; j += SEG) rc[j] = static_cast<uint8_t>(base_at(rd[X].ref, rd[X].ws + j));
-        for (uint32_t i = k; i < static_cast<uint32_t>(rd[X].ihi); i += SEG)
-          qc[i] = static_cast<uint8_t>(rd[X].strand ? 3u - base_at(row, rd[X].m - 1u - i) : base_at(row, i));
+        if (PACKED) {
+          // window words re-aligned to its first base; the reference is padded past its end
+          uint32_t* rw = rword_s + sl * kRW;
+          for (uint32_t w = k; w < (rd[X].jstar + 15) / 16; w += SEG) {
+            const uint64_t idx = rd[X].ws + 16ull * w;
+            const uint32_t sh = static_cast<uint32_t>(idx & 15u) * 2u;
+            const uint32_t* src = rd[X].ref + (idx >> 4);
+            rw[w] = sh ? (src[0] >> sh) | (src[1] << (32u - sh)) : src[0];
+          }
+          uint32_t* qw = qword_s + sl * kQW;
+          for (uint32_t w = k; w < static_cast<uint32_t>(kReadWords); w += SEG) {
+            uint32_t v = 0;
+            if (rd[X].strand) {
+              for (uint32_t t = 0; t < 16; ++t) {
+                const uint32_t i = 16 * w + t;
+                if (i < rd[X].m) v |= (3u - base_at(row, rd[X].m - 1u - i)) << (2 * t);
+              }
+            } else {
+              v = row[w];
+            }
+            qw[w] = v;
+          }
+        } else {
+          uint8_t* rc = rbyte_s + sl * kRB;
+          uint8_t* qc = qbyte_s + sl * kQB;
+          for (uint32_t j = k; j < rd[X].jstar; j += SEG) rc[j] = static_cast<uint8_t>(base_at(rd[X].ref, rd[X].ws + j));
+          for (uint32_t i = k; i < static_cast<uint32_t>(rd[X].ihi); i += SEG)
+            qc[i] = static_cast<uint8_t>(rd[X].strand ? 3u - base_at(row, rd[X].m - 1u - i) : base_at(row, i));
+        }
       }
     }
     __syncwarp();
@@ -459,44 +525,55 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     const int stB = rd[1].has ? 2 * (rd[1].ihi - 1) + rd[1].w : 0;
     const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(max(stA, stB) + 1)));
     const int p = k & 1;
+    // per half-step: the rows where this lane's diagonal is inside the window
+    // [rlo, rlo + cnt), the code offsets of row 1 and column 1, the row where
+    // it crosses the end column (or -1), the top border flag and the score
     struct Sub {
-      bool on, bd;          // lane inside the band; lane k + 1 outside it (top border)
-      int c, ilo, ihi, js;  // column = row + c; end rows searched in [ilo, ihi]
+      uint32_t rlo, cnt, qo, ro;
+      int icr;
+      bool bd;
       int32_t S;
-      const uint8_t* q;
-      const uint8_t* r;
     };
-    Sub s0, s1;
-    {
-      const TbRead& x0 = p ? rd[1] : rd[0];
-      const TbRead& x1 = p ? rd[0] : rd[1];
-      s0 = Sub{x0.has && k < x0.w, k + 1 >= x0.w, x0.dlo + k, x0.ilo, x0.ihi, static_cast<int>(x0.jstar), x0.S,
-               p ? qB : qA, p ? rB : rA};
-      s1 = Sub{x1.has && k < x1.w, k + 1 >= x1.w, x1.dlo + k, x1.ilo, x1.ihi, static_cast<int>(x1.jstar), x1.S,
-               p ? qA : qB, p ? rA : rB};
-    }
-    // one cell of row i of a read: neighbours left (hl, el), above (hu, fu), diagonal hd
-    auto cell = [&](const Sub& sb, int i, int32_t hl, int32_t el, int32_t hu, int32_t fu, int32_t hd,
+    auto sub_of = [&](const TbRead& x, int X) {
+      Sub u;
+      const int c = x.dlo + k;  // column = row + c
+      const int lo = max(1, 1 - c), hi = min(x.ihi, static_cast<int>(x.jstar) - c);
+      const bool on = x.has && k < x.w && hi >= lo;
+      u.rlo = static_cast<uint32_t>(lo);
+      u.cnt = on ? static_cast<uint32_t>(hi - lo + 1) : 0u;
+      const int sl = slot(seg, X);
+      // offsets such that row i, column i + c index codes (i - 1) and (i - 1 + c)
+      u.qo = static_cast<uint32_t>(sl * (PACKED ? kQW : kQB));
+      u.ro = static_cast<uint32_t>(sl * (PACKED ? kRW : kRB));
+      const int ir = static_cast<int>(x.jstar) - c;
+      u.icr = (on && ir >= x.ilo && ir >= lo && ir <= hi) ? ir : -1;
+      u.bd = k + 1 >= x.w;
+      u.S = x.S;
+      return u;
+    };
+    const int c0 = (p ? rd[1].dlo : rd[0].dlo) + k, c1 = (p ? rd[0].dlo : rd[1].dlo) + k;
+    const Sub s0 = p ? sub_of(rd[1], 1) : sub_of(rd[0], 0);
+    const Sub s1 = p ? sub_of(rd[0], 0) : sub_of(rd[1], 1);
+    // one cell of row i: neighbours left (hl, el), above (hu, fu), diagonal hd
+    auto cell = [&](const Sub& sb, int c, int i, int32_t hl, int32_t el, int32_t hu, int32_t fu, int32_t hd,
                     int32_t& nH, int32_t& nE, int32_t& nF, uint32_t& nib, uint32_t& ic) {
       nH = 0;
       nE = NEG;
       nF = NEG;
       nib = 0;
-      if (sb.on && i >= 1 && i <= sb.ihi) {
-        const int j = i + sb.c;
+      if (static_cast<uint32_t>(i) - sb.rlo < sb.cnt) {
         const int32_t eo = hl - goe, ee = el - a.ge, fo = hu - goe, fe = fu - a.ge;
         const int32_t E = max(eo, ee), F = max(fo, fe);
-        if (j >= 1 && j <= sb.js) {
-          const int32_t hs = hd + (sb.q[i - 1] == sb.r[j - 1] ? a.sa : -a.sb);
-          const int32_t H = max(max(0, hs), max(E, F));
-          nib = static_cast<uint32_t>(H == hs) | (static_cast<uint32_t>(H == E) << 1) |
-                (static_cast<uint32_t>(eo >= ee) << 2) | (static_cast<uint32_t>(fo >= fe) << 3);
-          nH = H;
-          nE = E;
-          nF = F;
-          // final-row mode ends in row m even where an earlier row also holds S
-          if (j == sb.js && H == sb.S && i >= sb.ilo) ic = min(ic, static_cast<uint32_t>(i));
-        }
+        const uint32_t i0 = static_cast<uint32_t>(i - 1);
+        const int32_t hs = hd + (cd.match(sb.qo, sb.ro, i0, i0 + static_cast<uint32_t>(c)) ? a.sa : -a.sb);
+        const int32_t H = max(max(0, hs), max(E, F));
+        nib = static_cast<uint32_t>(H == hs) | (static_cast<uint32_t>(H == E) << 1) |
+              (static_cast<uint32_t>(eo >= ee) << 2) | (static_cast<uint32_t>(fo >= fe) << 3);
+        nH = H;
+        nE = E;
+        nF = F;
+        // final-row mode ends in row m even where an earlier row also holds S
+        if (i == sb.icr && H == sb.S) ic = static_cast<uint32_t>(i);
       }
     };
     // cells of the previous pair of steps: half-step 0 (Ha, Ea, Fa) and 1 (Hb, Eb, Fb)
@@ -518,7 +595,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
           hu = 0;
           fu = NEG;
         }
-        cell(s0, ia, hl, el, hu, fu, Ha, Ha, Ea, Fa, nib, ic0);
+        cell(s0, c0, ia, hl, el, hu, fu, Ha, Ha, Ea, Fa, nib, ic0);
         // read A's nibble of a row waits for read B's of the same row
         if (p) {
           if (ia >= 1 && ia <= kMaxReadLen) dirs[(ia - 1) * SEG + k] = static_cast<uint8_t>(pend | (nib << 4));
@@ -540,7 +617,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
           fu = NEG;
         }
         const int ib = ia + p;
-        cell(s1, ib, hl, el, hu, fu, Hb, Hb, Eb, Fb, nib, ic1);
+        cell(s1, c1, ib, hl, el, hu, fu, Hb, Hb, Eb, Fb, nib, ic1);
         if (p) {
           pend = nib;
         } else if (ib >= 1 && ib <= kMaxReadLen) {
@@ -555,10 +632,34 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
       icB = min(icB, __shfl_xor_sync(FULL, icB, off, SEG));
     }
     __syncwarp();
-    // ---- walk back, read A then read B of each segment
-    tb_walk<SEG>(a, rd[0], icA, 0, dirs, qA, rA, k, seg, seg_mask);
-    __syncwarp(seg_mask);
-    tb_walk<SEG>(a, rd[1], icB, 4, dirs, qB, rB, k, seg, seg_mask);
+    // ---- walk back
+    if (PACKED) {
+      // narrow segments: the whole warp walks every read of the warp in turn
+      if (k == 0) {
+        walk_s[slot(seg, 0)] = walk_of(rd[0]);
+        walk_s[slot(seg, 1)] = walk_of(rd[1]);
+        iend_s[slot(seg, 0)] = icA;
+        iend_s[slot(seg, 1)] = icB;
+      }
+      __syncwarp();
+      for (int sg = 0; sg < NSEG; ++sg) {
+        for (int X = 0; X < 2; ++X) {
+          const int sl = slot(sg, X);
+          const WalkRead wr = walk_s[sl];
+          tb_walk<SEG, 32, PACKED>(a, wr, iend_s[sl], X ? 4 : 0, dirs_s[warp][sg], cd,
+                                   static_cast<uint32_t>(sl * kQW), static_cast<uint32_t>(sl * kRW) +
+                                   0u, lane, FULL, 0);
+          __syncwarp();
+        }
+      }
+    } else {
+      // read A, then read B of each segment, walked by the segment's lanes
+      tb_walk<SEG, SEG, PACKED>(a, walk_of(rd[0]), icA, 0, dirs, cd, static_cast<uint32_t>(slot(seg, 0) * kQB),
+                                static_cast<uint32_t>(slot(seg, 0) * kRB), k, seg_mask, SEG == 32 ? 0 : seg * SEG);
+      __syncwarp(seg_mask);
+      tb_walk<SEG, SEG, PACKED>(a, walk_of(rd[1]), icB, 4, dirs, cd, static_cast<uint32_t>(slot(seg, 1) * kQB),
+                                static_cast<uint32_t>(slot(seg, 1) * kRB), k, seg_mask, SEG == 32 ? 0 : seg * SEG);
+    }
     __syncwarp();
   }
 }
@@ -594,7 +695,8 @@ __global__ void __launch_bounds__(1024) k_tb_route(TbArgs a, uint32_t* code, uin
           hp->cigar_len = 0;
         } else {
           const TbBand b = tb_band(a.sa, a.go, a.ge, S, jstar, ilo, ihi);
-          bucket = b.w <= 8 ? 0 : (b.w <= 16 ? 1 : (b.w <= kTbMaxBand ? 2 : 3));
+          bucket = b.w <= 1 ? 0 : b.w <= 2 ? 1 : b.w <= 4 ? 2 : b.w <= 8 ? 3 : b.w <= 16 ? 4
+                 : b.w <= kTbMaxBand ? 5 : kTbBuckets - 1;
           last = ihi;
         }
       }
@@ -610,25 +712,32 @@ __global__ void __launch_bounds__(1024) k_tb_route(TbArgs a, uint32_t* code, uin
     if (sh[c]) atomicAdd(&hist[c], sh[c]);
 }
 
-// exclusive offsets of the codes (one block of kTbCodes threads) and each
+// exclusive offsets of the codes (one block, two codes per thread) and each
 // bucket's [begin, end) in the sorted list
-__global__ void __launch_bounds__(kTbCodes) k_tb_scan(uint32_t* cnt) {
-  __shared__ uint32_t sh[kTbCodes];
+constexpr int kTbScanThreads = (kTbCodes + 1) / 2;
+static_assert(kTbScanThreads <= 1024, "traceback code scan block");
+__global__ void __launch_bounds__(kTbScanThreads) k_tb_scan(uint32_t* cnt) {
+  __shared__ uint32_t sh[kTbScanThreads];
   const int t = threadIdx.x;
-  const uint32_t v = cnt[t];
-  sh[t] = v;
+  const uint32_t v0 = 2 * t < kTbCodes ? cnt[2 * t] : 0u;
+  const uint32_t v1 = 2 * t + 1 < kTbCodes ? cnt[2 * t + 1] : 0u;
+  sh[t] = v0 + v1;
   __syncthreads();
-  for (int off = 1; off < kTbCodes; off <<= 1) {
+  for (int off = 1; off < kTbScanThreads; off <<= 1) {
     const uint32_t x = t >= off ? sh[t - off] : 0u;
     __syncthreads();
     sh[t] += x;
     __syncthreads();
   }
-  cnt[kTbCodes + t] = sh[t] - v;
-  if (t % kMaxReadLen == 0) {
-    const int b = t / kMaxReadLen;
-    cnt[2 * kTbCodes + 2 * b] = sh[t] - v;
-    cnt[2 * kTbCodes + 2 * b + 1] = sh[t + kMaxReadLen - 1];
+  const uint32_t ex0 = sh[t] - v0 - v1;
+  if (2 * t < kTbCodes) cnt[kTbCodes + 2 * t] = ex0;
+  if (2 * t + 1 < kTbCodes) cnt[kTbCodes + 2 * t + 1] = ex0 + v0;
+  __syncthreads();
+  if (t < kTbBuckets) {
+    // bucket t spans codes [t * 256, (t + 1) * 256): begin = exclusive offset of its first code
+    const int c0 = t * kMaxReadLen, c1 = (t + 1) * kMaxReadLen;
+    cnt[2 * kTbCodes + 2 * t] = cnt[kTbCodes + c0];
+    cnt[2 * kTbCodes + 2 * t + 1] = cnt[kTbCodes + c1 - 1] + cnt[c1 - 1];
   }
 }
 
@@ -684,7 +793,7 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   const uint32_t* ranges = b.tb_count + 2 * kTbCodes;
   if (cudaMemsetAsync(hist, 0, kTbCodes * sizeof(uint32_t), st) != cudaSuccess) return -1;
   k_tb_route<<<(b.n_reads + 1023) / 1024, 1024, 0, st>>>(a, code, hist);
-  k_tb_scan<<<1, kTbCodes, 0, st>>>(b.tb_count);
+  k_tb_scan<<<1, kTbScanThreads, 0, st>>>(b.tb_count);
   k_tb_scatter<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, code, cursor, list);
   int launched = 3;
   auto wave = [&](auto kern, int bucket, int per_warp) -> bool {
@@ -696,7 +805,9 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
     ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
   };
-  if (!wave(k_tb_wave<8>, 0, 8) || !wave(k_tb_wave<16>, 1, 4) || !wave(k_tb_wave<32>, 2, 2)) return -1;
+  if (!wave(k_tb_wave<1>, 0, 64) || !wave(k_tb_wave<2>, 1, 32) || !wave(k_tb_wave<4>, 2, 16) ||
+      !wave(k_tb_wave<8>, 3, 8) || !wave(k_tb_wave<16>, 4, 4) || !wave(k_tb_wave<32>, 5, 2))
+    return -1;
   const size_t smem = static_cast<size_t>(kMaxWinLen) * 32 * sizeof(uint32_t);
   static bool attr = false;
   if (!attr) {

@@ -331,8 +331,12 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
       T[k] = INIT;
       E[k] = INIT;
     }
-    uint32_t tprev = INIT, Tbot = INIT, Fbot = INIT, best = INIT;
-    uint32_t jlo = 0, jhi = 0;
+    uint32_t tprev = INIT, Tbot = INIT, Fbot = INIT;
+    // best cell per half as the key (T << 16) | (0xffff - column): the max keeps the
+    // highest score and, among equal scores, the smallest (first) column
+    const uint32_t KINIT = (INIT & 0xffffu) << 16;
+    uint32_t kbl = KINIT, kbh = KINIT;
+    uint32_t jn = 0xfffeu + static_cast<uint32_t>(glane);  // 0xffff - (column of step s), column = s - glane + 1
     // mode 2: biased T value of the winner's score in each half, rows found
     uint32_t tgt_lo = 0, tgt_hi = 0, ilo = 0xffffffffu, ihi = 0xffffffffu;
     if (MODE == 2 && has_task) {
@@ -394,11 +398,8 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
           cm &= (static_cast<uint32_t>(j) < nlo ? 0xffffu : 0u) |
                 (static_cast<uint32_t>(j) < nhi ? 0xffff0000u : 0u);
         // strict improvement per half records the (1-based) column
-        const uint32_t nb = __vimax_s16x2_relu(best, cm);
-        const uint32_t chg = nb ^ best;
-        jlo = (chg & 0xffffu) ? static_cast<uint32_t>(j + 1) : jlo;
-        jhi = (chg >> 16) ? static_cast<uint32_t>(j + 1) : jhi;
-        best = nb;
+        kbl = max(kbl, prmt(jn - static_cast<uint32_t>(s), cm, 0x5410u));
+        kbh = max(kbh, prmt(jn - static_cast<uint32_t>(s), cm, 0x7610u));
       }
     }
 
@@ -416,11 +417,8 @@ __global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
       continue;
     }
     // ---- group reduction of (score, -column) and write-back
-    const int32_t base_t = kBias - goe;
-    const uint32_t slo = (best & 0xffffu) - base_t;
-    const uint32_t shi = (best >> 16) - base_t;
-    uint32_t klo = (slo << 16) | (0xffffu - (slo ? jlo : 0u));
-    uint32_t khi = (shi << 16) | (0xffffu - (shi ? jhi : 0u));
+    const uint32_t base_t = static_cast<uint32_t>(kBias - goe) << 16;
+    uint32_t klo = kbl - base_t, khi = kbh - base_t;  // (score << 16) | (0xffff - column)
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
       klo = max(klo, __shfl_xor_sync(FULL, klo, off, G));

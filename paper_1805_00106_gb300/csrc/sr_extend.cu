@@ -36,9 +36,24 @@ ExtArgs make_args(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc) 
 
 }  // namespace
 
+int fanout_begin(const Fanout& f, cudaStream_t st) {
+  if (cudaEventRecord(f.fork, st) != cudaSuccess) return -1;
+  for (int i = 0; i < kSide; ++i)
+    if (cudaStreamWaitEvent(f.side[i], f.fork, 0) != cudaSuccess) return -1;
+  return 0;
+}
+
+int fanout_end(const Fanout& f, cudaStream_t st) {
+  for (int i = 0; i < kSide; ++i) {
+    if (cudaEventRecord(f.join[i], f.side[i]) != cudaSuccess) return -1;
+    if (cudaStreamWaitEvent(st, f.join[i], 0) != cudaSuccess) return -1;
+  }
+  return 0;
+}
+
 int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
                        const TuneBin* bins, int n_bins, bool plain, uint32_t lanes, uint32_t rows,
-                       cudaStream_t st) {
+                       cudaStream_t st, const uint64_t* class_items, const Fanout* fan) {
   ExtArgs a = make_args(b, refs, sc);
   a.order = b.order;  // winners compacted per class
   a.class_range = b.wrange;
@@ -46,14 +61,18 @@ int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst&
   a.item_iend = b.item_iend;
   int launched = 0;
   const int classes = plain ? 1 : n_bins;
+  if (fan && fanout_begin(*fan, st) < 0) return -1;
+  int next = 0;
   for (int c = 0; c < classes; ++c) {
+    if (!plain && class_items && class_items[c] == 0) continue;  // no item, no winner
     a.cls = c;
     uint32_t g = lanes ? lanes : (plain ? 16u : bins[c].lanes);
     uint32_t r = rows ? rows : (plain ? 16u : bins[c].rows);
-    int k = dispatch_mode2(g, r, a, st);
+    int k = dispatch_mode2(g, r, a, fan ? fan->side[next++ % kSide] : st);
     if (k < 0) return -1;
     launched += k;
   }
+  if (fan && fanout_end(*fan, st) < 0) return -1;
   return launched;
 }
 
@@ -80,7 +99,7 @@ bool extend_config_supported(uint32_t lanes, uint32_t rows) {
 
 int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
                   const TuneBin* bins, int n_bins, int mode, bool plain, uint32_t lanes,
-                  uint32_t rows, cudaStream_t st) {
+                  uint32_t rows, cudaStream_t st, const uint64_t* class_items, const Fanout* fan) {
   ExtArgs a = make_args(b, refs, sc);
   int launched = 0;
   if (plain) {
@@ -93,23 +112,30 @@ int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
                       : dispatch_mode0(false, g, r, a, st, tasks);
     return k < 0 ? -1 : k;
   }
-  for (int c = 0; c < n_bins; ++c) {
+  if (fan && fanout_begin(*fan, st) < 0) return -1;
+  int next = 0;
+  // longest reads first: each side stream starts on a large bin
+  for (int c = n_bins - 1; c >= 0; --c) {
+    if (class_items && class_items[c] == 0) continue;
     a.cls = c;
     uint32_t g = lanes ? lanes : bins[c].lanes, r = rows ? rows : bins[c].rows;
-    int k = mode == 1 ? dispatch_mode1(true, g, r, a, st, 0) : dispatch_mode0(true, g, r, a, st, 0);
+    const cudaStream_t s = fan ? fan->side[next++ % kSide] : st;
+    int k = mode == 1 ? dispatch_mode1(true, g, r, a, s, 0) : dispatch_mode0(true, g, r, a, s, 0);
     if (k < 0) return -1;
     launched += k;
   }
   a.cls = kI32Class;
-  {
+  if (!class_items || class_items[kI32Class] != 0) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (mode == 1) k_extend32<1><<<nsm * 4, 128, 0, st>>>(a);
-    else k_extend32<0><<<nsm * 4, 128, 0, st>>>(a);
+    const cudaStream_t s = fan ? fan->side[next++ % kSide] : st;
+    if (mode == 1) k_extend32<1><<<nsm * 4, 128, 0, s>>>(a);
+    else k_extend32<0><<<nsm * 4, 128, 0, s>>>(a);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     ++launched;
   }
+  if (fan && fanout_end(*fan, st) < 0) return -1;
   return launched;
 }
 

@@ -136,6 +136,21 @@ __host__ __device__ inline uint32_t tb_min_row(int32_t sa, int32_t S) {
 }
 #endif
 
+// Independent kernels of one phase (the length bins, the traceback buckets)
+// run on side streams forked from the launching stream and joined back, so a
+// bin's tail overlaps the next bins and small batches do not pay the bins'
+// latencies one after another.  Events: one fork and kSide joins per phase.
+constexpr int kSide = 4;
+struct Fanout {
+  cudaStream_t side[kSide];
+  cudaEvent_t fork;
+  cudaEvent_t join[kSide];
+};
+// record the fork on st and make every side stream wait for it
+int fanout_begin(const Fanout& f, cudaStream_t st);
+// make st wait for everything enqueued on the side streams
+int fanout_end(const Fanout& f, cudaStream_t st);
+
 struct TuneBin {
   uint32_t upper;  // largest read length in the bin
   uint32_t lanes;  // G: lanes per alignment (power of two)
@@ -148,17 +163,20 @@ int launch_pack_refs(const char* ascii, uint64_t len, uint32_t* words, uint32_t*
 int launch_prepare(const BatchDev& b, const DevRefs& refs, cudaStream_t st);
 int launch_bins(const BatchDev& b, const ScoreConst& sc, const TuneBin* bins, int n_bins,
                 bool force_i32, bool plain, cudaStream_t st);
+// class_items: items per length class (host; nullptr = launch every class);
+// fan: side streams for the per-class kernels (nullptr = all on st)
 int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
                   const TuneBin* bins, int n_bins, int mode, bool plain, uint32_t lanes,
-                  uint32_t rows, cudaStream_t st);
+                  uint32_t rows, cudaStream_t st, const uint64_t* class_items = nullptr,
+                  const Fanout* fan = nullptr);
 int launch_select(const BatchDev& b, int n_refs, cudaStream_t st);
 int launch_winners(const BatchDev& b, const ScoreConst& sc, int mode, int n_refs, bool plain,
                    cudaStream_t st);
 int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
                        const TuneBin* bins, int n_bins, bool plain, uint32_t lanes, uint32_t rows,
-                       cudaStream_t st);
+                       cudaStream_t st, const uint64_t* class_items = nullptr, const Fanout* fan = nullptr);
 int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, int mode,
-                     int n_refs, cudaStream_t st);
+                     int n_refs, cudaStream_t st, const Fanout* fan = nullptr);
 int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);
 int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, cudaStream_t st);
 // exclusive scan of n counts into out[0..n] (out[n] = total) with a scratch of

@@ -124,6 +124,9 @@ struct sr_batch {
   bool ran = false;
   sr_align_opts last_opts{};
   cudaEvent_t ev[6] = {};  // around: whole path, extension kernels, traceback
+  // side streams and fork/join events of the extension, winner-pass and traceback phases
+  Fanout fan[3] = {};
+  bool fan_ok = false;
 };
 
 extern "C" const char* sr_last_error(void) { return g_err.c_str(); }
@@ -578,6 +581,21 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
       return cuda_error("sr_batch_stage events", cudaGetLastError());
     }
   }
+  {
+    bool ok = true;
+    cudaStream_t side[kSide] = {};
+    for (auto& x : side) ok = ok && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto& f : b->fan) {
+      for (int i = 0; i < kSide; ++i) f.side[i] = side[i];
+      ok = ok && cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
+      for (auto& j : f.join) ok = ok && cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess;
+    }
+    b->fan_ok = true;  // what was created is released by sr_batch_free
+    if (!ok) {
+      sr_batch_free(b);
+      return cuda_error("sr_batch_stage streams", cudaGetLastError());
+    }
+  }
   cudaStream_t st = b->stream;
   if (nb) e = cudaMemcpyAsync(const_cast<char*>(d.bases), reads->bases, nb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -611,6 +629,18 @@ extern "C" void sr_batch_free(sr_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto ev : b->ev)
     if (ev) cudaEventDestroy(ev);
+  if (b->fan_ok) {
+    for (auto& f : b->fan) {
+      if (f.fork) cudaEventDestroy(f.fork);
+      for (auto j : f.join)
+        if (j) cudaEventDestroy(j);
+    }
+    for (auto x : b->fan[0].side)
+      if (x) {
+        cudaStreamSynchronize(x);
+        cudaStreamDestroy(x);
+      }
+  }
   if (b->arena) {
     cudaStreamSynchronize(b->stream);
     // keep the larger of this arena and the session's spare for the next batch
@@ -649,12 +679,29 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
   if (cudaMemsetAsync(d.status, 0, 4, st) != cudaSuccess) return -1;
   if ((t = launch_prepare(d, b->s->refs, st)) < 0) return -1;
   k += t;
+  // windows per length class (as launch_bins will route them): empty classes launch nothing
+  uint64_t class_items[kNumClasses] = {};
+  {
+    const int32_t goe = sp.gap_open + sp.gap_extend;
+    const bool tables_fit = sp.match + goe <= 127 && goe - sp.mismatch >= -128 && goe + sp.gap_extend + 256 < kBias;
+    for (int m = 0; m <= kMaxReadLen; ++m) {
+      if (!b->items_by_len[m]) continue;
+      int c = kNumBins - 1;
+      for (int q = 0; q < kNumBins; ++q)
+        if (static_cast<uint32_t>(m) <= bins[q].upper) {
+          c = q;
+          break;
+        }
+      const bool i16_ok = tables_fit && static_cast<int64_t>(sp.match) * m <= 32767 - kBias;
+      class_items[(o.force_i32 || !i16_ok) ? kI32Class : c] += b->items_by_len[m];
+    }
+  }
   if (b->n_items) {
     if ((t = launch_bins(d, sc, bins, kNumBins, o.force_i32 != 0, plain, st)) < 0) return -1;
     k += t;
     if (!mark(2)) return -1;
     if ((t = launch_extend(d, b->s->refs, sc, bins, kNumBins, static_cast<int>(o.mode), plain, o.lanes,
-                           o.rows, st)) < 0)
+                           o.rows, st, class_items, &b->fan[0])) < 0)
       return -1;
     if (!mark(3)) return -1;
     k += t;
@@ -668,10 +715,12 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
     if ((t = launch_winners(d, sc, static_cast<int>(o.mode), nr, plain, st)) < 0) return -1;
     k += t;
     if (o.mode == SR_MODE_LOCAL && b->n_items) {
-      if ((t = launch_winner_rows(d, b->s->refs, sc, bins, kNumBins, plain, o.lanes, o.rows, st)) < 0) return -1;
+      if ((t = launch_winner_rows(d, b->s->refs, sc, bins, kNumBins, plain, o.lanes, o.rows, st, class_items,
+                                  &b->fan[1])) < 0)
+        return -1;
       k += t;
     }
-    if ((t = launch_traceback(d, b->s->refs, sc, static_cast<int>(o.mode), nr, st)) < 0) return -1;
+    if ((t = launch_traceback(d, b->s->refs, sc, static_cast<int>(o.mode), nr, st, &b->fan[2])) < 0) return -1;
     k += t;
     if ((t = launch_cigar_compact(d, nr, st)) < 0) return -1;
     k += t;
@@ -723,8 +772,15 @@ sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp,
     const int k = enqueue(b, *sp, o, bins, stream);
     if (k < 0) return cuda_error("sr_batch_run launch", cudaGetLastError());
     b->kernels = static_cast<uint64_t>(k);
+  } else if (!b->ran) {
+    // a batch's first run launches the kernels directly: a batch run once (one
+    // sr_align_batch call, one serving round) would not earn back a graph's
+    // capture and instantiation
+    const int k = enqueue(b, *sp, o, bins, stream);
+    if (k < 0) return cuda_error("sr_batch_run launch", cudaGetLastError());
+    b->kernels = static_cast<uint64_t>(k);
   } else {
-    // the batched engine replays the whole path as one CUDA graph
+    // later runs replay the whole path as one CUDA graph
     const bool reuse = b->graph && same_opts(b->g_opts, o) && memcmp(&b->g_sp, sp, sizeof(*sp)) == 0 &&
                        memcmp(b->g_bins, bins, sizeof(bins)) == 0;
     if (!reuse) {
@@ -943,7 +999,8 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
   const uint64_t o_cig = cig ? part(static_cast<uint64_t>(total) * 4) : 0;
   const uint64_t o_cls = cls ? part(n) : 0;
   uint64_t got = 0;
-  char* blk = static_cast<char*>(pool_take(s, off, &got));
+  // small results (serving rounds) use plain memory: pinning costs more than it saves
+  char* blk = off >= (16ull << 20) ? static_cast<char*>(pool_take(s, off, &got)) : nullptr;
   if (blk) {
     auto* box = reinterpret_cast<ResultsBox*>(r);
     box->pool_of = s;

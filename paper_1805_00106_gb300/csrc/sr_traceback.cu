@@ -759,7 +759,7 @@ __global__ void k_tb_scatter(uint32_t n_reads, const uint32_t* code, uint32_t* c
 }  // namespace
 
 int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, int mode,
-                     int n_refs, cudaStream_t st) {
+                     int n_refs, cudaStream_t st, const Fanout* fan) {
   if (b.n_reads == 0) return 0;
   TbArgs a{};
   a.rpack = b.rpack;
@@ -796,17 +796,21 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   k_tb_scan<<<1, kTbScanThreads, 0, st>>>(b.tb_count);
   k_tb_scatter<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, code, cursor, list);
   int launched = 3;
+  if (fan && fanout_begin(*fan, st) < 0) return -1;
+  int next = 0;
+  auto lane_of = [&]() { return fan ? fan->side[next++ % kSide] : st; };
   auto wave = [&](auto kern, int bucket, int per_warp) -> bool {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kTbWarps, 0) != cudaSuccess) return false;
     const uint32_t g0 = static_cast<uint32_t>(nsm) * static_cast<uint32_t>(per_sm > 0 ? per_sm : 1);
     const uint32_t need = (b.n_reads + kTbWarps * per_warp - 1) / (kTbWarps * per_warp);
-    kern<<<need < g0 ? need : g0, 32 * kTbWarps, 0, st>>>(a, list, ranges + 2 * bucket);
+    kern<<<need < g0 ? need : g0, 32 * kTbWarps, 0, lane_of()>>>(a, list, ranges + 2 * bucket);
     ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
   };
-  if (!wave(k_tb_wave<1>, 0, 64) || !wave(k_tb_wave<2>, 1, 32) || !wave(k_tb_wave<4>, 2, 16) ||
-      !wave(k_tb_wave<8>, 3, 8) || !wave(k_tb_wave<16>, 4, 4) || !wave(k_tb_wave<32>, 5, 2))
+  // widest bands (longest kernels) first
+  if (!wave(k_tb_wave<32>, 5, 2) || !wave(k_tb_wave<16>, 4, 4) || !wave(k_tb_wave<4>, 2, 16) ||
+      !wave(k_tb_wave<1>, 0, 64) || !wave(k_tb_wave<8>, 3, 8) || !wave(k_tb_wave<2>, 1, 32))
     return -1;
   const size_t smem = static_cast<size_t>(kMaxWinLen) * 32 * sizeof(uint32_t);
   static bool attr = false;
@@ -819,9 +823,11 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traceback, 32, smem) != cudaSuccess) return -1;
   const uint32_t grid = static_cast<uint32_t>(nsm) * static_cast<uint32_t>(per_sm > 0 ? per_sm : 1);
-  k_traceback<<<grid, 32, smem, st>>>(a, list, ranges + 2 * (kTbBuckets - 1));
+  k_traceback<<<grid, 32, smem, lane_of()>>>(a, list, ranges + 2 * (kTbBuckets - 1));
   ++launched;
-  return cudaPeekAtLastError() == cudaSuccess ? launched : -1;
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  if (fan && fanout_end(*fan, st) < 0) return -1;
+  return launched;
 }
 
 }  // namespace sr

@@ -40,7 +40,7 @@ static sr_status cuda_error(const char* where, cudaError_t e) {
 // ---- autotuner table (read-length bins -> kernel shape)
 static std::mutex g_tune_mu;
 // defaults = the autotuner's picks on GB300 for the c2 score parameters
-static TuneBin g_bins[kNumBins] = {{64, 4, 20},   {80, 4, 20},   {96, 4, 24},   {112, 4, 28},  {128, 4, 32},
+static TuneBin g_bins[kNumBins] = {{64, 4, 16},   {80, 4, 20},   {96, 8, 12},   {112, 8, 14},  {128, 8, 16},
                                    {144, 8, 18},  {160, 8, 20},  {176, 8, 22},  {192, 8, 24},  {208, 8, 26},
                                    {224, 16, 14}, {240, 16, 15}, {256, 16, 16}};
 
@@ -1462,21 +1462,27 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   for (int bi = 0; bi < kNumBins; ++bi) {
+    // reads of lengths spread over the bin (row padding counts as it will in use)
     const uint32_t m = cur[bi].upper;
+    const uint32_t m_lo = (bi ? cur[bi - 1].upper : 0u) + 1u;
     const uint32_t nw = 6;
-    std::vector<char> bases(static_cast<size_t>(sample_reads) * m);
-    for (auto& c : bases) c = "ACGT"[next() & 3];
     std::vector<uint64_t> roff(sample_reads + 1ull), coff(sample_reads + 1ull);
+    std::vector<uint32_t> mlen(sample_reads);
+    roff[0] = 0;
+    for (uint32_t r = 0; r < sample_reads; ++r) {
+      mlen[r] = m_lo + static_cast<uint32_t>(next() % (m - m_lo + 1));
+      roff[r + 1] = roff[r] + mlen[r];
+      coff[r + 1] = static_cast<uint64_t>(r + 1) * nw;
+    }
+    coff[0] = 0;
+    std::vector<char> bases(roff[sample_reads]);
+    for (auto& c : bases) c = "ACGT"[next() & 3];
     std::vector<uint8_t> cref(static_cast<size_t>(sample_reads) * nw, 0), cstr(cref.size(), 0);
     std::vector<uint64_t> cst(cref.size());
     std::vector<uint32_t> cln(cref.size());
     const uint64_t L = s->lens[0];
-    for (uint32_t r = 0; r <= sample_reads; ++r) {
-      roff[r] = static_cast<uint64_t>(r) * m;
-      coff[r] = static_cast<uint64_t>(r) * nw;
-    }
     for (size_t k = 0; k < cref.size(); ++k) {
-      const uint32_t wl = static_cast<uint32_t>(std::min<uint64_t>(m + 64, L));
+      const uint32_t wl = static_cast<uint32_t>(std::min<uint64_t>(mlen[k / nw] + 64, L));
       cln[k] = wl;
       cst[k] = (L > wl) ? next() % (L - wl) : 0;
     }
@@ -1503,8 +1509,8 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
       o.rows = sh[1];
       float tot = 0;
       bool ok = true;
-      for (int rep = 0; rep < 4 && ok; ++rep) {
-        if (rep == 1) cudaEventRecord(e0, b->stream);
+      for (int rep = 0; rep < 7 && ok; ++rep) {
+        if (rep == 2) cudaEventRecord(e0, b->stream);
         ok = batch_run_async(s, b, sp, &o) == SR_OK;
       }
       cudaEventRecord(e1, b->stream);
@@ -1512,7 +1518,7 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
       if (!ok) continue;
       cudaEventElapsedTime(&tot, e0, e1);
       if (verbose)
-        fprintf(stderr, "sr_tune bin<=%u lanes %u rows %u: %.3f ms for 3 runs\n", m, sh[0], sh[1], tot);
+        fprintf(stderr, "sr_tune bin<=%u lanes %u rows %u: %.3f ms for 5 runs\n", m, sh[0], sh[1], tot);
       if (tot < best_ms) {
         best_ms = tot;
         pick = TuneBin{m, sh[0], sh[1]};

@@ -284,7 +284,10 @@ def cal_finder_bench(sr, scale):
                         "overlapping seeds, cal_limit 1024, merge 32, pad 32",
             "host_reads_per_s": round(n / t_host, 1), "host_threads": os.cpu_count(),
             "device_reads_per_s": round(n / t_dev, 1), "device_ms": round(1e3 * t_dev, 2),
-            "windows_per_read": round(len(d["c_ref"]) / max(n, 1), 3), "identical": bool(same),
+            "windows_per_read": round(len(d["c_ref"]) / max(n, 1), 3),
+            "windows_per_read_quantiles": {q: int(np.quantile(np.diff(np.asarray(d["cand_off"], np.int64)), v))
+                                           for q, v in [("p50", 0.5), ("p90", 0.9), ("p99", 0.99), ("max", 1.0)]},
+            "identical": bool(same),
             "index_build_s": round(t_index, 2)}
 
 

@@ -396,6 +396,15 @@ sr_status sr_align_items_noalloc(sr_session* s, const char* d_bases, const uint6
  * attribute), used as the integer roofline denominator. */
 sr_status sr_probe_dpx(double* lane_ops_per_clk_per_sm, double* sm_clock_mhz);
 
+/* Check of the bounded device waits (no counterpart in the paper).  The
+ * extension kernels wait for their window copies on an mbarrier for a bounded
+ * number of polls, after which they record a timeout in the batch's status word
+ * and return (the batch then fails with SR_ETIMEOUT).  This probe runs that
+ * polling on a barrier that receives its arrival (arrive != 0: SR_OK) or never
+ * does (arrive == 0: SR_ETIMEOUT after poll_limit polls, 1..2^24, else
+ * SR_EINVAL); the context stays usable either way. */
+sr_status sr_probe_wait(uint32_t poll_limit, uint32_t arrive);
+
 #ifdef __cplusplus
 }
 #endif

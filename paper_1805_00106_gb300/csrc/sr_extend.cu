@@ -165,6 +165,37 @@ __global__ void k_probe_dpx(uint32_t* out, unsigned long long* cycles, uint32_t 
   if (threadIdx.x == 0) cycles[blockIdx.x] = static_cast<unsigned long long>(clock64() - t0);
 }
 
+// ---------------------------------------------------------------- bounded wait probe
+// The window copies of the extension kernels complete on an mbarrier that a
+// kernel polls a bounded number of times before it records kStTimeout and
+// returns.  This probe runs the same polling on a barrier that gets its one
+// arrival (arrive = 1) or none (a flag nothing sets), so a test can check that
+// a wait that never completes ends as a status, not a hang.
+__global__ void k_probe_wait(uint32_t poll_limit, int arrive, uint32_t* status) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    bool done = false;
+    for (uint32_t it = 0; it < poll_limit && !done; ++it) done = mbar_try_wait(&bar, 0);
+    if (!done) atomicOr(status, kStTimeout);
+  }
+}
+
+int probe_wait(uint32_t poll_limit, int arrive, uint32_t* status_out) {
+  uint32_t* d = nullptr;
+  if (cudaMalloc(&d, 4) != cudaSuccess) return -1;
+  cudaMemset(d, 0, 4);
+  k_probe_wait<<<1, 32>>>(poll_limit, arrive, d);
+  cudaError_t e = cudaMemcpy(status_out, d, 4, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess && cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int probe_dpx(double* lane_ops_per_clk_per_sm, double* clk_mhz) {
   int dev = 0, nsm = 0, clk_khz = 0;
   cudaGetDevice(&dev);

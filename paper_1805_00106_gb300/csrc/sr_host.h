@@ -3,6 +3,7 @@
 #include <stdint.h>
 
 #include "../../include/sr.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace sr {
 // records a thread-local message for sr_last_error() and returns `st`
@@ -26,4 +27,11 @@ struct IndexTables {
 IndexTables index_tables(const sr_index* idx);
 // a zeroed sr_results whose arrays the caller allocates with malloc (released by sr_results_free)
 sr_results* results_alloc();
+// NVTX range over a host stage (visible in profiler timelines; free without a tool attached)
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
 }  // namespace sr

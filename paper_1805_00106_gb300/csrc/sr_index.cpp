@@ -52,6 +52,7 @@ using namespace sr;
 
 extern "C" sr_status sr_index_build(const char* seq, uint64_t len, const sr_index_params* params,
                                     sr_index** out) {
+  Trace trace_("sr_index_build");
   if (!seq || !out) return set_error(SR_EINVAL, "sr_index_build: null argument");
   *out = nullptr;
   sr_index_params p{};
@@ -393,6 +394,7 @@ extern "C" void sr_cand_list_free(sr_cand_list* l) {
 
 extern "C" sr_status sr_candidates(const sr_index* const* idx, uint32_t n_refs, const sr_reads* reads,
                                    const sr_cand_params* params, sr_cand_list** out) {
+  Trace trace_("sr_candidates");
   if (!idx || !reads || !out || n_refs == 0 || n_refs > SR_MAX_REFS)
     return set_error(SR_EINVAL, "sr_candidates: bad arguments");
   *out = nullptr;

@@ -227,5 +227,7 @@ bool extend_config_supported(uint32_t lanes, uint32_t rows);
 // the built (lanes, rows) shapes; returns how many there are
 int extend_shapes(uint32_t* lanes, uint32_t* rows, int cap);
 int probe_dpx(double* lane_ops_per_clk_per_sm, double* clk_mhz);
+// bounded mbarrier wait with (arrive = 1) or without its arrival; status word out
+int probe_wait(uint32_t poll_limit, int arrive, uint32_t* status_out);
 
 }  // namespace sr

@@ -129,6 +129,7 @@ void format_read(const sr_reads* reads, const sr_results* res, const sr_sam_opts
 
 extern "C" sr_status sr_write_sam(const sr_reads* reads, const sr_results* res, const uint64_t* ref_lens,
                                   const sr_sam_opts* opts, const char* path) {
+  Trace trace_("sr_write_sam");
   if (!reads || !res || !path || (res->n_refs && !ref_lens))
     return set_error(SR_EINVAL, "sr_write_sam: null argument");
   if (reads->n_reads != res->n_reads) return set_error(SR_EINVAL, "sr_write_sam: reads and results differ");

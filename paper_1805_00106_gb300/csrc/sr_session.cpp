@@ -343,6 +343,7 @@ extern "C" sr_status sr_batch_stage(sr_session* s, const sr_reads* reads, const 
 
 sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
                                    void* cuda_stream, bool check_budget, sr_batch** out) {
+  Trace trace_("sr_batch_stage");
   if (!s || !reads || !cands || !out) return set_error(SR_EINVAL, "sr_batch_stage: null argument");
   *out = nullptr;
   const uint32_t n = reads->n_reads;
@@ -741,6 +742,7 @@ static bool same_opts(const sr_align_opts& a, const sr_align_opts& b) {
 }
 
 sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp, const sr_align_opts* opts) {
+  Trace trace_("sr_batch_run");
   if (!s || !b || b->s != s) return set_error(SR_EINVAL, "sr_batch_run: bad session/batch");
   sr_status st = check_score(sp);
   if (st != SR_OK) return st;
@@ -953,6 +955,7 @@ extern "C" void sr_results_free(sr_results* r) {
 }
 
 extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out) {
+  Trace trace_("sr_batch_fetch");
   if (!s || !b || !out) return set_error(SR_EINVAL, "sr_batch_fetch: null argument");
   if (!b->ran) return set_error(SR_EINVAL, "sr_batch_fetch: batch has not run");
   *out = nullptr;
@@ -1094,6 +1097,7 @@ extern "C" sr_status sr_session_attach_index(sr_session* s, const sr_index* cons
 
 extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, const sr_cand_params* params,
                                           sr_cand_list** out) {
+  Trace trace_("sr_candidates_device");
   if (!s || !reads || !out) return set_error(SR_EINVAL, "sr_candidates_device: null argument");
   *out = nullptr;
   if (s->didx.n_refs == 0) return set_error(SR_EINVAL, "sr_candidates_device: no index attached to the session");
@@ -1276,6 +1280,7 @@ extern "C" void sr_report_free(sr_report* rep) {
 }
 
 extern "C" sr_status sr_batch_report(sr_session* s, sr_batch* b, uint32_t kind, uint32_t n_best, sr_report** out) {
+  Trace trace_("sr_batch_report");
   if (!s || !b || !out || b->s != s) return set_error(SR_EINVAL, "sr_batch_report: bad argument");
   *out = nullptr;
   if (!b->ran) return set_error(SR_EINVAL, "sr_batch_report: batch has not run");
@@ -1354,6 +1359,7 @@ extern "C" sr_status sr_batch_report(sr_session* s, sr_batch* b, uint32_t kind, 
 
 extern "C" sr_status sr_align_batch(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
                                     const sr_score_params* sp, const sr_align_opts* opts, sr_results** out) {
+  Trace trace_("sr_align_batch");
   if (!out) return set_error(SR_EINVAL, "sr_align_batch: null out");
   *out = nullptr;
   sr_batch* b = nullptr;
@@ -1442,6 +1448,7 @@ extern "C" sr_status sr_tune_load(const char* path) {
 // 6 windows of length m + 64 each at random positions of reference 0) and keep
 // the fastest.
 extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t sample_reads) {
+  Trace trace_("sr_tune");
   if (!s) return set_error(SR_EINVAL, "sr_tune: null session");
   sr_status st = check_score(sp);
   if (st != SR_OK) return st;
@@ -1531,6 +1538,14 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
   cudaEventDestroy(e1);
   if (st != SR_OK) return st;
   tune_set_bins(cur);
+  return SR_OK;
+}
+
+extern "C" sr_status sr_probe_wait(uint32_t poll_limit, uint32_t arrive) {
+  if (poll_limit == 0 || poll_limit > (1u << 24)) return set_error(SR_EINVAL, "sr_probe_wait: poll_limit 1..2^24");
+  uint32_t st = 0;
+  if (probe_wait(poll_limit, arrive ? 1 : 0, &st) != 0) return cuda_error("sr_probe_wait", cudaGetLastError());
+  if (st & kStTimeout) return set_error(SR_ETIMEOUT, "sr_probe_wait: the bounded wait ran out (status word)");
   return SR_OK;
 }
 

@@ -163,6 +163,7 @@ def lib():
             "sr_tune_get": ([P, P, P, P, C.c_uint32], C.c_int32),
             "sr_tune_set": ([C.c_uint32, P, P, P], C.c_int32),
             "sr_probe_dpx": ([P, P], C.c_int32),
+            "sr_probe_wait": ([C.c_uint32, C.c_uint32], C.c_int32),
             "sr_align_items_noalloc": ([P, P, P, C.c_uint32, P, P, P, P, P, C.c_uint64,
                                         C.POINTER(ScoreParams), P, P, P], C.c_int32),
         }
@@ -555,3 +556,8 @@ def probe_dpx():
     r, mhz = C.c_double(), C.c_double()
     _check(lib().sr_probe_dpx(C.byref(r), C.byref(mhz)))
     return r.value, mhz.value
+
+
+def probe_wait(poll_limit=1000, arrive=False):
+    """Run the bounded device wait on a barrier that does (or never does) complete."""
+    _check(lib().sr_probe_wait(poll_limit, 1 if arrive else 0))

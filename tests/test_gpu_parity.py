@@ -262,3 +262,39 @@ def test_tiny_random_reads_both_readouts(sr, mode):
     for sp in [(2, 3, 5, 2), (3, 2, 2, 1), (1, 1, 1, 1), (2, 3, 0, 2)]:
         o = oracle_run(w, sp=sp, mode=mode)
         _check(gpu_run(s, w, sp=sp, mode=mode), o)
+
+
+def test_bounded_device_wait_times_out_as_a_status(sr):
+    """A device wait on a barrier that nothing completes ends after its poll
+    limit as SR_ETIMEOUT (status word), and the context stays usable."""
+    sr.probe_wait(poll_limit=1000, arrive=True)
+    with pytest.raises(sr.SrError) as e:
+        sr.probe_wait(poll_limit=1000, arrive=False)
+    assert e.value.status == sr.SR_ETIMEOUT
+    w = S.workload("c1", scale=0.005, seed=43)
+    _check(gpu_run(_session(sr, w), w), oracle_run(w))
+
+
+def test_outputs_identical_across_runs_and_shapes(sr):
+    """Determinism of the queues and atomics: 20 graph replays of one batch give
+    byte-identical outputs, and so do other kernel shapes and the plain engine."""
+    import hashlib
+    w = S.workload("c2", scale=0.0005, seed=47)
+    s = _session(sr, w)
+    b = s.stage(w["bases"], w["read_off"], w["cand_off"], w["c_ref"], w["c_strand"], w["c_start"], w["c_len"])
+
+    def digest(res):
+        h = hashlib.sha256()
+        for k in ["item_score", "item_end", "best", "best_per_ref", "cigar"]:
+            h.update(np.ascontiguousarray(res[k]).tobytes())
+        return h.hexdigest()
+
+    ref = None
+    for _ in range(20):
+        b.run(sr.score_params(*SP), sr.align_opts())
+        d = digest(b.fetch())
+        ref = ref or d
+        assert d == ref
+    for opts in [dict(lanes=16, rows=16), dict(lanes=32, rows=8), dict(engine=1)]:
+        b.run(sr.score_params(*SP), sr.align_opts(**opts))
+        assert digest(b.fetch()) == ref

@@ -60,10 +60,11 @@ struct ExtArgs {
 // kernel shapes (lanes per alignment, rows per lane) instantiated for the batched
 // engine; the plain engine uses the 256-row shapes only
 #define SR_SHAPES(X)                                                                         \
-  X(4, 16) X(4, 20) X(4, 24) X(4, 28) X(4, 32) X(8, 8) X(8, 10) X(8, 12) X(8, 14) X(8, 16)   \
-      X(8, 18) X(8, 20) X(8, 22) X(8, 24) X(8, 26) X(8, 28) X(8, 30) X(8, 32) X(16, 5)      \
-      X(16, 6) X(16, 7) X(16, 8) X(16, 9) X(16, 10) X(16, 11) X(16, 12) X(16, 13) X(16, 14) \
-      X(16, 15) X(16, 16) X(32, 4) X(32, 5) X(32, 6) X(32, 7) X(32, 8)
+  X(4, 16) X(4, 20) X(4, 24) X(4, 28) X(4, 32) X(8, 8) X(8, 10) X(8, 12) X(8, 13) X(8, 14)   \
+      X(8, 15) X(8, 16) X(8, 17) X(8, 18) X(8, 19) X(8, 20) X(8, 21) X(8, 22) X(8, 23)      \
+      X(8, 24) X(8, 25) X(8, 26) X(8, 27) X(8, 28) X(8, 29) X(8, 30) X(8, 31) X(8, 32)      \
+      X(16, 5) X(16, 6) X(16, 7) X(16, 8) X(16, 9) X(16, 10) X(16, 11) X(16, 12) X(16, 13)  \
+      X(16, 14) X(16, 15) X(16, 16) X(32, 4) X(32, 5) X(32, 6) X(32, 7) X(32, 8)
 #define SR_PLAIN_SHAPES(X) X(16, 16) X(32, 8)
 
 // launch the int16 kernel of one shape and readout mode; -1 if the shape is not built

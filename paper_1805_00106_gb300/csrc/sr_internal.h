@@ -21,7 +21,7 @@ constexpr int kMaxWinLen = 512;
 constexpr int kMaxRefs = 16;
 constexpr int kReadWords = 16;     // words per packed read row
 constexpr int kCigarStride = 776;  // CIGAR words reserved per read (>= 3*256 + 4 runs)
-constexpr int kNumBins = 13;       // read-length bins of the batched engine (16-row steps above 64)
+constexpr int kNumBins = 23;       // read-length bins of the batched engine (8-row steps above 96)
 constexpr int kNumClasses = kNumBins + 1;  // + the int32 class
 constexpr int kI32Class = kNumBins;
 constexpr int kKeysPerClass = kMaxWinLen;  // sort key = class*512 + (512 - n)

@@ -36,10 +36,11 @@ namespace {
 constexpr uint32_t kNaMaxReads = SR_NOALLOC_MAX_READS;
 constexpr uint32_t kNaMaxItems = SR_NOALLOC_MAX_ITEMS;
 // word layout of the scratch array
-constexpr size_t kNaQueue = 0;                              // kNumClasses + 8 counters
-constexpr size_t kNaRange = 32;                             // 2 * kNumClasses
-constexpr size_t kNaStatus = 64;                            // 1 word
-constexpr size_t kNaRlen = 128;                             // kNaMaxReads
+constexpr size_t kNaUp32(size_t x) { return (x + 31) / 32 * 32; }
+constexpr size_t kNaQueue = 0;                                          // kNumClasses + 8 counters
+constexpr size_t kNaRange = kNaUp32(sr::kNumClasses + 8);               // 2 * kNumClasses
+constexpr size_t kNaStatus = kNaUp32(kNaRange + 2 * sr::kNumClasses);   // 1 word
+constexpr size_t kNaRlen = kNaUp32(kNaStatus + 1) + 64;                 // kNaMaxReads
 constexpr size_t kNaRpack = kNaRlen + kNaMaxReads;          // kNaMaxReads * 16
 constexpr size_t kNaItemRead = kNaRpack + static_cast<size_t>(kNaMaxReads) * sr::kReadWords;
 constexpr size_t kNaWords = kNaItemRead + kNaMaxItems;      // about 3.3 MiB in all

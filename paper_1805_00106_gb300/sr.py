@@ -539,9 +539,9 @@ class Session:
 
 def tune_get():
     n = C.c_uint32()
-    up, la, ro = (np.zeros(16, np.uint32) for _ in range(3))
-    _check(lib().sr_tune_get(C.byref(n), _p(up), _p(la), _p(ro), 16))
-    k = n.value
+    up, la, ro = (np.zeros(64, np.uint32) for _ in range(3))
+    _check(lib().sr_tune_get(C.byref(n), _p(up), _p(la), _p(ro), 64))
+    k = min(n.value, 64)
     return [(int(up[i]), int(la[i]), int(ro[i])) for i in range(k)]
 
 

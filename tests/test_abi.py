@@ -54,11 +54,13 @@ def test_binding_has_no_compute_fallback():
 def test_tune_table_roundtrip(tmp_path):
     from paper_1805_00106_gb300 import sr
     bins = sr.tune_get()
-    assert len(bins) == 13 and bins[-1][0] == 256
+    assert len(bins) >= 8 and bins[-1][0] == 256
+    assert all(b[1] * b[2] >= b[0] for b in bins)
     p = str(tmp_path / "tune.txt")
     sr.lib().sr_tune_save(p.encode())
-    new = [(64, 4, 16), (80, 8, 10), (96, 8, 12), (112, 8, 14), (128, 8, 16), (144, 8, 18), (160, 16, 10),
-           (176, 8, 22), (192, 16, 12), (208, 8, 26), (224, 16, 14), (240, 8, 30), (256, 32, 8)]
+    # another valid table: every bin on a 32-lane shape that covers it
+    new = [(b[0], 32, max(4, -(-b[0] // 32))) for b in bins]
+    new = [(u, g, r if r in (4, 5, 6, 7, 8) else 8) for u, g, r in new]
     sr.tune_set(new)
     assert sr.tune_get() == new
     assert sr.lib().sr_tune_load(p.encode()) == 0

@@ -54,11 +54,9 @@ def test_reverse_strand_reads(sr):
     _check(gpu_run(s, w), oracle_run(w))
 
 
-@pytest.mark.parametrize("shape", [(4, 16), (4, 20), (4, 24), (4, 28), (4, 32), (8, 8), (8, 10), (8, 12),
-                                   (8, 14), (8, 16), (8, 18), (8, 20), (8, 22), (8, 24), (8, 26), (8, 28),
-                                   (8, 30), (8, 32), (16, 5), (16, 6), (16, 7), (16, 8), (16, 9), (16, 10),
-                                   (16, 11), (16, 12), (16, 13), (16, 14), (16, 15), (16, 16), (32, 4),
-                                   (32, 5), (32, 6), (32, 7), (32, 8)])
+@pytest.mark.parametrize("shape", [(4, 16), (4, 20), (4, 24), (4, 28), (4, 32)] +
+                         [(8, r) for r in (8, 10) + tuple(range(12, 33))] +
+                         [(16, r) for r in range(5, 17)] + [(32, r) for r in range(4, 9)])
 def test_forced_kernel_shapes(sr, shape):
     g_, r_ = shape
     cap = g_ * r_

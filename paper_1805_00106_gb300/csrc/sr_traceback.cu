@@ -232,13 +232,17 @@ __global__ void __launch_bounds__(32) k_traceback(TbArgs a, const uint32_t* list
 // of read B one step later, so every lane computes one cell per step, of A and B
 // in turn.  A cell's left neighbour (lane k-1, same row) and upper neighbour
 // (lane k+1, row above) belong to the same read and were computed at the
-// previous step, its diagonal neighbour (itself, row above) two steps before:
-// one shuffle each, no dependency chain within a step.  Each cell stores 4 bits
-// (H came from the diagonal, H equals E, E opened, F opened); read A's in the low
-// and read B's in the high nibble of one byte per (row, lane).  The walk jumps
-// along runs of diagonal steps, checking SEG cells per iteration with a prefix
-// sum of their scores.
+// previous step, its diagonal neighbour (itself, row above) two steps before.
+// Each cell computes the E of its right neighbour and the F of its lower one
+// (open from its H or extend its own gap value), so a step takes two shuffles
+// and no dependency chain.  Each cell stores 4 bits (H came from the diagonal,
+// H equals E, it opened its right neighbour's E, it opened its lower neighbour's
+// F); read A's in the low and read B's in the high nibble of one byte per (row,
+// lane).  The walk jumps along runs of diagonal steps, checking SEG cells per
+// iteration with a prefix sum of their scores; a gap step reads the open flag
+// at the cell it steps to.
 constexpr int kTbWarps = 2;  // static shared memory stays below 48 KB per block
+constexpr int kTbRowPad = 16;  // rows before row 1 / after row 256 a lane may reach (SEG / 2)
 constexpr uint32_t kNoRow = 0xffffffffu;
 
 struct TbRead {
@@ -383,11 +387,6 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const WalkRead& t, uint
       const uint32_t nib0 = __shfl_sync(gmask, nib, 0, WG);
       state = (nib0 & 2u) ? 1 : 2;
     } else {
-      if (i < 1 || j < 1) {
-        bad = true;
-        break;
-      }
-      const uint32_t nib = (dirs[(i - 1) * SEG + kk] >> shift) & 15u;
       const uint32_t op = state == 1 ? 2u : 1u;  // D : I
       if (cur_op == op) {
         ++cur_len;
@@ -401,9 +400,6 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const WalkRead& t, uint
         cur_op = op;
         cur_len = 1;
       }
-      const bool open = state == 1 ? (nib & 4u) : (nib & 8u);
-      h += open ? goe : a.ge;
-      if (open) state = 0;
       if (op == 2u) {
         --j;
         --kk;
@@ -411,6 +407,15 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const WalkRead& t, uint
         --i;
         ++kk;
       }
+      // the cell the gap came from holds whether it was opened there
+      if (i < 1 || j < 1 || kk < 0 || kk >= t.w) {
+        bad = true;
+        break;
+      }
+      const uint32_t nib = (dirs[(i - 1) * SEG + kk] >> shift) & 15u;
+      const bool open = op == 2u ? (nib & 4u) : (nib & 8u);
+      h += open ? goe : a.ge;
+      if (open) state = 0;
     }
   }
   if (k == 0) {
@@ -455,7 +460,9 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
   constexpr int kQW = PACKED ? kReadWords : 1;   // packed words per read
   constexpr int kRW = PACKED ? kWinWords : 1;
   constexpr int kSlots = kTbWarps * NSEG * 2;     // reads resident per block
-  __shared__ uint8_t dirs_s[kTbWarps][NSEG][kMaxReadLen * SEG];
+  // direction bytes of rows 1 - kTbRowPad .. kMaxReadLen + kTbRowPad: the
+  // wavefront's first and last steps run lanes above row 1 and below row m
+  __shared__ uint8_t dirs_s[kTbWarps][NSEG][(kMaxReadLen + 2 * kTbRowPad) * SEG];
   __shared__ uint8_t qbyte_s[kSlots * kQB];
   __shared__ uint8_t rbyte_s[kSlots * kRB];
   __shared__ uint32_t qword_s[kSlots * kQW];
@@ -467,10 +474,9 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
   const int seg = lane / SEG;
   const int k = lane % SEG;
   const uint32_t seg_mask = SEG == 32 ? FULL : (((1u << SEG) - 1u) << (seg * SEG));
-  uint8_t* dirs = dirs_s[warp][seg];
+  uint8_t* dirs = dirs_s[warp][seg] + kTbRowPad * SEG;
   const Codes<PACKED> cd{qbyte_s, rbyte_s, qword_s, rword_s};
   const int32_t goe = a.go + a.ge;
-  constexpr int32_t NEG = -(1 << 28);
   const uint32_t begin = range[0];
   const uint32_t count = range[1] - begin;
   constexpr uint32_t kPerWarp = 2 * NSEG;
@@ -526,13 +532,12 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(max(stA, stB) + 1)));
     const int p = k & 1;
     // per half-step: the rows where this lane's diagonal is inside the window
-    // [rlo, rlo + cnt), the code offsets of row 1 and column 1, the row where
-    // it crosses the end column (or -1), the top border flag and the score
+    // [rlo, rlo + cnt), the code offsets of row i and column i + c (offset + i),
+    // the row where it crosses the end column, the lower band edge flag
     struct Sub {
-      uint32_t rlo, cnt, qo, ro;
-      int icr;
+      uint32_t rlo, cnt, qa, ra;
+      int c, icr;
       bool bd;
-      int32_t S;
     };
     auto sub_of = [&](const TbRead& x, int X) {
       Sub u;
@@ -542,89 +547,80 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
       u.rlo = static_cast<uint32_t>(lo);
       u.cnt = on ? static_cast<uint32_t>(hi - lo + 1) : 0u;
       const int sl = slot(seg, X);
-      // offsets such that row i, column i + c index codes (i - 1) and (i - 1 + c)
-      u.qo = static_cast<uint32_t>(sl * (PACKED ? kQW : kQB));
-      u.ro = static_cast<uint32_t>(sl * (PACKED ? kRW : kRB));
+      // packed: the slot's word offsets; bytes: offsets that index codes by row
+      u.qa = static_cast<uint32_t>(PACKED ? sl * kQW : sl * kQB - 1);
+      u.ra = static_cast<uint32_t>(PACKED ? sl * kRW : sl * kRB + c - 1);
+      u.c = c;
       const int ir = static_cast<int>(x.jstar) - c;
-      u.icr = (on && ir >= x.ilo && ir >= lo && ir <= hi) ? ir : -1;
+      u.icr = (on && ir >= x.ilo && ir >= lo && ir <= hi) ? ir : -(1 << 20);
       u.bd = k + 1 >= x.w;
-      u.S = x.S;
       return u;
     };
-    const int c0 = (p ? rd[1].dlo : rd[0].dlo) + k, c1 = (p ? rd[0].dlo : rd[1].dlo) + k;
     const Sub s0 = p ? sub_of(rd[1], 1) : sub_of(rd[0], 0);
     const Sub s1 = p ? sub_of(rd[0], 0) : sub_of(rd[1], 1);
-    // one cell of row i: neighbours left (hl, el), above (hu, fu), diagonal hd
-    auto cell = [&](const Sub& sb, int c, int i, int32_t hl, int32_t el, int32_t hu, int32_t fu, int32_t hd,
-                    int32_t& nH, int32_t& nE, int32_t& nF, uint32_t& nib, uint32_t& ic) {
-      nH = 0;
-      nE = NEG;
-      nF = NEG;
-      nib = 0;
+    // One cell of row i.  E and F arrive complete from the left and upper
+    // neighbours, which computed them from their own cells (gap opened from
+    // their H or extended from their own gap value), and this cell does the same
+    // for its right (En) and lower (Fn) neighbour.  Cells outside the window
+    // score a mismatch: with the top and left borders at H = 0 and gap values at
+    // most -(go+ge) they keep H = 0, which is the border itself; cells right of
+    // j* or below the last row only feed cells that are never read.  The 4 bits:
+    // H came from the diagonal, H equals E, this cell opened its right
+    // neighbour's E, this cell opened its lower neighbour's F.
+    auto cell = [&](const Sub& sb, int i, int32_t E, int32_t F, int32_t& hd, int32_t& En, int32_t& Fn,
+                    uint32_t& nib, int32_t& hcr) {
+      bool eq = false;
       if (static_cast<uint32_t>(i) - sb.rlo < sb.cnt) {
-        const int32_t eo = hl - goe, ee = el - a.ge, fo = hu - goe, fe = fu - a.ge;
-        const int32_t E = max(eo, ee), F = max(fo, fe);
-        const uint32_t i0 = static_cast<uint32_t>(i - 1);
-        const int32_t hs = hd + (cd.match(sb.qo, sb.ro, i0, i0 + static_cast<uint32_t>(c)) ? a.sa : -a.sb);
-        const int32_t H = max(max(0, hs), max(E, F));
-        nib = static_cast<uint32_t>(H == hs) | (static_cast<uint32_t>(H == E) << 1) |
-              (static_cast<uint32_t>(eo >= ee) << 2) | (static_cast<uint32_t>(fo >= fe) << 3);
-        nH = H;
-        nE = E;
-        nF = F;
-        // final-row mode ends in row m even where an earlier row also holds S
-        if (i == sb.icr && H == sb.S) ic = static_cast<uint32_t>(i);
+        const uint32_t ui = static_cast<uint32_t>(i);
+        if (PACKED)
+          eq = cd.match(sb.qa, sb.ra, ui - 1u, ui - 1u + static_cast<uint32_t>(sb.c));
+        else
+          eq = qbyte_s[sb.qa + ui] == rbyte_s[sb.ra + ui];
       }
+      const int32_t hs = hd + (eq ? a.sa : -a.sb);
+      const int32_t H = max(max(hs, 0), max(E, F));
+      const int32_t g = H - goe, ee = E - a.ge, fe = F - a.ge;
+      En = max(g, ee);
+      Fn = max(g, fe);
+      nib = static_cast<uint32_t>(H == hs) | (static_cast<uint32_t>(H == E) << 1) |
+            (static_cast<uint32_t>(g >= ee) << 2) | (static_cast<uint32_t>(g >= fe) << 3);
+      if (i == sb.icr) hcr = H;
+      hd = H;
     };
-    // cells of the previous pair of steps: half-step 0 (Ha, Ea, Fa) and 1 (Hb, Eb, Fb)
-    int32_t Ha = 0, Ea = NEG, Fa = NEG, Hb = 0, Eb = NEG, Fb = NEG;
-    uint32_t pend = 0, ic0 = kNoRow, ic1 = kNoRow;
+    // what each half-step sent last: gap values for the neighbours, own H
+    int32_t Ha = 0, Hb = 0, Ena = -goe, Fna = -goe, Enb = -goe, Fnb = -goe;
+    int32_t hcr0 = -1, hcr1 = -1;
+    uint32_t pend = 0;
     int ia = 1 - ((k + p) >> 1);  // row of half-step 0 in this pair
-    for (int t = 0; t < nmax; t += 2, ++ia) {
+    uint8_t* drow = dirs + (ia - 1) * SEG + k;  // this lane's byte of row ia
+    for (int t = 0; t < nmax; t += 2, ++ia, drow += SEG) {
       uint32_t nib;
       {
-        int32_t hl = __shfl_up_sync(FULL, Hb, 1, SEG);
-        int32_t el = __shfl_up_sync(FULL, Eb, 1, SEG);
-        int32_t hu = __shfl_down_sync(FULL, Hb, 1, SEG);
-        int32_t fu = __shfl_down_sync(FULL, Fb, 1, SEG);
-        if (k == 0) {
-          hl = 0;
-          el = NEG;
-        }
-        if (s0.bd) {
-          hu = 0;
-          fu = NEG;
-        }
-        cell(s0, c0, ia, hl, el, hu, fu, Ha, Ha, Ea, Fa, nib, ic0);
+        int32_t E = __shfl_up_sync(FULL, Enb, 1, SEG);
+        int32_t F = __shfl_down_sync(FULL, Fnb, 1, SEG);
+        if (k == 0) E = -goe;
+        if (s0.bd) F = -goe;
+        cell(s0, ia, E, F, Ha, Ena, Fna, nib, hcr0);
         // read A's nibble of a row waits for read B's of the same row
-        if (p) {
-          if (ia >= 1 && ia <= kMaxReadLen) dirs[(ia - 1) * SEG + k] = static_cast<uint8_t>(pend | (nib << 4));
-        } else {
+        if (p)
+          *drow = static_cast<uint8_t>(pend | (nib << 4));
+        else
           pend = nib;
-        }
       }
       {
-        int32_t hl = __shfl_up_sync(FULL, Ha, 1, SEG);
-        int32_t el = __shfl_up_sync(FULL, Ea, 1, SEG);
-        int32_t hu = __shfl_down_sync(FULL, Ha, 1, SEG);
-        int32_t fu = __shfl_down_sync(FULL, Fa, 1, SEG);
-        if (k == 0) {
-          hl = 0;
-          el = NEG;
-        }
-        if (s1.bd) {
-          hu = 0;
-          fu = NEG;
-        }
-        const int ib = ia + p;
-        cell(s1, c1, ib, hl, el, hu, fu, Hb, Hb, Eb, Fb, nib, ic1);
-        if (p) {
+        int32_t E = __shfl_up_sync(FULL, Ena, 1, SEG);
+        int32_t F = __shfl_down_sync(FULL, Fna, 1, SEG);
+        if (k == 0) E = -goe;
+        if (s1.bd) F = -goe;
+        cell(s1, ia + p, E, F, Hb, Enb, Fnb, nib, hcr1);
+        if (p)
           pend = nib;
-        } else if (ib >= 1 && ib <= kMaxReadLen) {
-          dirs[(ib - 1) * SEG + k] = static_cast<uint8_t>(pend | (nib << 4));
-        }
+        else
+          *drow = static_cast<uint8_t>(pend | (nib << 4));
       }
     }
+    const uint32_t ic0 = (s0.icr > 0 && hcr0 == (p ? rd[1].S : rd[0].S)) ? static_cast<uint32_t>(s0.icr) : kNoRow;
+    const uint32_t ic1 = (s1.icr > 0 && hcr1 == (p ? rd[0].S : rd[1].S)) ? static_cast<uint32_t>(s1.icr) : kNoRow;
     uint32_t icA = p ? ic1 : ic0, icB = p ? ic0 : ic1;
 #pragma unroll
     for (int off = SEG / 2; off > 0; off >>= 1) {
@@ -646,7 +642,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
         for (int X = 0; X < 2; ++X) {
           const int sl = slot(sg, X);
           const WalkRead wr = walk_s[sl];
-          tb_walk<SEG, 32, PACKED>(a, wr, iend_s[sl], X ? 4 : 0, dirs_s[warp][sg], cd,
+          tb_walk<SEG, 32, PACKED>(a, wr, iend_s[sl], X ? 4 : 0, dirs_s[warp][sg] + kTbRowPad * SEG, cd,
                                    static_cast<uint32_t>(sl * kQW), static_cast<uint32_t>(sl * kRW) +
                                    0u, lane, FULL, 0);
           __syncwarp();

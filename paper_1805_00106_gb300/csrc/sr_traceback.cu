@@ -460,9 +460,9 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
   constexpr int kQW = PACKED ? kReadWords : 1;   // packed words per read
   constexpr int kRW = PACKED ? kWinWords : 1;
   constexpr int kSlots = kTbWarps * NSEG * 2;     // reads resident per block
-  // direction bytes of rows 1 - kTbRowPad .. kMaxReadLen + kTbRowPad: the
+  // direction bytes of rows 1 - kTbRowPad .. kMaxReadLen + kTbRowPad + 1: the
   // wavefront's first and last steps run lanes above row 1 and below row m
-  __shared__ uint8_t dirs_s[kTbWarps][NSEG][(kMaxReadLen + 2 * kTbRowPad) * SEG];
+  __shared__ uint8_t dirs_s[kTbWarps][NSEG][(kMaxReadLen + 2 * kTbRowPad + 1) * SEG];
   __shared__ uint8_t qbyte_s[kSlots * kQB];
   __shared__ uint8_t rbyte_s[kSlots * kRB];
   __shared__ uint32_t qword_s[kSlots * kQW];
@@ -569,13 +569,15 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     // neighbour's E, this cell opened its lower neighbour's F.
     auto cell = [&](const Sub& sb, int i, int32_t E, int32_t F, int32_t& hd, int32_t& En, int32_t& Fn,
                     uint32_t& nib, int32_t& hcr) {
+      // byte codes: loads from index 0 outside the window instead of a branch
       bool eq = false;
-      if (static_cast<uint32_t>(i) - sb.rlo < sb.cnt) {
-        const uint32_t ui = static_cast<uint32_t>(i);
-        if (PACKED)
-          eq = cd.match(sb.qa, sb.ra, ui - 1u, ui - 1u + static_cast<uint32_t>(sb.c));
-        else
-          eq = qbyte_s[sb.qa + ui] == rbyte_s[sb.ra + ui];
+      const uint32_t ui = static_cast<uint32_t>(i);
+      const bool in = ui - sb.rlo < sb.cnt;
+      if (PACKED) {
+        if (in) eq = cd.match(sb.qa, sb.ra, ui - 1u, ui - 1u + static_cast<uint32_t>(sb.c));
+      } else {
+        const uint32_t qi = in ? sb.qa + ui : 0u, ri = in ? sb.ra + ui : 0u;
+        eq = in & (qbyte_s[qi] == rbyte_s[ri]);
       }
       const int32_t hs = hd + (eq ? a.sa : -a.sb);
       const int32_t H = max(max(hs, 0), max(E, F));
@@ -601,11 +603,13 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
         if (k == 0) E = -goe;
         if (s0.bd) F = -goe;
         cell(s0, ia, E, F, Ha, Ena, Fna, nib, hcr0);
-        // read A's nibble of a row waits for read B's of the same row
-        if (p)
-          *drow = static_cast<uint8_t>(pend | (nib << 4));
-        else
-          pend = nib;
+        // A row's byte is read A's nibble (low) and read B's (high).  Every
+        // half-step stores the byte of its row with the other read's last
+        // nibble; the half-step that runs read B writes it last, and the
+        // earlier store of read A's half-step is overwritten (lanes with p = 1
+        // run read A one row ahead, so theirs goes to the next row).
+        *drow = static_cast<uint8_t>(pend + (nib << 4));
+        pend = nib;
       }
       {
         int32_t E = __shfl_up_sync(FULL, Ena, 1, SEG);
@@ -613,10 +617,8 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
         if (k == 0) E = -goe;
         if (s1.bd) F = -goe;
         cell(s1, ia + p, E, F, Hb, Enb, Fnb, nib, hcr1);
-        if (p)
-          pend = nib;
-        else
-          *drow = static_cast<uint8_t>(pend | (nib << 4));
+        drow[p ? SEG : 0] = static_cast<uint8_t>(pend + (nib << 4));
+        pend = nib;
       }
     }
     const uint32_t ic0 = (s0.icr > 0 && hcr0 == (p ? rd[1].S : rd[0].S)) ? static_cast<uint32_t>(s0.icr) : kNoRow;

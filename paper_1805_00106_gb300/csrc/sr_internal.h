@@ -102,13 +102,13 @@ struct BatchDev {
 
 // traceback routing.  A winner's end row i* is searched inside the band
 // (kTbFlagBand), comes from the extension kernels' winner mode (kTbFlagRow:
-// the band over every possible end row would be wider than 32 diagonals), or is
+// the band over every possible end row would be wider than 64 diagonals), or is
 // found by the full-rectangle kernel (kTbFlagFull: int32-class winners).
 enum : uint8_t { kTbFlagBand = 0, kTbFlagFull = 1, kTbFlagRow = 2 };
-constexpr int kTbBuckets = 7;                        // band <= 1 / 2 / 4 / 8 / 16 / 32 diagonals, full
+constexpr int kTbBuckets = 8;                        // band <= 1 / 2 / 4 / 8 / 16 / 32 / 64 diagonals, full
 constexpr int kTbCodes = kTbBuckets * kMaxReadLen;   // code = bucket * 256 + (256 - last row)
 constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + 8;
-constexpr int kTbMaxBand = 32;
+constexpr int kTbMaxBand = 64;
 
 // Diagonal band of a winner (score S >= 1 ending in column j*) whose end row lies
 // in [ilo, ihi]: every alignment of score S ending at (i, j*) has at most

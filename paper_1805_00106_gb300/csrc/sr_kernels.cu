@@ -241,7 +241,7 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
 // How each read's winner finds its end row for the traceback.  int32-class
 // winners go to the full-rectangle kernel.  Otherwise the band that covers every
 // row able to end the alignment (rows ceil(S / match) .. m in local mode, row m
-// in final-row mode) is searched directly when it is at most 32 diagonals wide;
+// in final-row mode) is searched directly when it is at most 64 diagonals wide;
 // wider ones first get their end row from the extension kernels' winner mode,
 // for which they are compacted per class into `order` (whose class ranges hold
 // at least as many slots).

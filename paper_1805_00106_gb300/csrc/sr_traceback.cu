@@ -3,12 +3,13 @@
 // traceback the paper runs on the host, Sec. 6.4).
 //
 // Most winners are traced by k_tb_wave (below), a banded DP that also finds the
-// end row i*.  Winners whose band is wider than 32 diagonals, and int32-class
-// winners, use k_traceback: one warp per read recomputes the DP of the winning window in
-// exact int32 over rows 1..m and columns 1..j* only (j* = the end column found
-// by the extension kernels; cells right of j* cannot influence the path) with
-// the same systolic sweep (8 rows per lane), and records per cell a 4-bit
-// direction code in shared memory:
+// end row i* (k_tb_wave2 for bands of 33-64 diagonals).  Winners whose band is
+// wider than 64 diagonals, and int32-class winners, use k_traceback: one warp
+// per read recomputes the DP of the winning window in exact int32 over rows
+// 1..m and columns 1..j* only (j* = the end column found by the extension
+// kernels; cells right of j* cannot influence the path) with the same systolic
+// sweep (8 rows per lane), and records per cell a 4-bit direction code in
+// shared memory:
 //   bit 0  E came from opening (H(i,j-1)-(go+ge) >= E(i,j-1)-ge)
 //   bit 1  F came from opening (H(i-1,j)-(go+ge) >= F(i-1,j)-ge)
 //   bit 2  H(i-1,j-1)+s >= E(i,j)
@@ -449,6 +450,74 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const WalkRead& t, uint
   }
 }
 
+// One read's band diagonal q (column = row + c, c = dlo + q) as a lane runs
+// it: the rows where it is inside the window [rlo, rlo + cnt), the code offsets
+// (packed: the slot's word offsets; bytes: offsets that index the codes by
+// row), the row where it crosses the end column, the lower band edge flag.
+struct TbSub {
+  uint32_t rlo, cnt, qa, ra;
+  int c, icr;
+  bool bd;
+};
+
+template <bool PACKED>
+__device__ __forceinline__ TbSub tb_sub(const TbRead& x, int q, uint32_t qslot, uint32_t rslot) {
+  TbSub u;
+  const int c = x.dlo + q;
+  const int lo = max(1, 1 - c), hi = min(x.ihi, static_cast<int>(x.jstar) - c);
+  const bool on = x.has && q < x.w && hi >= lo;
+  u.rlo = static_cast<uint32_t>(lo);
+  u.cnt = on ? static_cast<uint32_t>(hi - lo + 1) : 0u;
+  u.qa = PACKED ? qslot : qslot - 1u;
+  u.ra = PACKED ? rslot : rslot + static_cast<uint32_t>(c - 1);
+  u.c = c;
+  const int ir = static_cast<int>(x.jstar) - c;
+  u.icr = (on && ir >= x.ilo && ir >= lo && ir <= hi) ? ir : -(1 << 20);
+  u.bd = q + 1 >= x.w;
+  return u;
+}
+
+// Whether row i of a diagonal matches, from byte codes; outside the window the
+// codes load from index 0 (no branch) and never match.
+__device__ __forceinline__ bool tb_eq_bytes(const TbSub& sb, int i, const uint8_t* qb, const uint8_t* rb) {
+  const uint32_t ui = static_cast<uint32_t>(i);
+  const bool in = ui - sb.rlo < sb.cnt;
+  const uint32_t qi = in ? sb.qa + ui : 0u, ri = in ? sb.ra + ui : 0u;
+  return in & (qb[qi] == rb[ri]);
+}
+
+// One cell.  E and F arrive complete from the left and upper neighbours, which
+// computed them from their own cells (gap opened from their H or extended from
+// their own gap value), and this cell does the same for its right (En) and
+// lower (Fn) neighbour.  Cells outside the window score a mismatch: with the top
+// and left borders at H = 0 and gap values at most -(go+ge) they keep H = 0,
+// which is the border itself; cells right of j* or below the last row only feed
+// cells that are never read.  Returns the 4 bits: H came from the diagonal, H
+// equals E, this cell opened its right neighbour's E, this cell opened its lower
+// neighbour's F.  hd holds the diagonal's previous H and becomes this one.
+__device__ __forceinline__ uint32_t tb_cell(const TbArgs& a, int32_t goe, bool eq, int32_t E, int32_t F,
+                                            bool cross, int32_t& hd, int32_t& En, int32_t& Fn, int32_t& hcr) {
+  const int32_t hs = hd + (eq ? a.sa : -a.sb);
+  const int32_t H = max(max(hs, 0), max(E, F));
+  const int32_t g = H - goe, ee = E - a.ge, fe = F - a.ge;
+  En = max(g, ee);
+  Fn = max(g, fe);
+  if (cross) hcr = H;
+  hd = H;
+  return static_cast<uint32_t>(H == hs) | (static_cast<uint32_t>(H == E) << 1) |
+         (static_cast<uint32_t>(g >= ee) << 2) | (static_cast<uint32_t>(g >= fe) << 3);
+}
+
+// A read's codes as bytes (query rows up to ihi, window columns up to j*),
+// staged by the lanes k, k + step, ...
+__device__ __forceinline__ void tb_stage_bytes(const TbArgs& a, const TbRead& x, uint8_t* qc, uint8_t* rc,
+                                               uint32_t k, uint32_t step) {
+  const uint32_t* row = a.rpack + static_cast<uint64_t>(x.rd) * kReadWords;
+  for (uint32_t j = k; j < x.jstar; j += step) rc[j] = static_cast<uint8_t>(base_at(x.ref, x.ws + j));
+  for (uint32_t i = k; i < static_cast<uint32_t>(x.ihi); i += step)
+    qc[i] = static_cast<uint8_t>(x.strand ? 3u - base_at(row, x.m - 1u - i) : base_at(row, i));
+}
+
 template <int SEG>
 __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint32_t* list,
                                                            const uint32_t* range) {
@@ -515,11 +584,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
             qw[w] = v;
           }
         } else {
-          uint8_t* rc = rbyte_s + sl * kRB;
-          uint8_t* qc = qbyte_s + sl * kQB;
-          for (uint32_t j = k; j < rd[X].jstar; j += SEG) rc[j] = static_cast<uint8_t>(base_at(rd[X].ref, rd[X].ws + j));
-          for (uint32_t i = k; i < static_cast<uint32_t>(rd[X].ihi); i += SEG)
-            qc[i] = static_cast<uint8_t>(rd[X].strand ? 3u - base_at(row, rd[X].m - 1u - i) : base_at(row, i));
+          tb_stage_bytes(a, rd[X], qbyte_s + sl * kQB, rbyte_s + sl * kRB, static_cast<uint32_t>(k), SEG);
         }
       }
     }
@@ -531,63 +596,26 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     const int stB = rd[1].has ? 2 * (rd[1].ihi - 1) + rd[1].w : 0;
     const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(max(stA, stB) + 1)));
     const int p = k & 1;
-    // per half-step: the rows where this lane's diagonal is inside the window
-    // [rlo, rlo + cnt), the code offsets of row i and column i + c (offset + i),
-    // the row where it crosses the end column, the lower band edge flag
-    struct Sub {
-      uint32_t rlo, cnt, qa, ra;
-      int c, icr;
-      bool bd;
-    };
-    auto sub_of = [&](const TbRead& x, int X) {
-      Sub u;
-      const int c = x.dlo + k;  // column = row + c
-      const int lo = max(1, 1 - c), hi = min(x.ihi, static_cast<int>(x.jstar) - c);
-      const bool on = x.has && k < x.w && hi >= lo;
-      u.rlo = static_cast<uint32_t>(lo);
-      u.cnt = on ? static_cast<uint32_t>(hi - lo + 1) : 0u;
-      const int sl = slot(seg, X);
-      // packed: the slot's word offsets; bytes: offsets that index codes by row
-      u.qa = static_cast<uint32_t>(PACKED ? sl * kQW : sl * kQB - 1);
-      u.ra = static_cast<uint32_t>(PACKED ? sl * kRW : sl * kRB + c - 1);
-      u.c = c;
-      const int ir = static_cast<int>(x.jstar) - c;
-      u.icr = (on && ir >= x.ilo && ir >= lo && ir <= hi) ? ir : -(1 << 20);
-      u.bd = k + 1 >= x.w;
-      return u;
-    };
-    const Sub s0 = p ? sub_of(rd[1], 1) : sub_of(rd[0], 0);
-    const Sub s1 = p ? sub_of(rd[0], 0) : sub_of(rd[1], 1);
-    // One cell of row i.  E and F arrive complete from the left and upper
-    // neighbours, which computed them from their own cells (gap opened from
-    // their H or extended from their own gap value), and this cell does the same
-    // for its right (En) and lower (Fn) neighbour.  Cells outside the window
-    // score a mismatch: with the top and left borders at H = 0 and gap values at
-    // most -(go+ge) they keep H = 0, which is the border itself; cells right of
-    // j* or below the last row only feed cells that are never read.  The 4 bits:
-    // H came from the diagonal, H equals E, this cell opened its right
-    // neighbour's E, this cell opened its lower neighbour's F.
-    auto cell = [&](const Sub& sb, int i, int32_t E, int32_t F, int32_t& hd, int32_t& En, int32_t& Fn,
+    // the read of each half-step on this lane's diagonal
+    const int slA = slot(seg, 0), slB = slot(seg, 1);
+    const TbSub uA = tb_sub<PACKED>(rd[0], k, static_cast<uint32_t>(slA * (PACKED ? kQW : kQB)),
+                                    static_cast<uint32_t>(slA * (PACKED ? kRW : kRB)));
+    const TbSub uB = tb_sub<PACKED>(rd[1], k, static_cast<uint32_t>(slB * (PACKED ? kQW : kQB)),
+                                    static_cast<uint32_t>(slB * (PACKED ? kRW : kRB)));
+    const TbSub s0 = p ? uB : uA, s1 = p ? uA : uB;
+    auto cell = [&](const TbSub& sb, int i, int32_t E, int32_t F, int32_t& hd, int32_t& En, int32_t& Fn,
                     uint32_t& nib, int32_t& hcr) {
-      // byte codes: loads from index 0 outside the window instead of a branch
-      bool eq = false;
-      const uint32_t ui = static_cast<uint32_t>(i);
-      const bool in = ui - sb.rlo < sb.cnt;
+      bool eq;
       if (PACKED) {
-        if (in) eq = cd.match(sb.qa, sb.ra, ui - 1u, ui - 1u + static_cast<uint32_t>(sb.c));
+        // outside the window the codes load from index 0 instead of a branch
+        const uint32_t ui = static_cast<uint32_t>(i);
+        const bool in = ui - sb.rlo < sb.cnt;
+        const uint32_t i0 = in ? ui - 1u : 0u, j0 = in ? ui - 1u + static_cast<uint32_t>(sb.c) : 0u;
+        eq = in & cd.match(sb.qa, sb.ra, i0, j0);
       } else {
-        const uint32_t qi = in ? sb.qa + ui : 0u, ri = in ? sb.ra + ui : 0u;
-        eq = in & (qbyte_s[qi] == rbyte_s[ri]);
+        eq = tb_eq_bytes(sb, i, qbyte_s, rbyte_s);
       }
-      const int32_t hs = hd + (eq ? a.sa : -a.sb);
-      const int32_t H = max(max(hs, 0), max(E, F));
-      const int32_t g = H - goe, ee = E - a.ge, fe = F - a.ge;
-      En = max(g, ee);
-      Fn = max(g, fe);
-      nib = static_cast<uint32_t>(H == hs) | (static_cast<uint32_t>(H == E) << 1) |
-            (static_cast<uint32_t>(g >= ee) << 2) | (static_cast<uint32_t>(g >= fe) << 3);
-      if (i == sb.icr) hcr = H;
-      hd = H;
+      nib = tb_cell(a, goe, eq, E, F, i == sb.icr, hd, En, Fn, hcr);
     };
     // what each half-step sent last: gap values for the neighbours, own H
     int32_t Ha = 0, Hb = 0, Ena = -goe, Fna = -goe, Enb = -goe, Fnb = -goe;
@@ -662,8 +690,115 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
   }
 }
 
+// The same wavefront for bands of 33-64 diagonals: lane k runs band diagonals k
+// and k + 32 of both reads, the second 16 rows behind the first (its step for
+// row i is 32 later).  Diagonal 31's right neighbour (32) and diagonal 32's left
+// neighbour (31) sit on lanes 0 and 31, so the gap values that cross between the
+// lane's two diagonals go by rotating shuffles.
+constexpr int kTb2Diags = 64;
+constexpr int kTb2RowPad = 32;  // rows before row 1 the second diagonal reaches
+constexpr int kTb2Rows = kMaxReadLen + 2 * kTb2RowPad + 1;
+
+__global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint32_t* list, const uint32_t* range) {
+  constexpr int V = kTb2Diags;
+  constexpr int kSlots = kTbWarps * 2;
+  constexpr int kLag = 16 * V - 32;  // bytes from diagonal k's row i to diagonal k + 32's row i - 16
+  __shared__ uint8_t dirs_s[kTbWarps][kTb2Rows * V];
+  __shared__ uint8_t qbyte_s[kSlots * kMaxReadLen];
+  __shared__ uint8_t rbyte_s[kSlots * kMaxWinLen];
+  const int k = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  uint8_t* dirs = dirs_s[warp] + kTb2RowPad * V;
+  const Codes<false> cd{qbyte_s, rbyte_s, nullptr, nullptr};
+  const int32_t goe = a.go + a.ge;
+  const uint32_t begin = range[0];
+  const uint32_t count = range[1] - begin;
+  const uint32_t stride = gridDim.x * kTbWarps * 2;
+  const int up = (k + 31) & 31, dn = (k + 1) & 31;
+  for (uint32_t base = (blockIdx.x * kTbWarps + warp) * 2; base < count; base += stride) {
+    TbRead rd[2];
+#pragma unroll
+    for (int X = 0; X < 2; ++X) {
+      const uint32_t li = base + X;
+      rd[X] = tb_load(a, li < count, li < count ? list[begin + li] : 0u);
+      const int sl = warp * 2 + X;
+      if (rd[X].has) tb_stage_bytes(a, rd[X], qbyte_s + sl * kMaxReadLen, rbyte_s + sl * kMaxWinLen, k, 32);
+    }
+    __syncwarp();
+    const int stA = rd[0].has ? 2 * (rd[0].ihi - 1) + rd[0].w : 0;
+    const int stB = rd[1].has ? 2 * (rd[1].ihi - 1) + rd[1].w : 0;
+    const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(max(stA, stB) + 1)));
+    const int p = k & 1;
+    const uint32_t qA = warp * 2 * kMaxReadLen, rA = warp * 2 * kMaxWinLen;
+    const uint32_t qB = qA + kMaxReadLen, rB = rA + kMaxWinLen;
+    // [read of the half-step][diagonal k, k + 32]
+    const TbSub uA0 = tb_sub<false>(rd[0], k, qA, rA), uA1 = tb_sub<false>(rd[0], k + 32, qA, rA);
+    const TbSub uB0 = tb_sub<false>(rd[1], k, qB, rB), uB1 = tb_sub<false>(rd[1], k + 32, qB, rB);
+    const TbSub s00 = p ? uB0 : uA0, s01 = p ? uB1 : uA1, s10 = p ? uA0 : uB0, s11 = p ? uA1 : uB1;
+    int32_t Ha0 = 0, Ha1 = 0, Hb0 = 0, Hb1 = 0;
+    int32_t Ena0 = -goe, Ena1 = -goe, Fna0 = -goe, Fna1 = -goe;
+    int32_t Enb0 = -goe, Enb1 = -goe, Fnb0 = -goe, Fnb1 = -goe;
+    int32_t hcr00 = -1, hcr01 = -1, hcr10 = -1, hcr11 = -1;
+    uint32_t pend0 = 0, pend1 = 0;
+    int ia = 1 - ((k + p) >> 1);  // diagonal k's row at half-step 0
+    uint8_t* drow = dirs + (ia - 1) * V + k;
+    const int o1 = p ? V : 0;     // half-step 1 runs read A one row ahead on odd lanes
+    for (int t = 0; t < nmax; t += 2, ++ia, drow += V) {
+      {
+        int32_t E0 = __shfl_up_sync(FULL, Enb0, 1);
+        const int32_t E1 = __shfl_sync(FULL, k == 31 ? Enb0 : Enb1, up);
+        int32_t F0 = __shfl_sync(FULL, k == 0 ? Fnb1 : Fnb0, dn);
+        int32_t F1 = __shfl_down_sync(FULL, Fnb1, 1);
+        if (k == 0) E0 = -goe;
+        if (s00.bd) F0 = -goe;
+        if (s01.bd) F1 = -goe;
+        const uint32_t n0 = tb_cell(a, goe, tb_eq_bytes(s00, ia, qbyte_s, rbyte_s), E0, F0, ia == s00.icr, Ha0,
+                                    Ena0, Fna0, hcr00);
+        const uint32_t n1 = tb_cell(a, goe, tb_eq_bytes(s01, ia - 16, qbyte_s, rbyte_s), E1, F1, ia - 16 == s01.icr,
+                                    Ha1, Ena1, Fna1, hcr01);
+        // bytes as in k_tb_wave: read A's nibble low, read B's high
+        drow[0] = static_cast<uint8_t>(pend0 + (n0 << 4));
+        drow[-kLag] = static_cast<uint8_t>(pend1 + (n1 << 4));
+        pend0 = n0;
+        pend1 = n1;
+      }
+      {
+        int32_t E0 = __shfl_up_sync(FULL, Ena0, 1);
+        const int32_t E1 = __shfl_sync(FULL, k == 31 ? Ena0 : Ena1, up);
+        int32_t F0 = __shfl_sync(FULL, k == 0 ? Fna1 : Fna0, dn);
+        int32_t F1 = __shfl_down_sync(FULL, Fna1, 1);
+        if (k == 0) E0 = -goe;
+        if (s10.bd) F0 = -goe;
+        if (s11.bd) F1 = -goe;
+        const int ib = ia + p;
+        const uint32_t n0 = tb_cell(a, goe, tb_eq_bytes(s10, ib, qbyte_s, rbyte_s), E0, F0, ib == s10.icr, Hb0,
+                                    Enb0, Fnb0, hcr10);
+        const uint32_t n1 = tb_cell(a, goe, tb_eq_bytes(s11, ib - 16, qbyte_s, rbyte_s), E1, F1, ib - 16 == s11.icr,
+                                    Hb1, Enb1, Fnb1, hcr11);
+        drow[o1] = static_cast<uint8_t>(pend0 + (n0 << 4));
+        drow[o1 - kLag] = static_cast<uint8_t>(pend1 + (n1 << 4));
+        pend0 = n0;
+        pend1 = n1;
+      }
+    }
+    auto ic = [&](const TbSub& u, int32_t hcr, int32_t S) {
+      return (u.icr > 0 && hcr == S) ? static_cast<uint32_t>(u.icr) : kNoRow;
+    };
+    const int32_t S0 = p ? rd[1].S : rd[0].S, S1 = p ? rd[0].S : rd[1].S;
+    const uint32_t ic0 = min(ic(s00, hcr00, S0), ic(s01, hcr01, S0));
+    const uint32_t ic1 = min(ic(s10, hcr10, S1), ic(s11, hcr11, S1));
+    const uint32_t icA = __reduce_min_sync(FULL, p ? ic1 : ic0);
+    const uint32_t icB = __reduce_min_sync(FULL, p ? ic0 : ic1);
+    __syncwarp();
+    tb_walk<V, 32, false>(a, walk_of(rd[0]), icA, 0, dirs, cd, qA, rA, k, FULL, 0);
+    __syncwarp();
+    tb_walk<V, 32, false>(a, walk_of(rd[1]), icB, 4, dirs, cd, qB, rB, k, FULL, 0);
+    __syncwarp();
+  }
+}
+
 // Routing: clears reads without a winner, picks each winner's traceback kernel
-// (band <= 8 / 16 / 32 diagonals, else the full-rectangle kernel) and counts the
+// (band <= 1 / 2 / 4 / 8 / 16 / 32 / 64 diagonals, else the full-rectangle kernel) and counts the
 // sort code bucket * 256 + (256 - last row), so that each kernel's reads come
 // sorted by the number of rows their DP runs, longest first.
 __global__ void __launch_bounds__(1024) k_tb_route(TbArgs a, uint32_t* code, uint32_t* hist) {
@@ -694,7 +829,7 @@ __global__ void __launch_bounds__(1024) k_tb_route(TbArgs a, uint32_t* code, uin
         } else {
           const TbBand b = tb_band(a.sa, a.go, a.ge, S, jstar, ilo, ihi);
           bucket = b.w <= 1 ? 0 : b.w <= 2 ? 1 : b.w <= 4 ? 2 : b.w <= 8 ? 3 : b.w <= 16 ? 4
-                 : b.w <= kTbMaxBand ? 5 : kTbBuckets - 1;
+                 : b.w <= 32 ? 5 : b.w <= kTbMaxBand ? 6 : kTbBuckets - 1;
           last = ihi;
         }
       }
@@ -807,7 +942,7 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
     return cudaPeekAtLastError() == cudaSuccess;
   };
   // widest bands (longest kernels) first
-  if (!wave(k_tb_wave<32>, 5, 2) || !wave(k_tb_wave<16>, 4, 4) || !wave(k_tb_wave<4>, 2, 16) ||
+  if (!wave(k_tb_wave2, 6, 2) || !wave(k_tb_wave<32>, 5, 2) || !wave(k_tb_wave<16>, 4, 4) || !wave(k_tb_wave<4>, 2, 16) ||
       !wave(k_tb_wave<1>, 0, 64) || !wave(k_tb_wave<8>, 3, 8) || !wave(k_tb_wave<2>, 1, 32))
     return -1;
   const size_t smem = static_cast<size_t>(kMaxWinLen) * 32 * sizeof(uint32_t);

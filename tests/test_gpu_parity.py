@@ -296,3 +296,66 @@ def test_outputs_identical_across_runs_and_shapes(sr):
     for opts in [dict(lanes=16, rows=16), dict(lanes=32, rows=8), dict(engine=1)]:
         b.run(sr.score_params(*SP), sr.align_opts(**opts))
         assert digest(b.fetch()) == ref
+
+
+def _band_widths(w, o, sp=SP):
+    """Traceback band width of each read's winner over every row that can end it
+    (rows ceil(S / match) .. m) and with its end row known (2 g + 1)."""
+    sa, _, go, ge = sp
+    m = np.diff(w["read_off"]).astype(np.int64)
+    b = o["best"]
+    item, S = b["item"].astype(np.int64), b["score"].astype(np.int64)
+    ok = (item >= 0) & (S > 0)
+    jstar = np.where(ok, o["item_end_j"][np.maximum(item, 0)], 0).astype(np.int64)
+    iend = b["read_end"].astype(np.int64)
+    g_all = np.maximum(0, (sa * np.minimum(m, jstar) - S - go) // ge)
+    w_all = m - np.maximum(1, -(-S // sa)) + 2 * g_all + 1
+    g_row = np.maximum(0, (sa * np.minimum(iend, jstar) - S - go) // ge)
+    return ok, w_all, 2 * g_row + 1
+
+
+def test_traceback_band_classes(sr):
+    """Winners in every traceback class: bands up to 32 diagonals (one lane per
+    diagonal), 33-64 (two per lane), wider ones whose end row comes from the
+    extension kernels' winner mode, and wider still (full rectangle)."""
+    rng = np.random.default_rng(23)
+    ref = rng.choice(np.frombuffer(b"ACGT", np.uint8), 400_000)
+    reads, offs = [], [0]
+    cands = dict(cand_off=[0], c_ref=[], c_strand=[], c_start=[], c_len=[])
+    for r in range(1500):
+        m = int(rng.integers(60, 257))
+        pos = int(rng.integers(2000, len(ref) - 2000))
+        src = ref[pos:pos + m + 40].copy()
+        sub, indel = [(0.0, 0.0), (0.04, 0.01), (0.10, 0.02), (0.2, 0.04)][r % 4]
+        out = []
+        i = 0
+        while len(out) < m and i < len(src):
+            u = rng.random()
+            if u < indel / 2:
+                i += int(rng.integers(1, 6))           # deletion from the read
+            elif u < indel:
+                out.extend(rng.choice(np.frombuffer(b"ACGT", np.uint8), int(rng.integers(1, 6))))
+            else:
+                out.append(src[i] if rng.random() >= sub else rng.choice(np.frombuffer(b"ACGT", np.uint8)))
+                i += 1
+        q = np.array(out[:m], np.uint8)
+        if r % 7 == 0:  # only a part of the read in the window: a short local alignment
+            q = np.concatenate([q[: m // 3], rng.choice(np.frombuffer(b"ACGT", np.uint8), m - m // 3)])
+        reads.append(q)
+        offs.append(offs[-1] + len(q))
+        for d in (-32, int(rng.integers(-300, 300))):
+            cands["c_ref"].append(0)
+            cands["c_strand"].append(0)
+            cands["c_start"].append(pos + d)
+            cands["c_len"].append(len(q) + 64)
+        cands["cand_off"].append(len(cands["c_ref"]))
+    w = dict(refs=[ref], bases=np.concatenate(reads), read_off=np.array(offs, np.int64),
+             **{k: np.array(v) for k, v in cands.items()})
+    o = oracle_run(w)
+    ok, w_all, w_row = _band_widths(w, o)
+    assert np.sum(ok & (w_all <= 32)) > 100
+    assert np.sum(ok & (w_all > 32) & (w_all <= 64)) > 50
+    assert np.sum(ok & (w_all > 64) & (w_row <= 64)) > 20
+    assert np.sum(ok & (w_row > 64)) > 5
+    s = _session(sr, w)
+    _check(gpu_run(s, w), o)

@@ -184,6 +184,37 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
   if (r >= n_reads) return;
   const uint64_t c0 = cand_off[r], c1 = cand_off[r + 1];
   const int slots = 1 + n_refs;
+  if (c1 - c0 <= 32) {
+    // up to 32 windows: one per lane, loaded once; the same rules as below
+    const bool has = c0 + lane < c1;
+    const uint64_t c = c0 + lane;
+    const int32_t s = has ? item_score[c] : 0;
+    const uint32_t ref = has ? c_ref[c] : 0u, str = has ? c_strand[c] : 0u;
+    const unsigned long long gend = has ? c_start[c] + item_end[c] - 1 : 0ull;
+    const unsigned long long locus = (static_cast<unsigned long long>(ref) << 60) | (gend << 20) |
+                                     (static_cast<unsigned long long>(str) << 19);
+    for (int f = -1; f < n_refs; ++f) {
+      const bool in = has && (f < 0 || ref == static_cast<uint32_t>(f));
+      const int32_t best = __reduce_max_sync(FULL, in ? max(s, 0) : 0);
+      DevHit h{};
+      h.item = -1;
+      if (best > 0) {
+        const bool top = in && s == best;
+        const unsigned long long wk = wmin64(top ? locus | static_cast<unsigned long long>(lane) : ~0ull);
+        const int wl = static_cast<int>(wk & 0x7ffffull);
+        const unsigned long long wlocus = wk & ~0x7ffffull;
+        h.score = best;
+        h.second = __reduce_max_sync(FULL, (in && s > 0 && locus != wlocus) ? s : 0);
+        // ties: distinct loci among the best-scoring windows
+        const uint32_t tops = __ballot_sync(FULL, top);
+        const uint32_t same = __match_any_sync(FULL, top ? locus : ~0ull);
+        h.n_ties = static_cast<uint32_t>(__popc(__ballot_sync(FULL, top && (same & tops & ((1u << lane) - 1u)) == 0u)));
+        h.item = static_cast<int32_t>(c0 + static_cast<uint64_t>(wl));
+      }
+      if (lane == 0) hits[r * slots + (f + 1)] = h;
+    }
+    return;
+  }
   for (int f = -1; f < n_refs; ++f) {
     // best score
     int32_t best = 0;

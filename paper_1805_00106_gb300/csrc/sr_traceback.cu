@@ -797,7 +797,8 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint
   }
 }
 
-// Routing: clears reads without a winner, picks each winner's traceback kernel
+// Routing: clears reads without a winner, writes the CIGAR of reads matched
+// base for base (no DP needed), picks each other winner's traceback kernel
 // (band <= 1 / 2 / 4 / 8 / 16 / 32 / 64 diagonals, else the full-rectangle kernel) and counts the
 // sort code bucket * 256 + (256 - last row), so that each kernel's reads come
 // sorted by the number of rows their DP runs, longest first.
@@ -819,7 +820,15 @@ __global__ void __launch_bounds__(1024) k_tb_route(TbArgs a, uint32_t* code, uin
       const uint32_t jstar = a.item_end[item];
       int bucket = -1;
       uint32_t last = m;
-      if (a.tb_flag[r] == kTbFlagFull) {
+      if (m >= 1 && jstar >= m && static_cast<int64_t>(S) == static_cast<int64_t>(a.sa) * m) {
+        // every base matched: any mismatch or gap scores below match * m, so the
+        // alignment is the whole read on one diagonal ending at (m, j*)
+        a.cigar_slots[static_cast<uint64_t>(r) * kCigarStride] = m << 4;  // m M
+        hp->read_start = 1;
+        hp->read_end = static_cast<int32_t>(m);
+        hp->start_j = jstar - m + 1u;
+        hp->cigar_len = 1;
+      } else if (a.tb_flag[r] == kTbFlagFull) {
         bucket = kTbBuckets - 1;
       } else {
         uint32_t ilo = 0, ihi = 0;

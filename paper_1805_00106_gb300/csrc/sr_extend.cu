@@ -51,29 +51,17 @@ int fanout_end(const Fanout& f, cudaStream_t st) {
   return 0;
 }
 
-int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
-                       const TuneBin* bins, int n_bins, bool plain, uint32_t lanes, uint32_t rows,
-                       cudaStream_t st, const uint64_t* class_items, const Fanout* fan) {
+int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, uint32_t lanes,
+                       uint32_t rows, cudaStream_t st) {
   ExtArgs a = make_args(b, refs, sc);
-  a.order = b.order;  // winners compacted per class
+  a.order = b.order;  // winners of every read length in one range (class 0)
   a.class_range = b.wrange;
   a.queue = b.wqueue;
   a.item_iend = b.item_iend;
-  int launched = 0;
-  const int classes = plain ? 1 : n_bins;
-  if (fan && fanout_begin(*fan, st) < 0) return -1;
-  int next = 0;
-  for (int c = 0; c < classes; ++c) {
-    if (!plain && class_items && class_items[c] == 0) continue;  // no item, no winner
-    a.cls = c;
-    uint32_t g = lanes ? lanes : (plain ? 16u : bins[c].lanes);
-    uint32_t r = rows ? rows : (plain ? 16u : bins[c].rows);
-    int k = dispatch_mode2(g, r, a, fan ? fan->side[next++ % kSide] : st);
-    if (k < 0) return -1;
-    launched += k;
-  }
-  if (fan && fanout_end(*fan, st) < 0) return -1;
-  return launched;
+  a.cls = 0;
+  // one shape that holds every read length (256 rows)
+  const int k = dispatch_mode2(lanes ? lanes : 16u, rows ? rows : 16u, a, st);
+  return k < 0 ? -1 : k;
 }
 
 int extend_shapes(uint32_t* lanes, uint32_t* rows, int cap) {

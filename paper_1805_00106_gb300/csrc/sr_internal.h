@@ -172,9 +172,9 @@ int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
 int launch_select(const BatchDev& b, int n_refs, cudaStream_t st);
 int launch_winners(const BatchDev& b, const ScoreConst& sc, int mode, int n_refs, bool plain,
                    cudaStream_t st);
-int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
-                       const TuneBin* bins, int n_bins, bool plain, uint32_t lanes, uint32_t rows,
-                       cudaStream_t st, const uint64_t* class_items = nullptr, const Fanout* fan = nullptr);
+// end rows of the winners compacted by k_winners: one launch (lanes x rows, 0 = 16 x 16)
+int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, uint32_t lanes,
+                       uint32_t rows, cudaStream_t st);
 int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, int mode,
                      int n_refs, cudaStream_t st, const Fanout* fan = nullptr);
 int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);

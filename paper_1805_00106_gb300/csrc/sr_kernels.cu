@@ -274,8 +274,8 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
 // row able to end the alignment (rows ceil(S / match) .. m in local mode, row m
 // in final-row mode) is searched directly when it is at most 64 diagonals wide;
 // wider ones first get their end row from the extension kernels' winner mode,
-// for which they are compacted per class into `order` (whose class ranges hold
-// at least as many slots).
+// for which they are compacted into the front of `order` (one range for all
+// read lengths: there are few, and one launch costs less than one per bin).
 __global__ void k_winners(uint32_t n_reads, int slots, const DevHit* hits, const uint16_t* item_key,
                           const uint32_t* class_range, const uint32_t* rlen, const uint32_t* item_read,
                           const uint32_t* item_end, ScoreConst sc, int mode, bool plain,
@@ -294,20 +294,18 @@ __global__ void k_winners(uint32_t n_reads, int slots, const DevHit* hits, const
       const TbBand b = tb_band(sc.sa, sc.go, sc.ge, h.score, item_end[h.item], ilo < 1u ? 1u : ilo, m);
       if (b.w > kTbMaxBand) {
         flag = kTbFlagRow;
-        const uint32_t pos = atomicAdd(&wcount[cls], 1u);
-        order[(plain ? 0u : class_range[2 * cls]) + pos] = static_cast<uint32_t>(h.item);
+        order[atomicAdd(&wcount[0], 1u)] = static_cast<uint32_t>(h.item);
       }
     }
   }
   tb_flag[r] = flag;
 }
 
-__global__ void k_wrange(const uint32_t* class_range, const uint32_t* wcount, bool plain, uint32_t* wrange) {
+__global__ void k_wrange(const uint32_t* wcount, uint32_t* wrange) {
   const int c = threadIdx.x;
   if (c >= kNumClasses) return;
-  const uint32_t b = plain ? 0u : class_range[2 * c];
-  wrange[2 * c] = b;
-  wrange[2 * c + 1] = b + (c < kNumBins ? wcount[c] : 0u);
+  wrange[2 * c] = 0u;
+  wrange[2 * c + 1] = c == 0 ? wcount[0] : 0u;
 }
 
 __global__ void k_classify(uint32_t n_reads, int n_refs, const DevHit* hits, int32_t min_score,
@@ -452,7 +450,7 @@ int launch_winners(const BatchDev& b, const ScoreConst& sc, int mode, int n_refs
   k_winners<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, 1 + n_refs, b.hits, b.item_key,
                                                      b.class_range, b.rlen, b.item_read, b.item_end, sc,
                                                      mode, plain, b.wcount, b.order, b.tb_flag);
-  k_wrange<<<1, 32, 0, st>>>(b.class_range, b.wcount, plain, b.wrange);
+  k_wrange<<<1, 32, 0, st>>>(b.wcount, b.wrange);
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;
 }
 

@@ -126,8 +126,8 @@ struct sr_batch {
   bool ran = false;
   sr_align_opts last_opts{};
   cudaEvent_t ev[6] = {};  // around: whole path, extension kernels, traceback
-  // side streams and fork/join events of the extension, winner-pass and traceback phases
-  Fanout fan[3] = {};
+  // side streams and fork/join events of the extension and traceback phases
+  Fanout fan[2] = {};
   bool fan_ok = false;
 };
 
@@ -718,12 +718,11 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
     if ((t = launch_winners(d, sc, static_cast<int>(o.mode), nr, plain, st)) < 0) return -1;
     k += t;
     if (o.mode == SR_MODE_LOCAL && b->n_items) {
-      if ((t = launch_winner_rows(d, b->s->refs, sc, bins, kNumBins, plain, o.lanes, o.rows, st, class_items,
-                                  &b->fan[1])) < 0)
+      if ((t = launch_winner_rows(d, b->s->refs, sc, o.lanes, o.rows, st)) < 0)
         return -1;
       k += t;
     }
-    if ((t = launch_traceback(d, b->s->refs, sc, static_cast<int>(o.mode), nr, st, &b->fan[2])) < 0) return -1;
+    if ((t = launch_traceback(d, b->s->refs, sc, static_cast<int>(o.mode), nr, st, &b->fan[1])) < 0) return -1;
     k += t;
     if ((t = launch_cigar_compact(d, nr, st)) < 0) return -1;
     k += t;

@@ -80,6 +80,47 @@ static sr_align_opts default_opts() {
 
 using namespace sr;
 
+namespace {
+// A batch's timing events and the side streams and fork/join events of its
+// fan-out phases.  Creating streams and events costs tens of microseconds, so
+// the session keeps those of freed batches for the next ones.
+struct BatchRes {
+  cudaEvent_t ev[6] = {};  // around: whole path, extension kernels, traceback
+  Fanout fan[2] = {};      // extension and traceback phases (the same side streams)
+};
+
+void res_destroy(BatchRes& r) {
+  for (auto ev : r.ev)
+    if (ev) cudaEventDestroy(ev);
+  for (auto& f : r.fan) {
+    if (f.fork) cudaEventDestroy(f.fork);
+    for (auto j : f.join)
+      if (j) cudaEventDestroy(j);
+  }
+  for (auto x : r.fan[0].side)
+    if (x) {
+      cudaStreamSynchronize(x);
+      cudaStreamDestroy(x);
+    }
+  r = BatchRes{};
+}
+
+bool res_create(BatchRes& r) {
+  bool ok = true;
+  for (auto& ev : r.ev) ok = ok && cudaEventCreate(&ev) == cudaSuccess;
+  cudaStream_t side[kSide] = {};
+  for (auto& x : side) ok = ok && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
+  for (auto& f : r.fan) {
+    for (int i = 0; i < kSide; ++i) f.side[i] = side[i];
+    ok = ok && cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (auto& j : f.join) ok = ok && cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess;
+  }
+  if (!ok) res_destroy(r);
+  return ok;
+}
+constexpr size_t kResPool = 16;
+}  // namespace
+
 struct sr_session {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -103,6 +144,9 @@ struct sr_session {
   std::mutex spare_mu;
   void* spare = nullptr;
   uint64_t spare_bytes = 0;
+  // streams and events of freed batches
+  std::mutex res_mu;
+  std::vector<BatchRes> res_pool;
 };
 
 struct sr_batch {
@@ -125,10 +169,8 @@ struct sr_batch {
   uint64_t i32_items = 0;
   bool ran = false;
   sr_align_opts last_opts{};
-  cudaEvent_t ev[6] = {};  // around: whole path, extension kernels, traceback
-  // side streams and fork/join events of the extension and traceback phases
-  Fanout fan[2] = {};
-  bool fan_ok = false;
+  BatchRes res{};  // events, side streams (from the session's pool)
+  bool res_ok = false;
 };
 
 extern "C" const char* sr_last_error(void) { return g_err.c_str(); }
@@ -247,6 +289,7 @@ static void session_release(sr_session* s) {
   for (auto* w : s->d_words) cudaFree(w);
   for (auto* p : s->idx_bufs) cudaFree(p);
   for (auto& b : s->pool) cudaFreeHost(b.first);
+  for (auto& r : s->res_pool) res_destroy(r);
   if (s->spare) cudaFree(s->spare);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -361,91 +404,9 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   if (nc >= (1ull << 32)) return set_error(SR_EINVAL, "sr_batch_stage: too many windows");
   if (nc && (!cands->ref_id || !cands->strand || !cands->win_start || !cands->win_len))
     return set_error(SR_EINVAL, "sr_batch_stage: null candidate arrays");
-  // host-side validation: every kernel relies on these bounds (window copies,
-  // shared-memory column streams, packed read rows).  Read ranges are checked in
-  // parallel; the first bad read (lowest index) is reported.  The same pass
-  // counts the DP cells and the windows per read length.
-  struct Part {
-    uint64_t cells = 0;
-    uint32_t max_m = 0;
-    uint64_t by_len[kMaxReadLen + 1] = {};
-    uint32_t bad_read = UINT32_MAX;
-    int why = 0;  // 1 offsets, 2 read length, 3 window count, 4 window
-    uint64_t bad_win = 0;
-  };
-  const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  const uint32_t nthr = (n < 65536u) ? 1u : hw;
-  std::vector<Part> parts(nthr);
-  auto check = [&](uint32_t t) {
-    Part& P = parts[t];
-    const uint32_t r0 = static_cast<uint32_t>(static_cast<uint64_t>(n) * t / nthr);
-    const uint32_t r1 = static_cast<uint32_t>(static_cast<uint64_t>(n) * (t + 1) / nthr);
-    for (uint32_t r = r0; r < r1; ++r) {
-      const uint64_t a0 = reads->offsets[r], a1 = reads->offsets[r + 1];
-      const uint64_t c0 = cands->offsets[r], c1 = cands->offsets[r + 1];
-      if (a1 < a0 || c1 < c0 || c1 > nc) {
-        P.bad_read = r;
-        P.why = 1;
-        return;
-      }
-      const uint64_t m = a1 - a0;
-      if (m == 0 || m > SR_MAX_READ_LEN) {
-        P.bad_read = r;
-        P.why = 2;
-        return;
-      }
-      if (c1 - c0 >= (1ull << 19)) {
-        P.bad_read = r;
-        P.why = 3;
-        return;
-      }
-      for (uint64_t k = c0; k < c1; ++k) {
-        const uint32_t ref = cands->ref_id[k], len = cands->win_len[k];
-        if (ref >= s->n_refs || cands->strand[k] > 1 || len < 1 || len > SR_MAX_WIN_LEN ||
-            cands->win_start[k] > s->lens[ref] || cands->win_start[k] + len > s->lens[ref]) {
-          P.bad_read = r;
-          P.why = 4;
-          P.bad_win = k;
-          return;
-        }
-        P.cells += m * len;
-      }
-      P.by_len[m] += c1 - c0;
-      P.max_m = std::max<uint32_t>(P.max_m, static_cast<uint32_t>(m));
-    }
-  };
-  if (nthr == 1) {
-    check(0);
-  } else {
-    std::vector<std::thread> th;
-    for (uint32_t t = 0; t < nthr; ++t) th.emplace_back(check, t);
-    for (auto& x : th) x.join();
-  }
-  uint64_t cells = 0;
-  uint32_t max_m = 0;
-  uint64_t by_len[kMaxReadLen + 1] = {};
-  const Part* worst = nullptr;
-  for (const Part& P : parts) {
-    if (P.bad_read != UINT32_MAX && (!worst || P.bad_read < worst->bad_read)) worst = &P;
-    cells += P.cells;
-    max_m = std::max(max_m, P.max_m);
-    for (int m = 0; m <= kMaxReadLen; ++m) by_len[m] += P.by_len[m];
-  }
-  if (worst) {
-    const uint32_t r = worst->bad_read;
-    switch (worst->why) {
-      case 1:
-        return set_error(SR_EINVAL, "sr_batch_stage: decreasing or out-of-range offsets at read %u", r);
-      case 2:
-        return set_error(SR_EINVAL, "sr_batch_stage: read %u has length %llu, must be 1..256", r,
-                         static_cast<unsigned long long>(reads->offsets[r + 1] - reads->offsets[r]));
-      case 3:
-        return set_error(SR_EINVAL, "sr_batch_stage: read %u has more than 2^19-1 windows", r);
-      default:
-        return set_error(SR_EINVAL, "sr_batch_stage: window %llu is outside its reference or malformed",
-                         static_cast<unsigned long long>(worst->bad_win));
-    }
-  }
+  if (nb > static_cast<uint64_t>(n) * SR_MAX_READ_LEN)
+    return set_error(SR_EINVAL, "sr_batch_stage: %llu bases in %u reads: some read is longer than %d",
+                     static_cast<unsigned long long>(nb), n, SR_MAX_READ_LEN);
   const uint64_t bytes = batch_bytes_estimate(n, nc, nb, s->n_refs);
   if (check_budget && s->hbm_budget && s->hbm_used.load() + bytes > s->hbm_budget)
     return set_error(SR_ENOMEM, "sr_batch_stage: batch needs %llu bytes, over the HBM budget",
@@ -578,26 +539,20 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   d.n_reads = n;
   d.n_items = nc;
   s->hbm_used += b->bytes;
-  for (auto& ev : b->ev) {
-    if (cudaEventCreate(&ev) != cudaSuccess) {
-      sr_batch_free(b);
-      return cuda_error("sr_batch_stage events", cudaGetLastError());
+  {
+    std::lock_guard<std::mutex> lk(s->res_mu);
+    if (!s->res_pool.empty()) {
+      b->res = s->res_pool.back();
+      s->res_pool.pop_back();
+      b->res_ok = true;
     }
   }
-  {
-    bool ok = true;
-    cudaStream_t side[kSide] = {};
-    for (auto& x : side) ok = ok && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
-    for (auto& f : b->fan) {
-      for (int i = 0; i < kSide; ++i) f.side[i] = side[i];
-      ok = ok && cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
-      for (auto& j : f.join) ok = ok && cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess;
-    }
-    b->fan_ok = true;  // what was created is released by sr_batch_free
-    if (!ok) {
+  if (!b->res_ok) {
+    if (!res_create(b->res)) {
       sr_batch_free(b);
       return cuda_error("sr_batch_stage streams", cudaGetLastError());
     }
+    b->res_ok = true;
   }
   cudaStream_t st = b->stream;
   if (nb) e = cudaMemcpyAsync(const_cast<char*>(d.bases), reads->bases, nb, cudaMemcpyHostToDevice, st);
@@ -615,7 +570,101 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(const_cast<uint32_t*>(d.c_len), cands->win_len, nc * 4, cudaMemcpyHostToDevice, st);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    sr_batch_free(b);
+    return cuda_error("sr_batch_stage copy", e);
+  }
+  // host-side validation, while the copies run: every kernel relies on these
+  // bounds (window copies, shared-memory column streams, packed read rows).
+  // Read ranges are checked in parallel; the first bad read (lowest index) is
+  // reported.  The same pass counts the DP cells and the windows per read length.
+  struct Part {
+    uint64_t cells = 0;
+    uint32_t max_m = 0;
+    uint64_t by_len[kMaxReadLen + 1] = {};
+    uint32_t bad_read = UINT32_MAX;
+    int why = 0;  // 1 offsets, 2 read length, 3 window count, 4 window
+    uint64_t bad_win = 0;
+  };
+  const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const uint32_t nthr = (n < 65536u) ? 1u : hw;
+  std::vector<Part> parts(nthr);
+  auto check = [&](uint32_t t) {
+    Part& P = parts[t];
+    const uint32_t r0 = static_cast<uint32_t>(static_cast<uint64_t>(n) * t / nthr);
+    const uint32_t r1 = static_cast<uint32_t>(static_cast<uint64_t>(n) * (t + 1) / nthr);
+    for (uint32_t r = r0; r < r1; ++r) {
+      const uint64_t a0 = reads->offsets[r], a1 = reads->offsets[r + 1];
+      const uint64_t c0 = cands->offsets[r], c1 = cands->offsets[r + 1];
+      if (a1 < a0 || c1 < c0 || c1 > nc) {
+        P.bad_read = r;
+        P.why = 1;
+        return;
+      }
+      const uint64_t m = a1 - a0;
+      if (m == 0 || m > SR_MAX_READ_LEN) {
+        P.bad_read = r;
+        P.why = 2;
+        return;
+      }
+      if (c1 - c0 >= (1ull << 19)) {
+        P.bad_read = r;
+        P.why = 3;
+        return;
+      }
+      for (uint64_t k = c0; k < c1; ++k) {
+        const uint32_t ref = cands->ref_id[k], len = cands->win_len[k];
+        if (ref >= s->n_refs || cands->strand[k] > 1 || len < 1 || len > SR_MAX_WIN_LEN ||
+            cands->win_start[k] > s->lens[ref] || cands->win_start[k] + len > s->lens[ref]) {
+          P.bad_read = r;
+          P.why = 4;
+          P.bad_win = k;
+          return;
+        }
+        P.cells += m * len;
+      }
+      P.by_len[m] += c1 - c0;
+      P.max_m = std::max<uint32_t>(P.max_m, static_cast<uint32_t>(m));
+    }
+  };
+  if (nthr == 1) {
+    check(0);
+  } else {
+    std::vector<std::thread> th;
+    for (uint32_t t = 0; t < nthr; ++t) th.emplace_back(check, t);
+    for (auto& x : th) x.join();
+  }
+  uint64_t cells = 0;
+  uint32_t max_m = 0;
+  uint64_t by_len[kMaxReadLen + 1] = {};
+  const Part* worst = nullptr;
+  for (const Part& P : parts) {
+    if (P.bad_read != UINT32_MAX && (!worst || P.bad_read < worst->bad_read)) worst = &P;
+    cells += P.cells;
+    max_m = std::max(max_m, P.max_m);
+    for (int m = 0; m <= kMaxReadLen; ++m) by_len[m] += P.by_len[m];
+  }
+  if (worst) {
+    // the copies may still be reading the caller's arrays
+    cudaStreamSynchronize(st);
+    sr_batch_free(b);
+    const uint32_t r = worst->bad_read;
+    switch (worst->why) {
+      case 1:
+        return set_error(SR_EINVAL, "sr_batch_stage: decreasing or out-of-range offsets at read %u", r);
+      case 2:
+        return set_error(SR_EINVAL, "sr_batch_stage: read %u has length %llu, must be 1..256", r,
+                         static_cast<unsigned long long>(reads->offsets[r + 1] - reads->offsets[r]));
+      case 3:
+        return set_error(SR_EINVAL, "sr_batch_stage: read %u has more than 2^19-1 windows", r);
+      default:
+        return set_error(SR_EINVAL, "sr_batch_stage: window %llu is outside its reference or malformed",
+                         static_cast<unsigned long long>(worst->bad_win));
+    }
+  }
+  // the caller may reuse its arrays once this returns
+  e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     sr_batch_free(b);
     return cuda_error("sr_batch_stage copy", e);
@@ -630,19 +679,19 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
 extern "C" void sr_batch_free(sr_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (auto ev : b->ev)
-    if (ev) cudaEventDestroy(ev);
-  if (b->fan_ok) {
-    for (auto& f : b->fan) {
-      if (f.fork) cudaEventDestroy(f.fork);
-      for (auto j : f.join)
-        if (j) cudaEventDestroy(j);
-    }
-    for (auto x : b->fan[0].side)
-      if (x) {
-        cudaStreamSynchronize(x);
-        cudaStreamDestroy(x);
+  if (b->res_ok) {
+    // idle side streams before the next batch gets them
+    bool idle = true;
+    for (auto x : b->res.fan[0].side) idle = idle && cudaStreamSynchronize(x) == cudaSuccess;
+    bool kept = false;
+    if (idle) {
+      std::lock_guard<std::mutex> lk(b->s->res_mu);
+      if (b->s->res_pool.size() < kResPool) {
+        b->s->res_pool.push_back(b->res);
+        kept = true;
       }
+    }
+    if (!kept) res_destroy(b->res);
   }
   if (b->arena) {
     cudaStreamSynchronize(b->stream);
@@ -677,7 +726,7 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
   const unsigned evf = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-  auto mark = [&](int i) { return cudaEventRecordWithFlags(b->ev[i], st, evf) == cudaSuccess; };
+  auto mark = [&](int i) { return cudaEventRecordWithFlags(b->res.ev[i], st, evf) == cudaSuccess; };
   if (!mark(0)) return -1;
   if (cudaMemsetAsync(d.status, 0, 4, st) != cudaSuccess) return -1;
   if ((t = launch_prepare(d, b->s->refs, st)) < 0) return -1;
@@ -704,7 +753,7 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
     k += t;
     if (!mark(2)) return -1;
     if ((t = launch_extend(d, b->s->refs, sc, bins, kNumBins, static_cast<int>(o.mode), plain, o.lanes,
-                           o.rows, st, class_items, &b->fan[0])) < 0)
+                           o.rows, st, class_items, &b->res.fan[0])) < 0)
       return -1;
     if (!mark(3)) return -1;
     k += t;
@@ -722,7 +771,7 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
         return -1;
       k += t;
     }
-    if ((t = launch_traceback(d, b->s->refs, sc, static_cast<int>(o.mode), nr, st, &b->fan[1])) < 0) return -1;
+    if ((t = launch_traceback(d, b->s->refs, sc, static_cast<int>(o.mode), nr, st, &b->res.fan[1])) < 0) return -1;
     k += t;
     if ((t = launch_cigar_compact(d, nr, st)) < 0) return -1;
     k += t;
@@ -867,15 +916,15 @@ extern "C" sr_status sr_batch_timing(const sr_batch* b, float* total_ms, float* 
   if (!b || !b->ran) return set_error(SR_EINVAL, "sr_batch_timing: batch has not run");
   float t = 0;
   if (total_ms) {
-    if (cudaEventElapsedTime(&t, b->ev[0], b->ev[1]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
+    if (cudaEventElapsedTime(&t, b->res.ev[0], b->res.ev[1]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
     *total_ms = t;
   }
   if (extend_ms) {
-    if (cudaEventElapsedTime(&t, b->ev[2], b->ev[3]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
+    if (cudaEventElapsedTime(&t, b->res.ev[2], b->res.ev[3]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
     *extend_ms = t;
   }
   if (traceback_ms) {
-    if (cudaEventElapsedTime(&t, b->ev[4], b->ev[5]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
+    if (cudaEventElapsedTime(&t, b->res.ev[4], b->res.ev[5]) != cudaSuccess) return cuda_error("sr_batch_timing", cudaGetLastError());
     *traceback_ms = t;
   }
   return SR_OK;

@@ -332,9 +332,12 @@ struct Codes {
 
 // walk back from (i*, j*) through one read's nibbles (shift 0: read A, 4: read B)
 // with a group of WG lanes (lane k of the group); dirs rows have SEG bytes
-template <int SEG, int WG, bool PACKED>
+// (dirs entries of type DT hold the read's nibble at `shift`, its bits inverted
+// when INV = 15; cd.match(qo, ro, i0, j0) compares query row i0 with window
+// column j0, both 0-based)
+template <int SEG, int WG, typename CD, typename DT = uint8_t, uint32_t INV = 0>
 __device__ __forceinline__ void tb_walk(const TbArgs& a, const WalkRead& t, uint32_t istar, int shift,
-                                        const uint8_t* dirs, const Codes<PACKED>& cd, uint32_t qo, uint32_t ro,
+                                        const DT* dirs, const CD& cd, uint32_t qo, uint32_t ro,
                                         int k, uint32_t gmask, int gshift) {
   if (!t.has) return;
   const int32_t goe = a.go + a.ge;
@@ -355,7 +358,7 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const WalkRead& t, uint
       if (h == 0) break;
       const int ii = i - k, jj = j - k;
       const bool v = ii >= 1 && jj >= 1;
-      const uint32_t nib = v ? (dirs[(ii - 1) * SEG + kk] >> shift) & 15u : 0u;
+      const uint32_t nib = v ? ((static_cast<uint32_t>(dirs[(ii - 1) * SEG + kk]) >> shift) ^ INV) & 15u : 0u;
       const int32_t st = v ? (cd.match(qo, ro, ii - 1, jj - 1) ? a.sa : -a.sb) : 0;
       int32_t incl = st;
 #pragma unroll
@@ -413,7 +416,7 @@ __device__ __forceinline__ void tb_walk(const TbArgs& a, const WalkRead& t, uint
         bad = true;
         break;
       }
-      const uint32_t nib = (dirs[(i - 1) * SEG + kk] >> shift) & 15u;
+      const uint32_t nib = ((static_cast<uint32_t>(dirs[(i - 1) * SEG + kk]) >> shift) ^ INV) & 15u;
       const bool open = op == 2u ? (nib & 4u) : (nib & 8u);
       h += open ? goe : a.ge;
       if (open) state = 0;
@@ -477,13 +480,19 @@ __device__ __forceinline__ TbSub tb_sub(const TbRead& x, int q, uint32_t qslot, 
   return u;
 }
 
-// Whether row i of a diagonal matches, from byte codes; outside the window the
-// codes load from index 0 (no branch) and never match.
-__device__ __forceinline__ bool tb_eq_bytes(const TbSub& sb, int i, const uint8_t* qb, const uint8_t* rb) {
+// The byte codes of row i of a diagonal; outside the window they load from
+// index 0 (no branch) and never match.  The loops load a row's codes one pair
+// of steps ahead, so the loads' latency is off the wavefront's critical path.
+struct TbLd {
+  uint32_t q, r;
+  bool in;
+  __device__ __forceinline__ bool eq() const { return in & (q == r); }
+};
+__device__ __forceinline__ TbLd tb_ld_bytes(const TbSub& sb, int i, const uint8_t* qb, const uint8_t* rb) {
   const uint32_t ui = static_cast<uint32_t>(i);
   const bool in = ui - sb.rlo < sb.cnt;
   const uint32_t qi = in ? sb.qa + ui : 0u, ri = in ? sb.ra + ui : 0u;
-  return in & (qb[qi] == rb[ri]);
+  return TbLd{qb[qi], rb[ri], in};
 }
 
 // One cell.  E and F arrive complete from the left and upper neighbours, which
@@ -603,8 +612,8 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     const TbSub uB = tb_sub<PACKED>(rd[1], k, static_cast<uint32_t>(slB * (PACKED ? kQW : kQB)),
                                     static_cast<uint32_t>(slB * (PACKED ? kRW : kRB)));
     const TbSub s0 = p ? uB : uA, s1 = p ? uA : uB;
-    auto cell = [&](const TbSub& sb, int i, int32_t E, int32_t F, int32_t& hd, int32_t& En, int32_t& Fn,
-                    uint32_t& nib, int32_t& hcr) {
+    auto cell = [&](const TbSub& sb, int i, const TbLd& ld, int32_t E, int32_t F, int32_t& hd, int32_t& En,
+                    int32_t& Fn, uint32_t& nib, int32_t& hcr) {
       bool eq;
       if (PACKED) {
         // outside the window the codes load from index 0 instead of a branch
@@ -613,9 +622,12 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
         const uint32_t i0 = in ? ui - 1u : 0u, j0 = in ? ui - 1u + static_cast<uint32_t>(sb.c) : 0u;
         eq = in & cd.match(sb.qa, sb.ra, i0, j0);
       } else {
-        eq = tb_eq_bytes(sb, i, qbyte_s, rbyte_s);
+        eq = ld.eq();
       }
       nib = tb_cell(a, goe, eq, E, F, i == sb.icr, hd, En, Fn, hcr);
+    };
+    auto load = [&](const TbSub& sb, int i) {
+      return PACKED ? TbLd{0u, 0u, false} : tb_ld_bytes(sb, i, qbyte_s, rbyte_s);
     };
     // what each half-step sent last: gap values for the neighbours, own H
     int32_t Ha = 0, Hb = 0, Ena = -goe, Fna = -goe, Enb = -goe, Fnb = -goe;
@@ -623,14 +635,16 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     uint32_t pend = 0;
     int ia = 1 - ((k + p) >> 1);  // row of half-step 0 in this pair
     uint8_t* drow = dirs + (ia - 1) * SEG + k;  // this lane's byte of row ia
+    TbLd L0 = load(s0, ia), L1 = load(s1, ia + p);
     for (int t = 0; t < nmax; t += 2, ++ia, drow += SEG) {
+      const TbLd N0 = load(s0, ia + 1), N1 = load(s1, ia + 1 + p);
       uint32_t nib;
       {
         int32_t E = __shfl_up_sync(FULL, Enb, 1, SEG);
         int32_t F = __shfl_down_sync(FULL, Fnb, 1, SEG);
         if (k == 0) E = -goe;
         if (s0.bd) F = -goe;
-        cell(s0, ia, E, F, Ha, Ena, Fna, nib, hcr0);
+        cell(s0, ia, L0, E, F, Ha, Ena, Fna, nib, hcr0);
         // A row's byte is read A's nibble (low) and read B's (high).  Every
         // half-step stores the byte of its row with the other read's last
         // nibble; the half-step that runs read B writes it last, and the
@@ -644,10 +658,12 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
         int32_t F = __shfl_down_sync(FULL, Fna, 1, SEG);
         if (k == 0) E = -goe;
         if (s1.bd) F = -goe;
-        cell(s1, ia + p, E, F, Hb, Enb, Fnb, nib, hcr1);
+        cell(s1, ia + p, L1, E, F, Hb, Enb, Fnb, nib, hcr1);
         drow[p ? SEG : 0] = static_cast<uint8_t>(pend + (nib << 4));
         pend = nib;
       }
+      L0 = N0;
+      L1 = N1;
     }
     const uint32_t ic0 = (s0.icr > 0 && hcr0 == (p ? rd[1].S : rd[0].S)) ? static_cast<uint32_t>(s0.icr) : kNoRow;
     const uint32_t ic1 = (s1.icr > 0 && hcr1 == (p ? rd[0].S : rd[1].S)) ? static_cast<uint32_t>(s1.icr) : kNoRow;
@@ -672,7 +688,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
         for (int X = 0; X < 2; ++X) {
           const int sl = slot(sg, X);
           const WalkRead wr = walk_s[sl];
-          tb_walk<SEG, 32, PACKED>(a, wr, iend_s[sl], X ? 4 : 0, dirs_s[warp][sg] + kTbRowPad * SEG, cd,
+          tb_walk<SEG, 32, Codes<PACKED>>(a, wr, iend_s[sl], X ? 4 : 0, dirs_s[warp][sg] + kTbRowPad * SEG, cd,
                                    static_cast<uint32_t>(sl * kQW), static_cast<uint32_t>(sl * kRW) +
                                    0u, lane, FULL, 0);
           __syncwarp();
@@ -680,14 +696,199 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
       }
     } else {
       // read A, then read B of each segment, walked by the segment's lanes
-      tb_walk<SEG, SEG, PACKED>(a, walk_of(rd[0]), icA, 0, dirs, cd, static_cast<uint32_t>(slot(seg, 0) * kQB),
+      tb_walk<SEG, SEG, Codes<PACKED>>(a, walk_of(rd[0]), icA, 0, dirs, cd, static_cast<uint32_t>(slot(seg, 0) * kQB),
                                 static_cast<uint32_t>(slot(seg, 0) * kRB), k, seg_mask, SEG == 32 ? 0 : seg * SEG);
       __syncwarp(seg_mask);
-      tb_walk<SEG, SEG, PACKED>(a, walk_of(rd[1]), icB, 4, dirs, cd, static_cast<uint32_t>(slot(seg, 1) * kQB),
+      tb_walk<SEG, SEG, Codes<PACKED>>(a, walk_of(rd[1]), icB, 4, dirs, cd, static_cast<uint32_t>(slot(seg, 1) * kQB),
                                 static_cast<uint32_t>(slot(seg, 1) * kRB), k, seg_mask, SEG == 32 ? 0 : seg * SEG);
     }
     __syncwarp();
   }
+}
+
+// ---- The same wavefront with two reads per lane, in the 16-bit halves of each
+// value (DPX s16x2 arithmetic).  A segment holds four reads: pair 0 (reads 0,
+// 1) takes the place of read A above and pair 1 (reads 2, 3) that of read B.
+// The codes are staged per pair as 16-bit words indexed by row (query) and by
+// band offset t = i - 1 + k (window), with codes that never match outside the
+// read and the window, so a cell needs no range test: the XOR of its two words
+// is the prmt selector that picks both reads' scores from a byte table.  Each
+// cell stores its 4 bits inverted (1 = not equal): H = diagonal value, H = E,
+// En = the opened gap value, Fn = the opened gap value, tested per half by
+// min(XOR, 1).  Scores and gap costs must fit the byte table and keep every
+// value inside 16 bits (tb_pair_fits).
+constexpr int kTb4QOff = 16;                          // query word of row i at i - 1 + kTb4QOff
+constexpr int kTb4QN = kMaxReadLen + 3 * kTbRowPad;   // rows -15 .. 288
+constexpr int kTb4ROff = 32;                          // window word of band offset t at t + kTb4ROff
+constexpr int kTb4RN = kMaxReadLen + 6 * kTbRowPad;   // offsets -32 .. 319
+constexpr int kTb4Rows = kMaxReadLen + 2 * kTbRowPad + 1;
+
+__device__ __forceinline__ uint32_t tb_prmt(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// query code of 0-based row i0 (4 outside the read), window code of 0-based
+// column j0 (5 outside columns 1..j*)
+__device__ __forceinline__ uint32_t tb_qcode(const TbArgs& a, const TbRead& x, int i0) {
+  if (!x.has || i0 < 0 || i0 >= static_cast<int>(x.m)) return 4u;
+  const uint32_t* row = a.rpack + static_cast<uint64_t>(x.rd) * kReadWords;
+  return x.strand ? 3u - base_at(row, x.m - 1u - static_cast<uint32_t>(i0)) : base_at(row, static_cast<uint32_t>(i0));
+}
+__device__ __forceinline__ uint32_t tb_rcode(const TbRead& x, int j0) {
+  if (!x.has || j0 < 0 || j0 >= static_cast<int>(x.jstar)) return 5u;
+  return base_at(x.ref, x.ws + static_cast<uint64_t>(j0));
+}
+
+// codes of one read of a pair, for the walk
+struct PairCodes {
+  const uint16_t* q;
+  const uint16_t* r;
+  int shift;  // 0: the pair's low read, 8: its high read
+  int dlo;
+  __device__ __forceinline__ bool match(uint32_t, uint32_t, uint32_t i0, uint32_t j0) const {
+    const uint32_t x = static_cast<uint32_t>(q[static_cast<int>(i0) + kTb4QOff]) ^
+                       static_cast<uint32_t>(r[static_cast<int>(j0) - dlo + kTb4ROff]);
+    return ((x >> shift) & 7u) == 0u;
+  }
+};
+
+template <int SEG>
+__global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave4(TbArgs a, const uint32_t* list, const uint32_t* range) {
+  constexpr int NSEG = 32 / SEG;
+  __shared__ uint16_t dirs_s[kTbWarps][NSEG][kTb4Rows * SEG];
+  __shared__ uint16_t q_s[kTbWarps][NSEG * 2][kTb4QN];
+  __shared__ uint16_t r_s[kTbWarps][NSEG * 2][kTb4RN];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int seg = lane / SEG;
+  const int k = lane % SEG;
+  const uint32_t seg_mask = SEG == 32 ? FULL : (((1u << SEG) - 1u) << (seg * SEG));
+  uint16_t* dirs = dirs_s[warp][seg] + kTbRowPad * SEG;
+  const int32_t goe = a.go + a.ge;
+  auto pack2 = [](int32_t v) { return (static_cast<uint32_t>(v) & 0xffffu) * 0x10001u; };
+  const uint32_t NEG2 = 0x80008000u, ONE2 = 0x00010001u, NGOE2 = pack2(-goe), NGE2 = pack2(-a.ge);
+  const uint32_t nsb = static_cast<uint32_t>(-a.sb) & 0xffu;
+  const uint32_t tab_lo = (static_cast<uint32_t>(a.sa) & 0xffu) | nsb * 0x01010100u, tab_hi = nsb * 0x01010101u;
+  const uint32_t begin = range[0];
+  const uint32_t count = range[1] - begin;
+  constexpr uint32_t kPerWarp = 4 * NSEG;
+  const uint32_t stride = gridDim.x * kTbWarps * kPerWarp;
+  for (uint32_t base = (blockIdx.x * kTbWarps + warp) * kPerWarp; base < count; base += stride) {
+    TbRead rd[4];
+#pragma unroll
+    for (int X = 0; X < 4; ++X) {
+      const uint32_t li = base + 4 * seg + X;
+      rd[X] = tb_load(a, li < count, li < count ? list[begin + li] : 0u);
+    }
+#pragma unroll
+    for (int P = 0; P < 2; ++P) {
+      uint16_t* q = q_s[warp][seg * 2 + P];
+      uint16_t* r = r_s[warp][seg * 2 + P];
+      for (int u = k; u < kTb4QN; u += SEG) {
+        const uint32_t lo = tb_qcode(a, rd[2 * P], u - kTb4QOff), hi = tb_qcode(a, rd[2 * P + 1], u - kTb4QOff);
+        q[u] = static_cast<uint16_t>(lo | ((lo | 8u) << 4) | (hi << 8) | ((hi | 8u) << 12));
+      }
+      for (int u = k; u < kTb4RN; u += SEG) {
+        const int t = u - kTb4ROff;
+        const uint32_t lo = tb_rcode(rd[2 * P], t + rd[2 * P].dlo), hi = tb_rcode(rd[2 * P + 1], t + rd[2 * P + 1].dlo);
+        r[u] = static_cast<uint16_t>(lo | (lo << 4) | (hi << 8) | (hi << 12));
+      }
+    }
+    __syncwarp();
+    int st = 0;
+#pragma unroll
+    for (int X = 0; X < 4; ++X) st = max(st, rd[X].has ? 2 * (rd[X].ihi - 1) + rd[X].w : 0);
+    const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(st + 1)));
+    const int p = k & 1;
+    // per read on this lane's diagonal: the lower band edge and the row crossing j*
+    TbSub u[4];
+#pragma unroll
+    for (int X = 0; X < 4; ++X) u[X] = tb_sub<false>(rd[X], k, 0u, 0u);
+    // half-step 0 runs pair p, half-step 1 the other pair
+    const TbSub& l0 = p ? u[2] : u[0];
+    const TbSub& h0 = p ? u[3] : u[1];
+    const TbSub& l1 = p ? u[0] : u[2];
+    const TbSub& h1 = p ? u[1] : u[3];
+    const uint32_t keep0 = (l0.bd ? 0u : 0xffffu) | (h0.bd ? 0u : 0xffff0000u);
+    const uint32_t keep1 = (l1.bd ? 0u : 0xffffu) | (h1.bd ? 0u : 0xffff0000u);
+    const int cl0 = l0.icr, ch0 = h0.icr, cl1 = l1.icr, ch1 = h1.icr;
+    const int P0 = p, P1 = 1 - p;
+    const uint16_t* q0 = q_s[warp][seg * 2 + P0] + (kTb4QOff - 1);  // [i]: row i
+    const uint16_t* q1 = q_s[warp][seg * 2 + P1] + (kTb4QOff - 1);
+    const uint16_t* r0 = r_s[warp][seg * 2 + P0] + (kTb4ROff - 1 + k);  // [i]: row i on this diagonal
+    const uint16_t* r1 = r_s[warp][seg * 2 + P1] + (kTb4ROff - 1 + k);
+    uint32_t Ha = 0, Hb = 0, Ena = NGOE2, Fna = NGOE2, Enb = NGOE2, Fnb = NGOE2;
+    uint32_t xl0 = 0, xh0 = 0, xl1 = 0, xh1 = 0;  // H where the diagonal crosses j*
+    int ia = 1 - ((k + p) >> 1);
+    uint8_t* d0 = reinterpret_cast<uint8_t*>(dirs + (ia - 1) * SEG + k) + P0;
+    uint8_t* d1 = reinterpret_cast<uint8_t*>(dirs + (ia + p - 1) * SEG + k) + P1;
+    uint32_t x0 = static_cast<uint32_t>(q0[ia]) ^ static_cast<uint32_t>(r0[ia]);
+    uint32_t x1 = static_cast<uint32_t>(q1[ia + p]) ^ static_cast<uint32_t>(r1[ia + p]);
+    auto cell = [&](uint32_t E, uint32_t F, uint32_t x, uint32_t& hd, uint32_t& En, uint32_t& Fn) {
+      const uint32_t hs = __viaddmax_s16x2(hd, tb_prmt(tab_lo, tab_hi, x), NEG2);
+      const uint32_t H = __vimax3_s16x2_relu(hs, E, F);
+      const uint32_t g = __viaddmax_s16x2(H, NGOE2, NEG2);
+      En = __viaddmax_s16x2(E, NGE2, g);
+      Fn = __viaddmax_s16x2(F, NGE2, g);
+      const uint32_t z = __vimin3_u16x2(H ^ hs, ONE2, ONE2) + 2u * __vimin3_u16x2(H ^ E, ONE2, ONE2) +
+                         4u * __vimin3_u16x2(En ^ g, ONE2, ONE2) + 8u * __vimin3_u16x2(Fn ^ g, ONE2, ONE2);
+      hd = H;
+      return z | (z >> 12);
+    };
+    for (int t = 0; t < nmax; t += 2, ++ia, d0 += 2 * SEG, d1 += 2 * SEG) {
+      // the next pair of steps' code words, loaded ahead
+      const uint32_t qn0 = q0[ia + 1], rn0 = r0[ia + 1], qn1 = q1[ia + 1 + p], rn1 = r1[ia + 1 + p];
+      {
+        uint32_t E = __shfl_up_sync(FULL, Enb, 1, SEG);
+        uint32_t F = __shfl_down_sync(FULL, Fnb, 1, SEG);
+        if (k == 0) E = NGOE2;
+        F = (F & keep0) | (NGOE2 & ~keep0);
+        *d0 = static_cast<uint8_t>(cell(E, F, x0, Ha, Ena, Fna));
+        xl0 = ia == cl0 ? Ha : xl0;
+        xh0 = ia == ch0 ? Ha : xh0;
+      }
+      {
+        uint32_t E = __shfl_up_sync(FULL, Ena, 1, SEG);
+        uint32_t F = __shfl_down_sync(FULL, Fna, 1, SEG);
+        if (k == 0) E = NGOE2;
+        F = (F & keep1) | (NGOE2 & ~keep1);
+        const int ib = ia + p;
+        *d1 = static_cast<uint8_t>(cell(E, F, x1, Hb, Enb, Fnb));
+        xl1 = ib == cl1 ? Hb : xl1;
+        xh1 = ib == ch1 ? Hb : xh1;
+      }
+      x0 = qn0 ^ rn0;
+      x1 = qn1 ^ rn1;
+    }
+    // end row of each read: smallest crossing row whose H is the score
+    auto ic = [](int icr, int32_t hx, int32_t S) { return (icr > 0 && hx == S) ? static_cast<uint32_t>(icr) : kNoRow; };
+    const int32_t sl0 = static_cast<int16_t>(xl0 & 0xffffu), sh0 = static_cast<int16_t>(xh0 >> 16);
+    const int32_t sl1 = static_cast<int16_t>(xl1 & 0xffffu), sh1 = static_cast<int16_t>(xh1 >> 16);
+    const uint32_t il0 = ic(cl0, sl0, p ? rd[2].S : rd[0].S), ih0 = ic(ch0, sh0, p ? rd[3].S : rd[1].S);
+    const uint32_t il1 = ic(cl1, sl1, p ? rd[0].S : rd[2].S), ih1 = ic(ch1, sh1, p ? rd[1].S : rd[3].S);
+    uint32_t iend[4] = {p ? il1 : il0, p ? ih1 : ih0, p ? il0 : il1, p ? ih0 : ih1};
+#pragma unroll
+    for (int X = 0; X < 4; ++X)
+#pragma unroll
+      for (int off = SEG / 2; off > 0; off >>= 1) iend[X] = min(iend[X], __shfl_xor_sync(FULL, iend[X], off, SEG));
+    __syncwarp();
+#pragma unroll
+    for (int X = 0; X < 4; ++X) {
+      const PairCodes pc{q_s[warp][seg * 2 + (X >> 1)], r_s[warp][seg * 2 + (X >> 1)], 8 * (X & 1), rd[X].dlo};
+      tb_walk<SEG, SEG, PairCodes, uint16_t, 15u>(a, walk_of(rd[X]), iend[X], 4 * X, dirs, pc, 0u, 0u, k, seg_mask,
+                                                 SEG == 32 ? 0 : seg * SEG);
+      __syncwarp(seg_mask);
+    }
+    __syncwarp();
+  }
+}
+
+// whether the packed wavefront holds these scores: byte-table scores, and every
+// cell value (>= -(go+ge), <= the int16-class score) inside 16 bits
+bool tb_pair_fits(int32_t sa, int32_t sb, int32_t go, int32_t ge) {
+  return sa >= 1 && sa <= 127 && sb >= 1 && sb <= 128 && static_cast<int64_t>(go) + ge <= 8192;
 }
 
 // The same wavefront for bands of 33-64 diagonals: lane k runs band diagonals k
@@ -743,6 +944,8 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint
     int ia = 1 - ((k + p) >> 1);  // diagonal k's row at half-step 0
     uint8_t* drow = dirs + (ia - 1) * V + k;
     const int o1 = p ? V : 0;     // half-step 1 runs read A one row ahead on odd lanes
+    // (loading the codes a step ahead, as k_tb_wave does, costs this kernel
+    // more in registers than it saves)
     for (int t = 0; t < nmax; t += 2, ++ia, drow += V) {
       {
         int32_t E0 = __shfl_up_sync(FULL, Enb0, 1);
@@ -752,10 +955,10 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint
         if (k == 0) E0 = -goe;
         if (s00.bd) F0 = -goe;
         if (s01.bd) F1 = -goe;
-        const uint32_t n0 = tb_cell(a, goe, tb_eq_bytes(s00, ia, qbyte_s, rbyte_s), E0, F0, ia == s00.icr, Ha0,
+        const uint32_t n0 = tb_cell(a, goe, tb_ld_bytes(s00, ia, qbyte_s, rbyte_s).eq(), E0, F0, ia == s00.icr, Ha0,
                                     Ena0, Fna0, hcr00);
-        const uint32_t n1 = tb_cell(a, goe, tb_eq_bytes(s01, ia - 16, qbyte_s, rbyte_s), E1, F1, ia - 16 == s01.icr,
-                                    Ha1, Ena1, Fna1, hcr01);
+        const uint32_t n1 = tb_cell(a, goe, tb_ld_bytes(s01, ia - 16, qbyte_s, rbyte_s).eq(), E1, F1,
+                                    ia - 16 == s01.icr, Ha1, Ena1, Fna1, hcr01);
         // bytes as in k_tb_wave: read A's nibble low, read B's high
         drow[0] = static_cast<uint8_t>(pend0 + (n0 << 4));
         drow[-kLag] = static_cast<uint8_t>(pend1 + (n1 << 4));
@@ -771,10 +974,10 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint
         if (s10.bd) F0 = -goe;
         if (s11.bd) F1 = -goe;
         const int ib = ia + p;
-        const uint32_t n0 = tb_cell(a, goe, tb_eq_bytes(s10, ib, qbyte_s, rbyte_s), E0, F0, ib == s10.icr, Hb0,
+        const uint32_t n0 = tb_cell(a, goe, tb_ld_bytes(s10, ib, qbyte_s, rbyte_s).eq(), E0, F0, ib == s10.icr, Hb0,
                                     Enb0, Fnb0, hcr10);
-        const uint32_t n1 = tb_cell(a, goe, tb_eq_bytes(s11, ib - 16, qbyte_s, rbyte_s), E1, F1, ib - 16 == s11.icr,
-                                    Hb1, Enb1, Fnb1, hcr11);
+        const uint32_t n1 = tb_cell(a, goe, tb_ld_bytes(s11, ib - 16, qbyte_s, rbyte_s).eq(), E1, F1,
+                                    ib - 16 == s11.icr, Hb1, Enb1, Fnb1, hcr11);
         drow[o1] = static_cast<uint8_t>(pend0 + (n0 << 4));
         drow[o1 - kLag] = static_cast<uint8_t>(pend1 + (n1 << 4));
         pend0 = n0;
@@ -790,9 +993,9 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint
     const uint32_t icA = __reduce_min_sync(FULL, p ? ic1 : ic0);
     const uint32_t icB = __reduce_min_sync(FULL, p ? ic0 : ic1);
     __syncwarp();
-    tb_walk<V, 32, false>(a, walk_of(rd[0]), icA, 0, dirs, cd, qA, rA, k, FULL, 0);
+    tb_walk<V, 32, Codes<false>>(a, walk_of(rd[0]), icA, 0, dirs, cd, qA, rA, k, FULL, 0);
     __syncwarp();
-    tb_walk<V, 32, false>(a, walk_of(rd[1]), icB, 4, dirs, cd, qB, rB, k, FULL, 0);
+    tb_walk<V, 32, Codes<false>>(a, walk_of(rd[1]), icB, 4, dirs, cd, qB, rB, k, FULL, 0);
     __syncwarp();
   }
 }
@@ -951,7 +1154,9 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
     return cudaPeekAtLastError() == cudaSuccess;
   };
   // widest bands (longest kernels) first
-  if (!wave(k_tb_wave2, 6, 2) || !wave(k_tb_wave<32>, 5, 2) || !wave(k_tb_wave<16>, 4, 4) || !wave(k_tb_wave<4>, 2, 16) ||
+  const bool pair = tb_pair_fits(a.sa, a.sb, a.go, a.ge);
+  if (!wave(k_tb_wave2, 6, 2) || !(pair ? wave(k_tb_wave4<32>, 5, 4) : wave(k_tb_wave<32>, 5, 2)) ||
+      !(pair ? wave(k_tb_wave4<16>, 4, 8) : wave(k_tb_wave<16>, 4, 4)) || !wave(k_tb_wave<4>, 2, 16) ||
       !wave(k_tb_wave<1>, 0, 64) || !wave(k_tb_wave<8>, 3, 8) || !wave(k_tb_wave<2>, 1, 32))
     return -1;
   const size_t smem = static_cast<size_t>(kMaxWinLen) * 32 * sizeof(uint32_t);

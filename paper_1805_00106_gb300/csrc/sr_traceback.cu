@@ -729,16 +729,46 @@ __device__ __forceinline__ uint32_t tb_prmt(uint32_t a, uint32_t b, uint32_t c) 
   return d;
 }
 
-// query code of 0-based row i0 (4 outside the read), window code of 0-based
-// column j0 (5 outside columns 1..j*)
-__device__ __forceinline__ uint32_t tb_qcode(const TbArgs& a, const TbRead& x, int i0) {
-  if (!x.has || i0 < 0 || i0 >= static_cast<int>(x.m)) return 4u;
-  const uint32_t* row = a.rpack + static_cast<uint64_t>(x.rd) * kReadWords;
-  return x.strand ? 3u - base_at(row, x.m - 1u - static_cast<uint32_t>(i0)) : base_at(row, static_cast<uint32_t>(i0));
+// 16 packed codes at positions lo .. lo + 15 of a 2-bit array of nw words (0
+// for words outside it)
+__device__ __forceinline__ uint32_t tb_codes16(const uint32_t* w, int64_t lo, int64_t nw) {
+  const int64_t i = lo >> 4;  // floor
+  const uint32_t sh = static_cast<uint32_t>(lo & 15) * 2u;
+  const uint32_t x = (i >= 0 && i < nw) ? w[i] : 0u;
+  const uint32_t y = (i + 1 >= 0 && i + 1 < nw) ? w[i + 1] : 0u;
+  return sh ? (x >> sh) | (y << (32u - sh)) : x;
 }
-__device__ __forceinline__ uint32_t tb_rcode(const TbRead& x, int j0) {
-  if (!x.has || j0 < 0 || j0 >= static_cast<int>(x.jstar)) return 5u;
-  return base_at(x.ref, x.ws + static_cast<uint64_t>(j0));
+
+// A pair's query words for rows 16 c - 15 .. 16 c (code 4 outside the read) and
+// its window words for band offsets 16 c - 32 .. 16 c - 17 (code 5 outside
+// columns 1..j*), from the packed read rows and reference: one chunk of 16
+// words per call, a few loads instead of one per code.
+__device__ __forceinline__ uint32_t tb_qchunk(const TbArgs& a, const TbRead& x, int c, uint32_t* valid) {
+  *valid = 0u;
+  const int i0 = 16 * (c - 1);  // first 0-based row of the chunk (chunks are word-aligned)
+  if (!x.has || i0 < 0) return 0u;
+  const uint32_t* row = a.rpack + static_cast<uint64_t>(x.rd) * kReadWords;
+  const int m = static_cast<int>(x.m);
+  const int n = min(max(m - i0, 0), 16);
+  *valid = n >= 16 ? 0xffffu : ((1u << n) - 1u);
+  if (!n) return 0u;
+  if (!x.strand) return tb_codes16(row, i0, kReadWords);
+  // reverse complement: row i0 + b holds 3 - base(m - 1 - i0 - b)
+  uint32_t v = __brev(tb_codes16(row, m - 16 - i0, kReadWords));
+  v = ((v >> 1) & 0x55555555u) | ((v & 0x55555555u) << 1);
+  return ~v;
+}
+__device__ __forceinline__ uint32_t tb_rchunk(const TbRead& x, int c, uint32_t* valid) {
+  *valid = 0u;
+  if (!x.has) return 0u;
+  const int j0 = 16 * c - kTb4ROff + x.dlo;  // first 0-based window column of the chunk
+  uint32_t v = 0u;
+#pragma unroll
+  for (int b = 0; b < 16; ++b) v |= (j0 + b >= 0 && j0 + b < static_cast<int>(x.jstar)) ? (1u << b) : 0u;
+  *valid = v;
+  if (!v) return 0u;
+  const int64_t nw = static_cast<int64_t>((x.ws + x.jstar + 15) / 16) + 1;
+  return tb_codes16(x.ref, static_cast<int64_t>(x.ws) + j0, nw);
 }
 
 // codes of one read of a pair, for the walk
@@ -786,14 +816,25 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave4(TbArgs a, const uint
     for (int P = 0; P < 2; ++P) {
       uint16_t* q = q_s[warp][seg * 2 + P];
       uint16_t* r = r_s[warp][seg * 2 + P];
-      for (int u = k; u < kTb4QN; u += SEG) {
-        const uint32_t lo = tb_qcode(a, rd[2 * P], u - kTb4QOff), hi = tb_qcode(a, rd[2 * P + 1], u - kTb4QOff);
-        q[u] = static_cast<uint16_t>(lo | ((lo | 8u) << 4) | (hi << 8) | ((hi | 8u) << 12));
+      for (int c = k; c < kTb4QN / 16; c += SEG) {
+        uint32_t ma, mb;
+        const uint32_t va = tb_qchunk(a, rd[2 * P], c, &ma), vb = tb_qchunk(a, rd[2 * P + 1], c, &mb);
+#pragma unroll 2
+        for (int b = 0; b < 16; ++b) {
+          const uint32_t lo = (ma >> b) & 1u ? (va >> (2 * b)) & 3u : 4u;
+          const uint32_t hi = (mb >> b) & 1u ? (vb >> (2 * b)) & 3u : 4u;
+          q[16 * c + b] = static_cast<uint16_t>(lo | ((lo | 8u) << 4) | (hi << 8) | ((hi | 8u) << 12));
+        }
       }
-      for (int u = k; u < kTb4RN; u += SEG) {
-        const int t = u - kTb4ROff;
-        const uint32_t lo = tb_rcode(rd[2 * P], t + rd[2 * P].dlo), hi = tb_rcode(rd[2 * P + 1], t + rd[2 * P + 1].dlo);
-        r[u] = static_cast<uint16_t>(lo | (lo << 4) | (hi << 8) | (hi << 12));
+      for (int c = k; c < kTb4RN / 16; c += SEG) {
+        uint32_t ma, mb;
+        const uint32_t va = tb_rchunk(rd[2 * P], c, &ma), vb = tb_rchunk(rd[2 * P + 1], c, &mb);
+#pragma unroll 2
+        for (int b = 0; b < 16; ++b) {
+          const uint32_t lo = (ma >> b) & 1u ? (va >> (2 * b)) & 3u : 5u;
+          const uint32_t hi = (mb >> b) & 1u ? (vb >> (2 * b)) & 3u : 5u;
+          r[16 * c + b] = static_cast<uint16_t>(lo | (lo << 4) | (hi << 8) | (hi << 12));
+        }
       }
     }
     __syncwarp();

@@ -121,13 +121,30 @@ struct TbBand {
 #ifdef __CUDACC__
 __host__ __device__ inline TbBand tb_band(int32_t sa, int32_t go, int32_t ge, int32_t S, uint32_t jstar,
                                           uint32_t ilo, uint32_t ihi) {
+  // g(i): the most gap bases an alignment of score S ending in (i, j*) can
+  // hold; it lies in diagonals j* - i - g(i) .. j* - i + g(i).  The band is the
+  // union over the end rows ilo..ihi.  Its lower end is row ihi's.  On the upper
+  // end, j* - i + g(i) falls while g = 0, is monotone while g > 0 and i <= j*,
+  // and falls again past j*, so its maximum is at ilo or at an end of the middle
+  // piece.
+  const int64_t J = jstar, lo = ilo, hi = ihi;
+  auto g = [&](int64_t i) -> int64_t {
+    const int64_t v = (static_cast<int64_t>(sa) * (i < J ? i : J) - S - go) / ge;
+    return v > 0 ? v : 0;
+  };
+  auto f = [&](int64_t i) { return J - i + g(i); };
+  const int64_t i1 = (static_cast<int64_t>(S) + go + ge + sa - 1) / sa;  // first row with g > 0 (below j*)
+  int64_t up = f(lo);
+  if (i1 > lo && i1 <= hi) up = f(i1) > up ? f(i1) : up;
+  if (J >= lo && J <= hi) up = f(J) > up ? f(J) : up;
+  if (J + 1 > lo && J + 1 <= hi) up = f(J + 1) > up ? f(J + 1) : up;
+  up = f(hi) > up ? f(hi) : up;
   TbBand b;
-  const int64_t gl = (static_cast<int64_t>(sa) * (ihi < jstar ? ihi : jstar) - S - go) / ge;
   b.ilo = static_cast<int>(ilo);
   b.ihi = static_cast<int>(ihi);
-  b.g = gl > 0 ? static_cast<int>(gl) : 0;
-  b.w = b.ihi - b.ilo + 2 * b.g + 1;
-  b.dlo = static_cast<int>(jstar) - b.ihi - b.g;
+  b.g = static_cast<int>(g(hi));
+  b.dlo = static_cast<int>(J - hi - b.g);
+  b.w = static_cast<int>(up - b.dlo + 1);
   return b;
 }
 // smallest row that can end an alignment of score S (S <= sa * i)

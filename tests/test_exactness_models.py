@@ -9,7 +9,9 @@ on, checked against the oracle on random cases (CPU, no GPU):
 2. the traceback band: a DP restricted to the diagonals that can hold any
    alignment of score S ending in column j* at a row in [ceil(S/match), m]
    (cells outside: H = 0, E = F = -inf) finds the end row (smallest i with
-   H(i, j*) = S) and reproduces the full-DP traceback exactly.
+   H(i, j*) = S) and reproduces the full-DP traceback exactly; the band is
+   the union over those end rows of each row's diagonals, and the closed form
+   the kernels evaluate equals that union.
 
 These models mirror the kernels' arithmetic order, not their code."""
 import random
@@ -64,11 +66,34 @@ def systolic_best(q, r, sa, sb, go, ge, G, R, extra, virt_sc, mode):
     return score, (0xffff - (key & 0xffff)) if score else 0
 
 
+def gap_bound(i, jstar, S, sa, go, ge):
+    """Most gap bases an alignment of score S ending in (i, j*) can hold."""
+    return max(0, (sa * min(i, jstar) - S - go) // ge)
+
+
+def band_union(sa, go, ge, S, jstar, ilo, ihi):
+    """(dlo, w): the diagonals j* - i - g(i) .. j* - i + g(i) of every end row
+    i in ilo..ihi, united row by row."""
+    lo = min(jstar - i - gap_bound(i, jstar, S, sa, go, ge) for i in range(ilo, ihi + 1))
+    hi = max(jstar - i + gap_bound(i, jstar, S, sa, go, ge) for i in range(ilo, ihi + 1))
+    return lo, hi - lo + 1
+
+
+def band_closed_form(sa, go, ge, S, jstar, ilo, ihi):
+    """The kernels' evaluation of the same union: the lower end from row ihi,
+    the upper end as the largest of j* - i + g(i) at ilo, ihi, the first row with
+    g > 0, j* and j* + 1 (the ends of its monotone pieces)."""
+    f = lambda i: jstar - i + gap_bound(i, jstar, S, sa, go, ge)
+    i1 = -(-(S + go + ge) // sa)
+    cands = [ilo, ihi] + [i for i in (i1, jstar, jstar + 1) if ilo <= i <= ihi]
+    dlo = jstar - ihi - gap_bound(ihi, jstar, S, sa, go, ge)
+    return dlo, max(f(i) for i in cands) - dlo + 1
+
+
 def band_traceback(q, r, sa, sb, go, ge, S, jstar, mode):
     goe, m = go + ge, len(q)
     ilo, ihi = (m, m) if mode == 1 else (max(1, -(-S // sa)), m)
-    g = max(0, (sa * min(ihi, jstar) - S - go) // ge)
-    w, dlo = (ihi - ilo) + 2 * g + 1, jstar - ihi - g
+    dlo, w = band_union(sa, go, ge, S, jstar, ilo, ihi)
     H, Ev, Fv, dirs = {}, {}, {}, {}
     for i in range(1, ihi + 1):
         for k in range(w):
@@ -171,3 +196,18 @@ def test_band_finds_end_row_and_full_dp_path(seed):
             got = band_traceback(q, r, sa, sb, go, ge, o["score"], o["end_j"], mode)
             ops = "".join(c * ln for ln, c in [(ln, "MID?S"[op]) for ln, op in o["cigar"]] if c != "S")
             assert got == (o["start_i"], o["start_j"], o["end_i"], ops), (q, r, (sa, sb, go, ge), mode)
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_band_closed_form_is_the_union(seed):
+    rng = random.Random(seed)
+    for _ in range(3000):
+        sa, go, ge = rng.randint(1, 6), rng.randint(0, 12), rng.randint(1, 6)
+        m = rng.randint(1, 256)
+        jstar = rng.randint(1, 400)
+        S = rng.randint(1, sa * min(m, jstar))
+        ilo = max(1, -(-S // sa))
+        if ilo > m:
+            continue
+        for lo, hi in ((ilo, m), (m, m), (ilo, ilo)):
+            assert band_closed_form(sa, go, ge, S, jstar, lo, hi) == band_union(sa, go, ge, S, jstar, lo, hi)

@@ -19,7 +19,7 @@ NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SRCS = ["sr_extend.cu", "sr_extend_m0.cu", "sr_extend_m1.cu", "sr_extend_m2.cu", "sr_kernels.cu", "sr_report.cu", "sr_cal.cu",
            "sr_traceback.cu", "sr_noalloc.cu"]
-CPP_SRCS = ["sr_index.cpp", "sr_session.cpp", "sr_serve.cpp", "sr_sam.cpp"]
+CPP_SRCS = ["sr_index.cpp", "sr_session.cpp", "sr_serve.cpp", "sr_sam.cpp", "sr_pool.cpp"]
 _lock = threading.Lock()
 
 

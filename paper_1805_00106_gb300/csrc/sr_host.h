@@ -2,6 +2,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <functional>
+
 #include "../../include/sr.h"
 #include <nvtx3/nvToolsExt.h>
 
@@ -27,6 +29,10 @@ struct IndexTables {
 IndexTables index_tables(const sr_index* idx);
 // a zeroed sr_results whose arrays the caller allocates with malloc (released by sr_results_free)
 sr_results* results_alloc();
+// threads of the host pool (workers + the caller), at most 16
+unsigned host_threads();
+// fn(0) .. fn(n - 1) spread over the pool's threads; returns when all are done
+void parallel_for(uint32_t n, const std::function<void(uint32_t)>& fn);
 // NVTX range over a host stage (visible in profiler timelines; free without a tool attached)
 struct Trace {
   explicit Trace(const char* name) { nvtxRangePushA(name); }

@@ -587,9 +587,12 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
     int why = 0;  // 1 offsets, 2 read length, 3 window count, 4 window
     uint64_t bad_win = 0;
   };
-  const uint32_t hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  const uint32_t nthr = (n < 65536u) ? 1u : hw;
+  const uint32_t nthr = (n < 65536u) ? 1u : 4u * host_threads();
   std::vector<Part> parts(nthr);
+  static_assert((kMaxRefs & (kMaxRefs - 1)) == 0, "ref_id masking");
+  uint64_t lens16[kMaxRefs] = {};  // reference lengths, indexed by ref_id & (kMaxRefs - 1)
+  for (uint32_t q = 0; q < s->n_refs && q < static_cast<uint32_t>(kMaxRefs); ++q) lens16[q] = s->lens[q];
+  const uint32_t nref = s->n_refs;
   auto check = [&](uint32_t t) {
     Part& P = parts[t];
     const uint32_t r0 = static_cast<uint32_t>(static_cast<uint64_t>(n) * t / nthr);
@@ -613,28 +616,35 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
         P.why = 3;
         return;
       }
+      // all of a read's windows without a branch, then the first bad one if any
+      uint64_t suml = 0;
+      uint32_t bad = 0;
       for (uint64_t k = c0; k < c1; ++k) {
         const uint32_t ref = cands->ref_id[k], len = cands->win_len[k];
-        if (ref >= s->n_refs || cands->strand[k] > 1 || len < 1 || len > SR_MAX_WIN_LEN ||
-            cands->win_start[k] > s->lens[ref] || cands->win_start[k] + len > s->lens[ref]) {
-          P.bad_read = r;
-          P.why = 4;
-          P.bad_win = k;
-          return;
-        }
-        P.cells += m * len;
+        const uint64_t L = lens16[ref & (kMaxRefs - 1)], w0 = cands->win_start[k];
+        bad |= static_cast<uint32_t>(ref >= nref) | static_cast<uint32_t>(cands->strand[k] > 1) |
+               static_cast<uint32_t>(len - 1u >= static_cast<uint32_t>(SR_MAX_WIN_LEN)) |
+               static_cast<uint32_t>(w0 > L) | static_cast<uint32_t>(w0 + len > L);
+        suml += len;
       }
+      if (bad) {
+        for (uint64_t k = c0; k < c1; ++k) {
+          const uint32_t ref = cands->ref_id[k], len = cands->win_len[k];
+          if (ref >= nref || cands->strand[k] > 1 || len < 1 || len > SR_MAX_WIN_LEN ||
+              cands->win_start[k] > s->lens[ref] || cands->win_start[k] + len > s->lens[ref]) {
+            P.bad_read = r;
+            P.why = 4;
+            P.bad_win = k;
+            return;
+          }
+        }
+      }
+      P.cells += m * suml;
       P.by_len[m] += c1 - c0;
       P.max_m = std::max<uint32_t>(P.max_m, static_cast<uint32_t>(m));
     }
   };
-  if (nthr == 1) {
-    check(0);
-  } else {
-    std::vector<std::thread> th;
-    for (uint32_t t = 0; t < nthr; ++t) th.emplace_back(check, t);
-    for (auto& x : th) x.join();
-  }
+  parallel_for(nthr, check);
   uint64_t cells = 0;
   uint32_t max_m = 0;
   uint64_t by_len[kMaxReadLen + 1] = {};

@@ -359,3 +359,24 @@ def test_traceback_band_classes(sr):
     assert np.sum(ok & (w_row > 64)) > 5
     s = _session(sr, w)
     _check(gpu_run(s, w), o)
+
+
+def test_bad_window_in_a_large_batch_reports_the_first(sr):
+    """Batches of 64k reads and more are validated in parallel on the host pool:
+    the first malformed window (lowest index) is reported, before any launch."""
+    w = S.workload("c2", scale=0.08, seed=41)
+    assert len(w["read_off"]) - 1 >= 65536
+    s = _session(sr, w)
+    n_items = len(w["c_len"])
+    for field, value in (("c_ref", 7), ("c_len", 0), ("c_strand", 2), ("c_start", 1 << 60)):
+        bad = dict(w, **{field: w[field].copy()})
+        k1, k2 = n_items // 3, (2 * n_items) // 3
+        bad[field][k2] = value
+        bad[field][k1] = value
+        with pytest.raises(sr.SrError) as e:
+            gpu_run(s, bad)
+        assert e.value.status == sr.SR_EINVAL, field
+        assert f"window {k1} " in str(e.value), (field, str(e.value))
+    # the same batch, unmodified, still runs
+    g = gpu_run(s, w, want_cigar=0)
+    assert len(g["item_score"]) == n_items

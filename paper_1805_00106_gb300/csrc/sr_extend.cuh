@@ -192,8 +192,17 @@ __device__ __forceinline__ uint32_t read_code(const uint32_t* row, uint32_t m, u
   return strand ? 3u - base_at(row, m - 1u - i) : base_at(row, i);
 }
 
+// Blocks of 128 threads per SM the register budget is cut for: with 24 rows per
+// lane or fewer (22 in final-row mode, which keeps more per row) the sweep fits
+// 128 registers without spilling (4 blocks, 16 warps per SM); up to 27 rows
+// need 168 (3 blocks), more up to 255.
+template <int R, int MODE>
+constexpr int ext_min_blocks() {
+  return R <= (MODE == 1 ? 22 : 24) ? 4 : (R <= 27 ? 3 : 2);
+}
+
 template <int G, int R, int MODE, bool PERSIST>
-__global__ void __launch_bounds__(128) k_extend16(ExtArgs a) {
+__global__ void __launch_bounds__(128, ext_min_blocks<R, MODE>()) k_extend16(ExtArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GPW = 32 / G;
   const int lane = threadIdx.x & 31;

@@ -41,7 +41,7 @@ static sr_status cuda_error(const char* where, cudaError_t e) {
 static std::mutex g_tune_mu;
 // defaults = the autotuner's picks on GB300 for the c2 score parameters
 static TuneBin g_bins[kNumBins] = {
-    {64, 4, 16},   {80, 4, 20},   {96, 8, 12},   {104, 8, 13},  {112, 8, 14},  {120, 8, 15},
+    {64, 4, 16},   {80, 8, 10},   {96, 8, 12},   {104, 8, 13},  {112, 8, 14},  {120, 8, 15},
     {128, 8, 16},  {136, 8, 17},  {144, 8, 18},  {152, 8, 19},  {160, 8, 20},  {168, 8, 21},
     {176, 8, 22},  {184, 8, 23},  {192, 8, 24},  {200, 8, 25},  {208, 8, 26},  {216, 8, 27},
     {224, 16, 14}, {232, 16, 15}, {240, 16, 15}, {248, 16, 16}, {256, 16, 16}};

@@ -140,10 +140,10 @@ struct sr_session {
   // pinned host blocks that held fetched results, kept for the next fetch
   std::mutex pool_mu;
   std::vector<std::pair<void*, uint64_t>> pool;
-  // the arena of the last freed batch, kept for the next one (not counted in hbm_used)
+  // arenas of freed batches, kept for the next ones (not counted in hbm_used):
+  // up to two, so a two-deep serving pipeline allocates nothing in steady state
   std::mutex spare_mu;
-  void* spare = nullptr;
-  uint64_t spare_bytes = 0;
+  std::vector<std::pair<void*, uint64_t>> spares;
   // streams and events of freed batches
   std::mutex res_mu;
   std::vector<BatchRes> res_pool;
@@ -155,7 +155,7 @@ struct sr_batch {
   BatchDev d{};
   void* arena = nullptr;
   uint64_t bytes = 0;        // carved size (counted in the session's hbm_used)
-  uint64_t arena_bytes = 0;  // allocated size (>= bytes when taken from the session's spare)
+  uint64_t arena_bytes = 0;  // allocated size (>= bytes: a kept arena, or allocated with headroom)
   uint32_t n_reads = 0;
   uint64_t n_items = 0;
   uint64_t cells = 0;
@@ -290,7 +290,7 @@ static void session_release(sr_session* s) {
   for (auto* p : s->idx_bufs) cudaFree(p);
   for (auto& b : s->pool) cudaFreeHost(b.first);
   for (auto& r : s->res_pool) res_destroy(r);
-  if (s->spare) cudaFree(s->spare);
+  for (auto& a : s->spares) cudaFree(a.first);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
@@ -466,29 +466,37 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   c.take(d.out_per_ref, static_cast<uint64_t>(n) * s->n_refs);
   b->bytes = c.off + 256;
   {
+    // the smallest kept arena that holds this batch
     std::lock_guard<std::mutex> lk(s->spare_mu);
-    if (s->spare && s->spare_bytes >= b->bytes) {
-      b->arena = s->spare;
-      b->arena_bytes = s->spare_bytes;
-      s->spare = nullptr;
-      s->spare_bytes = 0;
+    int pick = -1;
+    for (int i = 0; i < static_cast<int>(s->spares.size()); ++i)
+      if (s->spares[i].second >= b->bytes && (pick < 0 || s->spares[i].second < s->spares[pick].second)) pick = i;
+    if (pick >= 0) {
+      b->arena = s->spares[pick].first;
+      b->arena_bytes = s->spares[pick].second;
+      s->spares.erase(s->spares.begin() + pick);
     }
   }
   if (!b->arena) {
-    cudaError_t e = cudaMalloc(&b->arena, b->bytes);
+    // a quarter of headroom, so batches a little larger later reuse this arena
+    uint64_t want = b->bytes + b->bytes / 4;
+    cudaError_t e = cudaMalloc(&b->arena, want);
     if (e != cudaSuccess) {
-      // the cached arena may be what is in the way
       cudaGetLastError();
-      void* sp = nullptr;
+      want = b->bytes;
+      e = cudaMalloc(&b->arena, want);
+    }
+    if (e != cudaSuccess) {
+      // the kept arenas may be what is in the way
+      cudaGetLastError();
+      std::vector<std::pair<void*, uint64_t>> sp;
       {
         std::lock_guard<std::mutex> lk(s->spare_mu);
-        sp = s->spare;
-        s->spare = nullptr;
-        s->spare_bytes = 0;
+        sp.swap(s->spares);
       }
-      if (sp) {
-        cudaFree(sp);
-        e = cudaMalloc(&b->arena, b->bytes);
+      if (!sp.empty()) {
+        for (auto& a : sp) cudaFree(a.first);
+        e = cudaMalloc(&b->arena, want);
       }
       if (e != cudaSuccess) {
         b->arena = nullptr;
@@ -498,7 +506,7 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
                          static_cast<unsigned long long>(c.off));
       }
     }
-    b->arena_bytes = b->bytes;
+    b->arena_bytes = want;
   }
   cudaError_t e = cudaSuccess;
   char* base = static_cast<char*>(b->arena);
@@ -705,14 +713,19 @@ extern "C" void sr_batch_free(sr_batch* b) {
   }
   if (b->arena) {
     cudaStreamSynchronize(b->stream);
-    // keep the larger of this arena and the session's spare for the next batch
-    void* drop = b->arena;
+    // keep this arena for the next batches; past two kept, drop the smallest
+    void* drop = nullptr;
     {
       std::lock_guard<std::mutex> lk(b->s->spare_mu);
-      if (!b->s->spare || b->s->spare_bytes < b->arena_bytes) {
-        drop = b->s->spare;
-        b->s->spare = b->arena;
-        b->s->spare_bytes = b->arena_bytes;
+      auto& sp = b->s->spares;
+      sp.emplace_back(b->arena, b->arena_bytes);
+      if (sp.size() > 2) {
+        auto it = std::min_element(sp.begin(), sp.end(),
+                                   [](const std::pair<void*, uint64_t>& x, const std::pair<void*, uint64_t>& y) {
+                                     return x.second < y.second;
+                                   });
+        drop = it->first;
+        sp.erase(it);
       }
     }
     if (drop) cudaFree(drop);

@@ -51,14 +51,27 @@ __global__ void k_pack_reads(const char* bases, const uint64_t* off, uint32_t n_
   const bool len_ok = o1 > o0 && m <= static_cast<uint64_t>(kMaxReadLen);
   uint32_t v = 0;
   bool bad = false;
-  if (len_ok) {
+  if (len_ok && 16u * w < m) {
+    // this word's bases as aligned 32-bit loads (an aligned word holding a valid
+    // byte never crosses a page), realigned by a funnel shift
+    const uint32_t nv = static_cast<uint32_t>(m - 16u * w < 16u ? m - 16u * w : 16u);  // valid bases
+    const uintptr_t at = reinterpret_cast<uintptr_t>(bases + o0 + 16u * w);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(at & ~static_cast<uintptr_t>(3));
+    const uint32_t lead = static_cast<uint32_t>(at & 3u);
+    uint32_t x[5];
 #pragma unroll
-    for (int b = 0; b < 16; ++b) {
-      const uint64_t p = static_cast<uint64_t>(w) * 16 + b;
-      if (p < m) {
-        uint32_t c = ascii_code(static_cast<uint8_t>(bases[o0 + p]));
-        bad |= c > 3u;
-        v |= (c & 3u) << (2 * b);
+    for (int k = 0; k < 5; ++k) x[k] = 4u * k < lead + nv ? src[k] : 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t y = __funnelshift_r(x[k], x[k + 1], 8u * lead);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t b = 4u * k + q;
+        if (b < nv) {
+          const uint32_t c = ascii_code((y >> (8 * q)) & 0xffu);
+          bad |= c > 3u;
+          v |= (c & 3u) << (2 * b);
+        }
       }
     }
   }
@@ -70,16 +83,16 @@ __global__ void k_pack_reads(const char* bases, const uint64_t* off, uint32_t n_
   if (bad) atomicOr(status, kStBadBase);
 }
 
-// warp per read: item -> read map and window validation
+// eight lanes per read: item -> read map and window validation
 __global__ void k_items(const uint64_t* cand_off, uint32_t n_reads, const uint8_t* c_ref,
                         const uint8_t* c_strand, const uint64_t* c_start, const uint32_t* c_len,
                         DevRefs refs, uint32_t* item_read, uint32_t* status) {
-  const uint64_t r = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const uint64_t r = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 3;
+  const int lane = threadIdx.x & 7;
   if (r >= n_reads) return;
   const uint64_t c0 = cand_off[r], c1 = cand_off[r + 1];
   bool bad = c1 < c0;
-  for (uint64_t c = c0 + lane; c < c1 && !bad; c += 32) {
+  for (uint64_t c = c0 + lane; c < c1 && !bad; c += 8) {
     item_read[c] = static_cast<uint32_t>(r);
     const uint32_t k = c_ref[c];
     const uint32_t n = c_len[c];
@@ -395,7 +408,7 @@ int launch_prepare(const BatchDev& b, const DevRefs& refs, cudaStream_t st) {
   const uint64_t t = static_cast<uint64_t>(b.n_reads) * 16;
   k_pack_reads<<<static_cast<unsigned>((t + 255) / 256), 256, 0, st>>>(
       b.bases, b.read_off, b.n_reads, b.rpack, b.rlen, b.status);
-  const uint64_t tw = static_cast<uint64_t>(b.n_reads) * 32;
+  const uint64_t tw = static_cast<uint64_t>(b.n_reads) * 8;
   k_items<<<static_cast<unsigned>((tw + 255) / 256), 256, 0, st>>>(
       b.cand_off, b.n_reads, b.c_ref, b.c_strand, b.c_start, b.c_len, refs, b.item_read, b.status);
   return cudaPeekAtLastError() == cudaSuccess ? 2 : -1;

@@ -92,6 +92,7 @@ struct BatchDev {
   uint8_t* tb_flag = nullptr;     // n_reads: how the winner's end row is found (kTbFlag*)
   uint32_t* tb_list = nullptr;    // 2 * n_reads: per-read sort code, then reads sorted by code
   uint32_t* tb_count = nullptr;   // kTbCountWords: code histogram, cursors, bucket ranges
+  uint32_t* tb_dirs = nullptr;    // tb_thread_warps(n_reads) * 256 rows * 32 lanes: narrow-band direction words
   uint32_t* cigar_off = nullptr;  // n_reads + 1 (exclusive scan of lengths)
   uint32_t* cigar = nullptr;      // compacted, n_reads * kCigarStride capacity
   uint8_t* read_class = nullptr;  // n_reads
@@ -109,6 +110,13 @@ constexpr int kTbBuckets = 8;                        // band <= 1 / 2 / 4 / 8 / 
 constexpr int kTbCodes = kTbBuckets * kMaxReadLen;   // code = bucket * 256 + (256 - last row)
 constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + 8;
 constexpr int kTbMaxBand = 64;
+// warps of the one-thread-per-read narrow-band traceback (each owns a scratch
+// of 256 rows x 32 lanes of direction words)
+constexpr uint32_t kTbThreadMaxWarps = 2048;
+inline uint32_t tb_thread_warps(uint32_t n_reads) {
+  const uint32_t w = (n_reads + 31u) / 32u;
+  return w < kTbThreadMaxWarps ? (w ? w : 1u) : kTbThreadMaxWarps;
+}
 
 // Diagonal band of a winner (score S >= 1 ending in column j*) whose end row lies
 // in [ilo, ihi]: every alignment of score S ending at (i, j*) has at most

@@ -377,6 +377,7 @@ uint64_t batch_bytes_estimate(uint32_t n_reads, uint64_t n_items, uint64_t n_bas
   c.take(p1, n_reads);
   c.take(p4, 4ull * n_reads);
   c.take(p4, 4);
+  c.take(p4, static_cast<uint64_t>(tb_thread_warps(n_reads)) * kMaxReadLen * 32);
   return c.off + 256;
 }
 }  // namespace sr
@@ -462,6 +463,7 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   c.take(d.tb_flag, n);
   c.take(d.tb_list, 2ull * n);
   c.take(d.tb_count, kTbCountWords);
+  c.take(d.tb_dirs, static_cast<uint64_t>(tb_thread_warps(n)) * kMaxReadLen * 32);
   c.take(d.out_best, n);
   c.take(d.out_per_ref, static_cast<uint64_t>(n) * s->n_refs);
   b->bytes = c.off + 256;
@@ -542,6 +544,7 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   rebase(d.tb_flag, base);
   rebase(d.tb_list, base);
   rebase(d.tb_count, base);
+  rebase(d.tb_dirs, base);
   rebase(d.out_best, base);
   rebase(d.out_per_ref, base);
   d.n_reads = n;

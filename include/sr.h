@@ -326,8 +326,9 @@ sr_status sr_classify(sr_session* s, sr_batch* b, const sr_classify_params* para
 /* -------------------------------------------------------------- serving
  * Continuous batching: sr_submit copies a request and returns a ticket at once;
  * a scheduler thread admits requests while their device footprint fits the
- * session's hbm_budget, merges every admitted request into the next device
- * round (copies of the next round overlap the current one), and completes each
+ * session's hbm_budget, merges the admitted requests into the next device
+ * round, up to 131072 reads per round (a single larger request runs alone;
+ * copies of the next round overlap the current one), and completes each
  * request as soon as its round finishes.  sr_wait blocks up to timeout_ms
  * (< 0 = forever) and returns SR_ETIMEOUT when the limit runs out.  A request
  * larger than the whole budget is rejected with SR_ENOMEM. */

@@ -3,8 +3,9 @@
 // Requests (a read batch plus its candidate windows) are copied at submit and
 // queued.  One scheduler thread runs a two-deep pipeline: while round k runs
 // on one CUDA stream, it admits every queued request whose device footprint
-// still fits the session's HBM budget (FIFO, bounded by max_inflight), merges
-// them into round k+1 and stages its inputs on the other stream; then it
+// still fits the session's HBM budget (FIFO, bounded by max_inflight and by
+// kMaxRoundReads reads per round), merges them into round k+1 and stages its
+// inputs on the other stream; then it
 // collects round k, splits the merged results back per request (item and
 // CIGAR indices rebased) and completes those requests, freeing their budget.
 // Each read's result depends only on that read and its windows, so a request
@@ -28,6 +29,7 @@
 namespace sr {
 namespace {
 using Clock = std::chrono::steady_clock;
+constexpr uint64_t kMaxRoundReads = 131072;
 
 struct Request {
   uint64_t ticket = 0;
@@ -215,10 +217,16 @@ void scheduler(Server* sv) {
       if (!running.b) sv->cv_work.wait(lk, [&] { return sv->stop || !sv->pending.empty(); });
       if (sv->stop && sv->pending.empty() && !running.b) break;
       const uint64_t budget = session_budget(sv->s);
+      uint64_t round_reads = 0;
       while (!sv->pending.empty()) {
         Request* q = sv->pending.front();
         if (budget && sv->reserved + q->bytes > budget) break;
         if (sv->max_inflight && sv->inflight >= sv->max_inflight) break;
+        // a round stays at most kMaxRoundReads reads (one request may exceed it alone),
+        // so a backlog drains in rounds of bounded latency and device memory
+        const uint64_t qn = q->roff.size() - 1;
+        if (!next.reqs.empty() && round_reads + qn > kMaxRoundReads) break;
+        round_reads += qn;
         sv->pending.pop_front();
         sv->reserved += q->bytes;
         ++sv->inflight;

@@ -2,9 +2,12 @@
 // arXiv 1805.00106: the reported alignment of Sec. 4.2 / SAM output, whose
 // traceback the paper runs on the host, Sec. 6.4).
 //
-// Most winners are traced by k_tb_wave (below), a banded DP that also finds the
-// end row i* (k_tb_wave2 for bands of 33-64 diagonals).  Winners whose band is
-// wider than 64 diagonals, and int32-class winners, use k_traceback: one warp
+// Most winners are traced by a banded DP that also finds the end row i*: one
+// thread per read for bands of at most 8 diagonals (k_tb_thread), a wavefront
+// over the band's diagonals for 9-32 (k_tb_wave4, or k_tb_wave when the scores
+// do not fit its 16-bit values) and two diagonals per lane for 33-64
+// (k_tb_wave2).  Winners whose band is wider than 64 diagonals, and int32-class
+// winners, use k_traceback: one warp
 // per read recomputes the DP of the winning window in exact int32 over rows
 // 1..m and columns 1..j* only (j* = the end column found by the extension
 // kernels; cells right of j* cannot influence the path) with the same systolic
@@ -300,8 +303,7 @@ __device__ __forceinline__ TbRead tb_load(const TbArgs& a, bool has, uint32_t r)
   return t;
 }
 
-// What the walk needs of one read (kept in shared memory for narrow segments,
-// whose reads are walked by the whole warp one after another).
+// What the walk needs of one read.
 struct WalkRead {
   int32_t has, r, m, jstar, ihi, w, dlo, S;
 };
@@ -311,21 +313,12 @@ __device__ __forceinline__ WalkRead walk_of(const TbRead& t) {
                   static_cast<int32_t>(t.jstar), t.ihi, t.w, t.dlo, t.S};
 }
 
-// Codes of a read and its window in shared memory, addressed by 32-bit offsets
-// into the kernel's flat arrays: one byte per base, or 2-bit packed (16 bases
-// per word) for narrow segments, which hold many reads per warp.
-template <bool PACKED>
+// Byte codes of a read and its window in shared memory, addressed by 32-bit
+// offsets into the kernel's flat arrays.
 struct Codes {
-  const uint8_t* qb;   // byte codes (flat array)
+  const uint8_t* qb;
   const uint8_t* rb;
-  const uint32_t* qw;  // packed codes (flat array)
-  const uint32_t* rw;
   __device__ __forceinline__ bool match(uint32_t qo, uint32_t ro, uint32_t i0, uint32_t j0) const {
-    if (PACKED) {
-      const uint32_t a = (qw[qo + (i0 >> 4)] >> ((i0 & 15u) * 2u)) & 3u;
-      const uint32_t b = (rw[ro + (j0 >> 4)] >> ((j0 & 15u) * 2u)) & 3u;
-      return a == b;
-    }
     return qb[qo + i0] == rb[ro + j0];
   }
 };
@@ -463,7 +456,6 @@ struct TbSub {
   bool bd;
 };
 
-template <bool PACKED>
 __device__ __forceinline__ TbSub tb_sub(const TbRead& x, int q, uint32_t qslot, uint32_t rslot) {
   TbSub u;
   const int c = x.dlo + q;
@@ -471,8 +463,8 @@ __device__ __forceinline__ TbSub tb_sub(const TbRead& x, int q, uint32_t qslot, 
   const bool on = x.has && q < x.w && hi >= lo;
   u.rlo = static_cast<uint32_t>(lo);
   u.cnt = on ? static_cast<uint32_t>(hi - lo + 1) : 0u;
-  u.qa = PACKED ? qslot : qslot - 1u;
-  u.ra = PACKED ? rslot : rslot + static_cast<uint32_t>(c - 1);
+  u.qa = qslot - 1u;
+  u.ra = rslot + static_cast<uint32_t>(c - 1);
   u.c = c;
   const int ir = static_cast<int>(x.jstar) - c;
   u.icr = (on && ir >= x.ilo && ir >= lo && ir <= hi) ? ir : -(1 << 20);
@@ -530,30 +522,23 @@ __device__ __forceinline__ void tb_stage_bytes(const TbArgs& a, const TbRead& x,
 template <int SEG>
 __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint32_t* list,
                                                            const uint32_t* range) {
+  static_assert(SEG >= 8, "narrow bands run one thread per read (k_tb_thread)");
   constexpr int NSEG = 32 / SEG;
-  constexpr bool PACKED = SEG <= 4;
-  constexpr int kWinWords = kMaxWinLen / 16 + 1;
-  constexpr int kQB = PACKED ? 1 : kMaxReadLen;  // byte codes per read (unused when packed)
-  constexpr int kRB = PACKED ? 1 : kMaxWinLen;
-  constexpr int kQW = PACKED ? kReadWords : 1;   // packed words per read
-  constexpr int kRW = PACKED ? kWinWords : 1;
-  constexpr int kSlots = kTbWarps * NSEG * 2;     // reads resident per block
+  constexpr int kQB = kMaxReadLen;  // byte codes per read
+  constexpr int kRB = kMaxWinLen;
+  constexpr int kSlots = kTbWarps * NSEG * 2;  // reads resident per block
   // direction bytes of rows 1 - kTbRowPad .. kMaxReadLen + kTbRowPad + 1: the
   // wavefront's first and last steps run lanes above row 1 and below row m
   __shared__ uint8_t dirs_s[kTbWarps][NSEG][(kMaxReadLen + 2 * kTbRowPad + 1) * SEG];
   __shared__ uint8_t qbyte_s[kSlots * kQB];
   __shared__ uint8_t rbyte_s[kSlots * kRB];
-  __shared__ uint32_t qword_s[kSlots * kQW];
-  __shared__ uint32_t rword_s[kSlots * kRW];
-  __shared__ WalkRead walk_s[PACKED ? kSlots : 1];
-  __shared__ uint32_t iend_s[PACKED ? kSlots : 1];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int seg = lane / SEG;
   const int k = lane % SEG;
   const uint32_t seg_mask = SEG == 32 ? FULL : (((1u << SEG) - 1u) << (seg * SEG));
   uint8_t* dirs = dirs_s[warp][seg] + kTbRowPad * SEG;
-  const Codes<PACKED> cd{qbyte_s, rbyte_s, qword_s, rword_s};
+  const Codes cd{qbyte_s, rbyte_s};
   const int32_t goe = a.go + a.ge;
   const uint32_t begin = range[0];
   const uint32_t count = range[1] - begin;
@@ -569,32 +554,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
       rd[X] = tb_load(a, li < count, li < count ? list[begin + li] : 0u);
       if (rd[X].has) {
         const int sl = slot(seg, X);
-        const uint32_t* row = a.rpack + static_cast<uint64_t>(rd[X].rd) * kReadWords;
-        if (PACKED) {
-          // window words re-aligned to its first base; the reference is padded past its end
-          uint32_t* rw = rword_s + sl * kRW;
-          for (uint32_t w = k; w < (rd[X].jstar + 15) / 16; w += SEG) {
-            const uint64_t idx = rd[X].ws + 16ull * w;
-            const uint32_t sh = static_cast<uint32_t>(idx & 15u) * 2u;
-            const uint32_t* src = rd[X].ref + (idx >> 4);
-            rw[w] = sh ? (src[0] >> sh) | (src[1] << (32u - sh)) : src[0];
-          }
-          uint32_t* qw = qword_s + sl * kQW;
-          for (uint32_t w = k; w < static_cast<uint32_t>(kReadWords); w += SEG) {
-            uint32_t v = 0;
-            if (rd[X].strand) {
-              for (uint32_t t = 0; t < 16; ++t) {
-                const uint32_t i = 16 * w + t;
-                if (i < rd[X].m) v |= (3u - base_at(row, rd[X].m - 1u - i)) << (2 * t);
-              }
-            } else {
-              v = row[w];
-            }
-            qw[w] = v;
-          }
-        } else {
-          tb_stage_bytes(a, rd[X], qbyte_s + sl * kQB, rbyte_s + sl * kRB, static_cast<uint32_t>(k), SEG);
-        }
+        tb_stage_bytes(a, rd[X], qbyte_s + sl * kQB, rbyte_s + sl * kRB, static_cast<uint32_t>(k), SEG);
       }
     }
     __syncwarp();
@@ -607,28 +567,14 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
     const int p = k & 1;
     // the read of each half-step on this lane's diagonal
     const int slA = slot(seg, 0), slB = slot(seg, 1);
-    const TbSub uA = tb_sub<PACKED>(rd[0], k, static_cast<uint32_t>(slA * (PACKED ? kQW : kQB)),
-                                    static_cast<uint32_t>(slA * (PACKED ? kRW : kRB)));
-    const TbSub uB = tb_sub<PACKED>(rd[1], k, static_cast<uint32_t>(slB * (PACKED ? kQW : kQB)),
-                                    static_cast<uint32_t>(slB * (PACKED ? kRW : kRB)));
+    const TbSub uA = tb_sub(rd[0], k, static_cast<uint32_t>(slA * kQB), static_cast<uint32_t>(slA * kRB));
+    const TbSub uB = tb_sub(rd[1], k, static_cast<uint32_t>(slB * kQB), static_cast<uint32_t>(slB * kRB));
     const TbSub s0 = p ? uB : uA, s1 = p ? uA : uB;
     auto cell = [&](const TbSub& sb, int i, const TbLd& ld, int32_t E, int32_t F, int32_t& hd, int32_t& En,
                     int32_t& Fn, uint32_t& nib, int32_t& hcr) {
-      bool eq;
-      if (PACKED) {
-        // outside the window the codes load from index 0 instead of a branch
-        const uint32_t ui = static_cast<uint32_t>(i);
-        const bool in = ui - sb.rlo < sb.cnt;
-        const uint32_t i0 = in ? ui - 1u : 0u, j0 = in ? ui - 1u + static_cast<uint32_t>(sb.c) : 0u;
-        eq = in & cd.match(sb.qa, sb.ra, i0, j0);
-      } else {
-        eq = ld.eq();
-      }
-      nib = tb_cell(a, goe, eq, E, F, i == sb.icr, hd, En, Fn, hcr);
+      nib = tb_cell(a, goe, ld.eq(), E, F, i == sb.icr, hd, En, Fn, hcr);
     };
-    auto load = [&](const TbSub& sb, int i) {
-      return PACKED ? TbLd{0u, 0u, false} : tb_ld_bytes(sb, i, qbyte_s, rbyte_s);
-    };
+    auto load = [&](const TbSub& sb, int i) { return tb_ld_bytes(sb, i, qbyte_s, rbyte_s); };
     // what each half-step sent last: gap values for the neighbours, own H
     int32_t Ha = 0, Hb = 0, Ena = -goe, Fna = -goe, Enb = -goe, Fnb = -goe;
     int32_t hcr0 = -1, hcr1 = -1;
@@ -674,34 +620,12 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
       icB = min(icB, __shfl_xor_sync(FULL, icB, off, SEG));
     }
     __syncwarp();
-    // ---- walk back
-    if (PACKED) {
-      // narrow segments: the whole warp walks every read of the warp in turn
-      if (k == 0) {
-        walk_s[slot(seg, 0)] = walk_of(rd[0]);
-        walk_s[slot(seg, 1)] = walk_of(rd[1]);
-        iend_s[slot(seg, 0)] = icA;
-        iend_s[slot(seg, 1)] = icB;
-      }
-      __syncwarp();
-      for (int sg = 0; sg < NSEG; ++sg) {
-        for (int X = 0; X < 2; ++X) {
-          const int sl = slot(sg, X);
-          const WalkRead wr = walk_s[sl];
-          tb_walk<SEG, 32, Codes<PACKED>>(a, wr, iend_s[sl], X ? 4 : 0, dirs_s[warp][sg] + kTbRowPad * SEG, cd,
-                                   static_cast<uint32_t>(sl * kQW), static_cast<uint32_t>(sl * kRW) +
-                                   0u, lane, FULL, 0);
-          __syncwarp();
-        }
-      }
-    } else {
-      // read A, then read B of each segment, walked by the segment's lanes
-      tb_walk<SEG, SEG, Codes<PACKED>>(a, walk_of(rd[0]), icA, 0, dirs, cd, static_cast<uint32_t>(slot(seg, 0) * kQB),
-                                static_cast<uint32_t>(slot(seg, 0) * kRB), k, seg_mask, SEG == 32 ? 0 : seg * SEG);
-      __syncwarp(seg_mask);
-      tb_walk<SEG, SEG, Codes<PACKED>>(a, walk_of(rd[1]), icB, 4, dirs, cd, static_cast<uint32_t>(slot(seg, 1) * kQB),
-                                static_cast<uint32_t>(slot(seg, 1) * kRB), k, seg_mask, SEG == 32 ? 0 : seg * SEG);
-    }
+    // ---- walk back: read A, then read B of each segment, walked by the segment's lanes
+    tb_walk<SEG, SEG, Codes>(a, walk_of(rd[0]), icA, 0, dirs, cd, static_cast<uint32_t>(slot(seg, 0) * kQB),
+                              static_cast<uint32_t>(slot(seg, 0) * kRB), k, seg_mask, SEG == 32 ? 0 : seg * SEG);
+    __syncwarp(seg_mask);
+    tb_walk<SEG, SEG, Codes>(a, walk_of(rd[1]), icB, 4, dirs, cd, static_cast<uint32_t>(slot(seg, 1) * kQB),
+                              static_cast<uint32_t>(slot(seg, 1) * kRB), k, seg_mask, SEG == 32 ? 0 : seg * SEG);
     __syncwarp();
   }
 }
@@ -846,7 +770,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave4(TbArgs a, const uint
     // per read on this lane's diagonal: the lower band edge and the row crossing j*
     TbSub u[4];
 #pragma unroll
-    for (int X = 0; X < 4; ++X) u[X] = tb_sub<false>(rd[X], k, 0u, 0u);
+    for (int X = 0; X < 4; ++X) u[X] = tb_sub(rd[X], k, 0u, 0u);
     // half-step 0 runs pair p, half-step 1 the other pair
     const TbSub& l0 = p ? u[2] : u[0];
     const TbSub& h0 = p ? u[3] : u[1];
@@ -951,7 +875,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint
   const int k = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   uint8_t* dirs = dirs_s[warp] + kTb2RowPad * V;
-  const Codes<false> cd{qbyte_s, rbyte_s, nullptr, nullptr};
+  const Codes cd{qbyte_s, rbyte_s};
   const int32_t goe = a.go + a.ge;
   const uint32_t begin = range[0];
   const uint32_t count = range[1] - begin;
@@ -974,8 +898,8 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint
     const uint32_t qA = warp * 2 * kMaxReadLen, rA = warp * 2 * kMaxWinLen;
     const uint32_t qB = qA + kMaxReadLen, rB = rA + kMaxWinLen;
     // [read of the half-step][diagonal k, k + 32]
-    const TbSub uA0 = tb_sub<false>(rd[0], k, qA, rA), uA1 = tb_sub<false>(rd[0], k + 32, qA, rA);
-    const TbSub uB0 = tb_sub<false>(rd[1], k, qB, rB), uB1 = tb_sub<false>(rd[1], k + 32, qB, rB);
+    const TbSub uA0 = tb_sub(rd[0], k, qA, rA), uA1 = tb_sub(rd[0], k + 32, qA, rA);
+    const TbSub uB0 = tb_sub(rd[1], k, qB, rB), uB1 = tb_sub(rd[1], k + 32, qB, rB);
     const TbSub s00 = p ? uB0 : uA0, s01 = p ? uB1 : uA1, s10 = p ? uA0 : uB0, s11 = p ? uA1 : uB1;
     int32_t Ha0 = 0, Ha1 = 0, Hb0 = 0, Hb1 = 0;
     int32_t Ena0 = -goe, Ena1 = -goe, Fna0 = -goe, Fna1 = -goe;
@@ -1034,9 +958,9 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave2(TbArgs a, const uint
     const uint32_t icA = __reduce_min_sync(FULL, p ? ic1 : ic0);
     const uint32_t icB = __reduce_min_sync(FULL, p ? ic0 : ic1);
     __syncwarp();
-    tb_walk<V, 32, Codes<false>>(a, walk_of(rd[0]), icA, 0, dirs, cd, qA, rA, k, FULL, 0);
+    tb_walk<V, 32, Codes>(a, walk_of(rd[0]), icA, 0, dirs, cd, qA, rA, k, FULL, 0);
     __syncwarp();
-    tb_walk<V, 32, Codes<false>>(a, walk_of(rd[1]), icB, 4, dirs, cd, qB, rB, k, FULL, 0);
+    tb_walk<V, 32, Codes>(a, walk_of(rd[1]), icB, 4, dirs, cd, qB, rB, k, FULL, 0);
     __syncwarp();
   }
 }

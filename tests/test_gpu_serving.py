@@ -108,3 +108,25 @@ def test_wait_timeout_returns_etimeout(env):
     b = s.wait(t2, timeout_ms=120_000)
     assert np.array_equal(a["item_score"], b["item_score"])
     s.serve_stop()
+
+
+def test_backlog_drains_in_bounded_rounds(env):
+    """A burst totalling more than one round's read cap (131072 reads) is split
+    over several rounds, and every request still gets the results it gets alone."""
+    sr, refs, _ = env
+    reqs = [request_of(refs, 20_000, 100 + i) for i in range(8)]  # 160k reads
+    s = sr.Session.open([bytes(r) for r in refs], hbm_budget=16 << 30)
+    alone = [s.align(*[q[k] for k in KEYS], sr.score_params(), sr.align_opts()) for q in reqs]
+    # a long request first, so the others queue up behind its round
+    s.serve_start(sr.score_params(), sr.align_opts(), max_inflight=0)
+    tickets = [s.submit(*[q[k] for k in KEYS]) for q in reqs]
+    served = [s.wait(t, timeout_ms=120_000) for t in tickets]
+    st = s.serve_stats()
+    s.serve_stop()
+    for a, b in zip(alone, served):
+        for k in ["item_score", "item_end", "cigar"]:
+            assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(a["best"], b["best"])
+    assert st["completed"] == len(reqs)
+    assert st["rounds"] >= 2
+    assert st["max_round_requests"] <= 6  # at most 131072 reads: six requests of 20k

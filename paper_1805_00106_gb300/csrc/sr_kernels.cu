@@ -180,27 +180,34 @@ __global__ void k_scatter(const uint16_t* item_key, uint64_t n_items, uint32_t* 
 }
 
 // ---- per-read tracker (Sec. 3.6, 4.2): winner, second best, ties, per reference
-__device__ __forceinline__ unsigned long long wmin64(unsigned long long v) {
+
+// G lanes per read (a group; two reads per warp for G = 16)
+template <int G>
+__device__ __forceinline__ unsigned long long gmin64(uint32_t gm, unsigned long long v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long x = __shfl_xor_sync(FULL, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) {
+    unsigned long long x = __shfl_xor_sync(gm, v, o, G);
     v = x < v ? x : v;
   }
   return v;
 }
 
+template <int G>
 __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32_t* item_score,
                          const uint32_t* item_end, const uint8_t* c_ref, const uint8_t* c_strand,
                          const uint64_t* c_start, int n_refs, DevHit* hits) {
-  const uint64_t r = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  static_assert(G == 16 || G == 32, "group of a half or a whole warp");
+  const uint64_t r = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) / G;
+  const int wl = threadIdx.x & 31;                       // lane in the warp
+  const int l = wl % G;                                  // lane in the group
+  const uint32_t gm = G == 32 ? FULL : (0xffffu << (wl & 16));  // the group's lanes
   if (r >= n_reads) return;
   const uint64_t c0 = cand_off[r], c1 = cand_off[r + 1];
   const int slots = 1 + n_refs;
-  if (c1 - c0 <= 32) {
-    // up to 32 windows: one per lane, loaded once; the same rules as below
-    const bool has = c0 + lane < c1;
-    const uint64_t c = c0 + lane;
+  if (c1 - c0 <= static_cast<uint64_t>(G)) {
+    // up to G windows: one per lane, loaded once; the same rules as below
+    const bool has = c0 + l < c1;
+    const uint64_t c = c0 + l;
     const int32_t s = has ? item_score[c] : 0;
     const uint32_t ref = has ? c_ref[c] : 0u, str = has ? c_strand[c] : 0u;
     const unsigned long long gend = has ? c_start[c] + item_end[c] - 1 : 0ull;
@@ -208,40 +215,41 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
                                      (static_cast<unsigned long long>(str) << 19);
     for (int f = -1; f < n_refs; ++f) {
       const bool in = has && (f < 0 || ref == static_cast<uint32_t>(f));
-      const int32_t best = __reduce_max_sync(FULL, in ? max(s, 0) : 0);
+      const int32_t best = __reduce_max_sync(gm, in ? max(s, 0) : 0);
       DevHit h{};
       h.item = -1;
       if (best > 0) {
         const bool top = in && s == best;
-        const unsigned long long wk = wmin64(top ? locus | static_cast<unsigned long long>(lane) : ~0ull);
-        const int wl = static_cast<int>(wk & 0x7ffffull);
+        const unsigned long long wk = gmin64<G>(gm, top ? locus | static_cast<unsigned long long>(l) : ~0ull);
+        const int win = static_cast<int>(wk & 0x7ffffull);
         const unsigned long long wlocus = wk & ~0x7ffffull;
         h.score = best;
-        h.second = __reduce_max_sync(FULL, (in && s > 0 && locus != wlocus) ? s : 0);
+        h.second = __reduce_max_sync(gm, (in && s > 0 && locus != wlocus) ? s : 0);
         // ties: distinct loci among the best-scoring windows
-        const uint32_t tops = __ballot_sync(FULL, top);
-        const uint32_t same = __match_any_sync(FULL, top ? locus : ~0ull);
-        h.n_ties = static_cast<uint32_t>(__popc(__ballot_sync(FULL, top && (same & tops & ((1u << lane) - 1u)) == 0u)));
-        h.item = static_cast<int32_t>(c0 + static_cast<uint64_t>(wl));
+        const uint32_t tops = __ballot_sync(gm, top);
+        const uint32_t same = __match_any_sync(gm, top ? locus : ~0ull);
+        h.n_ties = static_cast<uint32_t>(
+            __popc(__ballot_sync(gm, top && (same & tops & ((1u << wl) - 1u)) == 0u)));
+        h.item = static_cast<int32_t>(c0 + static_cast<uint64_t>(win));
       }
-      if (lane == 0) hits[r * slots + (f + 1)] = h;
+      if (l == 0) hits[r * slots + (f + 1)] = h;
     }
     return;
   }
   for (int f = -1; f < n_refs; ++f) {
     // best score
     int32_t best = 0;
-    for (uint64_t c = c0 + lane; c < c1; c += 32) {
+    for (uint64_t c = c0 + l; c < c1; c += G) {
       if (f >= 0 && c_ref[c] != f) continue;
       best = max(best, item_score[c]);
     }
-    best = __reduce_max_sync(FULL, best);
+    best = __reduce_max_sync(gm, best);
     DevHit h{};
     h.item = -1;
     if (best > 0) {
       // winner: smallest (ref, global end, strand, candidate index) among the best
       unsigned long long wk = ~0ull;
-      for (uint64_t c = c0 + lane; c < c1; c += 32) {
+      for (uint64_t c = c0 + l; c < c1; c += G) {
         if ((f >= 0 && c_ref[c] != f) || item_score[c] != best) continue;
         const unsigned long long gend = c_start[c] + item_end[c] - 1;
         const unsigned long long k = (static_cast<unsigned long long>(c_ref[c]) << 60) |
@@ -250,13 +258,13 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
                                      static_cast<unsigned long long>(c - c0);
         wk = k < wk ? k : wk;
       }
-      wk = wmin64(wk);
+      wk = gmin64<G>(gm, wk);
       const uint64_t wc = c0 + (wk & 0x7ffffull);
       const uint32_t wref = c_ref[wc], wstr = c_strand[wc];
       const unsigned long long wend = c_start[wc] + item_end[wc] - 1;
       int32_t second = 0;
       uint32_t ties = 0;
-      for (uint64_t c = c0 + lane; c < c1; c += 32) {
+      for (uint64_t c = c0 + l; c < c1; c += G) {
         if (f >= 0 && c_ref[c] != f) continue;
         const int32_t s = item_score[c];
         if (s <= 0) continue;
@@ -274,11 +282,11 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
         }
       }
       h.score = best;
-      h.second = __reduce_max_sync(FULL, second);
-      h.n_ties = __reduce_add_sync(FULL, ties);
+      h.second = __reduce_max_sync(gm, second);
+      h.n_ties = __reduce_add_sync(gm, ties);
       h.item = static_cast<int32_t>(wc);
     }
-    if (lane == 0) hits[r * slots + (f + 1)] = h;
+    if (l == 0) hits[r * slots + (f + 1)] = h;
   }
 }
 
@@ -448,8 +456,9 @@ int launch_bins(const BatchDev& b, const ScoreConst& sc, const TuneBin* bins, in
 
 int launch_select(const BatchDev& b, int n_refs, cudaStream_t st) {
   if (b.n_reads == 0) return 0;
-  const uint64_t t = static_cast<uint64_t>(b.n_reads) * 32;
-  k_select<<<static_cast<unsigned>((t + 255) / 256), 256, 0, st>>>(
+  // half a warp per read: c2's reads hold at most 16 windows nearly always
+  const uint64_t t = static_cast<uint64_t>(b.n_reads) * 16;
+  k_select<16><<<static_cast<unsigned>((t + 255) / 256), 256, 0, st>>>(
       b.cand_off, b.n_reads, b.item_score, b.item_end, b.c_ref, b.c_strand, b.c_start, n_refs,
       b.hits);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

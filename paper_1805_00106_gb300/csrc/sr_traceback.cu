@@ -977,10 +977,174 @@ constexpr int kTbTQW = kReadWords + 1;       // query words per lane (padded)
 constexpr int kTbTRW = kMaxWinLen / 16 + 1;  // window words per lane (33: odd, conflict-free)
 constexpr int kTbTWarps = 4;
 
+// One read on its thread (bands of at most W diagonals): the band DP row by row,
+// then the walk; qw / rw are the read's staged query and window words.
 template <int W>
-__global__ void __launch_bounds__(32 * kTbTWarps) k_tb_thread(TbArgs a, const uint32_t* list, const uint32_t* range,
-                                                            uint32_t* scratch, uint32_t n_warps) {
+__device__ __forceinline__ void tb_thread_read(const TbArgs& a, const TbRead& t, uint32_t* dirs, const uint32_t* qw,
+                                               const uint32_t* rw) {
   static_assert(W >= 1 && W <= 8, "one 32-bit word of nibbles per row");
+  const int32_t goe = a.go + a.ge;
+  constexpr int32_t NEG = -(1 << 28);
+  auto qcode = [&](int i) {  // query code of row i (1-based)
+    const uint32_t p = t.strand ? t.m - static_cast<uint32_t>(i) : static_cast<uint32_t>(i - 1);
+    const uint32_t c = (qw[p >> 4] >> ((p & 15u) * 2u)) & 3u;
+    return t.strand ? 3u - c : c;
+  };
+  auto rcode = [&](int j) {  // window code of column j (1-based, 1 <= j <= j*)
+    const uint32_t p = static_cast<uint32_t>(j - 1);
+    return (rw[p >> 4] >> ((p & 15u) * 2u)) & 3u;
+  };
+  // ---- the band DP, row by row
+  int32_t Hp[W + 1], Fp[W + 1];  // previous row; index W is outside the band
+#pragma unroll
+  for (int k = 0; k <= W; ++k) {
+    Hp[k] = 0;
+    Fp[k] = NEG;
+  }
+  uint32_t istar = kNoRow;
+  const int rows = t.has ? t.ihi : 0;
+  const int w = t.w;
+  const uint32_t wmask = w >= W ? 0xffffffffu : ((1u << w) - 1u);  // cells inside the band
+  for (int i = 1; i <= rows; ++i) {
+    const int c0 = i + t.dlo;  // column of cell 0 (1-based)
+    // cells whose column lies in 1..j*
+    const int klo = 1 - c0, khi = static_cast<int>(t.jstar) - c0;  // inclusive
+    uint32_t vm = wmask;
+    vm &= klo > 0 ? (klo >= 32 ? 0u : ~((1u << klo) - 1u)) : 0xffffffffu;
+    vm &= khi < 31 ? (khi < 0 ? 0u : ((2u << khi) - 1u)) : 0xffffffffu;
+    // the row's window codes, cell k at bits 2k; a match clears both bits of x
+    const int cs = c0 - 1;
+    const int rb = min(max(cs, 0), kMaxWinLen - 1);  // word (rb >> 4) + 1 <= 32 is staged space
+    const uint32_t sh = static_cast<uint32_t>(rb & 15) * 2u;
+    const uint32_t r0 = rw[rb >> 4], r1 = rw[(rb >> 4) + 1];
+    uint32_t rbits = sh ? (r0 >> sh) | (r1 << (32u - sh)) : r0;
+    if (cs < 0) rbits = -cs >= 16 ? 0u : rbits << (2 * -cs);
+    const uint32_t x = rbits ^ (qcode(i) * 0x55555555u);
+    const uint32_t mm = ~(x | (x >> 1));  // bit 2k: cell k matches
+    int32_t H[W], E[W];
+    int32_t Fn[W];
+    uint32_t word = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const int32_t hl = k > 0 ? H[k - 1] : 0, el = k > 0 ? E[k - 1] : NEG;
+      const bool up_in = k + 1 < w;
+      const int32_t hu = up_in ? Hp[k + 1] : 0, fu = up_in ? Fp[k + 1] : NEG;
+      const int32_t eo = hl - goe, ee = el - a.ge, fo = hu - goe, fe = fu - a.ge;
+      const int32_t Eh = max(eo, ee), Fh = max(fo, fe);
+      const bool in = (vm >> k) & 1u;
+      const int32_t hs = Hp[k] + (((mm >> (2 * k)) & 1u) ? a.sa : -a.sb);
+      const int32_t h = max(max(hs, 0), max(Eh, Fh));
+      word |= in ? (static_cast<uint32_t>(h == hs) | (static_cast<uint32_t>(h == Eh) << 1) |
+                    (static_cast<uint32_t>(eo >= ee) << 2) | (static_cast<uint32_t>(fo >= fe) << 3))
+                       << (4 * k)
+                 : 0u;
+      H[k] = in ? h : 0;
+      E[k] = in ? Eh : NEG;
+      Fn[k] = in ? Fh : NEG;
+    }
+    dirs[(i - 1) * 32] = word;
+    // end row: the smallest row at or past ilo whose cell in column j* holds S
+    const int kc = khi;  // cell of column j*
+    if (istar == kNoRow && i >= t.ilo && kc >= 0 && kc < w) {
+      int32_t hc = 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) hc = k == kc ? H[k] : hc;
+      if (hc == t.S) istar = static_cast<uint32_t>(i);
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      Hp[k] = H[k];
+      Fp[k] = Fn[k];
+    }
+  }
+  if (a.mode == 1 && t.has) istar = (istar == static_cast<uint32_t>(t.m)) ? istar : kNoRow;
+  // ---- walk back from (i*, j*)
+  if (t.has) {
+    uint32_t* out = a.cigar_slots + static_cast<uint64_t>(t.r) * kCigarStride;
+    int i = static_cast<int>(istar), j = static_cast<int>(t.jstar);
+    int32_t h = t.S;
+    int state = 0;
+    uint32_t nr = 0, cur_op = 0xffu, cur_len = 0;
+    bool bad = istar == kNoRow;
+    const int limit = t.ihi + static_cast<int>(t.jstar) + 4;
+    for (int it = 0; !bad; ++it) {
+      const int k = j - i - t.dlo;
+      if (it > limit || k < 0 || k >= w || i < 1 || j < 1) {
+        bad = !(state == 0 && h == 0);
+        break;
+      }
+      if (state == 0 && h == 0) break;
+      const uint32_t nib = (dirs[(i - 1) * 32] >> (4 * k)) & 15u;
+      uint32_t op;
+      if (state == 0) {
+        if (nib & 1u) {
+          op = 0u;  // M
+          h -= qcode(i) == rcode(j) ? a.sa : -a.sb;
+          --i;
+          --j;
+        } else {
+          state = (nib & 2u) ? 1 : 2;
+          continue;
+        }
+      } else if (state == 1) {
+        op = 2u;  // D
+        const bool open = nib & 4u;
+        h += open ? goe : a.ge;
+        if (open) state = 0;
+        --j;
+      } else {
+        op = 1u;  // I
+        const bool open = nib & 8u;
+        h += open ? goe : a.ge;
+        if (open) state = 0;
+        --i;
+      }
+      if (op == cur_op) {
+        ++cur_len;
+      } else {
+        if (nr + 4 >= static_cast<uint32_t>(kCigarStride)) {
+          bad = true;
+          break;
+        }
+        if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
+        cur_op = op;
+        cur_len = 1;
+      }
+    }
+    DevHit* hp = a.hits + static_cast<uint64_t>(t.r) * a.slots;
+    if (bad || nr + 3 > static_cast<uint32_t>(kCigarStride)) {
+      atomicOr(a.status, kStInternal);
+      hp->cigar_len = 0;
+    } else {
+      if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
+      for (uint32_t x = 0; x < nr / 2; ++x) {
+        const uint32_t t0 = out[1 + x];
+        out[1 + x] = out[nr - x];
+        out[nr - x] = t0;
+      }
+      const uint32_t start_i = static_cast<uint32_t>(i) + 1u;
+      uint32_t nc;
+      if (start_i > 1) {
+        out[0] = ((start_i - 1u) << 4) | 4u;
+        nc = nr + 1;
+      } else {
+        for (uint32_t x = 0; x < nr; ++x) out[x] = out[x + 1];
+        nc = nr;
+      }
+      if (istar < t.m) out[nc++] = ((t.m - istar) << 4) | 4u;
+      hp->read_start = static_cast<int32_t>(start_i);
+      hp->read_end = static_cast<int32_t>(istar);
+      hp->start_j = static_cast<uint32_t>(j) + 1u;
+      hp->cigar_len = nc;
+    }
+  }
+}
+
+// Reads of bands up to 8 diagonals, in band-width order: each warp runs the
+// narrowest cell count that holds its 32 reads.
+__global__ void __launch_bounds__(32 * kTbTWarps) k_tb_thread(TbArgs a, const uint32_t* list, const uint32_t* range_lo,
+                                                            const uint32_t* range_hi, uint32_t* scratch,
+                                                            uint32_t n_warps) {
   __shared__ uint32_t q_s[kTbTWarps][32 * kTbTQW];
   __shared__ uint32_t r_s[kTbTWarps][32 * kTbTRW];
   const int lane = threadIdx.x & 31;
@@ -990,13 +1154,11 @@ __global__ void __launch_bounds__(32 * kTbTWarps) k_tb_thread(TbArgs a, const ui
   uint32_t* dirs = scratch + static_cast<uint64_t>(gw) * kMaxReadLen * 32 + lane;  // [row][lane]
   uint32_t* qw = q_s[warp] + lane * kTbTQW;
   uint32_t* rw = r_s[warp] + lane * kTbTRW;
-  const int32_t goe = a.go + a.ge;
-  constexpr int32_t NEG = -(1 << 28);
-  const uint32_t begin = range[0];
-  const uint32_t count = range[1] - begin;
+  const uint32_t first = range_lo[0];
+  const uint32_t count = range_hi[1] - first;
   for (uint32_t base = gw * 32u; base < count; base += n_warps * 32u) {
     const uint32_t li = base + lane;
-    const TbRead t = tb_load(a, li < count, li < count ? list[begin + li] : 0u);
+    const TbRead t = tb_load(a, li < count, li < count ? list[first + li] : 0u);
     // stage this read's words: the query row as packed, the window from column 1
     if (t.has) {
       const uint32_t* row = a.rpack + static_cast<uint64_t>(t.rd) * kReadWords;
@@ -1009,159 +1171,15 @@ __global__ void __launch_bounds__(32 * kTbTWarps) k_tb_thread(TbArgs a, const ui
         rw[w] = sh ? (src[0] >> sh) | (src[1] << (32u - sh)) : src[0];
       }
     }
-    auto qcode = [&](int i) {  // query code of row i (1-based)
-      const uint32_t p = t.strand ? t.m - static_cast<uint32_t>(i) : static_cast<uint32_t>(i - 1);
-      const uint32_t c = (qw[p >> 4] >> ((p & 15u) * 2u)) & 3u;
-      return t.strand ? 3u - c : c;
-    };
-    auto rcode = [&](int j) {  // window code of column j (1-based, 1 <= j <= j*)
-      const uint32_t p = static_cast<uint32_t>(j - 1);
-      return (rw[p >> 4] >> ((p & 15u) * 2u)) & 3u;
-    };
-    // ---- the band DP, row by row
-    int32_t Hp[W + 1], Fp[W + 1];  // previous row; index W is outside the band
-#pragma unroll
-    for (int k = 0; k <= W; ++k) {
-      Hp[k] = 0;
-      Fp[k] = NEG;
-    }
-    uint32_t istar = kNoRow;
-    const int rows = t.has ? t.ihi : 0;
-    const int w = t.w;
-    const uint32_t wmask = w >= W ? 0xffffffffu : ((1u << w) - 1u);  // cells inside the band
-    for (int i = 1; i <= rows; ++i) {
-      const int c0 = i + t.dlo;  // column of cell 0 (1-based)
-      // cells whose column lies in 1..j*
-      const int klo = 1 - c0, khi = static_cast<int>(t.jstar) - c0;  // inclusive
-      uint32_t vm = wmask;
-      vm &= klo > 0 ? (klo >= 32 ? 0u : ~((1u << klo) - 1u)) : 0xffffffffu;
-      vm &= khi < 31 ? (khi < 0 ? 0u : ((2u << khi) - 1u)) : 0xffffffffu;
-      // the row's window codes, cell k at bits 2k; a match clears both bits of x
-      const int cs = c0 - 1;
-      const int rb = min(max(cs, 0), kMaxWinLen - 1);  // word (rb >> 4) + 1 <= 32 is staged space
-      const uint32_t sh = static_cast<uint32_t>(rb & 15) * 2u;
-      const uint32_t r0 = rw[rb >> 4], r1 = rw[(rb >> 4) + 1];
-      uint32_t rbits = sh ? (r0 >> sh) | (r1 << (32u - sh)) : r0;
-      if (cs < 0) rbits = -cs >= 16 ? 0u : rbits << (2 * -cs);
-      const uint32_t x = rbits ^ (qcode(i) * 0x55555555u);
-      const uint32_t mm = ~(x | (x >> 1));  // bit 2k: cell k matches
-      int32_t H[W], E[W];
-      int32_t Fn[W];
-      uint32_t word = 0;
-#pragma unroll
-      for (int k = 0; k < W; ++k) {
-        const int32_t hl = k > 0 ? H[k - 1] : 0, el = k > 0 ? E[k - 1] : NEG;
-        const bool up_in = k + 1 < w;
-        const int32_t hu = up_in ? Hp[k + 1] : 0, fu = up_in ? Fp[k + 1] : NEG;
-        const int32_t eo = hl - goe, ee = el - a.ge, fo = hu - goe, fe = fu - a.ge;
-        const int32_t Eh = max(eo, ee), Fh = max(fo, fe);
-        const bool in = (vm >> k) & 1u;
-        const int32_t hs = Hp[k] + (((mm >> (2 * k)) & 1u) ? a.sa : -a.sb);
-        const int32_t h = max(max(hs, 0), max(Eh, Fh));
-        word |= in ? (static_cast<uint32_t>(h == hs) | (static_cast<uint32_t>(h == Eh) << 1) |
-                      (static_cast<uint32_t>(eo >= ee) << 2) | (static_cast<uint32_t>(fo >= fe) << 3))
-                         << (4 * k)
-                   : 0u;
-        H[k] = in ? h : 0;
-        E[k] = in ? Eh : NEG;
-        Fn[k] = in ? Fh : NEG;
-      }
-      dirs[(i - 1) * 32] = word;
-      // end row: the smallest row at or past ilo whose cell in column j* holds S
-      const int kc = khi;  // cell of column j*
-      if (istar == kNoRow && i >= t.ilo && kc >= 0 && kc < w) {
-        int32_t hc = 0;
-#pragma unroll
-        for (int k = 0; k < W; ++k) hc = k == kc ? H[k] : hc;
-        if (hc == t.S) istar = static_cast<uint32_t>(i);
-      }
-#pragma unroll
-      for (int k = 0; k < W; ++k) {
-        Hp[k] = H[k];
-        Fp[k] = Fn[k];
-      }
-    }
-    if (a.mode == 1 && t.has) istar = (istar == static_cast<uint32_t>(t.m)) ? istar : kNoRow;
-    // ---- walk back from (i*, j*)
-    if (t.has) {
-      uint32_t* out = a.cigar_slots + static_cast<uint64_t>(t.r) * kCigarStride;
-      int i = static_cast<int>(istar), j = static_cast<int>(t.jstar);
-      int32_t h = t.S;
-      int state = 0;
-      uint32_t nr = 0, cur_op = 0xffu, cur_len = 0;
-      bool bad = istar == kNoRow;
-      const int limit = t.ihi + static_cast<int>(t.jstar) + 4;
-      for (int it = 0; !bad; ++it) {
-        const int k = j - i - t.dlo;
-        if (it > limit || k < 0 || k >= w || i < 1 || j < 1) {
-          bad = !(state == 0 && h == 0);
-          break;
-        }
-        if (state == 0 && h == 0) break;
-        const uint32_t nib = (dirs[(i - 1) * 32] >> (4 * k)) & 15u;
-        uint32_t op;
-        if (state == 0) {
-          if (nib & 1u) {
-            op = 0u;  // M
-            h -= qcode(i) == rcode(j) ? a.sa : -a.sb;
-            --i;
-            --j;
-          } else {
-            state = (nib & 2u) ? 1 : 2;
-            continue;
-          }
-        } else if (state == 1) {
-          op = 2u;  // D
-          const bool open = nib & 4u;
-          h += open ? goe : a.ge;
-          if (open) state = 0;
-          --j;
-        } else {
-          op = 1u;  // I
-          const bool open = nib & 8u;
-          h += open ? goe : a.ge;
-          if (open) state = 0;
-          --i;
-        }
-        if (op == cur_op) {
-          ++cur_len;
-        } else {
-          if (nr + 4 >= static_cast<uint32_t>(kCigarStride)) {
-            bad = true;
-            break;
-          }
-          if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
-          cur_op = op;
-          cur_len = 1;
-        }
-      }
-      DevHit* hp = a.hits + static_cast<uint64_t>(t.r) * a.slots;
-      if (bad || nr + 3 > static_cast<uint32_t>(kCigarStride)) {
-        atomicOr(a.status, kStInternal);
-        hp->cigar_len = 0;
-      } else {
-        if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
-        for (uint32_t x = 0; x < nr / 2; ++x) {
-          const uint32_t t0 = out[1 + x];
-          out[1 + x] = out[nr - x];
-          out[nr - x] = t0;
-        }
-        const uint32_t start_i = static_cast<uint32_t>(i) + 1u;
-        uint32_t nc;
-        if (start_i > 1) {
-          out[0] = ((start_i - 1u) << 4) | 4u;
-          nc = nr + 1;
-        } else {
-          for (uint32_t x = 0; x < nr; ++x) out[x] = out[x + 1];
-          nc = nr;
-        }
-        if (istar < t.m) out[nc++] = ((t.m - istar) << 4) | 4u;
-        hp->read_start = static_cast<int32_t>(start_i);
-        hp->read_end = static_cast<int32_t>(istar);
-        hp->start_j = static_cast<uint32_t>(j) + 1u;
-        hp->cigar_len = nc;
-      }
-    }
+    const uint32_t wmax = __reduce_max_sync(FULL, t.has ? static_cast<uint32_t>(t.w) : 0u);
+    if (wmax <= 1)
+      tb_thread_read<1>(a, t, dirs, qw, rw);
+    else if (wmax <= 2)
+      tb_thread_read<2>(a, t, dirs, qw, rw);
+    else if (wmax <= 4)
+      tb_thread_read<4>(a, t, dirs, qw, rw);
+    else
+      tb_thread_read<8>(a, t, dirs, qw, rw);
   }
 }
 
@@ -1318,17 +1336,13 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
     ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
   };
-  // bands of at most 8 diagonals: one thread per read, the four buckets one
-  // after another on one stream (they share the direction scratch)
+  // bands of at most 8 diagonals (buckets 0-3, adjacent in the sorted list): one
+  // thread per read, one launch
   auto threads = [&]() -> bool {
     const uint32_t nw = tb_thread_warps(b.n_reads);
-    const unsigned grid = (nw + kTbTWarps - 1) / kTbTWarps, block = 32 * kTbTWarps;
-    const cudaStream_t s = lane_of();
-    k_tb_thread<8><<<grid, block, 0, s>>>(a, list, ranges + 2 * 3, b.tb_dirs, nw);
-    k_tb_thread<4><<<grid, block, 0, s>>>(a, list, ranges + 2 * 2, b.tb_dirs, nw);
-    k_tb_thread<2><<<grid, block, 0, s>>>(a, list, ranges + 2 * 1, b.tb_dirs, nw);
-    k_tb_thread<1><<<grid, block, 0, s>>>(a, list, ranges + 2 * 0, b.tb_dirs, nw);
-    launched += 4;
+    k_tb_thread<<<(nw + kTbTWarps - 1) / kTbTWarps, 32 * kTbTWarps, 0, lane_of()>>>(
+        a, list, ranges + 2 * 0, ranges + 2 * 3, b.tb_dirs, nw);
+    ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
   };
   // widest bands (longest kernels) first

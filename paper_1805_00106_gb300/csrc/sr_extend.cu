@@ -102,12 +102,13 @@ int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
   }
   if (fan && fanout_begin(*fan, st) < 0) return -1;
   int next = 0;
+  const int width = fan_width(b.n_reads);
   // longest reads first: each side stream starts on a large bin
   for (int c = n_bins - 1; c >= 0; --c) {
     if (class_items && class_items[c] == 0) continue;
     a.cls = c;
     uint32_t g = lanes ? lanes : bins[c].lanes, r = rows ? rows : bins[c].rows;
-    const cudaStream_t s = fan ? fan->side[next++ % kSide] : st;
+    const cudaStream_t s = fan ? fan->side[next++ % width] : st;
     int k = mode == 1 ? dispatch_mode1(true, g, r, a, s, 0) : dispatch_mode0(true, g, r, a, s, 0);
     if (k < 0) return -1;
     launched += k;
@@ -117,7 +118,7 @@ int launch_extend(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc,
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const cudaStream_t s = fan ? fan->side[next++ % kSide] : st;
+    const cudaStream_t s = fan ? fan->side[next++ % width] : st;
     if (mode == 1) k_extend32<1><<<nsm * 4, 128, 0, s>>>(a);
     else k_extend32<0><<<nsm * 4, 128, 0, s>>>(a);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;

@@ -165,7 +165,10 @@ __host__ __device__ inline uint32_t tb_min_row(int32_t sa, int32_t S) {
 // run on side streams forked from the launching stream and joined back, so a
 // bin's tail overlaps the next bins and small batches do not pay the bins'
 // latencies one after another.  Events: one fork and kSide joins per phase.
-constexpr int kSide = 4;
+// Small batches spread over all kSide streams (latency); large ones over four,
+// where more concurrent kernels only contend.
+constexpr int kSide = 8;
+inline int fan_width(uint32_t n_reads) { return n_reads >= (1u << 18) ? 4 : kSide; }
 struct Fanout {
   cudaStream_t side[kSide];
   cudaEvent_t fork;

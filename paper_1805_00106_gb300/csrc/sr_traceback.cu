@@ -1326,7 +1326,8 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   int launched = 3;
   if (fan && fanout_begin(*fan, st) < 0) return -1;
   int next = 0;
-  auto lane_of = [&]() { return fan ? fan->side[next++ % kSide] : st; };
+  const int width = fan_width(b.n_reads);
+  auto lane_of = [&]() { return fan ? fan->side[next++ % width] : st; };
   auto wave = [&](auto kern, int bucket, int per_warp) -> bool {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kTbWarps, 0) != cudaSuccess) return false;

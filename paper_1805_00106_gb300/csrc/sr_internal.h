@@ -112,7 +112,7 @@ constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + 8;
 constexpr int kTbMaxBand = 64;
 // warps of the one-thread-per-read narrow-band traceback (each owns a scratch
 // of 256 rows x 32 lanes of direction words)
-constexpr uint32_t kTbThreadMaxWarps = 2048;
+constexpr uint32_t kTbThreadMaxWarps = 4096;
 inline uint32_t tb_thread_warps(uint32_t n_reads) {
   const uint32_t w = (n_reads + 31u) / 32u;
   return w < kTbThreadMaxWarps ? (w ? w : 1u) : kTbThreadMaxWarps;

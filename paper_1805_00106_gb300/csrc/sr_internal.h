@@ -206,7 +206,12 @@ int launch_winner_rows(const BatchDev& b, const DevRefs& refs, const ScoreConst&
 int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc, int mode,
                      int n_refs, cudaStream_t st, const Fanout* fan = nullptr);
 int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);
-int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, cudaStream_t st);
+// records in the public layout; a batch holding one part of a larger result
+// adds item_base to its window indexes and cigar_base to its CIGAR offsets
+int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, int32_t item_base, uint32_t cigar_base,
+                    cudaStream_t st);
+// off[0..n) -= base
+int launch_rebase_offsets(uint64_t* off, uint64_t n, uint64_t base, cudaStream_t st);
 // exclusive scan of n counts into out[0..n] (out[n] = total) with a scratch of
 // n / 1024 + 1 words (sr_report.cu)
 int launch_scan_u32(const uint32_t* in, uint32_t n, uint32_t* out, uint32_t* sums, cudaStream_t st);

@@ -481,7 +481,8 @@ int launch_winners(const BatchDev& b, const ScoreConst& sc, int mode, int n_refs
 // best window per reference.
 __global__ void k_assemble(uint32_t n_reads, int slots, const DevHit* hits, const uint8_t* c_ref,
                            const uint8_t* c_strand, const uint64_t* c_start, const uint32_t* item_end,
-                           const uint32_t* cigar_off, bool want_cigar, sr_hit* best, sr_hit* per_ref) {
+                           const uint32_t* cigar_off, bool want_cigar, int32_t item_base, uint32_t cigar_base,
+                           sr_hit* best, sr_hit* per_ref) {
   const uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   if (x >= static_cast<uint64_t>(n_reads) * slots) return;
   const uint64_t i = x / slots;
@@ -491,7 +492,7 @@ __global__ void k_assemble(uint32_t n_reads, int slots, const DevHit* hits, cons
   o.score = h.score;
   o.second = h.second;
   o.n_ties = h.n_ties;
-  o.item = h.item;
+  o.item = h.item >= 0 ? h.item + item_base : h.item;
   o.ref_id = 0;
   o.strand = 0;
   o.reserved = 0;
@@ -510,7 +511,7 @@ __global__ void k_assemble(uint32_t n_reads, int slots, const DevHit* hits, cons
       o.read_start = h.read_start;
       o.read_end = h.read_end;
       o.ref_start = c_start[it] + h.start_j - 1;
-      o.cigar_off = cigar_off[i];
+      o.cigar_off = cigar_base + cigar_off[i];
       o.cigar_len = h.cigar_len;
     }
   }
@@ -518,12 +519,26 @@ __global__ void k_assemble(uint32_t n_reads, int slots, const DevHit* hits, cons
   else per_ref[i * (slots - 1) + (sl - 1)] = o;
 }
 
-int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, cudaStream_t st) {
+int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, int32_t item_base, uint32_t cigar_base,
+                    cudaStream_t st) {
   if (b.n_reads == 0) return 0;
   const uint64_t total = static_cast<uint64_t>(b.n_reads) * (1 + n_refs);
   k_assemble<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(
       b.n_reads, 1 + n_refs, b.hits, b.c_ref, b.c_strand, b.c_start, b.item_end, b.cigar_off, want_cigar,
-      b.out_best, b.out_per_ref);
+      item_base, cigar_base, b.out_best, b.out_per_ref);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// A batch staged from a read range [r0, r1) of the caller's arrays receives
+// the range's offsets as they are; they are made batch-relative here.
+__global__ void k_rebase_offsets(uint64_t* off, uint64_t n, uint64_t base) {
+  const uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (x < n) off[x] -= base;
+}
+
+int launch_rebase_offsets(uint64_t* off, uint64_t n, uint64_t base, cudaStream_t st) {
+  if (n == 0 || base == 0) return 0;
+  k_rebase_offsets<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(off, n, base);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

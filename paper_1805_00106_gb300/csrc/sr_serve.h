@@ -17,4 +17,6 @@ Server*& session_server(sr_session* s);
 uint32_t session_n_refs(sr_session* s);
 sr_status batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
                                void* stream, bool check_budget, sr_batch** out);
+sr_status batch_stage_range(sr_session* s, const sr_reads* reads, const sr_cand_list* cands, uint32_t r0,
+                            uint32_t r1, void* stream, bool check_budget, sr_batch** out);
 }  // namespace sr

@@ -124,6 +124,7 @@ constexpr size_t kResPool = 16;
 struct sr_session {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t part_stream[2] = {};  // the two parts of a large sr_align_batch call
   uint32_t n_refs = 0;
   std::vector<uint32_t*> d_words;
   std::vector<uint64_t> lens;
@@ -188,7 +189,12 @@ static sr_status open_common(const uint8_t* const* codes, const char* const* asc
   auto* s = new sr_session;
   cudaGetDevice(&s->device);
   e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  for (auto& x : s->part_stream)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
+    if (s->stream) cudaStreamDestroy(s->stream);
+    for (auto x : s->part_stream)
+      if (x) cudaStreamDestroy(x);
     delete s;
     return cuda_error("session stream", e);
   }
@@ -292,6 +298,8 @@ static void session_release(sr_session* s) {
   for (auto& r : s->res_pool) res_destroy(r);
   for (auto& a : s->spares) cudaFree(a.first);
   if (s->stream) cudaStreamDestroy(s->stream);
+  for (auto x : s->part_stream)
+    if (x) cudaStreamDestroy(x);
   delete s;
 }
 
@@ -389,22 +397,39 @@ extern "C" sr_status sr_batch_stage(sr_session* s, const sr_reads* reads, const 
 
 sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
                                    void* cuda_stream, bool check_budget, sr_batch** out) {
+  return batch_stage_range(s, reads, cands, 0, reads ? reads->n_reads : 0, cuda_stream, check_budget, out);
+}
+
+// Stages reads [r0, r1) of the caller's arrays (and their windows) as one
+// batch: the whole list's header is checked, the range's arrays are copied and
+// its offsets made batch-relative on the device.  Reads and windows named in
+// error messages keep their indexes in the caller's arrays.
+sr_status sr::batch_stage_range(sr_session* s, const sr_reads* reads, const sr_cand_list* cands, uint32_t r0,
+                                uint32_t r1, void* cuda_stream, bool check_budget, sr_batch** out) {
   Trace trace_("sr_batch_stage");
   if (!s || !reads || !cands || !out) return set_error(SR_EINVAL, "sr_batch_stage: null argument");
   *out = nullptr;
-  const uint32_t n = reads->n_reads;
-  if (cands->n_reads != n) return set_error(SR_EINVAL, "sr_batch_stage: reads and candidates differ in n_reads");
+  const uint32_t n_all = reads->n_reads;
+  if (cands->n_reads != n_all) return set_error(SR_EINVAL, "sr_batch_stage: reads and candidates differ in n_reads");
+  if (r0 > r1 || r1 > n_all) return set_error(SR_EINVAL, "sr_batch_stage: bad read range");
+  const uint32_t n = r1 - r0;
   if (n > (8u << 20)) return set_error(SR_EINVAL, "sr_batch_stage: more than 8M reads in one batch");
-  if (n && (!reads->offsets || !reads->bases || !cands->offsets))
+  if (n_all && (!reads->offsets || !reads->bases || !cands->offsets))
     return set_error(SR_EINVAL, "sr_batch_stage: null arrays");
-  const uint64_t nb = n ? reads->offsets[n] : 0;
-  const uint64_t nc = n ? cands->offsets[n] : 0;
-  if (n && (reads->offsets[0] != 0 || cands->offsets[0] != 0))
+  const uint64_t nc_all = n_all ? cands->offsets[n_all] : 0;
+  if (n_all && (reads->offsets[0] != 0 || cands->offsets[0] != 0))
     return set_error(SR_EINVAL, "sr_batch_stage: offsets must start at 0");
-  if (nc != cands->n_cands) return set_error(SR_EINVAL, "sr_batch_stage: n_cands != offsets[n_reads]");
-  if (nc >= (1ull << 32)) return set_error(SR_EINVAL, "sr_batch_stage: too many windows");
-  if (nc && (!cands->ref_id || !cands->strand || !cands->win_start || !cands->win_len))
+  if (nc_all != cands->n_cands) return set_error(SR_EINVAL, "sr_batch_stage: n_cands != offsets[n_reads]");
+  if (nc_all >= (1ull << 32)) return set_error(SR_EINVAL, "sr_batch_stage: too many windows");
+  if (nc_all && (!cands->ref_id || !cands->strand || !cands->win_start || !cands->win_len))
     return set_error(SR_EINVAL, "sr_batch_stage: null candidate arrays");
+  // the range's first base and window, and its sizes
+  const uint64_t rb = n ? reads->offsets[r0] : 0, cb = n ? cands->offsets[r0] : 0;
+  const uint64_t re = n ? reads->offsets[r1] : 0, ce = n ? cands->offsets[r1] : 0;
+  if (re < rb || ce < cb || ce > nc_all)
+    return set_error(SR_EINVAL, "sr_batch_stage: decreasing or out-of-range offsets in reads %u..%u", r0, r1);
+  const uint64_t nb = re - rb;
+  const uint64_t nc = ce - cb;
   if (nb > static_cast<uint64_t>(n) * SR_MAX_READ_LEN)
     return set_error(SR_EINVAL, "sr_batch_stage: %llu bases in %u reads: some read is longer than %d",
                      static_cast<unsigned long long>(nb), n, SR_MAX_READ_LEN);
@@ -566,21 +591,27 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
     b->res_ok = true;
   }
   cudaStream_t st = b->stream;
-  if (nb) e = cudaMemcpyAsync(const_cast<char*>(d.bases), reads->bases, nb, cudaMemcpyHostToDevice, st);
+  if (nb) e = cudaMemcpyAsync(const_cast<char*>(d.bases), reads->bases + rb, nb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(const_cast<uint64_t*>(d.read_off), reads->offsets, (n + 1ull) * 8, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(const_cast<uint64_t*>(d.read_off), reads->offsets + r0, (n + 1ull) * 8,
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(const_cast<uint64_t*>(d.cand_off), cands->offsets, (n + 1ull) * 8, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(const_cast<uint64_t*>(d.cand_off), cands->offsets + r0, (n + 1ull) * 8,
+                        cudaMemcpyHostToDevice, st);
   if (nc) {
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(const_cast<uint8_t*>(d.c_ref), cands->ref_id, nc, cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(const_cast<uint8_t*>(d.c_ref), cands->ref_id + cb, nc, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(const_cast<uint8_t*>(d.c_strand), cands->strand, nc, cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(const_cast<uint8_t*>(d.c_strand), cands->strand + cb, nc, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(const_cast<uint64_t*>(d.c_start), cands->win_start, nc * 8, cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(const_cast<uint64_t*>(d.c_start), cands->win_start + cb, nc * 8, cudaMemcpyHostToDevice,
+                          st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(const_cast<uint32_t*>(d.c_len), cands->win_len, nc * 4, cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(const_cast<uint32_t*>(d.c_len), cands->win_len + cb, nc * 4, cudaMemcpyHostToDevice, st);
   }
+  if (e == cudaSuccess && n && (launch_rebase_offsets(const_cast<uint64_t*>(d.read_off), n + 1ull, rb, st) < 0 ||
+                                launch_rebase_offsets(const_cast<uint64_t*>(d.cand_off), n + 1ull, cb, st) < 0))
+    e = cudaGetLastError();
   if (e != cudaSuccess) {
     cudaStreamSynchronize(st);
     sr_batch_free(b);
@@ -606,12 +637,12 @@ sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const s
   const uint32_t nref = s->n_refs;
   auto check = [&](uint32_t t) {
     Part& P = parts[t];
-    const uint32_t r0 = static_cast<uint32_t>(static_cast<uint64_t>(n) * t / nthr);
-    const uint32_t r1 = static_cast<uint32_t>(static_cast<uint64_t>(n) * (t + 1) / nthr);
-    for (uint32_t r = r0; r < r1; ++r) {
+    const uint32_t p0 = static_cast<uint32_t>(static_cast<uint64_t>(n) * t / nthr);
+    const uint32_t p1 = static_cast<uint32_t>(static_cast<uint64_t>(n) * (t + 1) / nthr);
+    for (uint32_t r = r0 + p0; r < r0 + p1; ++r) {
       const uint64_t a0 = reads->offsets[r], a1 = reads->offsets[r + 1];
       const uint64_t c0 = cands->offsets[r], c1 = cands->offsets[r + 1];
-      if (a1 < a0 || c1 < c0 || c1 > nc) {
+      if (a1 < a0 || c1 < c0 || c1 > ce) {
         P.bad_read = r;
         P.why = 1;
         return;
@@ -966,6 +997,8 @@ struct ResultsBox {
   sr_session* pool_of = nullptr;
   void* block = nullptr;
   uint64_t block_bytes = 0;
+  void* cig_block = nullptr;  // the CIGAR words, when they sit in a block of their own
+  uint64_t cig_block_bytes = 0;
 };
 
 sr_results* results_alloc() {
@@ -1017,6 +1050,7 @@ extern "C" void sr_results_free(sr_results* r) {
   if (box->block) {
     sr_session* s = box->pool_of;
     pool_give(s, box->block, box->block_bytes);
+    if (box->cig_block) pool_give(s, box->cig_block, box->cig_block_bytes);
     free(box);
     session_release(s);
     return;
@@ -1050,7 +1084,7 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
   // comes back with one copy each on the batch's stream and a single wait
   const bool cig = b->last_opts.want_cigar != 0;
   const bool cls = b->last_opts.classify != 0;
-  if (launch_assemble(b->d, static_cast<int>(nr), cig, stream) < 0) {
+  if (launch_assemble(b->d, static_cast<int>(nr), cig, 0, 0, stream) < 0) {
     sr_results_free(r);
     return cuda_error("sr_batch_fetch assemble", cudaGetLastError());
   }
@@ -1433,11 +1467,150 @@ extern "C" sr_status sr_batch_report(sr_session* s, sr_batch* b, uint32_t kind, 
   return SR_OK;
 }
 
+namespace sr {
+// sr_align_batch calls of at least this many reads run as two batches
+constexpr uint32_t kPartMinReads = 1u << 19;
+
+// One large sr_align_batch call as two batches of consecutive reads, each on a
+// stream of its own.  The second part's copies and host checks run while the
+// first part computes, and the first part's results come back while the second
+// computes.  A read's windows all stay in its part, so every result is the one
+// a single batch gives; the second part's window indexes and CIGAR offsets are
+// shifted on the device as its records are assembled.  Returns false, with
+// nothing left allocated, when any step fails: the caller then runs the call
+// as one batch, which reports the same errors as a call that was never split.
+static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                           const sr_score_params* sp, const sr_align_opts& o, sr_results** out) {
+  Trace trace_("sr_align_batch parts");
+  const uint32_t n = reads->n_reads;
+  const uint64_t nc = cands->n_cands;
+  if (!reads->offsets || !cands->offsets || cands->n_reads != n || cands->offsets[n] != nc) return false;
+  // the boundary: the first read whose windows start at or past half of all
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (cands->offsets[mid] < nc / 2) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo == 0 || lo >= n) return false;
+  const uint32_t rr[3] = {0, lo, n};
+  sr_align_opts oo = o;
+  oo.cuda_stream = nullptr;
+  sr_batch* b[2] = {};
+  auto drop_parts = [&]() {
+    for (auto*& x : b)
+      if (x) {
+        sr_batch_free(x);
+        x = nullptr;
+      }
+  };
+  for (int k = 0; k < 2; ++k)
+    if (batch_stage_range(s, reads, cands, rr[k], rr[k + 1], s->part_stream[k], true, &b[k]) != SR_OK ||
+        batch_run_async(s, b[k], sp, &oo) != SR_OK) {
+      drop_parts();
+      return false;
+    }
+  const uint32_t nr = s->n_refs;
+  const bool cig = o.want_cigar != 0, cls = o.classify != 0;
+  // one pinned block for the arrays whose sizes are known now; the CIGAR
+  // words, counted only when both parts are done, get a second one
+  uint64_t off = 0;
+  auto part = [&](uint64_t bytes) {
+    const uint64_t at = off;
+    off = (off + (bytes ? bytes : 1) + 255) & ~255ull;
+    return at;
+  };
+  const uint64_t o_best = part(static_cast<uint64_t>(n) * sizeof(sr_hit));
+  const uint64_t o_per = part(static_cast<uint64_t>(n) * nr * sizeof(sr_hit));
+  const uint64_t o_sc = part(nc * 4);
+  const uint64_t o_end = part(nc * 4);
+  const uint64_t o_cls = cls ? part(n) : 0;
+  uint64_t got = 0;
+  char* blk = static_cast<char*>(pool_take(s, off, &got));
+  sr_results* r = blk ? results_alloc() : nullptr;
+  if (!r) {
+    if (blk) pool_give(s, blk, got);
+    drop_parts();
+    return false;
+  }
+  auto* box = reinterpret_cast<ResultsBox*>(r);
+  box->pool_of = s;
+  box->block = blk;
+  box->block_bytes = got;
+  s->live.fetch_add(1);
+  r->n_reads = n;
+  r->n_refs = nr;
+  r->n_items = nc;
+  r->cells = b[0]->cells + b[1]->cells;
+  r->best = reinterpret_cast<sr_hit*>(blk + o_best);
+  r->best_per_ref = reinterpret_cast<sr_hit*>(blk + o_per);
+  r->item_score = reinterpret_cast<int32_t*>(blk + o_sc);
+  r->item_end = reinterpret_cast<uint32_t*>(blk + o_end);
+  if (cls) r->read_class = reinterpret_cast<uint8_t*>(blk + o_cls);
+  auto fail = [&]() {
+    for (auto* x : b)
+      if (x) cudaStreamSynchronize(x->stream);
+    cudaGetLastError();
+    sr_results_free(r);
+    drop_parts();
+    return false;
+  };
+  cudaError_t e = cudaSuccess;
+  auto copy = [&](void* dst, const void* src, uint64_t bytes, cudaStream_t st) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+  };
+  uint32_t total[2] = {};
+  for (int k = 0; k < 2; ++k) {
+    sr_batch* x = b[k];
+    cudaStream_t st = x->stream;
+    if (batch_sync(x, st) != SR_OK) return fail();
+    const uint32_t r0 = rr[k];
+    const uint64_t i0 = k ? b[0]->n_items : 0;
+    if (launch_assemble(x->d, static_cast<int>(nr), cig, static_cast<int32_t>(i0), k ? total[0] : 0, st) < 0)
+      return fail();
+    if (cig) {
+      e = cudaMemcpyAsync(&total[k], x->d.cigar_off + x->n_reads, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    // part 0's results come back while part 1 still computes
+    copy(r->item_score + i0, x->d.item_score, x->n_items * 4, st);
+    copy(r->item_end + i0, x->d.item_end, x->n_items * 4, st);
+    copy(r->best + r0, x->d.out_best, static_cast<uint64_t>(x->n_reads) * sizeof(sr_hit), st);
+    copy(r->best_per_ref + static_cast<uint64_t>(r0) * nr, x->d.out_per_ref,
+         static_cast<uint64_t>(x->n_reads) * nr * sizeof(sr_hit), st);
+    if (cls) copy(r->read_class + r0, x->d.read_class, x->n_reads, st);
+    if (e != cudaSuccess) return fail();
+  }
+  if (cig) {
+    const uint64_t words = static_cast<uint64_t>(total[0]) + total[1];
+    uint64_t cgot = 0;
+    void* cblk = pool_take(s, std::max<uint64_t>(words * 4, 256), &cgot);
+    if (!cblk) return fail();
+    box->cig_block = cblk;
+    box->cig_block_bytes = cgot;
+    r->cigar = static_cast<uint32_t*>(cblk);
+    r->n_cigar = words;
+    copy(r->cigar, b[0]->d.cigar, static_cast<uint64_t>(total[0]) * 4, b[0]->stream);
+    copy(r->cigar + total[0], b[1]->d.cigar, static_cast<uint64_t>(total[1]) * 4, b[1]->stream);
+  }
+  for (auto* x : b)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return fail();
+  drop_parts();
+  *out = r;
+  return true;
+}
+}  // namespace sr
+
 extern "C" sr_status sr_align_batch(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
                                     const sr_score_params* sp, const sr_align_opts* opts, sr_results** out) {
   Trace trace_("sr_align_batch");
   if (!out) return set_error(SR_EINVAL, "sr_align_batch: null out");
   *out = nullptr;
+  if (s && reads && cands && sp && reads->n_reads >= kPartMinReads) {
+    const sr_align_opts o = opts ? *opts : default_opts();
+    if (!o.cuda_stream && o.engine != SR_ENGINE_PLAIN && align_in_parts(s, reads, cands, sp, o, out)) return SR_OK;
+  }
   sr_batch* b = nullptr;
   sr_status st = sr_batch_stage(s, reads, cands, opts ? opts->cuda_stream : nullptr, &b);
   if (st != SR_OK) return st;

@@ -74,3 +74,69 @@ def test_c5_full_sampled(sr):
     g = _run(sr, s, w)
     assert int(np.diff(w["cand_off"]).max()) == 256
     _sampled(sr, w, g, 800, 3)
+
+
+def _staged(sr, s, w, **opts):
+    b = s.stage(*[w[k] for k in KEYS])
+    try:
+        b.run(sr.score_params(2, 3, 5, 2), sr.align_opts(**opts))
+        return b.fetch()
+    finally:
+        b.close()
+
+
+def _same_results(g, h):
+    assert g["n_reads"] == h["n_reads"] and g["n_items"] == h["n_items"] and g["cells"] == h["cells"]
+    for key in ("item_score", "item_end", "cigar"):
+        assert np.array_equal(g[key], h[key]), key
+    for f in g["best"].dtype.names:
+        assert np.array_equal(g["best"][f], h["best"][f]), f
+        assert np.array_equal(g["best_per_ref"][f], h["best_per_ref"][f]), f
+    if h["read_class"] is not None:
+        assert np.array_equal(g["read_class"], h["read_class"])
+
+
+def test_c2_call_in_two_parts_equals_one_batch(sr):
+    """sr_align_batch runs calls of 2^19 reads and more as two batches of
+    consecutive reads on two streams; every array, window indexes and CIGAR
+    offsets included, equals that of the same reads staged as one batch."""
+    w = S.workload("c2")
+    s = sr.Session.open([bytes(r) for r in w["refs"]])
+    g = _run(sr, s, w)
+    h = _staged(sr, s, w)
+    _same_results(g, h)
+    # the second part's records point past the first part's windows and CIGARs
+    n = len(w["read_off"]) - 1
+    assert g["best"]["item"][n - 1] >= int(w["cand_off"][n // 2])
+    assert g["best"]["cigar_off"][n - 1] > 0.9 * len(g["cigar"])
+    # a repeat of the call gives the same arrays (the parts' arenas and pinned blocks are reused)
+    _same_results(_run(sr, s, w), h)
+
+
+def test_c3_call_in_two_parts_with_classification(sr):
+    """Two references and classification through the two-part call."""
+    w = S.workload("c3", scale=0.3)
+    assert len(w["read_off"]) - 1 >= (1 << 19)
+    idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=12, cal_limit=1024) for r in w["refs"]]
+    w.update(sr.candidates(idx, w["bases"], w["read_off"], seed_stride=1, merge_dist=32, pad=32))
+    s = sr.Session.from_indexes(idx)
+    opts = dict(classify=True, min_score=40, margin=5)
+    _same_results(_run(sr, s, w, **opts), _staged(sr, s, w, **opts))
+
+
+def test_bad_window_in_a_two_part_call_reports_the_first(sr):
+    """A malformed window in either part gives the error a single batch gives:
+    the first bad window (lowest index, in the caller's numbering)."""
+    w = S.workload("c2", scale=0.6)
+    n_items = len(w["c_len"])
+    s = sr.Session.open([bytes(r) for r in w["refs"]])
+    for k1, k2 in ((n_items * 3 // 4, n_items - 1), (n_items // 4, n_items * 3 // 4)):
+        bad = dict(w, c_len=w["c_len"].copy())
+        bad["c_len"][k1] = 0
+        bad["c_len"][k2] = 0
+        with pytest.raises(sr.SrError) as e:
+            _run(sr, s, bad)
+        assert e.value.status == sr.SR_EINVAL
+        assert f"window {k1} " in str(e.value), str(e.value)
+    g = _run(sr, s, w, want_cigar=0)
+    assert len(g["item_score"]) == n_items and len(g["cigar"]) == 0

@@ -537,7 +537,7 @@ def main():
         h2d = sum(v[1].nbytes for v in pin.values())
         ee = []
         res = None
-        for i in range(4):
+        for i in range(8):
             res = None  # the previous step's results are released before the next call
             t0 = time.perf_counter()
             res = sess.align(*[pin[k][1] for k in ["bases", "read_off", "cand_off", "c_ref", "c_strand",

@@ -124,7 +124,7 @@ constexpr size_t kResPool = 16;
 struct sr_session {
   int device = 0;
   cudaStream_t stream = nullptr;
-  cudaStream_t part_stream[2] = {};  // the two parts of a large sr_align_batch call
+  cudaStream_t part_stream[3] = {};  // the parts of a large sr_align_batch call
   uint32_t n_refs = 0;
   std::vector<uint32_t*> d_words;
   std::vector<uint64_t> lens;
@@ -1468,35 +1468,44 @@ extern "C" sr_status sr_batch_report(sr_session* s, sr_batch* b, uint32_t kind, 
 }
 
 namespace sr {
-// sr_align_batch calls of at least this many reads run as two batches
+// sr_align_batch calls of at least this many reads run as kParts batches
 constexpr uint32_t kPartMinReads = 1u << 19;
+constexpr int kParts = 3;
+// where the parts end, in sixths of the call's windows: a small first part
+// (whose staging nobody hides) and a small last part (whose fetch nobody hides)
+constexpr uint64_t kPartEnd[kParts] = {1, 5, 6};
 
-// One large sr_align_batch call as two batches of consecutive reads, each on a
-// stream of its own.  The second part's copies and host checks run while the
-// first part computes, and the first part's results come back while the second
-// computes.  A read's windows all stay in its part, so every result is the one
-// a single batch gives; the second part's window indexes and CIGAR offsets are
+// One large sr_align_batch call as kParts batches of consecutive reads, each on
+// a stream of its own.  A part's copies and host checks run while the parts
+// before it compute, and its results come back while the parts after it
+// compute.  A read's windows all stay in its part, so every result is the one a
+// single batch gives; a later part's window indexes and CIGAR offsets are
 // shifted on the device as its records are assembled.  Returns false, with
 // nothing left allocated, when any step fails: the caller then runs the call
 // as one batch, which reports the same errors as a call that was never split.
 static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
                            const sr_score_params* sp, const sr_align_opts& o, sr_results** out) {
   Trace trace_("sr_align_batch parts");
+  static_assert(kParts <= static_cast<int>(sizeof(sr_session::part_stream) / sizeof(cudaStream_t)), "streams");
   const uint32_t n = reads->n_reads;
   const uint64_t nc = cands->n_cands;
   if (!reads->offsets || !cands->offsets || cands->n_reads != n || cands->offsets[n] != nc) return false;
-  // the boundary: the first read whose windows start at or past half of all
-  uint32_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint32_t mid = lo + (hi - lo) / 2;
-    if (cands->offsets[mid] < nc / 2) lo = mid + 1;
-    else hi = mid;
+  // part k ends at the first read whose windows start at or past its share
+  uint32_t rr[kParts + 1] = {0};
+  for (int k = 0; k < kParts; ++k) {
+    const uint64_t want = nc / kPartEnd[kParts - 1] * kPartEnd[k];
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo) / 2;
+      if (cands->offsets[mid] < want) lo = mid + 1;
+      else hi = mid;
+    }
+    rr[k + 1] = k == kParts - 1 ? n : lo;
+    if (rr[k + 1] <= rr[k]) return false;
   }
-  if (lo == 0 || lo >= n) return false;
-  const uint32_t rr[3] = {0, lo, n};
   sr_align_opts oo = o;
   oo.cuda_stream = nullptr;
-  sr_batch* b[2] = {};
+  sr_batch* b[kParts] = {};
   auto drop_parts = [&]() {
     for (auto*& x : b)
       if (x) {
@@ -1504,7 +1513,7 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
         x = nullptr;
       }
   };
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < kParts; ++k)
     if (batch_stage_range(s, reads, cands, rr[k], rr[k + 1], s->part_stream[k], true, &b[k]) != SR_OK ||
         batch_run_async(s, b[k], sp, &oo) != SR_OK) {
       drop_parts();
@@ -1513,7 +1522,7 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   const uint32_t nr = s->n_refs;
   const bool cig = o.want_cigar != 0, cls = o.classify != 0;
   // one pinned block for the arrays whose sizes are known now; the CIGAR
-  // words, counted only when both parts are done, get a second one
+  // words, counted only when every part is done, get a second one
   uint64_t off = 0;
   auto part = [&](uint64_t bytes) {
     const uint64_t at = off;
@@ -1541,7 +1550,7 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   r->n_reads = n;
   r->n_refs = nr;
   r->n_items = nc;
-  r->cells = b[0]->cells + b[1]->cells;
+  for (auto* x : b) r->cells += x->cells;
   r->best = reinterpret_cast<sr_hit*>(blk + o_best);
   r->best_per_ref = reinterpret_cast<sr_hit*>(blk + o_per);
   r->item_score = reinterpret_cast<int32_t*>(blk + o_sc);
@@ -1559,20 +1568,22 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   auto copy = [&](void* dst, const void* src, uint64_t bytes, cudaStream_t st) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
   };
-  uint32_t total[2] = {};
-  for (int k = 0; k < 2; ++k) {
+  uint32_t total[kParts] = {};
+  uint64_t i0 = 0, c0 = 0;  // windows and CIGAR words of the parts before
+  for (int k = 0; k < kParts; ++k) {
     sr_batch* x = b[k];
     cudaStream_t st = x->stream;
     if (batch_sync(x, st) != SR_OK) return fail();
     const uint32_t r0 = rr[k];
-    const uint64_t i0 = k ? b[0]->n_items : 0;
-    if (launch_assemble(x->d, static_cast<int>(nr), cig, static_cast<int32_t>(i0), k ? total[0] : 0, st) < 0)
+    if (i0 > static_cast<uint64_t>(INT32_MAX) || c0 > UINT32_MAX ||
+        launch_assemble(x->d, static_cast<int>(nr), cig, static_cast<int32_t>(i0), static_cast<uint32_t>(c0),
+                        st) < 0)
       return fail();
     if (cig) {
       e = cudaMemcpyAsync(&total[k], x->d.cigar_off + x->n_reads, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    // part 0's results come back while part 1 still computes
+    // this part's results come back while the later parts compute
     copy(r->item_score + i0, x->d.item_score, x->n_items * 4, st);
     copy(r->item_end + i0, x->d.item_end, x->n_items * 4, st);
     copy(r->best + r0, x->d.out_best, static_cast<uint64_t>(x->n_reads) * sizeof(sr_hit), st);
@@ -1580,18 +1591,22 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
          static_cast<uint64_t>(x->n_reads) * nr * sizeof(sr_hit), st);
     if (cls) copy(r->read_class + r0, x->d.read_class, x->n_reads, st);
     if (e != cudaSuccess) return fail();
+    i0 += x->n_items;
+    c0 += total[k];
   }
   if (cig) {
-    const uint64_t words = static_cast<uint64_t>(total[0]) + total[1];
     uint64_t cgot = 0;
-    void* cblk = pool_take(s, std::max<uint64_t>(words * 4, 256), &cgot);
+    void* cblk = pool_take(s, std::max<uint64_t>(c0 * 4, 256), &cgot);
     if (!cblk) return fail();
     box->cig_block = cblk;
     box->cig_block_bytes = cgot;
     r->cigar = static_cast<uint32_t*>(cblk);
-    r->n_cigar = words;
-    copy(r->cigar, b[0]->d.cigar, static_cast<uint64_t>(total[0]) * 4, b[0]->stream);
-    copy(r->cigar + total[0], b[1]->d.cigar, static_cast<uint64_t>(total[1]) * 4, b[1]->stream);
+    r->n_cigar = c0;
+    uint64_t at = 0;
+    for (int k = 0; k < kParts; ++k) {
+      copy(r->cigar + at, b[k]->d.cigar, static_cast<uint64_t>(total[k]) * 4, b[k]->stream);
+      at += total[k];
+    }
   }
   for (auto* x : b)
     if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);

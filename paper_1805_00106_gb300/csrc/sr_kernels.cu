@@ -61,19 +61,24 @@ __global__ void k_pack_reads(const char* bases, const uint64_t* off, uint32_t n_
     uint32_t x[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) x[k] = 4u * k < lead + nv ? src[k] : 0u;
+    // four bases at a time: per byte the code of ascii_code (((c >> 1) ^ (c >> 2)) & 3
+    // of the lower-cased byte; bits shifted in from the next byte are masked
+    // off), checked by looking the code's letter up again and comparing
+    uint32_t diff = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const uint32_t y = __funnelshift_r(x[k], x[k + 1], 8u * lead);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t b = 4u * k + q;
-        if (b < nv) {
-          const uint32_t c = ascii_code((y >> (8 * q)) & 0xffu);
-          bad |= c > 3u;
-          v |= (c & 3u) << (2 * b);
-        }
-      }
+      const int left = static_cast<int>(nv) - 4 * k;  // valid bytes of y: min(max(left, 0), 4)
+      const uint32_t keep = left >= 4 ? 0xffffffffu : (left <= 0 ? 0u : (1u << (8 * left)) - 1u);
+      const uint32_t c = y | 0x20202020u;
+      const uint32_t code = ((c >> 1) ^ (c >> 2)) & 0x03030303u & keep;
+      const uint32_t t = code | (code >> 4);                       // codes as nibbles 0..3
+      const uint32_t letters = __byte_perm(0x74676361u, 0u, (t & 0xffu) | ((t >> 8) & 0xff00u));
+      diff |= (c ^ letters) & keep;                                // 'a' 'c' 'g' 't'
+      const uint32_t u = code | (code >> 6);                       // codes as 2-bit fields
+      v |= ((u & 0xfu) | ((u >> 12) & 0xf0u)) << (8 * k);
     }
+    bad = diff != 0;
   }
   rpack[r * kReadWords + w] = v;
   if (w == 0) {
@@ -204,6 +209,8 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
   if (r >= n_reads) return;
   const uint64_t c0 = cand_off[r], c1 = cand_off[r + 1];
   const int slots = 1 + n_refs;
+  // with one reference its record is the overall one: computed once, stored twice
+  const int f_end = n_refs == 1 ? 0 : n_refs;
   if (c1 - c0 <= static_cast<uint64_t>(G)) {
     // up to G windows: one per lane, loaded once; the same rules as below
     const bool has = c0 + l < c1;
@@ -213,7 +220,7 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
     const unsigned long long gend = has ? c_start[c] + item_end[c] - 1 : 0ull;
     const unsigned long long locus = (static_cast<unsigned long long>(ref) << 60) | (gend << 20) |
                                      (static_cast<unsigned long long>(str) << 19);
-    for (int f = -1; f < n_refs; ++f) {
+    for (int f = -1; f < f_end; ++f) {
       const bool in = has && (f < 0 || ref == static_cast<uint32_t>(f));
       const int32_t best = __reduce_max_sync(gm, in ? max(s, 0) : 0);
       DevHit h{};
@@ -232,11 +239,14 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
             __popc(__ballot_sync(gm, top && (same & tops & ((1u << wl) - 1u)) == 0u)));
         h.item = static_cast<int32_t>(c0 + static_cast<uint64_t>(win));
       }
-      if (l == 0) hits[r * slots + (f + 1)] = h;
+      if (l == 0) {
+        hits[r * slots + (f + 1)] = h;
+        if (f_end == 0) hits[r * slots + 1] = h;
+      }
     }
     return;
   }
-  for (int f = -1; f < n_refs; ++f) {
+  for (int f = -1; f < f_end; ++f) {
     // best score
     int32_t best = 0;
     for (uint64_t c = c0 + l; c < c1; c += G) {
@@ -286,7 +296,10 @@ __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32
       h.n_ties = __reduce_add_sync(gm, ties);
       h.item = static_cast<int32_t>(wc);
     }
-    if (l == 0) hits[r * slots + (f + 1)] = h;
+    if (l == 0) {
+      hits[r * slots + (f + 1)] = h;
+      if (f_end == 0) hits[r * slots + 1] = h;
+    }
   }
 }
 

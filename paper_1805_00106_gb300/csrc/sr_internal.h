@@ -111,8 +111,9 @@ constexpr int kTbCodes = kTbBuckets * kMaxReadLen;   // code = bucket * 256 + (2
 constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + 8;
 constexpr int kTbMaxBand = 64;
 // warps of the one-thread-per-read narrow-band traceback (each owns a scratch
-// of 256 rows x 32 lanes of direction words)
-constexpr uint32_t kTbThreadMaxWarps = 4096;
+// of 256 rows x 32 lanes of direction words): 152 SMs x 32, its register-bound
+// residency on GB300
+constexpr uint32_t kTbThreadMaxWarps = 4864;
 inline uint32_t tb_thread_warps(uint32_t n_reads) {
   const uint32_t w = (n_reads + 31u) / 32u;
   return w < kTbThreadMaxWarps ? (w ? w : 1u) : kTbThreadMaxWarps;

@@ -119,6 +119,7 @@ bool res_create(BatchRes& r) {
   return ok;
 }
 constexpr size_t kResPool = 16;
+constexpr size_t kKeptArenas = 3;
 }  // namespace
 
 struct sr_session {
@@ -142,7 +143,8 @@ struct sr_session {
   std::mutex pool_mu;
   std::vector<std::pair<void*, uint64_t>> pool;
   // arenas of freed batches, kept for the next ones (not counted in hbm_used):
-  // up to two, so a two-deep serving pipeline allocates nothing in steady state
+  // up to kKeptArenas, so that neither a two-deep serving pipeline nor the
+  // parts of a large sr_align_batch call allocate anything in steady state
   std::mutex spare_mu;
   std::vector<std::pair<void*, uint64_t>> spares;
   // streams and events of freed batches
@@ -747,13 +749,13 @@ extern "C" void sr_batch_free(sr_batch* b) {
   }
   if (b->arena) {
     cudaStreamSynchronize(b->stream);
-    // keep this arena for the next batches; past two kept, drop the smallest
+    // keep this arena for the next batches; past kKeptArenas kept, drop the smallest
     void* drop = nullptr;
     {
       std::lock_guard<std::mutex> lk(b->s->spare_mu);
       auto& sp = b->s->spares;
       sp.emplace_back(b->arena, b->arena_bytes);
-      if (sp.size() > 2) {
+      if (sp.size() > kKeptArenas) {
         auto it = std::min_element(sp.begin(), sp.end(),
                                    [](const std::pair<void*, uint64_t>& x, const std::pair<void*, uint64_t>& y) {
                                      return x.second < y.second;

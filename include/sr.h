@@ -228,7 +228,7 @@ sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, const sr_ca
  * (device->host).  Errors: SR_EINVAL (shapes, windows past the reference,
  * read or window too long, parameters), SR_EBADBASE, SR_ENOMEM, SR_ECUDA.
  * A call of 2^19 reads or more with opts->cuda_stream NULL (batched engine)
- * runs as three batches of consecutive reads (1/6, 4/6 and 1/6 of the windows)
+ * runs as three batches of consecutive reads (1/10, 8/10 and 1/10 of the windows)
  * on three streams of the session, so that staging and fetching overlap the
  * other parts' compute.  The results, errors included, are those of one batch:
  * window indexes and CIGAR offsets refer to the whole call.  The CIGAR words

@@ -1473,9 +1473,9 @@ namespace sr {
 // sr_align_batch calls of at least this many reads run as kParts batches
 constexpr uint32_t kPartMinReads = 1u << 19;
 constexpr int kParts = 3;
-// where the parts end, in sixths of the call's windows: a small first part
+// where the parts end, in tenths of the call's windows: a small first part
 // (whose staging nobody hides) and a small last part (whose fetch nobody hides)
-constexpr uint64_t kPartEnd[kParts] = {1, 5, 6};
+constexpr uint64_t kPartEnd[kParts] = {1, 9, 10};
 
 // One large sr_align_batch call as kParts batches of consecutive reads, each on
 // a stream of its own.  A part's copies and host checks run while the parts
@@ -1572,6 +1572,31 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   };
   uint32_t total[kParts] = {};
   uint64_t i0 = 0, c0 = 0;  // windows and CIGAR words of the parts before
+  // The CIGAR block is taken once every part but the last is done, sized for
+  // their words plus an estimate of the last part's (its reads at 1.25x the
+  // words per read so far), so the earlier parts' CIGARs come back while the
+  // last part computes.  An estimate that falls short is replaced at the end by
+  // a block of the exact size, into which every part is copied again.
+  int cig_parts = 0;  // parts whose CIGARs are copied into the block
+  uint64_t cig_cap = 0;
+  auto take_cigar_block = [&](uint64_t words) -> bool {
+    uint64_t got_c = 0;
+    void* p = pool_take(s, std::max<uint64_t>(words * 4, 256), &got_c);
+    if (!p) return false;
+    box->cig_block = p;
+    box->cig_block_bytes = got_c;
+    r->cigar = static_cast<uint32_t*>(p);
+    cig_cap = got_c / 4;
+    return true;
+  };
+  auto copy_cigars = [&](int upto) {
+    uint64_t at = 0;
+    for (int k = 0; k < upto; ++k) {
+      if (k >= cig_parts) copy(r->cigar + at, b[k]->d.cigar, static_cast<uint64_t>(total[k]) * 4, b[k]->stream);
+      at += total[k];
+    }
+    cig_parts = upto;
+  };
   for (int k = 0; k < kParts; ++k) {
     sr_batch* x = b[k];
     cudaStream_t st = x->stream;
@@ -1595,20 +1620,27 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
     if (e != cudaSuccess) return fail();
     i0 += x->n_items;
     c0 += total[k];
+    if (cig && k == kParts - 2) {
+      const uint64_t n_done = rr[k + 1], n_last = n - n_done;
+      if (!take_cigar_block(c0 + c0 * n_last * 5 / (4 * n_done) + 4096)) return fail();
+      copy_cigars(k + 1);
+      if (e != cudaSuccess) return fail();
+    }
   }
   if (cig) {
-    uint64_t cgot = 0;
-    void* cblk = pool_take(s, std::max<uint64_t>(c0 * 4, 256), &cgot);
-    if (!cblk) return fail();
-    box->cig_block = cblk;
-    box->cig_block_bytes = cgot;
-    r->cigar = static_cast<uint32_t*>(cblk);
-    r->n_cigar = c0;
-    uint64_t at = 0;
-    for (int k = 0; k < kParts; ++k) {
-      copy(r->cigar + at, b[k]->d.cigar, static_cast<uint64_t>(total[k]) * 4, b[k]->stream);
-      at += total[k];
+    if (c0 > cig_cap) {
+      // the estimate fell short: wait for the copies into the first block, then
+      // copy every part into one of the exact size
+      for (int k = 0; k < cig_parts; ++k)
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b[k]->stream);
+      if (e != cudaSuccess) return fail();
+      pool_give(s, box->cig_block, box->cig_block_bytes);
+      box->cig_block = nullptr;
+      cig_parts = 0;
+      if (!take_cigar_block(c0)) return fail();
     }
+    copy_cigars(kParts);
+    r->n_cigar = c0;
   }
   for (auto* x : b)
     if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);

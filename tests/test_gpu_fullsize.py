@@ -140,3 +140,28 @@ def test_bad_window_in_a_two_part_call_reports_the_first(sr):
         assert f"window {k1} " in str(e.value), str(e.value)
     g = _run(sr, s, w, want_cigar=0)
     assert len(g["item_score"]) == n_items and len(g["cigar"]) == 0
+
+
+def test_two_part_call_whose_last_part_has_long_cigars(sr):
+    """The CIGAR block of a call in parts is sized before its last part is done,
+    from the words per read so far; reads with many deletions at the end of the
+    call overrun that estimate, and the results must still equal one batch's."""
+    w = S.workload("c2", scale=0.55, seed=5)
+    n = len(w["read_off"]) - 1
+    tail = n - n // 8
+    off, bases = w["read_off"].astype(np.int64), w["bases"]
+    pieces, lens = [bases[: off[tail]]], []
+    for r in range(tail, n):
+        seq = bases[off[r]: off[r + 1]]
+        keep = np.ones(len(seq), bool)
+        keep[12::20] = False  # a deletion every 20 bases
+        pieces.append(seq[keep])
+        lens.append(int(keep.sum()))
+    w = dict(w, bases=np.concatenate(pieces),
+             read_off=np.concatenate([off[: tail + 1], off[tail] + np.cumsum(lens)]).astype(w["read_off"].dtype))
+    s = sr.Session.open([bytes(r) for r in w["refs"]])
+    g = _run(sr, s, w)
+    _same_results(g, _staged(sr, s, w))
+    words = g["best"]["cigar_len"].astype(np.int64)
+    # the deletion reads need several times the CIGAR words of the others
+    assert words[tail:].mean() > 3 * words[:tail].mean(), (words[tail:].mean(), words[:tail].mean())

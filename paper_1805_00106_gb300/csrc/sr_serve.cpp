@@ -75,7 +75,7 @@ struct Server {
 namespace {
 
 sr_results* slice_results(const sr_results* all, uint32_t r0, uint32_t r1, uint64_t i0, uint64_t i1,
-                          uint64_t cells) {
+                          uint64_t cells, uint64_t i32_items) {
   const uint32_t n = r1 - r0, nr = all->n_refs;
   const uint64_t ni = i1 - i0;
   sr_results* r = results_alloc();
@@ -84,6 +84,7 @@ sr_results* slice_results(const sr_results* all, uint32_t r0, uint32_t r1, uint6
   r->n_refs = nr;
   r->n_items = ni;
   r->cells = cells;
+  r->n_i32_items = i32_items;
   r->best = static_cast<sr_hit*>(malloc((n ? n : 1) * sizeof(sr_hit)));
   r->best_per_ref = static_cast<sr_hit*>(malloc(static_cast<size_t>(n ? n : 1) * nr * sizeof(sr_hit)));
   r->item_score = static_cast<int32_t*>(malloc((ni ? ni : 1) * 4));
@@ -134,11 +135,15 @@ void finish(Server* sv, Round& rd, sr_results* merged) {
   uint64_t i0 = 0;
   const auto now = Clock::now();
   std::vector<std::pair<Request*, sr_results*>> outs;
+  const uint32_t m32 = i32_min_read_len(sv->sp, sv->opts);
   for (Request* q : rd.reqs) {
     const uint32_t n = static_cast<uint32_t>(q->roff.size() - 1);
     const uint64_t ni = q->coff.back();
+    uint64_t n32 = 0;
+    for (uint32_t r = 0; r < n; ++r)
+      if (q->roff[r + 1] - q->roff[r] >= m32) n32 += q->coff[r + 1] - q->coff[r];
     sr_results* part = nullptr;
-    if (rd.status == SR_OK && merged) part = slice_results(merged, r0, r0 + n, i0, i0 + ni, q->cells);
+    if (rd.status == SR_OK && merged) part = slice_results(merged, r0, r0 + n, i0, i0 + ni, q->cells, n32);
     outs.emplace_back(q, part);
     r0 += n;
     i0 += ni;

@@ -17,6 +17,9 @@ Server*& session_server(sr_session* s);
 uint32_t session_n_refs(sr_session* s);
 sr_status batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
                                void* stream, bool check_budget, sr_batch** out);
+// the shortest read length whose windows the int32 kernel scores under these
+// parameters (0: every window; SR_MAX_READ_LEN + 1: none)
+uint32_t i32_min_read_len(const sr_score_params& sp, const sr_align_opts& o);
 sr_status batch_stage_range(sr_session* s, const sr_reads* reads, const sr_cand_list* cands, uint32_t r0,
                             uint32_t r1, void* stream, bool check_budget, sr_batch** out);
 }  // namespace sr

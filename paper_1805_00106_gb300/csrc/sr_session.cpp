@@ -850,6 +850,16 @@ static bool same_opts(const sr_align_opts& a, const sr_align_opts& b) {
          a.lanes == b.lanes && a.rows == b.rows;
 }
 
+uint32_t i32_min_read_len(const sr_score_params& sp, const sr_align_opts& o) {
+  if (o.engine == SR_ENGINE_PLAIN) return kMaxReadLen + 1;
+  const int32_t goe = sp.gap_open + sp.gap_extend;
+  const bool i16_tables = sp.match + goe <= 127 && goe - sp.mismatch >= -128 && goe + sp.gap_extend + 256 < kBias;
+  if (o.force_i32 || !i16_tables) return 0;
+  for (uint32_t m = 1; m <= static_cast<uint32_t>(kMaxReadLen); ++m)
+    if (static_cast<int64_t>(sp.match) * m > 32767 - kBias) return m;
+  return kMaxReadLen + 1;
+}
+
 sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp, const sr_align_opts* opts) {
   Trace trace_("sr_batch_run");
   if (!s || !b || b->s != s) return set_error(SR_EINVAL, "sr_batch_run: bad session/batch");
@@ -874,9 +884,9 @@ sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp,
   tune_get_bins(bins);
   {
     uint64_t n32 = 0;
-    for (int m = 0; m <= kMaxReadLen; ++m)
-      if (o.force_i32 || !i16_tables || static_cast<int64_t>(sp->match) * m > 32767 - kBias) n32 += b->items_by_len[m];
-    b->i32_items = o.engine == SR_ENGINE_PLAIN ? 0 : n32;
+    for (uint32_t m = i32_min_read_len(*sp, o); m <= static_cast<uint32_t>(kMaxReadLen); ++m)
+      n32 += b->items_by_len[m];
+    b->i32_items = n32;
   }
   const bool plain = o.engine == SR_ENGINE_PLAIN;
   if (plain) {
@@ -1082,6 +1092,7 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
   r->n_refs = nr;
   r->n_items = nc;
   r->cells = b->cells;
+  r->n_i32_items = b->i32_items;
   // records in the public layout are assembled on the device, then every array
   // comes back with one copy each on the batch's stream and a single wait
   const bool cig = b->last_opts.want_cigar != 0;
@@ -1552,7 +1563,10 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   r->n_reads = n;
   r->n_refs = nr;
   r->n_items = nc;
-  for (auto* x : b) r->cells += x->cells;
+  for (auto* x : b) {
+    r->cells += x->cells;
+    r->n_i32_items += x->i32_items;
+  }
   r->best = reinterpret_cast<sr_hit*>(blk + o_best);
   r->best_per_ref = reinterpret_cast<sr_hit*>(blk + o_per);
   r->item_score = reinterpret_cast<int32_t*>(blk + o_sc);

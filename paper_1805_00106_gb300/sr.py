@@ -260,7 +260,7 @@ def results_to_numpy(rp) -> dict:
         item_end=arr(r.item_end, ni, np.uint32),
         cigar=arr(r.cigar, r.n_cigar, np.uint32),
         read_class=arr(r.read_class, n, np.uint8) if r.read_class else None,
-        cells=int(r.cells),
+        cells=int(r.cells), n_i32_items=int(r.n_i32_items),
         n_reads=n, n_refs=nr, n_items=ni,
     )
     return out

@@ -87,6 +87,7 @@ def _staged(sr, s, w, **opts):
 
 def _same_results(g, h):
     assert g["n_reads"] == h["n_reads"] and g["n_items"] == h["n_items"] and g["cells"] == h["cells"]
+    assert g["n_i32_items"] == h["n_i32_items"]
     for key in ("item_score", "item_end", "cigar"):
         assert np.array_equal(g[key], h[key]), key
     for f in g["best"].dtype.names:

@@ -74,7 +74,10 @@ def test_forced_kernel_shapes(sr, shape):
 def test_int32_path_forced(sr):
     w = S.workload("c1", scale=0.01, seed=13)
     s = _session(sr, w)
-    _check(gpu_run(s, w, force_i32=True), oracle_run(w))
+    g = gpu_run(s, w, force_i32=True)
+    _check(g, oracle_run(w))
+    assert g["n_i32_items"] == g["n_items"] > 0
+    assert gpu_run(s, w)["n_i32_items"] == 0
 
 
 def test_overflow_promotion_large_match_score(sr):
@@ -97,7 +100,10 @@ def test_overflow_promotion_large_match_score(sr):
     sp = (200, 3, 5, 2)
     o = oracle_run(w, sp=sp)
     assert o["item_score"].max() == 50000
-    _check(gpu_run(s, w, sp=sp), o)
+    g = gpu_run(s, w, sp=sp)
+    _check(g, o)
+    # a match score this large does not fit the 16-bit kernel's tables: every window is int32
+    assert g["n_i32_items"] == g["n_items"] == 10
 
 
 def test_final_row_mode(sr):

@@ -54,6 +54,7 @@ def test_results_alone_equal_results_in_the_mix(env):
     for a, b in zip(alone, served):
         for k in ["item_score", "item_end", "cigar", "read_class"]:
             assert np.array_equal(a[k], b[k]), k
+        assert a["cells"] == b["cells"] and a["n_i32_items"] == b["n_i32_items"] == 0
         for f in a["best"].dtype.names:
             assert np.array_equal(a["best"][f], b["best"][f]), f
             assert np.array_equal(a["best_per_ref"][f], b["best_per_ref"][f]), f
@@ -61,6 +62,23 @@ def test_results_alone_equal_results_in_the_mix(env):
     assert st["max_round_requests"] >= 2, st  # requests shared device rounds
     assert st["rounds"] < len(reqs)
     assert st["p99_us"] >= st["p50_us"] > 0
+
+
+def test_served_int32_windows_are_counted(env):
+    """A served request's results count its own windows scored by the int32
+    kernel, as a call of its own does."""
+    sr, refs, reqs = env
+    s = sr.Session.open([bytes(r) for r in refs], hbm_budget=6 << 30)
+    opts = sr.align_opts(force_i32=True)
+    some = reqs[:6]
+    alone = [s.align(*[q[k] for k in KEYS], sr.score_params(), opts) for q in some]
+    s.serve_start(sr.score_params(), opts, max_inflight=0)
+    tickets = [s.submit(*[q[k] for k in KEYS]) for q in some]
+    served = [s.wait(t, timeout_ms=120_000) for t in tickets]
+    s.serve_stop()
+    for q, a, b in zip(some, alone, served):
+        assert b["n_i32_items"] == a["n_i32_items"] == len(q["c_len"])
+        assert np.array_equal(a["item_score"], b["item_score"])
 
 
 def test_served_results_match_oracle(env):

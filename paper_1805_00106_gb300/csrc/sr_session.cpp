@@ -1535,7 +1535,7 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   const uint32_t nr = s->n_refs;
   const bool cig = o.want_cigar != 0, cls = o.classify != 0;
   // one pinned block for the arrays whose sizes are known now; the CIGAR
-  // words, counted only when every part is done, get a second one
+  // words get a second one (below)
   uint64_t off = 0;
   auto part = [&](uint64_t bytes) {
     const uint64_t at = off;

@@ -67,3 +67,35 @@ def test_tune_table_roundtrip(tmp_path):
     assert sr.tune_get() == bins
     with pytest.raises(sr.SrError):
         sr.tune_set([(64, 4, 8)] + bins[1:])  # rows do not cover the bin
+
+
+# each ctypes structure of the binding and the C type it mirrors
+LAYOUTS = {"IndexParams": "sr_index_params", "Reads": "sr_reads", "CandParams": "sr_cand_params",
+           "CandList": "sr_cand_list", "ScoreParams": "sr_score_params", "AlignOpts": "sr_align_opts",
+           "Hit": "sr_hit", "Results": "sr_results", "ReportHit": "sr_report_hit", "Report": "sr_report",
+           "SamOpts": "sr_sam_opts"}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every structure the binding passes across the C ABI has the size and the
+    field offsets of its declaration in include/sr.h, as gcc lays it out."""
+    import ctypes
+
+    from paper_1805_00106_gb300 import sr
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sr.h"', "int main(void) {"]
+    for py, c in LAYOUTS.items():
+        lines.append(f'  printf("{py} size %zu\\n", sizeof({c}));')
+        for f, _ in getattr(sr, py)._fields_:
+            lines.append(f'  printf("{py} {f} %zu\\n", offsetof({c}, {f}));')
+    lines.append("  return 0;\n}")
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    assert len(out) == sum(1 + len(getattr(sr, py)._fields_) for py in LAYOUTS)
+    for line in out:
+        py, what, val = line.split()
+        cls = getattr(sr, py)
+        expect = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert int(val) == expect, (py, what, int(val), expect)

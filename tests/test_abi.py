@@ -99,3 +99,29 @@ def test_binding_structs_match_the_header(tmp_path):
         cls = getattr(sr, py)
         expect = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
         assert int(val) == expect, (py, what, int(val), expect)
+
+
+# binding constant -> the header's name for it
+CONSTANTS = {"SR_OK": "SR_OK", "SR_EINVAL": "SR_EINVAL", "SR_ENOMEM": "SR_ENOMEM", "SR_ECUDA": "SR_ECUDA",
+             "SR_EBADBASE": "SR_EBADBASE", "SR_ETIMEOUT": "SR_ETIMEOUT", "SR_EBUSY": "SR_EBUSY",
+             "SR_EIO": "SR_EIO", "MODE_LOCAL": "SR_MODE_LOCAL", "MODE_FINAL_ROW": "SR_MODE_FINAL_ROW",
+             "ENGINE_BATCHED": "SR_ENGINE_BATCHED", "ENGINE_PLAIN": "SR_ENGINE_PLAIN",
+             "CLASS_UNALIGNED": "SR_CLASS_UNALIGNED", "CLASS_A": "SR_CLASS_A", "CLASS_B": "SR_CLASS_B",
+             "CLASS_AMBIGUOUS": "SR_CLASS_AMBIGUOUS", "CIGAR_STRIDE": "SR_CIGAR_STRIDE",
+             "REPORT_BEST_N": "SR_REPORT_BEST_N", "REPORT_TIED": "SR_REPORT_TIED", "REPORT_MAX": "SR_REPORT_MAX"}
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Status codes, modes, engines, classes and limits the binding names have
+    the header's values."""
+    from paper_1805_00106_gb300 import sr
+    body = "\n".join(f'  printf("{py} %lld\\n", (long long)({c}));' for py, c in CONSTANTS.items())
+    src, exe = tmp_path / "consts.c", tmp_path / "consts"
+    src.write_text('#include <stdio.h>\n#include "sr.h"\nint main(void) {\n' + body + "\n  return 0;\n}\n")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    assert len(out) == len(CONSTANTS)
+    for line in out:
+        py, val = line.split()
+        assert getattr(sr, py) == int(val), (py, getattr(sr, py), int(val))

@@ -21,6 +21,9 @@ constexpr int kMaxWinLen = 512;
 constexpr int kMaxRefs = 16;
 constexpr int kReadWords = 16;     // words per packed read row
 constexpr int kCigarStride = 776;  // CIGAR words reserved per read (>= 3*256 + 4 runs)
+static_assert(kMaxReadLen == SR_MAX_READ_LEN && kMaxWinLen == SR_MAX_WIN_LEN && kMaxRefs == SR_MAX_REFS &&
+                  kCigarStride == SR_CIGAR_STRIDE && kReadWords * 16 == kMaxReadLen,
+              "device limits agree with the public header");
 constexpr int kNumBins = 23;       // read-length bins of the batched engine (8-row steps above 96)
 constexpr int kNumClasses = kNumBins + 1;  // + the int32 class
 constexpr int kI32Class = kNumBins;

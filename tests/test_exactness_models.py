@@ -11,7 +11,13 @@ on, checked against the oracle on random cases (CPU, no GPU):
    (cells outside: H = 0, E = F = -inf) finds the end row (smallest i with
    H(i, j*) = S) and reproduces the full-DP traceback exactly; the band is
    the union over those end rows of each row's diagonals, and the closed form
-   the kernels evaluate equals that union.
+   the kernels evaluate equals that union;
+3. four bases per step in the read packing: per byte of a 32-bit word, the
+   2-bit code ((c >> 1) ^ (c >> 2)) & 3 of the lower-cased byte c (the bits a
+   shift brings in from the next byte are masked off), and the check that
+   looking the code's letter up again gives c back, equal the per-base
+   definition: A/C/G/T in either case map to 0-3, every other byte is
+   rejected.
 
 These models mirror the kernels' arithmetic order, not their code."""
 import random
@@ -211,3 +217,56 @@ def test_band_closed_form_is_the_union(seed):
             continue
         for lo, hi in ((ilo, m), (m, m), (ilo, ilo)):
             assert band_closed_form(sa, go, ge, S, jstar, lo, hi) == band_union(sa, go, ge, S, jstar, lo, hi)
+
+
+def _byte_perm(x, y, sel):
+    """prmt: output byte i is byte (sel >> 4i) & 7 of the eight bytes of y:x."""
+    v = (y << 32) | x
+    return sum(((v >> (8 * ((sel >> (4 * i)) & 7))) & 0xFF) << (8 * i) for i in range(4))
+
+
+def _pack4(word, nvalid):
+    """Four bytes -> (packed 2-bit codes of the first nvalid, any byte not ACGT)."""
+    keep = 0xFFFFFFFF if nvalid >= 4 else (1 << (8 * nvalid)) - 1
+    c = word | 0x20202020
+    code = ((c >> 1) ^ (c >> 2)) & 0x03030303 & keep
+    t = code | (code >> 4)
+    letters = _byte_perm(0x74676361, 0, (t & 0xFF) | ((t >> 8) & 0xFF00))
+    bad = ((c ^ letters) & keep) != 0
+    u = code | (code >> 6)
+    return (u & 0xF) | ((u >> 12) & 0xF0), bad
+
+
+def _pack4_definition(bs, nvalid):
+    codes = {ord("A"): 0, ord("C"): 1, ord("G"): 2, ord("T"): 3, ord("a"): 0, ord("c"): 1, ord("g"): 2,
+             ord("t"): 3}
+    v, bad = 0, False
+    for i in range(nvalid):
+        if bs[i] in codes:
+            v |= codes[bs[i]] << (2 * i)
+        else:
+            bad = True
+    return v, bad
+
+
+def test_four_base_packing_equals_the_per_base_definition():
+    # every single byte, alone in its word and followed by each letter
+    for x in range(256):
+        for nxt in b"ACGTN\x00\xff":
+            word = x | (nxt << 8) | (0x41 << 16) | (0x74 << 24)
+            v, bad = _pack4(word, 1)
+            dv, dbad = _pack4_definition(bytes([x, nxt, 0x41, 0x74]), 1)
+            assert bad == dbad, x
+            if not bad:
+                assert v == dv, x
+    # random words of letters, lower case and other bytes, every count of valid bytes
+    rng = random.Random(11)
+    pool = list(b"ACGTacgt") * 6 + list(range(256))
+    for _ in range(20000):
+        bs = bytes(rng.choice(pool) for _ in range(4))
+        nvalid = rng.randint(0, 4)
+        v, bad = _pack4(int.from_bytes(bs, "little"), nvalid)
+        dv, dbad = _pack4_definition(bs, nvalid)
+        assert bad == dbad, (bs, nvalid)
+        if not bad:
+            assert v == dv, (bs, nvalid)

@@ -270,6 +270,35 @@ def test_final_row_mode_is_read_end_anchored():
         assert O.align(q, r, mode=1)["score"] <= O.align(q, r)["score"]
 
 
+@pytest.mark.parametrize("q,r,params", _brute_cases())
+def test_brute_force_final_row_end_column_and_traceback(q, r, params):
+    """Final-row readout (Sec. 3.5-3.6: the best cell of the read's last row),
+    pinned by enumeration: the score is the best over alignments that consume
+    the whole read (end row m, which may end in an insertion), the end column
+    is the smallest window column reaching it, and the CIGAR is the
+    priority-ranked co-optimal alignment ending in that cell."""
+    sa, sb, go, ge = params
+    m = len(q)
+    res = O.align(q, r, O.score_params(*params), mode=1)
+    alns = [a for a in enumerate_alignments(q, r, sa, sb, go, ge) if a[3] == m]
+    S = max([0] + [a[0] for a in alns])
+    assert res["score"] == S
+    if S == 0:
+        assert (res["end_i"], res["end_j"]) == (0, 0)
+        assert res["cigar"] == []
+        return
+    ej = min(a[4] for a in alns if a[0] == S)
+    assert (res["end_i"], res["end_j"]) == (m, ej)
+    if go == 0:
+        return  # adjacent gap runs tie with free gap opening (as in the local readout)
+    cands = [a for a in alns if a[0] == S and a[4] == ej]
+    chosen = min(cands, key=lambda a: backward_rank(a[5]))
+    assert (res["start_i"], res["start_j"]) == (chosen[1], chosen[2])
+    assert cigar_ops(res["cigar"]) == chosen[5]
+    # the CIGAR covers the whole read: leading soft clip only, no trailing clip
+    assert res["cigar"][-1][1] != O.OP_S
+
+
 # ------------------------------------------------------- paper worked examples
 
 def _golden(name):

@@ -1493,16 +1493,21 @@ constexpr uint64_t kPartEnd[kParts] = {1, 9, 10};
 // before it compute, and its results come back while the parts after it
 // compute.  A read's windows all stay in its part, so every result is the one a
 // single batch gives; a later part's window indexes and CIGAR offsets are
-// shifted on the device as its records are assembled.  Returns false, with
-// nothing left allocated, when any step fails: the caller then runs the call
-// as one batch, which reports the same errors as a call that was never split.
-static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
-                           const sr_score_params* sp, const sr_align_opts& o, sr_results** out) {
+// shifted on the device as its records are assembled.  An input error or a
+// device error (bad base, window, timeout) is returned as it stands: staging
+// checks the parts in read order and reports indexes in the caller's arrays, so
+// the status and message are those of an unsplit call.  Only when a resource
+// runs out (device arena, pinned host block, the call's shape does not split)
+// does it return kRunAsOne, with nothing left allocated; the caller then runs
+// the call as one batch.
+constexpr sr_status kRunAsOne = 1;
+static sr_status align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                                const sr_score_params* sp, const sr_align_opts& o, sr_results** out) {
   Trace trace_("sr_align_batch parts");
   static_assert(kParts <= static_cast<int>(sizeof(sr_session::part_stream) / sizeof(cudaStream_t)), "streams");
   const uint32_t n = reads->n_reads;
   const uint64_t nc = cands->n_cands;
-  if (!reads->offsets || !cands->offsets || cands->n_reads != n || cands->offsets[n] != nc) return false;
+  if (!reads->offsets || !cands->offsets || cands->n_reads != n || cands->offsets[n] != nc) return kRunAsOne;
   // part k ends at the first read whose windows start at or past its share
   uint32_t rr[kParts + 1] = {0};
   for (int k = 0; k < kParts; ++k) {
@@ -1514,7 +1519,7 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
       else hi = mid;
     }
     rr[k + 1] = k == kParts - 1 ? n : lo;
-    if (rr[k + 1] <= rr[k]) return false;
+    if (rr[k + 1] <= rr[k]) return kRunAsOne;
   }
   sr_align_opts oo = o;
   oo.cuda_stream = nullptr;
@@ -1526,12 +1531,14 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
         x = nullptr;
       }
   };
-  for (int k = 0; k < kParts; ++k)
-    if (batch_stage_range(s, reads, cands, rr[k], rr[k + 1], s->part_stream[k], true, &b[k]) != SR_OK ||
-        batch_run_async(s, b[k], sp, &oo) != SR_OK) {
+  for (int k = 0; k < kParts; ++k) {
+    sr_status st = batch_stage_range(s, reads, cands, rr[k], rr[k + 1], s->part_stream[k], true, &b[k]);
+    if (st == SR_OK) st = batch_run_async(s, b[k], sp, &oo);
+    if (st != SR_OK) {
       drop_parts();
-      return false;
+      return st == SR_ENOMEM ? kRunAsOne : st;
     }
+  }
   const uint32_t nr = s->n_refs;
   const bool cig = o.want_cigar != 0, cls = o.classify != 0;
   // one pinned block for the arrays whose sizes are known now; the CIGAR
@@ -1553,7 +1560,7 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   if (!r) {
     if (blk) pool_give(s, blk, got);
     drop_parts();
-    return false;
+    return kRunAsOne;
   }
   auto* box = reinterpret_cast<ResultsBox*>(r);
   box->pool_of = s;
@@ -1572,13 +1579,14 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   r->item_score = reinterpret_cast<int32_t*>(blk + o_sc);
   r->item_end = reinterpret_cast<uint32_t*>(blk + o_end);
   if (cls) r->read_class = reinterpret_cast<uint8_t*>(blk + o_cls);
-  auto fail = [&]() {
+  // st_fail: the status to return (kRunAsOne when a host block ran out)
+  auto fail = [&](sr_status st_fail) {
     for (auto* x : b)
       if (x) cudaStreamSynchronize(x->stream);
     cudaGetLastError();
     sr_results_free(r);
     drop_parts();
-    return false;
+    return st_fail;
   };
   cudaError_t e = cudaSuccess;
   auto copy = [&](void* dst, const void* src, uint64_t bytes, cudaStream_t st) {
@@ -1614,12 +1622,14 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
   for (int k = 0; k < kParts; ++k) {
     sr_batch* x = b[k];
     cudaStream_t st = x->stream;
-    if (batch_sync(x, st) != SR_OK) return fail();
+    const sr_status sst = batch_sync(x, st);
+    if (sst != SR_OK) return fail(sst);
     const uint32_t r0 = rr[k];
-    if (i0 > static_cast<uint64_t>(INT32_MAX) || c0 > UINT32_MAX ||
-        launch_assemble(x->d, static_cast<int>(nr), cig, static_cast<int32_t>(i0), static_cast<uint32_t>(c0),
+    if (i0 > static_cast<uint64_t>(INT32_MAX) || c0 > UINT32_MAX)
+      return fail(set_error(SR_EINVAL, "sr_align_batch: more than 2^31 windows or 2^32 CIGAR words"));
+    if (launch_assemble(x->d, static_cast<int>(nr), cig, static_cast<int32_t>(i0), static_cast<uint32_t>(c0),
                         st) < 0)
-      return fail();
+      return fail(cuda_error("sr_align_batch assemble", cudaGetLastError()));
     if (cig) {
       e = cudaMemcpyAsync(&total[k], x->d.cigar_off + x->n_reads, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1631,14 +1641,14 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
     copy(r->best_per_ref + static_cast<uint64_t>(r0) * nr, x->d.out_per_ref,
          static_cast<uint64_t>(x->n_reads) * nr * sizeof(sr_hit), st);
     if (cls) copy(r->read_class + r0, x->d.read_class, x->n_reads, st);
-    if (e != cudaSuccess) return fail();
+    if (e != cudaSuccess) return fail(cuda_error("sr_align_batch copy", e));
     i0 += x->n_items;
     c0 += total[k];
     if (cig && k == kParts - 2) {
       const uint64_t n_done = rr[k + 1], n_last = n - n_done;
-      if (!take_cigar_block(c0 + c0 * n_last * 5 / (4 * n_done) + 4096)) return fail();
+      if (!take_cigar_block(c0 + c0 * n_last * 5 / (4 * n_done) + 4096)) return fail(kRunAsOne);
       copy_cigars(k + 1);
-      if (e != cudaSuccess) return fail();
+      if (e != cudaSuccess) return fail(cuda_error("sr_align_batch copy", e));
     }
   }
   if (cig) {
@@ -1647,21 +1657,21 @@ static bool align_in_parts(sr_session* s, const sr_reads* reads, const sr_cand_l
       // copy every part into one of the exact size
       for (int k = 0; k < cig_parts; ++k)
         if (e == cudaSuccess) e = cudaStreamSynchronize(b[k]->stream);
-      if (e != cudaSuccess) return fail();
+      if (e != cudaSuccess) return fail(cuda_error("sr_align_batch copy", e));
       pool_give(s, box->cig_block, box->cig_block_bytes);
       box->cig_block = nullptr;
       cig_parts = 0;
-      if (!take_cigar_block(c0)) return fail();
+      if (!take_cigar_block(c0)) return fail(kRunAsOne);
     }
     copy_cigars(kParts);
     r->n_cigar = c0;
   }
   for (auto* x : b)
     if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
-  if (e != cudaSuccess) return fail();
+  if (e != cudaSuccess) return fail(cuda_error("sr_align_batch copy", e));
   drop_parts();
   *out = r;
-  return true;
+  return SR_OK;
 }
 }  // namespace sr
 
@@ -1672,7 +1682,10 @@ extern "C" sr_status sr_align_batch(sr_session* s, const sr_reads* reads, const 
   *out = nullptr;
   if (s && reads && cands && sp && reads->n_reads >= kPartMinReads) {
     const sr_align_opts o = opts ? *opts : default_opts();
-    if (!o.cuda_stream && o.engine != SR_ENGINE_PLAIN && align_in_parts(s, reads, cands, sp, o, out)) return SR_OK;
+    if (!o.cuda_stream && o.engine != SR_ENGINE_PLAIN) {
+      const sr_status st = align_in_parts(s, reads, cands, sp, o, out);
+      if (st != kRunAsOne) return st;
+    }
   }
   sr_batch* b = nullptr;
   sr_status st = sr_batch_stage(s, reads, cands, opts ? opts->cuda_stream : nullptr, &b);

@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="wall budget of the oracle sample")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default bins)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving latency run")
-    ap.add_argument("--serve-seconds", type=float, default=4.0, help="duration of each offered load")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="duration of each offered load")
+    ap.add_argument("--serve-budget-mb", type=int, default=1024,
+                    help="HBM budget of the serving session (admission binds at high load)")
     ap.add_argument("--no-cal", action="store_true", help="skip the CAL finder comparison")
     ap.add_argument("--sweep", action="store_true",
                     help="seed length x CAL limit sweep on the xenograft and repeat-heavy workloads "
@@ -191,11 +193,16 @@ def slice_reads(w, r0, r1):
                 c_start=w["c_start"][c0:c1], c_len=w["c_len"][c0:c1])
 
 
-def serving_bench(sr, scale, seconds=4.0, pool_size=48, seed=404):
+SIZE_BUCKETS = (256, 1024, 2048, 4096)
+
+
+def serving_bench(sr, scale, seconds=30.0, pool_size=48, seed=404, budget_mb=1024):
     """Continuous batching on the xenograft reference pair (64 Mbp A and a diverged
     B, held on the device): requests of 1-4096 reads (75-250 bp, 0-64 windows
     each) arrive as a Poisson process at 0.25x, 0.5x and 0.9x of the served
-    saturation rate; latency is submit -> completion per request."""
+    saturation rate; latency is submit -> completion per request, also split by
+    request size; the HBM budget is small enough that admission waits at high
+    load."""
     import threading
     from paper_1805_00106_gb300 import synth
     a = synth.ref_iid(max(20000, int(64_000_000 * scale)), seed)
@@ -203,7 +210,7 @@ def serving_bench(sr, scale, seconds=4.0, pool_size=48, seed=404):
                      min(10_000, len(a) // 40), min(1_000_000, len(a) // 20))
     pool = synth.serving_batches([a, b], pool_size, seed + 2)
     keys = ["bases", "read_off", "cand_off", "c_ref", "c_strand", "c_start", "c_len"]
-    sess = sr.Session.open([bytes(a), bytes(b)], hbm_budget=8 << 30)
+    sess = sr.Session.open([bytes(a), bytes(b)], hbm_budget=budget_mb << 20)
     spp = sr.score_params(*SP)
     opts = sr.align_opts(classify=True)
 
@@ -247,16 +254,27 @@ def serving_bench(sr, scale, seconds=4.0, pool_size=48, seed=404):
         th.join()
         el = time.perf_counter() - t0
         st = sess.serve_stats()
+        bs = sess.serve_stats_by_size(SIZE_BUCKETS)
+        ov = sess.serve_overlap()
         sess.serve_stop()
+        lo = 0
+        by_size = []
+        for x in bs:
+            by_size.append({"reads": f"{lo + 1}-{x['max_reads']}", "requests": x["count"],
+                            "p50_ms": round(x["p50_us"] / 1e3, 3), "p99_ms": round(x["p99_us"] / 1e3, 3)})
+            lo = x["max_reads"]
         return dict(requests=len(tickets), req_per_s=round(len(tickets) / el, 2),
                     reads_per_s=round(sum(reads) / el, 1), p50_ms=round(st["p50_us"] / 1e3, 3),
                     p99_ms=round(st["p99_us"] / 1e3, 3), rounds=st["rounds"],
-                    max_round_requests=st["max_round_requests"])
+                    max_round_requests=st["max_round_requests"], by_size=by_size,
+                    rounds_overlapping_previous=ov["overlapped"], device_gap_ms=round(ov["device_idle_ms"], 1),
+                    budget_waits=ov["budget_waits"], seconds=round(el, 1))
 
     run(1.0, 0, burst=True)  # warm-up: graph shapes, host pages
     sat = run(1.0, 0, burst=True)
     out = {"workload": "xenograft pair 64 Mbp (A, B = A with 15% substitutions, 2% indels, 50 block "
                        "moves); requests of 1-4096 reads, 75-250 bp, 0-64 windows each; Poisson arrivals",
+           "hbm_budget_mb": budget_mb, "rounds_in_flight": 2,
            "saturation": {"req_per_s": sat["req_per_s"], "reads_per_s": sat["reads_per_s"]}, "loads": []}
     for f in (0.25, 0.5, 0.9):
         r = run(f * sat["req_per_s"], seconds)
@@ -551,7 +569,7 @@ def main():
                        "d2h_bytes_per_step": int(d2h), "ms_per_step": round(1e3 * e2e_t, 2),
                        "reads_per_s": round(n_reads / e2e_t, 1)}
     if rank == 0 and not args.no_serve:
-        line["serving"] = serving_bench(sr, args.scale, args.serve_seconds)
+        line["serving"] = serving_bench(sr, args.scale, args.serve_seconds, budget_mb=args.serve_budget_mb)
     if rank == 0 and not args.no_cal:
         line["cal_finder"] = cal_finder_bench(sr, args.scale)
     if rank == 0 and not args.no_cpu_baseline:

@@ -330,14 +330,22 @@ sr_status sr_classify(sr_session* s, sr_batch* b, const sr_classify_params* para
                       uint8_t* class_out);
 
 /* -------------------------------------------------------------- serving
- * Continuous batching: sr_submit copies a request and returns a ticket at once;
- * a scheduler thread admits requests while their device footprint fits the
- * session's hbm_budget, merges the admitted requests into the next device
- * round, up to 131072 reads per round (a single larger request runs alone;
- * copies of the next round overlap the current one), and completes each
- * request as soon as its round finishes.  sr_wait blocks up to timeout_ms
- * (< 0 = forever) and returns SR_ETIMEOUT when the limit runs out.  A request
- * larger than the whole budget is rejected with SR_ENOMEM. */
+ * Continuous batching (reads are handed to the aligners as they arrive,
+ * Sec. 4.2): sr_submit copies a request and returns a ticket at once.  A
+ * scheduler thread admits queued requests in arrival order while their device
+ * footprint fits the session's hbm_budget, merges them into the next device
+ * round (up to 131072 reads; a single larger request runs alone), stages it and
+ * launches all its kernels on a stream of its own while the previous round is
+ * still on the device: two rounds are in flight at once.  The new round's read
+ * packing and length binning run beside the previous round's last kernels; its
+ * extension kernels wait on the device for that round's last kernel.  A second
+ * thread completes the rounds in order: it copies a round's results back and
+ * splits them per request while the next round computes.  sr_wait blocks up to
+ * timeout_ms (< 0 = forever) and returns SR_ETIMEOUT when the limit runs out.
+ * A request larger than the whole budget is rejected with SR_ENOMEM.  The
+ * score parameters and options of every request are the ones given to
+ * sr_serve_start (opts NULL: CIGARs on, no classification; the batched engine
+ * only, else SR_EINVAL; opts->cuda_stream is ignored). */
 sr_status sr_serve_start(sr_session* s, const sr_score_params* sp, const sr_align_opts* opts,
                          uint32_t max_inflight_requests);
 sr_status sr_submit(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
@@ -347,6 +355,27 @@ sr_status sr_wait(sr_session* s, uint64_t ticket, int32_t timeout_ms, sr_results
  * p50, p99, count; rounds run and the largest number of requests in a round. */
 sr_status sr_serve_stats(sr_session* s, double* p50_us, double* p99_us, uint64_t* completed,
                          uint64_t* rounds, uint64_t* max_round_requests);
+/* The same latency split by request size: bucket k holds the requests of
+ * max_reads[k-1] + 1 .. max_reads[k] reads (bucket 0: 0 .. max_reads[0]);
+ * bounds must increase.  p50_us, p99_us and count have n_buckets entries each
+ * (any may be NULL). */
+sr_status sr_serve_stats_by_size(sr_session* s, uint32_t n_buckets, const uint32_t* max_reads,
+                                 double* p50_us, double* p99_us, uint64_t* count);
+/* Device timeline of the completed rounds, from CUDA events the server records
+ * on each round's stream: first_ms[k] when round k's first kernel finished,
+ * last_ms[k] when its last kernel finished, both in ms after sr_serve_start
+ * (rounds in launch order; up to cap entries written, 65536 rounds kept).
+ * overlapped counts the rounds whose first kernel finished before the previous
+ * round's last kernel; device_idle_ms sums, over the other consecutive pairs,
+ * the time from one round's last kernel to the end of the next one's first
+ * kernel (it includes the time when no request was waiting).  budget_waits
+ * counts the admissions the HBM budget deferred.  Any pointer may be NULL
+ * (first_ms / last_ms only when cap is 0). */
+sr_status sr_serve_overlap(sr_session* s, uint64_t* timed_rounds, uint64_t* overlapped,
+                           double* device_idle_ms, uint64_t* budget_waits, uint32_t cap,
+                           float* first_ms, float* last_ms);
+/* Stops the server after every queued request has run; results not yet taken
+ * with sr_wait are freed. */
 sr_status sr_serve_stop(sr_session* s);
 
 /* ------------------------------------------------------------ autotuner

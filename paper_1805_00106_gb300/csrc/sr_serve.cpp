@@ -1,13 +1,21 @@
 // sr_serve.cpp -- continuous batching for libsr.
 //
 // Requests (a read batch plus its candidate windows) are copied at submit and
-// queued.  One scheduler thread runs a two-deep pipeline: while round k runs
-// on one CUDA stream, it admits every queued request whose device footprint
-// still fits the session's HBM budget (FIFO, bounded by max_inflight and by
-// kMaxRoundReads reads per round), merges them into round k+1 and stages its
-// inputs on the other stream; then it
-// collects round k, splits the merged results back per request (item and
-// CIGAR indices rebased) and completes those requests, freeing their budget.
+// queued.  Two threads keep the device busy:
+//  - the scheduler admits every queued request whose device footprint still
+//    fits the session's HBM budget (FIFO, bounded by max_inflight and by
+//    kMaxRoundReads reads per round), merges them into the next round, stages
+//    its inputs and launches every kernel of the round on a stream of its own,
+//    as long as fewer than kDepth rounds are in flight;
+//  - the completer waits for the oldest round, copies its results back, splits
+//    them per request (window and CIGAR indexes rebased) and completes those
+//    requests, freeing their budget and the round's slot.
+// So round k+1 is on the device before round k ends: its first kernels (read
+// packing, work list, length bins) run beside round k's last ones, and its
+// extension kernels wait on the device (not on the host) for round k's last
+// kernel, so that round k's latency-bound tail (selection, traceback, result
+// records) is not crowded out by round k+1's persistent kernels.  Round k's
+// copies back, the split and the frees run while round k+1 computes.
 // Each read's result depends only on that read and its windows, so a request
 // gets identical results alone or in any mix.
 #include <cuda_runtime.h>
@@ -30,6 +38,11 @@ namespace sr {
 namespace {
 using Clock = std::chrono::steady_clock;
 constexpr uint64_t kMaxRoundReads = 131072;
+// rounds in flight (launched, not yet completed): one computing, the next
+// queued behind it on the device
+constexpr int kDepth = 2;
+// device timelines of the most recent rounds kept for sr_serve_overlap
+constexpr size_t kTimelineCap = 1u << 16;
 
 struct Request {
   uint64_t ticket = 0;
@@ -38,16 +51,27 @@ struct Request {
   std::vector<uint8_t> cref, cstr;
   std::vector<uint32_t> clen;
   uint64_t bytes = 0, cells = 0;
+  uint32_t n_reads = 0;
   Clock::time_point t_submit, t_done;
   sr_results* res = nullptr;
   sr_status status = SR_OK;
   bool done = false;
 };
 
+// a round's stream and the events that time it on the device
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t first = nullptr;  // after the round's first kernel
+  cudaEvent_t last = nullptr;   // after its last kernel
+  bool busy = false;
+};
+
 struct Round {
   std::vector<Request*> reqs;
   sr_batch* b = nullptr;
   sr_status status = SR_OK;
+  int slot = -1;
+  bool timed = false;  // its events were recorded
 };
 
 }  // namespace
@@ -59,17 +83,26 @@ struct Server {
   sr_align_opts opts{};
   uint32_t max_inflight = 0;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_round;
   std::deque<Request*> pending;
   std::map<uint64_t, Request*> all;
   uint64_t next_ticket = 1;
   uint64_t reserved = 0;
   uint64_t inflight = 0;
   bool stop = false;
-  std::thread th;
+  bool sched_done = false;
+  std::thread th_sched, th_done;
+  // completed requests: latency (us) and size (reads)
   std::vector<double> lat_us;
-  uint64_t rounds = 0, max_round = 0;
-  cudaStream_t streams[2] = {nullptr, nullptr};
+  std::vector<uint32_t> lat_reads;
+  uint64_t rounds = 0, rounds_done = 0, max_round = 0, budget_waits = 0;
+  // rounds launched and not yet completed, oldest first (the completer's queue)
+  std::deque<Round> launched;
+  Slot slots[kDepth];
+  cudaEvent_t t0 = nullptr;      // device time origin of the timelines
+  int last_slot = -1;            // slot of the round launched last
+  // per completed round: (first kernel done, last kernel done) in ms after t0
+  std::vector<std::pair<float, float>> timeline;
 };
 
 namespace {
@@ -137,7 +170,7 @@ void finish(Server* sv, Round& rd, sr_results* merged) {
   std::vector<std::pair<Request*, sr_results*>> outs;
   const uint32_t m32 = i32_min_read_len(sv->sp, sv->opts);
   for (Request* q : rd.reqs) {
-    const uint32_t n = static_cast<uint32_t>(q->roff.size() - 1);
+    const uint32_t n = q->n_reads;
     const uint64_t ni = q->coff.back();
     uint64_t n32 = 0;
     for (uint32_t r = 0; r < n; ++r)
@@ -158,16 +191,17 @@ void finish(Server* sv, Round& rd, sr_results* merged) {
     sv->reserved -= q->bytes;
     --sv->inflight;
     sv->lat_us.push_back(std::chrono::duration<double, std::micro>(now - q->t_submit).count());
+    sv->lat_reads.push_back(q->n_reads);
   }
   sv->cv_done.notify_all();
   sv->cv_work.notify_all();
 }
 
-sr_batch* stage_round(Server* sv, Round& rd, int stream_idx) {
+sr_batch* stage_round(Server* sv, Round& rd, cudaStream_t stream) {
   uint32_t n = 0;
   uint64_t nb = 0, ni = 0;
   for (Request* q : rd.reqs) {
-    n += static_cast<uint32_t>(q->roff.size() - 1);
+    n += q->n_reads;
     nb += q->roff.back();
     ni += q->coff.back();
   }
@@ -178,7 +212,7 @@ sr_batch* stage_round(Server* sv, Round& rd, int stream_idx) {
   uint32_t r = 0;
   uint64_t ob = 0, oi = 0;
   for (Request* q : rd.reqs) {
-    const uint32_t qn = static_cast<uint32_t>(q->roff.size() - 1);
+    const uint32_t qn = q->n_reads;
     if (q->roff.back()) memcpy(bases.data() + ob, q->bases.data(), q->roff.back());
     for (uint32_t k = 0; k < qn; ++k) {
       roff[r + k] = ob + q->roff[k];
@@ -207,65 +241,111 @@ sr_batch* stage_round(Server* sv, Round& rd, int stream_idx) {
   cl.win_start = cstart.data();
   cl.win_len = clen.data();
   sr_batch* b = nullptr;
-  rd.status = batch_stage_internal(sv->s, &reads, &cl, sv->streams[stream_idx], false, &b);
+  rd.status = batch_stage_internal(sv->s, &reads, &cl, stream, false, &b);
   return rd.status == SR_OK ? b : nullptr;
 }
 
+// Admits, stages and launches rounds while fewer than kDepth are in flight.
 void scheduler(Server* sv) {
   cudaSetDevice(sv->device);
-  Round running;
-  int next_stream = 0;
   for (;;) {
     Round next;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
-      if (!running.b) sv->cv_work.wait(lk, [&] { return sv->stop || !sv->pending.empty(); });
-      if (sv->stop && sv->pending.empty() && !running.b) break;
+      auto free_slot = [&] {
+        for (int i = 0; i < kDepth; ++i)
+          if (!sv->slots[i].busy) return i;
+        return -1;
+      };
+      // on stop, the queued requests are still run before the scheduler exits
+      sv->cv_work.wait(lk, [&] {
+        return (sv->stop && sv->pending.empty()) || (!sv->pending.empty() && free_slot() >= 0);
+      });
+      if (sv->pending.empty()) break;
       const uint64_t budget = session_budget(sv->s);
       uint64_t round_reads = 0;
       while (!sv->pending.empty()) {
         Request* q = sv->pending.front();
-        if (budget && sv->reserved + q->bytes > budget) break;
+        if (budget && sv->reserved + q->bytes > budget) {
+          ++sv->budget_waits;
+          break;
+        }
         if (sv->max_inflight && sv->inflight >= sv->max_inflight) break;
         // a round stays at most kMaxRoundReads reads (one request may exceed it alone),
         // so a backlog drains in rounds of bounded latency and device memory
-        const uint64_t qn = q->roff.size() - 1;
-        if (!next.reqs.empty() && round_reads + qn > kMaxRoundReads) break;
-        round_reads += qn;
+        if (!next.reqs.empty() && round_reads + q->n_reads > kMaxRoundReads) break;
+        round_reads += q->n_reads;
         sv->pending.pop_front();
         sv->reserved += q->bytes;
         ++sv->inflight;
         next.reqs.push_back(q);
       }
-    }
-    if (!next.reqs.empty()) next.b = stage_round(sv, next, next_stream);  // overlaps `running`
-    if (running.b || !running.reqs.empty()) {
-      sr_results* merged = nullptr;
-      if (running.status == SR_OK) running.status = sr_batch_fetch(sv->s, running.b, &merged);
-      finish(sv, running, merged);
-      sr_results_free(merged);
-      sr_batch_free(running.b);
-      running = Round();
-    }
-    if (!next.reqs.empty()) {
-      if (next.status == SR_OK) {
-        sr_align_opts o = sv->opts;
-        o.cuda_stream = sv->streams[next_stream];
-        next.status = sr_batch_run_async(sv->s, next.b, &sv->sp, &o);
+      if (next.reqs.empty()) {
+        // the front request does not fit: rounds are in flight (an empty device
+        // admits any request under the budget), and their completion frees budget
+        const uint64_t seen = sv->rounds_done;
+        sv->cv_work.wait(lk, [&] { return sv->rounds_done != seen; });
+        continue;
       }
-      {
-        std::lock_guard<std::mutex> g(sv->mu);
-        ++sv->rounds;
-        sv->max_round = std::max<uint64_t>(sv->max_round, next.reqs.size());
-      }
-      if (next.status != SR_OK) {
-        finish(sv, next, nullptr);
-        sr_batch_free(next.b);
-      } else {
-        running = next;
-        next_stream ^= 1;
+      next.slot = free_slot();
+      sv->slots[next.slot].busy = true;
+    }
+    Slot& sl = sv->slots[next.slot];
+    next.b = stage_round(sv, next, sl.stream);
+    if (next.status == SR_OK) {
+      sr_align_opts o = sv->opts;
+      o.cuda_stream = sl.stream;
+      // the previous round's last kernel (its slot still holds that record)
+      cudaEvent_t prev = sv->last_slot >= 0 ? sv->slots[sv->last_slot].last : nullptr;
+      next.status = batch_run_serving(sv->s, next.b, &sv->sp, &o, sl.first, prev);
+      if (next.status == SR_OK && cudaEventRecord(sl.last, sl.stream) == cudaSuccess) {
+        next.timed = true;
+        sv->last_slot = next.slot;
       }
     }
+    std::lock_guard<std::mutex> g(sv->mu);
+    ++sv->rounds;
+    sv->max_round = std::max<uint64_t>(sv->max_round, next.reqs.size());
+    sv->launched.push_back(std::move(next));
+    sv->cv_round.notify_all();
+  }
+  std::lock_guard<std::mutex> g(sv->mu);
+  sv->sched_done = true;
+  sv->cv_round.notify_all();
+}
+
+// Completes the launched rounds in order: waits for each, copies its results
+// back (the records were built on the device), splits them per request.
+void completer(Server* sv) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    Round rd;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv_round.wait(lk, [&] { return !sv->launched.empty() || sv->sched_done; });
+      if (sv->launched.empty()) break;  // the scheduler has exited and every round is complete
+      rd = std::move(sv->launched.front());
+      sv->launched.pop_front();
+    }
+    sr_results* merged = nullptr;
+    if (rd.status == SR_OK) rd.status = sr_batch_fetch(sv->s, rd.b, &merged);
+    const Slot& sl = sv->slots[rd.slot];
+    float a = 0, z = 0;
+    const bool timed = rd.timed && rd.status == SR_OK && cudaEventElapsedTime(&a, sv->t0, sl.first) == cudaSuccess &&
+                       cudaEventElapsedTime(&z, sv->t0, sl.last) == cudaSuccess;
+    cudaGetLastError();
+    if (timed) {
+      // before the requests complete, so a caller that has all its results sees this round
+      std::lock_guard<std::mutex> g(sv->mu);
+      if (sv->timeline.size() < kTimelineCap) sv->timeline.emplace_back(a, z);
+    }
+    finish(sv, rd, merged);
+    sr_results_free(merged);
+    sr_batch_free(rd.b);
+    std::lock_guard<std::mutex> g(sv->mu);
+    sv->slots[rd.slot].busy = false;
+    ++sv->rounds_done;
+    sv->cv_work.notify_all();
   }
 }
 
@@ -278,13 +358,18 @@ void serve_destroy(Server* sv) {
     sv->stop = true;
   }
   sv->cv_work.notify_all();
-  if (sv->th.joinable()) sv->th.join();
+  if (sv->th_sched.joinable()) sv->th_sched.join();
+  if (sv->th_done.joinable()) sv->th_done.join();
   for (auto& kv : sv->all) {
     sr_results_free(kv.second->res);
     delete kv.second;
   }
-  for (auto st : sv->streams)
-    if (st) cudaStreamDestroy(st);
+  for (auto& sl : sv->slots) {
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.first) cudaEventDestroy(sl.first);
+    if (sl.last) cudaEventDestroy(sl.last);
+  }
+  if (sv->t0) cudaEventDestroy(sv->t0);
   delete sv;
 }
 
@@ -296,26 +381,36 @@ extern "C" sr_status sr_serve_start(sr_session* s, const sr_score_params* sp, co
                                     uint32_t max_inflight_requests) {
   if (!s || !sp) return set_error(SR_EINVAL, "sr_serve_start: null argument");
   if (session_server(s)) return set_error(SR_EBUSY, "sr_serve_start: already serving");
+  if (opts && opts->engine != SR_ENGINE_BATCHED) return set_error(SR_EINVAL, "sr_serve_start: serving runs the batched engine");
   auto* sv = new Server;
   sv->s = s;
   cudaGetDevice(&sv->device);
   sv->sp = *sp;
   if (opts) {
     sv->opts = *opts;
+    sv->opts.cuda_stream = nullptr;
   } else {
     sv->opts.want_cigar = 1;
     sv->opts.min_score = 40;
     sv->opts.margin = 5;
   }
   sv->max_inflight = max_inflight_requests;
-  for (auto& st : sv->streams) {
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-      serve_destroy(sv);
-      return set_error(SR_ECUDA, "sr_serve_start: stream creation failed");
-    }
+  bool ok = cudaEventCreate(&sv->t0) == cudaSuccess;
+  for (auto& sl : sv->slots) {
+    ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreate(&sl.first) == cudaSuccess && cudaEventCreate(&sl.last) == cudaSuccess;
+  }
+  // the origin of the round timelines, recorded before any round
+  ok = ok && cudaEventRecord(sv->t0, sv->slots[0].stream) == cudaSuccess &&
+       cudaEventSynchronize(sv->t0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    serve_destroy(sv);
+    return set_error(SR_ECUDA, "sr_serve_start: stream or event creation failed");
   }
   session_server(s) = sv;
-  sv->th = std::thread(scheduler, sv);
+  sv->th_sched = std::thread(scheduler, sv);
+  sv->th_done = std::thread(completer, sv);
   return SR_OK;
 }
 
@@ -338,6 +433,7 @@ extern "C" sr_status sr_submit(sr_session* s, const sr_reads* reads, const sr_ca
   auto* q = new Request;
   q->roff.assign(reads->offsets, reads->offsets + n + 1);
   q->coff.assign(cands->offsets, cands->offsets + n + 1);
+  q->n_reads = n;
   if (n == 0) {
     q->roff.assign(1, 0);
     q->coff.assign(1, 0);
@@ -404,6 +500,15 @@ extern "C" sr_status sr_wait(sr_session* s, uint64_t ticket, int32_t timeout_ms,
   return SR_OK;
 }
 
+namespace {
+double percentile(std::vector<double>& v, double p) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const size_t k = static_cast<size_t>(p * (v.size() - 1) + 0.5);
+  return v[std::min(k, v.size() - 1)];
+}
+}  // namespace
+
 extern "C" sr_status sr_serve_stats(sr_session* s, double* p50_us, double* p99_us, uint64_t* completed,
                                     uint64_t* rounds, uint64_t* max_round_requests) {
   if (!s) return set_error(SR_EINVAL, "sr_serve_stats: null session");
@@ -416,14 +521,65 @@ extern "C" sr_status sr_serve_stats(sr_session* s, double* p50_us, double* p99_u
     if (rounds) *rounds = sv->rounds;
     if (max_round_requests) *max_round_requests = sv->max_round;
   }
-  std::sort(v.begin(), v.end());
-  auto pct = [&](double p) {
-    if (v.empty()) return 0.0;
-    size_t k = static_cast<size_t>(p * (v.size() - 1) + 0.5);
-    return v[std::min(k, v.size() - 1)];
-  };
-  if (p50_us) *p50_us = pct(0.50);
-  if (p99_us) *p99_us = pct(0.99);
   if (completed) *completed = v.size();
+  const double p50 = percentile(v, 0.50), p99 = percentile(v, 0.99);
+  if (p50_us) *p50_us = p50;
+  if (p99_us) *p99_us = p99;
+  return SR_OK;
+}
+
+extern "C" sr_status sr_serve_stats_by_size(sr_session* s, uint32_t n_buckets, const uint32_t* max_reads,
+                                            double* p50_us, double* p99_us, uint64_t* count) {
+  if (!s || (n_buckets && !max_reads)) return set_error(SR_EINVAL, "sr_serve_stats_by_size: null argument");
+  for (uint32_t k = 1; k < n_buckets; ++k)
+    if (max_reads[k] <= max_reads[k - 1]) return set_error(SR_EINVAL, "sr_serve_stats_by_size: bucket bounds must increase");
+  Server* sv = session_server(s);
+  if (!sv) return set_error(SR_EINVAL, "sr_serve_stats_by_size: not serving");
+  std::vector<double> lat;
+  std::vector<uint32_t> sz;
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    lat = sv->lat_us;
+    sz = sv->lat_reads;
+  }
+  for (uint32_t k = 0; k < n_buckets; ++k) {
+    std::vector<double> v;
+    const uint32_t lo = k ? max_reads[k - 1] : 0;
+    for (size_t i = 0; i < lat.size(); ++i)
+      if ((k == 0 || sz[i] > lo) && sz[i] <= max_reads[k]) v.push_back(lat[i]);
+    if (count) count[k] = v.size();
+    const double p50 = percentile(v, 0.50), p99 = percentile(v, 0.99);
+    if (p50_us) p50_us[k] = p50;
+    if (p99_us) p99_us[k] = p99;
+  }
+  return SR_OK;
+}
+
+extern "C" sr_status sr_serve_overlap(sr_session* s, uint64_t* timed_rounds, uint64_t* overlapped,
+                                      double* device_idle_ms, uint64_t* budget_waits, uint32_t cap,
+                                      float* first_ms, float* last_ms) {
+  if (!s || (cap && (!first_ms || !last_ms))) return set_error(SR_EINVAL, "sr_serve_overlap: null argument");
+  Server* sv = session_server(s);
+  if (!sv) return set_error(SR_EINVAL, "sr_serve_overlap: not serving");
+  std::vector<std::pair<float, float>> t;
+  {
+    std::lock_guard<std::mutex> g(sv->mu);
+    t = sv->timeline;
+    if (budget_waits) *budget_waits = sv->budget_waits;
+  }
+  uint64_t ov = 0;
+  double idle = 0;
+  for (size_t k = 1; k < t.size(); ++k) {
+    if (t[k].first < t[k - 1].second) ++ov;
+    else idle += t[k].first - t[k - 1].second;
+  }
+  if (timed_rounds) *timed_rounds = t.size();
+  if (overlapped) *overlapped = ov;
+  if (device_idle_ms) *device_idle_ms = idle;
+  const size_t n = std::min<size_t>(cap, t.size());
+  for (size_t k = 0; k < n; ++k) {
+    first_ms[k] = t[k].first;
+    last_ms[k] = t[k].second;
+  }
   return SR_OK;
 }

@@ -20,6 +20,12 @@ sr_status batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_ca
 // the shortest read length whose windows the int32 kernel scores under these
 // parameters (0: every window; SR_MAX_READ_LEN + 1: none)
 uint32_t i32_min_read_len(const sr_score_params& sp, const sr_align_opts& o);
+// a serving round: every kernel of the path plus the result records, launched
+// directly on the batch's stream; ev_first is recorded once the first kernel is
+// done, and the extension kernels (and all after them) wait for wait_extend
+// (either may be null)
+sr_status batch_run_serving(sr_session* s, sr_batch* b, const sr_score_params* sp, const sr_align_opts* opts,
+                            cudaEvent_t ev_first, cudaEvent_t wait_extend);
 sr_status batch_stage_range(sr_session* s, const sr_reads* reads, const sr_cand_list* cands, uint32_t r0,
                             uint32_t r1, void* stream, bool check_budget, sr_batch** out);
 }  // namespace sr

@@ -171,6 +171,7 @@ struct sr_batch {
   uint64_t kernels = 0;
   uint64_t i32_items = 0;
   bool ran = false;
+  bool assembled = false;  // the last run also assembled the result records (serving rounds)
   sr_align_opts last_opts{};
   BatchRes res{};  // events, side streams (from the session's pool)
   bool res_ok = false;
@@ -774,9 +775,14 @@ extern "C" void sr_batch_free(sr_batch* b) {
 
 namespace sr {
 
-// enqueue every kernel of the path for one batch; returns kernels launched or -1
+// enqueue every kernel of the path for one batch; returns kernels launched or -1.
+// Serving rounds pass ev_first (recorded once the first kernel is done),
+// wait_extend (the extension kernels and everything after them wait for it:
+// the previous round's last kernel) and assemble (the result records are built
+// at the end, so fetching them needs copies only).
 static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& o,
-                   const TuneBin* bins, cudaStream_t st) {
+                   const TuneBin* bins, cudaStream_t st, cudaEvent_t ev_first = nullptr,
+                   cudaEvent_t wait_extend = nullptr, bool assemble = false) {
   const BatchDev& d = b->d;
   const ScoreConst sc{sp.match, sp.mismatch, sp.gap_open, sp.gap_extend};
   const bool plain = o.engine == SR_ENGINE_PLAIN;
@@ -790,6 +796,7 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
   if (cudaMemsetAsync(d.status, 0, 4, st) != cudaSuccess) return -1;
   if ((t = launch_prepare(d, b->s->refs, st)) < 0) return -1;
   k += t;
+  if (ev_first && cudaEventRecord(ev_first, st) != cudaSuccess) return -1;
   // windows per length class (as launch_bins will route them): empty classes launch nothing
   uint64_t class_items[kNumClasses] = {};
   {
@@ -810,6 +817,7 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
   if (b->n_items) {
     if ((t = launch_bins(d, sc, bins, kNumBins, o.force_i32 != 0, plain, st)) < 0) return -1;
     k += t;
+    if (wait_extend && cudaStreamWaitEvent(st, wait_extend, 0) != cudaSuccess) return -1;
     if (!mark(2)) return -1;
     if ((t = launch_extend(d, b->s->refs, sc, bins, kNumBins, static_cast<int>(o.mode), plain, o.lanes,
                            o.rows, st, class_items, &b->res.fan[0])) < 0)
@@ -817,6 +825,7 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
     if (!mark(3)) return -1;
     k += t;
   } else {
+    if (wait_extend && cudaStreamWaitEvent(st, wait_extend, 0) != cudaSuccess) return -1;
     if (!mark(2) || !mark(3)) return -1;
   }
   if ((t = launch_select(d, nr, st)) < 0) return -1;
@@ -841,6 +850,10 @@ static int enqueue(sr_batch* b, const sr_score_params& sp, const sr_align_opts& 
     k += t;
   }
   if (!mark(1)) return -1;
+  if (assemble) {
+    if ((t = launch_assemble(d, nr, o.want_cigar != 0, 0, 0, st)) < 0) return -1;
+    k += t;
+  }
   return k;
 }
 
@@ -860,12 +873,13 @@ uint32_t i32_min_read_len(const sr_score_params& sp, const sr_align_opts& o) {
   return kMaxReadLen + 1;
 }
 
-sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp, const sr_align_opts* opts) {
-  Trace trace_("sr_batch_run");
+// checks a run's arguments against the batch; o receives the options to use
+static sr_status run_args(sr_session* s, sr_batch* b, const sr_score_params* sp, const sr_align_opts* opts,
+                          sr_align_opts& o) {
   if (!s || !b || b->s != s) return set_error(SR_EINVAL, "sr_batch_run: bad session/batch");
   sr_status st = check_score(sp);
   if (st != SR_OK) return st;
-  sr_align_opts o = opts ? *opts : default_opts();
+  o = opts ? *opts : default_opts();
   if (o.mode > 1 || o.engine > 1) return set_error(SR_EINVAL, "sr_batch_run: bad mode/engine");
   if ((o.lanes || o.rows) && !extend_config_supported(o.lanes, o.rows))
     return set_error(SR_EINVAL, "sr_batch_run: unsupported lanes x rows shape");
@@ -879,15 +893,44 @@ sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp,
   if (o.engine == SR_ENGINE_PLAIN &&
       (!i16_tables || o.force_i32 || static_cast<int64_t>(sp->match) * b->max_m > 32767 - kBias))
     return set_error(SR_EINVAL, "sr_batch_run: the plain engine runs the int16 kernel only; use the batched engine");
+  return SR_OK;
+}
+
+static void count_i32_items(sr_batch* b, const sr_score_params& sp, const sr_align_opts& o) {
+  uint64_t n32 = 0;
+  for (uint32_t m = i32_min_read_len(sp, o); m <= static_cast<uint32_t>(kMaxReadLen); ++m) n32 += b->items_by_len[m];
+  b->i32_items = n32;
+}
+
+sr_status batch_run_serving(sr_session* s, sr_batch* b, const sr_score_params* sp, const sr_align_opts* opts,
+                            cudaEvent_t ev_first, cudaEvent_t wait_extend) {
+  Trace trace_("sr_batch_run serving");
+  sr_align_opts o;
+  sr_status st = run_args(s, b, sp, opts, o);
+  if (st != SR_OK) return st;
+  if (o.engine != SR_ENGINE_BATCHED) return set_error(SR_EINVAL, "serving runs the batched engine");
   cudaStream_t stream = o.cuda_stream ? static_cast<cudaStream_t>(o.cuda_stream) : b->stream;
   TuneBin bins[kNumBins];
   tune_get_bins(bins);
-  {
-    uint64_t n32 = 0;
-    for (uint32_t m = i32_min_read_len(*sp, o); m <= static_cast<uint32_t>(kMaxReadLen); ++m)
-      n32 += b->items_by_len[m];
-    b->i32_items = n32;
-  }
+  count_i32_items(b, *sp, o);
+  const int k = enqueue(b, *sp, o, bins, stream, ev_first, wait_extend, true);
+  if (k < 0) return cuda_error("serving round launch", cudaGetLastError());
+  b->kernels = static_cast<uint64_t>(k);
+  b->ran = true;
+  b->assembled = true;
+  b->last_opts = o;
+  return SR_OK;
+}
+
+sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp, const sr_align_opts* opts) {
+  Trace trace_("sr_batch_run");
+  sr_align_opts o;
+  sr_status st = run_args(s, b, sp, opts, o);
+  if (st != SR_OK) return st;
+  cudaStream_t stream = o.cuda_stream ? static_cast<cudaStream_t>(o.cuda_stream) : b->stream;
+  TuneBin bins[kNumBins];
+  tune_get_bins(bins);
+  count_i32_items(b, *sp, o);
   const bool plain = o.engine == SR_ENGINE_PLAIN;
   if (plain) {
     const int k = enqueue(b, *sp, o, bins, stream);
@@ -933,6 +976,7 @@ sr_status batch_run_async(sr_session* s, sr_batch* b, const sr_score_params* sp,
     if (e != cudaSuccess) return cuda_error("sr_batch_run graph launch", e);
   }
   b->ran = true;
+  b->assembled = false;
   b->last_opts = o;
   return SR_OK;
 }
@@ -1097,7 +1141,7 @@ extern "C" sr_status sr_batch_fetch(sr_session* s, sr_batch* b, sr_results** out
   // comes back with one copy each on the batch's stream and a single wait
   const bool cig = b->last_opts.want_cigar != 0;
   const bool cls = b->last_opts.classify != 0;
-  if (launch_assemble(b->d, static_cast<int>(nr), cig, 0, 0, stream) < 0) {
+  if (!b->assembled && launch_assemble(b->d, static_cast<int>(nr), cig, 0, 0, stream) < 0) {
     sr_results_free(r);
     return cuda_error("sr_batch_fetch assemble", cudaGetLastError());
   }

@@ -156,6 +156,8 @@ def lib():
             "sr_submit": ([P, C.POINTER(Reads), C.POINTER(CandList), C.POINTER(C.c_uint64)], C.c_int32),
             "sr_wait": ([P, C.c_uint64, C.c_int32, C.POINTER(C.POINTER(Results))], C.c_int32),
             "sr_serve_stats": ([P, P, P, P, P, P], C.c_int32),
+            "sr_serve_stats_by_size": ([P, C.c_uint32, P, P, P, P], C.c_int32),
+            "sr_serve_overlap": ([P, P, P, P, P, C.c_uint32, P, P], C.c_int32),
             "sr_serve_stop": ([P], C.c_int32),
             "sr_tune": ([P, C.POINTER(ScoreParams), C.c_uint32], C.c_int32),
             "sr_tune_save": ([C.c_char_p], C.c_int32),
@@ -521,6 +523,29 @@ class Session:
                                     C.byref(mx)))
         return dict(p50_us=p50.value, p99_us=p99.value, completed=n.value, rounds=rounds.value,
                     max_round_requests=mx.value)
+
+    def serve_stats_by_size(self, max_reads=(256, 1024, 2048, 4096)):
+        """p50/p99 latency (us) and count per request-size bucket: bucket k holds
+        requests of max_reads[k-1] + 1 .. max_reads[k] reads."""
+        b = np.ascontiguousarray(max_reads, np.uint32)
+        p50, p99 = np.zeros(len(b)), np.zeros(len(b))
+        cnt = np.zeros(len(b), np.uint64)
+        _check(lib().sr_serve_stats_by_size(self.h, len(b), _p(b), _p(p50), _p(p99), _p(cnt)))
+        return [dict(max_reads=int(b[k]), count=int(cnt[k]), p50_us=float(p50[k]), p99_us=float(p99[k]))
+                for k in range(len(b))]
+
+    def serve_overlap(self, cap=0):
+        """Device timeline of completed rounds (first kernel done, last kernel
+        done; ms after serve_start), rounds that overlapped the previous one,
+        idle time between the others and the admissions the budget deferred."""
+        n, ov, bw = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        idle = C.c_double()
+        first, last = np.zeros(max(cap, 1), np.float32), np.zeros(max(cap, 1), np.float32)
+        _check(lib().sr_serve_overlap(self.h, C.byref(n), C.byref(ov), C.byref(idle), C.byref(bw), cap,
+                                      _p(first) if cap else None, _p(last) if cap else None))
+        k = min(cap, n.value)
+        return dict(timed_rounds=n.value, overlapped=ov.value, device_idle_ms=idle.value, budget_waits=bw.value,
+                    first_ms=first[:k], last_ms=last[:k])
 
     def serve_stop(self):
         _check(lib().sr_serve_stop(self.h))

@@ -148,3 +148,39 @@ def test_backlog_drains_in_bounded_rounds(env):
     assert st["completed"] == len(reqs)
     assert st["rounds"] >= 2
     assert st["max_round_requests"] <= 6  # at most 131072 reads: six requests of 20k
+
+
+def test_next_round_starts_before_the_previous_one_ends(env):
+    """Rounds overlap on the device: with requests arriving while others run,
+    the CUDA events the server records on each round's stream show round k+1's
+    first kernel finishing before round k's last kernel, and every request's
+    results are still those it gets alone."""
+    sr, refs, _ = env
+    reqs = [request_of(refs, 3000, 300 + i) for i in range(12)]
+    s = sr.Session.open([bytes(r) for r in refs], hbm_budget=8 << 30)
+    alone = [s.align(*[q[k] for k in KEYS], sr.score_params(), sr.align_opts()) for q in reqs]
+    s.serve_start(sr.score_params(), sr.align_opts(), max_inflight=0)
+    tickets = []
+    for rep in range(4):
+        for q in reqs:
+            tickets.append(s.submit(*[q[k] for k in KEYS]))
+            time.sleep(0.0005)
+    served = [s.wait(t, timeout_ms=120_000) for t in tickets]
+    ov = s.serve_overlap(cap=4096)
+    st = s.serve_stats()
+    by_size = s.serve_stats_by_size([2048, 4096])
+    s.serve_stop()
+    for i, b in enumerate(served):
+        a = alone[i % len(reqs)]
+        for k in ["item_score", "item_end", "cigar"]:
+            assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(a["best"], b["best"])
+    n = ov["timed_rounds"]
+    assert n == st["rounds"] and n >= 2, (ov, st)
+    first, last = ov["first_ms"], ov["last_ms"]
+    assert np.all(last >= first)
+    pairs = int(np.sum(first[1:] < last[:-1]))
+    assert pairs == ov["overlapped"] >= 1, (pairs, ov["overlapped"], first[:8], last[:8])
+    # every request has 3000 reads: all fall in the second size bucket
+    assert by_size[0]["count"] == 0 and by_size[1]["count"] == len(tickets)
+    assert by_size[1]["p50_us"] == st["p50_us"] and by_size[1]["p99_us"] == st["p99_us"]

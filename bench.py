@@ -27,8 +27,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = ("c2 batched uneven: 100 Mbp reference (41% GC), 1M reads uniform 75-250 bp with 1% "
-            "substitutions and 0.1% indels, Poisson(6) windows per read capped at 64, each read "
-            "length + 2x32 bp; scores +2/-3, gap 5+2k")
+            "substitutions and 0.1% indels, half of them from the reverse strand, Poisson(6) windows "
+            "per read capped at 64, each read length + 2x32 bp; scores +2/-3, gap 5+2k")
+RC_FRAC = 0.5  # reads drawn from the reverse strand (aligned through their '-' windows)
+ENGINE = "batched (length bins, LPT persistent kernels, one CUDA graph)"
 SP = (2, 3, 5, 2)
 METRIC = "SW GCUPS (whole path: pack, bins, extension, select, traceback)"
 OPS_PER_CELL = 3  # packed 16-bit ops per cell of the score-only recurrence (6 per s16x2 pair)
@@ -51,10 +53,14 @@ def parse():
     ap.add_argument("--serve-budget-mb", type=int, default=1024,
                     help="HBM budget of the serving session (admission binds at high load)")
     ap.add_argument("--no-cal", action="store_true", help="skip the CAL finder comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the xenograft and repeat-heavy workloads (full size by default)")
     ap.add_argument("--sweep", action="store_true",
                     help="seed length x CAL limit sweep on the xenograft and repeat-heavy workloads "
                          "(one JSON line per setting) instead of the bench line")
-    ap.add_argument("--sweep-scale", type=float, default=0.25)
+    ap.add_argument("--sweep-scale", type=float, default=1.0)
+    ap.add_argument("--sweep-seconds", type=float, default=900.0,
+                    help="wall budget of the sweep: settings not started by then are skipped")
     return ap.parse_args()
 
 
@@ -327,13 +333,26 @@ def sweep(args):
     true locus)."""
     from paper_1805_00106_gb300 import sr, synth
     spp = sr.score_params(*SP)
+    t_start = time.perf_counter()
+
+    def over_budget(what):
+        if time.perf_counter() - t_start <= args.sweep_seconds:
+            return False
+        print(json.dumps({"sweep": "skipped (wall budget)", "setting": what,
+                          "budget_s": args.sweep_seconds}), flush=True)
+        return True
+
     for name in ["c3", "c5"]:
-        w = synth.workload(name, scale=args.sweep_scale, seed=11)
+        w = synth.workload(name, scale=args.sweep_scale, seed=11, rc_frac=RC_FRAC)
         n = len(w["read_off"]) - 1
         truth_end = np.asarray(w["t_pos"], np.int64) + np.asarray(w["t_span"], np.int64) - 1
         for k in (20, 25):
             for limit in (0, 1024, 128):
+                if over_budget(f"{name} k={k} limit={limit or 'inf'}"):
+                    continue
+                t0 = time.perf_counter()
                 idx = [sr.Index.build(bytes(r), seed_len=k, address_bases=12, cal_limit=limit) for r in w["refs"]]
+                t_index = time.perf_counter() - t0
                 sess = sr.Session.from_indexes(idx)
                 sess.attach_index(idx)
                 opts = sr.align_opts(classify=name == "c3", min_score=40, margin=5)
@@ -349,7 +368,8 @@ def sweep(args):
                         "reads": n, "ref_mbp": [round(len(r) / 1e6, 1) for r in w["refs"]],
                         "seed_len": k, "cal_limit": limit or "inf",
                         "windows_per_read": round(len(cd["c_ref"]) / n, 3),
-                        "reads_per_s": round(n / t, 1), "ms": round(1e3 * t, 2)}
+                        "reads_per_s": round(n / t, 1), "ms": round(1e3 * t, 2),
+                        "index_build_s": round(t_index, 1)}
                 if name == "c3":
                     cls = res["read_class"]
                     exp = np.where(np.asarray(w["t_ref"]) == 0, 1, 2)
@@ -368,6 +388,8 @@ def sweep(args):
     n = len(w["read_off"]) - 1
     m = np.diff(np.asarray(w["read_off"], np.int64))
     for with_junctions in (False, True):
+        if over_budget(f"splicing junctions={with_junctions}"):
+            continue
         refs = [w["genome"]] + ([w["junctions"]] if with_junctions else [])
         idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=12, cal_limit=1024) for r in refs]
         sess = sr.Session.from_indexes(idx)
@@ -395,7 +417,120 @@ def sweep(args):
 
 def make_workload(scale, rank):
     from paper_1805_00106_gb300 import synth
-    return synth.workload("c2", scale=scale, seed=rank * 1009)
+    return synth.workload("c2", scale=scale, seed=rank * 1009, rc_frac=RC_FRAC)
+
+
+def bench_config(w, scale):
+    """The workload as both arms name it (the engine each arm runs is a key of its own)."""
+    ro = np.asarray(w["read_off"], np.int64)
+    co = np.asarray(w["cand_off"], np.int64)
+    m = np.diff(ro)
+    cells = float(np.sum(np.repeat(m, np.diff(co)) * np.asarray(w["c_len"], np.int64)))
+    return {"workload": WORKLOAD, "reads": len(ro) - 1, "windows": int(co[-1]), "cells": cells,
+            "l2": "inputs larger than L2 (no flush)", "scale": scale}
+
+
+def _timed_runs(batch, spp, opts, steps):
+    """Graph replays of a staged batch: per-run device ms (whole path, extension,
+    traceback) from the library's events."""
+    for _ in range(2):
+        batch.run(spp, opts)
+    tt = []
+    for _ in range(steps):
+        batch.run_async(spp, opts)
+        batch.sync()
+        tt.append(batch.timing())
+    return [statistics.median(x) for x in zip(*tt)]
+
+
+def xenograft_bench(sr, stream, scale=1.0, steps=5):
+    """The xenograft workload at its stated shape: 2M x 100 bp reads (70% from
+    reference A, 30% from B, both strands) against 2 x 64 Mbp, candidates from
+    the device CAL finder (k = 20, overlapping seeds, CAL limit 1024, merge 32,
+    pad 32), classification by margin 5 / minimum score 40 (Sec. 6.2-6.4).
+    Device GCUPS and reads/s of the whole path (graph replays), the CAL finder's
+    time, CALs per read, and the classes against the simulated origin, next to
+    the paper's Table 2-3 FPGA percentages (real human/mouse RNA-seq; context)."""
+    from paper_1805_00106_gb300 import synth
+    w = synth.workload("c3", scale=scale, seed=0, rc_frac=RC_FRAC)
+    n = len(w["read_off"]) - 1
+    t0 = time.perf_counter()
+    idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=12, cal_limit=1024) for r in w["refs"]]
+    t_index = time.perf_counter() - t0
+    sess = sr.Session.from_indexes(idx)
+    sess.attach_index(idx)
+    prm = dict(seed_stride=1, merge_dist=32, pad=32)
+    cd = sess.candidates(w["bases"], w["read_off"], **prm)
+    t0 = time.perf_counter()
+    cd = sess.candidates(w["bases"], w["read_off"], **prm)
+    t_cal = time.perf_counter() - t0
+    spp = sr.score_params(*SP)
+    opts = sr.align_opts(classify=True, min_score=40, margin=5, stream=stream.cuda_stream)
+    b = sess.stage(w["bases"], w["read_off"], cd["cand_off"], cd["c_ref"], cd["c_strand"], cd["c_start"],
+                   cd["c_len"], stream=stream.cuda_stream)
+    cells = float(b.stats()["cells"])
+    tot, ext, tb = _timed_runs(b, spp, opts, steps)
+    res = b.fetch()
+    cls = res["read_class"]
+    src = np.where(np.asarray(w["t_ref"]) == 0, sr.CLASS_A, sr.CLASS_B)
+    other = np.where(src == sr.CLASS_A, sr.CLASS_B, sr.CLASS_A)
+    cnt = np.diff(np.asarray(cd["cand_off"], np.int64))
+    out = {"workload": f"xenograft: A {len(w['refs'][0]) / 1e6:.0f} Mbp uniform, B = A with 15% substitutions, "
+                       f"2% indels, 50 block moves; {n} reads x 100 bp (70% A / 30% B, half reverse strand, "
+                       "1% errors); device CAL finder k = 20, CAL limit 1024; margin 5, min score 40",
+           "reads": n, "windows": len(cd["c_ref"]), "cells": cells,
+           "gcups": round(cells / tot * 1e3 / 1e9, 1), "reads_per_s": round(n / tot * 1e3, 1),
+           "ms": round(tot, 3), "extension_ms": round(ext, 3), "traceback_ms": round(tb, 3),
+           "cal_finder_ms": round(1e3 * t_cal, 2), "index_build_s": round(t_index, 1),
+           "cals_per_read": round(float(cnt.mean()), 3),
+           "cals_per_read_quantiles": {q: int(np.quantile(cnt, v)) for q, v in
+                                       [("p50", 0.5), ("p90", 0.9), ("p99", 0.99), ("max", 1.0)]},
+           "classes": {"correct": round(float(np.mean(cls == src)), 5),
+                       "incorrect": round(float(np.mean(cls == other)), 5),
+                       "ambiguous": round(float(np.mean(cls == sr.CLASS_AMBIGUOUS)), 5),
+                       "unaligned": round(float(np.mean(cls == sr.CLASS_UNALIGNED)), 5)},
+           "paper_fpga_context": {"table2_without_splicing": {"correct": 0.933, "incorrect": 0.0257,
+                                                              "tie": 0.0332, "unaligned": 0.008},
+                                  "table3_with_splicing": {"correct": 0.954, "incorrect": 0.0072,
+                                                           "tie": 0.0342, "unaligned": 0.0048}}}
+    b.close()
+    sess.close()
+    return out
+
+
+def repeat_bench(sr, stream, scale=1.0, steps=5):
+    """The repeat-heavy workload at its stated shape: 100k x 250 bp reads (both
+    strands) against 200 Mbp with 30% tandem and interspersed repeats, a
+    heavy-tailed Pareto(1.1) count of windows per read capped at 256 (decoys
+    mostly in repeat copies), windows of 250 + 2 x 32 bp."""
+    from paper_1805_00106_gb300 import synth
+    w = synth.workload("c5", scale=scale, seed=0, rc_frac=RC_FRAC)
+    n = len(w["read_off"]) - 1
+    sess = sr.Session.open([bytes(w["refs"][0])])
+    spp = sr.score_params(*SP)
+    opts = sr.align_opts(stream=stream.cuda_stream)
+    b = sess.stage(w["bases"], w["read_off"], w["cand_off"], w["c_ref"], w["c_strand"], w["c_start"],
+                   w["c_len"], stream=stream.cuda_stream)
+    cells = float(b.stats()["cells"])
+    tot, ext, tb = _timed_runs(b, spp, opts, steps)
+    res = b.fetch()
+    truth_end = np.asarray(w["t_pos"], np.int64) + np.asarray(w["t_span"], np.int64) - 1
+    bb = res["best"]
+    ok = (bb["item"] >= 0) & (np.abs(bb["ref_end"].astype(np.int64) - truth_end) <= 20)
+    cnt = np.diff(np.asarray(w["cand_off"], np.int64))
+    out = {"workload": f"repeat-heavy: {len(w['refs'][0]) / 1e6:.0f} Mbp with 30% repeats (unit 2-300 bp, 5% "
+                       f"divergence); {n} reads x 250 bp, half reverse strand; Pareto(1.1) windows per read "
+                       "capped at 256, 314 bp each",
+           "reads": n, "windows": int(cnt.sum()), "cells": cells,
+           "gcups": round(cells / tot * 1e3 / 1e9, 1), "reads_per_s": round(n / tot * 1e3, 1),
+           "ms": round(tot, 3), "extension_ms": round(ext, 3), "traceback_ms": round(tb, 3),
+           "windows_per_read": round(float(cnt.mean()), 3),
+           "windows_per_read_quantiles": {q: int(np.quantile(cnt, v)) for q, v in
+                                          [("p50", 0.5), ("p90", 0.9), ("p99", 0.99), ("max", 1.0)]},
+           "winner_at_true_locus": round(float(np.mean(ok)), 4)}
+    b.close()
+    sess.close()
+    return out
 
 
 def run_reference(args):
@@ -413,18 +548,13 @@ def run_reference(args):
             cells += cb["cells"]
             reads += cb["reads"]
     v = cells / total / 1e9
-    n_items = int(w["cand_off"][-1])
-    full_cells = float(np.sum(np.diff(np.asarray(w["read_off"], np.int64))[
-        np.repeat(np.arange(len(w["read_off"]) - 1), np.diff(np.asarray(w["cand_off"], np.int64)))] *
-        np.asarray(w["c_len"], np.int64)))
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GCUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reads": len(w["read_off"]) - 1, "windows": n_items,
-                       "cells": full_cells, "engine": "oracle (plain C, full matrices) on the host cores",
-                       "l2": "n/a (CPU)", "scale": args.scale,
-                       "sample": "each step a bounded read prefix of this workload (cpu_baseline.sample)"},
+            "config": bench_config(w, args.scale),
+            "engine": "oracle (plain C, full matrices) on the host cores; each step a bounded read prefix "
+                      "of the workload (cpu_baseline.sample)",
             "cpu_baseline": {"value": round(v, 4), "unit": "GCUPS", "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": round(v, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -516,9 +646,7 @@ def main():
             "ms_per_step": round(1e3 * elapsed / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int16x2 (int32 promotion)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reads": n_reads, "windows": n_items, "cells": cells,
-                       "engine": "batched (length bins, LPT persistent kernels, one CUDA graph)",
-                       "l2": "inputs larger than L2 (no flush)", "scale": args.scale},
+            "config": bench_config(w, args.scale), "engine": ENGINE,
             "reads_per_s": round(reads_per_s, 1),
             "gcups_without_traceback": round(cells / (statistics.mean(tot_ms) - statistics.mean(tb_ms)) * 1e3 / 1e9, 3),
             "gpu_launches": int(kernels_per_step * args.steps),
@@ -572,6 +700,9 @@ def main():
         line["serving"] = serving_bench(sr, args.scale, args.serve_seconds, budget_mb=args.serve_budget_mb)
     if rank == 0 and not args.no_cal:
         line["cal_finder"] = cal_finder_bench(sr, args.scale)
+    if rank == 0 and not args.no_extra:
+        line["xenograft"] = xenograft_bench(sr, stream, args.scale)
+        line["repeat_heavy"] = repeat_bench(sr, stream, args.scale)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(w, args.cpu_seconds).items()
                                 if k in ("value", "unit", "cores", "kind", "sample", "one_core")}

@@ -89,10 +89,19 @@ void sr_index_free(sr_index* idx);
 sr_status sr_index_info(const sr_index* idx, uint64_t* ref_len, uint64_t* n_entries);
 
 /* ------------------------------------------------------------------ reads
- * CSR batch of reads: read r is bases[offsets[r] .. offsets[r+1]). */
+ * CSR batch of reads: read r is bases[offsets[r] .. offsets[r+1]).
+ * flags: 0 = host memory; SR_FLAG_DEVICE = bases and offsets are device
+ * pointers on the current device (for example torch tensors' data_ptr()).
+ * Device inputs are accepted by sr_batch_stage and sr_align_batch only (the
+ * other calls that take reads or candidates return SR_EINVAL for them); they
+ * are read on the call's stream (sr_batch_stage's cuda_stream, sr_align_opts
+ * cuda_stream, else the session's stream), so whatever produces them must have
+ * finished or run on that stream.  The library copies them into its own device
+ * buffers and never frees them. */
+enum { SR_FLAG_DEVICE = 1 };
 typedef struct {
   uint32_t n_reads;
-  uint32_t reserved;
+  uint32_t flags;          /* 0 or SR_FLAG_DEVICE */
   const char* bases;
   const uint64_t* offsets; /* n_reads + 1 entries, offsets[0] = 0 */
 } sr_reads;
@@ -118,7 +127,8 @@ typedef struct {
 
 typedef struct {
   uint32_t n_reads;
-  uint32_t reserved;
+  uint32_t flags;     /* 0 or SR_FLAG_DEVICE: offsets, ref_id, strand, win_start and
+                         win_len are device pointers (as for sr_reads) */
   uint64_t n_cands;
   uint64_t* offsets;  /* n_reads + 1: read r owns windows offsets[r] .. offsets[r+1] */
   uint8_t* ref_id;    /* reference index per window */
@@ -224,10 +234,12 @@ sr_status sr_session_attach_index(sr_session* s, const sr_index* const* idx, uin
 sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, const sr_cand_params* params,
                                sr_cand_list** out);
 
-/* Whole batch, host buffers in and out: stage (host->device), run, fetch
- * (device->host).  Errors: SR_EINVAL (shapes, windows past the reference,
- * read or window too long, parameters), SR_EBADBASE, SR_ENOMEM, SR_ECUDA.
- * A call of 2^19 reads or more with opts->cuda_stream NULL (batched engine)
+/* Whole batch: stage (inputs to the device), run, fetch (results to host
+ * buffers).  Inputs are host memory or, flagged SR_FLAG_DEVICE, device memory
+ * (then copied device to device and checked by a kernel, with the same errors).
+ * Errors: SR_EINVAL (shapes, windows past the reference, read or window too
+ * long, parameters), SR_EBADBASE, SR_ENOMEM, SR_ECUDA.
+ * A call of 2^19 reads or more with host inputs and opts->cuda_stream NULL (batched engine)
  * runs as three batches of consecutive reads (1/10, 8/10 and 1/10 of the windows)
  * on three streams of the session, so that staging and fetching overlap the
  * other parts' compute.  The results, errors included, are those of one batch:
@@ -320,14 +332,29 @@ sr_status sr_write_sam(const sr_reads* reads, const sr_results* res, const uint6
  * sr_batch_run.  Any pointer may be NULL. */
 sr_status sr_batch_timing(const sr_batch* b, float* total_ms, float* extend_ms, float* traceback_ms);
 
-/* Re-classify a batch that has run, on the device, with other thresholds
- * (Sec. 6.4); class_out (n_reads bytes, caller-owned) receives SR_CLASS_*. */
+/* Classification of each read between references 0 and 1 (Sec. 6.1, 6.2, 6.4,
+ * Table 2): the reference with the higher best score wins when it leads by at
+ * least `margin`; equal-enough scores are SR_CLASS_AMBIGUOUS (margin 1 = the
+ * paper's exact-tie rule); a read under min_score on one reference counts for
+ * the other; under min_score on both it is SR_CLASS_UNALIGNED.
+ * sr_classify reads res->best_per_ref (n_reads x n_refs records, n_refs >= 2;
+ * the score field of references 0 and 1) and writes n_reads SR_CLASS_* bytes
+ * to class_out (caller-owned).  Either may be host memory (results from
+ * sr_align_batch, sr_batch_fetch or sr_wait; pinned or not) or device memory
+ * (found with cudaPointerGetAttributes); the classes are computed by a kernel
+ * on the current device either way (host records are copied over first, on
+ * the per-thread default stream; the call returns when the classes are in
+ * class_out).  params NULL = defaults.  Errors: SR_EINVAL (fewer than 2
+ * references, null arrays), SR_ECUDA. */
 typedef struct {
   int32_t min_score; /* default 40 */
   int32_t margin;    /* default 5; 1 = the paper's exact-tie rule */
 } sr_classify_params;
-sr_status sr_classify(sr_session* s, sr_batch* b, const sr_classify_params* params,
-                      uint8_t* class_out);
+sr_status sr_classify(const sr_results* res, const sr_classify_params* params, uint8_t* class_out);
+/* The same for a batch that has run, from its device-resident records, with
+ * other thresholds; class_out is host memory (n_reads bytes). */
+sr_status sr_batch_classify(sr_session* s, sr_batch* b, const sr_classify_params* params,
+                            uint8_t* class_out);
 
 /* -------------------------------------------------------------- serving
  * Continuous batching (reads are handed to the aligners as they arrive,
@@ -412,7 +439,8 @@ sr_status sr_tune_set(uint32_t n_bins, const uint32_t* upper, const uint32_t* la
  *  - Scores must fit the packed 16-bit kernel (match + gap_open + 2*gap_extend
  *    small, match * 256 <= 31743); otherwise SR_EINVAL (use sr_align_batch).
  *  - Runs on cuda_stream (NULL = default stream) and returns when the work is
- *    done; bad offsets, reads or windows give SR_EINVAL / SR_EBADBASE.
+ *    done; bad offsets, reads or windows give SR_EINVAL / SR_EBADBASE.  The
+ *    current device must be the one the session was opened on (else SR_EINVAL).
  *  - The first call on a device looks up the scratch array's device address
  *    with that device current; make that first call before any stream capture.
  *  - All calls share the one scratch array: calls whose work overlaps on the

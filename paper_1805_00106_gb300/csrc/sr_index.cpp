@@ -398,6 +398,7 @@ extern "C" sr_status sr_candidates(const sr_index* const* idx, uint32_t n_refs, 
   if (!idx || !reads || !out || n_refs == 0 || n_refs > SR_MAX_REFS)
     return set_error(SR_EINVAL, "sr_candidates: bad arguments");
   *out = nullptr;
+  if (reads->flags) return set_error(SR_EINVAL, "sr_candidates: reads must be in host memory (flags 0)");
   for (uint32_t r = 0; r < n_refs; ++r) {
     if (!idx[r]) return set_error(SR_EINVAL, "sr_candidates: null index");
     if (idx[r]->p.seed_len != idx[0]->p.seed_len || idx[r]->p.address_bases != idx[0]->p.address_bases)

@@ -102,6 +102,7 @@ struct BatchDev {
   uint32_t* scan_tmp = nullptr;   // block sums for scans
   sr_hit* out_best = nullptr;     // n_reads: results in the public layout (fetch)
   sr_hit* out_per_ref = nullptr;  // n_reads * n_refs
+  void* check = nullptr;          // staging checks of device inputs (a StageCheck)
 };
 
 // traceback routing.  A winner's end row i* is searched inside the band
@@ -111,7 +112,11 @@ struct BatchDev {
 enum : uint8_t { kTbFlagBand = 0, kTbFlagFull = 1, kTbFlagRow = 2 };
 constexpr int kTbBuckets = 8;                        // band <= 1 / 2 / 4 / 8 / 16 / 32 / 64 diagonals, full
 constexpr int kTbCodes = kTbBuckets * kMaxReadLen;   // code = bucket * 256 + (256 - last row)
-constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + 8;
+// sub-ranges of the packed-wavefront buckets (bands 9-16 and 17-32) by the rows
+// their reads' DP runs: over 192, 129-192, up to 128 (kernels sized for each)
+constexpr int kTbRowClasses = 3;
+constexpr int kTbSplitWords = 2 * 2 * kTbRowClasses;
+constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + kTbSplitWords + 8;
 constexpr int kTbMaxBand = 64;
 // warps of the one-thread-per-read narrow-band traceback (each owns a scratch
 // of 256 rows x 32 lanes of direction words): 152 SMs x 32, its register-bound
@@ -214,6 +219,19 @@ int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st);
 // adds item_base to its window indexes and cigar_base to its CIGAR offsets
 int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, int32_t item_base, uint32_t cigar_base,
                     cudaStream_t st);
+// checks of a batch whose inputs were staged from device memory
+struct StageCheck {
+  unsigned long long cells;
+  unsigned long long bad;      // (read << 3) | reason of the first bad read, ~0 if none
+                               // (1 offsets, 2 read length, 3 window count, 4 a window)
+  unsigned long long bad_win;  // the first bad window of that read (reason 4), ~0 if none
+  uint32_t max_m;
+  uint32_t pad;
+  unsigned long long by_len[kMaxReadLen + 1];  // windows per read length
+};
+int launch_stage_check(const BatchDev& b, const DevRefs& refs, StageCheck* out, cudaStream_t st);
+int launch_first_bad_window(const BatchDev& b, const DevRefs& refs, uint32_t read, StageCheck* out,
+                            cudaStream_t st);
 // off[0..n) -= base
 int launch_rebase_offsets(uint64_t* off, uint64_t n, uint64_t base, cudaStream_t st);
 // exclusive scan of n counts into out[0..n] (out[n] = total) with a scratch of
@@ -260,6 +278,10 @@ int launch_report_write(const BatchDev& b, int n_refs, int kind, uint32_t n_best
                         sr_report_hit* out, cudaStream_t st);
 int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,
                     cudaStream_t st);
+// the same on public records in device memory: per_ref holds n_reads * n_refs
+// sr_hit (n_refs >= 2), classes of references 0 and 1 into out[n_reads]
+int launch_classify_hits(const sr_hit* per_ref, uint32_t n_reads, uint32_t n_refs, int32_t min_score,
+                         int32_t margin, uint8_t* out, cudaStream_t st);
 bool extend_config_supported(uint32_t lanes, uint32_t rows);
 // the built (lanes, rows) shapes; returns how many there are
 int extend_shapes(uint32_t* lanes, uint32_t* rows, int cap);

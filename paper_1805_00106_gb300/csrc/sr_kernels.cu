@@ -342,13 +342,17 @@ __global__ void k_wrange(const uint32_t* wcount, uint32_t* wrange) {
   wrange[2 * c + 1] = c == 0 ? wcount[0] : 0u;
 }
 
-__global__ void k_classify(uint32_t n_reads, int n_refs, const DevHit* hits, int32_t min_score,
-                           int32_t margin, uint8_t* cls) {
+// Classification of each read between references 0 and 1 (Sec. 6.1-6.4): the
+// higher score wins by at least `margin`; a read under min_score on one
+// reference counts for the other; under min_score on both it is unaligned.
+// Scores are read with a stride (in 32-bit words) so that both the device hit
+// slots and the public sr_hit records can be classified in place.
+__global__ void k_classify(uint32_t n_reads, const int32_t* score_a, const int32_t* score_b, uint64_t stride,
+                           int32_t min_score, int32_t margin, uint8_t* cls) {
   const uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   if (r >= n_reads) return;
-  const int slots = 1 + n_refs;
-  const int32_t a = n_refs > 0 ? hits[r * slots + 1].score : 0;
-  const int32_t b = n_refs > 1 ? hits[r * slots + 2].score : 0;
+  const int32_t a = score_a ? score_a[r * stride] : 0;
+  const int32_t b = score_b ? score_b[r * stride] : 0;
   uint8_t c;
   if (max(a, b) < min_score) c = 0;
   else if (b < min_score) c = 1;
@@ -544,6 +548,84 @@ int launch_assemble(const BatchDev& b, int n_refs, bool want_cigar, int32_t item
 
 // A batch staged from a read range [r0, r1) of the caller's arrays receives
 // the range's offsets as they are; they are made batch-relative here.
+// ---- checks of a batch staged from device memory (the host path runs the same
+// checks on the caller's host arrays): per read, its offsets, length, window
+// count and windows; the first bad read (lowest index) with the reason, and for
+// good batches the DP cells, the longest read and the windows per read length.
+__global__ void k_stage_check(const uint64_t* read_off, const uint64_t* cand_off, uint32_t n, uint64_t nc,
+                              const uint8_t* c_ref, const uint8_t* c_strand, const uint64_t* c_start,
+                              const uint32_t* c_len, DevRefs refs, StageCheck* out) {
+  __shared__ uint32_t hist[kMaxReadLen + 1];
+  __shared__ unsigned long long cells_sh;
+  for (int k = threadIdx.x; k <= kMaxReadLen; k += blockDim.x) hist[k] = 0;
+  if (threadIdx.x == 0) cells_sh = 0;
+  __syncthreads();
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long cells = 0;
+  if (r < n) {
+    const uint64_t a0 = read_off[r], a1 = read_off[r + 1], c0 = cand_off[r], c1 = cand_off[r + 1];
+    uint32_t why = 0;
+    if (a1 < a0 || c1 < c0 || c1 > nc) why = 1;
+    else if (a1 - a0 == 0 || a1 - a0 > static_cast<uint64_t>(kMaxReadLen)) why = 2;
+    else if (c1 - c0 >= (1ull << 19)) why = 3;
+    if (!why) {
+      const uint64_t m = a1 - a0;
+      uint64_t suml = 0;
+      for (uint64_t k = c0; k < c1; ++k) {
+        const uint32_t ref = c_ref[k], len = c_len[k];
+        const uint64_t w0 = c_start[k];
+        const bool ok = ref < static_cast<uint32_t>(refs.n) && c_strand[k] <= 1 && len >= 1 &&
+                        len <= static_cast<uint32_t>(kMaxWinLen) && w0 <= refs.len[ref] && w0 + len <= refs.len[ref];
+        if (!ok) {
+          why = 4;
+          break;
+        }
+        suml += len;
+      }
+      if (!why) {
+        cells = m * suml;
+        if (c1 > c0) atomicAdd(&hist[m], static_cast<uint32_t>(c1 - c0));
+        atomicMax(&out->max_m, static_cast<uint32_t>(m));
+      }
+    }
+    if (why) atomicMin(&out->bad, (static_cast<unsigned long long>(r) << 3) | why);
+  }
+  for (int o = 16; o; o >>= 1) cells += __shfl_xor_sync(0xffffffffu, cells, o);
+  if ((threadIdx.x & 31) == 0 && cells) atomicAdd(&cells_sh, cells);
+  __syncthreads();
+  for (int k = threadIdx.x; k <= kMaxReadLen; k += blockDim.x)
+    if (hist[k]) atomicAdd(&out->by_len[k], static_cast<unsigned long long>(hist[k]));
+  if (threadIdx.x == 0 && cells_sh) atomicAdd(&out->cells, cells_sh);
+}
+
+// the first bad window of read r (after k_stage_check found one there)
+__global__ void k_first_bad_window(uint32_t r, const uint64_t* cand_off, const uint8_t* c_ref, const uint8_t* c_strand,
+                                   const uint64_t* c_start, const uint32_t* c_len, DevRefs refs, StageCheck* out) {
+  const uint64_t c0 = cand_off[r], c1 = cand_off[r + 1];
+  for (uint64_t k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
+    const uint32_t ref = c_ref[k], len = c_len[k];
+    const uint64_t w0 = c_start[k];
+    const bool ok = ref < static_cast<uint32_t>(refs.n) && c_strand[k] <= 1 && len >= 1 &&
+                    len <= static_cast<uint32_t>(kMaxWinLen) && w0 <= refs.len[ref] && w0 + len <= refs.len[ref];
+    if (!ok) atomicMin(&out->bad_win, static_cast<unsigned long long>(k));
+  }
+}
+
+int launch_stage_check(const BatchDev& b, const DevRefs& refs, StageCheck* out, cudaStream_t st) {
+  if (cudaMemsetAsync(out, 0, sizeof(StageCheck), st) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(&out->bad, 0xff, 2 * sizeof(unsigned long long), st) != cudaSuccess) return -1;
+  if (b.n_reads == 0) return 0;
+  k_stage_check<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.read_off, b.cand_off, b.n_reads, b.n_items, b.c_ref,
+                                                         b.c_strand, b.c_start, b.c_len, refs, out);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_first_bad_window(const BatchDev& b, const DevRefs& refs, uint32_t read, StageCheck* out,
+                            cudaStream_t st) {
+  k_first_bad_window<<<1, 256, 0, st>>>(read, b.cand_off, b.c_ref, b.c_strand, b.c_start, b.c_len, refs, out);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 __global__ void k_rebase_offsets(uint64_t* off, uint64_t n, uint64_t base) {
   const uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   if (x < n) off[x] -= base;
@@ -558,8 +640,21 @@ int launch_rebase_offsets(uint64_t* off, uint64_t n, uint64_t base, cudaStream_t
 int launch_classify(const BatchDev& b, int n_refs, int32_t min_score, int32_t margin,
                     cudaStream_t st) {
   if (b.n_reads == 0) return 0;
-  k_classify<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, n_refs, b.hits, min_score, margin,
-                                                      b.read_class);
+  static_assert(sizeof(DevHit) % 4 == 0, "hit slots are whole words");
+  const uint64_t stride = (1ull + n_refs) * sizeof(DevHit) / 4;
+  k_classify<<<(b.n_reads + 255) / 256, 256, 0, st>>>(b.n_reads, n_refs > 0 ? &b.hits[1].score : nullptr,
+                                                      n_refs > 1 ? &b.hits[2].score : nullptr, stride, min_score,
+                                                      margin, b.read_class);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_classify_hits(const sr_hit* per_ref, uint32_t n_reads, uint32_t n_refs, int32_t min_score,
+                         int32_t margin, uint8_t* out, cudaStream_t st) {
+  if (n_reads == 0) return 0;
+  static_assert(sizeof(sr_hit) % 4 == 0, "sr_hit records are whole words");
+  const uint64_t stride = static_cast<uint64_t>(n_refs) * sizeof(sr_hit) / 4;
+  k_classify<<<(n_reads + 255) / 256, 256, 0, st>>>(n_reads, &per_ref[0].score, &per_ref[1].score, stride, min_score,
+                                                    margin, out);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -28,6 +28,7 @@
 namespace sr {
 const DevRefs& session_refs(sr_session* s);
 uint32_t session_n_refs(sr_session* s);
+int session_device(sr_session* s);
 sr_status set_error(sr_status st, const char* fmt, ...);
 }  // namespace sr
 
@@ -102,6 +103,10 @@ extern "C" sr_status sr_align_items_noalloc(sr_session* s, const char* d_bases, 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail("device", e);
+  // the session's references live on its device; kernels run on the current one
+  if (dev != session_device(s))
+    return set_error(SR_EINVAL, "sr_align_items_noalloc: current device %d is not the session's device %d", dev,
+                     session_device(s));
   uint32_t* base;
   {
     std::lock_guard<std::mutex> g(g_na_mu);
@@ -165,7 +170,10 @@ extern "C" sr_status sr_align_items_noalloc(sr_session* s, const char* d_bases, 
   TuneBin bins[kNumBins];
   for (int c = 0; c < kNumBins; ++c) bins[c] = TuneBin{kMaxReadLen, 16, 16};
   const ScoreConst sc{sp->match, sp->mismatch, sp->gap_open, sp->gap_extend};
-  if (launch_extend(d, refs, sc, bins, kNumBins, 0, false, 16, 16, st) < 0)
+  // only the first class holds items: one persistent 16 x 16 grid, no int32 grid
+  uint64_t class_items[kNumClasses] = {};
+  class_items[0] = n_items;
+  if (launch_extend(d, refs, sc, bins, kNumBins, 0, false, 16, 16, st, class_items) < 0)
     return cuda_fail("extension", cudaGetLastError());
   e = cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

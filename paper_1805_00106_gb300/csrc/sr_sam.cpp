@@ -133,6 +133,7 @@ extern "C" sr_status sr_write_sam(const sr_reads* reads, const sr_results* res, 
   if (!reads || !res || !path || (res->n_refs && !ref_lens))
     return set_error(SR_EINVAL, "sr_write_sam: null argument");
   if (reads->n_reads != res->n_reads) return set_error(SR_EINVAL, "sr_write_sam: reads and results differ");
+  if (reads->flags) return set_error(SR_EINVAL, "sr_write_sam: reads must be in host memory (flags 0)");
   const uint32_t n = res->n_reads;
   if (n && (!reads->bases || !reads->offsets || !res->best)) return set_error(SR_EINVAL, "sr_write_sam: null arrays");
   for (uint32_t r = 0; r < n; ++r) {

@@ -429,6 +429,7 @@ extern "C" sr_status sr_submit(sr_session* s, const sr_reads* reads, const sr_ca
   if (!sv) return set_error(SR_EINVAL, "sr_submit: call sr_serve_start first");
   const uint32_t n = reads->n_reads;
   if (cands->n_reads != n) return set_error(SR_EINVAL, "sr_submit: reads and candidates differ in n_reads");
+  if (reads->flags || cands->flags) return set_error(SR_EINVAL, "sr_submit: requests are copied from host memory (flags 0)");
   if (n && (!reads->offsets || !reads->bases || !cands->offsets)) return set_error(SR_EINVAL, "sr_submit: null arrays");
   auto* q = new Request;
   q->roff.assign(reads->offsets, reads->offsets + n + 1);

@@ -322,6 +322,7 @@ std::atomic<uint64_t>& session_used(sr_session* s) { return s->hbm_used; }
 Server*& session_server(sr_session* s) { return s->server; }
 uint32_t session_n_refs(sr_session* s) { return s->n_refs; }
 const DevRefs& session_refs(sr_session* s) { return s->refs; }
+int session_device(sr_session* s) { return s->device; }
 }  // namespace sr
 
 // ------------------------------------------------------------------ batches
@@ -349,105 +350,11 @@ void rebase_c(const T*& p, char* base) {
 }  // namespace
 
 namespace sr {
-uint64_t batch_bytes_estimate(uint32_t n_reads, uint64_t n_items, uint64_t n_bases, uint32_t n_refs) {
+namespace {
+// Lays out a batch's arena: every pointer of d becomes an offset from the
+// arena's start; returns the bytes the arena needs.
+uint64_t carve_batch(BatchDev& d, uint32_t n, uint64_t nb, uint64_t nc, uint32_t n_refs) {
   Carve c;
-  char* p1;
-  uint64_t* p8;
-  uint32_t* p4;
-  uint16_t* p2;
-  DevHit* ph;
-  c.take(p1, n_bases);
-  c.take(p8, n_reads + 1ull);
-  c.take(p8, n_reads + 1ull);
-  c.take(p1, n_items);
-  c.take(p1, n_items);
-  c.take(p8, n_items);
-  c.take(p4, n_items);
-  c.take(p4, n_reads * 16ull);
-  c.take(p4, n_reads);
-  c.take(p4, n_items);
-  c.take(p2, n_items);
-  c.take(p4, n_items);
-  c.take(p4, kNumKeys);
-  c.take(p4, kNumKeys);
-  c.take(p4, 2 * kNumClasses);
-  c.take(p4, kNumClasses + 8);
-  c.take(p4, 4);
-  c.take(p4, n_items);
-  c.take(p4, n_items);
-  c.take(ph, static_cast<uint64_t>(n_reads) * (1 + n_refs));
-  c.take(p4, static_cast<uint64_t>(n_reads) * kCigarStride);
-  c.take(p4, n_reads + 1ull);
-  c.take(p4, static_cast<uint64_t>(n_reads) * kCigarStride);
-  c.take(p1, n_reads);
-  c.take(p4, n_reads / 1024 + 4ull);
-  c.take(p4, n_items);
-  c.take(p4, kNumClasses);
-  c.take(p4, 2 * kNumClasses);
-  c.take(p4, kNumClasses + 8);
-  c.take(p1, n_reads);
-  c.take(p4, 4ull * n_reads);
-  c.take(p4, 4);
-  c.take(p4, static_cast<uint64_t>(tb_thread_warps(n_reads)) * kMaxReadLen * 32);
-  return c.off + 256;
-}
-}  // namespace sr
-
-extern "C" sr_status sr_batch_stage(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
-                                    void* cuda_stream, sr_batch** out) {
-  return batch_stage_internal(s, reads, cands, cuda_stream, true, out);
-}
-
-sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
-                                   void* cuda_stream, bool check_budget, sr_batch** out) {
-  return batch_stage_range(s, reads, cands, 0, reads ? reads->n_reads : 0, cuda_stream, check_budget, out);
-}
-
-// Stages reads [r0, r1) of the caller's arrays (and their windows) as one
-// batch: the whole list's header is checked, the range's arrays are copied and
-// its offsets made batch-relative on the device.  Reads and windows named in
-// error messages keep their indexes in the caller's arrays.
-sr_status sr::batch_stage_range(sr_session* s, const sr_reads* reads, const sr_cand_list* cands, uint32_t r0,
-                                uint32_t r1, void* cuda_stream, bool check_budget, sr_batch** out) {
-  Trace trace_("sr_batch_stage");
-  if (!s || !reads || !cands || !out) return set_error(SR_EINVAL, "sr_batch_stage: null argument");
-  *out = nullptr;
-  const uint32_t n_all = reads->n_reads;
-  if (cands->n_reads != n_all) return set_error(SR_EINVAL, "sr_batch_stage: reads and candidates differ in n_reads");
-  if (r0 > r1 || r1 > n_all) return set_error(SR_EINVAL, "sr_batch_stage: bad read range");
-  const uint32_t n = r1 - r0;
-  if (n > (8u << 20)) return set_error(SR_EINVAL, "sr_batch_stage: more than 8M reads in one batch");
-  if (n_all && (!reads->offsets || !reads->bases || !cands->offsets))
-    return set_error(SR_EINVAL, "sr_batch_stage: null arrays");
-  const uint64_t nc_all = n_all ? cands->offsets[n_all] : 0;
-  if (n_all && (reads->offsets[0] != 0 || cands->offsets[0] != 0))
-    return set_error(SR_EINVAL, "sr_batch_stage: offsets must start at 0");
-  if (nc_all != cands->n_cands) return set_error(SR_EINVAL, "sr_batch_stage: n_cands != offsets[n_reads]");
-  if (nc_all >= (1ull << 32)) return set_error(SR_EINVAL, "sr_batch_stage: too many windows");
-  if (nc_all && (!cands->ref_id || !cands->strand || !cands->win_start || !cands->win_len))
-    return set_error(SR_EINVAL, "sr_batch_stage: null candidate arrays");
-  // the range's first base and window, and its sizes
-  const uint64_t rb = n ? reads->offsets[r0] : 0, cb = n ? cands->offsets[r0] : 0;
-  const uint64_t re = n ? reads->offsets[r1] : 0, ce = n ? cands->offsets[r1] : 0;
-  if (re < rb || ce < cb || ce > nc_all)
-    return set_error(SR_EINVAL, "sr_batch_stage: decreasing or out-of-range offsets in reads %u..%u", r0, r1);
-  const uint64_t nb = re - rb;
-  const uint64_t nc = ce - cb;
-  if (nb > static_cast<uint64_t>(n) * SR_MAX_READ_LEN)
-    return set_error(SR_EINVAL, "sr_batch_stage: %llu bases in %u reads: some read is longer than %d",
-                     static_cast<unsigned long long>(nb), n, SR_MAX_READ_LEN);
-  const uint64_t bytes = batch_bytes_estimate(n, nc, nb, s->n_refs);
-  if (check_budget && s->hbm_budget && s->hbm_used.load() + bytes > s->hbm_budget)
-    return set_error(SR_ENOMEM, "sr_batch_stage: batch needs %llu bytes, over the HBM budget",
-                     static_cast<unsigned long long>(bytes));
-  auto* b = new sr_batch;
-  b->s = s;
-  s->live.fetch_add(1);
-  b->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : s->stream;
-  b->n_reads = n;
-  b->n_items = nc;
-  Carve c;
-  BatchDev& d = b->d;
   char* p1;
   c.take(p1, nb);
   d.bases = p1;
@@ -478,7 +385,7 @@ sr_status sr::batch_stage_range(sr_session* s, const sr_reads* reads, const sr_c
   c.take(d.status, 4);
   c.take(d.item_score, nc);
   c.take(d.item_end, nc);
-  c.take(d.hits, static_cast<uint64_t>(n) * (1 + s->n_refs));
+  c.take(d.hits, static_cast<uint64_t>(n) * (1 + n_refs));
   c.take(d.cigar_slots, static_cast<uint64_t>(n) * kCigarStride);
   c.take(d.cigar_off, n + 1ull);
   c.take(d.cigar, static_cast<uint64_t>(n) * kCigarStride);
@@ -493,8 +400,77 @@ sr_status sr::batch_stage_range(sr_session* s, const sr_reads* reads, const sr_c
   c.take(d.tb_count, kTbCountWords);
   c.take(d.tb_dirs, static_cast<uint64_t>(tb_thread_warps(n)) * kMaxReadLen * 32);
   c.take(d.out_best, n);
-  c.take(d.out_per_ref, static_cast<uint64_t>(n) * s->n_refs);
-  b->bytes = c.off + 256;
+  c.take(d.out_per_ref, static_cast<uint64_t>(n) * n_refs);
+  StageCheck* pc;
+  c.take(pc, 1);
+  d.check = pc;
+  return c.off + 256;
+}
+
+void rebase_batch(BatchDev& d, char* base) {
+  rebase_c(d.bases, base);
+  rebase_c(d.read_off, base);
+  rebase_c(d.cand_off, base);
+  rebase_c(d.c_ref, base);
+  rebase_c(d.c_strand, base);
+  rebase_c(d.c_start, base);
+  rebase_c(d.c_len, base);
+  rebase(d.rpack, base);
+  rebase(d.rlen, base);
+  rebase(d.item_read, base);
+  rebase(d.item_key, base);
+  rebase(d.order, base);
+  rebase(d.hist, base);
+  rebase(d.cursor, base);
+  rebase(d.class_range, base);
+  rebase(d.queue, base);
+  rebase(d.status, base);
+  rebase(d.item_score, base);
+  rebase(d.item_end, base);
+  rebase(d.hits, base);
+  rebase(d.cigar_slots, base);
+  rebase(d.cigar_off, base);
+  rebase(d.cigar, base);
+  rebase(d.read_class, base);
+  rebase(d.scan_tmp, base);
+  rebase(d.item_iend, base);
+  rebase(d.wcount, base);
+  rebase(d.wrange, base);
+  rebase(d.wqueue, base);
+  rebase(d.tb_flag, base);
+  rebase(d.tb_list, base);
+  rebase(d.tb_count, base);
+  rebase(d.tb_dirs, base);
+  rebase(d.out_best, base);
+  rebase(d.out_per_ref, base);
+  rebase(d.check, base);
+}
+}  // namespace
+
+uint64_t batch_bytes_estimate(uint32_t n_reads, uint64_t n_items, uint64_t n_bases, uint32_t n_refs) {
+  BatchDev d;
+  return carve_batch(d, n_reads, n_bases, n_items, n_refs);
+}
+}  // namespace sr
+
+namespace {
+// A batch of n reads, nb bases and nc windows on `stream`, its arena taken from
+// the session's kept arenas or allocated, and its events and side streams from
+// the session's pool.  Counts its bytes in the session's hbm_used.
+sr_status batch_alloc(sr_session* s, uint32_t n, uint64_t nb, uint64_t nc, cudaStream_t stream, bool check_budget,
+                      sr_batch** out) {
+  BatchDev d;
+  const uint64_t bytes = carve_batch(d, n, nb, nc, s->n_refs);
+  if (check_budget && s->hbm_budget && s->hbm_used.load() + bytes > s->hbm_budget)
+    return set_error(SR_ENOMEM, "sr_batch_stage: batch needs %llu bytes, over the HBM budget",
+                     static_cast<unsigned long long>(bytes));
+  auto* b = new sr_batch;
+  b->s = s;
+  s->live.fetch_add(1);
+  b->stream = stream;
+  b->n_reads = n;
+  b->n_items = nc;
+  b->bytes = bytes;
   {
     // the smallest kept arena that holds this batch
     std::lock_guard<std::mutex> lk(s->spare_mu);
@@ -533,50 +509,15 @@ sr_status sr::batch_stage_range(sr_session* s, const sr_reads* reads, const sr_c
         sr_batch_free(b);
         cudaGetLastError();
         return set_error(SR_ENOMEM, "sr_batch_stage: device allocation of %llu bytes failed",
-                         static_cast<unsigned long long>(c.off));
+                         static_cast<unsigned long long>(bytes));
       }
     }
     b->arena_bytes = want;
   }
-  cudaError_t e = cudaSuccess;
-  char* base = static_cast<char*>(b->arena);
-  rebase_c(d.bases, base);
-  rebase_c(d.read_off, base);
-  rebase_c(d.cand_off, base);
-  rebase_c(d.c_ref, base);
-  rebase_c(d.c_strand, base);
-  rebase_c(d.c_start, base);
-  rebase_c(d.c_len, base);
-  rebase(d.rpack, base);
-  rebase(d.rlen, base);
-  rebase(d.item_read, base);
-  rebase(d.item_key, base);
-  rebase(d.order, base);
-  rebase(d.hist, base);
-  rebase(d.cursor, base);
-  rebase(d.class_range, base);
-  rebase(d.queue, base);
-  rebase(d.status, base);
-  rebase(d.item_score, base);
-  rebase(d.item_end, base);
-  rebase(d.hits, base);
-  rebase(d.cigar_slots, base);
-  rebase(d.cigar_off, base);
-  rebase(d.cigar, base);
-  rebase(d.read_class, base);
-  rebase(d.scan_tmp, base);
-  rebase(d.item_iend, base);
-  rebase(d.wcount, base);
-  rebase(d.wrange, base);
-  rebase(d.wqueue, base);
-  rebase(d.tb_flag, base);
-  rebase(d.tb_list, base);
-  rebase(d.tb_count, base);
-  rebase(d.tb_dirs, base);
-  rebase(d.out_best, base);
-  rebase(d.out_per_ref, base);
+  rebase_batch(d, static_cast<char*>(b->arena));
   d.n_reads = n;
   d.n_items = nc;
+  b->d = d;
   s->hbm_used += b->bytes;
   {
     std::lock_guard<std::mutex> lk(s->res_mu);
@@ -593,6 +534,152 @@ sr_status sr::batch_stage_range(sr_session* s, const sr_reads* reads, const sr_c
     }
     b->res_ok = true;
   }
+  *out = b;
+  return SR_OK;
+}
+
+// Stages a batch whose reads or candidates (sr_reads / sr_cand_list flags) sit
+// in device memory: the header is read with two small copies, every array is
+// copied into the arena (device to device, or host to device for the other
+// struct) and checked there by a kernel, which also counts the cells and the
+// windows per read length.  Errors name the same read and window as the host
+// checks do.
+sr_status stage_device(sr_session* s, const sr_reads* reads, const sr_cand_list* cands, cudaStream_t st,
+                       bool check_budget, sr_batch** out) {
+  const uint32_t n = reads->n_reads;
+  const bool rdev = (reads->flags & SR_FLAG_DEVICE) != 0, cdev = (cands->flags & SR_FLAG_DEVICE) != 0;
+  if (n > (8u << 20)) return set_error(SR_EINVAL, "sr_batch_stage: more than 8M reads in one batch");
+  if (!reads->offsets || !cands->offsets || (n && !reads->bases))
+    return set_error(SR_EINVAL, "sr_batch_stage: null arrays");
+  // offsets[0] and offsets[n] of both lists
+  uint64_t ends[4] = {};
+  cudaError_t e = cudaSuccess;
+  auto get = [&](uint64_t* dst, const uint64_t* src, bool dev) {
+    if (!dev) *dst = *src;
+    else if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, 8, cudaMemcpyDefault, st);
+  };
+  get(&ends[0], reads->offsets, rdev);
+  get(&ends[1], reads->offsets + n, rdev);
+  get(&ends[2], cands->offsets, cdev);
+  get(&ends[3], cands->offsets + n, cdev);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error("sr_batch_stage offsets", e);
+  if (ends[0] != 0 || ends[2] != 0) return set_error(SR_EINVAL, "sr_batch_stage: offsets must start at 0");
+  const uint64_t nb = ends[1], nc = ends[3];
+  if (nc != cands->n_cands) return set_error(SR_EINVAL, "sr_batch_stage: n_cands != offsets[n_reads]");
+  if (nc >= (1ull << 32)) return set_error(SR_EINVAL, "sr_batch_stage: too many windows");
+  if (nc && (!cands->ref_id || !cands->strand || !cands->win_start || !cands->win_len))
+    return set_error(SR_EINVAL, "sr_batch_stage: null candidate arrays");
+  if (nb > static_cast<uint64_t>(n) * SR_MAX_READ_LEN)
+    return set_error(SR_EINVAL, "sr_batch_stage: %llu bases in %u reads: some read is longer than %d",
+                     static_cast<unsigned long long>(nb), n, SR_MAX_READ_LEN);
+  sr_batch* b = nullptr;
+  sr_status rs = batch_alloc(s, n, nb, nc, st, check_budget, &b);
+  if (rs != SR_OK) return rs;
+  BatchDev& d = b->d;
+  auto copy = [&](const void* dst, const void* src, uint64_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyDefault, st);
+  };
+  copy(d.bases, reads->bases, nb);
+  copy(d.read_off, reads->offsets, (n + 1ull) * 8);
+  copy(d.cand_off, cands->offsets, (n + 1ull) * 8);
+  copy(d.c_ref, cands->ref_id, nc);
+  copy(d.c_strand, cands->strand, nc);
+  copy(d.c_start, cands->win_start, nc * 8);
+  copy(d.c_len, cands->win_len, nc * 4);
+  StageCheck* dc = static_cast<StageCheck*>(d.check);
+  if (e == cudaSuccess && launch_stage_check(d, s->refs, dc, st) < 0) e = cudaGetLastError();
+  StageCheck hc{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, dc, sizeof(hc), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && hc.bad != ~0ull && (hc.bad & 7) == 4) {
+    if (launch_first_bad_window(d, s->refs, static_cast<uint32_t>(hc.bad >> 3), dc, st) < 0) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc.bad_win, &dc->bad_win, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    sr_batch_free(b);
+    return cuda_error("sr_batch_stage copy", e);
+  }
+  if (hc.bad != ~0ull) {
+    sr_batch_free(b);
+    const uint32_t r = static_cast<uint32_t>(hc.bad >> 3);
+    switch (hc.bad & 7) {
+      case 1:
+        return set_error(SR_EINVAL, "sr_batch_stage: decreasing or out-of-range offsets at read %u", r);
+      case 2:
+        return set_error(SR_EINVAL, "sr_batch_stage: read %u has a length outside 1..256", r);
+      case 3:
+        return set_error(SR_EINVAL, "sr_batch_stage: read %u has more than 2^19-1 windows", r);
+      default:
+        return set_error(SR_EINVAL, "sr_batch_stage: window %llu is outside its reference or malformed",
+                         static_cast<unsigned long long>(hc.bad_win));
+    }
+  }
+  b->cells = hc.cells;
+  b->max_m = hc.max_m;
+  for (int m = 0; m <= kMaxReadLen; ++m) b->items_by_len[m] = hc.by_len[m];
+  *out = b;
+  return SR_OK;
+}
+}  // namespace
+
+extern "C" sr_status sr_batch_stage(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                                    void* cuda_stream, sr_batch** out) {
+  return batch_stage_internal(s, reads, cands, cuda_stream, true, out);
+}
+
+sr_status sr::batch_stage_internal(sr_session* s, const sr_reads* reads, const sr_cand_list* cands,
+                                   void* cuda_stream, bool check_budget, sr_batch** out) {
+  return batch_stage_range(s, reads, cands, 0, reads ? reads->n_reads : 0, cuda_stream, check_budget, out);
+}
+
+// Stages reads [r0, r1) of the caller's arrays (and their windows) as one
+// batch: the whole list's header is checked, the range's arrays are copied and
+// its offsets made batch-relative on the device.  Reads and windows named in
+// error messages keep their indexes in the caller's arrays.
+sr_status sr::batch_stage_range(sr_session* s, const sr_reads* reads, const sr_cand_list* cands, uint32_t r0,
+                                uint32_t r1, void* cuda_stream, bool check_budget, sr_batch** out) {
+  Trace trace_("sr_batch_stage");
+  if (!s || !reads || !cands || !out) return set_error(SR_EINVAL, "sr_batch_stage: null argument");
+  *out = nullptr;
+  const uint32_t n_all = reads->n_reads;
+  if (cands->n_reads != n_all) return set_error(SR_EINVAL, "sr_batch_stage: reads and candidates differ in n_reads");
+  if ((reads->flags | cands->flags) & ~static_cast<uint32_t>(SR_FLAG_DEVICE))
+    return set_error(SR_EINVAL, "sr_batch_stage: unknown flags");
+  const cudaStream_t stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : s->stream;
+  if ((reads->flags | cands->flags) & SR_FLAG_DEVICE) {
+    if (r0 != 0 || r1 != n_all) return set_error(SR_EINVAL, "sr_batch_stage: device inputs are staged whole");
+    return stage_device(s, reads, cands, stream, check_budget, out);
+  }
+  if (r0 > r1 || r1 > n_all) return set_error(SR_EINVAL, "sr_batch_stage: bad read range");
+  const uint32_t n = r1 - r0;
+  if (n > (8u << 20)) return set_error(SR_EINVAL, "sr_batch_stage: more than 8M reads in one batch");
+  if (n_all && (!reads->offsets || !reads->bases || !cands->offsets))
+    return set_error(SR_EINVAL, "sr_batch_stage: null arrays");
+  const uint64_t nc_all = n_all ? cands->offsets[n_all] : 0;
+  if (n_all && (reads->offsets[0] != 0 || cands->offsets[0] != 0))
+    return set_error(SR_EINVAL, "sr_batch_stage: offsets must start at 0");
+  if (nc_all != cands->n_cands) return set_error(SR_EINVAL, "sr_batch_stage: n_cands != offsets[n_reads]");
+  if (nc_all >= (1ull << 32)) return set_error(SR_EINVAL, "sr_batch_stage: too many windows");
+  if (nc_all && (!cands->ref_id || !cands->strand || !cands->win_start || !cands->win_len))
+    return set_error(SR_EINVAL, "sr_batch_stage: null candidate arrays");
+  // the range's first base and window, and its sizes
+  const uint64_t rb = n ? reads->offsets[r0] : 0, cb = n ? cands->offsets[r0] : 0;
+  const uint64_t re = n ? reads->offsets[r1] : 0, ce = n ? cands->offsets[r1] : 0;
+  if (re < rb || ce < cb || ce > nc_all)
+    return set_error(SR_EINVAL, "sr_batch_stage: decreasing or out-of-range offsets in reads %u..%u", r0, r1);
+  const uint64_t nb = re - rb;
+  const uint64_t nc = ce - cb;
+  if (nb > static_cast<uint64_t>(n) * SR_MAX_READ_LEN)
+    return set_error(SR_EINVAL, "sr_batch_stage: %llu bases in %u reads: some read is longer than %d",
+                     static_cast<unsigned long long>(nb), n, SR_MAX_READ_LEN);
+  sr_batch* b = nullptr;
+  sr_status rs = batch_alloc(s, n, nb, nc, stream, check_budget, &b);
+  if (rs != SR_OK) return rs;
+  const BatchDev& d = b->d;
+  cudaError_t e = cudaSuccess;
   cudaStream_t st = b->stream;
   if (nb) e = cudaMemcpyAsync(const_cast<char*>(d.bases), reads->bases + rb, nb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -1268,6 +1355,7 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
   if (!s || !reads || !out) return set_error(SR_EINVAL, "sr_candidates_device: null argument");
   *out = nullptr;
   if (s->didx.n_refs == 0) return set_error(SR_EINVAL, "sr_candidates_device: no index attached to the session");
+  if (reads->flags) return set_error(SR_EINVAL, "sr_candidates_device: reads must be in host memory (flags 0)");
   sr_cand_params cp{};
   if (params) cp = *params;
   if (!cp.seed_stride) cp.seed_stride = 1;
@@ -1724,7 +1812,8 @@ extern "C" sr_status sr_align_batch(sr_session* s, const sr_reads* reads, const 
   Trace trace_("sr_align_batch");
   if (!out) return set_error(SR_EINVAL, "sr_align_batch: null out");
   *out = nullptr;
-  if (s && reads && cands && sp && reads->n_reads >= kPartMinReads) {
+  // inputs in device memory are staged as one batch: with no host copies to hide, parts gain nothing
+  if (s && reads && cands && sp && reads->n_reads >= kPartMinReads && !((reads->flags | cands->flags) & SR_FLAG_DEVICE)) {
     const sr_align_opts o = opts ? *opts : default_opts();
     if (!o.cuda_stream && o.engine != SR_ENGINE_PLAIN) {
       const sr_status st = align_in_parts(s, reads, cands, sp, o, out);
@@ -1740,16 +1829,69 @@ extern "C" sr_status sr_align_batch(sr_session* s, const sr_reads* reads, const 
   return st;
 }
 
-extern "C" sr_status sr_classify(sr_session* s, sr_batch* b, const sr_classify_params* params, uint8_t* class_out) {
-  if (!s || !b || !class_out) return set_error(SR_EINVAL, "sr_classify: null argument");
-  if (!b->ran) return set_error(SR_EINVAL, "sr_classify: batch has not run");
-  if (s->n_refs < 2) return set_error(SR_EINVAL, "sr_classify: needs 2 references");
+extern "C" sr_status sr_batch_classify(sr_session* s, sr_batch* b, const sr_classify_params* params,
+                                       uint8_t* class_out) {
+  if (!s || !b || !class_out) return set_error(SR_EINVAL, "sr_batch_classify: null argument");
+  if (!b->ran) return set_error(SR_EINVAL, "sr_batch_classify: batch has not run");
+  if (s->n_refs < 2) return set_error(SR_EINVAL, "sr_batch_classify: needs 2 references");
   const int32_t ms = params ? params->min_score : 40, mg = params ? params->margin : 5;
   cudaStream_t stream = b->stream;
   if (launch_classify(b->d, static_cast<int>(s->n_refs), ms, mg, stream) < 0)
-    return cuda_error("sr_classify launch", cudaGetLastError());
+    return cuda_error("sr_batch_classify launch", cudaGetLastError());
   cudaError_t e = cudaMemcpyAsync(class_out, b->d.read_class, b->n_reads, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_error("sr_batch_classify", e);
+  return SR_OK;
+}
+
+namespace {
+// device (or managed) memory, as opposed to host memory, pinned or not
+bool on_device(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+extern "C" sr_status sr_classify(const sr_results* res, const sr_classify_params* params, uint8_t* class_out) {
+  Trace trace_("sr_classify");
+  if (!res || !class_out) return set_error(SR_EINVAL, "sr_classify: null argument");
+  if (res->n_refs < 2) return set_error(SR_EINVAL, "sr_classify: needs results over 2 references");
+  const uint32_t n = res->n_reads, nr = res->n_refs;
+  if (n == 0) return SR_OK;
+  if (!res->best_per_ref) return set_error(SR_EINVAL, "sr_classify: results have no per-reference records");
+  const int32_t ms = params ? params->min_score : 40, mg = params ? params->margin : 5;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return set_error(SR_ECUDA, "sr_classify: no CUDA device available");
+  }
+  cudaStream_t st = cudaStreamPerThread;
+  const bool hits_dev = on_device(res->best_per_ref), out_dev = on_device(class_out);
+  const uint64_t hit_bytes = static_cast<uint64_t>(n) * nr * sizeof(sr_hit);
+  const sr_hit* d_hits = res->best_per_ref;
+  uint8_t* d_out = class_out;
+  void* tmp_hits = nullptr;
+  void* tmp_out = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!hits_dev) {
+    e = cudaMallocAsync(&tmp_hits, hit_bytes, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp_hits, res->best_per_ref, hit_bytes, cudaMemcpyHostToDevice, st);
+    d_hits = static_cast<const sr_hit*>(tmp_hits);
+  }
+  if (e == cudaSuccess && !out_dev) {
+    e = cudaMallocAsync(&tmp_out, n, st);
+    d_out = static_cast<uint8_t*>(tmp_out);
+  }
+  if (e == cudaSuccess && launch_classify_hits(d_hits, n, nr, ms, mg, d_out, st) < 0) e = cudaGetLastError();
+  if (e == cudaSuccess && !out_dev) e = cudaMemcpyAsync(class_out, d_out, n, cudaMemcpyDeviceToHost, st);
+  if (tmp_hits) cudaFreeAsync(tmp_hits, st);
+  if (tmp_out) cudaFreeAsync(tmp_out, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return cuda_error("sr_classify", e);
   return SR_OK;
 }

@@ -641,11 +641,17 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
 // En = the opened gap value, Fn = the opened gap value, tested per half by
 // min(XOR, 1).  Scores and gap costs must fit the byte table and keep every
 // value inside 16 bits (tb_pair_fits).
-constexpr int kTb4QOff = 16;                          // query word of row i at i - 1 + kTb4QOff
-constexpr int kTb4QN = kMaxReadLen + 3 * kTbRowPad;   // rows -15 .. 288
-constexpr int kTb4ROff = 32;                          // window word of band offset t at t + kTb4ROff
-constexpr int kTb4RN = kMaxReadLen + 6 * kTbRowPad;   // offsets -32 .. 319
-constexpr int kTb4Rows = kMaxReadLen + 2 * kTbRowPad + 1;
+// Shared-memory extents of a packed wavefront whose reads' DP runs at most
+// ROWS rows (256, 192 or 128; smaller extents let more warps reside per SM)
+constexpr int kTb4QOff = 16;  // query word of row i at i - 1 + kTb4QOff
+constexpr int kTb4ROff = 32;  // window word of band offset t at t + kTb4ROff
+template <int ROWS>
+struct Tb4Ext {
+  static constexpr int QN = ROWS + 3 * kTbRowPad;    // rows -15 .. ROWS + 32
+  static constexpr int RN = ROWS + 6 * kTbRowPad;    // offsets -32 .. ROWS + 63
+  static constexpr int Rows = ROWS + 2 * kTbRowPad + 1;
+  static_assert(QN % 16 == 0 && RN % 16 == 0, "whole 16-code chunks");
+};
 
 __device__ __forceinline__ uint32_t tb_prmt(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
@@ -708,10 +714,11 @@ struct PairCodes {
   }
 };
 
-template <int SEG>
+template <int SEG, int ROWS>
 __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave4(TbArgs a, const uint32_t* list, const uint32_t* range) {
   constexpr int NSEG = 32 / SEG;
-  __shared__ uint16_t dirs_s[kTbWarps][NSEG][kTb4Rows * SEG];
+  constexpr int kTb4QN = Tb4Ext<ROWS>::QN, kTb4RN = Tb4Ext<ROWS>::RN;
+  __shared__ uint16_t dirs_s[kTbWarps][NSEG][Tb4Ext<ROWS>::Rows * SEG];
   __shared__ uint16_t q_s[kTbWarps][NSEG * 2][kTb4QN];
   __shared__ uint16_t r_s[kTbWarps][NSEG * 2][kTb4RN];
   const int lane = threadIdx.x & 31;
@@ -735,6 +742,10 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave4(TbArgs a, const uint
     for (int X = 0; X < 4; ++X) {
       const uint32_t li = base + 4 * seg + X;
       rd[X] = tb_load(a, li < count, li < count ? list[begin + li] : 0u);
+      if (rd[X].has && rd[X].ihi > ROWS) {  // routed by rows, so never expected: keep shared memory in bounds
+        atomicOr(a.status, kStInternal);
+        rd[X].has = false;
+      }
     }
 #pragma unroll
     for (int P = 0; P < 2; ++P) {
@@ -1267,6 +1278,14 @@ __global__ void __launch_bounds__(kTbScanThreads) k_tb_scan(uint32_t* cnt) {
     cnt[2 * kTbCodes + 2 * t] = cnt[kTbCodes + c0];
     cnt[2 * kTbCodes + 2 * t + 1] = cnt[kTbCodes + c1 - 1] + cnt[c1 - 1];
   }
+  if (t < 2 * kTbRowClasses) {
+    // buckets 4 and 5 by rows: codes b * 256 + [0, 64) run 193-256 rows, [64, 128)
+    // 129-192, [128, 256) at most 128
+    const int b = 4 + t / kTbRowClasses, rc = t % kTbRowClasses;
+    const int c0 = b * kMaxReadLen + 64 * rc, c1 = rc == kTbRowClasses - 1 ? (b + 1) * kMaxReadLen : c0 + 64;
+    cnt[2 * kTbCodes + 2 * kTbBuckets + 2 * t] = cnt[kTbCodes + c0];
+    cnt[2 * kTbCodes + 2 * kTbBuckets + 2 * t + 1] = cnt[kTbCodes + c1 - 1] + cnt[c1 - 1];
+  }
 }
 
 __global__ void k_tb_scatter(uint32_t n_reads, const uint32_t* code, uint32_t* cursor, uint32_t* list) {
@@ -1346,10 +1365,20 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
     ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
   };
+  // the packed wavefront of one bucket (4: SEG 16, 5: SEG 32) as three launches
+  // by rows (kernels with smaller shared extents hold more warps per SM)
+  auto wave4 = [&](auto k256, auto k192, auto k128, int bucket, int per_warp) -> bool {
+    const int sub = 2 * kTbBuckets + 2 * kTbRowClasses * (bucket - 4);
+    return wave(k256, sub / 2, per_warp) && wave(k192, sub / 2 + 1, per_warp) && wave(k128, sub / 2 + 2, per_warp);
+  };
   // widest bands (longest kernels) first
   const bool pair = tb_pair_fits(a.sa, a.sb, a.go, a.ge);
-  if (!wave(k_tb_wave2, 6, 2) || !(pair ? wave(k_tb_wave4<32>, 5, 4) : wave(k_tb_wave<32>, 5, 2)) ||
-      !(pair ? wave(k_tb_wave4<16>, 4, 8) : wave(k_tb_wave<16>, 4, 4)) || !threads())
+  if (!wave(k_tb_wave2, 6, 2) ||
+      !(pair ? wave4(k_tb_wave4<32, 256>, k_tb_wave4<32, 192>, k_tb_wave4<32, 128>, 5, 4)
+             : wave(k_tb_wave<32>, 5, 2)) ||
+      !(pair ? wave4(k_tb_wave4<16, 256>, k_tb_wave4<16, 192>, k_tb_wave4<16, 128>, 4, 8)
+             : wave(k_tb_wave<16>, 4, 4)) ||
+      !threads())
     return -1;
   const size_t smem = static_cast<size_t>(kMaxWinLen) * 32 * sizeof(uint32_t);
   static bool attr = false;

@@ -24,6 +24,7 @@ ENGINE_BATCHED, ENGINE_PLAIN = 0, 1
 CLASS_UNALIGNED, CLASS_A, CLASS_B, CLASS_AMBIGUOUS = 0, 1, 2, 3
 OP_M, OP_I, OP_D, OP_S = 0, 1, 2, 4
 CIGAR_STRIDE = 776
+FLAG_DEVICE = 1  # sr_reads / sr_cand_list arrays are device pointers
 
 P = C.c_void_p
 
@@ -40,7 +41,7 @@ class IndexParams(C.Structure):
 
 
 class Reads(C.Structure):
-    _fields_ = [("n_reads", C.c_uint32), ("reserved", C.c_uint32), ("bases", P), ("offsets", P)]
+    _fields_ = [("n_reads", C.c_uint32), ("flags", C.c_uint32), ("bases", P), ("offsets", P)]
 
 
 class CandParams(C.Structure):
@@ -49,7 +50,7 @@ class CandParams(C.Structure):
 
 
 class CandList(C.Structure):
-    _fields_ = [("n_reads", C.c_uint32), ("reserved", C.c_uint32), ("n_cands", C.c_uint64),
+    _fields_ = [("n_reads", C.c_uint32), ("flags", C.c_uint32), ("n_cands", C.c_uint64),
                 ("offsets", P), ("ref_id", P), ("strand", P), ("win_start", P), ("win_len", P),
                 ("hits", P)]
 
@@ -148,7 +149,8 @@ def lib():
             "sr_batch_stats": ([P, P, P, P, P], C.c_int32),
             "sr_batch_timing": ([P, P, P, P], C.c_int32),
             "sr_results_free": ([C.POINTER(Results)], None),
-            "sr_classify": ([P, P, P, P], C.c_int32),
+            "sr_classify": ([P, P, P], C.c_int32),
+            "sr_batch_classify": ([P, P, P, P], C.c_int32),
             "sr_batch_report": ([P, P, C.c_uint32, C.c_uint32, C.POINTER(C.POINTER(Report))], C.c_int32),
             "sr_report_free": ([C.POINTER(Report)], None),
             "sr_write_sam": ([C.POINTER(Reads), C.POINTER(Results), P, C.POINTER(SamOpts), C.c_char_p], C.c_int32),
@@ -228,6 +230,32 @@ def make_cands(cand_off, c_ref, c_strand, c_start, c_len, keep: _Keep):
     return cl
 
 
+def _dptr(t, dtype):
+    """Device address of a contiguous CUDA tensor whose elements are `dtype`-sized."""
+    assert t.is_cuda and t.is_contiguous(), "device inputs must be contiguous CUDA tensors"
+    assert t.element_size() == np.dtype(dtype).itemsize, (t.dtype, dtype)
+    return C.c_void_p(t.data_ptr())
+
+
+def make_reads_device(bases, offsets):
+    """sr_reads over CUDA tensors (uint8 bases, int64 / uint64 offsets), flagged as device memory."""
+    return Reads(offsets.numel() - 1, FLAG_DEVICE, _dptr(bases, np.uint8), _dptr(offsets, np.uint64))
+
+
+def make_cands_device(cand_off, c_ref, c_strand, c_start, c_len, n_cands):
+    """sr_cand_list over CUDA tensors (offsets and starts 8-byte, ref ids and
+    strands 1-byte, lengths 4-byte integers), flagged as device memory; n_cands
+    is cand_off's last value (known to the caller, not read back here)."""
+    cl = CandList()
+    cl.n_reads = cand_off.numel() - 1
+    cl.flags = FLAG_DEVICE
+    cl.n_cands = int(n_cands)
+    cl.offsets, cl.ref_id = _dptr(cand_off, np.uint64), _dptr(c_ref, np.uint8)
+    cl.strand, cl.win_start = _dptr(c_strand, np.uint8), _dptr(c_start, np.uint64)
+    cl.win_len, cl.hits = _dptr(c_len, np.uint32), None
+    return cl
+
+
 class _ResultsOwner:
     """Frees an sr_results when the last array viewing it is gone."""
 
@@ -303,6 +331,33 @@ def write_sam(path, bases, read_off, res: dict, ref_lens, read_names=None, ref_n
         keep.refs.append(rp)
         o.secondary = C.pointer(rp)
     _check(lib().sr_write_sam(C.byref(reads), C.byref(r), _p(lens), C.byref(o), os.fsencode(path)))
+
+
+def classify(res: dict, min_score=40, margin=5, out=None):
+    """sr_classify on a results dict (align / fetch / wait): the class of every
+    read between references 0 and 1, computed on the device.  res["best_per_ref"]
+    may be the numpy records or a CUDA tensor holding them (n_reads x n_refs
+    records of HIT_DTYPE bytes); `out` may be a CUDA uint8 tensor (filled in
+    place, returned) or None (a numpy array is returned)."""
+    per = res["best_per_ref"]
+    keep = _Keep()
+    r = Results()
+    if hasattr(per, "data_ptr"):  # device records
+        n, nr = int(res["n_reads"]), int(res["n_refs"])
+        assert per.is_cuda and per.numel() * per.element_size() >= n * nr * HIT_DTYPE.itemsize
+        r.best_per_ref = C.cast(per.data_ptr(), C.POINTER(Hit))
+    else:
+        per = keep.arr(per, HIT_DTYPE)
+        n, nr = per.shape[0], (per.shape[1] if per.ndim == 2 else int(res["n_refs"]))
+        r.best_per_ref = C.cast(per.ctypes.data, C.POINTER(Hit))
+    r.n_reads, r.n_refs = n, nr
+    prm = np.array([min_score, margin], np.int32)
+    if out is None:
+        o = np.zeros(max(n, 1), np.uint8)
+        _check(lib().sr_classify(C.byref(r), _p(prm), _p(o)))
+        return o[:n]
+    _check(lib().sr_classify(C.byref(r), _p(prm), C.c_void_p(out.data_ptr())))
+    return out
 
 
 def cigar_of(res: dict, read: int):
@@ -402,7 +457,7 @@ class Batch:
         n = self.n_reads
         out = np.zeros(max(n, 1), np.uint8)
         prm = np.array([min_score, margin], np.int32)
-        _check(lib().sr_classify(self.session.h, self.h, _p(prm), _p(out)))
+        _check(lib().sr_batch_classify(self.session.h, self.h, _p(prm), _p(out)))
         return out[:n]
 
     def report(self, kind=REPORT_BEST_N, n_best=1):
@@ -480,6 +535,18 @@ class Session:
         keep = _Keep()
         reads = make_reads(bases, read_off, keep)
         cands = make_cands(cand_off, c_ref, c_strand, c_start, c_len, keep)
+        out = C.POINTER(Results)()
+        _check(lib().sr_align_batch(self.h, C.byref(reads), C.byref(cands), C.byref(sp or score_params()),
+                                    C.byref(opts or align_opts()), C.byref(out)))
+        return results_to_numpy(out)
+
+    def align_device(self, bases, read_off, cand_off, c_ref, c_strand, c_start, c_len, n_cands, sp=None,
+                     opts=None):
+        """sr_align_batch on inputs that already sit in device memory (CUDA
+        tensors; see make_reads_device / make_cands_device); results come back
+        to host arrays as with align()."""
+        reads = make_reads_device(bases, read_off)
+        cands = make_cands_device(cand_off, c_ref, c_strand, c_start, c_len, n_cands)
         out = C.POINTER(Results)()
         _check(lib().sr_align_batch(self.h, C.byref(reads), C.byref(cands), C.byref(sp or score_params()),
                                     C.byref(opts or align_opts()), C.byref(out)))

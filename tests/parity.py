@@ -168,3 +168,40 @@ def whole_batch_properties(g, w):
             bad.append(f"read {r}: CIGAR does not consume the read")
             break
     return bad
+
+
+def edge_workload(seed=23):
+    """Reads of edge lengths (1, 2, tile boundaries 15-17, 31-33, ..., 255, 256),
+    each with windows clamped at both reference ends, a 1-base window, a
+    512-base window, windows shorter than the read, alternating strands, and a
+    read with no windows at all, on a 3 kbp reference."""
+    rng = np.random.default_rng(seed)
+    L = 3000
+    ref = rng.choice(np.frombuffer(b"ACGT", np.uint8), L)
+    reads, offs = [], [0]
+    cand = dict(cand_off=[0], c_ref=[], c_strand=[], c_start=[], c_len=[])
+    lengths = [1, 2, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 255, 256]
+    for m in lengths:
+        pos = int(rng.integers(0, L - m))
+        r = ref[pos:pos + m].copy()
+        if m > 10:
+            r[m // 2] = ord("A") if r[m // 2] != ord("A") else ord("C")
+        reads.append(r)
+        offs.append(offs[-1] + m)
+        wins = [(pos, m), (max(0, pos - 64), min(L - max(0, pos - 64), m + 128)), (0, min(L, m + 5)),
+                (L - min(L, m + 7), min(L, m + 7)), (pos, 1), (max(0, pos - 3), min(5, L)),
+                (max(0, min(pos, L - 512)), 512)]
+        if m > 12:
+            wins.append((pos + 2, m - 10))
+        for k, (st, ln) in enumerate(wins):
+            cand["c_ref"].append(0)
+            cand["c_strand"].append(k % 2)
+            cand["c_start"].append(st)
+            cand["c_len"].append(ln)
+        cand["cand_off"].append(len(cand["c_ref"]))
+    # a read with no windows at all
+    reads.append(ref[10:90])
+    offs.append(offs[-1] + 80)
+    cand["cand_off"].append(len(cand["c_ref"]))
+    return dict(refs=[ref], bases=np.concatenate(reads), read_off=np.array(offs),
+                **{k: np.array(v) for k, v in cand.items()})

@@ -108,7 +108,8 @@ CONSTANTS = {"SR_OK": "SR_OK", "SR_EINVAL": "SR_EINVAL", "SR_ENOMEM": "SR_ENOMEM
              "ENGINE_BATCHED": "SR_ENGINE_BATCHED", "ENGINE_PLAIN": "SR_ENGINE_PLAIN",
              "CLASS_UNALIGNED": "SR_CLASS_UNALIGNED", "CLASS_A": "SR_CLASS_A", "CLASS_B": "SR_CLASS_B",
              "CLASS_AMBIGUOUS": "SR_CLASS_AMBIGUOUS", "CIGAR_STRIDE": "SR_CIGAR_STRIDE",
-             "REPORT_BEST_N": "SR_REPORT_BEST_N", "REPORT_TIED": "SR_REPORT_TIED", "REPORT_MAX": "SR_REPORT_MAX"}
+             "REPORT_BEST_N": "SR_REPORT_BEST_N", "REPORT_TIED": "SR_REPORT_TIED", "REPORT_MAX": "SR_REPORT_MAX",
+             "FLAG_DEVICE": "SR_FLAG_DEVICE"}
 
 
 def test_binding_constants_match_the_header(tmp_path):

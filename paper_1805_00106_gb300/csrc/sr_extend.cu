@@ -30,6 +30,7 @@ ExtArgs make_args(const BatchDev& b, const DevRefs& refs, const ScoreConst& sc) 
   a.sb = sc.sb;
   a.go = sc.go;
   a.ge = sc.ge;
+  a.k16 = 65536u;
   return a;
 }
 

@@ -24,7 +24,9 @@
 // The best cell: per lane, the max over its rows of each column is compared
 // with the running best; a strict improvement records the column, so the
 // smallest column reaching the best wins; the group then reduces
-// (score, -column) keys.  Rows beyond the read are added at the top with
+// (score, -column) keys.  The keys and the top-border substitution of lane 0
+// are built with integer multiply-adds, which issue on the FMA pipe, so that
+// the ALU pipe carries the recurrence, the column maximum and two key maxima.  Rows beyond the read are added at the top with
 // mismatch scores; they stay at H = 0 and leave the recurrence unchanged
 // (they act like the H = 0 / F = -inf top border).
 #include <cuda_runtime.h>
@@ -55,6 +57,10 @@ struct ExtArgs {
   uint64_t n_items;             // plain engine: items in input order
   int cls;
   int32_t sa, sb, go, ge;
+  // 65536, passed at run time so that the per-column key arithmetic stays
+  // multiply-adds (the FMA pipe) instead of being folded into shifts and
+  // byte permutes on the ALU pipe, which the recurrence saturates
+  uint32_t k16;
 };
 
 // kernel shapes (lanes per alignment, rows per lane) instantiated for the batched
@@ -146,6 +152,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint3
   return false;
 }
 
+// a * b + c and the high word of a * b as 32-bit integer multiply-adds (issued
+// on the FMA pipe, beside the ALU pipe that runs the DPX recurrence)
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t imulhi(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
 // byte permute, default mode: selector nibble bits 2:0 pick one of the 8 bytes
 // of {b, a}; bit 3 replicates that byte's sign bit (PTX prmt.b32)
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
@@ -192,17 +211,23 @@ __device__ __forceinline__ uint32_t read_code(const uint32_t* row, uint32_t m, u
   return strand ? 3u - base_at(row, m - 1u - i) : base_at(row, i);
 }
 
-// Blocks of 128 threads per SM the register budget is cut for: with 24 rows per
-// lane or fewer (22 in final-row mode, which keeps more per row) the sweep fits
-// 128 registers without spilling (4 blocks, 16 warps per SM); up to 27 rows
-// need 168 (3 blocks), more up to 255.
-template <int R, int MODE>
+// Blocks of 128 threads per SM the register budget is cut for (the sweep is
+// bound by the ALU pipe and the latency of its DPX chains, so resident warps
+// count).  Persistent kernels: up to 12 rows per lane fit 80 registers (6
+// blocks, 24 warps per SM), up to 17 rows 96 (16 in final-row mode, which keeps
+// more per row; 5 blocks), up to 24 rows (22) 128 (4 blocks), up to 27 rows 168
+// (3 blocks), more up to 255.  The one-launch (plain) kernels keep the 128
+// register budget up to 24 rows.  None of them spills.
+template <int R, int MODE, bool PERSIST>
 constexpr int ext_min_blocks() {
-  return R <= (MODE == 1 ? 22 : 24) ? 4 : (R <= 27 ? 3 : 2);
+  return (PERSIST && R <= 12) ? 6
+         : (PERSIST && R <= (MODE == 1 ? 16 : 17)) ? 5
+         : R <= (MODE == 1 ? 22 : 24) ? 4
+         : (R <= 27 ? 3 : 2);
 }
 
 template <int G, int R, int MODE, bool PERSIST>
-__global__ void __launch_bounds__(128, ext_min_blocks<R, MODE>()) k_extend16(ExtArgs a) {
+__global__ void __launch_bounds__(128, ext_min_blocks<R, MODE, PERSIST>()) k_extend16(ExtArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GPW = 32 / G;
   const int lane = threadIdx.x & 31;
@@ -346,7 +371,13 @@ __global__ void __launch_bounds__(128, ext_min_blocks<R, MODE>()) k_extend16(Ext
     // highest score and, among equal scores, the smallest (first) column
     const uint32_t KINIT = (INIT & 0xffffu) << 16;
     uint32_t kbl = KINIT, kbh = KINIT;
-    uint32_t jn = 0xfffeu + static_cast<uint32_t>(glane);  // 0xffff - (column of step s), column = s - glane + 1
+    // 0x7fff - (column of step s), column = s - glane + 1: in 0x7fff - 544 .. 0x7fff + 31,
+    // so it never carries into a key's score half
+    const uint32_t jn = 0x7ffeu + static_cast<uint32_t>(glane);
+    const uint32_t K16 = a.k16;
+    // lane 0's row above is the top border (H = 0, F = -inf): its shuffled-in
+    // values v become (v - INIT) * nz + INIT, with nz = 0 on lane 0, else 1
+    const uint32_t nz = glane == 0 ? 0u : 1u;
     // mode 2: biased T value of the winner's score in each half, rows found
     uint32_t tgt_lo = 0, tgt_hi = 0, ilo = 0xffffffffu, ihi = 0xffffffffu;
     if (MODE == 2 && has_task) {
@@ -357,12 +388,8 @@ __global__ void __launch_bounds__(128, ext_min_blocks<R, MODE>()) k_extend16(Ext
     const uint16_t* colp = gs->col + kColLead - glane;  // colp[s] = column s - glane
     for (int s = 0; s < nsteps; ++s) {
       // lane 0's row above is the top border (H = 0, F = -inf): tin = fin = INIT
-      uint32_t tin = __shfl_up_sync(FULL, Tbot, 1, G);
-      uint32_t fin = __shfl_up_sync(FULL, Fbot, 1, G);
-      if (glane == 0) {
-        tin = INIT;
-        fin = INIT;
-      }
+      const uint32_t tin = imad(__shfl_up_sync(FULL, Tbot, 1, G) - INIT, nz, INIT);
+      const uint32_t fin = imad(__shfl_up_sync(FULL, Fbot, 1, G) - INIT, nz, INIT);
       const int j = s - glane;
       {
         const uint32_t sel = colp[s];
@@ -407,9 +434,11 @@ __global__ void __launch_bounds__(128, ext_min_blocks<R, MODE>()) k_extend16(Ext
         if (MODE == 1)
           cm &= (static_cast<uint32_t>(j) < nlo ? 0xffffu : 0u) |
                 (static_cast<uint32_t>(j) < nhi ? 0xffff0000u : 0u);
-        // strict improvement per half records the (1-based) column
-        kbl = max(kbl, prmt(jn - static_cast<uint32_t>(s), cm, 0x5410u));
-        kbh = max(kbh, prmt(jn - static_cast<uint32_t>(s), cm, 0x7610u));
+        // strict improvement per half records the (1-based) column: keys
+        // (half << 16) | (0x7fff - column)
+        const uint32_t jc = jn - static_cast<uint32_t>(s);
+        kbl = max(kbl, imad(cm, K16, jc));
+        kbh = max(kbh, imad(imulhi(cm, K16), K16, jc));
       }
     }
 
@@ -437,10 +466,10 @@ __global__ void __launch_bounds__(128, ext_min_blocks<R, MODE>()) k_extend16(Ext
     if (has_task && glane == 0) {
       const uint32_t sl = klo >> 16, sh = khi >> 16;
       a.item_score[lo.item] = static_cast<int32_t>(sl);
-      a.item_end[lo.item] = sl ? 0xffffu - (klo & 0xffffu) : 0u;
+      a.item_end[lo.item] = sl ? 0x7fffu - (klo & 0xffffu) : 0u;
       if (hi_valid) {
         a.item_score[hi.item] = static_cast<int32_t>(sh);
-        a.item_end[hi.item] = sh ? 0xffffu - (khi & 0xffffu) : 0u;
+        a.item_end[hi.item] = sh ? 0x7fffu - (khi & 0xffffu) : 0u;
       }
     }
     __syncwarp();

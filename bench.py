@@ -13,6 +13,7 @@ Under torchrun (N > 1) every rank aligns its own batch of the same shape
 over ranks.
 """
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -50,7 +51,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default bins)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving latency run")
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="duration of each offered load")
-    ap.add_argument("--serve-budget-mb", type=int, default=1024,
+    ap.add_argument("--serve-budget-mb", type=int, default=512,
                     help="HBM budget of the serving session (admission binds at high load)")
     ap.add_argument("--no-cal", action="store_true", help="skip the CAL finder comparison")
     ap.add_argument("--no-extra", action="store_true",
@@ -202,7 +203,7 @@ def slice_reads(w, r0, r1):
 SIZE_BUCKETS = (256, 1024, 2048, 4096)
 
 
-def serving_bench(sr, scale, seconds=30.0, pool_size=48, seed=404, budget_mb=1024):
+def serving_bench(sr, scale, seconds=30.0, pool_size=48, seed=404, budget_mb=512):
     """Continuous batching on the xenograft reference pair (64 Mbp A and a diverged
     B, held on the device): requests of 1-4096 reads (75-250 bp, 0-64 windows
     each) arrive as a Poisson process at 0.25x, 0.5x and 0.9x of the served
@@ -221,6 +222,10 @@ def serving_bench(sr, scale, seconds=30.0, pool_size=48, seed=404, budget_mb=102
     opts = sr.align_opts(classify=True)
 
     def run(rate, duration, burst=False):
+        # the load generator runs in Python: a garbage-collection pause of the
+        # interpreter would hold back submissions and release them as a burst
+        gc.collect()
+        gc.disable()
         sess.serve_start(spp, opts)
         rng = np.random.default_rng(seed)
         tickets, reads = [], []
@@ -259,9 +264,11 @@ def serving_bench(sr, scale, seconds=30.0, pool_size=48, seed=404, budget_mb=102
         done.set()
         th.join()
         el = time.perf_counter() - t0
+        gc.enable()
         st = sess.serve_stats()
         bs = sess.serve_stats_by_size(SIZE_BUCKETS)
         ov = sess.serve_overlap()
+        lat = sess.serve_latencies()
         sess.serve_stop()
         lo = 0
         by_size = []
@@ -274,7 +281,8 @@ def serving_bench(sr, scale, seconds=30.0, pool_size=48, seed=404, budget_mb=102
                     p99_ms=round(st["p99_us"] / 1e3, 3), rounds=st["rounds"],
                     max_round_requests=st["max_round_requests"], by_size=by_size,
                     rounds_overlapping_previous=ov["overlapped"], device_gap_ms=round(ov["device_idle_ms"], 1),
-                    budget_waits=ov["budget_waits"], seconds=round(el, 1))
+                    budget_waits=ov["budget_waits"], seconds=round(el, 1),
+                    max_ms=round(float(lat["us"].max()) / 1e3, 3) if len(lat["us"]) else 0.0)
 
     run(1.0, 0, burst=True)  # warm-up: graph shapes, host pages
     sat = run(1.0, 0, burst=True)
@@ -650,7 +658,8 @@ def main():
             "reads_per_s": round(reads_per_s, 1),
             "gcups_without_traceback": round(cells / (statistics.mean(tot_ms) - statistics.mean(tb_ms)) * 1e3 / 1e9, 3),
             "gpu_launches": int(kernels_per_step * args.steps),
-            "roofline": roofline, "clocks": clk}
+            "roofline": roofline, "clocks": clk,
+            "length_bins": [{"max_len": u, "lanes": g, "rows": r} for u, g, r in sr.tune_get()]}
 
     if rank == 0 and not args.no_plain:
         popts = sr.align_opts(engine=sr.ENGINE_PLAIN, stream=stream.cuda_stream)

@@ -388,6 +388,12 @@ sr_status sr_serve_stats(sr_session* s, double* p50_us, double* p99_us, uint64_t
  * (any may be NULL). */
 sr_status sr_serve_stats_by_size(sr_session* s, uint32_t n_buckets, const uint32_t* max_reads,
                                  double* p50_us, double* p99_us, uint64_t* count);
+/* Every completed request in completion order, from index `first` on: up to
+ * cap entries of latency (us, submit to completion), size (reads) and
+ * completion time (s after sr_serve_start); n_out receives the number of
+ * requests completed so far. */
+sr_status sr_serve_latencies(sr_session* s, uint64_t first, uint32_t cap, double* us, uint32_t* reads,
+                             double* done_s, uint64_t* n_out);
 /* Device timeline of the completed rounds, from CUDA events the server records
  * on each round's stream: first_ms[k] when round k's first kernel finished,
  * last_ms[k] when its last kernel finished, both in ms after sr_serve_start

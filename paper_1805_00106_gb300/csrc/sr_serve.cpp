@@ -92,9 +92,12 @@ struct Server {
   bool stop = false;
   bool sched_done = false;
   std::thread th_sched, th_done;
-  // completed requests: latency (us) and size (reads)
+  // completed requests, in completion order: latency (us), size (reads) and
+  // completion time (s after sr_serve_start)
   std::vector<double> lat_us;
   std::vector<uint32_t> lat_reads;
+  std::vector<double> lat_done_s;
+  Clock::time_point t_start = Clock::now();
   uint64_t rounds = 0, rounds_done = 0, max_round = 0, budget_waits = 0;
   // rounds launched and not yet completed, oldest first (the completer's queue)
   std::deque<Round> launched;
@@ -192,6 +195,7 @@ void finish(Server* sv, Round& rd, sr_results* merged) {
     --sv->inflight;
     sv->lat_us.push_back(std::chrono::duration<double, std::micro>(now - q->t_submit).count());
     sv->lat_reads.push_back(q->n_reads);
+    sv->lat_done_s.push_back(std::chrono::duration<double>(now - sv->t_start).count());
   }
   sv->cv_done.notify_all();
   sv->cv_work.notify_all();
@@ -553,6 +557,23 @@ extern "C" sr_status sr_serve_stats_by_size(sr_session* s, uint32_t n_buckets, c
     if (p50_us) p50_us[k] = p50;
     if (p99_us) p99_us[k] = p99;
   }
+  return SR_OK;
+}
+
+extern "C" sr_status sr_serve_latencies(sr_session* s, uint64_t first, uint32_t cap, double* us, uint32_t* reads,
+                                        double* done_s, uint64_t* n_out) {
+  if (!s || (cap && (!us || !reads || !done_s)) || !n_out) return set_error(SR_EINVAL, "sr_serve_latencies: null argument");
+  Server* sv = session_server(s);
+  if (!sv) return set_error(SR_EINVAL, "sr_serve_latencies: not serving");
+  std::lock_guard<std::mutex> g(sv->mu);
+  const uint64_t n = sv->lat_us.size();
+  uint64_t k = 0;
+  for (uint64_t i = first; i < n && k < cap; ++i, ++k) {
+    us[k] = sv->lat_us[i];
+    reads[k] = sv->lat_reads[i];
+    done_s[k] = sv->lat_done_s[i];
+  }
+  *n_out = n;
   return SR_OK;
 }
 

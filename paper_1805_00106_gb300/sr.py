@@ -160,6 +160,7 @@ def lib():
             "sr_serve_stats": ([P, P, P, P, P, P], C.c_int32),
             "sr_serve_stats_by_size": ([P, C.c_uint32, P, P, P, P], C.c_int32),
             "sr_serve_overlap": ([P, P, P, P, P, C.c_uint32, P, P], C.c_int32),
+            "sr_serve_latencies": ([P, C.c_uint64, C.c_uint32, P, P, P, P], C.c_int32),
             "sr_serve_stop": ([P], C.c_int32),
             "sr_tune": ([P, C.POINTER(ScoreParams), C.c_uint32], C.c_int32),
             "sr_tune_save": ([C.c_char_p], C.c_int32),
@@ -600,6 +601,16 @@ class Session:
         _check(lib().sr_serve_stats_by_size(self.h, len(b), _p(b), _p(p50), _p(p99), _p(cnt)))
         return [dict(max_reads=int(b[k]), count=int(cnt[k]), p50_us=float(p50[k]), p99_us=float(p99[k]))
                 for k in range(len(b))]
+
+    def serve_latencies(self):
+        """Every completed request in completion order: latency (us), reads and
+        completion time (s after serve_start)."""
+        n = C.c_uint64()
+        _check(lib().sr_serve_latencies(self.h, 0, 0, None, None, None, C.byref(n)))
+        k = n.value
+        us, rd, t = np.zeros(max(k, 1)), np.zeros(max(k, 1), np.uint32), np.zeros(max(k, 1))
+        _check(lib().sr_serve_latencies(self.h, 0, k, _p(us), _p(rd), _p(t), C.byref(n)))
+        return dict(us=us[:k], reads=rd[:k], done_s=t[:k])
 
     def serve_overlap(self, cap=0):
         """Device timeline of completed rounds (first kernel done, last kernel

@@ -201,11 +201,11 @@ template <int G>
 __global__ void k_select(const uint64_t* cand_off, uint32_t n_reads, const int32_t* item_score,
                          const uint32_t* item_end, const uint8_t* c_ref, const uint8_t* c_strand,
                          const uint64_t* c_start, int n_refs, DevHit* hits) {
-  static_assert(G == 16 || G == 32, "group of a half or a whole warp");
+  static_assert(G == 4 || G == 8 || G == 16 || G == 32, "groups of 4, 8, 16 or 32 lanes");
   const uint64_t r = (blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x) / G;
   const int wl = threadIdx.x & 31;                       // lane in the warp
   const int l = wl % G;                                  // lane in the group
-  const uint32_t gm = G == 32 ? FULL : (0xffffu << (wl & 16));  // the group's lanes
+  const uint32_t gm = G == 32 ? FULL : (((1u << G) - 1u) << (wl & (32 - G)));  // the group's lanes
   if (r >= n_reads) return;
   const uint64_t c0 = cand_off[r], c1 = cand_off[r + 1];
   const int slots = 1 + n_refs;
@@ -473,11 +473,20 @@ int launch_bins(const BatchDev& b, const ScoreConst& sc, const TuneBin* bins, in
 
 int launch_select(const BatchDev& b, int n_refs, cudaStream_t st) {
   if (b.n_reads == 0) return 0;
-  // half a warp per read: c2's reads hold at most 16 windows nearly always
-  const uint64_t t = static_cast<uint64_t>(b.n_reads) * 16;
-  k_select<16><<<static_cast<unsigned>((t + 255) / 256), 256, 0, st>>>(
-      b.cand_off, b.n_reads, b.item_score, b.item_end, b.c_ref, b.c_strand, b.c_start, n_refs,
-      b.hits);
+  // G lanes per read, by the batch's windows per read: a read with up to G
+  // windows is handled one window per lane, more in a loop.  Half a warp when
+  // reads hold several windows (c2: Poisson(6)); 4 or 8 lanes when they hold one
+  // or two (index candidates on a diverged reference pair: 1.3 per read), so
+  // that fewer lanes idle.
+  const uint64_t wpr = (b.n_items + b.n_reads - 1) / b.n_reads;  // mean windows per read, rounded up
+  auto go = [&](auto kern, int G) {
+    const uint64_t t = static_cast<uint64_t>(b.n_reads) * G;
+    kern<<<static_cast<unsigned>((t + 255) / 256), 256, 0, st>>>(b.cand_off, b.n_reads, b.item_score, b.item_end,
+                                                                 b.c_ref, b.c_strand, b.c_start, n_refs, b.hits);
+  };
+  if (wpr <= 2) go(k_select<4>, 4);
+  else if (wpr <= 4) go(k_select<8>, 8);
+  else go(k_select<16>, 16);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

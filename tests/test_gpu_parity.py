@@ -361,3 +361,35 @@ def test_bad_window_in_a_large_batch_reports_the_first(sr):
     # the same batch, unmodified, still runs
     g = gpu_run(s, w, want_cigar=0)
     assert len(g["item_score"]) == n_items
+
+
+@pytest.mark.parametrize("per_read", [1, 3])
+def test_select_lane_groups_with_crowded_reads(sr, per_read):
+    """The per-read selection runs 4, 8 or 16 lanes per read by the batch's mean
+    windows per read. Batches of mostly one (or three) window per read, where a
+    few reads hold 20-40 windows (each window four times, so the winner's
+    duplicates must not count as its second best), take the small groups' loop
+    path for those reads."""
+    w = S.workload("c2", scale=0.002, seed=91, rc_frac=0.5)
+    rng = np.random.default_rng(92)
+    co = np.asarray(w["cand_off"], np.int64)
+    n = len(co) - 1
+    keep = []
+    for r in range(n):
+        c0, c1 = co[r], co[r + 1]
+        if c1 == c0:
+            keep.append([])
+            continue
+        if r % 97 == 5:  # a crowded read: its windows repeated, plus decoys
+            idx = list(range(c0, c1)) * 4 + list(rng.integers(0, co[-1], 12))
+        else:
+            idx = list(range(c0, min(c1, c0 + per_read)))
+        keep.append(idx)
+    items = np.array([i for k in keep for i in k], np.int64)
+    cand_off = np.concatenate([[0], np.cumsum([len(k) for k in keep])])
+    w2 = dict(w, cand_off=cand_off, **{k: np.asarray(w[k])[items] for k in ["c_ref", "c_strand", "c_start", "c_len"]})
+    assert len(items) / n <= (2 if per_read == 1 else 4)
+    s = _session(sr, w2)
+    o = oracle_run(w2)
+    _check(gpu_run(s, w2), o)
+    assert int(np.max(np.diff(cand_off))) >= 20

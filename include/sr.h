@@ -342,10 +342,12 @@ sr_status sr_batch_timing(const sr_batch* b, float* total_ms, float* extend_ms, 
  * to class_out (caller-owned).  Either may be host memory (results from
  * sr_align_batch, sr_batch_fetch or sr_wait; pinned or not) or device memory
  * (found with cudaPointerGetAttributes); the classes are computed by a kernel
- * on the current device either way (host records are copied over first, on
- * the per-thread default stream; the call returns when the classes are in
- * class_out).  params NULL = defaults.  Errors: SR_EINVAL (fewer than 2
- * references, null arrays), SR_ECUDA. */
+ * on the current device either way (host records are copied over first).  The
+ * work runs on the per-thread default stream, which waits for the legacy
+ * default stream; device records or a device class array that work on other
+ * streams writes must be finished before the call.  It returns when the
+ * classes are in class_out.  params NULL = defaults.  Errors: SR_EINVAL (fewer
+ * than 2 references, null arrays), SR_ECUDA. */
 typedef struct {
   int32_t min_score; /* default 40 */
   int32_t margin;    /* default 5; 1 = the paper's exact-tie rule */

@@ -123,6 +123,8 @@ typedef struct {
   uint32_t pad;         /* default 32 */
   uint32_t max_cands;   /* 0 = all */
   uint32_t n_threads;   /* 0 = hardware concurrency */
+  uint32_t flags;       /* sr_candidates_device only: SR_FLAG_DEVICE = leave the list in device
+                           memory (flagged so, ready for sr_align_batch); sr_candidates: 0 */
 } sr_cand_params;
 
 typedef struct {
@@ -144,6 +146,8 @@ sr_status sr_candidates(const sr_index* const* idx, uint32_t n_refs, const sr_re
                         const sr_cand_params* params, sr_cand_list** out);
 /* Allocate an empty list the caller fills (for windows chosen elsewhere). */
 sr_status sr_cand_list_alloc(uint32_t n_reads, uint64_t n_cands, sr_cand_list** out);
+/* Frees a list the library allocated: host arrays, or device arrays when the
+ * list is flagged SR_FLAG_DEVICE. */
 void sr_cand_list_free(sr_cand_list* list);
 
 /* ---------------------------------------------------------------- scoring */
@@ -228,7 +232,12 @@ void sr_session_close(sr_session* s);
  * attached set is allowed.  sr_candidates_device then returns exactly the list
  * sr_candidates returns for those indexes (same windows, order and hits): one
  * warp per read looks up its seeds, one block per read sorts and merges its
- * CALs.  Reads longer than SR_MAX_READ_LEN are SR_EINVAL, non-ACGT bases
+ * CALs.  The reads may be host memory or, flagged SR_FLAG_DEVICE, device
+ * memory (read on the session's stream); params->flags = SR_FLAG_DEVICE leaves
+ * the list in device memory (its arrays device pointers, the list flagged
+ * SR_FLAG_DEVICE), so that reads, windows and the alignment stay on the device
+ * (sr_align_batch takes such a list as it is).  Reads longer than
+ * SR_MAX_READ_LEN or with decreasing offsets are SR_EINVAL, non-ACGT bases
  * SR_EBADBASE, no attached index SR_EINVAL.  params->n_threads is unused. */
 sr_status sr_session_attach_index(sr_session* s, const sr_index* const* idx, uint32_t n_refs);
 sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, const sr_cand_params* params,

@@ -90,9 +90,10 @@ struct SeedArgs {
   const uint64_t* read_off;
   uint32_t r0, nr;        // reads r0 .. r0 + nr
   uint32_t stride;
-  uint32_t* count;        // count pass: CALs per read (indexed r - r0)
+  uint32_t* count;        // count pass: an upper bound of the CALs of each read (indexed r - r0)
   const uint64_t* off;    // emit pass: first slot of each read (indexed r - r0)
   uint64_t* cals;         // emit pass
+  uint32_t* actual;       // emit pass: the CALs written for each read (indexed r - r0)
   uint32_t* status;
 };
 
@@ -110,12 +111,15 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
   const int k = a.di.k;
   for (uint32_t rr = blockIdx.x * kCalWarps + warp; rr < a.nr; rr += gridDim.x * kCalWarps) {
     const uint32_t r = a.r0 + rr;
-    const uint64_t o0 = a.read_off[r];
-    const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - o0);  // <= 256, checked on the host
+    const uint64_t o0 = a.read_off[r], o1 = a.read_off[r + 1];
+    const uint32_t m = static_cast<uint32_t>(o1 - o0);
     if (lane == 0) ctr[warp] = 0;
     __syncwarp();
     uint32_t n = 0;
-    if (load_codes(a.bases, o0, m, q, lane, a.status) && m >= static_cast<uint32_t>(k)) {
+    // offsets and lengths: checked on the host for host reads, here for device reads
+    const bool len_ok = o1 >= o0 && o1 - o0 <= static_cast<uint64_t>(kMaxReadLen);
+    if (!len_ok && lane == 0) atomicOr(a.status, kStBadRead);
+    if (len_ok && load_codes(a.bases, o0, m, q, lane, a.status) && m >= static_cast<uint32_t>(k)) {
       const uint64_t base = EMIT ? a.off[rr] : 0;
       // 32 seeds per round, one per lane; the matching entries of all of them
       // are then shared out over the warp (a repeat seed may have thousands)
@@ -130,7 +134,14 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
         for (int r2 = 0; r2 < a.di.n_refs; ++r2) {
           uint64_t lo = 0, hi = 0;
           if (live) lookup(a.di, r2, canon, &lo, &hi);
-          uint32_t cnt = static_cast<uint32_t>(hi - lo), sc = cnt;
+          uint32_t cnt = static_cast<uint32_t>(hi - lo);
+          if (!EMIT) {
+            // an entry gives one CAL unless the seed is its own reverse complement
+            // (then at most two): a bound that needs no entry loads
+            n += rori == 3u ? 2u * cnt : cnt;
+            continue;
+          }
+          uint32_t sc = cnt;
 #pragma unroll
           for (int off = 1; off < 32; off <<= 1) {
             const uint32_t x = __shfl_up_sync(FULL, sc, off);
@@ -175,6 +186,8 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
     if (!EMIT) {
       n = __reduce_add_sync(FULL, n);
       if (lane == 0) a.count[rr] = n;
+    } else if (lane == 0) {
+      a.actual[rr] = ctr[warp];
     }
     __syncwarp();
   }
@@ -210,7 +223,8 @@ struct FilterArgs {
   const uint64_t* read_off;
   uint32_t r0, nr;
   uint32_t merge_dist, pad, max_cands;
-  const uint32_t* count;  // CALs per read
+  const uint32_t* count;  // upper bound of the CALs of each read (routes it to a kernel, sizes its space)
+  const uint32_t* actual; // CALs of each read
   const uint64_t* off;    // first slot of each read in cals / the window arrays
   uint64_t* cals;
   uint32_t smem_cap;      // reads with more CALs are left to the large-read kernel
@@ -220,41 +234,118 @@ struct FilterArgs {
   uint32_t* wlen;
 };
 
-// the filter of one read (whole block); keys: its CALs, room for P keys
+// Block-wide exclusive prefix sum of one 64-bit value per thread; *total gets
+// the block's sum.  (Two 32-bit counts packed as high:low add without carries
+// while each total stays below 2^32.)
+__device__ uint64_t block_exscan(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t warp_sum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint64_t t = lane < nw ? warp_sum[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(FULL, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) warp_sum[lane] = t;
+  }
+  __syncthreads();
+  const uint64_t before = (w ? warp_sum[w - 1] : 0ull) + x - v;
+  *total = warp_sum[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+// The filter of one read (whole block).  keys has room for P CALs (P the power
+// of two at or above n) followed by the merge's work space: cal_filter_words(P)
+// words in all.
+//
+// The merge (Sec. 3.3) in parallel: in the sorted CALs, a window starts where
+// the (ref, strand) changes or the gap to the previous CAL exceeds merge_dist,
+// and a run of equal values starts where the value changes.  One prefix sum
+// numbers both; every run offers (length, position in its window) to its
+// window by an atomic max, so each window keeps its most frequent value and,
+// among equally frequent ones, the first (smallest) -- the rule a serial scan
+// of the sorted CALs applies.
 __device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, uint32_t n) {
   __shared__ uint32_t s_nw;
   const uint32_t r = a.r0 + rr;
   const uint64_t base = a.off[rr];
   const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - a.read_off[r]);
   const uint32_t P = pow2_at_least(n);
+  unsigned long long* wbest = reinterpret_cast<unsigned long long*>(keys + P);  // P per window
+  uint32_t* pos_run = reinterpret_cast<uint32_t*>(keys + 2 * P);                // P + 1 run starts
+  uint32_t* pos_win = pos_run + P + 1;                                          // P + 1 window starts
   for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) keys[i] = i < n ? a.cals[base + i] : kNoKey;
   __syncthreads();
   bitonic(keys, P);
-  // merge: consecutive CALs of one (ref, strand) at most merge_dist apart; the
-  // window keeps the most frequent value (first, i.e. smallest, on ties)
-  if (threadIdx.x == 0) {
-    uint32_t nw = 0;
-    for (uint32_t t = 0; t < n;) {
-      uint32_t u = t + 1;
-      while (u < n && (keys[u] >> 59) == (keys[t] >> 59) && keys[u] - keys[u - 1] <= a.merge_dist) ++u;
-      uint32_t best = 0;
-      uint64_t bk = keys[t];
-      for (uint32_t v = t; v < u;) {
-        uint32_t x = v;
-        while (x < u && keys[x] == keys[v]) ++x;
-        if (x - v > best) {
-          best = x - v;
-          bk = keys[v];
-        }
-        v = x;
-      }
-      a.wkey[base + nw] = bk;
-      a.whits[base + nw] = u - t;
-      ++nw;
-      t = u;
+  const uint32_t T = blockDim.x;
+  const uint32_t per = (n + T - 1) / T;  // each thread a contiguous slice of the sorted CALs
+  const uint32_t i0 = min(n, threadIdx.x * per), i1 = min(n, i0 + per);
+  const uint64_t md = a.merge_dist;
+  auto starts = [&](uint32_t i, bool* rs, bool* ws) {
+    const uint64_t k = keys[i];
+    if (i == 0) {
+      *rs = *ws = true;
+      return;
     }
-    s_nw = nw;
+    const uint64_t p = keys[i - 1];
+    *rs = k != p;
+    *ws = (k >> 59) != (p >> 59) || k - p > md;
+  };
+  uint64_t cnt = 0;
+  for (uint32_t i = i0; i < i1; ++i) {
+    bool rs, ws;
+    starts(i, &rs, &ws);
+    cnt += (static_cast<uint64_t>(ws) << 32) | static_cast<uint64_t>(rs);
   }
+  uint64_t tot = 0;
+  const uint64_t pre = block_exscan(cnt, &tot);
+  const uint32_t nruns = static_cast<uint32_t>(tot), nwin = static_cast<uint32_t>(tot >> 32);
+  {
+    uint32_t rk = static_cast<uint32_t>(pre), wk = static_cast<uint32_t>(pre >> 32);
+    for (uint32_t i = i0; i < i1; ++i) {
+      bool rs, ws;
+      starts(i, &rs, &ws);
+      if (rs) pos_run[rk++] = i;
+      if (ws) pos_win[wk++] = i;
+    }
+  }
+  if (threadIdx.x == 0) {
+    pos_run[nruns] = n;
+    pos_win[nwin] = n;
+  }
+  for (uint32_t j = threadIdx.x; j < nwin; j += T) wbest[j] = 0ull;
+  __syncthreads();
+  {
+    uint32_t rk = static_cast<uint32_t>(pre), wk = static_cast<uint32_t>(pre >> 32);
+    for (uint32_t i = i0; i < i1; ++i) {
+      bool rs, ws;
+      starts(i, &rs, &ws);
+      wk += ws ? 1u : 0u;
+      if (rs) {
+        const uint32_t w = wk - 1;  // the window holding this run
+        const uint32_t len = pos_run[rk + 1] - i, at = i - pos_win[w];
+        atomicMax(&wbest[w], (static_cast<unsigned long long>(len) << 32) | (0xffffffffu - at));
+        ++rk;
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < nwin; j += T) {
+    const uint32_t at = 0xffffffffu - static_cast<uint32_t>(wbest[j] & 0xffffffffull);
+    a.wkey[base + j] = keys[pos_win[j] + at];
+    a.whits[base + j] = pos_win[j + 1] - pos_win[j];
+  }
+  if (threadIdx.x == 0) s_nw = nwin;
   __syncthreads();
   uint32_t nw = s_nw;
   if (a.max_cands && nw > a.max_cands) {
@@ -301,7 +392,7 @@ __global__ void __launch_bounds__(256) k_cal_filter(FilterArgs a, uint32_t lo, u
   for (uint32_t rr = blockIdx.x; rr < a.nr; rr += gridDim.x) {
     const uint32_t n = a.count[rr];
     if (n < lo || n > hi) continue;
-    filter_read(a, rr, skeys, n);
+    filter_read(a, rr, skeys, a.actual[rr]);
   }
 }
 
@@ -309,7 +400,7 @@ __global__ void __launch_bounds__(256) k_cal_filter(FilterArgs a, uint32_t lo, u
 __global__ void __launch_bounds__(1024) k_cal_filter_big(FilterArgs a, const uint32_t* big, const uint64_t* soff,
                                                          uint64_t* scratch) {
   const uint32_t rr = big[blockIdx.x];
-  filter_read(a, rr, scratch + soff[blockIdx.x], a.count[rr]);
+  filter_read(a, rr, scratch + soff[blockIdx.x], a.actual[rr]);
 }
 
 __global__ void k_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,
@@ -334,10 +425,10 @@ __global__ void k_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* 
 }  // namespace
 
 int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
-                     uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* status,
-                     cudaStream_t st) {
+                     uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* actual,
+                     uint32_t* status, cudaStream_t st) {
   if (nr == 0) return 0;
-  SeedArgs a{di, bases, read_off, r0, nr, stride, count, off, cals, status};
+  SeedArgs a{di, bases, read_off, r0, nr, stride, count, off, cals, actual, status};
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -349,17 +440,17 @@ int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read
 }
 
 int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
-                      uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint64_t* off, uint64_t* cals,
-                      uint32_t max_small, uint32_t max_mid, const uint32_t* big, const uint64_t* big_soff,
-                      uint32_t n_big, uint64_t* scratch, uint32_t* nwin, uint64_t* wkey, uint32_t* whits,
-                      uint32_t* wlen, cudaStream_t st) {
+                      uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint32_t* actual,
+                      const uint64_t* off, uint64_t* cals, uint32_t max_small, uint32_t max_mid, const uint32_t* big,
+                      const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint32_t* nwin, uint64_t* wkey,
+                      uint32_t* whits, uint32_t* wlen, cudaStream_t st) {
   if (nr == 0) return 0;
-  FilterArgs a{di, read_off, r0, nr, merge_dist, pad, max_cands, count, off, cals, kCalSmemKeys,
+  FilterArgs a{di, read_off, r0, nr, merge_dist, pad, max_cands, count, actual, off, cals, kCalSmemKeys,
                nwin, wkey, whits, wlen};
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_cal_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kCalSmemKeys * sizeof(uint64_t))) != cudaSuccess)
+                             static_cast<int>(cal_filter_words(kCalSmemKeys) * sizeof(uint64_t))) != cudaSuccess)
       return -1;
     attr = true;
   }
@@ -372,15 +463,15 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
     return p;
   };
   int launched = 0;
-  // small reads: 8 KB or less of keys per block, many blocks per SM
+  // small reads: 24 KB or less of shared memory per block, many blocks per SM
   {
-    const size_t smem = static_cast<size_t>(p2(max_small)) * sizeof(uint64_t);
+    const size_t smem = static_cast<size_t>(cal_filter_words(p2(max_small))) * sizeof(uint64_t);
     const uint32_t grid = nr < static_cast<uint32_t>(nsm) * 32 ? nr : static_cast<uint32_t>(nsm) * 32;
     k_cal_filter<<<grid, 128, smem, st>>>(a, 0u, kCalSmallKeys);
     ++launched;
   }
   if (max_mid) {
-    const size_t smem = static_cast<size_t>(p2(max_mid)) * sizeof(uint64_t);
+    const size_t smem = static_cast<size_t>(cal_filter_words(p2(max_mid))) * sizeof(uint64_t);
     const uint32_t grid = static_cast<uint32_t>(nsm) * 2;
     k_cal_filter<<<grid, 256, smem, st>>>(a, kCalSmallKeys + 1, kCalSmemKeys);
     ++launched;
@@ -390,6 +481,16 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
     ++launched;
   }
   return cudaPeekAtLastError() == cudaSuccess ? launched : -1;
+}
+
+__global__ void k_cal_offsets(const uint32_t* woff, uint32_t nr, uint64_t base, uint64_t* out) {
+  const uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (i <= nr) out[i] = base + woff[i];
+}
+
+int launch_cal_offsets(const uint32_t* woff, uint32_t nr, uint64_t base, uint64_t* out, cudaStream_t st) {
+  k_cal_offsets<<<(nr + 256) / 256, 256, 0, st>>>(woff, nr, base, out);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,

@@ -9,6 +9,8 @@
 #include <thread>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "sr_host.h"
 #include "sr_seed.h"
 
@@ -383,6 +385,14 @@ extern "C" sr_status sr_cand_list_alloc(uint32_t n_reads, uint64_t n_cands, sr_c
 
 extern "C" void sr_cand_list_free(sr_cand_list* l) {
   if (!l) return;
+  if (l->flags & SR_FLAG_DEVICE) {
+    // a list sr_candidates_device left on the device
+    void* arrays[6] = {l->offsets, l->ref_id, l->strand, l->win_start, l->win_len, l->hits};
+    for (void* p : arrays)
+      if (p) cudaFree(p);
+    free(l);
+    return;
+  }
   free(l->offsets);
   free(l->ref_id);
   free(l->strand);

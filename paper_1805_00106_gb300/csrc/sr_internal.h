@@ -248,23 +248,31 @@ struct DevIndex {
   uint64_t hash_seed[kMaxRefs];
   int n_refs, k, a;
 };
-constexpr uint32_t kCalSmallKeys = 1024;  // reads up to this many CALs: small-block filter (8 KB)
-constexpr uint32_t kCalSmemKeys = 16384;  // up to this many: sorted in shared memory (128 KB)
-// count pass (cals == nullptr: CALs per read into count) or emit pass (CAL keys
-// of read r0 + i into cals[off[i] ...]) over reads r0 .. r0 + nr
+constexpr uint32_t kCalSmallKeys = 1024;  // reads up to this many CALs: small-block filter (24 KB)
+constexpr uint32_t kCalSmemKeys = 8192;   // up to this many: filtered in shared memory (192 KB)
+// shared or scratch words (u64) the filter of a read of up to P CALs uses (P a
+// power of two): its keys, each window's best run, run and window start positions
+constexpr uint64_t cal_filter_words(uint64_t P) { return 3 * P + 1; }
+// count pass (cals == nullptr: an upper bound of the CALs of each read into
+// count, exact unless a seed is its own reverse complement; reads with bad
+// offsets or over kMaxReadLen bases set kStBadRead) or emit pass (CAL keys of
+// read r0 + i into cals[off[i] ...], their number into actual[i]) over reads
+// r0 .. r0 + nr
 int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
-                     uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* status,
-                     cudaStream_t st);
+                     uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* actual,
+                     uint32_t* status, cudaStream_t st);
 // windows of each read at off[i] (nwin[i] of them).  Reads with up to
 // kCalSmallKeys CALs (largest: max_small) and up to kCalSmemKeys (largest:
 // max_mid, 0 = none) sort in shared memory; the n_big others (device list big
 // of indices into the chunk) sort in scratch from slot big_soff[b] (pow2 of
 // their count each)
 int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
-                      uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint64_t* off, uint64_t* cals,
-                      uint32_t max_small, uint32_t max_mid, const uint32_t* big, const uint64_t* big_soff,
-                      uint32_t n_big, uint64_t* scratch, uint32_t* nwin, uint64_t* wkey, uint32_t* whits,
-                      uint32_t* wlen, cudaStream_t st);
+                      uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint32_t* actual,
+                      const uint64_t* off, uint64_t* cals, uint32_t max_small, uint32_t max_mid, const uint32_t* big,
+                      const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint32_t* nwin, uint64_t* wkey,
+                      uint32_t* whits, uint32_t* wlen, cudaStream_t st);
+// out[i] = base + woff[i] for i = 0 .. nr (a chunk's window offsets in the whole list)
+int launch_cal_offsets(const uint32_t* woff, uint32_t nr, uint64_t base, uint64_t* out, cudaStream_t st);
 int launch_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,
                        const uint64_t* wkey, const uint32_t* whits, const uint32_t* wlen, uint8_t* o_ref,
                        uint8_t* o_strand, uint64_t* o_start, uint32_t* o_len, uint32_t* o_hits, cudaStream_t st);

@@ -1355,52 +1355,127 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
   if (!s || !reads || !out) return set_error(SR_EINVAL, "sr_candidates_device: null argument");
   *out = nullptr;
   if (s->didx.n_refs == 0) return set_error(SR_EINVAL, "sr_candidates_device: no index attached to the session");
-  if (reads->flags) return set_error(SR_EINVAL, "sr_candidates_device: reads must be in host memory (flags 0)");
   sr_cand_params cp{};
   if (params) cp = *params;
   if (!cp.seed_stride) cp.seed_stride = 1;
+  if ((reads->flags | cp.flags) & ~static_cast<uint32_t>(SR_FLAG_DEVICE))
+    return set_error(SR_EINVAL, "sr_candidates_device: unknown flags");
+  const bool in_dev = (reads->flags & SR_FLAG_DEVICE) != 0, out_dev = (cp.flags & SR_FLAG_DEVICE) != 0;
   const uint32_t n = reads->n_reads;
-  if (n && (!reads->bases || !reads->offsets)) return set_error(SR_EINVAL, "sr_candidates_device: null reads");
-  if (n && reads->offsets[0] != 0) return set_error(SR_EINVAL, "sr_candidates_device: offsets must start at 0");
-  for (uint32_t r = 0; r < n; ++r) {
-    if (reads->offsets[r + 1] < reads->offsets[r])
-      return set_error(SR_EINVAL, "sr_candidates_device: decreasing read offsets");
-    if (reads->offsets[r + 1] - reads->offsets[r] > SR_MAX_READ_LEN)
-      return set_error(SR_EINVAL, "sr_candidates_device: read %u longer than %u bases", r, SR_MAX_READ_LEN);
+  if (!reads->offsets || (n && !reads->bases)) return set_error(SR_EINVAL, "sr_candidates_device: null reads");
+  cudaStream_t st = s->stream;
+  uint64_t nb = 0;
+  if (in_dev) {
+    // the read lengths are checked by the count kernel
+    uint64_t ends[2] = {};
+    cudaError_t e = cudaMemcpyAsync(&ends[0], reads->offsets, 8, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], reads->offsets + n, 8, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error("sr_candidates_device offsets", e);
+    if (ends[0] != 0) return set_error(SR_EINVAL, "sr_candidates_device: offsets must start at 0");
+    nb = ends[1];
+    if (nb > static_cast<uint64_t>(n) * SR_MAX_READ_LEN)
+      return set_error(SR_EINVAL, "sr_candidates_device: some read is longer than %u bases", SR_MAX_READ_LEN);
+  } else {
+    if (reads->offsets[0] != 0) return set_error(SR_EINVAL, "sr_candidates_device: offsets must start at 0");
+    for (uint32_t r = 0; r < n; ++r) {
+      if (reads->offsets[r + 1] < reads->offsets[r])
+        return set_error(SR_EINVAL, "sr_candidates_device: decreasing read offsets");
+      if (reads->offsets[r + 1] - reads->offsets[r] > SR_MAX_READ_LEN)
+        return set_error(SR_EINVAL, "sr_candidates_device: read %u longer than %u bases", r, SR_MAX_READ_LEN);
+    }
+    nb = reads->offsets[n];
   }
-  std::vector<uint64_t> offsets(n + 1ull, 0);
+  std::vector<void*> bufs;
+  cudaError_t e = cudaSuccess;
+  auto dalloc = [&](uint64_t bytes) -> void* {
+    void* d = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d, bytes ? bytes : 1);
+    if (e == cudaSuccess) bufs.push_back(d);
+    return e == cudaSuccess ? d : nullptr;
+  };
+  // the result list: host arrays, or device arrays grown chunk by chunk
+  sr_cand_list* l = static_cast<sr_cand_list*>(calloc(1, sizeof(sr_cand_list)));
+  if (!l) return set_error(SR_ENOMEM, "sr_candidates_device: out of memory");
+  l->n_reads = n;
+  l->flags = out_dev ? static_cast<uint32_t>(SR_FLAG_DEVICE) : 0u;
+  uint64_t cap_out = 0;  // windows the device result arrays hold
+  auto done = [&](sr_status stt, const char* msg) -> sr_status {
+    cudaStreamSynchronize(st);
+    for (auto* p : bufs) cudaFree(p);
+    cudaGetLastError();
+    if (stt == SR_OK) return static_cast<sr_status>(SR_OK);
+    sr_cand_list_free(l);
+    if (stt == SR_ECUDA) return cuda_error(msg, e == cudaSuccess ? cudaErrorUnknown : e);
+    return set_error(stt, "%s", msg);
+  };
+  std::vector<uint64_t> offsets;
   std::vector<uint8_t> o_ref, o_strand;
   std::vector<uint64_t> o_start;
   std::vector<uint32_t> o_len, o_hits;
-  if (n) {
-    cudaStream_t st = s->stream;
-    const uint64_t nb = reads->offsets[n];
-    std::vector<void*> bufs;
-    cudaError_t e = cudaSuccess;
-    auto dalloc = [&](uint64_t bytes) -> void* {
-      void* d = nullptr;
-      if (e == cudaSuccess) e = cudaMalloc(&d, bytes ? bytes : 1);
-      if (e == cudaSuccess) bufs.push_back(d);
-      return e == cudaSuccess ? d : nullptr;
-    };
-    auto done = [&](sr_status stt, const char* msg) -> sr_status {
-      cudaStreamSynchronize(st);
-      for (auto* p : bufs) cudaFree(p);
+  if (out_dev) {
+    if (cudaMalloc(&l->offsets, (n + 1ull) * 8) != cudaSuccess) {
+      e = cudaGetLastError();
+      return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+    }
+    if (n == 0 && cudaMemsetAsync(l->offsets, 0, 8, st) != cudaSuccess) {
+      e = cudaGetLastError();
+      return done(SR_ECUDA, "sr_candidates_device offsets");
+    }
+  } else {
+    offsets.assign(n + 1ull, 0);
+  }
+  // grows the device result arrays to hold `need` windows, keeping the first `keep`
+  auto grow_out = [&](uint64_t need, uint64_t keep) -> bool {
+    if (need <= cap_out) return true;
+    const uint64_t c = std::max<uint64_t>(need, cap_out + cap_out / 2);
+    void *r8 = nullptr, *s8 = nullptr, *st64 = nullptr, *ln32 = nullptr, *h32 = nullptr;
+    bool ok = cudaMalloc(&r8, c) == cudaSuccess && cudaMalloc(&s8, c) == cudaSuccess &&
+              cudaMalloc(&st64, c * 8) == cudaSuccess && cudaMalloc(&ln32, c * 4) == cudaSuccess &&
+              cudaMalloc(&h32, c * 4) == cudaSuccess;
+    if (ok && keep) {
+      ok = cudaMemcpyAsync(r8, l->ref_id, keep, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(s8, l->strand, keep, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(st64, l->win_start, keep * 8, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(ln32, l->win_len, keep * 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaMemcpyAsync(h32, l->hits, keep * 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    void* old[5] = {l->ref_id, l->strand, l->win_start, l->win_len, l->hits};
+    void* fresh[5] = {r8, s8, st64, ln32, h32};
+    if (!ok) {
+      for (void* p : fresh)
+        if (p) cudaFree(p);
       cudaGetLastError();
-      if (stt == SR_OK) return static_cast<sr_status>(SR_OK);
-      if (stt == SR_ECUDA) return cuda_error(msg, e == cudaSuccess ? cudaErrorUnknown : e);
-      return set_error(stt, "%s", msg);
-    };
-    char* d_bases = static_cast<char*>(dalloc(nb));
-    uint64_t* d_roff = static_cast<uint64_t*>(dalloc((n + 1ull) * 8));
+      return false;
+    }
+    for (void* p : old)
+      if (p) cudaFree(p);
+    l->ref_id = static_cast<uint8_t*>(r8);
+    l->strand = static_cast<uint8_t*>(s8);
+    l->win_start = static_cast<uint64_t*>(st64);
+    l->win_len = static_cast<uint32_t*>(ln32);
+    l->hits = static_cast<uint32_t*>(h32);
+    cap_out = c;
+    return true;
+  };
+  uint64_t total_w = 0;
+  if (n) {
+    const char* d_bases = in_dev ? reads->bases : static_cast<const char*>(dalloc(nb));
+    const uint64_t* d_roff = in_dev ? reads->offsets : static_cast<const uint64_t*>(dalloc((n + 1ull) * 8));
     uint32_t* d_count = static_cast<uint32_t*>(dalloc(n * 4ull));
+    uint32_t* d_actual = static_cast<uint32_t*>(dalloc(n * 4ull));
     uint32_t* d_status = static_cast<uint32_t*>(dalloc(4));
     if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-    if (nb) e = cudaMemcpyAsync(d_bases, reads->bases, nb, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_roff, reads->offsets, (n + 1ull) * 8, cudaMemcpyHostToDevice, st);
+    if (!in_dev) {
+      if (nb) e = cudaMemcpyAsync(const_cast<char*>(d_bases), reads->bases, nb, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<uint64_t*>(d_roff), reads->offsets, (n + 1ull) * 8, cudaMemcpyHostToDevice, st);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 4, st);
     if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
-    if (launch_cal_seeds(s->didx, d_bases, d_roff, 0, n, cp.seed_stride, d_count, nullptr, nullptr, d_status, st) < 0) {
+    if (launch_cal_seeds(s->didx, d_bases, d_roff, 0, n, cp.seed_stride, d_count, nullptr, nullptr, nullptr,
+                         d_status, st) < 0) {
       e = cudaGetLastError();
       return done(SR_ECUDA, "sr_candidates_device count");
     }
@@ -1410,9 +1485,12 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device count copy");
+    if (status & kStBadRead) return done(SR_EINVAL, "sr_candidates_device: decreasing read offsets or a read longer than 256 bases");
     if (status & kStBadBase) return done(SR_EBADBASE, "sr_candidates_device: read has a non-ACGT base");
-    // chunks of reads whose CALs fit the buffers
-    uint64_t cap = 16ull << 20;
+    // chunks of reads whose CALs (upper bounds) fit the buffers
+    uint64_t sum = 0;
+    for (uint32_t r = 0; r < n; ++r) sum += count[r];
+    uint64_t cap = std::min<uint64_t>(std::max<uint64_t>(sum, 1), 64ull << 20);
     for (uint32_t r = 0; r < n; ++r) cap = std::max<uint64_t>(cap, count[r]);
     uint64_t* d_cals = static_cast<uint64_t*>(dalloc(cap * 8));
     uint64_t* d_wkey = static_cast<uint64_t*>(dalloc(cap * 8));
@@ -1433,8 +1511,7 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     uint64_t* d_scratch = nullptr;
     uint64_t scratch_keys = 0;
     std::vector<uint64_t> off(n), bigoff;
-    std::vector<uint32_t> big, woff;
-    uint64_t total_w = 0;
+    std::vector<uint32_t> big;
     for (uint32_t r0 = 0; r0 < n;) {
       uint32_t r1 = r0;
       uint64_t used = 0;
@@ -1450,7 +1527,7 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
           while (p2 < count[r1]) p2 <<= 1;
           big.push_back(r1 - r0);
           bigoff.push_back(big_keys);
-          big_keys += p2;
+          big_keys += cal_filter_words(p2);
         } else if (count[r1] > kCalSmallKeys) {
           max_mid = std::max(max_mid, count[r1]);
         } else {
@@ -1472,56 +1549,94 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
           e = cudaMemcpyAsync(d_bigoff, bigoff.data(), bigoff.size() * 8ull, cudaMemcpyHostToDevice, st);
       }
       if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
-      if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_status, st) < 0 ||
-          launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_off, d_cals,
-                            max_small, max_mid, d_big, d_bigoff, static_cast<uint32_t>(big.size()), d_scratch,
-                            d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
+      if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_actual,
+                           d_status, st) < 0 ||
+          launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_actual,
+                            d_off, d_cals, max_small, max_mid, d_big, d_bigoff, static_cast<uint32_t>(big.size()),
+                            d_scratch, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
           launch_scan_u32(d_nwin, nr, d_woff, d_sums, st) < 0) {
         e = cudaGetLastError();
         return done(SR_ECUDA, "sr_candidates_device filter");
       }
-      woff.resize(nr + 1ull);
-      e = cudaMemcpyAsync(woff.data(), d_woff, (nr + 1ull) * 4, cudaMemcpyDeviceToHost, st);
+      uint32_t nw32 = 0;
+      std::vector<uint32_t> woff;
+      if (out_dev) {
+        e = cudaMemcpyAsync(&nw32, d_woff + nr, 4, cudaMemcpyDeviceToHost, st);
+      } else {
+        woff.resize(nr + 1ull);
+        e = cudaMemcpyAsync(woff.data(), d_woff, (nr + 1ull) * 4, cudaMemcpyDeviceToHost, st);
+      }
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window count");
-      const uint64_t nw = woff[nr];
+      const uint64_t nw = out_dev ? nw32 : woff[nr];
       if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, d_oref, d_ostr, d_ostart, d_olen,
                              d_ohits, st) < 0) {
         e = cudaGetLastError();
         return done(SR_ECUDA, "sr_candidates_device compact");
       }
-      o_ref.resize(total_w + nw);
-      o_strand.resize(total_w + nw);
-      o_start.resize(total_w + nw);
-      o_len.resize(total_w + nw);
-      o_hits.resize(total_w + nw);
-      if (nw) {
-        e = cudaMemcpyAsync(o_ref.data() + total_w, d_oref, nw, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(o_strand.data() + total_w, d_ostr, nw, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(o_start.data() + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(o_len.data() + total_w, d_olen, nw * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(o_hits.data() + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
+      if (out_dev) {
+        // this chunk's offsets in the whole list, its windows appended on the device
+        if (launch_cal_offsets(d_woff, nr, total_w, l->offsets + r0, st) < 0) {
+          e = cudaGetLastError();
+          return done(SR_ECUDA, "sr_candidates_device offsets");
+        }
+        if (!grow_out(total_w + nw, total_w)) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+        if (nw) {
+          e = cudaMemcpyAsync(l->ref_id + total_w, d_oref, nw, cudaMemcpyDeviceToDevice, st);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(l->strand + total_w, d_ostr, nw, cudaMemcpyDeviceToDevice, st);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(l->win_start + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToDevice, st);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(l->win_len + total_w, d_olen, nw * 4, cudaMemcpyDeviceToDevice, st);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(l->hits + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToDevice, st);
+          if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
+        }
+      } else {
+        o_ref.resize(total_w + nw);
+        o_strand.resize(total_w + nw);
+        o_start.resize(total_w + nw);
+        o_len.resize(total_w + nw);
+        o_hits.resize(total_w + nw);
+        if (nw) {
+          e = cudaMemcpyAsync(o_ref.data() + total_w, d_oref, nw, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(o_strand.data() + total_w, d_ostr, nw, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(o_start.data() + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(o_len.data() + total_w, d_olen, nw * 4, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(o_hits.data() + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+          if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
+        }
+        for (uint32_t i = 0; i <= nr; ++i) offsets[r0 + i] = total_w + woff[i];
       }
-      for (uint32_t i = 0; i <= nr; ++i) offsets[r0 + i] = total_w + woff[i];
       total_w += nw;
       r0 = r1;
     }
+    // the chunk buffers are freed below; the device result arrays must be complete first
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device");
+  }
+  l->n_cands = total_w;
+  if (out_dev) {
+    if (!grow_out(std::max<uint64_t>(total_w, 1), total_w)) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
     sr_status stt = done(SR_OK, "");
     if (stt != SR_OK) return stt;
+    *out = l;
+    return SR_OK;
   }
-  const uint64_t total = offsets[n];
-  sr_cand_list* l = nullptr;
-  sr_status st2 = sr_cand_list_alloc(n, total, &l);
+  sr_status stt = done(SR_OK, "");
+  if (stt != SR_OK) return stt;
+  sr_cand_list_free(l);
+  l = nullptr;
+  sr_status st2 = sr_cand_list_alloc(n, total_w, &l);
   if (st2 != SR_OK) return st2;
   std::memcpy(l->offsets, offsets.data(), (n + 1ull) * 8);
-  if (total) {
-    std::memcpy(l->ref_id, o_ref.data(), total);
-    std::memcpy(l->strand, o_strand.data(), total);
-    std::memcpy(l->win_start, o_start.data(), total * 8);
-    std::memcpy(l->win_len, o_len.data(), total * 4);
-    std::memcpy(l->hits, o_hits.data(), total * 4);
+  if (total_w) {
+    std::memcpy(l->ref_id, o_ref.data(), total_w);
+    std::memcpy(l->strand, o_strand.data(), total_w);
+    std::memcpy(l->win_start, o_start.data(), total_w * 8);
+    std::memcpy(l->win_len, o_len.data(), total_w * 4);
+    std::memcpy(l->hits, o_hits.data(), total_w * 4);
   }
   *out = l;
   return SR_OK;

@@ -46,7 +46,7 @@ class Reads(C.Structure):
 
 class CandParams(C.Structure):
     _fields_ = [("seed_stride", C.c_uint32), ("merge_dist", C.c_uint32), ("pad", C.c_uint32),
-                ("max_cands", C.c_uint32), ("n_threads", C.c_uint32)]
+                ("max_cands", C.c_uint32), ("n_threads", C.c_uint32), ("flags", C.c_uint32)]
 
 
 class CandList(C.Structure):
@@ -409,7 +409,7 @@ def candidates(indexes, bases, read_off, seed_stride=1, merge_dist=32, pad=32, m
     keep = _Keep()
     reads = make_reads(bases, read_off, keep)
     arr = (P * len(indexes))(*[ix.h for ix in indexes])
-    cp = CandParams(seed_stride, merge_dist, pad, max_cands, threads)
+    cp = CandParams(seed_stride, merge_dist, pad, max_cands, threads, 0)
     out = C.POINTER(CandList)()
     _check(lib().sr_candidates(C.cast(arr, P), len(indexes), C.byref(reads), C.byref(cp), C.byref(out)))
     return _cand_list_to_numpy(out)
@@ -432,6 +432,51 @@ def _cand_list_to_numpy(out):
         res["cand_off"] = np.zeros(n + 1, np.int64)
     lib().sr_cand_list_free(out)
     return res
+
+
+class _CudaArray:
+    """A device array of the library seen through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr, n, typestr, owner):
+        self.owner = owner
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2}
+
+
+class DeviceCandList:
+    """An sr_cand_list whose arrays sit in device memory (sr_candidates_device with
+    SR_FLAG_DEVICE); freed with sr_cand_list_free when this object goes away."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+        l = ptr.contents
+        self.n_reads, self.n_cands = int(l.n_reads), int(l.n_cands)
+        assert l.flags & FLAG_DEVICE
+
+    def tensors(self):
+        """The arrays as CUDA tensors sharing the list's memory (kept alive by them)."""
+        import torch
+        l = self.ptr.contents
+        n, nc = self.n_reads, self.n_cands
+        v = lambda p, k, t: torch.as_tensor(_CudaArray(C.cast(p, C.c_void_p).value, k, t, self), device="cuda")
+        return dict(cand_off=v(l.offsets, n + 1, "<u8"), c_ref=v(l.ref_id, nc, "|u1"), c_strand=v(l.strand, nc, "|u1"),
+                    c_start=v(l.win_start, nc, "<u8"), c_len=v(l.win_len, nc, "<u4"), c_hits=v(l.hits, nc, "<u4"))
+
+    def to_numpy(self):
+        """A host copy in the layout candidates() returns."""
+        t = self.tensors()
+        out = {k: x.cpu().numpy() for k, x in t.items()}
+        out["cand_off"] = out["cand_off"].astype(np.int64)
+        out["c_start"] = out["c_start"].astype(np.int64)
+        out["c_len"] = out["c_len"].astype(np.int32)
+        return out
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                lib().sr_cand_list_free(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
 
 
 class Batch:
@@ -553,18 +598,31 @@ class Session:
                                     C.byref(opts or align_opts()), C.byref(out)))
         return results_to_numpy(out)
 
+    def align_cands(self, bases, read_off, cands, sp=None, opts=None):
+        """sr_align_batch with the windows of a DeviceCandList (left on the device by
+        candidates(..., out_device=True)); the reads are numpy arrays or CUDA tensors."""
+        keep = _Keep()
+        reads = make_reads_device(bases, read_off) if hasattr(bases, "data_ptr") else make_reads(bases, read_off, keep)
+        out = C.POINTER(Results)()
+        _check(lib().sr_align_batch(self.h, C.byref(reads), cands.ptr, C.byref(sp or score_params()),
+                                    C.byref(opts or align_opts()), C.byref(out)))
+        return results_to_numpy(out)
+
     # device CAL finder (Sec. 3.2-3.3 on the GPU)
     def attach_index(self, indexes):
         arr = (P * len(indexes))(*[ix.h for ix in indexes])
         _check(lib().sr_session_attach_index(self.h, C.cast(arr, P), len(indexes)))
 
-    def candidates(self, bases, read_off, seed_stride=1, merge_dist=32, pad=32, max_cands=0):
+    def candidates(self, bases, read_off, seed_stride=1, merge_dist=32, pad=32, max_cands=0, out_device=False):
+        """Device CAL finder.  bases / read_off: numpy arrays, or CUDA tensors (uint8,
+        int64) already on the device.  Returns numpy arrays, or with out_device a
+        DeviceCandList whose arrays stay in device memory."""
         keep = _Keep()
-        reads = make_reads(bases, read_off, keep)
-        cp = CandParams(seed_stride, merge_dist, pad, max_cands, 0)
+        reads = make_reads_device(bases, read_off) if hasattr(bases, "data_ptr") else make_reads(bases, read_off, keep)
+        cp = CandParams(seed_stride, merge_dist, pad, max_cands, 0, FLAG_DEVICE if out_device else 0)
         out = C.POINTER(CandList)()
         _check(lib().sr_candidates_device(self.h, C.byref(reads), C.byref(cp), C.byref(out)))
-        return _cand_list_to_numpy(out)
+        return DeviceCandList(out) if out_device else _cand_list_to_numpy(out)
 
     # serving
     def serve_start(self, sp=None, opts=None, max_inflight=0):

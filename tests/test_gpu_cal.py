@@ -66,13 +66,18 @@ def test_device_matches_bruteforce_oracle(sr):
 
 def test_reads_with_very_many_cals(sr):
     """A tandem repeat gives reads tens of thousands of CALs: the large-read
-    filter (global-memory sort) must agree with the host too."""
+    filter (global-memory sort) must agree with the host too; a shorter one
+    (60 copies) gives a few thousand, the shared-memory filter of mid-size reads."""
     rng = np.random.default_rng(11)
     unit = rng.choice(np.frombuffer(b"ACGT", np.uint8), 23)
+    unit2 = rng.choice(np.frombuffer(b"ACGT", np.uint8), 31)
     ref = np.concatenate([rng.choice(np.frombuffer(b"ACGT", np.uint8), 2000), np.tile(unit, 900),
-                          rng.choice(np.frombuffer(b"ACGT", np.uint8), 2000)])
+                          rng.choice(np.frombuffer(b"ACGT", np.uint8), 2000), np.tile(unit2, 60),
+                          rng.choice(np.frombuffer(b"ACGT", np.uint8), 500)])
+    t2 = 2000 + 23 * 900 + 2000  # start of the 60-copy repeat
     reads, offs = [], [0]
-    for st, m in [(2500, 200), (3000, 256), (100, 100), (2100, 60), (20000, 120)]:
+    for st, m in [(2500, 200), (3000, 256), (100, 100), (2100, 60), (20000, 120), (t2 + 200, 150),
+                  (t2 - 40, 100)]:
         reads.append(ref[st:st + m])
         offs.append(offs[-1] + m)
     bases = np.concatenate(reads)
@@ -87,6 +92,8 @@ def test_reads_with_very_many_cals(sr):
             # one window per repeat copy: ~900 windows from ~200k CALs (the large-read path)
             assert int(np.max(np.diff(h["cand_off"]))) > 500
             assert int(np.max(h["c_hits"])) > 100
+            # the read inside the 60-copy repeat: 131 seeds x 60 copies, between the small and large paths
+            assert 30 <= int(np.diff(h["cand_off"])[5]) <= 120
 
 
 def test_device_candidates_errors_and_empty(sr):
@@ -109,3 +116,46 @@ def test_device_candidates_errors_and_empty(sr):
     assert e.value.status == sr.SR_EINVAL
     d = s.candidates(np.zeros(0, np.uint8), np.zeros(1, np.int64))
     assert len(d["cand_off"]) == 1 and len(d["c_ref"]) == 0
+
+
+def _dev(a, dt):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+
+
+def test_device_reads_and_device_list(sr):
+    """Reads already in device memory and the list left in device memory give
+    the host stage's windows; the device list feeds sr_align_batch as it is,
+    with the results of the all-host pipeline."""
+    import torch
+    w = S.workload("c3", scale=0.002, seed=23, rc_frac=0.5)
+    idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=10, cal_limit=1024) for r in w["refs"]]
+    s = sr.Session.from_indexes(idx)
+    s.attach_index(idx)
+    prm = dict(seed_stride=1, merge_dist=32, pad=32)
+    h = sr.candidates(idx, w["bases"], w["read_off"], **prm)
+    db, do = _dev(w["bases"], np.uint8), _dev(w["read_off"], np.int64)
+    torch.cuda.synchronize()
+    _same(s.candidates(db, do, **prm), h)                               # device reads, host list
+    dl = s.candidates(w["bases"], w["read_off"], out_device=True, **prm)  # host reads, device list
+    assert dl.n_cands == len(h["c_ref"]) and dl.n_reads == len(w["read_off"]) - 1
+    _same(dl.to_numpy(), h)
+    dl2 = s.candidates(db, do, out_device=True, **prm)                   # both on the device
+    _same(dl2.to_numpy(), h)
+    opts = sr.align_opts(classify=True)
+    ref = s.align(w["bases"], w["read_off"], h["cand_off"], h["c_ref"], h["c_strand"], h["c_start"], h["c_len"],
+                  sr.score_params(), opts)
+    for g in (s.align_cands(db, do, dl2, sr.score_params(), opts),
+              s.align_cands(w["bases"], w["read_off"], dl, sr.score_params(), opts)):
+        for k in ["item_score", "item_end", "cigar", "read_class"]:
+            assert np.array_equal(g[k], ref[k]), k
+        assert np.array_equal(g["best"], ref["best"]) and np.array_equal(g["best_per_ref"], ref["best_per_ref"])
+    # an empty batch and a read too long, from device reads
+    e0 = s.candidates(_dev(np.zeros(0, np.uint8), np.uint8), _dev(np.zeros(1, np.int64), np.int64), out_device=True)
+    assert e0.n_cands == 0 and e0.n_reads == 0
+    lo = np.concatenate([w["read_off"], [w["read_off"][-1] + 300]])
+    long = np.concatenate([w["bases"], np.full(300, ord("A"), np.uint8)])
+    torch.cuda.synchronize()
+    with pytest.raises(sr.SrError) as e:
+        s.candidates(_dev(long, np.uint8), _dev(lo, np.int64))
+    assert e.value.status == sr.SR_EINVAL

@@ -473,6 +473,21 @@ def xenograft_bench(sr, stream, scale=1.0, steps=5):
     cd = sess.candidates(w["bases"], w["read_off"], **prm)
     t_cal = time.perf_counter() - t0
     spp = sr.score_params(*SP)
+    # the whole pipeline with its intermediate on the device: reads (already in HBM)
+    # -> device CAL finder -> window list in HBM -> sr_align_batch -> results on the host
+    import torch
+    db = torch.from_numpy(np.ascontiguousarray(w["bases"], np.uint8)).cuda()
+    do = torch.from_numpy(np.ascontiguousarray(w["read_off"], np.int64)).cuda()
+    popts = sr.align_opts(classify=True, min_score=40, margin=5)
+    pipe = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dl = sess.candidates(db, do, out_device=True, **prm)
+        sess.align_cands(db, do, dl, spp, popts)
+        pipe.append(time.perf_counter() - t0)
+        del dl
+    t_pipe = statistics.median(pipe)
     opts = sr.align_opts(classify=True, min_score=40, margin=5, stream=stream.cuda_stream)
     b = sess.stage(w["bases"], w["read_off"], cd["cand_off"], cd["c_ref"], cd["c_strand"], cd["c_start"],
                    cd["c_len"], stream=stream.cuda_stream)
@@ -490,6 +505,9 @@ def xenograft_bench(sr, stream, scale=1.0, steps=5):
            "gcups": round(cells / tot * 1e3 / 1e9, 1), "reads_per_s": round(n / tot * 1e3, 1),
            "ms": round(tot, 3), "extension_ms": round(ext, 3), "traceback_ms": round(tb, 3),
            "cal_finder_ms": round(1e3 * t_cal, 2), "index_build_s": round(t_index, 1),
+           "pipeline": {"what": "reads in HBM -> device CAL finder -> windows kept in HBM -> sr_align_batch "
+                                "(classification) -> results on the host", "ms": round(1e3 * t_pipe, 2),
+                        "reads_per_s": round(n / t_pipe, 1)},
            "cals_per_read": round(float(cnt.mean()), 3),
            "cals_per_read_quantiles": {q: int(np.quantile(cnt, v)) for q, v in
                                        [("p50", 0.5), ("p90", 0.9), ("p99", 0.99), ("max", 1.0)]},

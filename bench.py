@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cal", action="store_true", help="skip the CAL finder comparison")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the xenograft and repeat-heavy workloads (full size by default)")
+    ap.add_argument("--only", choices=["xenograft", "repeat_heavy"],
+                    help="run only this workload's leg at --scale and print its JSON (profiling)")
     ap.add_argument("--sweep", action="store_true",
                     help="seed length x CAL limit sweep on the xenograft and repeat-heavy workloads "
                          "(one JSON line per setting) instead of the bench line")
@@ -595,6 +597,13 @@ def main():
         return
     if args.sweep:
         sweep(args)
+        return
+    if args.only:
+        import torch
+        from paper_1805_00106_gb300 import sr
+        stream = torch.cuda.Stream()
+        leg = xenograft_bench if args.only == "xenograft" else repeat_bench
+        print(json.dumps({args.only: leg(sr, stream, args.scale)}), flush=True)
         return
     import torch
     from paper_1805_00106_gb300 import sr

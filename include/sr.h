@@ -372,7 +372,8 @@ sr_status sr_batch_classify(sr_session* s, sr_batch* b, const sr_classify_params
  * Sec. 4.2): sr_submit copies a request and returns a ticket at once.  A
  * scheduler thread admits queued requests in arrival order while their device
  * footprint fits the session's hbm_budget, merges them into the next device
- * round (up to 131072 reads; a single larger request runs alone), stages it and
+ * round (up to 131072 reads and half the budget; a single larger request runs
+ * alone), stages it and
  * launches all its kernels on a stream of its own while the previous round is
  * still on the device: two rounds are in flight at once.  The new round's read
  * packing and length binning run beside the previous round's last kernels; its

@@ -95,7 +95,39 @@ struct SeedArgs {
   uint64_t* cals;         // emit pass
   uint32_t* actual;       // emit pass: the CALs written for each read (indexed r - r0)
   uint32_t* status;
+  // Seed lookups kept from the count pass for the emit pass (nullptr: the emit
+  // pass looks its seeds up again): per read (indexed r - rbase) its records
+  // start at seed_off, one per (seed, reference) in that order; recount (per
+  // read) marks the reads whose records could not hold a lookup
+  uint64_t* ranges;
+  const uint32_t* seed_off;
+  uint8_t* recount;
+  uint32_t rbase;
 };
+
+// a kept lookup: first matching entry (38 bits), their number (24 bits) and the
+// seed's orientation bits (2)
+constexpr uint32_t kRangeCntMax = (1u << 24) - 1u;
+constexpr uint64_t kRangeLoMax = (1ull << 38) - 1ull;
+__device__ __forceinline__ uint64_t range_pack(uint64_t lo, uint32_t cnt, uint32_t rori) {
+  return (lo << 26) | (static_cast<uint64_t>(cnt) << 2) | rori;
+}
+
+// seeds x references of each read (the lookup records the count pass keeps);
+// reads with decreasing offsets or over kMaxReadLen bases set kStBadRead
+__global__ void k_cal_slots(const uint64_t* read_off, uint32_t n, int k, uint32_t stride, int n_refs,
+                            uint32_t* slots, uint32_t* status) {
+  const uint64_t r = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (r >= n) return;
+  const uint64_t o0 = read_off[r], o1 = read_off[r + 1];
+  if (o1 < o0 || o1 - o0 > static_cast<uint64_t>(kMaxReadLen)) {
+    atomicOr(status, kStBadRead);
+    slots[r] = 0;
+    return;
+  }
+  const uint32_t m = static_cast<uint32_t>(o1 - o0);
+  slots[r] = m >= static_cast<uint32_t>(k) ? ((m - k) / stride + 1u) * static_cast<uint32_t>(n_refs) : 0u;
+}
 
 template <bool EMIT>
 __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
@@ -119,26 +151,49 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
     // offsets and lengths: checked on the host for host reads, here for device reads
     const bool len_ok = o1 >= o0 && o1 - o0 <= static_cast<uint64_t>(kMaxReadLen);
     if (!len_ok && lane == 0) atomicOr(a.status, kStBadRead);
-    if (len_ok && load_codes(a.bases, o0, m, q, lane, a.status) && m >= static_cast<uint32_t>(k)) {
+    // the emit pass takes the count pass's lookups when they were kept for this read
+    const bool kept = EMIT && a.ranges && !a.recount[r - a.rbase];
+    uint64_t* rec = a.ranges ? a.ranges + (len_ok ? a.seed_off[r - a.rbase] : 0u) : nullptr;
+    bool fits = true;
+    if (len_ok && (kept || load_codes(a.bases, o0, m, q, lane, a.status)) && m >= static_cast<uint32_t>(k)) {
       const uint64_t base = EMIT ? a.off[rr] : 0;
       // 32 seeds per round, one per lane; the matching entries of all of them
       // are then shared out over the warp (a repeat seed may have thousands)
       for (uint32_t o_base = 0; o_base + k <= m; o_base += 32 * a.stride) {
         const uint32_t o = o_base + lane * a.stride;
+        const uint32_t si = o / a.stride;  // the seed's index in the read
         const bool live = o + k <= m;
-        Kmer km;
-        if (live)
-          for (int t = 0; t < k; ++t) kmer_push(km, q[o + t], k);
-        const uint64_t canon = km.fwd < km.rc ? km.fwd : km.rc;
-        const uint32_t rori = (km.fwd == canon ? 1u : 0u) | (km.rc == canon ? 2u : 0u);
+        uint64_t canon = 0;
+        uint32_t rori = 0;
+        if (!kept) {
+          Kmer km;
+          if (live)
+            for (int t = 0; t < k; ++t) kmer_push(km, q[o + t], k);
+          canon = km.fwd < km.rc ? km.fwd : km.rc;
+          rori = (km.fwd == canon ? 1u : 0u) | (km.rc == canon ? 2u : 0u);
+        }
         for (int r2 = 0; r2 < a.di.n_refs; ++r2) {
           uint64_t lo = 0, hi = 0;
-          if (live) lookup(a.di, r2, canon, &lo, &hi);
+          if (kept) {
+            if (live) {
+              const uint64_t x = rec[static_cast<uint64_t>(si) * a.di.n_refs + r2];
+              lo = x >> 26;
+              hi = lo + ((x >> 2) & kRangeCntMax);
+              rori = static_cast<uint32_t>(x & 3u);
+            }
+          } else if (live) {
+            lookup(a.di, r2, canon, &lo, &hi);
+          }
           uint32_t cnt = static_cast<uint32_t>(hi - lo);
           if (!EMIT) {
             // an entry gives one CAL unless the seed is its own reverse complement
             // (then at most two): a bound that needs no entry loads
             n += rori == 3u ? 2u * cnt : cnt;
+            if (rec && live) {
+              const bool ok = hi - lo <= kRangeCntMax && lo <= kRangeLoMax;
+              fits = fits && ok;
+              rec[static_cast<uint64_t>(si) * a.di.n_refs + r2] = ok ? range_pack(lo, cnt, rori) : 0ull;
+            }
             continue;
           }
           uint32_t sc = cnt;
@@ -186,6 +241,10 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
     if (!EMIT) {
       n = __reduce_add_sync(FULL, n);
       if (lane == 0) a.count[rr] = n;
+      if (a.ranges) {
+        const bool all_fit = __all_sync(FULL, fits);
+        if (lane == 0) a.recount[r - a.rbase] = all_fit ? 0 : 1;
+      }
     } else if (lane == 0) {
       a.actual[rr] = ctr[warp];
     }
@@ -424,11 +483,19 @@ __global__ void k_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* 
 
 }  // namespace
 
+int launch_cal_slots(const uint64_t* read_off, uint32_t n, int k, uint32_t stride, int n_refs, uint32_t* slots,
+                     uint32_t* status, cudaStream_t st) {
+  if (n == 0) return 0;
+  k_cal_slots<<<(n + 255) / 256, 256, 0, st>>>(read_off, n, k, stride, n_refs, slots, status);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
                      uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* actual,
-                     uint32_t* status, cudaStream_t st) {
+                     uint32_t* status, const CalRanges& kept, cudaStream_t st) {
   if (nr == 0) return 0;
-  SeedArgs a{di, bases, read_off, r0, nr, stride, count, off, cals, actual, status};
+  SeedArgs a{di, bases, read_off, r0, nr, stride, count, off, cals, actual, status,
+             kept.ranges, kept.seed_off, kept.recount, kept.rbase};
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

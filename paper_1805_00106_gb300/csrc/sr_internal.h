@@ -258,8 +258,21 @@ constexpr uint64_t cal_filter_words(uint64_t P) { return 3 * P + 1; }
 // offsets or over kMaxReadLen bases set kStBadRead) or emit pass (CAL keys of
 // read r0 + i into cals[off[i] ...], their number into actual[i]) over reads
 // r0 .. r0 + nr
+// Seed lookups the count pass keeps for the emit pass: records start at
+// seed_off[r - rbase] for read r (seeds x references of it, from
+// launch_cal_slots); recount[r - rbase] = 1 where they could not be kept
+struct CalRanges {
+  uint64_t* ranges = nullptr;
+  const uint32_t* seed_off = nullptr;
+  uint8_t* recount = nullptr;
+  uint32_t rbase = 0;
+};
 int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
                      uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* actual,
+                     uint32_t* status, const CalRanges& kept, cudaStream_t st);
+// lookup records of each of n reads (seeds x n_refs); bad offsets or reads
+// over kMaxReadLen bases set kStBadRead
+int launch_cal_slots(const uint64_t* read_off, uint32_t n, int k, uint32_t stride, int n_refs, uint32_t* slots,
                      uint32_t* status, cudaStream_t st);
 // windows of each read at off[i] (nwin[i] of them).  Reads with up to
 // kCalSmallKeys CALs (largest: max_small) and up to kCalSmemKeys (largest:

@@ -267,7 +267,7 @@ void scheduler(Server* sv) {
       });
       if (sv->pending.empty()) break;
       const uint64_t budget = session_budget(sv->s);
-      uint64_t round_reads = 0;
+      uint64_t round_reads = 0, round_bytes = 0;
       while (!sv->pending.empty()) {
         Request* q = sv->pending.front();
         if (budget && sv->reserved + q->bytes > budget) {
@@ -278,7 +278,12 @@ void scheduler(Server* sv) {
         // a round stays at most kMaxRoundReads reads (one request may exceed it alone),
         // so a backlog drains in rounds of bounded latency and device memory
         if (!next.reqs.empty() && round_reads + q->n_reads > kMaxRoundReads) break;
+        // and at most half the budget (one larger request runs alone), so that the
+        // next round always fits beside a running one: under memory pressure the
+        // device still has a round queued instead of idling until one completes
+        if (budget && !next.reqs.empty() && round_bytes + q->bytes > budget / 2) break;
         round_reads += q->n_reads;
+        round_bytes += q->bytes;
         sv->pending.pop_front();
         sv->reserved += q->bytes;
         ++sv->inflight;

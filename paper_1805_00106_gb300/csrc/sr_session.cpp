@@ -1474,143 +1474,205 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 4, st);
     if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
-    if (launch_cal_seeds(s->didx, d_bases, d_roff, 0, n, cp.seed_stride, d_count, nullptr, nullptr, nullptr,
-                         d_status, st) < 0) {
+    // lookup records (seeds x references) of every read, for the count pass to
+    // keep its lookups for the emit pass; read chunks of at most kRangeRecords
+    uint32_t* d_slots = static_cast<uint32_t*>(dalloc(n * 4ull));
+    if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+    if (launch_cal_slots(d_roff, n, s->didx.k, cp.seed_stride, s->didx.n_refs, d_slots, d_status, st) < 0) {
       e = cudaGetLastError();
-      return done(SR_ECUDA, "sr_candidates_device count");
+      return done(SR_ECUDA, "sr_candidates_device slots");
     }
-    std::vector<uint32_t> count(n);
+    std::vector<uint32_t> slots(n);
     uint32_t status = 0;
-    e = cudaMemcpyAsync(count.data(), d_count, n * 4ull, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(slots.data(), d_slots, n * 4ull, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device count copy");
+    if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device slots copy");
     if (status & kStBadRead) return done(SR_EINVAL, "sr_candidates_device: decreasing read offsets or a read longer than 256 bases");
-    if (status & kStBadBase) return done(SR_EBADBASE, "sr_candidates_device: read has a non-ACGT base");
-    // chunks of reads whose CALs (upper bounds) fit the buffers
-    uint64_t sum = 0;
-    for (uint32_t r = 0; r < n; ++r) sum += count[r];
-    uint64_t cap = std::min<uint64_t>(std::max<uint64_t>(sum, 1), 64ull << 20);
-    for (uint32_t r = 0; r < n; ++r) cap = std::max<uint64_t>(cap, count[r]);
-    uint64_t* d_cals = static_cast<uint64_t*>(dalloc(cap * 8));
-    uint64_t* d_wkey = static_cast<uint64_t*>(dalloc(cap * 8));
-    uint32_t* d_whits = static_cast<uint32_t*>(dalloc(cap * 4));
-    uint32_t* d_wlen = static_cast<uint32_t*>(dalloc(cap * 4));
-    uint8_t* d_oref = static_cast<uint8_t*>(dalloc(cap));
-    uint8_t* d_ostr = static_cast<uint8_t*>(dalloc(cap));
-    uint64_t* d_ostart = static_cast<uint64_t*>(dalloc(cap * 8));
-    uint32_t* d_olen = static_cast<uint32_t*>(dalloc(cap * 4));
-    uint32_t* d_ohits = static_cast<uint32_t*>(dalloc(cap * 4));
-    uint64_t* d_off = static_cast<uint64_t*>(dalloc(n * 8ull));
-    uint32_t* d_nwin = static_cast<uint32_t*>(dalloc(n * 4ull));
-    uint32_t* d_woff = static_cast<uint32_t*>(dalloc((n + 1ull) * 4));
-    uint32_t* d_sums = static_cast<uint32_t*>(dalloc((n / 1024 + 2ull) * 4));
-    uint32_t* d_big = static_cast<uint32_t*>(dalloc(n * 4ull));
-    uint64_t* d_bigoff = static_cast<uint64_t*>(dalloc(n * 8ull));
+    constexpr uint64_t kRangeRecords = 128ull << 20;  // 1 GiB of kept lookups at most
+    std::vector<uint32_t> rchunk{0};                   // read chunk boundaries
+    uint64_t max_rec = 0;
+    uint32_t max_reads = 0;
+    {
+      uint64_t acc = 0;
+      for (uint32_t r = 0; r < n; ++r) {
+        if (acc + slots[r] > kRangeRecords && r > rchunk.back()) {
+          max_rec = std::max(max_rec, acc);
+          max_reads = std::max(max_reads, r - rchunk.back());
+          rchunk.push_back(r);
+          acc = 0;
+        }
+        acc += slots[r];
+      }
+      max_rec = std::max(max_rec, acc);
+      max_reads = std::max(max_reads, n - rchunk.back());
+      rchunk.push_back(n);
+    }
+    uint64_t* d_ranges = static_cast<uint64_t*>(dalloc(std::max<uint64_t>(max_rec, 1) * 8));
+    uint32_t* d_seed_off = static_cast<uint32_t*>(dalloc((max_reads + 1ull) * 4));
+    uint8_t* d_recount = static_cast<uint8_t*>(dalloc(max_reads + 1ull));
+    std::vector<uint32_t> count(n);
+    // the emit / filter buffers, sized for the largest read chunk (its CAL bounds are known
+    // once its count pass ran): allocated on the first chunk, grown when a chunk needs more
+    uint64_t cap = 0;
+    uint64_t *d_cals = nullptr, *d_wkey = nullptr, *d_ostart = nullptr, *d_off = nullptr, *d_bigoff = nullptr;
+    uint32_t *d_whits = nullptr, *d_wlen = nullptr, *d_olen = nullptr, *d_ohits = nullptr, *d_nwin = nullptr,
+             *d_woff = nullptr, *d_sums = nullptr, *d_big = nullptr;
+    uint8_t *d_oref = nullptr, *d_ostr = nullptr;
+    d_off = static_cast<uint64_t*>(dalloc(max_reads * 8ull + 8));
+    d_nwin = static_cast<uint32_t*>(dalloc(max_reads * 4ull + 4));
+    d_woff = static_cast<uint32_t*>(dalloc((max_reads + 1ull) * 4));
+    d_sums = static_cast<uint32_t*>(dalloc((max_reads / 1024 + 2ull) * 4));
+    d_big = static_cast<uint32_t*>(dalloc(max_reads * 4ull + 4));
+    d_bigoff = static_cast<uint64_t*>(dalloc(max_reads * 8ull + 8));
     if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
     uint64_t* d_scratch = nullptr;
     uint64_t scratch_keys = 0;
-    std::vector<uint64_t> off(n), bigoff;
-    std::vector<uint32_t> big;
-    for (uint32_t r0 = 0; r0 < n;) {
-      uint32_t r1 = r0;
-      uint64_t used = 0;
-      uint32_t max_small = 1, max_mid = 0;
-      uint64_t big_keys = 0;
-      big.clear();
-      bigoff.clear();
-      while (r1 < n && used + count[r1] <= cap) {
-        off[r1 - r0] = used;
-        used += count[r1];
-        if (count[r1] > kCalSmemKeys) {
-          uint64_t p2 = 1;
-          while (p2 < count[r1]) p2 <<= 1;
-          big.push_back(r1 - r0);
-          bigoff.push_back(big_keys);
-          big_keys += cal_filter_words(p2);
-        } else if (count[r1] > kCalSmallKeys) {
-          max_mid = std::max(max_mid, count[r1]);
-        } else {
-          max_small = std::max(max_small, count[r1]);
-        }
-        ++r1;
+    std::vector<uint64_t> off(max_reads + 1ull), bigoff;
+    std::vector<uint32_t> big, seed_off(max_reads + 1ull);
+    for (size_t ci = 0; ci + 1 < rchunk.size(); ++ci) {
+      const uint32_t R0 = rchunk[ci], R1 = rchunk[ci + 1];
+      // this chunk's record offsets, then its count pass (which keeps the lookups)
+      uint32_t acc = 0;
+      for (uint32_t r = R0; r < R1; ++r) {
+        seed_off[r - R0] = acc;
+        acc += slots[r];
       }
-      const uint32_t nr = r1 - r0;
-      if (big_keys > scratch_keys) {
-        e = cudaMalloc(&d_scratch, big_keys * 8);
-        if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-        bufs.push_back(d_scratch);
-        scratch_keys = big_keys;
-      }
-      e = cudaMemcpyAsync(d_off, off.data(), nr * 8ull, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess && !big.empty()) {
-        e = cudaMemcpyAsync(d_big, big.data(), big.size() * 4ull, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(d_bigoff, bigoff.data(), bigoff.size() * 8ull, cudaMemcpyHostToDevice, st);
-      }
+      seed_off[R1 - R0] = acc;
+      e = cudaMemcpyAsync(d_seed_off, seed_off.data(), (R1 - R0 + 1ull) * 4, cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
-      if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_actual,
-                           d_status, st) < 0 ||
-          launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_actual,
-                            d_off, d_cals, max_small, max_mid, d_big, d_bigoff, static_cast<uint32_t>(big.size()),
-                            d_scratch, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
-          launch_scan_u32(d_nwin, nr, d_woff, d_sums, st) < 0) {
+      const CalRanges kept{d_ranges, d_seed_off, d_recount, R0};
+      if (launch_cal_seeds(s->didx, d_bases, d_roff, R0, R1 - R0, cp.seed_stride, d_count + R0, nullptr, nullptr,
+                           nullptr, d_status, kept, st) < 0) {
         e = cudaGetLastError();
-        return done(SR_ECUDA, "sr_candidates_device filter");
+        return done(SR_ECUDA, "sr_candidates_device count");
       }
-      uint32_t nw32 = 0;
-      std::vector<uint32_t> woff;
-      if (out_dev) {
-        e = cudaMemcpyAsync(&nw32, d_woff + nr, 4, cudaMemcpyDeviceToHost, st);
-      } else {
-        woff.resize(nr + 1ull);
-        e = cudaMemcpyAsync(woff.data(), d_woff, (nr + 1ull) * 4, cudaMemcpyDeviceToHost, st);
-      }
+      e = cudaMemcpyAsync(count.data() + R0, d_count + R0, (R1 - R0) * 4ull, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window count");
-      const uint64_t nw = out_dev ? nw32 : woff[nr];
-      if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, d_oref, d_ostr, d_ostart, d_olen,
-                             d_ohits, st) < 0) {
-        e = cudaGetLastError();
-        return done(SR_ECUDA, "sr_candidates_device compact");
+      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device count copy");
+      if (status & kStBadRead) return done(SR_EINVAL, "sr_candidates_device: decreasing read offsets or a read longer than 256 bases");
+      if (status & kStBadBase) return done(SR_EBADBASE, "sr_candidates_device: read has a non-ACGT base");
+      // sub-chunks of reads whose CALs (upper bounds) fit the buffers
+      uint64_t sum = 0, one = 0;
+      for (uint32_t r = R0; r < R1; ++r) {
+        sum += count[r];
+        one = std::max<uint64_t>(one, count[r]);
       }
-      if (out_dev) {
-        // this chunk's offsets in the whole list, its windows appended on the device
-        if (launch_cal_offsets(d_woff, nr, total_w, l->offsets + r0, st) < 0) {
+      const uint64_t want = std::max<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(sum, 1), 64ull << 20), one);
+      if (want > cap) {
+        cap = want;
+        d_cals = static_cast<uint64_t*>(dalloc(cap * 8));
+        d_wkey = static_cast<uint64_t*>(dalloc(cap * 8));
+        d_whits = static_cast<uint32_t*>(dalloc(cap * 4));
+        d_wlen = static_cast<uint32_t*>(dalloc(cap * 4));
+        d_oref = static_cast<uint8_t*>(dalloc(cap));
+        d_ostr = static_cast<uint8_t*>(dalloc(cap));
+        d_ostart = static_cast<uint64_t*>(dalloc(cap * 8));
+        d_olen = static_cast<uint32_t*>(dalloc(cap * 4));
+        d_ohits = static_cast<uint32_t*>(dalloc(cap * 4));
+        if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+      }
+      for (uint32_t r0 = R0; r0 < R1;) {
+        uint32_t r1 = r0;
+        uint64_t used = 0;
+        uint32_t max_small = 1, max_mid = 0;
+        uint64_t big_keys = 0;
+        big.clear();
+        bigoff.clear();
+        while (r1 < R1 && used + count[r1] <= cap) {
+          off[r1 - r0] = used;
+          used += count[r1];
+          if (count[r1] > kCalSmemKeys) {
+            uint64_t p2 = 1;
+            while (p2 < count[r1]) p2 <<= 1;
+            big.push_back(r1 - r0);
+            bigoff.push_back(big_keys);
+            big_keys += cal_filter_words(p2);
+          } else if (count[r1] > kCalSmallKeys) {
+            max_mid = std::max(max_mid, count[r1]);
+          } else {
+            max_small = std::max(max_small, count[r1]);
+          }
+          ++r1;
+        }
+        const uint32_t nr = r1 - r0;
+        if (big_keys > scratch_keys) {
+          e = cudaMalloc(&d_scratch, big_keys * 8);
+          if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+          bufs.push_back(d_scratch);
+          scratch_keys = big_keys;
+        }
+        e = cudaMemcpyAsync(d_off, off.data(), nr * 8ull, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !big.empty()) {
+          e = cudaMemcpyAsync(d_big, big.data(), big.size() * 4ull, cudaMemcpyHostToDevice, st);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_bigoff, bigoff.data(), bigoff.size() * 8ull, cudaMemcpyHostToDevice, st);
+        }
+        if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
+        if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_actual,
+                             d_status, kept, st) < 0 ||
+            launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_actual,
+                              d_off, d_cals, max_small, max_mid, d_big, d_bigoff, static_cast<uint32_t>(big.size()),
+                              d_scratch, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
+            launch_scan_u32(d_nwin, nr, d_woff, d_sums, st) < 0) {
           e = cudaGetLastError();
-          return done(SR_ECUDA, "sr_candidates_device offsets");
+          return done(SR_ECUDA, "sr_candidates_device filter");
         }
-        if (!grow_out(total_w + nw, total_w)) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-        if (nw) {
-          e = cudaMemcpyAsync(l->ref_id + total_w, d_oref, nw, cudaMemcpyDeviceToDevice, st);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(l->strand + total_w, d_ostr, nw, cudaMemcpyDeviceToDevice, st);
-          if (e == cudaSuccess)
-            e = cudaMemcpyAsync(l->win_start + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToDevice, st);
-          if (e == cudaSuccess)
-            e = cudaMemcpyAsync(l->win_len + total_w, d_olen, nw * 4, cudaMemcpyDeviceToDevice, st);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(l->hits + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToDevice, st);
-          if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
+        uint32_t nw32 = 0;
+        std::vector<uint32_t> woff;
+        if (out_dev) {
+          e = cudaMemcpyAsync(&nw32, d_woff + nr, 4, cudaMemcpyDeviceToHost, st);
+        } else {
+          woff.resize(nr + 1ull);
+          e = cudaMemcpyAsync(woff.data(), d_woff, (nr + 1ull) * 4, cudaMemcpyDeviceToHost, st);
         }
-      } else {
-        o_ref.resize(total_w + nw);
-        o_strand.resize(total_w + nw);
-        o_start.resize(total_w + nw);
-        o_len.resize(total_w + nw);
-        o_hits.resize(total_w + nw);
-        if (nw) {
-          e = cudaMemcpyAsync(o_ref.data() + total_w, d_oref, nw, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(o_strand.data() + total_w, d_ostr, nw, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess)
-            e = cudaMemcpyAsync(o_start.data() + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(o_len.data() + total_w, d_olen, nw * 4, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(o_hits.data() + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-          if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window count");
+        const uint64_t nw = out_dev ? nw32 : woff[nr];
+        if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, d_oref, d_ostr, d_ostart, d_olen,
+                               d_ohits, st) < 0) {
+          e = cudaGetLastError();
+          return done(SR_ECUDA, "sr_candidates_device compact");
         }
-        for (uint32_t i = 0; i <= nr; ++i) offsets[r0 + i] = total_w + woff[i];
+        if (out_dev) {
+          // this chunk's offsets in the whole list, its windows appended on the device
+          if (launch_cal_offsets(d_woff, nr, total_w, l->offsets + r0, st) < 0) {
+            e = cudaGetLastError();
+            return done(SR_ECUDA, "sr_candidates_device offsets");
+          }
+          if (!grow_out(total_w + nw, total_w)) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+          if (nw) {
+            e = cudaMemcpyAsync(l->ref_id + total_w, d_oref, nw, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(l->strand + total_w, d_ostr, nw, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+              e = cudaMemcpyAsync(l->win_start + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+              e = cudaMemcpyAsync(l->win_len + total_w, d_olen, nw * 4, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(l->hits + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
+          }
+        } else {
+          o_ref.resize(total_w + nw);
+          o_strand.resize(total_w + nw);
+          o_start.resize(total_w + nw);
+          o_len.resize(total_w + nw);
+          o_hits.resize(total_w + nw);
+          if (nw) {
+            e = cudaMemcpyAsync(o_ref.data() + total_w, d_oref, nw, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(o_strand.data() + total_w, d_ostr, nw, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+              e = cudaMemcpyAsync(o_start.data() + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(o_len.data() + total_w, d_olen, nw * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(o_hits.data() + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
+          }
+          for (uint32_t i = 0; i <= nr; ++i) offsets[r0 + i] = total_w + woff[i];
+        }
+        total_w += nw;
+        r0 = r1;
       }
-      total_w += nw;
-      r0 = r1;
     }
     // the chunk buffers are freed below; the device result arrays must be complete first
     e = cudaStreamSynchronize(st);

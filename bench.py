@@ -732,11 +732,14 @@ def main():
         line["e2e"] = {"value": round(cells / e2e_t / 1e9, 3), "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "ms_per_step": round(1e3 * e2e_t, 2),
                        "reads_per_s": round(n_reads / e2e_t, 1)}
-    if rank == 0 and not args.no_serve:
+    # the single-GPU legs (serving, CAL finder, xenograft, repeat-heavy) run at N = 1 only:
+    # under torchrun they would hold every rank's GPU at the final barrier for minutes
+    solo = ws == 1
+    if rank == 0 and solo and not args.no_serve:
         line["serving"] = serving_bench(sr, args.scale, args.serve_seconds, budget_mb=args.serve_budget_mb)
-    if rank == 0 and not args.no_cal:
+    if rank == 0 and solo and not args.no_cal:
         line["cal_finder"] = cal_finder_bench(sr, args.scale)
-    if rank == 0 and not args.no_extra:
+    if rank == 0 and solo and not args.no_extra:
         line["xenograft"] = xenograft_bench(sr, stream, args.scale)
         line["repeat_heavy"] = repeat_bench(sr, stream, args.scale)
     if rank == 0 and not args.no_cpu_baseline:

@@ -95,7 +95,7 @@ struct BatchDev {
   uint8_t* tb_flag = nullptr;     // n_reads: how the winner's end row is found (kTbFlag*)
   uint32_t* tb_list = nullptr;    // 2 * n_reads: per-read sort code, then reads sorted by code
   uint32_t* tb_count = nullptr;   // kTbCountWords: code histogram, cursors, bucket ranges
-  uint32_t* tb_dirs = nullptr;    // tb_thread_warps(n_reads) * 256 rows * 32 lanes: narrow-band direction words
+  uint32_t* tb_dirs = nullptr;    // tb_dirs_words(n_reads): narrow-band direction words
   uint32_t* cigar_off = nullptr;  // n_reads + 1 (exclusive scan of lengths)
   uint32_t* cigar = nullptr;      // compacted, n_reads * kCigarStride capacity
   uint8_t* read_class = nullptr;  // n_reads
@@ -125,6 +125,21 @@ constexpr uint32_t kTbThreadMaxWarps = 4864;
 inline uint32_t tb_thread_warps(uint32_t n_reads) {
   const uint32_t w = (n_reads + 31u) / 32u;
   return w < kTbThreadMaxWarps ? (w ? w : 1u) : kTbThreadMaxWarps;
+}
+// warps of the two-reads-per-thread traceback for bands of at most 16 diagonals
+// (64 reads per warp; each owns a scratch of 256 rows x 4 words x 32 lanes):
+// 152 SMs x 24, its residency on GB300
+constexpr uint32_t kTbPairMaxWarps = 3648;
+constexpr uint64_t kTbPairWarpWords = 256ull * 4 * 32;
+inline uint32_t tb_pair_warps(uint32_t n_reads) {
+  const uint32_t w = (n_reads + 63u) / 64u;
+  return w < kTbPairMaxWarps ? (w ? w : 1u) : kTbPairMaxWarps;
+}
+// the narrow-band scratch serves whichever of the two kernels runs
+inline uint64_t tb_dirs_words(uint32_t n_reads) {
+  const uint64_t a = static_cast<uint64_t>(tb_thread_warps(n_reads)) * 256 * 32;
+  const uint64_t b = static_cast<uint64_t>(tb_pair_warps(n_reads)) * kTbPairWarpWords;
+  return a > b ? a : b;
 }
 
 // Diagonal band of a winner (score S >= 1 ending in column j*) whose end row lies

@@ -398,7 +398,7 @@ uint64_t carve_batch(BatchDev& d, uint32_t n, uint64_t nb, uint64_t nc, uint32_t
   c.take(d.tb_flag, n);
   c.take(d.tb_list, 2ull * n);
   c.take(d.tb_count, kTbCountWords);
-  c.take(d.tb_dirs, static_cast<uint64_t>(tb_thread_warps(n)) * kMaxReadLen * 32);
+  c.take(d.tb_dirs, tb_dirs_words(n));
   c.take(d.out_best, n);
   c.take(d.out_per_ref, static_cast<uint64_t>(n) * n_refs);
   StageCheck* pc;

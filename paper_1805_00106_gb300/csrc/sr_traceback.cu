@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sr_internal.h"
 
 namespace sr {
@@ -55,6 +57,7 @@ struct TbArgs {
   int slots;
   int mode;
   int32_t sa, sb, go, ge;
+  uint32_t k2;  // 2, passed at run time (multiply-adds by it stay on the FMA pipe)
 };
 
 __global__ void __launch_bounds__(32) k_traceback(TbArgs a, const uint32_t* list, const uint32_t* range) {
@@ -658,6 +661,11 @@ __device__ __forceinline__ uint32_t tb_prmt(uint32_t a, uint32_t b, uint32_t c) 
   asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
+__device__ __forceinline__ uint32_t imad_u32(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
 
 // 16 packed codes at positions lo .. lo + 15 of a 2-bit array of nw words (0
 // for words outside it)
@@ -1194,6 +1202,312 @@ __global__ void __launch_bounds__(32 * kTbTWarps) k_tb_thread(TbArgs a, const ui
   }
 }
 
+// ---- Bands of at most 16 diagonals: two reads per thread, one in each 16-bit
+// half (DPX s16x2 arithmetic), each pair swept row by row with the row's W
+// cells in registers.  Cell k of row i is band diagonal dlo + k (column
+// i + dlo + k); its left neighbour is cell k - 1 of the same row, its upper one
+// cell k + 1 and its diagonal cell k of the row above.  The cell arithmetic is
+// the packed wavefront's: E and F arrive complete, the cell computes its right
+// neighbour's E and its lower neighbour's F (gap opened from its H or extended)
+// and stores 4 bits, inverted (1 = not equal): H = diagonal value, H = E,
+// En = the opened gap value, Fn = the opened gap value.  Cells that are not
+// needed still compute: the band they form is wider than the winner's, and the
+// banded DP is exact for any band holding every alignment of the score (cells
+// left of column 1 score a mismatch and so stay at the H = 0 border; cells right
+// of j* feed only cells right of j*).
+//
+// Scores: per row and read, the window codes of the row's W cells come from one
+// funnel shift of the staged window words; XOR with the row's query code gives
+// 2 bits per cell (0: match), folded to one mismatch bit per cell.  Four cells'
+// bits are spread to four bytes (0x80 + 0x11 n: the prmt selector nibbles n,
+// n | 8 that pick byte n of the score table sign-extended), and per cell one
+// prmt takes read A's byte and read B's into the selector of a second prmt that
+// picks both scores.  Direction words, one per 4 cells and row, hold read A's 4
+// nibbles in the low half and read B's in the high half, in a per-warp scratch
+// laid out [row][word][lane] so that a warp's stores coalesce.
+constexpr int kTbPWarps = 4;                     // warps per block
+constexpr int kTbPMaxW = 16;                     // cells per row at most
+constexpr int kTbPQ = kReadWords;                // staged query words per read
+constexpr int kTbPR = kMaxReadLen / 16 + 1;      // staged window words per read (band offsets 0 .. 271)
+constexpr int kTbPLane = 2 * kTbPQ + 2 * kTbPR + 1;  // per-lane shared words (odd: conflict-free)
+static_assert(kTbPLane % 2 == 1, "odd per-lane stride");
+
+struct TbPairConst {
+  uint32_t NEG2, ONE2, NGOE2, NGE2, tab;
+  uint32_t K2, KN[3];  // 2, 16, 256, 4096 held in registers: the multiply-adds stay on the FMA pipe
+};
+
+// codes 0..3 of query row i (1-based) of a staged read, complemented for the
+// '-' strand by the caller's mask
+__device__ __forceinline__ uint32_t tbp_qcode(const uint32_t* q, const TbRead& t, int i) {
+  const int p = t.strand ? max(static_cast<int>(t.m) - i, 0) : i - 1;
+  return (q[p >> 4] >> ((p & 15) * 2)) & 3u;
+}
+// window code of band offset u (column u + dlo + 1)
+__device__ __forceinline__ uint32_t tbp_rcode(const uint32_t* r, int u) { return (r[u >> 4] >> ((u & 15) * 2)) & 3u; }
+
+// walk read X (0: low half, 1: high half) back from (i*, j*) through the scratch
+// of direction words with Q words per row
+__device__ __forceinline__ void tbp_walk(const TbArgs& a, const TbRead& t, uint32_t istar, int X, const uint32_t* dirs,
+                                         int Q, const uint32_t* q, const uint32_t* r) {
+  const int32_t goe = a.go + a.ge;
+  uint32_t* out = a.cigar_slots + static_cast<uint64_t>(t.r) * kCigarStride;
+  const uint32_t cm = t.strand ? 3u : 0u;
+  int i = static_cast<int>(istar), j = static_cast<int>(t.jstar);
+  int kk = j - i - t.dlo;
+  int32_t h = t.S;
+  int state = 0;
+  uint32_t nr = 0, cur_op = 0xffu, cur_len = 0;
+  bool bad = istar == kNoRow;
+  const int limit = t.ihi + static_cast<int>(t.jstar) + 4;
+  const int sh0 = 16 * X;
+  auto nib_at = [&](int ii, int k) {
+    const uint32_t wd = dirs[(static_cast<uint32_t>((ii - 1) * Q + (k >> 2))) * 32u];
+    return ((wd >> (sh0 + 4 * (k & 3))) & 15u) ^ 15u;
+  };
+  for (int it = 0; !bad; ++it) {
+    if (it > limit || kk < 0 || kk >= t.w || i < 1 || j < 1) {
+      bad = !(state == 0 && h == 0);
+      break;
+    }
+    uint32_t op;
+    if (state == 0) {
+      if (h == 0) break;
+      const uint32_t nib = nib_at(i, kk);
+      if (nib & 1u) {
+        op = 0u;  // M
+        h -= (tbp_qcode(q, t, i) ^ cm) == tbp_rcode(r, j - 1 - t.dlo) ? a.sa : -a.sb;
+        --i;
+        --j;
+      } else {
+        state = (nib & 2u) ? 1 : 2;
+        continue;
+      }
+    } else {
+      op = state == 1 ? 2u : 1u;  // D : I
+      if (op == 2u) {
+        --j;
+        --kk;
+      } else {
+        --i;
+        ++kk;
+      }
+      // the cell the gap came from holds whether it was opened there
+      if (i < 1 || j < 1 || kk < 0 || kk >= t.w) {
+        bad = true;
+        break;
+      }
+      const uint32_t nib = nib_at(i, kk);
+      const bool open = op == 2u ? (nib & 4u) : (nib & 8u);
+      h += open ? goe : a.ge;
+      if (open) state = 0;
+    }
+    if (op == cur_op) {
+      ++cur_len;
+    } else {
+      if (nr + 4 >= static_cast<uint32_t>(kCigarStride)) {
+        bad = true;
+        break;
+      }
+      if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
+      cur_op = op;
+      cur_len = 1;
+    }
+  }
+  DevHit* hp = a.hits + static_cast<uint64_t>(t.r) * a.slots;
+  if (bad || nr + 3 > static_cast<uint32_t>(kCigarStride)) {
+    atomicOr(a.status, kStInternal);
+    hp->cigar_len = 0;
+    return;
+  }
+  if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
+  for (uint32_t x = 0; x < nr / 2; ++x) {
+    const uint32_t t0 = out[1 + x];
+    out[1 + x] = out[nr - x];
+    out[nr - x] = t0;
+  }
+  const uint32_t start_i = static_cast<uint32_t>(i) + 1u;
+  uint32_t nc;
+  if (start_i > 1) {
+    out[0] = ((start_i - 1u) << 4) | 4u;
+    nc = nr + 1;
+  } else {
+    for (uint32_t x = 0; x < nr; ++x) out[x] = out[x + 1];
+    nc = nr;
+  }
+  if (istar < t.m) out[nc++] = ((t.m - istar) << 4) | 4u;
+  hp->read_start = static_cast<int32_t>(start_i);
+  hp->read_end = static_cast<int32_t>(istar);
+  hp->start_j = static_cast<uint32_t>(j) + 1u;
+  hp->cigar_len = nc;
+}
+
+// the band DP of a thread's two reads (W cells per row), then both walks
+template <int W>
+__device__ __forceinline__ void tb_pair_reads(const TbArgs& a, const TbRead (&t)[2], uint32_t* dirs,
+                                              const uint32_t* sq, const uint32_t* sr, const TbPairConst& c) {
+  static_assert(W == 4 || W == 8 || W == 16, "cells per row");
+  constexpr int Q = W / 4;  // direction words per row
+  const int rows = max(t[0].has ? t[0].ihi : 0, t[1].has ? t[1].ihi : 0);
+  uint32_t Hp[W], Fp[W];  // the row above: H, and the F it sends down-left
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    Hp[k] = 0u;
+    Fp[k] = c.NGOE2;
+  }
+  // per read: the complement mask of its query codes, the virtual-cell mask of
+  // the row (pattern 01 in the 2-bit code of every cell left of column 1), the
+  // rows where the band crosses column j* inside [ilo, ihi], and i*
+  uint32_t cmask[2], ist[2];
+  int lsh[2], clo[2], chi[2];
+#pragma unroll
+  for (int X = 0; X < 2; ++X) {
+    cmask[X] = t[X].strand ? 0xffffffffu : 0u;
+    // cells k < 1 - i - dlo lie left of column 1: the row's mask is 0x55555555
+    // shifted right by 32 - 2 (1 - i - dlo), clamped to 0 .. 32
+    lsh[X] = 32 + 2 * t[X].dlo;
+    const int jd = static_cast<int>(t[X].jstar) - t[X].dlo;  // row where cell 0 is column j*
+    clo[X] = t[X].has ? max(t[X].ilo, jd - W + 1) : 1;
+    chi[X] = t[X].has ? min(t[X].ihi, jd) : 0;
+    ist[X] = kNoRow;
+  }
+  const uint32_t* q0 = sq;
+  const uint32_t* q1 = sq + kTbPQ;
+  const uint32_t* r0 = sr;
+  const uint32_t* r1 = sr + kTbPR;
+  for (int i = 1; i <= rows; ++i) {
+    // mismatch bits of the row (bit 2k: cell k), per read
+    uint32_t nb[2];
+#pragma unroll
+    for (int X = 0; X < 2; ++X) {
+      const uint32_t* q = X ? q1 : q0;
+      const uint32_t* r = X ? r1 : r0;
+      const int u = i - 1;  // band offset of cell 0
+      const uint32_t sl = __funnelshift_r(r[u >> 4], r[(u >> 4) + 1], (u & 15) * 2);
+      const uint32_t lm = __funnelshift_rc(0x55555555u, 0u, static_cast<uint32_t>(max(lsh[X], 0)));
+      lsh[X] += 2;
+      const uint32_t x = (sl ^ imad_u32(tbp_qcode(q, t[X], i), 0x55555555u, 0u) ^ cmask[X]) | lm;
+      nb[X] = (x | (x >> 1)) & 0x55555555u;
+    }
+    uint32_t E = c.NGOE2;  // arriving at cell 0 from outside the band
+    uint32_t acc = 0u, sA = 0u, sB = 0u;
+    uint32_t* drow = dirs + static_cast<uint32_t>((i - 1) * Q) * 32u;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      if ((k & 3) == 0) {
+        // cells k .. k + 3: mismatch bits at 0, 2, 4, 6 -> bytes 0x80 + 0x11 n
+        const uint32_t bA = tb_prmt(nb[0], 0u, 0x4440u | static_cast<uint32_t>(k >> 2));
+        const uint32_t bB = tb_prmt(nb[1], 0u, 0x4440u | static_cast<uint32_t>(k >> 2));
+        sA = imad_u32(imad_u32(bA, 0x41041u, 0u) & 0x01010101u, 0x11u, 0x80808080u);
+        sB = imad_u32(imad_u32(bB, 0x41041u, 0u) & 0x01010101u, 0x11u, 0x80808080u);
+      }
+      const uint32_t sel = tb_prmt(sA, sB, static_cast<uint32_t>((k & 3) | ((4 + (k & 3)) << 4)));
+      const uint32_t sc = tb_prmt(c.tab, 0u, sel);
+      const uint32_t F = k + 1 < W ? Fp[k + 1] : c.NGOE2;
+      const uint32_t hs = __viaddmax_s16x2(Hp[k], sc, c.NEG2);
+      const uint32_t H = __vimax3_s16x2_relu(hs, E, F);
+      const uint32_t g = __viaddmax_s16x2(H, c.NGOE2, c.NEG2);
+      const uint32_t En = __viaddmax_s16x2(E, c.NGE2, g);
+      const uint32_t Fn = __viaddmax_s16x2(F, c.NGE2, g);
+      // bits (inverted) by Horner steps: Fn, En, H = E, H = diagonal
+      uint32_t z = imad_u32(__vimin3_u16x2(Fn ^ g, c.ONE2, c.ONE2), c.K2, __vimin3_u16x2(En ^ g, c.ONE2, c.ONE2));
+      z = imad_u32(z, c.K2, __vimin3_u16x2(H ^ E, c.ONE2, c.ONE2));
+      z = imad_u32(z, c.K2, __vimin3_u16x2(H ^ hs, c.ONE2, c.ONE2));
+      acc = (k & 3) ? imad_u32(z, c.KN[(k & 3) - 1], acc) : z;
+      if ((k & 3) == 3) drow[(k >> 2) * 32] = acc;
+      Hp[k] = H;
+      Fp[k] = Fn;
+      E = En;
+    }
+    // end rows: the smallest row in [ilo, ihi] whose cell in column j* holds S
+#pragma unroll
+    for (int X = 0; X < 2; ++X) {
+      if (ist[X] == kNoRow && i >= clo[X] && i <= chi[X]) {
+        const int kc = static_cast<int>(t[X].jstar) - i - t[X].dlo;
+        uint32_t hc = 0u;
+#pragma unroll
+        for (int k = 0; k < W; ++k) hc = k == kc ? Hp[k] : hc;
+        const int32_t v = X ? static_cast<int16_t>(hc >> 16) : static_cast<int16_t>(hc & 0xffffu);
+        if (v == t[X].S) ist[X] = static_cast<uint32_t>(i);
+      }
+    }
+  }
+  if (t[0].has) tbp_walk(a, t[0], ist[0], 0, dirs, Q, q0, r0);
+  if (t[1].has) tbp_walk(a, t[1], ist[1], 1, dirs, Q, q1, r1);
+}
+
+// Reads of bands up to 16 diagonals, in band-width order, 64 per warp: each warp
+// runs the narrowest row width (4, 8 or 16 cells) that holds its reads.
+__global__ void __launch_bounds__(32 * kTbPWarps) k_tb_pair(TbArgs a, const uint32_t* list, const uint32_t* range_lo,
+                                                          const uint32_t* range_hi, uint32_t* scratch,
+                                                          uint32_t n_warps) {
+  __shared__ uint32_t s_s[kTbPWarps][32 * kTbPLane];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const uint32_t gw = blockIdx.x * kTbPWarps + warp;
+  if (gw >= n_warps) return;
+  uint32_t* dirs = scratch + static_cast<uint64_t>(gw) * kMaxReadLen * (kTbPMaxW / 4) * 32 + lane;
+  uint32_t* sq = s_s[warp] + lane * kTbPLane;  // [query A][query B][window A][window B]
+  uint32_t* sr = sq + 2 * kTbPQ;
+  auto pack2 = [](int32_t v) { return (static_cast<uint32_t>(v) & 0xffffu) * 0x10001u; };
+  const int32_t goe = a.go + a.ge;
+  TbPairConst c;
+  c.NEG2 = 0x80008000u;
+  c.ONE2 = 0x00010001u;
+  c.NGOE2 = pack2(-goe);
+  c.NGE2 = pack2(-a.ge);
+  c.tab = (static_cast<uint32_t>(a.sa) & 0xffu) | ((static_cast<uint32_t>(-a.sb) & 0xffu) << 8);
+  c.K2 = a.k2;
+  c.KN[0] = a.k2 << 3;
+  c.KN[1] = a.k2 << 7;
+  c.KN[2] = a.k2 << 11;
+  const uint32_t first = range_lo[0];
+  const uint32_t count = range_hi[1] - first;
+  for (uint32_t base = gw * 64u; base < count; base += n_warps * 64u) {
+    TbRead t[2];
+#pragma unroll
+    for (int X = 0; X < 2; ++X) {
+      const uint32_t li = base + 2 * lane + X;
+      t[X] = tb_load(a, li < count, li < count ? list[first + li] : 0u);
+      if (t[X].has && t[X].w > kTbPMaxW) {  // routed by band width, so never expected: keep the scratch in bounds
+        atomicOr(a.status, kStInternal);
+        t[X].has = false;
+      }
+      uint32_t* q = sq + X * kTbPQ;
+      uint32_t* r = sr + X * kTbPR;
+      if (!t[X].has) continue;
+      const uint32_t* row = a.rpack + static_cast<uint64_t>(t[X].rd) * kReadWords;
+      for (int w = 0; w < kTbPQ; ++w) q[w] = row[w];
+      // band offsets 16 w .. 16 w + 15 hold window positions dlo + 16 w + b:
+      // reference words realigned; positions before the reference start or past
+      // j* (never needed) read as 0
+      const int64_t nref = static_cast<int64_t>((t[X].ws + t[X].jstar) >> 4) + 1;
+      for (int w = 0; w < kTbPR; ++w) {
+        const int64_t P = static_cast<int64_t>(t[X].ws) + t[X].dlo + 16 * w;
+        uint32_t v = 0u;
+        if (t[X].dlo + 16 * w <= static_cast<int>(t[X].jstar)) {
+          const int64_t wi = P >> 4;  // floor
+          const uint32_t sh = static_cast<uint32_t>(P & 15) * 2u;
+          const uint32_t lo = (wi >= 0 && wi <= nref) ? t[X].ref[wi] : 0u;
+          const uint32_t hi = (wi + 1 >= 0 && wi + 1 <= nref) ? t[X].ref[wi + 1] : 0u;
+          v = __funnelshift_r(lo, hi, sh);
+        }
+        r[w] = v;
+      }
+    }
+    uint32_t wmax = 0;
+#pragma unroll
+    for (int X = 0; X < 2; ++X) wmax = max(wmax, t[X].has ? static_cast<uint32_t>(t[X].w) : 0u);
+    wmax = __reduce_max_sync(FULL, wmax);
+    if (wmax <= 4)
+      tb_pair_reads<4>(a, t, dirs, sq, sr, c);
+    else if (wmax <= 8)
+      tb_pair_reads<8>(a, t, dirs, sq, sr, c);
+    else
+      tb_pair_reads<16>(a, t, dirs, sq, sr, c);
+  }
+}
+
 // Routing: clears reads without a winner, writes the CIGAR of reads matched
 // base for base (no DP needed), picks each other winner's traceback kernel
 // (band <= 1 / 2 / 4 / 8 / 16 / 32 / 64 diagonals, else the full-rectangle kernel) and counts the
@@ -1330,6 +1644,7 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   a.sb = sc.sb;
   a.go = sc.go;
   a.ge = sc.ge;
+  a.k2 = 2u;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1365,6 +1680,19 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
     ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
   };
+  // bands of at most 16 diagonals (buckets 0-4) with packed scores: two reads
+  // per thread, one launch
+  auto pairs = [&]() -> bool {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tb_pair, 32 * kTbPWarps, 0) != cudaSuccess)
+      return false;
+    const uint32_t cap = static_cast<uint32_t>(nsm) * static_cast<uint32_t>(per_sm > 0 ? per_sm : 1) * kTbPWarps;
+    const uint32_t nw = std::min(tb_pair_warps(b.n_reads), cap);  // within the carved scratch
+    k_tb_pair<<<(nw + kTbPWarps - 1) / kTbPWarps, 32 * kTbPWarps, 0, lane_of()>>>(a, list, ranges + 2 * 0,
+                                                                               ranges + 2 * 4, b.tb_dirs, nw);
+    ++launched;
+    return cudaPeekAtLastError() == cudaSuccess;
+  };
   // the packed wavefront of one bucket (4: SEG 16, 5: SEG 32) as three launches
   // by rows (kernels with smaller shared extents hold more warps per SM)
   auto wave4 = [&](auto k256, auto k192, auto k128, int bucket, int per_warp) -> bool {
@@ -1376,9 +1704,7 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   if (!wave(k_tb_wave2, 6, 2) ||
       !(pair ? wave4(k_tb_wave4<32, 256>, k_tb_wave4<32, 192>, k_tb_wave4<32, 128>, 5, 4)
              : wave(k_tb_wave<32>, 5, 2)) ||
-      !(pair ? wave4(k_tb_wave4<16, 256>, k_tb_wave4<16, 192>, k_tb_wave4<16, 128>, 4, 8)
-             : wave(k_tb_wave<16>, 4, 4)) ||
-      !threads())
+      !(pair ? pairs() : (wave(k_tb_wave<16>, 4, 4) && threads())))
     return -1;
   const size_t smem = static_cast<size_t>(kMaxWinLen) * 32 * sizeof(uint32_t);
   static bool attr = false;

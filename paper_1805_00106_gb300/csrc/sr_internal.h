@@ -96,6 +96,7 @@ struct BatchDev {
   uint32_t* tb_list = nullptr;    // 2 * n_reads: per-read sort code, then reads sorted by code
   uint32_t* tb_count = nullptr;   // kTbCountWords: code histogram, cursors, bucket ranges
   uint32_t* tb_dirs = nullptr;    // tb_dirs_words(n_reads): narrow-band direction words
+  uint32_t* tb_dirs32 = nullptr;  // tb_dirs32_words(n_reads): direction words of 17-32-diagonal bands
   uint32_t* cigar_off = nullptr;  // n_reads + 1 (exclusive scan of lengths)
   uint32_t* cigar = nullptr;      // compacted, n_reads * kCigarStride capacity
   uint8_t* read_class = nullptr;  // n_reads
@@ -134,6 +135,18 @@ constexpr uint64_t kTbPairWarpWords = 256ull * 4 * 32;
 inline uint32_t tb_pair_warps(uint32_t n_reads) {
   const uint32_t w = (n_reads + 63u) / 64u;
   return w < kTbPairMaxWarps ? (w ? w : 1u) : kTbPairMaxWarps;
+}
+// warps of its 32-cell variant (bands of 17-32 diagonals, a few percent of the
+// reads: warps for up to 1/8 of the batch, more reads take more rounds; each
+// owns 256 rows x 8 words x 32 lanes)
+constexpr uint32_t kTbPair32MaxWarps = 2432;  // 152 SMs x 16, its residency on GB300
+constexpr uint64_t kTbPair32WarpWords = 256ull * 8 * 32;
+inline uint32_t tb_pair32_warps(uint32_t n_reads) {
+  const uint32_t w = (n_reads + 511u) / 512u;
+  return w < kTbPair32MaxWarps ? (w ? w : 1u) : kTbPair32MaxWarps;
+}
+inline uint64_t tb_dirs32_words(uint32_t n_reads) {
+  return static_cast<uint64_t>(tb_pair32_warps(n_reads)) * kTbPair32WarpWords;
 }
 // the narrow-band scratch serves whichever of the two kernels runs
 inline uint64_t tb_dirs_words(uint32_t n_reads) {

@@ -399,6 +399,7 @@ uint64_t carve_batch(BatchDev& d, uint32_t n, uint64_t nb, uint64_t nc, uint32_t
   c.take(d.tb_list, 2ull * n);
   c.take(d.tb_count, kTbCountWords);
   c.take(d.tb_dirs, tb_dirs_words(n));
+  c.take(d.tb_dirs32, tb_dirs32_words(n));
   c.take(d.out_best, n);
   c.take(d.out_per_ref, static_cast<uint64_t>(n) * n_refs);
   StageCheck* pc;
@@ -441,6 +442,7 @@ void rebase_batch(BatchDev& d, char* base) {
   rebase(d.tb_list, base);
   rebase(d.tb_count, base);
   rebase(d.tb_dirs, base);
+  rebase(d.tb_dirs32, base);
   rebase(d.out_best, base);
   rebase(d.out_per_ref, base);
   rebase(d.check, base);

@@ -1226,11 +1226,15 @@ __global__ void __launch_bounds__(32 * kTbTWarps) k_tb_thread(TbArgs a, const ui
 // nibbles in the low half and read B's in the high half, in a per-warp scratch
 // laid out [row][word][lane] so that a warp's stores coalesce.
 constexpr int kTbPWarps = 4;                     // warps per block
-constexpr int kTbPMaxW = 16;                     // cells per row at most
 constexpr int kTbPQ = kReadWords;                // staged query words per read
-constexpr int kTbPR = kMaxReadLen / 16 + 1;      // staged window words per read (band offsets 0 .. 271)
-constexpr int kTbPLane = 2 * kTbPQ + 2 * kTbPR + 1;  // per-lane shared words (odd: conflict-free)
-static_assert(kTbPLane % 2 == 1, "odd per-lane stride");
+// staged window words per read for rows of at most MAXW cells (band offsets
+// 0 .. 255 + MAXW - 1, read by funnel shifts of consecutive words)
+template <int MAXW>
+__host__ __device__ constexpr int tbp_rwords() { return (kMaxReadLen + MAXW - 1) / 16 + 1; }
+// per-lane shared words [query A][query B][window A][window B] (odd: conflict-free)
+template <int MAXW>
+__host__ __device__ constexpr int tbp_lane() { return 2 * kTbPQ + 2 * tbp_rwords<MAXW>() + 1; }
+static_assert(tbp_lane<16>() % 2 == 1 && tbp_lane<32>() % 2 == 1, "odd per-lane stride");
 
 struct TbPairConst {
   uint32_t NEG2, ONE2, NGOE2, NGE2, tab;
@@ -1273,16 +1277,46 @@ __device__ __forceinline__ void tbp_walk(const TbArgs& a, const TbRead& t, uint3
     uint32_t op;
     if (state == 0) {
       if (h == 0) break;
-      const uint32_t nib = nib_at(i, kk);
-      if (nib & 1u) {
-        op = 0u;  // M
-        h -= (tbp_qcode(q, t, i) ^ cm) == tbp_rcode(r, j - 1 - t.dlo) ? a.sa : -a.sb;
-        --i;
-        --j;
-      } else {
-        state = (nib & 2u) ? 1 : 2;
+      // a run of up to 8 diagonal steps: the words of band cell kk in rows
+      // i .. i - 7 load together, so a run pays one memory latency, not eight
+      uint32_t wv[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        wv[c] = i - c >= 1 ? dirs[static_cast<uint32_t>((i - 1 - c) * Q + (kk >> 2)) * 32u] : 0u;
+      const int sh = sh0 + 4 * (kk & 3);
+      int L = 0;
+      bool run = true;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (run) {
+          const int ii = i - c, jj = j - c;
+          const uint32_t nib = ((wv[c] >> sh) & 15u) ^ 15u;
+          if (ii < 1 || jj < 1 || h == 0 || !(nib & 1u)) {
+            run = false;
+          } else {
+            h -= (tbp_qcode(q, t, ii) ^ cm) == tbp_rcode(r, jj - 1 - t.dlo) ? a.sa : -a.sb;
+            ++L;
+          }
+        }
+      }
+      if (L == 0) {  // (i, j) did not come from the diagonal: a gap ends here
+        state = ((((wv[0] >> sh) & 15u) ^ 15u) & 2u) ? 1 : 2;
         continue;
       }
+      i -= L;
+      j -= L;
+      if (cur_op == 0u) {
+        cur_len += static_cast<uint32_t>(L);
+      } else {
+        if (nr + 4 >= static_cast<uint32_t>(kCigarStride)) {
+          bad = true;
+          break;
+        }
+        if (cur_len) out[1 + nr++] = (cur_len << 4) | cur_op;
+        cur_op = 0u;  // M
+        cur_len = static_cast<uint32_t>(L);
+      }
+      continue;
     } else {
       op = state == 1 ? 2u : 1u;  // D : I
       if (op == 2u) {
@@ -1342,12 +1376,14 @@ __device__ __forceinline__ void tbp_walk(const TbArgs& a, const TbRead& t, uint3
   hp->cigar_len = nc;
 }
 
-// the band DP of a thread's two reads (W cells per row), then both walks
-template <int W>
+// the band DP of a thread's two reads (W cells per row), then both walks; RW
+// window words are staged per read
+template <int W, int RW>
 __device__ __forceinline__ void tb_pair_reads(const TbArgs& a, const TbRead (&t)[2], uint32_t* dirs,
                                               const uint32_t* sq, const uint32_t* sr, const TbPairConst& c) {
-  static_assert(W == 4 || W == 8 || W == 16, "cells per row");
-  constexpr int Q = W / 4;  // direction words per row
+  static_assert(W == 4 || W == 8 || W == 16 || W == 32, "cells per row");
+  constexpr int Q = W / 4;                 // direction words per row
+  constexpr int NS = W > 16 ? 2 : 1;       // 16-cell code slices per row
   const int rows = max(t[0].has ? t[0].ihi : 0, t[1].has ? t[1].ihi : 0);
   uint32_t Hp[W], Fp[W];  // the row above: H, and the F it sends down-left
 #pragma unroll
@@ -1355,16 +1391,17 @@ __device__ __forceinline__ void tb_pair_reads(const TbArgs& a, const TbRead (&t)
     Hp[k] = 0u;
     Fp[k] = c.NGOE2;
   }
-  // per read: the complement mask of its query codes, the virtual-cell mask of
-  // the row (pattern 01 in the 2-bit code of every cell left of column 1), the
-  // rows where the band crosses column j* inside [ilo, ihi], and i*
+  // per read: the complement mask of its query codes, the shift of its
+  // virtual-cell mask, the rows where the band crosses column j* inside
+  // [ilo, ihi], and i*
   uint32_t cmask[2], ist[2];
   int lsh[2], clo[2], chi[2];
 #pragma unroll
   for (int X = 0; X < 2; ++X) {
     cmask[X] = t[X].strand ? 0xffffffffu : 0u;
-    // cells k < 1 - i - dlo lie left of column 1: the row's mask is 0x55555555
-    // shifted right by 32 - 2 (1 - i - dlo), clamped to 0 .. 32
+    // cells k < 1 - i - dlo lie left of column 1: in a row's first slice they are
+    // the low cells of 0x55555555 shifted right by 32 - 2 (1 - i - dlo) (clamped
+    // to 0 .. 32), in the second slice by 32 more
     lsh[X] = 32 + 2 * t[X].dlo;
     const int jd = static_cast<int>(t[X].jstar) - t[X].dlo;  // row where cell 0 is column j*
     clo[X] = t[X].has ? max(t[X].ilo, jd - W + 1) : 1;
@@ -1374,20 +1411,24 @@ __device__ __forceinline__ void tb_pair_reads(const TbArgs& a, const TbRead (&t)
   const uint32_t* q0 = sq;
   const uint32_t* q1 = sq + kTbPQ;
   const uint32_t* r0 = sr;
-  const uint32_t* r1 = sr + kTbPR;
+  const uint32_t* r1 = sr + RW;
   for (int i = 1; i <= rows; ++i) {
-    // mismatch bits of the row (bit 2k: cell k), per read
-    uint32_t nb[2];
+    // mismatch bits of the row (slice s, bit 2k: cell 16 s + k), per read
+    uint32_t nb[2][NS];
 #pragma unroll
     for (int X = 0; X < 2; ++X) {
       const uint32_t* q = X ? q1 : q0;
       const uint32_t* r = X ? r1 : r0;
       const int u = i - 1;  // band offset of cell 0
-      const uint32_t sl = __funnelshift_r(r[u >> 4], r[(u >> 4) + 1], (u & 15) * 2);
-      const uint32_t lm = __funnelshift_rc(0x55555555u, 0u, static_cast<uint32_t>(max(lsh[X], 0)));
+      const uint32_t qr = imad_u32(tbp_qcode(q, t[X], i), 0x55555555u, 0u) ^ cmask[X];
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        const uint32_t cw = __funnelshift_r(r[(u >> 4) + sl], r[(u >> 4) + sl + 1], (u & 15) * 2);
+        const uint32_t lm = __funnelshift_rc(0x55555555u, 0u, static_cast<uint32_t>(max(lsh[X] + 32 * sl, 0)));
+        const uint32_t x = (cw ^ qr) | lm;
+        nb[X][sl] = (x | (x >> 1)) & 0x55555555u;
+      }
       lsh[X] += 2;
-      const uint32_t x = (sl ^ imad_u32(tbp_qcode(q, t[X], i), 0x55555555u, 0u) ^ cmask[X]) | lm;
-      nb[X] = (x | (x >> 1)) & 0x55555555u;
     }
     uint32_t E = c.NGOE2;  // arriving at cell 0 from outside the band
     uint32_t acc = 0u, sA = 0u, sB = 0u;
@@ -1396,8 +1437,9 @@ __device__ __forceinline__ void tb_pair_reads(const TbArgs& a, const TbRead (&t)
     for (int k = 0; k < W; ++k) {
       if ((k & 3) == 0) {
         // cells k .. k + 3: mismatch bits at 0, 2, 4, 6 -> bytes 0x80 + 0x11 n
-        const uint32_t bA = tb_prmt(nb[0], 0u, 0x4440u | static_cast<uint32_t>(k >> 2));
-        const uint32_t bB = tb_prmt(nb[1], 0u, 0x4440u | static_cast<uint32_t>(k >> 2));
+        const uint32_t sel4 = 0x4440u | static_cast<uint32_t>((k >> 2) & 3);
+        const uint32_t bA = tb_prmt(nb[0][k >> 4], 0u, sel4);
+        const uint32_t bB = tb_prmt(nb[1][k >> 4], 0u, sel4);
         sA = imad_u32(imad_u32(bA, 0x41041u, 0u) & 0x01010101u, 0x11u, 0x80808080u);
         sB = imad_u32(imad_u32(bB, 0x41041u, 0u) & 0x01010101u, 0x11u, 0x80808080u);
       }
@@ -1436,18 +1478,22 @@ __device__ __forceinline__ void tb_pair_reads(const TbArgs& a, const TbRead (&t)
   if (t[1].has) tbp_walk(a, t[1], ist[1], 1, dirs, Q, q1, r1);
 }
 
-// Reads of bands up to 16 diagonals, in band-width order, 64 per warp: each warp
-// runs the narrowest row width (4, 8 or 16 cells) that holds its reads.
+// Reads of bands up to MAXW diagonals (16: buckets 0-4, each warp running the
+// narrowest row width, 4, 8 or 16 cells, that holds its reads; 32: bucket 5),
+// in band-width order, 64 per warp.
+template <int MAXW>
 __global__ void __launch_bounds__(32 * kTbPWarps) k_tb_pair(TbArgs a, const uint32_t* list, const uint32_t* range_lo,
                                                           const uint32_t* range_hi, uint32_t* scratch,
                                                           uint32_t n_warps) {
-  __shared__ uint32_t s_s[kTbPWarps][32 * kTbPLane];
+  constexpr int RW = tbp_rwords<MAXW>();
+  constexpr int LANE = tbp_lane<MAXW>();
+  __shared__ uint32_t s_s[kTbPWarps][32 * LANE];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const uint32_t gw = blockIdx.x * kTbPWarps + warp;
   if (gw >= n_warps) return;
-  uint32_t* dirs = scratch + static_cast<uint64_t>(gw) * kMaxReadLen * (kTbPMaxW / 4) * 32 + lane;
-  uint32_t* sq = s_s[warp] + lane * kTbPLane;  // [query A][query B][window A][window B]
+  uint32_t* dirs = scratch + static_cast<uint64_t>(gw) * kMaxReadLen * (MAXW / 4) * 32 + lane;
+  uint32_t* sq = s_s[warp] + lane * LANE;  // [query A][query B][window A][window B]
   uint32_t* sr = sq + 2 * kTbPQ;
   auto pack2 = [](int32_t v) { return (static_cast<uint32_t>(v) & 0xffffu) * 0x10001u; };
   const int32_t goe = a.go + a.ge;
@@ -1469,12 +1515,12 @@ __global__ void __launch_bounds__(32 * kTbPWarps) k_tb_pair(TbArgs a, const uint
     for (int X = 0; X < 2; ++X) {
       const uint32_t li = base + 2 * lane + X;
       t[X] = tb_load(a, li < count, li < count ? list[first + li] : 0u);
-      if (t[X].has && t[X].w > kTbPMaxW) {  // routed by band width, so never expected: keep the scratch in bounds
+      if (t[X].has && t[X].w > MAXW) {  // routed by band width, so never expected: keep the scratch in bounds
         atomicOr(a.status, kStInternal);
         t[X].has = false;
       }
       uint32_t* q = sq + X * kTbPQ;
-      uint32_t* r = sr + X * kTbPR;
+      uint32_t* r = sr + X * RW;
       if (!t[X].has) continue;
       const uint32_t* row = a.rpack + static_cast<uint64_t>(t[X].rd) * kReadWords;
       for (int w = 0; w < kTbPQ; ++w) q[w] = row[w];
@@ -1482,7 +1528,7 @@ __global__ void __launch_bounds__(32 * kTbPWarps) k_tb_pair(TbArgs a, const uint
       // reference words realigned; positions before the reference start or past
       // j* (never needed) read as 0
       const int64_t nref = static_cast<int64_t>((t[X].ws + t[X].jstar) >> 4) + 1;
-      for (int w = 0; w < kTbPR; ++w) {
+      for (int w = 0; w < RW; ++w) {
         const int64_t P = static_cast<int64_t>(t[X].ws) + t[X].dlo + 16 * w;
         uint32_t v = 0u;
         if (t[X].dlo + 16 * w <= static_cast<int>(t[X].jstar)) {
@@ -1495,16 +1541,20 @@ __global__ void __launch_bounds__(32 * kTbPWarps) k_tb_pair(TbArgs a, const uint
         r[w] = v;
       }
     }
-    uint32_t wmax = 0;
+    if (MAXW == 32) {
+      tb_pair_reads<32, RW>(a, t, dirs, sq, sr, c);
+    } else {
+      uint32_t wmax = 0;
 #pragma unroll
-    for (int X = 0; X < 2; ++X) wmax = max(wmax, t[X].has ? static_cast<uint32_t>(t[X].w) : 0u);
-    wmax = __reduce_max_sync(FULL, wmax);
-    if (wmax <= 4)
-      tb_pair_reads<4>(a, t, dirs, sq, sr, c);
-    else if (wmax <= 8)
-      tb_pair_reads<8>(a, t, dirs, sq, sr, c);
-    else
-      tb_pair_reads<16>(a, t, dirs, sq, sr, c);
+      for (int X = 0; X < 2; ++X) wmax = max(wmax, t[X].has ? static_cast<uint32_t>(t[X].w) : 0u);
+      wmax = __reduce_max_sync(FULL, wmax);
+      if (wmax <= 4)
+        tb_pair_reads<4, RW>(a, t, dirs, sq, sr, c);
+      else if (wmax <= 8)
+        tb_pair_reads<8, RW>(a, t, dirs, sq, sr, c);
+      else
+        tb_pair_reads<16, RW>(a, t, dirs, sq, sr, c);
+    }
   }
 }
 
@@ -1682,14 +1732,17 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   };
   // bands of at most 16 diagonals (buckets 0-4) with packed scores: two reads
   // per thread, one launch
-  auto pairs = [&]() -> bool {
+  // bands of at most 16 diagonals (buckets 0-4) and of 17-32 (bucket 5) with
+  // packed scores: two reads per thread, one launch each, each with a scratch of
+  // its own
+  auto pairs = [&](auto kern, int b0, int b1, uint32_t nw_max, uint32_t* scratch) -> bool {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tb_pair, 32 * kTbPWarps, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kTbPWarps, 0) != cudaSuccess)
       return false;
     const uint32_t cap = static_cast<uint32_t>(nsm) * static_cast<uint32_t>(per_sm > 0 ? per_sm : 1) * kTbPWarps;
-    const uint32_t nw = std::min(tb_pair_warps(b.n_reads), cap);  // within the carved scratch
-    k_tb_pair<<<(nw + kTbPWarps - 1) / kTbPWarps, 32 * kTbPWarps, 0, lane_of()>>>(a, list, ranges + 2 * 0,
-                                                                               ranges + 2 * 4, b.tb_dirs, nw);
+    const uint32_t nw = std::min(nw_max, cap);  // within the carved scratch
+    kern<<<(nw + kTbPWarps - 1) / kTbPWarps, 32 * kTbPWarps, 0, lane_of()>>>(a, list, ranges + 2 * b0,
+                                                                          ranges + 2 * b1, scratch, nw);
     ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
   };
@@ -1702,9 +1755,10 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   // widest bands (longest kernels) first
   const bool pair = tb_pair_fits(a.sa, a.sb, a.go, a.ge);
   if (!wave(k_tb_wave2, 6, 2) ||
-      !(pair ? wave4(k_tb_wave4<32, 256>, k_tb_wave4<32, 192>, k_tb_wave4<32, 128>, 5, 4)
+      !(pair ? pairs(k_tb_pair<32>, 5, 5, tb_pair32_warps(b.n_reads), b.tb_dirs32)
              : wave(k_tb_wave<32>, 5, 2)) ||
-      !(pair ? pairs() : (wave(k_tb_wave<16>, 4, 4) && threads())))
+      !(pair ? pairs(k_tb_pair<16>, 0, 4, tb_pair_warps(b.n_reads), b.tb_dirs)
+             : (wave(k_tb_wave<16>, 4, 4) && threads())))
     return -1;
   const size_t smem = static_cast<size_t>(kMaxWinLen) * 32 * sizeof(uint32_t);
   static bool attr = false;

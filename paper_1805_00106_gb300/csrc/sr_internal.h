@@ -113,11 +113,7 @@ struct BatchDev {
 enum : uint8_t { kTbFlagBand = 0, kTbFlagFull = 1, kTbFlagRow = 2 };
 constexpr int kTbBuckets = 8;                        // band <= 1 / 2 / 4 / 8 / 16 / 32 / 64 diagonals, full
 constexpr int kTbCodes = kTbBuckets * kMaxReadLen;   // code = bucket * 256 + (256 - last row)
-// sub-ranges of the packed-wavefront buckets (bands 9-16 and 17-32) by the rows
-// their reads' DP runs: over 192, 129-192, up to 128 (kernels sized for each)
-constexpr int kTbRowClasses = 3;
-constexpr int kTbSplitWords = 2 * 2 * kTbRowClasses;
-constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + kTbSplitWords + 8;
+constexpr int kTbCountWords = 2 * kTbCodes + 2 * kTbBuckets + 8;
 constexpr int kTbMaxBand = 64;
 // warps of the one-thread-per-read narrow-band traceback (each owns a scratch
 // of 256 rows x 32 lanes of direction words): 152 SMs x 32, its register-bound

@@ -2,12 +2,14 @@
 // arXiv 1805.00106: the reported alignment of Sec. 4.2 / SAM output, whose
 // traceback the paper runs on the host, Sec. 6.4).
 //
-// Most winners are traced by a banded DP that also finds the end row i*: one
-// thread per read for bands of at most 8 diagonals (k_tb_thread), a wavefront
-// over the band's diagonals for 9-32 (k_tb_wave4, or k_tb_wave when the scores
-// do not fit its 16-bit values) and two diagonals per lane for 33-64
-// (k_tb_wave2).  Winners whose band is wider than 64 diagonals, and int32-class
-// winners, use k_traceback: one warp
+// Most winners are traced by a banded DP that also finds the end row i*: two
+// reads per thread in the 16-bit halves of each value, swept row by row, for
+// bands of at most 16 diagonals (k_tb_pair<16>) and of 17-32 (k_tb_pair<32>);
+// when the scores do not fit those 16-bit values, one thread per read for at
+// most 8 diagonals (k_tb_thread) and a wavefront over the band's diagonals for
+// 9-32 (k_tb_wave); two diagonals per lane for 33-64 (k_tb_wave2).  Winners
+// whose band is wider than 64 diagonals, and int32-class winners, use
+// k_traceback: one warp
 // per read recomputes the DP of the winning window in exact int32 over rows
 // 1..m and columns 1..j* only (j* = the end column found by the extension
 // kernels; cells right of j* cannot influence the path) with the same systolic
@@ -633,29 +635,7 @@ __global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave(TbArgs a, const uint3
   }
 }
 
-// ---- The same wavefront with two reads per lane, in the 16-bit halves of each
-// value (DPX s16x2 arithmetic).  A segment holds four reads: pair 0 (reads 0,
-// 1) takes the place of read A above and pair 1 (reads 2, 3) that of read B.
-// The codes are staged per pair as 16-bit words indexed by row (query) and by
-// band offset t = i - 1 + k (window), with codes that never match outside the
-// read and the window, so a cell needs no range test: the XOR of its two words
-// is the prmt selector that picks both reads' scores from a byte table.  Each
-// cell stores its 4 bits inverted (1 = not equal): H = diagonal value, H = E,
-// En = the opened gap value, Fn = the opened gap value, tested per half by
-// min(XOR, 1).  Scores and gap costs must fit the byte table and keep every
-// value inside 16 bits (tb_pair_fits).
-// Shared-memory extents of a packed wavefront whose reads' DP runs at most
-// ROWS rows (256, 192 or 128; smaller extents let more warps reside per SM)
-constexpr int kTb4QOff = 16;  // query word of row i at i - 1 + kTb4QOff
-constexpr int kTb4ROff = 32;  // window word of band offset t at t + kTb4ROff
-template <int ROWS>
-struct Tb4Ext {
-  static constexpr int QN = ROWS + 3 * kTbRowPad;    // rows -15 .. ROWS + 32
-  static constexpr int RN = ROWS + 6 * kTbRowPad;    // offsets -32 .. ROWS + 63
-  static constexpr int Rows = ROWS + 2 * kTbRowPad + 1;
-  static_assert(QN % 16 == 0 && RN % 16 == 0, "whole 16-code chunks");
-};
-
+// byte permute (prmt.b32) and a multiply-add that stays a multiply-add
 __device__ __forceinline__ uint32_t tb_prmt(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
   asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
@@ -667,210 +647,9 @@ __device__ __forceinline__ uint32_t imad_u32(uint32_t a, uint32_t b, uint32_t c)
   return d;
 }
 
-// 16 packed codes at positions lo .. lo + 15 of a 2-bit array of nw words (0
-// for words outside it)
-__device__ __forceinline__ uint32_t tb_codes16(const uint32_t* w, int64_t lo, int64_t nw) {
-  const int64_t i = lo >> 4;  // floor
-  const uint32_t sh = static_cast<uint32_t>(lo & 15) * 2u;
-  const uint32_t x = (i >= 0 && i < nw) ? w[i] : 0u;
-  const uint32_t y = (i + 1 >= 0 && i + 1 < nw) ? w[i + 1] : 0u;
-  return sh ? (x >> sh) | (y << (32u - sh)) : x;
-}
-
-// A pair's query words for rows 16 c - 15 .. 16 c (code 4 outside the read) and
-// its window words for band offsets 16 c - 32 .. 16 c - 17 (code 5 outside
-// columns 1..j*), from the packed read rows and reference: one chunk of 16
-// words per call, a few loads instead of one per code.
-__device__ __forceinline__ uint32_t tb_qchunk(const TbArgs& a, const TbRead& x, int c, uint32_t* valid) {
-  *valid = 0u;
-  const int i0 = 16 * (c - 1);  // first 0-based row of the chunk (chunks are word-aligned)
-  if (!x.has || i0 < 0) return 0u;
-  const uint32_t* row = a.rpack + static_cast<uint64_t>(x.rd) * kReadWords;
-  const int m = static_cast<int>(x.m);
-  const int n = min(max(m - i0, 0), 16);
-  *valid = n >= 16 ? 0xffffu : ((1u << n) - 1u);
-  if (!n) return 0u;
-  if (!x.strand) return tb_codes16(row, i0, kReadWords);
-  // reverse complement: row i0 + b holds 3 - base(m - 1 - i0 - b)
-  uint32_t v = __brev(tb_codes16(row, m - 16 - i0, kReadWords));
-  v = ((v >> 1) & 0x55555555u) | ((v & 0x55555555u) << 1);
-  return ~v;
-}
-__device__ __forceinline__ uint32_t tb_rchunk(const TbRead& x, int c, uint32_t* valid) {
-  *valid = 0u;
-  if (!x.has) return 0u;
-  const int j0 = 16 * c - kTb4ROff + x.dlo;  // first 0-based window column of the chunk
-  uint32_t v = 0u;
-#pragma unroll
-  for (int b = 0; b < 16; ++b) v |= (j0 + b >= 0 && j0 + b < static_cast<int>(x.jstar)) ? (1u << b) : 0u;
-  *valid = v;
-  if (!v) return 0u;
-  const int64_t nw = static_cast<int64_t>((x.ws + x.jstar + 15) / 16) + 1;
-  return tb_codes16(x.ref, static_cast<int64_t>(x.ws) + j0, nw);
-}
-
-// codes of one read of a pair, for the walk
-struct PairCodes {
-  const uint16_t* q;
-  const uint16_t* r;
-  int shift;  // 0: the pair's low read, 8: its high read
-  int dlo;
-  __device__ __forceinline__ bool match(uint32_t, uint32_t, uint32_t i0, uint32_t j0) const {
-    const uint32_t x = static_cast<uint32_t>(q[static_cast<int>(i0) + kTb4QOff]) ^
-                       static_cast<uint32_t>(r[static_cast<int>(j0) - dlo + kTb4ROff]);
-    return ((x >> shift) & 7u) == 0u;
-  }
-};
-
-template <int SEG, int ROWS>
-__global__ void __launch_bounds__(32 * kTbWarps) k_tb_wave4(TbArgs a, const uint32_t* list, const uint32_t* range) {
-  constexpr int NSEG = 32 / SEG;
-  constexpr int kTb4QN = Tb4Ext<ROWS>::QN, kTb4RN = Tb4Ext<ROWS>::RN;
-  __shared__ uint16_t dirs_s[kTbWarps][NSEG][Tb4Ext<ROWS>::Rows * SEG];
-  __shared__ uint16_t q_s[kTbWarps][NSEG * 2][kTb4QN];
-  __shared__ uint16_t r_s[kTbWarps][NSEG * 2][kTb4RN];
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int seg = lane / SEG;
-  const int k = lane % SEG;
-  const uint32_t seg_mask = SEG == 32 ? FULL : (((1u << SEG) - 1u) << (seg * SEG));
-  uint16_t* dirs = dirs_s[warp][seg] + kTbRowPad * SEG;
-  const int32_t goe = a.go + a.ge;
-  auto pack2 = [](int32_t v) { return (static_cast<uint32_t>(v) & 0xffffu) * 0x10001u; };
-  const uint32_t NEG2 = 0x80008000u, ONE2 = 0x00010001u, NGOE2 = pack2(-goe), NGE2 = pack2(-a.ge);
-  const uint32_t nsb = static_cast<uint32_t>(-a.sb) & 0xffu;
-  const uint32_t tab_lo = (static_cast<uint32_t>(a.sa) & 0xffu) | nsb * 0x01010100u, tab_hi = nsb * 0x01010101u;
-  const uint32_t begin = range[0];
-  const uint32_t count = range[1] - begin;
-  constexpr uint32_t kPerWarp = 4 * NSEG;
-  const uint32_t stride = gridDim.x * kTbWarps * kPerWarp;
-  for (uint32_t base = (blockIdx.x * kTbWarps + warp) * kPerWarp; base < count; base += stride) {
-    TbRead rd[4];
-#pragma unroll
-    for (int X = 0; X < 4; ++X) {
-      const uint32_t li = base + 4 * seg + X;
-      rd[X] = tb_load(a, li < count, li < count ? list[begin + li] : 0u);
-      if (rd[X].has && rd[X].ihi > ROWS) {  // routed by rows, so never expected: keep shared memory in bounds
-        atomicOr(a.status, kStInternal);
-        rd[X].has = false;
-      }
-    }
-#pragma unroll
-    for (int P = 0; P < 2; ++P) {
-      uint16_t* q = q_s[warp][seg * 2 + P];
-      uint16_t* r = r_s[warp][seg * 2 + P];
-      for (int c = k; c < kTb4QN / 16; c += SEG) {
-        uint32_t ma, mb;
-        const uint32_t va = tb_qchunk(a, rd[2 * P], c, &ma), vb = tb_qchunk(a, rd[2 * P + 1], c, &mb);
-#pragma unroll 2
-        for (int b = 0; b < 16; ++b) {
-          const uint32_t lo = (ma >> b) & 1u ? (va >> (2 * b)) & 3u : 4u;
-          const uint32_t hi = (mb >> b) & 1u ? (vb >> (2 * b)) & 3u : 4u;
-          q[16 * c + b] = static_cast<uint16_t>(lo | ((lo | 8u) << 4) | (hi << 8) | ((hi | 8u) << 12));
-        }
-      }
-      for (int c = k; c < kTb4RN / 16; c += SEG) {
-        uint32_t ma, mb;
-        const uint32_t va = tb_rchunk(rd[2 * P], c, &ma), vb = tb_rchunk(rd[2 * P + 1], c, &mb);
-#pragma unroll 2
-        for (int b = 0; b < 16; ++b) {
-          const uint32_t lo = (ma >> b) & 1u ? (va >> (2 * b)) & 3u : 5u;
-          const uint32_t hi = (mb >> b) & 1u ? (vb >> (2 * b)) & 3u : 5u;
-          r[16 * c + b] = static_cast<uint16_t>(lo | (lo << 4) | (hi << 8) | (hi << 12));
-        }
-      }
-    }
-    __syncwarp();
-    int st = 0;
-#pragma unroll
-    for (int X = 0; X < 4; ++X) st = max(st, rd[X].has ? 2 * (rd[X].ihi - 1) + rd[X].w : 0);
-    const int nmax = static_cast<int>(__reduce_max_sync(FULL, static_cast<uint32_t>(st + 1)));
-    const int p = k & 1;
-    // per read on this lane's diagonal: the lower band edge and the row crossing j*
-    TbSub u[4];
-#pragma unroll
-    for (int X = 0; X < 4; ++X) u[X] = tb_sub(rd[X], k, 0u, 0u);
-    // half-step 0 runs pair p, half-step 1 the other pair
-    const TbSub& l0 = p ? u[2] : u[0];
-    const TbSub& h0 = p ? u[3] : u[1];
-    const TbSub& l1 = p ? u[0] : u[2];
-    const TbSub& h1 = p ? u[1] : u[3];
-    const uint32_t keep0 = (l0.bd ? 0u : 0xffffu) | (h0.bd ? 0u : 0xffff0000u);
-    const uint32_t keep1 = (l1.bd ? 0u : 0xffffu) | (h1.bd ? 0u : 0xffff0000u);
-    const int cl0 = l0.icr, ch0 = h0.icr, cl1 = l1.icr, ch1 = h1.icr;
-    const int P0 = p, P1 = 1 - p;
-    const uint16_t* q0 = q_s[warp][seg * 2 + P0] + (kTb4QOff - 1);  // [i]: row i
-    const uint16_t* q1 = q_s[warp][seg * 2 + P1] + (kTb4QOff - 1);
-    const uint16_t* r0 = r_s[warp][seg * 2 + P0] + (kTb4ROff - 1 + k);  // [i]: row i on this diagonal
-    const uint16_t* r1 = r_s[warp][seg * 2 + P1] + (kTb4ROff - 1 + k);
-    uint32_t Ha = 0, Hb = 0, Ena = NGOE2, Fna = NGOE2, Enb = NGOE2, Fnb = NGOE2;
-    uint32_t xl0 = 0, xh0 = 0, xl1 = 0, xh1 = 0;  // H where the diagonal crosses j*
-    int ia = 1 - ((k + p) >> 1);
-    uint8_t* d0 = reinterpret_cast<uint8_t*>(dirs + (ia - 1) * SEG + k) + P0;
-    uint8_t* d1 = reinterpret_cast<uint8_t*>(dirs + (ia + p - 1) * SEG + k) + P1;
-    uint32_t x0 = static_cast<uint32_t>(q0[ia]) ^ static_cast<uint32_t>(r0[ia]);
-    uint32_t x1 = static_cast<uint32_t>(q1[ia + p]) ^ static_cast<uint32_t>(r1[ia + p]);
-    auto cell = [&](uint32_t E, uint32_t F, uint32_t x, uint32_t& hd, uint32_t& En, uint32_t& Fn) {
-      const uint32_t hs = __viaddmax_s16x2(hd, tb_prmt(tab_lo, tab_hi, x), NEG2);
-      const uint32_t H = __vimax3_s16x2_relu(hs, E, F);
-      const uint32_t g = __viaddmax_s16x2(H, NGOE2, NEG2);
-      En = __viaddmax_s16x2(E, NGE2, g);
-      Fn = __viaddmax_s16x2(F, NGE2, g);
-      const uint32_t z = __vimin3_u16x2(H ^ hs, ONE2, ONE2) + 2u * __vimin3_u16x2(H ^ E, ONE2, ONE2) +
-                         4u * __vimin3_u16x2(En ^ g, ONE2, ONE2) + 8u * __vimin3_u16x2(Fn ^ g, ONE2, ONE2);
-      hd = H;
-      return z | (z >> 12);
-    };
-    for (int t = 0; t < nmax; t += 2, ++ia, d0 += 2 * SEG, d1 += 2 * SEG) {
-      // the next pair of steps' code words, loaded ahead
-      const uint32_t qn0 = q0[ia + 1], rn0 = r0[ia + 1], qn1 = q1[ia + 1 + p], rn1 = r1[ia + 1 + p];
-      {
-        uint32_t E = __shfl_up_sync(FULL, Enb, 1, SEG);
-        uint32_t F = __shfl_down_sync(FULL, Fnb, 1, SEG);
-        if (k == 0) E = NGOE2;
-        F = (F & keep0) | (NGOE2 & ~keep0);
-        *d0 = static_cast<uint8_t>(cell(E, F, x0, Ha, Ena, Fna));
-        xl0 = ia == cl0 ? Ha : xl0;
-        xh0 = ia == ch0 ? Ha : xh0;
-      }
-      {
-        uint32_t E = __shfl_up_sync(FULL, Ena, 1, SEG);
-        uint32_t F = __shfl_down_sync(FULL, Fna, 1, SEG);
-        if (k == 0) E = NGOE2;
-        F = (F & keep1) | (NGOE2 & ~keep1);
-        const int ib = ia + p;
-        *d1 = static_cast<uint8_t>(cell(E, F, x1, Hb, Enb, Fnb));
-        xl1 = ib == cl1 ? Hb : xl1;
-        xh1 = ib == ch1 ? Hb : xh1;
-      }
-      x0 = qn0 ^ rn0;
-      x1 = qn1 ^ rn1;
-    }
-    // end row of each read: smallest crossing row whose H is the score
-    auto ic = [](int icr, int32_t hx, int32_t S) { return (icr > 0 && hx == S) ? static_cast<uint32_t>(icr) : kNoRow; };
-    const int32_t sl0 = static_cast<int16_t>(xl0 & 0xffffu), sh0 = static_cast<int16_t>(xh0 >> 16);
-    const int32_t sl1 = static_cast<int16_t>(xl1 & 0xffffu), sh1 = static_cast<int16_t>(xh1 >> 16);
-    const uint32_t il0 = ic(cl0, sl0, p ? rd[2].S : rd[0].S), ih0 = ic(ch0, sh0, p ? rd[3].S : rd[1].S);
-    const uint32_t il1 = ic(cl1, sl1, p ? rd[0].S : rd[2].S), ih1 = ic(ch1, sh1, p ? rd[1].S : rd[3].S);
-    uint32_t iend[4] = {p ? il1 : il0, p ? ih1 : ih0, p ? il0 : il1, p ? ih0 : ih1};
-#pragma unroll
-    for (int X = 0; X < 4; ++X)
-#pragma unroll
-      for (int off = SEG / 2; off > 0; off >>= 1) iend[X] = min(iend[X], __shfl_xor_sync(FULL, iend[X], off, SEG));
-    __syncwarp();
-#pragma unroll
-    for (int X = 0; X < 4; ++X) {
-      const PairCodes pc{q_s[warp][seg * 2 + (X >> 1)], r_s[warp][seg * 2 + (X >> 1)], 8 * (X & 1), rd[X].dlo};
-      tb_walk<SEG, SEG, PairCodes, uint16_t, 15u>(a, walk_of(rd[X]), iend[X], 4 * X, dirs, pc, 0u, 0u, k, seg_mask,
-                                                 SEG == 32 ? 0 : seg * SEG);
-      __syncwarp(seg_mask);
-    }
-    __syncwarp();
-  }
-}
-
-// whether the packed wavefront holds these scores: byte-table scores, and every
-// cell value (>= -(go+ge), <= the int16-class score) inside 16 bits
+// whether the packed (two reads per thread) kernels hold these scores:
+// byte-table scores, and every cell value (>= -(go+ge), <= the int16-class
+// score) inside 16 bits
 bool tb_pair_fits(int32_t sa, int32_t sb, int32_t go, int32_t ge) {
   return sa >= 1 && sa <= 127 && sb >= 1 && sb <= 128 && static_cast<int64_t>(go) + ge <= 8192;
 }
@@ -1642,14 +1421,6 @@ __global__ void __launch_bounds__(kTbScanThreads) k_tb_scan(uint32_t* cnt) {
     cnt[2 * kTbCodes + 2 * t] = cnt[kTbCodes + c0];
     cnt[2 * kTbCodes + 2 * t + 1] = cnt[kTbCodes + c1 - 1] + cnt[c1 - 1];
   }
-  if (t < 2 * kTbRowClasses) {
-    // buckets 4 and 5 by rows: codes b * 256 + [0, 64) run 193-256 rows, [64, 128)
-    // 129-192, [128, 256) at most 128
-    const int b = 4 + t / kTbRowClasses, rc = t % kTbRowClasses;
-    const int c0 = b * kMaxReadLen + 64 * rc, c1 = rc == kTbRowClasses - 1 ? (b + 1) * kMaxReadLen : c0 + 64;
-    cnt[2 * kTbCodes + 2 * kTbBuckets + 2 * t] = cnt[kTbCodes + c0];
-    cnt[2 * kTbCodes + 2 * kTbBuckets + 2 * t + 1] = cnt[kTbCodes + c1 - 1] + cnt[c1 - 1];
-  }
 }
 
 __global__ void k_tb_scatter(uint32_t n_reads, const uint32_t* code, uint32_t* cursor, uint32_t* list) {
@@ -1745,12 +1516,6 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
                                                                           ranges + 2 * b1, scratch, nw);
     ++launched;
     return cudaPeekAtLastError() == cudaSuccess;
-  };
-  // the packed wavefront of one bucket (4: SEG 16, 5: SEG 32) as three launches
-  // by rows (kernels with smaller shared extents hold more warps per SM)
-  auto wave4 = [&](auto k256, auto k192, auto k128, int bucket, int per_warp) -> bool {
-    const int sub = 2 * kTbBuckets + 2 * kTbRowClasses * (bucket - 4);
-    return wave(k256, sub / 2, per_warp) && wave(k192, sub / 2 + 1, per_warp) && wave(k128, sub / 2 + 2, per_warp);
   };
   // widest bands (longest kernels) first
   const bool pair = tb_pair_fits(a.sa, a.sb, a.go, a.ge);

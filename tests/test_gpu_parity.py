@@ -342,6 +342,49 @@ def test_traceback_band_classes(sr):
     _check(gpu_run(s, w), o)
 
 
+def test_traceback_reads_overhanging_the_window_start(sr):
+    """Reads whose first o bases (1..40) lie before their window's start, from
+    both strands: the alignment is soft-clipped at the read's start and its band
+    reaches left of column 1 by about o diagonals, so the two-reads-per-thread
+    kernels run rows whose first cells are virtual (in the first 16-cell slice,
+    and for o > 16 in the second slice of the 32-cell rows)."""
+    rng = np.random.default_rng(31)
+    acgt = np.frombuffer(b"ACGT", np.uint8)
+    comp = np.zeros(256, np.uint8)
+    comp[list(b"ACGT")] = list(b"TGCA")
+    ref = rng.choice(acgt, 300_000)
+    reads, offs, over = [], [0], []
+    cands = dict(cand_off=[0], c_ref=[], c_strand=[], c_start=[], c_len=[])
+    for r in range(1200):
+        m = int(rng.integers(80, 257))
+        o = int(rng.integers(1, 41))
+        pos = int(rng.integers(1000, len(ref) - 1000))
+        q = ref[pos:pos + m].copy()
+        hit = rng.random(m) < [0.0, 0.01, 0.03][r % 3]
+        q[hit] = rng.choice(acgt, int(hit.sum()))
+        strand = r % 2
+        if strand:
+            q = comp[q[::-1]]  # the read as sequenced from the other strand
+        reads.append(q)
+        offs.append(offs[-1] + m)
+        over.append(o)
+        cands["c_ref"].append(0)
+        cands["c_strand"].append(strand)
+        cands["c_start"].append(pos + o)
+        cands["c_len"].append(m + 64 - o)
+        cands["cand_off"].append(len(cands["c_ref"]))
+    w = dict(refs=[ref], bases=np.concatenate(reads), read_off=np.array(offs, np.int64),
+             **{k: np.array(v) for k, v in cands.items()})
+    o_run = oracle_run(w)
+    ok, w_all, _ = _band_widths(w, o_run)
+    over = np.array(over)
+    assert np.sum(ok & (w_all <= 16) & (over >= 4)) > 50
+    assert np.sum(ok & (w_all > 16) & (w_all <= 32) & (over > 16)) > 50
+    assert np.all(o_run["best"]["read_start"][ok] > 1)
+    s = _session(sr, w)
+    _check(gpu_run(s, w), o_run)
+
+
 def test_bad_window_in_a_large_batch_reports_the_first(sr):
     """Batches of 64k reads and more are validated in parallel on the host pool:
     the first malformed window (lowest index) is reported, before any launch."""

@@ -620,7 +620,7 @@ def main():
     sess = sr.Session.open([bytes(r) for r in w["refs"]])
     spp = sr.score_params(*SP)
     if not args.no_tune:
-        sr.lib().sr_tune(sess.h, sr.C.byref(spp), 8192)
+        sr.lib().sr_tune(sess.h, sr.C.byref(spp), 32768)
     stream = torch.cuda.Stream()
     batch = sess.stage(w["bases"], w["read_off"], w["cand_off"], w["c_ref"], w["c_strand"],
                        w["c_start"], w["c_len"], stream=stream.cuda_stream)

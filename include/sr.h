@@ -425,8 +425,10 @@ sr_status sr_serve_stop(sr_session* s);
 
 /* ------------------------------------------------------------ autotuner
  * Measures candidate kernel shapes (lanes per alignment x rows per lane) for
- * each read-length bin on a synthetic sample on the current GPU and keeps the
- * fastest; the table is used by SR_ENGINE_BATCHED.  save/load use a small text
+ * each read-length bin on a synthetic sample of sample_reads reads (0: 4096)
+ * with 6 windows each on the current GPU and keeps the fastest, unless the
+ * bin's current shape is within 1.5% of it (then the current shape stays); the
+ * table is used by SR_ENGINE_BATCHED.  save/load use a small text
  * file keyed by device name.  sr_tune_get writes up to cap entries of
  * (bin upper read length, lanes, rows). */
 sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t sample_reads);

@@ -215,15 +215,15 @@ __device__ __forceinline__ uint32_t read_code(const uint32_t* row, uint32_t m, u
 // bound by the ALU pipe and the latency of its DPX chains, so resident warps
 // count).  Persistent kernels: up to 12 rows per lane fit 80 registers (6
 // blocks, 24 warps per SM), up to 17 rows 96 (16 in final-row mode, which keeps
-// more per row; 5 blocks), up to 24 rows (22) 128 (4 blocks), up to 27 rows 168
-// (3 blocks), more up to 255.  The one-launch (plain) kernels keep the 128
+// more per row; 5 blocks), up to 24 rows (22) 128 (4 blocks), up to 32 rows
+// (30) 168 (3 blocks), more up to 255.  The one-launch (plain) kernels keep the 128
 // register budget up to 24 rows.  None of them spills.
 template <int R, int MODE, bool PERSIST>
 constexpr int ext_min_blocks() {
   return (PERSIST && R <= 12) ? 6
          : (PERSIST && R <= (MODE == 1 ? 16 : 17)) ? 5
          : R <= (MODE == 1 ? 22 : 24) ? 4
-         : (R <= 27 ? 3 : 2);
+         : (R <= (MODE == 1 ? 30 : 32) ? 3 : 2);
 }
 
 template <int G, int R, int MODE, bool PERSIST>

@@ -44,7 +44,7 @@ static TuneBin g_bins[kNumBins] = {
     {64, 4, 16},   {80, 8, 10},   {96, 8, 12},   {104, 8, 13},  {112, 8, 14},  {120, 8, 15},
     {128, 8, 16},  {136, 8, 17},  {144, 8, 18},  {152, 8, 19},  {160, 8, 20},  {168, 8, 21},
     {176, 8, 22},  {184, 8, 23},  {192, 8, 24},  {200, 8, 25},  {208, 8, 26},  {216, 8, 27},
-    {224, 16, 14}, {232, 16, 15}, {240, 16, 15}, {248, 16, 16}, {256, 16, 16}};
+    {224, 8, 28},  {232, 8, 29},  {240, 8, 30},  {248, 8, 31},  {256, 8, 32}};
 
 void tune_get_bins(TuneBin* out) {
   std::lock_guard<std::mutex> g(g_tune_mu);
@@ -2195,7 +2195,7 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
     sr_batch* b = nullptr;
     st = batch_stage_internal(s, &rd, &cl, nullptr, false, &b);
     if (st != SR_OK) break;
-    float best_ms = 1e30f;
+    float best_ms = 1e30f, cur_ms = -1.0f;
     TuneBin pick = cur[bi];
     for (int q = 0; q < n_shapes; ++q) {
       const uint32_t sh[2] = {sh_lanes[q], sh_rows[q]};
@@ -2216,12 +2216,17 @@ extern "C" sr_status sr_tune(sr_session* s, const sr_score_params* sp, uint32_t 
       cudaEventElapsedTime(&tot, e0, e1);
       if (verbose)
         fprintf(stderr, "sr_tune bin<=%u lanes %u rows %u: %.3f ms for 5 runs\n", m, sh[0], sh[1], tot);
+      if (sh[0] == cur[bi].lanes && sh[1] == cur[bi].rows) cur_ms = tot;
       if (tot < best_ms) {
         best_ms = tot;
         pick = TuneBin{m, sh[0], sh[1]};
       }
     }
     sr_batch_free(b);
+    // the bin's current shape stays unless a candidate beats it by more than
+    // 1.5%: a persistent grid's tail on the sample is about that size, and the
+    // sample runs alone where the batch's bins share the device
+    if (cur_ms > 0.0f && best_ms > cur_ms / 1.015f) pick = cur[bi];
     cur[bi] = pick;
   }
   cudaEventDestroy(e0);

@@ -132,13 +132,14 @@ inline uint32_t tb_pair_warps(uint32_t n_reads) {
   const uint32_t w = (n_reads + 63u) / 64u;
   return w < kTbPairMaxWarps ? (w ? w : 1u) : kTbPairMaxWarps;
 }
-// warps of its 32-cell variant (bands of 17-32 diagonals, a few percent of the
-// reads: warps for up to 1/8 of the batch, more reads take more rounds; each
-// owns 256 rows x 8 words x 32 lanes)
+// warps of its 32-cell variant (bands of 17-32 diagonals: a few percent of
+// short reads, more of long ones; warps for up to half of the batch's reads,
+// more take more rounds, each a latency-bound pass; each warp owns 256 rows x 8
+// words x 32 lanes)
 constexpr uint32_t kTbPair32MaxWarps = 2432;  // 152 SMs x 16, its residency on GB300
 constexpr uint64_t kTbPair32WarpWords = 256ull * 8 * 32;
 inline uint32_t tb_pair32_warps(uint32_t n_reads) {
-  const uint32_t w = (n_reads + 511u) / 512u;
+  const uint32_t w = (n_reads + 127u) / 128u;
   return w < kTbPair32MaxWarps ? (w ? w : 1u) : kTbPair32MaxWarps;
 }
 inline uint64_t tb_dirs32_words(uint32_t n_reads) {

@@ -555,6 +555,131 @@ __global__ void k_cal_offsets(const uint32_t* woff, uint32_t nr, uint64_t base, 
   if (i <= nr) out[i] = base + woff[i];
 }
 
+namespace {
+constexpr int kScanBlock64 = 1024;
+
+// per block: exclusive scan of the counts (64-bit), the block's total into sums
+__global__ void __launch_bounds__(kScanBlock64) k_scan64_a(const uint32_t* in, uint32_t n, uint64_t* out,
+                                                         uint64_t* sums) {
+  __shared__ uint64_t sh[kScanBlock64];
+  const uint32_t i = blockIdx.x * kScanBlock64 + threadIdx.x;
+  const uint64_t v = i < n ? in[i] : 0u;
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int d = 1; d < kScanBlock64; d <<= 1) {
+    const uint64_t x = threadIdx.x >= static_cast<unsigned>(d) ? sh[threadIdx.x - d] : 0ull;
+    __syncthreads();
+    sh[threadIdx.x] += x;
+    __syncthreads();
+  }
+  if (i < n) out[i] = sh[threadIdx.x] - v;
+  if (threadIdx.x == kScanBlock64 - 1) sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+// one block: exclusive scan of the block totals in place, the total into *end
+__global__ void __launch_bounds__(kScanBlock64) k_scan64_b(uint64_t* sums, uint32_t nb, uint64_t* end) {
+  __shared__ uint64_t sh[kScanBlock64];
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t b0 = 0; b0 < nb; b0 += kScanBlock64) {
+    const uint32_t i = b0 + threadIdx.x;
+    const uint64_t v = i < nb ? sums[i] : 0ull;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int d = 1; d < kScanBlock64; d <<= 1) {
+      const uint64_t x = threadIdx.x >= static_cast<unsigned>(d) ? sh[threadIdx.x - d] : 0ull;
+      __syncthreads();
+      sh[threadIdx.x] += x;
+      __syncthreads();
+    }
+    if (i < nb) sums[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += sh[kScanBlock64 - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *end = carry;
+}
+
+__global__ void k_scan64_c(uint64_t* out, uint32_t n, const uint64_t* sums) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += sums[i / kScanBlock64];
+}
+
+// the filter's routing of reads by their CAL bounds (big: nullptr to take the
+// maxima only)
+__global__ void k_cal_route(const uint32_t* count, uint32_t nr, uint32_t* big, uint64_t* big_soff, CalPlan* plan) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t c = i < nr ? count[i] : 0u;
+  uint32_t small = 0, mid = 0;
+  if (i < nr) {
+    if (c > kCalSmemKeys) {
+      if (big) {
+        const uint32_t b = atomicAdd(&plan->n_big, 1u);
+        big[b] = i;
+        big_soff[b] = atomicAdd(&plan->scratch, static_cast<unsigned long long>(cal_filter_words(pow2_at_least(c))));
+      }
+    } else if (c > kCalSmallKeys) {
+      mid = c;
+    } else {
+      small = c;
+    }
+  }
+  const uint32_t all = __reduce_max_sync(FULL, c);
+  small = __reduce_max_sync(FULL, small);
+  mid = __reduce_max_sync(FULL, mid);
+  if ((threadIdx.x & 31) == 0) {
+    if (small) atomicMax(&plan->max_small, small);
+    if (mid) atomicMax(&plan->max_mid, mid);
+    if (all) atomicMax(&plan->max_all, all);
+  }
+}
+
+// bounds[p / span] = the first read whose prefix p = pre[r] falls in that span
+__global__ void k_cal_bounds(const uint64_t* pre, uint32_t nr, uint64_t span, uint32_t* bounds) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const uint64_t j = pre[r] / span;
+  if (r == 0 || pre[r - 1] / span != j) bounds[j] = r;
+}
+
+// out[i] = pre[a + i] - pre[a], i = 0 .. cnt, 64- or 32-bit
+__global__ void k_cal_rebase(const uint64_t* pre, uint32_t a, uint32_t cnt, uint64_t* out64, uint32_t* out32) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > cnt) return;
+  const uint64_t v = pre[a + i] - pre[a];
+  if (out64) out64[i] = v;
+  else out32[i] = static_cast<uint32_t>(v);
+}
+}  // namespace
+
+int launch_scan_u64(const uint32_t* in, uint32_t n, uint64_t* out, uint64_t* sums, cudaStream_t st) {
+  const uint32_t nb = (n + kScanBlock64 - 1) / kScanBlock64;
+  if (nb) k_scan64_a<<<nb, kScanBlock64, 0, st>>>(in, n, out, sums);
+  k_scan64_b<<<1, kScanBlock64, 0, st>>>(sums, nb, out + n);
+  if (nb) k_scan64_c<<<(n + 255) / 256, 256, 0, st>>>(out, n, sums);
+  return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
+}
+
+int launch_cal_route(const uint32_t* count, uint32_t nr, uint32_t* big, uint64_t* big_soff, CalPlan* plan,
+                     cudaStream_t st) {
+  if (nr == 0) return 0;
+  k_cal_route<<<(nr + 255) / 256, 256, 0, st>>>(count, nr, big, big_soff, plan);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_cal_bounds(const uint64_t* pre, uint32_t nr, uint64_t span, uint32_t* bounds, cudaStream_t st) {
+  if (nr == 0) return 0;
+  k_cal_bounds<<<(nr + 255) / 256, 256, 0, st>>>(pre, nr, span, bounds);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_cal_rebase(const uint64_t* pre, uint32_t a, uint32_t cnt, uint64_t* out64, uint32_t* out32,
+                      cudaStream_t st) {
+  k_cal_rebase<<<(cnt + 256) / 256, 256, 0, st>>>(pre, a, cnt, out64, out32);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int launch_cal_offsets(const uint32_t* woff, uint32_t nr, uint64_t base, uint64_t* out, cudaStream_t st) {
   k_cal_offsets<<<(nr + 256) / 256, 256, 0, st>>>(woff, nr, base, out);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

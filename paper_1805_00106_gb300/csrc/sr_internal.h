@@ -277,7 +277,7 @@ constexpr uint32_t kCalSmallKeys = 1024;  // reads up to this many CALs: small-b
 constexpr uint32_t kCalSmemKeys = 8192;   // up to this many: filtered in shared memory (192 KB)
 // shared or scratch words (u64) the filter of a read of up to P CALs uses (P a
 // power of two): its keys, each window's best run, run and window start positions
-constexpr uint64_t cal_filter_words(uint64_t P) { return 3 * P + 1; }
+__host__ __device__ constexpr uint64_t cal_filter_words(uint64_t P) { return 3 * P + 1; }
 // count pass (cals == nullptr: an upper bound of the CALs of each read into
 // count, exact unless a seed is its own reverse complement; reads with bad
 // offsets or over kMaxReadLen bases set kStBadRead) or emit pass (CAL keys of
@@ -311,6 +311,27 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
                       uint32_t* whits, uint32_t* wlen, cudaStream_t st);
 // out[i] = base + woff[i] for i = 0 .. nr (a chunk's window offsets in the whole list)
 int launch_cal_offsets(const uint32_t* woff, uint32_t nr, uint64_t base, uint64_t* out, cudaStream_t st);
+// exclusive 64-bit scan of n counts into out[0..n] (out[n] = the total) with a
+// scratch of n / 1024 + 1 words (sr_cal.cu)
+int launch_scan_u64(const uint32_t* in, uint32_t n, uint64_t* out, uint64_t* sums, cudaStream_t st);
+// The CAL filter's routing of nr reads by their CAL bounds: reads over
+// kCalSmemKeys CALs listed in big (indices into the reads, in any order) with
+// their scratch offsets in big_soff, and the largest small, mid-size and
+// overall bound; big = nullptr takes the maxima only.  plan must be zeroed.
+struct CalPlan {
+  unsigned long long scratch;  // scratch words of the listed large reads
+  unsigned int n_big, max_small, max_mid, max_all;
+};
+int launch_cal_route(const uint32_t* count, uint32_t nr, uint32_t* big, uint64_t* big_soff, CalPlan* plan,
+                     cudaStream_t st);
+// cuts of a prefix sum pre[0..nr) into pieces of span: bounds[j] = the first
+// index whose prefix lies in [j span, (j + 1) span) (every j up to
+// pre[nr - 1] / span has one when no single count reaches span)
+int launch_cal_bounds(const uint64_t* pre, uint32_t nr, uint64_t span, uint32_t* bounds, cudaStream_t st);
+// a piece's prefix sums from 0: out[i] = pre[a + i] - pre[a] for i = 0 .. cnt
+// into out64 or, when it is nullptr, out32
+int launch_cal_rebase(const uint64_t* pre, uint32_t a, uint32_t cnt, uint64_t* out64, uint32_t* out32,
+                      cudaStream_t st);
 int launch_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,
                        const uint64_t* wkey, const uint32_t* whits, const uint32_t* wlen, uint8_t* o_ref,
                        uint8_t* o_strand, uint64_t* o_start, uint32_t* o_len, uint32_t* o_hits, cudaStream_t st);

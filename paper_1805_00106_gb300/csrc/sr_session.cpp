@@ -120,6 +120,20 @@ bool res_create(BatchRes& r) {
 }
 constexpr size_t kResPool = 16;
 constexpr size_t kKeptArenas = 3;
+// a positive integer from the environment, else dflt
+uint64_t env_u64(const char* name, uint64_t dflt) {
+  const char* v = getenv(name);
+  if (!v || !*v) return dflt;
+  char* end = nullptr;
+  const unsigned long long x = strtoull(v, &end, 10);
+  return (end && *end == 0 && x > 0) ? static_cast<uint64_t>(x) : dflt;
+}
+// roles of the device CAL finder's cached scratch buffers
+enum CalBuf : int {
+  kCbBases, kCbRoff, kCbCount, kCbActual, kCbStatus, kCbSlots, kCbPre, kCbSums, kCbBounds, kCbPlan,
+  kCbRanges, kCbSeedOff, kCbRecount, kCbCpre, kCbOff, kCbNwin, kCbWoff, kCbWsums, kCbBig, kCbBigOff,
+  kCbCals, kCbWkey, kCbWhits, kCbWlen, kCbOref, kCbOstr, kCbOstart, kCbOlen, kCbOhits, kCbScratch, kCalBufs
+};
 }  // namespace
 
 struct sr_session {
@@ -150,6 +164,11 @@ struct sr_session {
   // streams and events of freed batches
   std::mutex res_mu;
   std::vector<BatchRes> res_pool;
+  // scratch of the device CAL finder by role, kept between calls and grown on
+  // demand (not counted in hbm_used); one sr_candidates_device call at a time
+  std::mutex cal_mu;
+  void* cal_buf[kCalBufs] = {};
+  uint64_t cal_bytes[kCalBufs] = {};
 };
 
 struct sr_batch {
@@ -300,6 +319,8 @@ static void session_release(sr_session* s) {
   for (auto& b : s->pool) cudaFreeHost(b.first);
   for (auto& r : s->res_pool) res_destroy(r);
   for (auto& a : s->spares) cudaFree(a.first);
+  for (void* p : s->cal_buf)
+    if (p) cudaFree(p);
   if (s->stream) cudaStreamDestroy(s->stream);
   for (auto x : s->part_stream)
     if (x) cudaStreamDestroy(x);
@@ -1388,13 +1409,32 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     }
     nb = reads->offsets[n];
   }
-  std::vector<void*> bufs;
+  // the call's scratch comes from the session's cache (grown with a quarter of
+  // headroom when a call needs more), so steady-state calls allocate only
+  // their result list
+  std::lock_guard<std::mutex> cal_lock(s->cal_mu);
   cudaError_t e = cudaSuccess;
-  auto dalloc = [&](uint64_t bytes) -> void* {
-    void* d = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&d, bytes ? bytes : 1);
-    if (e == cudaSuccess) bufs.push_back(d);
-    return e == cudaSuccess ? d : nullptr;
+  auto cbuf = [&](int role, uint64_t bytes) -> void* {
+    if (e != cudaSuccess) return nullptr;
+    bytes = std::max<uint64_t>(bytes, 16);
+    if (s->cal_bytes[role] < bytes) {
+      if (s->cal_buf[role]) {
+        // earlier launches of this call may still use the smaller buffer
+        e = cudaStreamSynchronize(st);
+        cudaFree(s->cal_buf[role]);
+        s->cal_buf[role] = nullptr;
+        s->cal_bytes[role] = 0;
+        if (e != cudaSuccess) return nullptr;
+      }
+      const uint64_t want = bytes + bytes / 4;
+      e = cudaMalloc(&s->cal_buf[role], want);
+      if (e != cudaSuccess) {
+        s->cal_buf[role] = nullptr;
+        return nullptr;
+      }
+      s->cal_bytes[role] = want;
+    }
+    return s->cal_buf[role];
   };
   // the result list: host arrays, or device arrays grown chunk by chunk
   sr_cand_list* l = static_cast<sr_cand_list*>(calloc(1, sizeof(sr_cand_list)));
@@ -1404,7 +1444,6 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
   uint64_t cap_out = 0;  // windows the device result arrays hold
   auto done = [&](sr_status stt, const char* msg) -> sr_status {
     cudaStreamSynchronize(st);
-    for (auto* p : bufs) cudaFree(p);
     cudaGetLastError();
     if (stt == SR_OK) return static_cast<sr_status>(SR_OK);
     sr_cand_list_free(l);
@@ -1463,11 +1502,17 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
   };
   uint64_t total_w = 0;
   if (n) {
-    const char* d_bases = in_dev ? reads->bases : static_cast<const char*>(dalloc(nb));
-    const uint64_t* d_roff = in_dev ? reads->offsets : static_cast<const uint64_t*>(dalloc((n + 1ull) * 8));
-    uint32_t* d_count = static_cast<uint32_t*>(dalloc(n * 4ull));
-    uint32_t* d_actual = static_cast<uint32_t*>(dalloc(n * 4ull));
-    uint32_t* d_status = static_cast<uint32_t*>(dalloc(4));
+    const char* d_bases = in_dev ? reads->bases : static_cast<const char*>(cbuf(kCbBases, nb));
+    const uint64_t* d_roff = in_dev ? reads->offsets : static_cast<const uint64_t*>(cbuf(kCbRoff, (n + 1ull) * 8));
+    uint32_t* d_count = static_cast<uint32_t*>(cbuf(kCbCount, n * 4ull));
+    uint32_t* d_actual = static_cast<uint32_t*>(cbuf(kCbActual, n * 4ull));
+    uint32_t* d_status = static_cast<uint32_t*>(cbuf(kCbStatus, 4));
+    // per read: its lookup records (seeds x references), then their prefix sums
+    uint32_t* d_slots = static_cast<uint32_t*>(cbuf(kCbSlots, n * 4ull));
+    uint64_t* d_pre = static_cast<uint64_t*>(cbuf(kCbPre, (n + 1ull) * 8));
+    uint64_t* d_sums = static_cast<uint64_t*>(cbuf(kCbSums, (n / 1024 + 2ull) * 8));
+    uint32_t* d_bounds = static_cast<uint32_t*>(cbuf(kCbBounds, (n + 1ull) * 4));
+    CalPlan* d_plan = static_cast<CalPlan*>(cbuf(kCbPlan, sizeof(CalPlan)));
     if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
     if (!in_dev) {
       if (nb) e = cudaMemcpyAsync(const_cast<char*>(d_bases), reads->bases, nb, cudaMemcpyHostToDevice, st);
@@ -1476,207 +1521,211 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 4, st);
     if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
-    // lookup records (seeds x references) of every read, for the count pass to
-    // keep its lookups for the emit pass; read chunks of at most kRangeRecords
-    uint32_t* d_slots = static_cast<uint32_t*>(dalloc(n * 4ull));
-    if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-    if (launch_cal_slots(d_roff, n, s->didx.k, cp.seed_stride, s->didx.n_refs, d_slots, d_status, st) < 0) {
+    // The count pass keeps each seed's lookup (one record per seed and
+    // reference) for the emit pass.  Reads run in chunks of at most
+    // kRangeRecords records: a chunk is cut where the records' prefix sum crosses
+    // a multiple of kRangeRecords less one read's most records, so that no chunk
+    // exceeds it; all cuts are made on the device.
+    const uint64_t rec_read = (static_cast<uint64_t>(kMaxReadLen) / cp.seed_stride + 1) * s->didx.n_refs;
+    // 1 GiB of kept lookups at most; SR_CAL_CHUNK_RECORDS lowers it (tests of the cuts)
+    const uint64_t kRangeRecords = std::max<uint64_t>(env_u64("SR_CAL_CHUNK_RECORDS", 128ull << 20), 2 * rec_read);
+    const uint64_t rec_span = kRangeRecords - rec_read;
+    uint64_t ends[2] = {};  // prefix of the last read, total records
+    uint32_t status = 0;
+    if (launch_cal_slots(d_roff, n, s->didx.k, cp.seed_stride, s->didx.n_refs, d_slots, d_status, st) < 0 ||
+        launch_scan_u64(d_slots, n, d_pre, d_sums, st) < 0 || launch_cal_bounds(d_pre, n, rec_span, d_bounds, st) < 0) {
       e = cudaGetLastError();
       return done(SR_ECUDA, "sr_candidates_device slots");
     }
-    std::vector<uint32_t> slots(n);
-    uint32_t status = 0;
-    e = cudaMemcpyAsync(slots.data(), d_slots, n * 4ull, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(ends, d_pre + n - 1, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device slots copy");
     if (status & kStBadRead) return done(SR_EINVAL, "sr_candidates_device: decreasing read offsets or a read longer than 256 bases");
-    constexpr uint64_t kRangeRecords = 128ull << 20;  // 1 GiB of kept lookups at most
-    std::vector<uint32_t> rchunk{0};                   // read chunk boundaries
-    uint64_t max_rec = 0;
+    const uint32_t n_chunks = static_cast<uint32_t>(ends[0] / rec_span) + 1;
+    std::vector<uint32_t> rchunk(n_chunks + 1ull);
+    e = cudaMemcpyAsync(rchunk.data(), d_bounds, n_chunks * 4ull, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device chunks");
+    rchunk[n_chunks] = n;
     uint32_t max_reads = 0;
-    {
-      uint64_t acc = 0;
-      for (uint32_t r = 0; r < n; ++r) {
-        if (acc + slots[r] > kRangeRecords && r > rchunk.back()) {
-          max_rec = std::max(max_rec, acc);
-          max_reads = std::max(max_reads, r - rchunk.back());
-          rchunk.push_back(r);
-          acc = 0;
-        }
-        acc += slots[r];
-      }
-      max_rec = std::max(max_rec, acc);
-      max_reads = std::max(max_reads, n - rchunk.back());
-      rchunk.push_back(n);
-    }
-    uint64_t* d_ranges = static_cast<uint64_t*>(dalloc(std::max<uint64_t>(max_rec, 1) * 8));
-    uint32_t* d_seed_off = static_cast<uint32_t*>(dalloc((max_reads + 1ull) * 4));
-    uint8_t* d_recount = static_cast<uint8_t*>(dalloc(max_reads + 1ull));
-    std::vector<uint32_t> count(n);
-    // the emit / filter buffers, sized for the largest read chunk (its CAL bounds are known
-    // once its count pass ran): allocated on the first chunk, grown when a chunk needs more
-    uint64_t cap = 0;
-    uint64_t *d_cals = nullptr, *d_wkey = nullptr, *d_ostart = nullptr, *d_off = nullptr, *d_bigoff = nullptr;
-    uint32_t *d_whits = nullptr, *d_wlen = nullptr, *d_olen = nullptr, *d_ohits = nullptr, *d_nwin = nullptr,
-             *d_woff = nullptr, *d_sums = nullptr, *d_big = nullptr;
-    uint8_t *d_oref = nullptr, *d_ostr = nullptr;
-    d_off = static_cast<uint64_t*>(dalloc(max_reads * 8ull + 8));
-    d_nwin = static_cast<uint32_t*>(dalloc(max_reads * 4ull + 4));
-    d_woff = static_cast<uint32_t*>(dalloc((max_reads + 1ull) * 4));
-    d_sums = static_cast<uint32_t*>(dalloc((max_reads / 1024 + 2ull) * 4));
-    d_big = static_cast<uint32_t*>(dalloc(max_reads * 4ull + 4));
-    d_bigoff = static_cast<uint64_t*>(dalloc(max_reads * 8ull + 8));
+    uint64_t max_rec = 0;
+    for (uint32_t c = 0; c < n_chunks; ++c) max_reads = std::max(max_reads, rchunk[c + 1] - rchunk[c]);
+    max_rec = std::min<uint64_t>(ends[1], kRangeRecords);
+    uint64_t* d_ranges = static_cast<uint64_t*>(cbuf(kCbRanges, std::max<uint64_t>(max_rec, 1) * 8));
+    uint32_t* d_seed_off = static_cast<uint32_t*>(cbuf(kCbSeedOff, (max_reads + 1ull) * 4));
+    uint8_t* d_recount = static_cast<uint8_t*>(cbuf(kCbRecount, max_reads + 1ull));
+    // per chunk: the prefix sums of its reads' CAL bounds, a sub-chunk's offsets
+    // (from 0) and its large-read list
+    uint64_t* d_cpre = static_cast<uint64_t*>(cbuf(kCbCpre, (max_reads + 1ull) * 8));
+    uint64_t* d_off = static_cast<uint64_t*>(cbuf(kCbOff, (max_reads + 1ull) * 8));
+    uint32_t* d_nwin = static_cast<uint32_t*>(cbuf(kCbNwin, max_reads * 4ull + 4));
+    uint32_t* d_woff = static_cast<uint32_t*>(cbuf(kCbWoff, (max_reads + 1ull) * 4));
+    uint32_t* d_wsums = static_cast<uint32_t*>(cbuf(kCbWsums, (max_reads / 1024 + 2ull) * 4));
+    uint32_t* d_big = static_cast<uint32_t*>(cbuf(kCbBig, max_reads * 4ull + 4));
+    uint64_t* d_bigoff = static_cast<uint64_t*>(cbuf(kCbBigOff, max_reads * 8ull + 8));
     if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+    // the emit / filter buffers, sized for the largest sub-chunk so far
+    uint64_t cap = 0;
+    uint64_t *d_cals = nullptr, *d_wkey = nullptr, *d_ostart = nullptr;
+    uint32_t *d_whits = nullptr, *d_wlen = nullptr, *d_olen = nullptr, *d_ohits = nullptr;
+    uint8_t *d_oref = nullptr, *d_ostr = nullptr;
     uint64_t* d_scratch = nullptr;
     uint64_t scratch_keys = 0;
-    std::vector<uint64_t> off(max_reads + 1ull), bigoff;
-    std::vector<uint32_t> big, seed_off(max_reads + 1ull);
-    for (size_t ci = 0; ci + 1 < rchunk.size(); ++ci) {
-      const uint32_t R0 = rchunk[ci], R1 = rchunk[ci + 1];
-      // this chunk's record offsets, then its count pass (which keeps the lookups)
-      uint32_t acc = 0;
-      for (uint32_t r = R0; r < R1; ++r) {
-        seed_off[r - R0] = acc;
-        acc += slots[r];
-      }
-      seed_off[R1 - R0] = acc;
-      e = cudaMemcpyAsync(d_seed_off, seed_off.data(), (R1 - R0 + 1ull) * 4, cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
-      const CalRanges kept{d_ranges, d_seed_off, d_recount, R0};
-      if (launch_cal_seeds(s->didx, d_bases, d_roff, R0, R1 - R0, cp.seed_stride, d_count + R0, nullptr, nullptr,
-                           nullptr, d_status, kept, st) < 0) {
-        e = cudaGetLastError();
-        return done(SR_ECUDA, "sr_candidates_device count");
-      }
-      e = cudaMemcpyAsync(count.data() + R0, d_count + R0, (R1 - R0) * 4ull, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
+    std::vector<uint32_t> woff, sub;
+    // one sub-chunk (reads r0 .. r0 + nr of the chunk at R0, offsets in d_off):
+    // routing, emit, filter, window offsets and the compacted windows
+    auto run_sub = [&](uint32_t r0, uint32_t nr, const CalRanges& kept) -> sr_status {
+      CalPlan plan{};
+      e = cudaMemsetAsync(d_plan, 0, sizeof(CalPlan), st);
+      if (e != cudaSuccess || launch_cal_route(d_count + r0, nr, d_big, d_bigoff, d_plan, st) < 0)
+        return done(SR_ECUDA, "sr_candidates_device route");
+      e = cudaMemcpyAsync(&plan, d_plan, sizeof(CalPlan), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device count copy");
-      if (status & kStBadRead) return done(SR_EINVAL, "sr_candidates_device: decreasing read offsets or a read longer than 256 bases");
-      if (status & kStBadBase) return done(SR_EBADBASE, "sr_candidates_device: read has a non-ACGT base");
-      // sub-chunks of reads whose CALs (upper bounds) fit the buffers
-      uint64_t sum = 0, one = 0;
-      for (uint32_t r = R0; r < R1; ++r) {
-        sum += count[r];
-        one = std::max<uint64_t>(one, count[r]);
-      }
-      const uint64_t want = std::max<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(sum, 1), 64ull << 20), one);
-      if (want > cap) {
-        cap = want;
-        d_cals = static_cast<uint64_t*>(dalloc(cap * 8));
-        d_wkey = static_cast<uint64_t*>(dalloc(cap * 8));
-        d_whits = static_cast<uint32_t*>(dalloc(cap * 4));
-        d_wlen = static_cast<uint32_t*>(dalloc(cap * 4));
-        d_oref = static_cast<uint8_t*>(dalloc(cap));
-        d_ostr = static_cast<uint8_t*>(dalloc(cap));
-        d_ostart = static_cast<uint64_t*>(dalloc(cap * 8));
-        d_olen = static_cast<uint32_t*>(dalloc(cap * 4));
-        d_ohits = static_cast<uint32_t*>(dalloc(cap * 4));
+      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device route copy");
+      if (plan.scratch > scratch_keys) {
+        d_scratch = static_cast<uint64_t*>(cbuf(kCbScratch, plan.scratch * 8));
         if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+        scratch_keys = plan.scratch;
       }
-      for (uint32_t r0 = R0; r0 < R1;) {
-        uint32_t r1 = r0;
-        uint64_t used = 0;
-        uint32_t max_small = 1, max_mid = 0;
-        uint64_t big_keys = 0;
-        big.clear();
-        bigoff.clear();
-        while (r1 < R1 && used + count[r1] <= cap) {
-          off[r1 - r0] = used;
-          used += count[r1];
-          if (count[r1] > kCalSmemKeys) {
-            uint64_t p2 = 1;
-            while (p2 < count[r1]) p2 <<= 1;
-            big.push_back(r1 - r0);
-            bigoff.push_back(big_keys);
-            big_keys += cal_filter_words(p2);
-          } else if (count[r1] > kCalSmallKeys) {
-            max_mid = std::max(max_mid, count[r1]);
-          } else {
-            max_small = std::max(max_small, count[r1]);
-          }
-          ++r1;
-        }
-        const uint32_t nr = r1 - r0;
-        if (big_keys > scratch_keys) {
-          e = cudaMalloc(&d_scratch, big_keys * 8);
-          if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-          bufs.push_back(d_scratch);
-          scratch_keys = big_keys;
-        }
-        e = cudaMemcpyAsync(d_off, off.data(), nr * 8ull, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && !big.empty()) {
-          e = cudaMemcpyAsync(d_big, big.data(), big.size() * 4ull, cudaMemcpyHostToDevice, st);
-          if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_bigoff, bigoff.data(), bigoff.size() * 8ull, cudaMemcpyHostToDevice, st);
-        }
-        if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device copy");
-        if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_actual,
-                             d_status, kept, st) < 0 ||
-            launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_actual,
-                              d_off, d_cals, max_small, max_mid, d_big, d_bigoff, static_cast<uint32_t>(big.size()),
-                              d_scratch, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
-            launch_scan_u32(d_nwin, nr, d_woff, d_sums, st) < 0) {
+      if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_actual,
+                           d_status, kept, st) < 0 ||
+          launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_actual,
+                            d_off, d_cals, std::max(plan.max_small, 1u), plan.max_mid, d_big, d_bigoff, plan.n_big,
+                            d_scratch, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
+          launch_scan_u32(d_nwin, nr, d_woff, d_wsums, st) < 0) {
+        e = cudaGetLastError();
+        return done(SR_ECUDA, "sr_candidates_device filter");
+      }
+      uint32_t nw32 = 0;
+      if (out_dev) {
+        e = cudaMemcpyAsync(&nw32, d_woff + nr, 4, cudaMemcpyDeviceToHost, st);
+      } else {
+        woff.resize(nr + 1ull);
+        e = cudaMemcpyAsync(woff.data(), d_woff, (nr + 1ull) * 4, cudaMemcpyDeviceToHost, st);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window count");
+      const uint64_t nw = out_dev ? nw32 : woff[nr];
+      if (out_dev) {
+        // this sub-chunk's offsets in the whole list, its windows compacted
+        // straight into the list's arrays after the windows so far
+        if (launch_cal_offsets(d_woff, nr, total_w, l->offsets + r0, st) < 0) {
           e = cudaGetLastError();
-          return done(SR_ECUDA, "sr_candidates_device filter");
+          return done(SR_ECUDA, "sr_candidates_device offsets");
         }
-        uint32_t nw32 = 0;
-        std::vector<uint32_t> woff;
-        if (out_dev) {
-          e = cudaMemcpyAsync(&nw32, d_woff + nr, 4, cudaMemcpyDeviceToHost, st);
-        } else {
-          woff.resize(nr + 1ull);
-          e = cudaMemcpyAsync(woff.data(), d_woff, (nr + 1ull) * 4, cudaMemcpyDeviceToHost, st);
+        if (!grow_out(total_w + nw, total_w)) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+        if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, l->ref_id + total_w,
+                               l->strand + total_w, l->win_start + total_w, l->win_len + total_w, l->hits + total_w,
+                               st) < 0) {
+          e = cudaGetLastError();
+          return done(SR_ECUDA, "sr_candidates_device compact");
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window count");
-        const uint64_t nw = out_dev ? nw32 : woff[nr];
+      } else {
         if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, d_oref, d_ostr, d_ostart, d_olen,
                                d_ohits, st) < 0) {
           e = cudaGetLastError();
           return done(SR_ECUDA, "sr_candidates_device compact");
         }
-        if (out_dev) {
-          // this chunk's offsets in the whole list, its windows appended on the device
-          if (launch_cal_offsets(d_woff, nr, total_w, l->offsets + r0, st) < 0) {
-            e = cudaGetLastError();
-            return done(SR_ECUDA, "sr_candidates_device offsets");
-          }
-          if (!grow_out(total_w + nw, total_w)) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-          if (nw) {
-            e = cudaMemcpyAsync(l->ref_id + total_w, d_oref, nw, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(l->strand + total_w, d_ostr, nw, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess)
-              e = cudaMemcpyAsync(l->win_start + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess)
-              e = cudaMemcpyAsync(l->win_len + total_w, d_olen, nw * 4, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(l->hits + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
-          }
-        } else {
-          o_ref.resize(total_w + nw);
-          o_strand.resize(total_w + nw);
-          o_start.resize(total_w + nw);
-          o_len.resize(total_w + nw);
-          o_hits.resize(total_w + nw);
-          if (nw) {
-            e = cudaMemcpyAsync(o_ref.data() + total_w, d_oref, nw, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(o_strand.data() + total_w, d_ostr, nw, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess)
-              e = cudaMemcpyAsync(o_start.data() + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(o_len.data() + total_w, d_olen, nw * 4, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(o_hits.data() + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
-          }
-          for (uint32_t i = 0; i <= nr; ++i) offsets[r0 + i] = total_w + woff[i];
+        o_ref.resize(total_w + nw);
+        o_strand.resize(total_w + nw);
+        o_start.resize(total_w + nw);
+        o_len.resize(total_w + nw);
+        o_hits.resize(total_w + nw);
+        if (nw) {
+          e = cudaMemcpyAsync(o_ref.data() + total_w, d_oref, nw, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(o_strand.data() + total_w, d_ostr, nw, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(o_start.data() + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(o_len.data() + total_w, d_olen, nw * 4, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaMemcpyAsync(o_hits.data() + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToHost, st);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+          if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
         }
-        total_w += nw;
-        r0 = r1;
+        for (uint32_t i = 0; i <= nr; ++i) offsets[r0 + i] = total_w + woff[i];
+      }
+      total_w += nw;
+      return static_cast<sr_status>(SR_OK);
+    };
+    for (uint32_t ci = 0; ci < n_chunks; ++ci) {
+      const uint32_t R0 = rchunk[ci], R1 = rchunk[ci + 1], nrc = R1 - R0;
+      // this chunk's record offsets from 0, then its count pass (which keeps the lookups)
+      if (launch_cal_rebase(d_pre, R0, nrc, nullptr, d_seed_off, st) < 0) {
+        e = cudaGetLastError();
+        return done(SR_ECUDA, "sr_candidates_device records");
+      }
+      const CalRanges kept{d_ranges, d_seed_off, d_recount, R0};
+      // the chunk's CAL bounds: their prefix sums and largest
+      CalPlan whole{};
+      uint64_t cends[2] = {};  // prefix of the last read, total
+      e = cudaMemsetAsync(d_plan, 0, sizeof(CalPlan), st);
+      if (e != cudaSuccess ||
+          launch_cal_seeds(s->didx, d_bases, d_roff, R0, nrc, cp.seed_stride, d_count + R0, nullptr, nullptr,
+                           nullptr, d_status, kept, st) < 0 ||
+          launch_scan_u64(d_count + R0, nrc, d_cpre, d_sums, st) < 0 ||
+          launch_cal_route(d_count + R0, nrc, nullptr, nullptr, d_plan, st) < 0) {
+        e = cudaGetLastError();
+        return done(SR_ECUDA, "sr_candidates_device count");
+      }
+      e = cudaMemcpyAsync(cends, d_cpre + nrc - 1, 16, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&whole, d_plan, sizeof(CalPlan), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device count copy");
+      if (status & kStBadRead) return done(SR_EINVAL, "sr_candidates_device: decreasing read offsets or a read longer than 256 bases");
+      if (status & kStBadBase) return done(SR_EBADBASE, "sr_candidates_device: read has a non-ACGT base");
+      // sub-chunks of at most kCalChunkKeys CAL bounds (more only for a read that
+      // alone has more), cut where the prefix sum crosses multiples of that less
+      // the largest read's bound
+      // SR_CAL_CHUNK_KEYS lowers it (tests of the cuts)
+      const uint64_t kCalChunkKeys = std::max<uint64_t>(env_u64("SR_CAL_CHUNK_KEYS", 64ull << 20), 1);
+      const uint64_t one = whole.max_all;
+      const uint64_t want = std::max<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(cends[1], 1), kCalChunkKeys), 2 * one);
+      if (want > cap) {
+        cap = want;
+        d_cals = static_cast<uint64_t*>(cbuf(kCbCals, cap * 8));
+        d_wkey = static_cast<uint64_t*>(cbuf(kCbWkey, cap * 8));
+        d_whits = static_cast<uint32_t*>(cbuf(kCbWhits, cap * 4));
+        d_wlen = static_cast<uint32_t*>(cbuf(kCbWlen, cap * 4));
+        if (!out_dev) {  // a device list is compacted straight into its arrays
+          d_oref = static_cast<uint8_t*>(cbuf(kCbOref, cap));
+          d_ostr = static_cast<uint8_t*>(cbuf(kCbOstr, cap));
+          d_ostart = static_cast<uint64_t*>(cbuf(kCbOstart, cap * 8));
+          d_olen = static_cast<uint32_t*>(cbuf(kCbOlen, cap * 4));
+          d_ohits = static_cast<uint32_t*>(cbuf(kCbOhits, cap * 4));
+        }
+        if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+      }
+      if (cends[1] <= cap) {
+        // the whole chunk in one sub-chunk: its prefix sums are its offsets
+        e = cudaMemcpyAsync(d_off, d_cpre, (nrc + 1ull) * 8, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device offsets");
+        const sr_status r = run_sub(R0, nrc, kept);
+        if (r != SR_OK) return r;
+        continue;
+      }
+      const uint64_t span = cap - one;
+      const uint32_t n_sub = static_cast<uint32_t>(cends[0] / span) + 1;
+      sub.assign(n_sub + 1ull, 0);
+      if (launch_cal_bounds(d_cpre, nrc, span, d_bounds, st) < 0) {
+        e = cudaGetLastError();
+        return done(SR_ECUDA, "sr_candidates_device sub-chunks");
+      }
+      e = cudaMemcpyAsync(sub.data(), d_bounds, n_sub * 4ull, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device sub-chunks");
+      sub[n_sub] = nrc;
+      for (uint32_t si = 0; si < n_sub; ++si) {
+        const uint32_t a0 = sub[si], a1 = sub[si + 1];
+        if (launch_cal_rebase(d_cpre, a0, a1 - a0, d_off, nullptr, st) < 0) {
+          e = cudaGetLastError();
+          return done(SR_ECUDA, "sr_candidates_device offsets");
+        }
+        const sr_status r = run_sub(R0 + a0, a1 - a0, kept);
+        if (r != SR_OK) return r;
       }
     }
-    // the chunk buffers are freed below; the device result arrays must be complete first
+    // the device result arrays must be complete before the call returns
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device");
   }

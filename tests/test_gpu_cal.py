@@ -159,3 +159,27 @@ def test_device_reads_and_device_list(sr):
     with pytest.raises(sr.SrError) as e:
         s.candidates(_dev(long, np.uint8), _dev(lo, np.int64))
     assert e.value.status == sr.SR_EINVAL
+
+
+@pytest.mark.parametrize("records, keys", [(2000, 1 << 26), (1 << 27, 3000), (3000, 2500)])
+def test_chunk_and_sub_chunk_cuts(sr, monkeypatch, records, keys):
+    """Large calls run in chunks of kept lookups and sub-chunks of CAL bounds,
+    both cut on the device where a prefix sum crosses a multiple of the limit
+    (less one read's largest share, so that no piece exceeds it).  With the
+    limits lowered so that a small batch is cut into many pieces, every output
+    equals the uncut call's and the host stage's: host list and device list."""
+    import torch
+    w = S.workload("c3", scale=0.0015, seed=29, rc_frac=0.5)
+    idx = [sr.Index.build(bytes(r), seed_len=20, address_bases=10, cal_limit=1024) for r in w["refs"]]
+    s = sr.Session.from_indexes(idx)
+    s.attach_index(idx)
+    prm = dict(seed_stride=1, merge_dist=32, pad=32)
+    h = sr.candidates(idx, w["bases"], w["read_off"], **prm)
+    base = s.candidates(w["bases"], w["read_off"], **prm)
+    _same(base, h)
+    monkeypatch.setenv("SR_CAL_CHUNK_RECORDS", str(records))
+    monkeypatch.setenv("SR_CAL_CHUNK_KEYS", str(keys))
+    _same(s.candidates(w["bases"], w["read_off"], **prm), h)
+    db, do = _dev(w["bases"], np.uint8), _dev(w["read_off"], np.int64)
+    torch.cuda.synchronize()
+    _same(s.candidates(db, do, out_device=True, **prm).to_numpy(), h)

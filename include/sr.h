@@ -236,9 +236,14 @@ void sr_session_close(sr_session* s);
  * memory (read on the session's stream); params->flags = SR_FLAG_DEVICE leaves
  * the list in device memory (its arrays device pointers, the list flagged
  * SR_FLAG_DEVICE), so that reads, windows and the alignment stay on the device
- * (sr_align_batch takes such a list as it is).  Reads longer than
- * SR_MAX_READ_LEN or with decreasing offsets are SR_EINVAL, non-ACGT bases
- * SR_EBADBASE, no attached index SR_EINVAL.  params->n_threads is unused. */
+ * (sr_align_batch takes such a list as it is).  The call's scratch (kept seed
+ * lookups, 8 bytes per seed and reference, up to 1 GiB; CAL keys and window
+ * arrays, 24 bytes per CAL bound, 42 for a host list, up to 64M bounds; a few
+ * words per read) stays allocated in the session for the next call and is
+ * released by sr_session_close; calls on one session run one at a time.  Reads
+ * longer than SR_MAX_READ_LEN or with decreasing offsets are SR_EINVAL,
+ * non-ACGT bases SR_EBADBASE, no attached index SR_EINVAL.  params->n_threads
+ * is unused. */
 sr_status sr_session_attach_index(sr_session* s, const sr_index* const* idx, uint32_t n_refs);
 sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, const sr_cand_params* params,
                                sr_cand_list** out);

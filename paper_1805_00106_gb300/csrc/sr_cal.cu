@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sr_internal.h"
 #include "sr_seed.h"
 
@@ -445,6 +447,165 @@ __device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, ui
   __syncthreads();
 }
 
+// The same filter for a read of at most 32 E CALs on one warp, without block
+// barriers: element e = 32 h + lane of the warp's E registers per lane.  A
+// bitonic network sorts the keys (partners in other lanes by shuffle, in the
+// same lane by register); run and window starts become ballot masks; each run
+// offers (its length, its position in its window) to its window by an atomic
+// max in shared memory; the max_cands cut keeps the windows of rank below it
+// (most hits first, then the smaller key), in key order.
+constexpr int kFilterWarps = 8;
+template <int E>
+__global__ void __launch_bounds__(32 * kFilterWarps) k_cal_filter_warp(FilterArgs a, uint32_t lo, uint32_t hi) {
+  constexpr int P = 32 * E;
+  __shared__ uint64_t sk_s[kFilterWarps][P];                 // sorted keys
+  __shared__ unsigned long long sb_s[kFilterWarps][P];       // per window: (run length << 32) | ~position
+  __shared__ uint32_t sp_s[kFilterWarps][P + 1];             // window starts, then n
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  uint64_t* sk = sk_s[wi];
+  unsigned long long* sb = sb_s[wi];
+  uint32_t* sp = sp_s[wi];
+  const uint32_t le = (2u << lane) - 1u;  // lanes at or below this one (lane 31: all)
+  for (uint32_t rr = blockIdx.x * kFilterWarps + wi; rr < a.nr; rr += gridDim.x * kFilterWarps) {
+    const uint32_t c = a.count[rr];
+    if (c < lo || c > hi) continue;
+    const uint32_t n = a.actual[rr];
+    const uint32_t r = a.r0 + rr;
+    const uint64_t base = a.off[rr];
+    const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - a.read_off[r]);
+    uint64_t k[E];
+#pragma unroll
+    for (int h = 0; h < E; ++h) {
+      const uint32_t e = 32 * h + lane;
+      k[h] = e < n ? a.cals[base + e] : kNoKey;
+    }
+    // bitonic sort, ascending: the lower index of a pair keeps the minimum in
+    // ascending runs ((e & size) == 0), the maximum in descending ones
+#pragma unroll
+    for (int size = 2; size <= P; size <<= 1) {
+#pragma unroll
+      for (int stride = size / 2; stride > 0; stride >>= 1) {
+        if (stride >= 32) {
+          const int hs = stride / 32;
+#pragma unroll
+          for (int h = 0; h < E; ++h) {
+            if (h & hs) continue;
+            const uint32_t e = 32 * h + lane;
+            const bool up = (e & size) == 0;
+            const uint64_t x = k[h], y = k[h | hs];
+            if ((x > y) == up) {
+              k[h] = y;
+              k[h | hs] = x;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < E; ++h) {
+            const uint32_t e = 32 * h + lane;
+            const uint64_t y = __shfl_xor_sync(FULL, k[h], stride);
+            const bool up = (e & size) == 0, low = (lane & stride) == 0;
+            k[h] = (low == up) ? (k[h] < y ? k[h] : y) : (k[h] > y ? k[h] : y);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < E; ++h) sk[32 * h + lane] = k[h];
+    __syncwarp();
+    // run starts (value changes) and window starts ((ref, strand) changes or a
+    // gap over merge_dist), as masks of the E groups of 32 elements
+    uint32_t rm[E], wm[E];
+    uint32_t nwin = 0;
+#pragma unroll
+    for (int h = 0; h < E; ++h) {
+      const uint32_t e = 32 * h + lane;
+      bool rs = false, ws = false;
+      if (e < n) {
+        if (e == 0) {
+          rs = ws = true;
+        } else {
+          const uint64_t p = sk[e - 1];
+          rs = k[h] != p;
+          ws = (k[h] >> 59) != (p >> 59) || k[h] - p > a.merge_dist;
+        }
+      }
+      rm[h] = __ballot_sync(FULL, rs);
+      wm[h] = __ballot_sync(FULL, ws);
+      nwin += __popc(wm[h]);
+    }
+    for (uint32_t j = lane; j < nwin; j += 32) sb[j] = 0ull;
+    __syncwarp();
+    uint32_t wbefore = 0;  // window starts in the groups before h
+#pragma unroll
+    for (int h = 0; h < E; ++h) {
+      const uint32_t e = 32 * h + lane;
+      if ((wm[h] >> lane) & 1u) sp[wbefore + __popc(wm[h] & (le >> 1))] = e;
+      if ((rm[h] >> lane) & 1u) {
+        // the window holding this run, the next run start, this run's window start
+        const uint32_t w = wbefore + __popc(wm[h] & le) - 1u;
+        uint32_t next = n;
+        const uint32_t above = rm[h] & ~le;
+        if (above) {
+          next = 32 * h + __ffs(above) - 1;
+        } else {
+#pragma unroll
+          for (int h2 = E - 1; h2 > h; --h2)
+            if (rm[h2]) next = 32 * h2 + __ffs(rm[h2]) - 1;
+        }
+        uint32_t wst = 0;
+        const uint32_t below = wm[h] & le;
+        if (below) {
+          wst = 32 * h + 31 - __clz(below);
+        } else {
+#pragma unroll
+          for (int h2 = 0; h2 < h; ++h2)
+            if (wm[h2]) wst = 32 * h2 + 31 - __clz(wm[h2]);
+        }
+        atomicMax(&sb[w], (static_cast<unsigned long long>(next - e) << 32) | (0xffffffffu - (e - wst)));
+      }
+      wbefore += __popc(wm[h]);
+    }
+    if (lane == 0) sp[nwin] = n;
+    __syncwarp();
+    // windows kept (all, or the max_cands of rank below it) in key order, each
+    // clamped to [cal - pad, cal + m + pad) within its reference
+    const bool cut = a.max_cands && nwin > a.max_cands;
+    uint32_t kept_before = 0;
+    for (uint32_t j0 = 0; j0 < nwin; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      const bool in = j < nwin;
+      const uint32_t hits = in ? sp[j + 1] - sp[j] : 0u;
+      bool keep = in;
+      if (cut && in) {
+        uint32_t rank = 0;
+        for (uint32_t q = 0; q < nwin; ++q) {
+          const uint32_t hq = sp[q + 1] - sp[q];
+          rank += (hq > hits || (hq == hits && q < j)) ? 1u : 0u;
+        }
+        keep = rank < a.max_cands;
+      }
+      const uint32_t km = __ballot_sync(FULL, keep);
+      if (keep) {
+        const uint32_t dst = kept_before + __popc(km & (le >> 1));
+        const uint32_t at = 0xffffffffu - static_cast<uint32_t>(sb[j] & 0xffffffffull);
+        const uint64_t key = sk[sp[j] + at];
+        const uint32_t ref = static_cast<uint32_t>(key >> 60);
+        const int64_t cal = static_cast<int64_t>(key & kCalMask) - static_cast<int64_t>(kCalBias);
+        const int64_t N = static_cast<int64_t>(a.di.ref_len[ref]);
+        int64_t wlo = cal - static_cast<int64_t>(a.pad), whi = cal + m + static_cast<int64_t>(a.pad);
+        if (wlo < 0) wlo = 0;
+        if (whi > N) whi = N;
+        a.wkey[base + dst] = (key & ~kCalMask) | static_cast<uint64_t>(wlo);
+        a.whits[base + dst] = hits;
+        a.wlen[base + dst] = static_cast<uint32_t>(whi - wlo);
+      }
+      kept_before += __popc(km);
+    }
+    if (lane == 0) a.nwin[rr] = kept_before;
+    __syncwarp();
+  }
+}
+
 // reads with lo <= count <= hi, keys in shared memory
 __global__ void __launch_bounds__(256) k_cal_filter(FilterArgs a, uint32_t lo, uint32_t hi) {
   extern __shared__ uint64_t skeys[];
@@ -530,11 +691,22 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
     return p;
   };
   int launched = 0;
-  // small reads: 24 KB or less of shared memory per block, many blocks per SM
+  // reads of at most 64 and of 65-128 CALs: one warp each
   {
+    const uint32_t warps = static_cast<uint32_t>(nsm) * 8 * kFilterWarps;
+    const uint32_t grid = (std::min(nr, warps) + kFilterWarps - 1) / kFilterWarps;
+    k_cal_filter_warp<2><<<grid, 32 * kFilterWarps, 0, st>>>(a, 0u, 64u);
+    ++launched;
+    if (max_small > 64) {
+      k_cal_filter_warp<4><<<grid, 32 * kFilterWarps, 0, st>>>(a, 65u, 128u);
+      ++launched;
+    }
+  }
+  // the other small reads: 24 KB or less of shared memory per block, many blocks per SM
+  if (max_small > 128) {
     const size_t smem = static_cast<size_t>(cal_filter_words(p2(max_small))) * sizeof(uint64_t);
     const uint32_t grid = nr < static_cast<uint32_t>(nsm) * 32 ? nr : static_cast<uint32_t>(nsm) * 32;
-    k_cal_filter<<<grid, 128, smem, st>>>(a, 0u, kCalSmallKeys);
+    k_cal_filter<<<grid, 128, smem, st>>>(a, 129u, kCalSmallKeys);
     ++launched;
   }
   if (max_mid) {

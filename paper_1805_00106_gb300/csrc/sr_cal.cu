@@ -50,6 +50,23 @@ __device__ __forceinline__ uint32_t code_of(char ch) {
   }
 }
 
+// packed index: entries [lo, hi) of reference r with key `key` in bucket b
+__device__ __forceinline__ void lookup_packed(const DevIndex& di, uint64_t b, uint32_t key, int r, uint64_t* lo,
+                                              uint64_t* hi) {
+  const uint64_t s0 = di.jptr[b * di.n_refs + r], s1 = di.jptr[(b + 1) * di.n_refs + r];
+  const uint16_t* K = di.key16[r];
+  uint64_t l = s0, u = s1;
+  while (l < u) {
+    const uint64_t mid = l + ((u - l) >> 1);
+    if (K[mid] < key) l = mid + 1;
+    else u = mid;
+  }
+  uint64_t e = l;
+  while (e < s1 && K[e] == key) ++e;
+  *lo = l;
+  *hi = e;
+}
+
 // entries [lo, hi) of reference r whose key equals the seed's
 __device__ __forceinline__ void lookup(const DevIndex& di, int r, uint64_t canon, uint64_t* lo, uint64_t* hi) {
   const int kb = 2 * (di.k - di.a);
@@ -174,6 +191,16 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
           canon = km.fwd < km.rc ? km.fwd : km.rc;
           rori = (km.fwd == canon ? 1u : 0u) | (km.rc == canon ? 2u : 0u);
         }
+        // packed index: one hash (the references share its seed) gives the bucket
+        // and key in every reference
+        uint64_t pb = 0;
+        uint32_t pkey = 0;
+        if (a.di.packed && !kept && live) {
+          const int kb = 2 * (k - a.di.a);
+          const uint64_t h = seed_hash(canon, k, a.di.hash_seed[0]);
+          pb = h >> kb;
+          pkey = static_cast<uint32_t>(h & mask_bits(kb));
+        }
         for (int r2 = 0; r2 < a.di.n_refs; ++r2) {
           uint64_t lo = 0, hi = 0;
           if (kept) {
@@ -184,7 +211,8 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
               rori = static_cast<uint32_t>(x & 3u);
             }
           } else if (live) {
-            lookup(a.di, r2, canon, &lo, &hi);
+            if (a.di.packed) lookup_packed(a.di, pb, pkey, r2, &lo, &hi);
+            else lookup(a.di, r2, canon, &lo, &hi);
           }
           uint32_t cnt = static_cast<uint32_t>(hi - lo);
           if (!EMIT) {
@@ -224,11 +252,13 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
             const uint32_t before = own ? incl[own - 1] : 0u;
             const uint64_t e = lo_s[warp][own] + (j - before);
             const uint32_t so = o_s[warp][own], sro = ro_s[warp][own];
-            const uint32_t fo = a.di.orient[r2][e];
+            // packed index: position and orientation bits in one word
+            const uint32_t po = a.di.packed ? a.di.posor[r2][e] : 0u;
+            const uint32_t fo = a.di.packed ? po >> 30 : a.di.orient[r2][e];
             const bool plus = ((fo & 1u) && (sro & 1u)) || ((fo & 2u) && (sro & 2u));
             const bool minus = ((fo & 1u) && (sro & 2u)) || ((fo & 2u) && (sro & 1u));
             if (EMIT) {
-              const int64_t p = a.di.pos[r2][e];
+              const int64_t p = a.di.packed ? (po & 0x3fffffffu) : a.di.pos[r2][e];
               if (plus) a.cals[base + atomicAdd(&ctr[warp], 1u)] = cal_key(r2, 0, p - so);
               if (minus) a.cals[base + atomicAdd(&ctr[warp], 1u)] =
                   cal_key(r2, 1, p - static_cast<int64_t>(m - so - k));

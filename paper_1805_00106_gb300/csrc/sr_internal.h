@@ -269,6 +269,16 @@ struct DevIndex {
   const uint32_t* key[kMaxRefs];
   const uint32_t* pos[kMaxRefs];
   const uint8_t* orient[kMaxRefs];
+  // packed form (packed = 1, the arrays above unset): the bucket starts of all
+  // references interleaved as 32-bit values, jptr[b * n_refs + r], so that one
+  // sector holds a seed's bucket in every reference; 16-bit keys; each entry's
+  // position with its orientation bits in the top two (posor), one load per
+  // entry.  Used when the references share one hash seed, each has under 2^32
+  // entries and at most 2^30 bases, and keys fit 16 bits (2 (k - a) <= 16).
+  const uint32_t* jptr;
+  const uint16_t* key16[kMaxRefs];
+  const uint32_t* posor[kMaxRefs];
+  int packed;
   uint64_t ref_len[kMaxRefs];
   uint64_t hash_seed[kMaxRefs];
   int n_refs, k, a;

@@ -1349,22 +1349,54 @@ extern "C" sr_status sr_session_attach_index(sr_session* s, const sr_index* cons
     *dst = d;
     return true;
   };
-  for (uint32_t r = 0; r < n_refs; ++r) {
-    void *pp, *pk, *ps, *po;
-    if (!up(t[r].ptr, t[r].n_ptr * 8, &pp) || !up(t[r].key, t[r].n_entries * 4, &pk) ||
-        !up(t[r].pos, t[r].n_entries * 4, &ps) || !up(t[r].orient, t[r].n_entries, &po)) {
-      for (auto* p : s->idx_bufs) cudaFree(p);
-      s->idx_bufs.clear();
-      s->didx = DevIndex{};
-      cudaGetLastError();
-      return set_error(SR_ENOMEM, "sr_session_attach_index: device upload failed");
+  auto fail = [&]() -> sr_status {
+    for (auto* p : s->idx_bufs) cudaFree(p);
+    s->idx_bufs.clear();
+    s->didx = DevIndex{};
+    cudaGetLastError();
+    return set_error(SR_ENOMEM, "sr_session_attach_index: device upload failed");
+  };
+  // the packed device form when the references allow it (see DevIndex)
+  bool packed = 2 * (static_cast<int>(t[0].seed_len) - static_cast<int>(t[0].address_bases)) <= 16;
+  for (uint32_t r = 0; r < n_refs && packed; ++r)
+    packed = t[r].hash_seed == t[0].hash_seed && t[r].n_ptr == t[0].n_ptr && t[r].n_entries < (1ull << 32) &&
+             t[r].ref_len <= (1ull << 30);
+  if (packed) {
+    const uint64_t nb = t[0].n_ptr;  // buckets + 1, the same in every reference
+    std::vector<uint32_t> jp(nb * n_refs);
+    for (uint64_t b = 0; b < nb; ++b)
+      for (uint32_t r = 0; r < n_refs; ++r) jp[b * n_refs + r] = static_cast<uint32_t>(t[r].ptr[b]);
+    void* pj;
+    if (!up(jp.data(), jp.size() * 4, &pj)) return fail();
+    s->didx.jptr = static_cast<const uint32_t*>(pj);
+    for (uint32_t r = 0; r < n_refs; ++r) {
+      std::vector<uint16_t> k16(t[r].n_entries);
+      std::vector<uint32_t> po(t[r].n_entries);
+      for (uint64_t i = 0; i < t[r].n_entries; ++i) {
+        k16[i] = static_cast<uint16_t>(t[r].key[i]);
+        po[i] = t[r].pos[i] | (static_cast<uint32_t>(t[r].orient[i] & 3u) << 30);
+      }
+      void *pk, *pp;
+      if (!up(k16.data(), k16.size() * 2, &pk) || !up(po.data(), po.size() * 4, &pp)) return fail();
+      s->didx.key16[r] = static_cast<const uint16_t*>(pk);
+      s->didx.posor[r] = static_cast<const uint32_t*>(pp);
+      s->didx.ref_len[r] = t[r].ref_len;
+      s->didx.hash_seed[r] = t[r].hash_seed;
     }
-    s->didx.ptr[r] = static_cast<const uint64_t*>(pp);
-    s->didx.key[r] = static_cast<const uint32_t*>(pk);
-    s->didx.pos[r] = static_cast<const uint32_t*>(ps);
-    s->didx.orient[r] = static_cast<const uint8_t*>(po);
-    s->didx.ref_len[r] = t[r].ref_len;
-    s->didx.hash_seed[r] = t[r].hash_seed;
+    s->didx.packed = 1;
+  } else {
+    for (uint32_t r = 0; r < n_refs; ++r) {
+      void *pp, *pk, *ps, *po;
+      if (!up(t[r].ptr, t[r].n_ptr * 8, &pp) || !up(t[r].key, t[r].n_entries * 4, &pk) ||
+          !up(t[r].pos, t[r].n_entries * 4, &ps) || !up(t[r].orient, t[r].n_entries, &po))
+        return fail();
+      s->didx.ptr[r] = static_cast<const uint64_t*>(pp);
+      s->didx.key[r] = static_cast<const uint32_t*>(pk);
+      s->didx.pos[r] = static_cast<const uint32_t*>(ps);
+      s->didx.orient[r] = static_cast<const uint8_t*>(po);
+      s->didx.ref_len[r] = t[r].ref_len;
+      s->didx.hash_seed[r] = t[r].hash_seed;
+    }
   }
   s->didx.n_refs = static_cast<int>(n_refs);
   s->didx.k = static_cast<int>(t[0].seed_len);

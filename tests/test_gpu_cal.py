@@ -24,10 +24,15 @@ def _same(a, b):
         assert np.array_equal(np.asarray(a[k], np.int64), np.asarray(b[k], np.int64)), k
 
 
-@pytest.mark.parametrize("k,addr,cal_limit", [(20, 10, 1024), (22, 11, 0), (16, 8, 64)])
-def test_device_matches_host_xenograft(sr, k, addr, cal_limit):
+# (20, 12) with one hash seed and (16, 8) take the device index's packed form
+# (shared bucket starts, 16-bit keys); the others, and different hash seeds per
+# reference, the per-reference form
+@pytest.mark.parametrize("k,addr,cal_limit,seeds", [(20, 10, 1024, (0, 0)), (22, 11, 0, (0, 0)), (16, 8, 64, (0, 0)),
+                                                    (20, 12, 1024, (0, 0)), (20, 12, 1024, (5, 9))])
+def test_device_matches_host_xenograft(sr, k, addr, cal_limit, seeds):
     w = S.workload("c3", scale=0.002, seed=17)
-    idx = [sr.Index.build(bytes(r), seed_len=k, address_bases=addr, cal_limit=cal_limit) for r in w["refs"]]
+    idx = [sr.Index.build(bytes(r), seed_len=k, address_bases=addr, cal_limit=cal_limit, hash_seed=hs)
+           for r, hs in zip(w["refs"], seeds)]
     s = sr.Session.from_indexes(idx)
     s.attach_index(idx)
     for prm in [dict(seed_stride=1, merge_dist=32, pad=32), dict(seed_stride=k, merge_dist=32, pad=16),

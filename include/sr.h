@@ -229,7 +229,12 @@ void sr_session_close(sr_session* s);
  * Sec. 4.1-4.2; here the index lives in HBM next to the references).
  * sr_session_attach_index uploads idx[r], the index of the session's reference
  * r (same length; all with one seed_len and address_bases), once; replacing an
- * attached set is allowed.  sr_candidates_device then returns exactly the list
+ * attached set is allowed.  When the indexes share one hash_seed, each has
+ * under 2^32 entries and at most 2^30 bases, and 2 * (seed_len -
+ * address_bases) <= 16, the device copy is packed (bucket starts of all
+ * references interleaved in 32 bits, 16-bit keys, position and orientation in
+ * one word: about 2 + 6 bytes per entry); otherwise each reference's tables are
+ * copied as they are (about 17 bytes per entry).  sr_candidates_device then returns exactly the list
  * sr_candidates returns for those indexes (same windows, order and hits): one
  * warp per read looks up its seeds, one block per read sorts and merges its
  * CALs.  The reads may be host memory or, flagged SR_FLAG_DEVICE, device

@@ -233,8 +233,8 @@ void sr_session_close(sr_session* s);
  * under 2^32 entries and at most 2^30 bases, and 2 * (seed_len -
  * address_bases) <= 16, the device copy is packed (bucket starts of all
  * references interleaved in 32 bits, 16-bit keys, position and orientation in
- * one word: about 2 + 6 bytes per entry); otherwise each reference's tables are
- * copied as they are (about 17 bytes per entry).  sr_candidates_device then returns exactly the list
+ * one word: 6 bytes per entry and 4 per bucket); otherwise each reference's
+ * tables are copied as they are (9 bytes per entry and 8 per bucket).  sr_candidates_device then returns exactly the list
  * sr_candidates returns for those indexes (same windows, order and hits): one
  * warp per read looks up its seeds, one block per read sorts and merges its
  * CALs.  The reads may be host memory or, flagged SR_FLAG_DEVICE, device

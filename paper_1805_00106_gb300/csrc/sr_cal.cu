@@ -896,4 +896,24 @@ int launch_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, c
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+int preload_cal() {
+  int n_ = 0;
+  SR_TOUCH(k_cal_slots);
+  SR_TOUCH(k_cal_seeds<false>);
+  SR_TOUCH(k_cal_seeds<true>);
+  SR_TOUCH(k_cal_filter);
+  SR_TOUCH(k_cal_filter_big);
+  SR_TOUCH(k_cal_filter_warp<2>);
+  SR_TOUCH(k_cal_filter_warp<4>);
+  SR_TOUCH(k_cal_compact);
+  SR_TOUCH(k_cal_offsets);
+  SR_TOUCH(k_scan64_a);
+  SR_TOUCH(k_scan64_b);
+  SR_TOUCH(k_scan64_c);
+  SR_TOUCH(k_cal_route);
+  SR_TOUCH(k_cal_bounds);
+  SR_TOUCH(k_cal_rebase);
+  return n_;
+}
+
 }  // namespace sr

@@ -231,4 +231,13 @@ int probe_dpx(double* lane_ops_per_clk_per_sm, double* clk_mhz) {
   return 0;
 }
 
+int preload_extend() {
+  int n_ = 0;
+  SR_TOUCH(k_extend32<0>);
+  SR_TOUCH(k_extend32<1>);
+  SR_TOUCH(k_probe_dpx);
+  SR_TOUCH(k_probe_wait);
+  return n_;
+}
+
 }  // namespace sr

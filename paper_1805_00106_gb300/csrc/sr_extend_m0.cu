@@ -20,4 +20,15 @@ int dispatch_mode0(bool persist, uint32_t lanes, uint32_t rows, const ExtArgs& a
   return -1;
 }
 
+int preload_mode0() {
+  int n_ = 0;
+#define SR_CASE(g, r) SR_TOUCH((k_extend16<g, r, 0, true>));
+  SR_SHAPES(SR_CASE)
+#undef SR_CASE
+#define SR_CASE(g, r) SR_TOUCH((k_extend16<g, r, 0, false>));
+  SR_PLAIN_SHAPES(SR_CASE)
+#undef SR_CASE
+  return n_;
+}
+
 }  // namespace sr

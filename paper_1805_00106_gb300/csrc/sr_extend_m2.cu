@@ -12,4 +12,12 @@ int dispatch_mode2(uint32_t lanes, uint32_t rows, const ExtArgs& a, cudaStream_t
   return -1;
 }
 
+int preload_mode2() {
+  int n_ = 0;
+#define SR_CASE(g, r) SR_TOUCH((k_extend16<g, r, 2, true>));
+  SR_SHAPES(SR_CASE)
+#undef SR_CASE
+  return n_;
+}
+
 }  // namespace sr

@@ -362,6 +362,25 @@ int launch_classify_hits(const sr_hit* per_ref, uint32_t n_reads, uint32_t n_ref
 bool extend_config_supported(uint32_t lanes, uint32_t rows);
 // the built (lanes, rows) shapes; returns how many there are
 int extend_shapes(uint32_t* lanes, uint32_t* rows, int cap);
+// Loading every kernel of the library at session open (cudaFuncGetAttributes
+// loads a kernel's module): with lazy module loading the first launch of a
+// rarely used kernel (the winner end-row pass, the int32 path, a selection
+// width) would otherwise stall the host in the middle of enqueuing a batch.
+// One per source file; each returns the number of kernels touched.
+int preload_mode0();
+int preload_mode1();
+int preload_mode2();
+int preload_extend();
+int preload_kernels();
+int preload_traceback();
+int preload_cal();
+int preload_report();
+int preload_noalloc();
+#define SR_TOUCH(k)                                                             \
+  do {                                                                          \
+    cudaFuncAttributes fa_;                                                     \
+    if (cudaFuncGetAttributes(&fa_, reinterpret_cast<const void*>(&(k))) == cudaSuccess) ++n_; \
+  } while (0)
 int probe_dpx(double* lane_ops_per_clk_per_sm, double* clk_mhz);
 // bounded mbarrier wait with (arrive = 1) or without its arrival; status word out
 int probe_wait(uint32_t poll_limit, int arrive, uint32_t* status_out);

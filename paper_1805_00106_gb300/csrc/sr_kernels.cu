@@ -678,4 +678,29 @@ int launch_cigar_compact(const BatchDev& b, int n_refs, cudaStream_t st) {
   return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
 }
 
+int preload_kernels() {
+  int n_ = 0;
+  SR_TOUCH(k_pack_ref);
+  SR_TOUCH(k_pack_reads);
+  SR_TOUCH(k_items);
+  SR_TOUCH(k_keys);
+  SR_TOUCH(k_scan_keys);
+  SR_TOUCH(k_scatter);
+  SR_TOUCH(k_select<4>);
+  SR_TOUCH(k_select<8>);
+  SR_TOUCH(k_select<16>);
+  SR_TOUCH(k_select<32>);
+  SR_TOUCH(k_winners);
+  SR_TOUCH(k_wrange);
+  SR_TOUCH(k_classify);
+  SR_TOUCH(k_scan_block);
+  SR_TOUCH(k_scan_sums);
+  SR_TOUCH(k_cigar_gather);
+  SR_TOUCH(k_assemble);
+  SR_TOUCH(k_stage_check);
+  SR_TOUCH(k_first_bad_window);
+  SR_TOUCH(k_rebase_offsets);
+  return n_;
+}
+
 }  // namespace sr

@@ -181,3 +181,11 @@ extern "C" sr_status sr_align_items_noalloc(sr_session* s, const char* d_bases, 
   if (hst) return status_error(hst);
   return SR_OK;
 }
+
+namespace sr {
+int preload_noalloc() {
+  int n_ = 0;
+  SR_TOUCH(k_noalloc_check);
+  return n_;
+}
+}  // namespace sr

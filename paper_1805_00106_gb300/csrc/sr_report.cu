@@ -235,4 +235,13 @@ int launch_report_write(const BatchDev& b, int n_refs, int kind, uint32_t n_best
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+int preload_report() {
+  int n_ = 0;
+  SR_TOUCH(k_report);
+  SR_TOUCH(k_scan_a);
+  SR_TOUCH(k_scan_b);
+  SR_TOUCH(k_scan_c);
+  return n_;
+}
+
 }  // namespace sr

@@ -200,6 +200,25 @@ extern "C" const char* sr_last_error(void) { return g_err.c_str(); }
 extern "C" const char* sr_version(void) { return "libsr 0.1 (sm_103a)"; }
 
 // ------------------------------------------------------------------ session
+// every kernel of the library loaded once per device (see preload_kernels)
+static void preload_all(int dev) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  preload_mode0();
+  preload_mode1();
+  preload_mode2();
+  preload_extend();
+  preload_kernels();
+  preload_traceback();
+  preload_cal();
+  preload_report();
+  preload_noalloc();
+  cudaGetLastError();
+  done[dev] = true;
+}
+
 static sr_status open_common(const uint8_t* const* codes, const char* const* ascii,
                              const uint64_t* lens, uint32_t n_refs, uint64_t budget,
                              sr_session** out) {
@@ -210,6 +229,7 @@ static sr_status open_common(const uint8_t* const* codes, const char* const* asc
   if (e != cudaSuccess || ndev == 0) return set_error(SR_ECUDA, "session: no CUDA device available");
   auto* s = new sr_session;
   cudaGetDevice(&s->device);
+  preload_all(s->device);
   e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   for (auto& x : s->part_stream)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
@@ -1187,12 +1207,17 @@ static void* pool_take(sr_session* s, uint64_t bytes, uint64_t* got) {
       return p;
     }
   }
+  // new blocks in whole units of 64 MiB: pinning pages costs time on the caller's
+  // path (the serving completer), so a pool of a few such blocks covers the
+  // result sizes that follow instead of growing by every larger round
+  constexpr uint64_t kUnit = 64ull << 20;
+  const uint64_t want = (bytes + kUnit - 1) / kUnit * kUnit;
   void* p = nullptr;
-  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+  if (cudaMallocHost(&p, want) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  *got = bytes;
+  *got = want;
   return p;
 }
 
@@ -1201,7 +1226,7 @@ static void pool_give(sr_session* s, void* p, uint64_t bytes) {
   {
     std::lock_guard<std::mutex> lk(s->pool_mu);
     s->pool.emplace_back(p, bytes);
-    if (s->pool.size() > 4) {  // keep the four most recent blocks
+    if (s->pool.size() > 8) {  // keep the eight most recent blocks (results a caller still holds take some)
       drop = s->pool.front().first;
       s->pool.erase(s->pool.begin());
     }

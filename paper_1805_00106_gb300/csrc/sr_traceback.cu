@@ -1543,4 +1543,19 @@ int launch_traceback(const BatchDev& b, const DevRefs& refs, const ScoreConst& s
   return launched;
 }
 
+int preload_traceback() {
+  int n_ = 0;
+  SR_TOUCH(k_traceback);
+  SR_TOUCH(k_tb_wave<16>);
+  SR_TOUCH(k_tb_wave<32>);
+  SR_TOUCH(k_tb_wave2);
+  SR_TOUCH(k_tb_thread);
+  SR_TOUCH(k_tb_pair<16>);
+  SR_TOUCH(k_tb_pair<32>);
+  SR_TOUCH(k_tb_route);
+  SR_TOUCH(k_tb_scan);
+  SR_TOUCH(k_tb_scatter);
+  return n_;
+}
+
 }  // namespace sr

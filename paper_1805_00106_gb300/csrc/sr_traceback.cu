@@ -981,12 +981,12 @@ __global__ void __launch_bounds__(32 * kTbTWarps) k_tb_thread(TbArgs a, const ui
   }
 }
 
-// ---- Bands of at most 16 diagonals: two reads per thread, one in each 16-bit
-// half (DPX s16x2 arithmetic), each pair swept row by row with the row's W
-// cells in registers.  Cell k of row i is band diagonal dlo + k (column
+// ---- Bands of at most 16 (or 32) diagonals: two reads per thread, one in each
+// 16-bit half (DPX s16x2 arithmetic), each pair swept row by row with the row's
+// W cells in registers.  Cell k of row i is band diagonal dlo + k (column
 // i + dlo + k); its left neighbour is cell k - 1 of the same row, its upper one
-// cell k + 1 and its diagonal cell k of the row above.  The cell arithmetic is
-// the packed wavefront's: E and F arrive complete, the cell computes its right
+// cell k + 1 and its diagonal cell k of the row above.  As in the wavefront
+// (tb_cell), E and F arrive complete, the cell computes its right
 // neighbour's E and its lower neighbour's F (gap opened from its H or extended)
 // and stores 4 bits, inverted (1 = not equal): H = diagonal value, H = E,
 // En = the opened gap value, Fn = the opened gap value.  Cells that are not

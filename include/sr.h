@@ -243,9 +243,11 @@ void sr_session_close(sr_session* s);
  * SR_FLAG_DEVICE), so that reads, windows and the alignment stay on the device
  * (sr_align_batch takes such a list as it is).  The call's scratch (kept seed
  * lookups, 8 bytes per seed and reference, up to 1 GiB; CAL keys and window
- * arrays, 24 bytes per CAL bound, 42 for a host list, up to 64M bounds; a few
- * words per read) stays allocated in the session for the next call and is
- * released by sr_session_close; calls on one session run one at a time.  Reads
+ * arrays, 24 bytes per CAL bound, up to 64M bounds; a few words per read; for a
+ * host list, the list itself, 8 bytes per read and 18 per window, built on the
+ * device and copied out once through a pinned block of the session's pool)
+ * stays allocated in the session for the next call and is released by
+ * sr_session_close; calls on one session run one at a time.  Reads
  * longer than SR_MAX_READ_LEN or with decreasing offsets are SR_EINVAL,
  * non-ACGT bases SR_EBADBASE, no attached index SR_EINVAL.  params->n_threads
  * is unused. */

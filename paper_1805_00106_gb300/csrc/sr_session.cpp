@@ -132,7 +132,8 @@ uint64_t env_u64(const char* name, uint64_t dflt) {
 enum CalBuf : int {
   kCbBases, kCbRoff, kCbCount, kCbActual, kCbStatus, kCbSlots, kCbPre, kCbSums, kCbBounds, kCbPlan,
   kCbRanges, kCbSeedOff, kCbRecount, kCbCpre, kCbOff, kCbNwin, kCbWoff, kCbWsums, kCbBig, kCbBigOff,
-  kCbCals, kCbWkey, kCbWhits, kCbWlen, kCbOref, kCbOstr, kCbOstart, kCbOlen, kCbOhits, kCbScratch, kCalBufs
+  kCbCals, kCbWkey, kCbWhits, kCbWlen, kCbScratch, kCbLoff, kCbLref, kCbLstr, kCbLstart, kCbLlen, kCbLhits,
+  kCalBufs
 };
 }  // namespace
 
@@ -1493,40 +1494,77 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     }
     return s->cal_buf[role];
   };
-  // the result list: host arrays, or device arrays grown chunk by chunk
+  // The list is built on the device in either case: in the caller's list arrays
+  // (device output, grown chunk by chunk), or in the session's cached arrays
+  // (host output: copied out once at the end, through a pinned block).
   sr_cand_list* l = static_cast<sr_cand_list*>(calloc(1, sizeof(sr_cand_list)));
   if (!l) return set_error(SR_ENOMEM, "sr_candidates_device: out of memory");
   l->n_reads = n;
   l->flags = out_dev ? static_cast<uint32_t>(SR_FLAG_DEVICE) : 0u;
+  struct {
+    uint64_t* off;
+    uint8_t *ref, *str;
+    uint64_t* start;
+    uint32_t *len, *hits;
+  } L{};
   uint64_t cap_out = 0;  // windows the device result arrays hold
   auto done = [&](sr_status stt, const char* msg) -> sr_status {
     cudaStreamSynchronize(st);
     cudaGetLastError();
     if (stt == SR_OK) return static_cast<sr_status>(SR_OK);
-    sr_cand_list_free(l);
+    sr_cand_list_free(l);  // host output: its arrays are still unset
     if (stt == SR_ECUDA) return cuda_error(msg, e == cudaSuccess ? cudaErrorUnknown : e);
     return set_error(stt, "%s", msg);
   };
-  std::vector<uint64_t> offsets;
-  std::vector<uint8_t> o_ref, o_strand;
-  std::vector<uint64_t> o_start;
-  std::vector<uint32_t> o_len, o_hits;
   if (out_dev) {
     if (cudaMalloc(&l->offsets, (n + 1ull) * 8) != cudaSuccess) {
       e = cudaGetLastError();
       return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
     }
-    if (n == 0 && cudaMemsetAsync(l->offsets, 0, 8, st) != cudaSuccess) {
-      e = cudaGetLastError();
-      return done(SR_ECUDA, "sr_candidates_device offsets");
-    }
+    L.off = l->offsets;
   } else {
-    offsets.assign(n + 1ull, 0);
+    L.off = static_cast<uint64_t*>(cbuf(kCbLoff, (n + 1ull) * 8));
+    if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
   }
+  if (n == 0 && cudaMemsetAsync(L.off, 0, 8, st) != cudaSuccess) {
+    e = cudaGetLastError();
+    return done(SR_ECUDA, "sr_candidates_device offsets");
+  }
+  // a cached array grown to `need` bytes, its first `keep` bytes kept
+  auto cgrow = [&](int role, uint64_t need, uint64_t keep) -> void* {
+    if (s->cal_bytes[role] >= need) return s->cal_buf[role];
+    void* p = nullptr;
+    const uint64_t want = need + need / 4;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    if (keep && s->cal_buf[role] &&
+        cudaMemcpyAsync(p, s->cal_buf[role], keep, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(p);
+      return nullptr;
+    }
+    cudaStreamSynchronize(st);
+    if (s->cal_buf[role]) cudaFree(s->cal_buf[role]);
+    s->cal_buf[role] = p;
+    s->cal_bytes[role] = want;
+    return p;
+  };
   // grows the device result arrays to hold `need` windows, keeping the first `keep`
   auto grow_out = [&](uint64_t need, uint64_t keep) -> bool {
     if (need <= cap_out) return true;
     const uint64_t c = std::max<uint64_t>(need, cap_out + cap_out / 2);
+    if (!out_dev) {
+      L.ref = static_cast<uint8_t*>(cgrow(kCbLref, c, keep));
+      L.str = static_cast<uint8_t*>(cgrow(kCbLstr, c, keep));
+      L.start = static_cast<uint64_t*>(cgrow(kCbLstart, c * 8, keep * 8));
+      L.len = static_cast<uint32_t*>(cgrow(kCbLlen, c * 4, keep * 4));
+      L.hits = static_cast<uint32_t*>(cgrow(kCbLhits, c * 4, keep * 4));
+      if (!L.ref || !L.str || !L.start || !L.len || !L.hits) return false;
+      cap_out = c;
+      return true;
+    }
     void *r8 = nullptr, *s8 = nullptr, *st64 = nullptr, *ln32 = nullptr, *h32 = nullptr;
     bool ok = cudaMalloc(&r8, c) == cudaSuccess && cudaMalloc(&s8, c) == cudaSuccess &&
               cudaMalloc(&st64, c * 8) == cudaSuccess && cudaMalloc(&ln32, c * 4) == cudaSuccess &&
@@ -1554,6 +1592,11 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     l->win_start = static_cast<uint64_t*>(st64);
     l->win_len = static_cast<uint32_t*>(ln32);
     l->hits = static_cast<uint32_t*>(h32);
+    L.ref = l->ref_id;
+    L.str = l->strand;
+    L.start = l->win_start;
+    L.len = l->win_len;
+    L.hits = l->hits;
     cap_out = c;
     return true;
   };
@@ -1624,12 +1667,11 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
     // the emit / filter buffers, sized for the largest sub-chunk so far
     uint64_t cap = 0;
-    uint64_t *d_cals = nullptr, *d_wkey = nullptr, *d_ostart = nullptr;
-    uint32_t *d_whits = nullptr, *d_wlen = nullptr, *d_olen = nullptr, *d_ohits = nullptr;
-    uint8_t *d_oref = nullptr, *d_ostr = nullptr;
+    uint64_t *d_cals = nullptr, *d_wkey = nullptr;
+    uint32_t *d_whits = nullptr, *d_wlen = nullptr;
     uint64_t* d_scratch = nullptr;
     uint64_t scratch_keys = 0;
-    std::vector<uint32_t> woff, sub;
+    std::vector<uint32_t> sub;
     // one sub-chunk (reads r0 .. r0 + nr of the chunk at R0, offsets in d_off):
     // routing, emit, filter, window offsets and the compacted windows
     auto run_sub = [&](uint32_t r0, uint32_t nr, const CalRanges& kept) -> sr_status {
@@ -1655,51 +1697,21 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
         return done(SR_ECUDA, "sr_candidates_device filter");
       }
       uint32_t nw32 = 0;
-      if (out_dev) {
-        e = cudaMemcpyAsync(&nw32, d_woff + nr, 4, cudaMemcpyDeviceToHost, st);
-      } else {
-        woff.resize(nr + 1ull);
-        e = cudaMemcpyAsync(woff.data(), d_woff, (nr + 1ull) * 4, cudaMemcpyDeviceToHost, st);
-      }
+      e = cudaMemcpyAsync(&nw32, d_woff + nr, 4, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window count");
-      const uint64_t nw = out_dev ? nw32 : woff[nr];
-      if (out_dev) {
-        // this sub-chunk's offsets in the whole list, its windows compacted
-        // straight into the list's arrays after the windows so far
-        if (launch_cal_offsets(d_woff, nr, total_w, l->offsets + r0, st) < 0) {
-          e = cudaGetLastError();
-          return done(SR_ECUDA, "sr_candidates_device offsets");
-        }
-        if (!grow_out(total_w + nw, total_w)) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-        if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, l->ref_id + total_w,
-                               l->strand + total_w, l->win_start + total_w, l->win_len + total_w, l->hits + total_w,
-                               st) < 0) {
-          e = cudaGetLastError();
-          return done(SR_ECUDA, "sr_candidates_device compact");
-        }
-      } else {
-        if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, d_oref, d_ostr, d_ostart, d_olen,
-                               d_ohits, st) < 0) {
-          e = cudaGetLastError();
-          return done(SR_ECUDA, "sr_candidates_device compact");
-        }
-        o_ref.resize(total_w + nw);
-        o_strand.resize(total_w + nw);
-        o_start.resize(total_w + nw);
-        o_len.resize(total_w + nw);
-        o_hits.resize(total_w + nw);
-        if (nw) {
-          e = cudaMemcpyAsync(o_ref.data() + total_w, d_oref, nw, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(o_strand.data() + total_w, d_ostr, nw, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess)
-            e = cudaMemcpyAsync(o_start.data() + total_w, d_ostart, nw * 8, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(o_len.data() + total_w, d_olen, nw * 4, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(o_hits.data() + total_w, d_ohits, nw * 4, cudaMemcpyDeviceToHost, st);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-          if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device window copy");
-        }
-        for (uint32_t i = 0; i <= nr; ++i) offsets[r0 + i] = total_w + woff[i];
+      const uint64_t nw = nw32;
+      // this sub-chunk's offsets in the whole list, its windows compacted
+      // straight into the list's arrays after the windows so far
+      if (launch_cal_offsets(d_woff, nr, total_w, L.off + r0, st) < 0) {
+        e = cudaGetLastError();
+        return done(SR_ECUDA, "sr_candidates_device offsets");
+      }
+      if (!grow_out(total_w + nw, total_w)) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
+      if (launch_cal_compact(nr, d_off, d_nwin, d_woff, d_wkey, d_whits, d_wlen, L.ref + total_w, L.str + total_w,
+                             L.start + total_w, L.len + total_w, L.hits + total_w, st) < 0) {
+        e = cudaGetLastError();
+        return done(SR_ECUDA, "sr_candidates_device compact");
       }
       total_w += nw;
       return static_cast<sr_status>(SR_OK);
@@ -1744,13 +1756,6 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
         d_wkey = static_cast<uint64_t*>(cbuf(kCbWkey, cap * 8));
         d_whits = static_cast<uint32_t*>(cbuf(kCbWhits, cap * 4));
         d_wlen = static_cast<uint32_t*>(cbuf(kCbWlen, cap * 4));
-        if (!out_dev) {  // a device list is compacted straight into its arrays
-          d_oref = static_cast<uint8_t*>(cbuf(kCbOref, cap));
-          d_ostr = static_cast<uint8_t*>(cbuf(kCbOstr, cap));
-          d_ostart = static_cast<uint64_t*>(cbuf(kCbOstart, cap * 8));
-          d_olen = static_cast<uint32_t*>(cbuf(kCbOlen, cap * 4));
-          d_ohits = static_cast<uint32_t*>(cbuf(kCbOhits, cap * 4));
-        }
         if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
       }
       if (cends[1] <= cap) {
@@ -1794,21 +1799,47 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
     *out = l;
     return SR_OK;
   }
-  sr_status stt = done(SR_OK, "");
-  if (stt != SR_OK) return stt;
-  sr_cand_list_free(l);
-  l = nullptr;
-  sr_status st2 = sr_cand_list_alloc(n, total_w, &l);
-  if (st2 != SR_OK) return st2;
-  std::memcpy(l->offsets, offsets.data(), (n + 1ull) * 8);
-  if (total_w) {
-    std::memcpy(l->ref_id, o_ref.data(), total_w);
-    std::memcpy(l->strand, o_strand.data(), total_w);
-    std::memcpy(l->win_start, o_start.data(), total_w * 8);
-    std::memcpy(l->win_len, o_len.data(), total_w * 4);
-    std::memcpy(l->hits, o_hits.data(), total_w * 4);
+  // host output: the device list copied out through one pinned block, then
+  // spread over the host threads into the list's own arrays
+  sr_cand_list* h = nullptr;
+  const sr_status sa = sr_cand_list_alloc(n, total_w, &h);
+  if (sa != SR_OK) return done(sa, "sr_candidates_device: out of memory");
+  const uint64_t part_bytes[6] = {(n + 1ull) * 8, total_w, total_w, total_w * 8, total_w * 4, total_w * 4};
+  const void* src[6] = {L.off, L.ref, L.str, L.start, L.len, L.hits};
+  void* dst[6] = {h->offsets, h->ref_id, h->strand, h->win_start, h->win_len, h->hits};
+  uint64_t at[7] = {0};
+  for (int k = 0; k < 6; ++k) at[k + 1] = (at[k] + part_bytes[k] + 255) & ~255ull;
+  uint64_t got = 0;
+  char* blk = static_cast<char*>(pool_take(s, at[6], &got));
+  if (!blk) {
+    sr_cand_list_free(h);
+    return done(SR_ENOMEM, "sr_candidates_device: pinned host allocation failed");
   }
-  *out = l;
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+    if (part_bytes[k]) e = cudaMemcpyAsync(blk + at[k], src[k], part_bytes[k], cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    pool_give(s, blk, got);
+    sr_cand_list_free(h);
+    return done(SR_ECUDA, "sr_candidates_device list copy");
+  }
+  constexpr uint64_t kSlice = 4ull << 20;  // bytes per host copy task
+  std::vector<std::pair<int, uint64_t>> tasks;
+  for (int k = 0; k < 6; ++k)
+    for (uint64_t o = 0; o < part_bytes[k]; o += kSlice) tasks.emplace_back(k, o);
+  parallel_for(static_cast<uint32_t>(tasks.size()), [&](uint32_t t) {
+    const int k = tasks[t].first;
+    const uint64_t o = tasks[t].second, len = std::min(kSlice, part_bytes[k] - o);
+    std::memcpy(static_cast<char*>(dst[k]) + o, blk + at[k] + o, len);
+  });
+  pool_give(s, blk, got);
+  const sr_status stt = done(SR_OK, "");
+  sr_cand_list_free(l);
+  if (stt != SR_OK) {
+    sr_cand_list_free(h);
+    return stt;
+  }
+  *out = h;
   return SR_OK;
 }
 

@@ -67,6 +67,38 @@ __device__ __forceinline__ void lookup_packed(const DevIndex& di, uint64_t b, ui
   *hi = e;
 }
 
+// packed index with bucket heads: entries [lo0, hi0) of reference 0 and [lo1,
+// hi1) of reference 1 with key `key` in bucket b, from the bucket's head alone
+// (an empty range may start anywhere); false when the bucket spilled (its
+// entries are then looked up in jptr / key16)
+__device__ __forceinline__ bool lookup_head(const uint4* heads, uint64_t b, uint32_t key, uint32_t* lo0,
+                                            uint32_t* hi0, uint32_t* lo1, uint32_t* hi1) {
+  const uint4* h = heads + b * 4;
+  const uint4 v0 = __ldg(h), v1 = __ldg(h + 1), v2 = __ldg(h + 2), v3 = __ldg(h + 3);
+  if (v0.z == kHeadSpill) return false;
+  const uint32_t w[13] = {v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w, v3.x, v3.y, v3.z, v3.w};
+  // bit i: the head's key i equals the seed's, two keys per word: a 16-bit half
+  // of w ^ (key, key) is zero exactly when adding 0x7fff to its low 15 bits
+  // leaves its top bit clear and its top bit was clear
+  const uint32_t kk = key | (key << 16);
+  uint32_t eq = 0;
+#pragma unroll
+  for (int j = 0; j < 13; ++j) {
+    const uint32_t x = w[j] ^ kk;
+    const uint32_t z = ~(((x & 0x7fff7fffu) + 0x7fff7fffu) | x) & 0x80008000u;
+    eq |= (((z >> 15) & 1u) | (z >> 30)) << (2 * j);
+  }
+  // equal keys are consecutive within each reference's run of sorted keys
+  const uint32_t n0 = v0.z & 0xffffu, n1 = v0.z >> 16;
+  const uint32_t m0 = (1u << n0) - 1u, m1 = ((1u << (n0 + n1)) - 1u) & ~m0;
+  const uint32_t e0 = eq & m0, e1 = eq & m1;
+  *lo0 = v0.x + (e0 ? __ffs(e0) - 1u : 0u);
+  *hi0 = *lo0 + __popc(e0);
+  *lo1 = v0.y + (e1 ? __ffs(e1) - 1u - n0 : 0u);
+  *hi1 = *lo1 + __popc(e1);
+  return true;
+}
+
 // entries [lo, hi) of reference r whose key equals the seed's
 __device__ __forceinline__ void lookup(const DevIndex& di, int r, uint64_t canon, uint64_t* lo, uint64_t* hi) {
   const int kb = 2 * (di.k - di.a);
@@ -101,6 +133,48 @@ __device__ __forceinline__ bool load_codes(const char* bases, uint64_t o0, uint3
   if (bad && lane == 0) atomicOr(status, kStBadBase);
   __syncwarp();
   return !bad;
+}
+
+// The read's codes as 2-bit fields, first base highest, in kPackWords 32-bit
+// words (kMaxReadLen bases and two words of padding): Pk for the read, Rk for
+// the reverse complement of the read padded to kMaxReadLen bases, so that a
+// seed's forward and reverse-complement k-mers (Kmer's fwd and rc) are each
+// read with two funnel shifts.  Bases past the read's end are never extracted.
+constexpr int kPackWords = kMaxReadLen / 16 + 2;
+
+// q: the codes (one byte each, 4-byte aligned); lanes 0-15 pack word j
+__device__ __forceinline__ void pack_codes(const uint8_t* q, uint32_t* Pk, uint32_t* Rk, int lane) {
+  const uint32_t* q32 = reinterpret_cast<const uint32_t*>(q);
+  uint32_t w = 0;
+  if (lane < kMaxReadLen / 16) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      // four codes, first in byte 0, to one byte with the first code highest
+      const uint32_t x = __byte_perm(q32[4 * lane + i] & 0x03030303u, 0, 0x0123);
+      const uint32_t t = (x | (x >> 6)) & 0x000F000Fu;
+      w = (w << 8) | ((t | (t >> 12)) & 0xFFu);
+    }
+  }
+  // the reverse complement: words in reverse order, 2-bit fields reversed, complemented
+  const uint32_t src = __shfl_sync(FULL, w, (kMaxReadLen / 16 - 1 - lane) & 31);
+  uint32_t r = __brev(~src);
+  r = ((r >> 1) & 0x55555555u) | ((r << 1) & 0xAAAAAAAAu);
+  if (lane < kMaxReadLen / 16) {
+    Pk[lane] = w;
+    Rk[lane] = r;
+  } else if (lane < kPackWords) {
+    Pk[lane] = 0;
+    Rk[lane] = 0;
+  }
+  __syncwarp();
+}
+
+// the k bases at o of a packed string, first base highest (k <= 32)
+__device__ __forceinline__ uint64_t kmer_at(const uint32_t* W, uint32_t o, int k) {
+  const uint32_t b = 2 * o, j = b >> 5, s = b & 31;
+  const uint32_t w0 = W[j], w1 = W[j + 1], w2 = W[j + 2];
+  const uint64_t win = (static_cast<uint64_t>(__funnelshift_l(w1, w0, s)) << 32) | __funnelshift_l(w2, w1, s);
+  return win >> (64 - 2 * k);
 }
 
 struct SeedArgs {
@@ -148,9 +222,11 @@ __global__ void k_cal_slots(const uint64_t* read_off, uint32_t n, int k, uint32_
   slots[r] = m >= static_cast<uint32_t>(k) ? ((m - k) / stride + 1u) * static_cast<uint32_t>(n_refs) : 0u;
 }
 
+// 12 blocks per SM: 40 registers, no spills (48 warps per SM)
 template <bool EMIT>
-__global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
-  __shared__ uint8_t qs[kCalWarps][kMaxReadLen];
+__global__ void __launch_bounds__(32 * kCalWarps, 12) k_cal_seeds(SeedArgs a) {
+  __shared__ __align__(16) uint8_t qs[kCalWarps][kMaxReadLen];
+  __shared__ uint32_t pk_s[kCalWarps][kPackWords], rk_s[kCalWarps][kPackWords];
   __shared__ uint32_t ctr[kCalWarps];
   __shared__ uint32_t incl_s[kCalWarps][32];  // inclusive scan of the lanes' entry counts
   __shared__ uint64_t lo_s[kCalWarps][32];     // each lane's first matching entry
@@ -175,21 +251,23 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
     uint64_t* rec = a.ranges ? a.ranges + (len_ok ? a.seed_off[r - a.rbase] : 0u) : nullptr;
     bool fits = true;
     if (len_ok && (kept || load_codes(a.bases, o0, m, q, lane, a.status)) && m >= static_cast<uint32_t>(k)) {
+      if (!kept) pack_codes(q, pk_s[warp], rk_s[warp], lane);
       const uint64_t base = EMIT ? a.off[rr] : 0;
       // 32 seeds per round, one per lane; the matching entries of all of them
       // are then shared out over the warp (a repeat seed may have thousands)
-      for (uint32_t o_base = 0; o_base + k <= m; o_base += 32 * a.stride) {
+      for (uint32_t o_base = 0, si_base = 0; o_base + k <= m; o_base += 32 * a.stride, si_base += 32) {
         const uint32_t o = o_base + lane * a.stride;
-        const uint32_t si = o / a.stride;  // the seed's index in the read
+        const uint32_t si = si_base + lane;  // the seed's index in the read
         const bool live = o + k <= m;
         uint64_t canon = 0;
         uint32_t rori = 0;
         if (!kept) {
-          Kmer km;
-          if (live)
-            for (int t = 0; t < k; ++t) kmer_push(km, q[o + t], k);
-          canon = km.fwd < km.rc ? km.fwd : km.rc;
-          rori = (km.fwd == canon ? 1u : 0u) | (km.rc == canon ? 2u : 0u);
+          // Kmer's fwd and rc of the seed (the reverse complement's k-mer at
+          // kMaxReadLen - o - k of the padded reverse complement)
+          const uint64_t fwd = live ? kmer_at(pk_s[warp], o, k) : 0;
+          const uint64_t rc = live ? kmer_at(rk_s[warp], kMaxReadLen - o - k, k) : 0;
+          canon = fwd < rc ? fwd : rc;
+          rori = (fwd == canon ? 1u : 0u) | (rc == canon ? 2u : 0u);
         }
         // packed index: one hash (the references share its seed) gives the bucket
         // and key in every reference
@@ -201,6 +279,11 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
           pb = h >> kb;
           pkey = static_cast<uint32_t>(h & mask_bits(kb));
         }
+        // with bucket heads, one access answers both references (at most two);
+        // the count pass only (the emit pass reads the lookups it kept)
+        uint32_t hl0 = 0, hh0 = 0, hl1 = 0, hh1 = 0;
+        bool head = false;
+        if (!EMIT && a.di.heads && live) head = lookup_head(a.di.heads, pb, pkey, &hl0, &hh0, &hl1, &hh1);
         for (int r2 = 0; r2 < a.di.n_refs; ++r2) {
           uint64_t lo = 0, hi = 0;
           if (kept) {
@@ -211,8 +294,14 @@ __global__ void __launch_bounds__(32 * kCalWarps) k_cal_seeds(SeedArgs a) {
               rori = static_cast<uint32_t>(x & 3u);
             }
           } else if (live) {
-            if (a.di.packed) lookup_packed(a.di, pb, pkey, r2, &lo, &hi);
-            else lookup(a.di, r2, canon, &lo, &hi);
+            if (head) {
+              lo = r2 ? hl1 : hl0;
+              hi = r2 ? hh1 : hh0;
+            } else if (a.di.packed) {
+              lookup_packed(a.di, pb, pkey, r2, &lo, &hi);
+            } else {
+              lookup(a.di, r2, canon, &lo, &hi);
+            }
           }
           uint32_t cnt = static_cast<uint32_t>(hi - lo);
           if (!EMIT) {
@@ -681,6 +770,37 @@ int launch_cal_slots(const uint64_t* read_off, uint32_t n, int k, uint32_t strid
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+// one thread per bucket: its head from jptr and key16 (the layout at DevIndex)
+__global__ void k_cal_heads(DevIndex di, uint64_t nb, uint4* heads) {
+  const uint64_t b = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+  if (b >= nb) return;
+  const int R = di.n_refs;
+  const uint32_t s0 = di.jptr[b * R], e0 = di.jptr[(b + 1) * R];
+  const uint32_t s1 = R > 1 ? di.jptr[b * R + 1] : 0u, e1 = R > 1 ? di.jptr[(b + 1) * R + 1] : 0u;
+  const uint64_t n0 = e0 - s0, n1 = e1 - s1;
+  uint32_t w[16];
+  for (int i = 0; i < 16; ++i) w[i] = 0;
+  w[0] = s0;
+  w[1] = s1;
+  if (n0 + n1 <= static_cast<uint64_t>(kHeadKeys)) {
+    w[2] = static_cast<uint32_t>(n0 | (n1 << 16));
+    for (uint32_t i = 0; i < n0 + n1; ++i) {
+      const uint32_t kk = i < n0 ? di.key16[0][s0 + i] : di.key16[1][s1 + (i - n0)];
+      w[3 + (i >> 1)] |= kk << (16 * (i & 1));
+    }
+  } else {
+    w[2] = kHeadSpill;
+  }
+  for (int j = 0; j < 4; ++j) heads[b * 4 + j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+}
+
+int launch_cal_heads(const DevIndex& di, uint64_t nbuckets, uint4* heads, cudaStream_t st) {
+  if (!di.packed || di.n_refs < 1 || di.n_refs > 2) return -1;
+  if (nbuckets == 0) return 0;
+  k_cal_heads<<<static_cast<unsigned>((nbuckets + 255) / 256), 256, 0, st>>>(di, nbuckets, heads);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
                      uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* actual,
                      uint32_t* status, const CalRanges& kept, cudaStream_t st) {
@@ -899,6 +1019,7 @@ int launch_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, c
 int preload_cal() {
   int n_ = 0;
   SR_TOUCH(k_cal_slots);
+  SR_TOUCH(k_cal_heads);
   SR_TOUCH(k_cal_seeds<false>);
   SR_TOUCH(k_cal_seeds<true>);
   SR_TOUCH(k_cal_filter);

@@ -279,6 +279,13 @@ struct DevIndex {
   const uint16_t* key16[kMaxRefs];
   const uint32_t* posor[kMaxRefs];
   int packed;
+  // bucket heads (packed form, one or two references; nullptr otherwise): 64
+  // bytes per bucket, read with one access: its first entry in references 0 and
+  // 1 (words 0, 1), their entry counts (word 2, 16 bits each) and up to
+  // kHeadKeys keys, reference 0's then reference 1's in entry order (words 3-15,
+  // two per word, low half first).  Word 2 is kHeadSpill where they do not fit:
+  // that bucket is looked up in jptr and key16.
+  const uint4* heads;
   uint64_t ref_len[kMaxRefs];
   uint64_t hash_seed[kMaxRefs];
   int n_refs, k, a;
@@ -302,6 +309,10 @@ struct CalRanges {
   uint8_t* recount = nullptr;
   uint32_t rbase = 0;
 };
+constexpr int kHeadKeys = 26;
+constexpr uint32_t kHeadSpill = 0xffffffffu;
+// the bucket heads of a packed index (nbuckets buckets, n_refs <= 2) into heads
+int launch_cal_heads(const DevIndex& di, uint64_t nbuckets, uint4* heads, cudaStream_t st);
 int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
                      uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* actual,
                      uint32_t* status, const CalRanges& kept, cudaStream_t st);

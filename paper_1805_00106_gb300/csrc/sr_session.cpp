@@ -1427,6 +1427,26 @@ extern "C" sr_status sr_session_attach_index(sr_session* s, const sr_index* cons
   s->didx.n_refs = static_cast<int>(n_refs);
   s->didx.k = static_cast<int>(t[0].seed_len);
   s->didx.a = static_cast<int>(t[0].address_bases);
+  // bucket heads, built on the device from the packed tables: where buckets are
+  // small (at most half a head's keys on average) a seed's lookup in both
+  // references is one 64-byte access instead of three dependent ones
+  // (SR_CAL_HEADS=0 leaves them out)
+  const uint64_t nbk = t[0].n_ptr ? t[0].n_ptr - 1 : 0;
+  uint64_t entries = 0;
+  for (uint32_t r = 0; r < n_refs; ++r) entries += t[r].n_entries;
+  if (packed && n_refs <= 2 && nbk && nbk <= (1ull << 26) && entries <= nbk * (kHeadKeys / 2) &&
+      env_u64("SR_CAL_HEADS", 1) != 0) {
+    void* ph = nullptr;
+    if (cudaMalloc(&ph, nbk * 64) == cudaSuccess) {
+      s->idx_bufs.push_back(ph);
+      if (launch_cal_heads(s->didx, nbk, static_cast<uint4*>(ph), s->stream) < 0 ||
+          cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return fail();
+      s->didx.heads = static_cast<const uint4*>(ph);
+    } else {
+      cudaGetLastError();  // the heads are optional: without them the lookups read jptr / key16
+    }
+  }
   return SR_OK;
 }
 

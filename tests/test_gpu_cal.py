@@ -43,6 +43,21 @@ def test_device_matches_host_xenograft(sr, k, addr, cal_limit, seeds):
         _same(d, h)
 
 
+@pytest.mark.parametrize("heads", ["1", "0"])
+def test_packed_index_with_and_without_bucket_heads(sr, monkeypatch, heads):
+    """The packed index's lookups through the bucket heads (one access per seed
+    for both references) and through the bucket starts and keys give the same
+    list as the host stage; SR_CAL_HEADS=0 at attach time leaves the heads out."""
+    monkeypatch.setenv("SR_CAL_HEADS", heads)
+    w = S.workload("c3", scale=0.002, seed=23, rc_frac=0.5)
+    for k, addr in [(16, 8), (20, 12)]:
+        idx = [sr.Index.build(bytes(r), seed_len=k, address_bases=addr, cal_limit=0) for r in w["refs"]]
+        s = sr.Session.from_indexes(idx)
+        s.attach_index(idx)
+        for prm in [dict(seed_stride=1, merge_dist=32, pad=32), dict(seed_stride=2, merge_dist=0, pad=8, max_cands=2)]:
+            _same(s.candidates(w["bases"], w["read_off"], **prm), sr.candidates(idx, w["bases"], w["read_off"], **prm))
+
+
 def test_device_matches_bruteforce_oracle(sr):
     rng = np.random.default_rng(3)
     ref = rng.choice(np.frombuffer(b"ACGT", np.uint8), 3000)
@@ -69,10 +84,13 @@ def test_device_matches_bruteforce_oracle(sr):
         assert got == list(zip(e_ref.tolist(), e_str.tolist(), e_st.tolist(), e_len.tolist(), e_hits.tolist()))
 
 
-def test_reads_with_very_many_cals(sr):
+@pytest.mark.parametrize("k,addr", [(20, 10), (16, 8)])
+def test_reads_with_very_many_cals(sr, k, addr):
     """A tandem repeat gives reads tens of thousands of CALs: the large-read
     filter (global-memory sort) must agree with the host too; a shorter one
-    (60 copies) gives a few thousand, the shared-memory filter of mid-size reads."""
+    (60 copies) gives a few thousand, the shared-memory filter of mid-size reads.
+    With (16, 8) the index takes the packed form with bucket heads, and the
+    repeat's buckets (hundreds of entries) spill out of their heads."""
     rng = np.random.default_rng(11)
     unit = rng.choice(np.frombuffer(b"ACGT", np.uint8), 23)
     unit2 = rng.choice(np.frombuffer(b"ACGT", np.uint8), 31)
@@ -86,14 +104,14 @@ def test_reads_with_very_many_cals(sr):
         reads.append(ref[st:st + m])
         offs.append(offs[-1] + m)
     bases = np.concatenate(reads)
-    idx = [sr.Index.build(bytes(ref), seed_len=20, address_bases=10, cal_limit=0)]
+    idx = [sr.Index.build(bytes(ref), seed_len=k, address_bases=addr, cal_limit=0)]
     s = sr.Session.from_indexes(idx)
     s.attach_index(idx)
     for prm in [dict(merge_dist=0, pad=8), dict(merge_dist=32, pad=32), dict(merge_dist=5, pad=0, max_cands=7)]:
         h = sr.candidates(idx, bases, np.array(offs), **prm)
         d = s.candidates(bases, np.array(offs), **prm)
         _same(d, h)
-        if prm["merge_dist"] == 0:
+        if prm["merge_dist"] == 0 and k == 20:
             # one window per repeat copy: ~900 windows from ~200k CALs (the large-read path)
             assert int(np.max(np.diff(h["cand_off"]))) > 500
             assert int(np.max(h["c_hits"])) > 100

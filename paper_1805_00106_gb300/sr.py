@@ -415,23 +415,42 @@ def candidates(indexes, bases, read_off, seed_stride=1, merge_dist=32, pad=32, m
     return _cand_list_to_numpy(out)
 
 
+class _CandListOwner:
+    """Frees a host sr_cand_list once no array viewing it is left."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if self.ptr is not None and _lib is not None:
+            _lib.sr_cand_list_free(self.ptr)
+        self.ptr = None
+
+
+class _HostView:
+    """numpy view of count elements of a library array (no copy); holds its owner."""
+
+    def __init__(self, owner, addr, count, typestr):
+        self.owner = owner
+        self.__array_interface__ = {"data": (addr, False), "shape": (count,), "typestr": typestr, "version": 3}
+
+
 def _cand_list_to_numpy(out):
+    """The list's arrays as numpy views of the library's own buffers (the list is
+    freed with the last of them); cand_off and c_start read as int64, c_len as
+    int32 (same bits: offsets, starts and lengths stay below 2^31 / 2^63)."""
     l = out.contents
     n, nc = l.n_reads, l.n_cands
+    owner = _CandListOwner(out)
 
-    def a(ptr, count, dt):
-        if count == 0:
-            return np.zeros(0, dt)
-        buf = (C.c_char * (count * np.dtype(dt).itemsize)).from_address(ptr)
-        return np.frombuffer(buf, dt).copy()
+    def a(ptr, count, typestr, dt):
+        if count == 0 or not ptr:
+            return np.zeros(count, dt)
+        return np.asarray(_HostView(owner, ptr, count, typestr))
 
-    res = dict(cand_off=a(l.offsets, n + 1, np.uint64).astype(np.int64), c_ref=a(l.ref_id, nc, np.uint8),
-               c_strand=a(l.strand, nc, np.uint8), c_start=a(l.win_start, nc, np.uint64).astype(np.int64),
-               c_len=a(l.win_len, nc, np.uint32).astype(np.int32), c_hits=a(l.hits, nc, np.uint32))
-    if n + 1 and len(res["cand_off"]) == 0:
-        res["cand_off"] = np.zeros(n + 1, np.int64)
-    lib().sr_cand_list_free(out)
-    return res
+    return dict(cand_off=a(l.offsets, n + 1, "<i8", np.int64), c_ref=a(l.ref_id, nc, "|u1", np.uint8),
+                c_strand=a(l.strand, nc, "|u1", np.uint8), c_start=a(l.win_start, nc, "<i8", np.int64),
+                c_len=a(l.win_len, nc, "<i4", np.int32), c_hits=a(l.hits, nc, "<u4", np.uint32))
 
 
 class _CudaArray:

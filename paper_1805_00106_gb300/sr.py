@@ -427,14 +427,6 @@ class _CandListOwner:
         self.ptr = None
 
 
-class _HostView:
-    """numpy view of count elements of a library array (no copy); holds its owner."""
-
-    def __init__(self, owner, addr, count, typestr):
-        self.owner = owner
-        self.__array_interface__ = {"data": (addr, False), "shape": (count,), "typestr": typestr, "version": 3}
-
-
 def _cand_list_to_numpy(out):
     """The list's arrays as numpy views of the library's own buffers (the list is
     freed with the last of them); cand_off and c_start read as int64, c_len as
@@ -443,14 +435,16 @@ def _cand_list_to_numpy(out):
     n, nc = l.n_reads, l.n_cands
     owner = _CandListOwner(out)
 
-    def a(ptr, count, typestr, dt):
+    def a(ptr, count, dt):
         if count == 0 or not ptr:
             return np.zeros(count, dt)
-        return np.asarray(_HostView(owner, ptr, count, typestr))
+        buf = (C.c_char * (count * np.dtype(dt).itemsize)).from_address(ptr)
+        buf._owner = owner
+        return np.frombuffer(buf, dt)
 
-    return dict(cand_off=a(l.offsets, n + 1, "<i8", np.int64), c_ref=a(l.ref_id, nc, "|u1", np.uint8),
-                c_strand=a(l.strand, nc, "|u1", np.uint8), c_start=a(l.win_start, nc, "<i8", np.int64),
-                c_len=a(l.win_len, nc, "<i4", np.int32), c_hits=a(l.hits, nc, "<u4", np.uint32))
+    return dict(cand_off=a(l.offsets, n + 1, np.int64), c_ref=a(l.ref_id, nc, np.uint8),
+                c_strand=a(l.strand, nc, np.uint8), c_start=a(l.win_start, nc, np.int64),
+                c_len=a(l.win_len, nc, np.int32), c_hits=a(l.hits, nc, np.uint32))
 
 
 class _CudaArray:

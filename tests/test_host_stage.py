@@ -115,3 +115,23 @@ def test_bad_inputs(sr):
     with pytest.raises(sr.SrError) as e:
         sr.candidates([idx], np.frombuffer(b"ACGTXACGTACGT", np.uint8), np.array([0, 13]))
     assert e.value.status == sr.SR_EBADBASE
+
+
+def test_candidate_arrays_outlive_their_dict(sr):
+    """The list's arrays are views of the library's buffers: they stay valid (and
+    keep their values) after the dict and every other array are dropped, and
+    many lists in a row neither leak into each other nor fail to free."""
+    import gc
+    w = S.workload("c3", scale=0.0002, seed=4, rc_frac=0.5)
+    idx = [sr.Index.build(bytes(r), seed_len=16, address_bases=8) for r in w["refs"]]
+    g = sr.candidates(idx, w["bases"], w["read_off"], seed_stride=1, merge_dist=24, pad=16)
+    want = {k: np.array(v, copy=True) for k, v in g.items()}
+    start, off = g["c_start"], g["cand_off"]
+    assert start.dtype == np.int64 and off.dtype == np.int64 and g["c_len"].dtype == np.int32
+    del g
+    gc.collect()
+    for _ in range(20):  # other lists allocated and freed meanwhile
+        h = sr.candidates(idx, w["bases"][::-1].copy(), w["read_off"], seed_stride=2, merge_dist=0, pad=0)
+        del h
+    gc.collect()
+    assert np.array_equal(start, want["c_start"]) and np.array_equal(off, want["cand_off"])

@@ -234,7 +234,12 @@ void sr_session_close(sr_session* s);
  * address_bases) <= 16, the device copy is packed (bucket starts of all
  * references interleaved in 32 bits, 16-bit keys, position and orientation in
  * one word: 6 bytes per entry and 4 per bucket); otherwise each reference's
- * tables are copied as they are (9 bytes per entry and 8 per bucket).  sr_candidates_device then returns exactly the list
+ * tables are copied as they are (9 bytes per entry and 8 per bucket).  A packed
+ * copy of one or two references with at most 2^26 buckets and at most 13
+ * entries per bucket on average also gets 64-byte bucket heads (both
+ * references' starts and counts and up to 26 keys, built on the device; left
+ * out if they cannot be allocated, or with SR_CAL_HEADS=0 in the environment).
+ * sr_candidates_device then returns exactly the list
  * sr_candidates returns for those indexes (same windows, order and hits): one
  * warp per read looks up its seeds, one block per read sorts and merges its
  * CALs.  The reads may be host memory or, flagged SR_FLAG_DEVICE, device

@@ -169,10 +169,6 @@ __device__ __forceinline__ void pack_codes(const uint8_t* q, uint32_t* Pk, uint3
   __syncwarp();
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // the k bases at o of a packed string, first base highest (k <= 32)
 __device__ __forceinline__ uint64_t kmer_at(const uint32_t* W, uint32_t o, int k) {
   const uint32_t b = 2 * o, j = b >> 5, s = b & 31;
@@ -240,15 +236,9 @@ __global__ void __launch_bounds__(32 * kCalWarps, 12) k_cal_seeds(SeedArgs a) {
   uint8_t* q = qs[warp];
   uint32_t* incl = incl_s[warp];
   const int k = a.di.k;
-  const uint32_t rstep = gridDim.x * kCalWarps;
-  // lanes 0 and 1 hold the next read's two offsets, loaded a read ahead
-  uint64_t nxt = 0;
-  if (blockIdx.x * kCalWarps + warp < a.nr && lane < 2) nxt = a.read_off[a.r0 + blockIdx.x * kCalWarps + warp + lane];
-  for (uint32_t rr = blockIdx.x * kCalWarps + warp; rr < a.nr; rr += rstep) {
+  for (uint32_t rr = blockIdx.x * kCalWarps + warp; rr < a.nr; rr += gridDim.x * kCalWarps) {
     const uint32_t r = a.r0 + rr;
-    const uint64_t o0 = __shfl_sync(FULL, nxt, 0), o1 = __shfl_sync(FULL, nxt, 1);
-    const bool more = rr + rstep < a.nr;
-    if (more && lane < 2) nxt = a.read_off[r + rstep + lane];
+    const uint64_t o0 = a.read_off[r], o1 = a.read_off[r + 1];
     const uint32_t m = static_cast<uint32_t>(o1 - o0);
     if (lane == 0) ctr[warp] = 0;
     __syncwarp();
@@ -262,12 +252,6 @@ __global__ void __launch_bounds__(32 * kCalWarps, 12) k_cal_seeds(SeedArgs a) {
     bool fits = true;
     if (len_ok && (kept || load_codes(a.bases, o0, m, q, lane, a.status)) && m >= static_cast<uint32_t>(k)) {
       if (!kept) pack_codes(q, pk_s[warp], rk_s[warp], lane);
-      if (!EMIT) {
-        // the next read's bases on their way to L2 while this read's seeds are looked up
-        // (only addresses inside that read: lane l takes byte 128 l of it)
-        const uint64_t on = __shfl_sync(FULL, nxt, 0), on1 = __shfl_sync(FULL, nxt, 1);
-        if (more && lane < 2 && on + 128u * lane < on1) prefetch_l2(a.bases + on + 128u * lane);
-      }
       const uint64_t base = EMIT ? a.off[rr] : 0;
       // 32 seeds per round, one per lane; the matching entries of all of them
       // are then shared out over the warp (a repeat seed may have thousands)

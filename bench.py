@@ -62,6 +62,9 @@ def parse():
                     help="seed length x CAL limit sweep on the xenograft and repeat-heavy workloads "
                          "(one JSON line per setting) instead of the bench line")
     ap.add_argument("--sweep-scale", type=float, default=1.0)
+    ap.add_argument("--sweep-only", default="",
+                    help="comma-separated settings to run, each workload[:k[:limit]] "
+                         "(e.g. c5:20:inf; workloads c3, c5, splicing; profiling)")
     ap.add_argument("--sweep-seconds", type=float, default=900.0,
                     help="wall budget of the sweep: settings not started by then are skipped")
     return ap.parse_args()
@@ -352,12 +355,31 @@ def sweep(args):
                           "budget_s": args.sweep_seconds}), flush=True)
         return True
 
+    only = [x.split(":") for x in args.sweep_only.split(",") if x]
+
+    def wanted(name, k=None, limit=None):
+        if not only:
+            return True
+        for o in only:
+            if o[0] != name:
+                continue
+            if k is not None and len(o) > 1 and int(o[1]) != k:
+                continue
+            if limit is not None and len(o) > 2 and (0 if o[2] == "inf" else int(o[2])) != limit:
+                continue
+            return True
+        return False
+
     for name in ["c3", "c5"]:
+        if not wanted(name):
+            continue
         w = synth.workload(name, scale=args.sweep_scale, seed=11, rc_frac=RC_FRAC)
         n = len(w["read_off"]) - 1
         truth_end = np.asarray(w["t_pos"], np.int64) + np.asarray(w["t_span"], np.int64) - 1
         for k in (20, 25):
             for limit in (0, 1024, 128):
+                if not wanted(name, k, limit):
+                    continue
                 if over_budget(f"{name} k={k} limit={limit or 'inf'}"):
                     continue
                 t0 = time.perf_counter()
@@ -394,6 +416,8 @@ def sweep(args):
                 print(json.dumps(line), flush=True)
                 del sess, idx
     # alternative splicing (Table 4): the genome alone vs the genome plus the exon-junction library
+    if not wanted("splicing"):
+        return
     w = synth.splicing(scale=args.sweep_scale, seed=13)
     n = len(w["read_off"]) - 1
     m = np.diff(np.asarray(w["read_off"], np.int64))

@@ -455,7 +455,10 @@ __device__ uint64_t block_exscan(uint64_t v, uint64_t* total) {
 // window by an atomic max, so each window keeps its most frequent value and,
 // among equally frequent ones, the first (smallest) -- the rule a serial scan
 // of the sorted CALs applies.
-__device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, uint32_t n) {
+// keys: the read's work space (keys, then the window and run arrays); sorted:
+// its keys are already there, in order (the large-read sort), else they are
+// loaded and sorted here
+__device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, uint32_t n, bool sorted = false) {
   __shared__ uint32_t s_nw;
   const uint32_t r = a.r0 + rr;
   const uint64_t base = a.off[rr];
@@ -464,9 +467,11 @@ __device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, ui
   unsigned long long* wbest = reinterpret_cast<unsigned long long*>(keys + P);  // P per window
   uint32_t* pos_run = reinterpret_cast<uint32_t*>(keys + 2 * P);                // P + 1 run starts
   uint32_t* pos_win = pos_run + P + 1;                                          // P + 1 window starts
-  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) keys[i] = i < n ? a.cals[base + i] : kNoKey;
-  __syncthreads();
-  bitonic(keys, P);
+  if (!sorted) {
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) keys[i] = i < n ? a.cals[base + i] : kNoKey;
+    __syncthreads();
+    bitonic(keys, P);
+  }
   const uint32_t T = blockDim.x;
   const uint32_t per = (n + T - 1) / T;  // each thread a contiguous slice of the sorted CALs
   const uint32_t i0 = min(n, threadIdx.x * per), i1 = min(n, i0 + per);
@@ -736,10 +741,128 @@ __global__ void __launch_bounds__(256) k_cal_filter(FilterArgs a, uint32_t lo, u
 }
 
 // one block per large read (big[b]), keys in a global scratch from slot soff[b]
+// reads of more than kCalSmemKeys CALs, one block each, on keys the
+// large-read sort below left in order in their scratch
 __global__ void __launch_bounds__(1024) k_cal_filter_big(FilterArgs a, const uint32_t* big, const uint64_t* soff,
                                                          uint64_t* scratch) {
   const uint32_t rr = big[blockIdx.x];
-  filter_read(a, rr, scratch + soff[blockIdx.x], a.actual[rr]);
+  filter_read(a, rr, scratch + soff[blockIdx.x], a.actual[rr], true);
+}
+
+// The large-read sort: the keys of every large read (a power of two of them
+// with kNoKey padding, at least one tile) bitonic-sorted by many blocks at once.
+// A block takes one tile of kSortTile keys: stages with strides below a tile
+// run in shared memory, those of a tile or more as passes over global memory
+// (one block per tile of lower partners); each compare-exchange sorts up where
+// its lower index has bit `size` clear, the order of one whole bitonic network.
+constexpr uint32_t kSortTile = 4096;
+
+__device__ __forceinline__ uint32_t big_sort_len(const FilterArgs& a, uint32_t rr) {
+  const uint32_t P = pow2_at_least(a.actual[rr]);
+  return P > kSortTile ? P : kSortTile;
+}
+
+__global__ void k_bsort_count(FilterArgs a, const uint32_t* big, uint32_t n_big, uint32_t* tiles) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n_big) tiles[b] = big_sort_len(a, big[b]) / kSortTile;
+}
+
+// the large read (index into big) and tile of this block, from the exclusive
+// prefix tpre of the reads' tiles; false for blocks past the last tile
+__device__ __forceinline__ bool bsort_tile(const uint64_t* tpre, uint32_t n_big, uint32_t* b, uint32_t* ti) {
+  __shared__ uint32_t sb, st;
+  if (threadIdx.x == 0) {
+    const uint64_t t = blockIdx.x;
+    uint32_t lo = 0, hi = n_big;  // the last read whose first tile is <= t
+    while (lo + 1 < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (tpre[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    const bool in = t < tpre[n_big];
+    sb = in ? lo : 0xffffffffu;
+    st = in ? static_cast<uint32_t>(t - tpre[lo]) : 0u;
+  }
+  __syncthreads();
+  *b = sb;
+  *ti = st;
+  return sb != 0xffffffffu;
+}
+
+__device__ __forceinline__ void cmp_swap(uint64_t& x, uint64_t& y, bool up) {
+  if ((x > y) == up) {
+    const uint64_t t = x;
+    x = y;
+    y = t;
+  }
+}
+
+// all stages of sizes 2 .. kSortTile, each tile in shared memory, from the CALs into the scratch
+__global__ void __launch_bounds__(1024) k_bsort_local(FilterArgs a, const uint32_t* big, const uint64_t* soff,
+                                                      const uint64_t* tpre, uint32_t n_big, uint64_t* scratch) {
+  __shared__ uint64_t sk[kSortTile];
+  uint32_t b, ti;
+  if (!bsort_tile(tpre, n_big, &b, &ti)) return;
+  const uint32_t rr = big[b], n = a.actual[rr];
+  const uint64_t base = a.off[rr];
+  const uint32_t g0 = ti * kSortTile;
+  for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x)
+    sk[i] = g0 + i < n ? a.cals[base + g0 + i] : kNoKey;
+  __syncthreads();
+  for (uint32_t size = 2; size <= kSortTile; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t p = threadIdx.x; p < kSortTile / 2; p += blockDim.x) {
+        const uint32_t lo = 2 * p - (p & (stride - 1));
+        cmp_swap(sk[lo], sk[lo + stride], ((g0 + lo) & size) == 0);
+      }
+      __syncthreads();
+    }
+  }
+  uint64_t* keys = scratch + soff[b];
+  for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x) keys[g0 + i] = sk[i];
+}
+
+// one stage of size `size` and a stride of a tile or more, over global memory
+__global__ void __launch_bounds__(1024) k_bsort_global(FilterArgs a, const uint32_t* big, const uint64_t* soff,
+                                                       const uint64_t* tpre, uint32_t n_big, uint64_t* scratch,
+                                                       uint32_t size, uint32_t stride) {
+  uint32_t b, ti;
+  if (!bsort_tile(tpre, n_big, &b, &ti)) return;
+  const uint32_t g0 = ti * kSortTile;
+  if (big_sort_len(a, big[b]) < size || (g0 & stride)) return;  // sorted already, or an upper partner
+  uint64_t* keys = scratch + soff[b];
+  for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x) {
+    const uint32_t lo = g0 + i;
+    uint64_t x = keys[lo], y = keys[lo + stride];
+    const bool up = (lo & size) == 0;
+    if ((x > y) == up) {
+      keys[lo] = y;
+      keys[lo + stride] = x;
+    }
+  }
+}
+
+// the stages of size `size` with strides below a tile, each tile in shared memory
+__global__ void __launch_bounds__(1024) k_bsort_tail(FilterArgs a, const uint32_t* big, const uint64_t* soff,
+                                                     const uint64_t* tpre, uint32_t n_big, uint64_t* scratch,
+                                                     uint32_t size) {
+  __shared__ uint64_t sk[kSortTile];
+  uint32_t b, ti;
+  if (!bsort_tile(tpre, n_big, &b, &ti)) return;
+  if (big_sort_len(a, big[b]) < size) return;
+  const uint32_t g0 = ti * kSortTile;
+  uint64_t* keys = scratch + soff[b];
+  for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x) sk[i] = keys[g0 + i];
+  __syncthreads();
+  const bool up = (g0 & size) == 0;  // size > kSortTile: one direction for the whole tile
+  for (uint32_t stride = kSortTile / 2; stride > 0; stride >>= 1) {
+    for (uint32_t p = threadIdx.x; p < kSortTile / 2; p += blockDim.x) {
+      const uint32_t lo = 2 * p - (p & (stride - 1));
+      cmp_swap(sk[lo], sk[lo + stride], up);
+    }
+    __syncthreads();
+  }
+  for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x) keys[g0 + i] = sk[i];
 }
 
 __global__ void k_cal_compact(uint32_t nr, const uint64_t* off, const uint32_t* nwin, const uint32_t* woff,
@@ -820,8 +943,9 @@ int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read
 int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
                       uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint32_t* actual,
                       const uint64_t* off, uint64_t* cals, uint32_t max_small, uint32_t max_mid, const uint32_t* big,
-                      const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint32_t* nwin, uint64_t* wkey,
-                      uint32_t* whits, uint32_t* wlen, cudaStream_t st) {
+                      const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint64_t scratch_words,
+                      uint32_t max_all, uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen,
+                      cudaStream_t st) {
   if (nr == 0) return 0;
   FilterArgs a{di, read_off, r0, nr, merge_dist, pad, max_cands, count, actual, off, cals, kCalSmemKeys,
                nwin, wkey, whits, wlen};
@@ -866,6 +990,23 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
     ++launched;
   }
   if (n_big) {
+    // the large reads' keys sorted by the whole GPU, then each read's windows by one block
+    uint32_t* tiles = reinterpret_cast<uint32_t*>(scratch + scratch_words);
+    uint64_t* tpre = scratch + scratch_words + (n_big + 1) / 2 + 1;
+    uint64_t* sums = tpre + n_big + 1;
+    k_bsort_count<<<(n_big + 255) / 256, 256, 0, st>>>(a, big, n_big, tiles);
+    if (launch_scan_u64(tiles, n_big, tpre, sums, st) < 0) return -1;
+    // every large read's scratch holds 3 x (a power of two at least its sort length) words
+    const uint32_t grid = static_cast<uint32_t>(scratch_words / (3ull * kSortTile)) + 1u;
+    const uint32_t pmax = std::max(p2(max_all), kSortTile);
+    k_bsort_local<<<grid, 1024, 0, st>>>(a, big, big_soff, tpre, n_big, scratch);
+    launched += 5;
+    for (uint32_t size = 2 * kSortTile; size <= pmax; size <<= 1) {
+      for (uint32_t stride = size / 2; stride >= kSortTile; stride >>= 1, ++launched)
+        k_bsort_global<<<grid, 1024, 0, st>>>(a, big, big_soff, tpre, n_big, scratch, size, stride);
+      k_bsort_tail<<<grid, 1024, 0, st>>>(a, big, big_soff, tpre, n_big, scratch, size);
+      ++launched;
+    }
     k_cal_filter_big<<<n_big, 1024, 0, st>>>(a, big, big_soff, scratch);
     ++launched;
   }
@@ -1024,6 +1165,10 @@ int preload_cal() {
   SR_TOUCH(k_cal_seeds<true>);
   SR_TOUCH(k_cal_filter);
   SR_TOUCH(k_cal_filter_big);
+  SR_TOUCH(k_bsort_count);
+  SR_TOUCH(k_bsort_local);
+  SR_TOUCH(k_bsort_global);
+  SR_TOUCH(k_bsort_tail);
   SR_TOUCH(k_cal_filter_warp<2>);
   SR_TOUCH(k_cal_filter_warp<4>);
   SR_TOUCH(k_cal_compact);

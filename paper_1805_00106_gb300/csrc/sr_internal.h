@@ -324,12 +324,17 @@ int launch_cal_slots(const uint64_t* read_off, uint32_t n, int k, uint32_t strid
 // kCalSmallKeys CALs (largest: max_small) and up to kCalSmemKeys (largest:
 // max_mid, 0 = none) sort in shared memory; the n_big others (device list big
 // of indices into the chunk) sort in scratch from slot big_soff[b] (pow2 of
-// their count each)
+// their count each, scratch_words in all, max_all the largest count), followed
+// by cal_sort_words(n_big) words of the large-read sort's tile tables
 int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
                       uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint32_t* actual,
                       const uint64_t* off, uint64_t* cals, uint32_t max_small, uint32_t max_mid, const uint32_t* big,
-                      const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint32_t* nwin, uint64_t* wkey,
-                      uint32_t* whits, uint32_t* wlen, cudaStream_t st);
+                      const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint64_t scratch_words,
+                      uint32_t max_all, uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen,
+                      cudaStream_t st);
+// words after a filter's scratch for the large-read sort of n_big reads: their
+// tile counts (32-bit), the prefix of those and the prefix's block sums
+constexpr uint64_t cal_sort_words(uint64_t n_big) { return (n_big + 1) / 2 + 1 + (n_big + 1) + n_big / 1024 + 2; }
 // out[i] = base + woff[i] for i = 0 .. nr (a chunk's window offsets in the whole list)
 int launch_cal_offsets(const uint32_t* woff, uint32_t nr, uint64_t base, uint64_t* out, cudaStream_t st);
 // exclusive 64-bit scan of n counts into out[0..n] (out[n] = the total) with a

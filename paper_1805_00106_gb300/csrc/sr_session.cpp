@@ -1702,16 +1702,17 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
       e = cudaMemcpyAsync(&plan, d_plan, sizeof(CalPlan), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device route copy");
-      if (plan.scratch > scratch_keys) {
-        d_scratch = static_cast<uint64_t*>(cbuf(kCbScratch, plan.scratch * 8));
+      const uint64_t scratch_need = plan.scratch + (plan.n_big ? cal_sort_words(plan.n_big) : 0);
+      if (scratch_need > scratch_keys) {
+        d_scratch = static_cast<uint64_t*>(cbuf(kCbScratch, scratch_need * 8));
         if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
-        scratch_keys = plan.scratch;
+        scratch_keys = scratch_need;
       }
       if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_actual,
                            d_status, kept, st) < 0 ||
           launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_actual,
                             d_off, d_cals, std::max(plan.max_small, 1u), plan.max_mid, d_big, d_bigoff, plan.n_big,
-                            d_scratch, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
+                            d_scratch, plan.scratch, plan.max_all, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
           launch_scan_u32(d_nwin, nr, d_woff, d_wsums, st) < 0) {
         e = cudaGetLastError();
         return done(SR_ECUDA, "sr_candidates_device filter");

@@ -94,13 +94,16 @@ def test_reads_with_very_many_cals(sr, k, addr):
     rng = np.random.default_rng(11)
     unit = rng.choice(np.frombuffer(b"ACGT", np.uint8), 23)
     unit2 = rng.choice(np.frombuffer(b"ACGT", np.uint8), 31)
+    unit3 = rng.choice(np.frombuffer(b"ACGT", np.uint8), 37)
     ref = np.concatenate([rng.choice(np.frombuffer(b"ACGT", np.uint8), 2000), np.tile(unit, 900),
                           rng.choice(np.frombuffer(b"ACGT", np.uint8), 2000), np.tile(unit2, 60),
-                          rng.choice(np.frombuffer(b"ACGT", np.uint8), 500)])
+                          rng.choice(np.frombuffer(b"ACGT", np.uint8), 500), np.tile(unit3, 130),
+                          rng.choice(np.frombuffer(b"ACGT", np.uint8), 300)])
     t2 = 2000 + 23 * 900 + 2000  # start of the 60-copy repeat
+    t3 = t2 + 31 * 60 + 500  # start of the 130-copy repeat: reads of about 10k CALs (four sort tiles)
     reads, offs = [], [0]
     for st, m in [(2500, 200), (3000, 256), (100, 100), (2100, 60), (20000, 120), (t2 + 200, 150),
-                  (t2 - 40, 100)]:
+                  (t2 - 40, 100), (t3 + 400, 100), (t3 + 37 * 128, 120)]:
         reads.append(ref[st:st + m])
         offs.append(offs[-1] + m)
     bases = np.concatenate(reads)

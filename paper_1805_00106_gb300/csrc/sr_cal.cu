@@ -248,9 +248,13 @@ __global__ void __launch_bounds__(32 * kCalWarps, 12) k_cal_seeds(SeedArgs a) {
     if (!len_ok && lane == 0) atomicOr(a.status, kStBadRead);
     // the emit pass takes the count pass's lookups when they were kept for this read
     const bool kept = EMIT && a.ranges && !a.recount[r - a.rbase];
+    // emit pass: a read of more CALs than kCalSmemKeys whose lookups were kept
+    // is left to k_cal_emit_big (its bound, in count, is then its exact count)
+    const bool split = kept && a.count && a.count[rr] > kCalSmemKeys;
     uint64_t* rec = a.ranges ? a.ranges + (len_ok ? a.seed_off[r - a.rbase] : 0u) : nullptr;
     bool fits = true;
-    if (len_ok && (kept || load_codes(a.bases, o0, m, q, lane, a.status)) && m >= static_cast<uint32_t>(k)) {
+    if (!split && len_ok && (kept || load_codes(a.bases, o0, m, q, lane, a.status)) &&
+        m >= static_cast<uint32_t>(k)) {
       if (!kept) pack_codes(q, pk_s[warp], rk_s[warp], lane);
       const uint64_t base = EMIT ? a.off[rr] : 0;
       // 32 seeds per round, one per lane; the matching entries of all of them
@@ -367,7 +371,7 @@ __global__ void __launch_bounds__(32 * kCalWarps, 12) k_cal_seeds(SeedArgs a) {
         if (lane == 0) a.recount[r - a.rbase] = all_fit ? 0 : 1;
       }
     } else if (lane == 0) {
-      a.actual[rr] = ctr[warp];
+      a.actual[rr] = split ? a.count[rr] : ctr[warp];
     }
     __syncwarp();
   }
@@ -396,6 +400,29 @@ __device__ __forceinline__ uint32_t pow2_at_least(uint32_t n) {
   uint32_t p = 1;
   while (p < n) p <<= 1;
   return p;
+}
+
+// the large read (index into big) and the part of it (tile or chunk) this block
+// takes, from the exclusive prefix tpre of the reads' parts; false for blocks
+// past the last part
+__device__ __forceinline__ bool block_item(const uint64_t* tpre, uint32_t n_big, uint32_t* b, uint32_t* ti) {
+  __shared__ uint32_t sb, st;
+  if (threadIdx.x == 0) {
+    const uint64_t t = blockIdx.x;
+    uint32_t lo = 0, hi = n_big;  // the last read whose first tile is <= t
+    while (lo + 1 < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (tpre[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    const bool in = t < tpre[n_big];
+    sb = in ? lo : 0xffffffffu;
+    st = in ? static_cast<uint32_t>(t - tpre[lo]) : 0u;
+  }
+  __syncthreads();
+  *b = sb;
+  *ti = st;
+  return sb != 0xffffffffu;
 }
 
 struct FilterArgs {
@@ -767,28 +794,6 @@ __global__ void k_bsort_count(FilterArgs a, const uint32_t* big, uint32_t n_big,
   if (b < n_big) tiles[b] = big_sort_len(a, big[b]) / kSortTile;
 }
 
-// the large read (index into big) and tile of this block, from the exclusive
-// prefix tpre of the reads' tiles; false for blocks past the last tile
-__device__ __forceinline__ bool bsort_tile(const uint64_t* tpre, uint32_t n_big, uint32_t* b, uint32_t* ti) {
-  __shared__ uint32_t sb, st;
-  if (threadIdx.x == 0) {
-    const uint64_t t = blockIdx.x;
-    uint32_t lo = 0, hi = n_big;  // the last read whose first tile is <= t
-    while (lo + 1 < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (tpre[mid] <= t) lo = mid;
-      else hi = mid;
-    }
-    const bool in = t < tpre[n_big];
-    sb = in ? lo : 0xffffffffu;
-    st = in ? static_cast<uint32_t>(t - tpre[lo]) : 0u;
-  }
-  __syncthreads();
-  *b = sb;
-  *ti = st;
-  return sb != 0xffffffffu;
-}
-
 __device__ __forceinline__ void cmp_swap(uint64_t& x, uint64_t& y, bool up) {
   if ((x > y) == up) {
     const uint64_t t = x;
@@ -802,7 +807,7 @@ __global__ void __launch_bounds__(1024) k_bsort_local(FilterArgs a, const uint32
                                                       const uint64_t* tpre, uint32_t n_big, uint64_t* scratch) {
   __shared__ uint64_t sk[kSortTile];
   uint32_t b, ti;
-  if (!bsort_tile(tpre, n_big, &b, &ti)) return;
+  if (!block_item(tpre, n_big, &b, &ti)) return;
   const uint32_t rr = big[b], n = a.actual[rr];
   const uint64_t base = a.off[rr];
   const uint32_t g0 = ti * kSortTile;
@@ -827,7 +832,7 @@ __global__ void __launch_bounds__(1024) k_bsort_global(FilterArgs a, const uint3
                                                        const uint64_t* tpre, uint32_t n_big, uint64_t* scratch,
                                                        uint32_t size, uint32_t stride) {
   uint32_t b, ti;
-  if (!bsort_tile(tpre, n_big, &b, &ti)) return;
+  if (!block_item(tpre, n_big, &b, &ti)) return;
   const uint32_t g0 = ti * kSortTile;
   if (big_sort_len(a, big[b]) < size || (g0 & stride)) return;  // sorted already, or an upper partner
   uint64_t* keys = scratch + soff[b];
@@ -848,7 +853,7 @@ __global__ void __launch_bounds__(1024) k_bsort_tail(FilterArgs a, const uint32_
                                                      uint32_t size) {
   __shared__ uint64_t sk[kSortTile];
   uint32_t b, ti;
-  if (!bsort_tile(tpre, n_big, &b, &ti)) return;
+  if (!block_item(tpre, n_big, &b, &ti)) return;
   if (big_sort_len(a, big[b]) < size) return;
   const uint32_t g0 = ti * kSortTile;
   uint64_t* keys = scratch + soff[b];
@@ -922,6 +927,90 @@ int launch_cal_heads(const DevIndex& di, uint64_t nbuckets, uint4* heads, cudaSt
   if (nbuckets == 0) return 0;
   k_cal_heads<<<static_cast<unsigned>((nbuckets + 255) / 256), 256, 0, st>>>(di, nbuckets, heads);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+// Emit pass of the large reads whose lookups were kept, by many blocks per read.
+// Their count bound is exact: a matching entry gives one CAL, two (the '+' one,
+// then the '-' one) when the seed is its own reverse complement.  So a CAL's
+// slot follows from the prefix of the CAL counts of the read's records (seed x
+// reference, in order), and each block takes kEmitChunk consecutive slots of
+// one read: it scans the read's records in shared memory, finds each slot's
+// record by binary search and writes the CAL of that entry.
+constexpr uint32_t kEmitChunk = 8192;
+constexpr uint32_t kEmitRecs = static_cast<uint32_t>(kMaxReadLen) * kMaxRefs;
+
+__global__ void k_emit_count(const uint32_t* bound, const uint32_t* big, uint32_t n_big, uint32_t* chunks) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < n_big) chunks[b] = (bound[big[b]] + kEmitChunk - 1) / kEmitChunk;
+}
+
+__global__ void __launch_bounds__(512) k_cal_emit_big(SeedArgs a, const uint32_t* big, uint32_t n_big,
+                                                      const uint64_t* cpre) {
+  __shared__ uint32_t spre[kEmitRecs + 1];
+  uint32_t b, ci;
+  if (!block_item(cpre, n_big, &b, &ci)) return;
+  const uint32_t rr = big[b], r = a.r0 + rr;
+  if (a.recount[r - a.rbase]) return;  // looked up again and emitted by k_cal_seeds
+  const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - a.read_off[r]);
+  const int k = a.di.k;
+  const uint32_t nref = static_cast<uint32_t>(a.di.n_refs);
+  const uint32_t nrec = ((m - k) / a.stride + 1) * nref;  // the read has CALs, so m >= k
+  const uint64_t* rec = a.ranges + a.seed_off[r - a.rbase];
+  // exclusive prefix of the records' CAL counts
+  const uint32_t per = (nrec + blockDim.x - 1) / blockDim.x, q0 = min(nrec, threadIdx.x * per),
+                 q1 = min(nrec, q0 + per);
+  uint64_t sum = 0;
+  for (uint32_t q = q0; q < q1; ++q) {
+    const uint64_t x = rec[q];
+    sum += ((x >> 2) & kRangeCntMax) << ((x & 3u) == 3u ? 1 : 0);
+  }
+  uint64_t tot = 0;
+  uint64_t pre = block_exscan(sum, &tot);
+  for (uint32_t q = q0; q < q1; ++q) {
+    spre[q] = static_cast<uint32_t>(pre);
+    const uint64_t x = rec[q];
+    pre += ((x >> 2) & kRangeCntMax) << ((x & 3u) == 3u ? 1 : 0);
+  }
+  if (threadIdx.x == 0) spre[nrec] = static_cast<uint32_t>(tot);
+  __syncthreads();
+  const uint32_t s1 = min(static_cast<uint32_t>(tot), (ci + 1) * kEmitChunk);
+  const uint64_t base = a.off[rr];
+  for (uint32_t sl = ci * kEmitChunk + threadIdx.x; sl < s1; sl += blockDim.x) {
+    uint32_t lo = 0, hi = nrec;  // the last record whose first slot is <= sl (it has CALs)
+    while (lo + 1 < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (spre[mid] <= sl) lo = mid;
+      else hi = mid;
+    }
+    const uint64_t x = rec[lo];
+    const uint32_t rori = static_cast<uint32_t>(x & 3u), u = sl - spre[lo];
+    const bool two = rori == 3u;
+    const uint64_t e = (x >> 26) + (two ? u >> 1 : u);
+    const uint32_t si = lo / nref, r2 = lo - si * nref, so = si * a.stride;
+    const uint32_t po = a.di.packed ? a.di.posor[r2][e] : 0u;
+    const uint32_t fo = a.di.packed ? po >> 30 : a.di.orient[r2][e];
+    const int64_t p = a.di.packed ? static_cast<int64_t>(po & 0x3fffffffu) : static_cast<int64_t>(a.di.pos[r2][e]);
+    const bool plus = two ? (u & 1u) == 0u : ((fo & 1u) && (rori & 1u)) || ((fo & 2u) && (rori & 2u));
+    a.cals[base + sl] = plus ? cal_key(r2, 0, p - so) : cal_key(r2, 1, p - static_cast<int64_t>(m - so - k));
+  }
+}
+
+int launch_cal_emit_big(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t stride,
+                        const uint32_t* bound, const uint64_t* off, uint64_t* cals, const CalRanges& kept,
+                        const uint32_t* big, uint32_t n_big, uint64_t* scratch, uint64_t scratch_words,
+                        cudaStream_t st) {
+  if (nr == 0 || n_big == 0 || !kept.ranges) return 0;
+  SeedArgs a{di, nullptr, read_off, r0, nr, stride, const_cast<uint32_t*>(bound), off, cals, nullptr, nullptr,
+             kept.ranges, kept.seed_off, kept.recount, kept.rbase};
+  uint32_t* chunks = reinterpret_cast<uint32_t*>(scratch + scratch_words);
+  uint64_t* cpre = scratch + scratch_words + (n_big + 1) / 2 + 1;
+  uint64_t* sums = cpre + n_big + 1;
+  k_emit_count<<<(n_big + 255) / 256, 256, 0, st>>>(bound, big, n_big, chunks);
+  if (launch_scan_u64(chunks, n_big, cpre, sums, st) < 0) return -1;
+  // a large read's bound is at most the power of two of its scratch (3 of them per read)
+  const uint32_t grid = static_cast<uint32_t>(scratch_words / (3ull * kEmitChunk)) + n_big + 1u;
+  k_cal_emit_big<<<grid, 512, 0, st>>>(a, big, n_big, cpre);
+  return cudaPeekAtLastError() == cudaSuccess ? 5 : -1;
 }
 
 int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
@@ -1165,6 +1254,8 @@ int preload_cal() {
   SR_TOUCH(k_cal_seeds<true>);
   SR_TOUCH(k_cal_filter);
   SR_TOUCH(k_cal_filter_big);
+  SR_TOUCH(k_emit_count);
+  SR_TOUCH(k_cal_emit_big);
   SR_TOUCH(k_bsort_count);
   SR_TOUCH(k_bsort_local);
   SR_TOUCH(k_bsort_global);

@@ -313,6 +313,15 @@ constexpr int kHeadKeys = 26;
 constexpr uint32_t kHeadSpill = 0xffffffffu;
 // the bucket heads of a packed index (nbuckets buckets, n_refs <= 2) into heads
 int launch_cal_heads(const DevIndex& di, uint64_t nbuckets, uint4* heads, cudaStream_t st);
+// Emit pass of the large reads (device list big, n_big of them: over
+// kCalSmemKeys CAL bounds) whose lookups were kept, by many blocks per read,
+// after launch_cal_seeds' emit pass (given the bounds as count, it leaves those
+// reads out); its part tables take cal_sort_words(n_big) words after the
+// filter's scratch_words
+int launch_cal_emit_big(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t stride,
+                        const uint32_t* bound, const uint64_t* off, uint64_t* cals, const CalRanges& kept,
+                        const uint32_t* big, uint32_t n_big, uint64_t* scratch, uint64_t scratch_words,
+                        cudaStream_t st);
 int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read_off, uint32_t r0, uint32_t nr,
                      uint32_t stride, uint32_t* count, const uint64_t* off, uint64_t* cals, uint32_t* actual,
                      uint32_t* status, const CalRanges& kept, cudaStream_t st);

@@ -1708,8 +1708,10 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
         if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");
         scratch_keys = scratch_need;
       }
-      if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, nullptr, d_off, d_cals, d_actual,
+      if (launch_cal_seeds(s->didx, d_bases, d_roff, r0, nr, cp.seed_stride, d_count + r0, d_off, d_cals, d_actual,
                            d_status, kept, st) < 0 ||
+          launch_cal_emit_big(s->didx, d_roff, r0, nr, cp.seed_stride, d_count + r0, d_off, d_cals, kept, d_big,
+                              plan.n_big, d_scratch, plan.scratch, st) < 0 ||
           launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_actual,
                             d_off, d_cals, std::max(plan.max_small, 1u), plan.max_mid, d_big, d_bigoff, plan.n_big,
                             d_scratch, plan.scratch, plan.max_all, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||

@@ -789,9 +789,52 @@ __device__ __forceinline__ uint32_t big_sort_len(const FilterArgs& a, uint32_t r
   return P > kSortTile ? P : kSortTile;
 }
 
-__global__ void k_bsort_count(FilterArgs a, const uint32_t* big, uint32_t n_big, uint32_t* tiles) {
+// The large reads in classes of equal sort length, longest first, so that a
+// pass over the tiles of the reads at least `size` long covers a prefix of the
+// tiles: perm lists the reads (indices into big) class by class.
+constexpr int kSortLgMin = 12;    // log2 kSortTile
+constexpr int kSortClasses = 20;  // sort lengths 2^12 .. 2^31
+struct SortClasses {
+  uint32_t n;                     // classes present
+  uint32_t lg[kSortClasses];      // log2 of their sort length, decreasing
+  uint32_t read0[kSortClasses];   // position of their first read in perm
+  uint32_t count[kSortClasses];   // their reads
+  uint64_t tile0[kSortClasses];   // their first tile
+};
+
+__device__ __forceinline__ uint32_t sort_lg(const FilterArgs& a, uint32_t rr) {
+  return 31u - static_cast<uint32_t>(__clz(big_sort_len(a, rr)));
+}
+
+__global__ void k_bsort_hist(FilterArgs a, const uint32_t* big, uint32_t n_big, uint32_t* hist) {
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < n_big) tiles[b] = big_sort_len(a, big[b]) / kSortTile;
+  if (b < n_big) atomicAdd(&hist[sort_lg(a, big[b]) - kSortLgMin], 1u);
+}
+
+__global__ void k_bsort_order(FilterArgs a, const uint32_t* big, uint32_t n_big, SortClasses c, uint32_t* fill,
+                              uint32_t* perm) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_big) return;
+  const uint32_t lg = sort_lg(a, big[b]);
+  for (uint32_t ci = 0; ci < c.n; ++ci)
+    if (c.lg[ci] == lg) perm[c.read0[ci] + atomicAdd(&fill[ci], 1u)] = b;
+}
+
+// the large read (index into big) and tile of this block
+__device__ __forceinline__ bool sort_tile(const SortClasses& c, const uint32_t* perm, uint32_t* b, uint32_t* ti,
+                                          uint32_t* P) {
+  const uint64_t t = blockIdx.x;
+  for (uint32_t ci = 0; ci < c.n; ++ci) {
+    const uint32_t tpr = 1u << (c.lg[ci] - kSortLgMin);  // tiles per read
+    if (t < c.tile0[ci] + static_cast<uint64_t>(c.count[ci]) * tpr) {
+      const uint64_t x = t - c.tile0[ci];
+      *b = perm[c.read0[ci] + static_cast<uint32_t>(x >> (c.lg[ci] - kSortLgMin))];
+      *ti = static_cast<uint32_t>(x & (tpr - 1u));
+      *P = 1u << c.lg[ci];
+      return true;
+    }
+  }
+  return false;
 }
 
 __device__ __forceinline__ void cmp_swap(uint64_t& x, uint64_t& y, bool up) {
@@ -804,10 +847,10 @@ __device__ __forceinline__ void cmp_swap(uint64_t& x, uint64_t& y, bool up) {
 
 // all stages of sizes 2 .. kSortTile, each tile in shared memory, from the CALs into the scratch
 __global__ void __launch_bounds__(1024) k_bsort_local(FilterArgs a, const uint32_t* big, const uint64_t* soff,
-                                                      const uint64_t* tpre, uint32_t n_big, uint64_t* scratch) {
+                                                      SortClasses c, const uint32_t* perm, uint64_t* scratch) {
   __shared__ uint64_t sk[kSortTile];
-  uint32_t b, ti;
-  if (!block_item(tpre, n_big, &b, &ti)) return;
+  uint32_t b, ti, P;
+  if (!sort_tile(c, perm, &b, &ti, &P)) return;
   const uint32_t rr = big[b], n = a.actual[rr];
   const uint64_t base = a.off[rr];
   const uint32_t g0 = ti * kSortTile;
@@ -829,12 +872,12 @@ __global__ void __launch_bounds__(1024) k_bsort_local(FilterArgs a, const uint32
 
 // one stage of size `size` and a stride of a tile or more, over global memory
 __global__ void __launch_bounds__(1024) k_bsort_global(FilterArgs a, const uint32_t* big, const uint64_t* soff,
-                                                       const uint64_t* tpre, uint32_t n_big, uint64_t* scratch,
+                                                       SortClasses c, const uint32_t* perm, uint64_t* scratch,
                                                        uint32_t size, uint32_t stride) {
-  uint32_t b, ti;
-  if (!block_item(tpre, n_big, &b, &ti)) return;
+  uint32_t b, ti, P;
+  if (!sort_tile(c, perm, &b, &ti, &P)) return;
   const uint32_t g0 = ti * kSortTile;
-  if (big_sort_len(a, big[b]) < size || (g0 & stride)) return;  // sorted already, or an upper partner
+  if (P < size || (g0 & stride)) return;  // sorted already, or an upper partner
   uint64_t* keys = scratch + soff[b];
   for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x) {
     const uint32_t lo = g0 + i;
@@ -849,12 +892,12 @@ __global__ void __launch_bounds__(1024) k_bsort_global(FilterArgs a, const uint3
 
 // the stages of size `size` with strides below a tile, each tile in shared memory
 __global__ void __launch_bounds__(1024) k_bsort_tail(FilterArgs a, const uint32_t* big, const uint64_t* soff,
-                                                     const uint64_t* tpre, uint32_t n_big, uint64_t* scratch,
+                                                     SortClasses c, const uint32_t* perm, uint64_t* scratch,
                                                      uint32_t size) {
   __shared__ uint64_t sk[kSortTile];
-  uint32_t b, ti;
-  if (!block_item(tpre, n_big, &b, &ti)) return;
-  if (big_sort_len(a, big[b]) < size) return;
+  uint32_t b, ti, P;
+  if (!sort_tile(c, perm, &b, &ti, &P)) return;
+  if (P < size) return;
   const uint32_t g0 = ti * kSortTile;
   uint64_t* keys = scratch + soff[b];
   for (uint32_t i = threadIdx.x; i < kSortTile; i += blockDim.x) sk[i] = keys[g0 + i];
@@ -1079,21 +1122,47 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
     ++launched;
   }
   if (n_big) {
-    // the large reads' keys sorted by the whole GPU, then each read's windows by one block
-    uint32_t* tiles = reinterpret_cast<uint32_t*>(scratch + scratch_words);
-    uint64_t* tpre = scratch + scratch_words + (n_big + 1) / 2 + 1;
-    uint64_t* sums = tpre + n_big + 1;
-    k_bsort_count<<<(n_big + 255) / 256, 256, 0, st>>>(a, big, n_big, tiles);
-    if (launch_scan_u64(tiles, n_big, tpre, sums, st) < 0) return -1;
-    // every large read's scratch holds 3 x (a power of two at least its sort length) words
-    const uint32_t grid = static_cast<uint32_t>(scratch_words / (3ull * kSortTile)) + 1u;
-    const uint32_t pmax = std::max(p2(max_all), kSortTile);
-    k_bsort_local<<<grid, 1024, 0, st>>>(a, big, big_soff, tpre, n_big, scratch);
-    launched += 5;
-    for (uint32_t size = 2 * kSortTile; size <= pmax; size <<= 1) {
+    // the large reads' keys sorted by the whole GPU, then each read's windows by
+    // one block; the reads' classes of sort length come back to the host, which
+    // sizes each pass to the tiles of the reads it still has to sort
+    uint32_t* hist = reinterpret_cast<uint32_t*>(scratch + scratch_words);
+    uint32_t* fill = hist + kSortClasses;
+    uint32_t* perm = fill + kSortClasses;
+    uint32_t h[kSortClasses] = {};
+    if (cudaMemsetAsync(hist, 0, 2 * kSortClasses * sizeof(uint32_t), st) != cudaSuccess) return -1;
+    k_bsort_hist<<<(n_big + 255) / 256, 256, 0, st>>>(a, big, n_big, hist);
+    if (cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return -1;
+    SortClasses c{};
+    uint32_t rank = 0;
+    uint64_t tiles = 0;
+    for (int lg = kSortLgMin + kSortClasses - 1; lg >= kSortLgMin; --lg) {
+      const uint32_t cnt = h[lg - kSortLgMin];
+      if (!cnt) continue;
+      c.lg[c.n] = static_cast<uint32_t>(lg);
+      c.read0[c.n] = rank;
+      c.count[c.n] = cnt;
+      c.tile0[c.n] = tiles;
+      ++c.n;
+      rank += cnt;
+      tiles += static_cast<uint64_t>(cnt) << (lg - kSortLgMin);
+    }
+    // tiles of the reads at least `size` long: a prefix
+    auto tiles_ge = [&](uint32_t size) {
+      for (uint32_t ci = 0; ci < c.n; ++ci)
+        if ((1ull << c.lg[ci]) < size) return c.tile0[ci];
+      return tiles;
+    };
+    k_bsort_order<<<(n_big + 255) / 256, 256, 0, st>>>(a, big, n_big, c, fill, perm);
+    k_bsort_local<<<static_cast<uint32_t>(tiles), 1024, 0, st>>>(a, big, big_soff, c, perm, scratch);
+    launched += 3;
+    const uint32_t pmax = c.n ? 1u << c.lg[0] : kSortTile;
+    for (uint32_t size = 2 * kSortTile; size <= pmax && size != 0; size <<= 1) {
+      const uint32_t grid = static_cast<uint32_t>(tiles_ge(size));
       for (uint32_t stride = size / 2; stride >= kSortTile; stride >>= 1, ++launched)
-        k_bsort_global<<<grid, 1024, 0, st>>>(a, big, big_soff, tpre, n_big, scratch, size, stride);
-      k_bsort_tail<<<grid, 1024, 0, st>>>(a, big, big_soff, tpre, n_big, scratch, size);
+        k_bsort_global<<<grid, 1024, 0, st>>>(a, big, big_soff, c, perm, scratch, size, stride);
+      k_bsort_tail<<<grid, 1024, 0, st>>>(a, big, big_soff, c, perm, scratch, size);
       ++launched;
     }
     k_cal_filter_big<<<n_big, 1024, 0, st>>>(a, big, big_soff, scratch);
@@ -1256,7 +1325,8 @@ int preload_cal() {
   SR_TOUCH(k_cal_filter_big);
   SR_TOUCH(k_emit_count);
   SR_TOUCH(k_cal_emit_big);
-  SR_TOUCH(k_bsort_count);
+  SR_TOUCH(k_bsort_hist);
+  SR_TOUCH(k_bsort_order);
   SR_TOUCH(k_bsort_local);
   SR_TOUCH(k_bsort_global);
   SR_TOUCH(k_bsort_tail);

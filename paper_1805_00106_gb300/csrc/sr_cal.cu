@@ -482,23 +482,20 @@ __device__ uint64_t block_exscan(uint64_t v, uint64_t* total) {
 // window by an atomic max, so each window keeps its most frequent value and,
 // among equally frequent ones, the first (smallest) -- the rule a serial scan
 // of the sorted CALs applies.
-// keys: the read's work space (keys, then the window and run arrays); sorted:
-// its keys are already there, in order (the large-read sort), else they are
-// loaded and sorted here
-__device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, uint32_t n, bool sorted = false) {
+__device__ void filter_finish(const FilterArgs& a, uint32_t rr, uint64_t* keys, uint32_t nw);
+__device__ __forceinline__ void window_clamp(const FilterArgs& a, uint64_t base, uint32_t m, uint32_t i);
+
+// keys: the read's work space (keys, then the window and run arrays)
+__device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, uint32_t n) {
   __shared__ uint32_t s_nw;
-  const uint32_t r = a.r0 + rr;
   const uint64_t base = a.off[rr];
-  const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - a.read_off[r]);
   const uint32_t P = pow2_at_least(n);
   unsigned long long* wbest = reinterpret_cast<unsigned long long*>(keys + P);  // P per window
   uint32_t* pos_run = reinterpret_cast<uint32_t*>(keys + 2 * P);                // P + 1 run starts
   uint32_t* pos_win = pos_run + P + 1;                                          // P + 1 window starts
-  if (!sorted) {
-    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) keys[i] = i < n ? a.cals[base + i] : kNoKey;
-    __syncthreads();
-    bitonic(keys, P);
-  }
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) keys[i] = i < n ? a.cals[base + i] : kNoKey;
+  __syncthreads();
+  bitonic(keys, P);
   const uint32_t T = blockDim.x;
   const uint32_t per = (n + T - 1) / T;  // each thread a contiguous slice of the sorted CALs
   const uint32_t i0 = min(n, threadIdx.x * per), i1 = min(n, i0 + per);
@@ -559,7 +556,16 @@ __device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, ui
   }
   if (threadIdx.x == 0) s_nw = nwin;
   __syncthreads();
-  uint32_t nw = s_nw;
+  filter_finish(a, rr, keys, s_nw);
+}
+
+// the end of a read's filter once its nw windows have their key and hits: the
+// max_cands cut (keys: work space of at least the power of two of nw), the
+// window clamping and the window count
+__device__ void filter_finish(const FilterArgs& a, uint32_t rr, uint64_t* keys, uint32_t nw) {
+  const uint32_t r = a.r0 + rr;
+  const uint64_t base = a.off[rr];
+  const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - a.read_off[r]);
   if (a.max_cands && nw > a.max_cands) {
     // keep the max_cands windows with most hits (ties: smaller key), in key order
     const uint32_t P2 = pow2_at_least(nw);
@@ -581,21 +587,23 @@ __device__ void filter_read(const FilterArgs& a, uint32_t rr, uint64_t* keys, ui
     nw = a.max_cands;
     __syncthreads();
   }
-  // window [cal - pad, cal + m + pad) clamped to the reference
-  for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) {
-    const uint64_t key = a.wkey[base + i];
-    const uint32_t ref = static_cast<uint32_t>(key >> 60);
-    const int64_t cal = static_cast<int64_t>(key & kCalMask) - static_cast<int64_t>(kCalBias);
-    const int64_t N = static_cast<int64_t>(a.di.ref_len[ref]);
-    int64_t lo = cal - static_cast<int64_t>(a.pad), hi = cal + m + static_cast<int64_t>(a.pad);
-    if (lo < 0) lo = 0;
-    if (hi > N) hi = N;
-    a.wlen[base + i] = static_cast<uint32_t>(hi - lo);
-    // the key's ref and strand bits stay for the compaction; the start replaces the CAL
-    a.wkey[base + i] = (key & ~kCalMask) | static_cast<uint64_t>(lo);
-  }
+  for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) window_clamp(a, base, m, i);
   if (threadIdx.x == 0) a.nwin[rr] = nw;
   __syncthreads();
+}
+
+// window i of the read at base: [cal - pad, cal + m + pad) clamped to the reference
+__device__ __forceinline__ void window_clamp(const FilterArgs& a, uint64_t base, uint32_t m, uint32_t i) {
+  const uint64_t key = a.wkey[base + i];
+  const uint32_t ref = static_cast<uint32_t>(key >> 60);
+  const int64_t cal = static_cast<int64_t>(key & kCalMask) - static_cast<int64_t>(kCalBias);
+  const int64_t N = static_cast<int64_t>(a.di.ref_len[ref]);
+  int64_t lo = cal - static_cast<int64_t>(a.pad), hi = cal + m + static_cast<int64_t>(a.pad);
+  if (lo < 0) lo = 0;
+  if (hi > N) hi = N;
+  a.wlen[base + i] = static_cast<uint32_t>(hi - lo);
+  // the key's ref and strand bits stay for the compaction; the start replaces the CAL
+  a.wkey[base + i] = (key & ~kCalMask) | static_cast<uint64_t>(lo);
 }
 
 // The same filter for a read of at most 32 E CALs on one warp, without block
@@ -768,12 +776,15 @@ __global__ void __launch_bounds__(256) k_cal_filter(FilterArgs a, uint32_t lo, u
 }
 
 // one block per large read (big[b]), keys in a global scratch from slot soff[b]
-// reads of more than kCalSmemKeys CALs, one block each, on keys the
-// large-read sort below left in order in their scratch
+// reads of more than kCalSmemKeys CALs, one block each, once the large-read
+// merge below has given them their windows: the max_cands cut where it applies
+// (the merge has clamped the windows of the others)
 __global__ void __launch_bounds__(1024) k_cal_filter_big(FilterArgs a, const uint32_t* big, const uint64_t* soff,
                                                          uint64_t* scratch) {
   const uint32_t rr = big[blockIdx.x];
-  filter_read(a, rr, scratch + soff[blockIdx.x], a.actual[rr], true);
+  const uint32_t nw = a.nwin[rr];
+  if (!(a.max_cands && nw > a.max_cands)) return;
+  filter_finish(a, rr, scratch + soff[blockIdx.x], nw);
 }
 
 // The large-read sort: the keys of every large read (a power of two of them
@@ -782,7 +793,7 @@ __global__ void __launch_bounds__(1024) k_cal_filter_big(FilterArgs a, const uin
 // run in shared memory, those of a tile or more as passes over global memory
 // (one block per tile of lower partners); each compare-exchange sorts up where
 // its lower index has bit `size` clear, the order of one whole bitonic network.
-constexpr uint32_t kSortTile = 4096;
+constexpr uint32_t kSortTile = kCalSortTile;
 
 __device__ __forceinline__ uint32_t big_sort_len(const FilterArgs& a, uint32_t rr) {
   const uint32_t P = pow2_at_least(a.actual[rr]);
@@ -1072,6 +1083,127 @@ int launch_cal_seeds(const DevIndex& di, const char* bases, const uint64_t* read
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+// The large-read merge, over the sorted keys by the same tiles: run starts (the
+// value changes) and window starts ((reference, strand) changes, or a gap over
+// merge_dist) are counted per tile, numbered by scans over the tiles, and each
+// run offers (its length, its position in its window) to its window by an
+// atomic max: the rule of filter_read, by many blocks.  The layout of a read's
+// work space is filter_read's (keys, window bests, run starts, window starts).
+struct MergeTabs {
+  uint32_t *trs, *tws;  // run and window starts per tile
+  uint64_t *prs, *pws;  // their exclusive prefixes over all tiles (tiles + 1 entries)
+};
+
+// this thread's four keys g0 + 4 t .. + 3 (those below n): run and window start bits
+__device__ __forceinline__ uint32_t merge_flags(const uint64_t* K, uint32_t g0, uint32_t n, uint64_t md) {
+  uint32_t f = 0;
+  const uint32_t i0 = g0 + 4 * threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const uint32_t i = i0 + u;
+    if (i >= n) break;
+    if (i == 0) {
+      f |= 3u << (2 * u);
+      continue;
+    }
+    const uint64_t k = K[i], p = K[i - 1];
+    f |= ((k != p ? 1u : 0u) | (((k >> 59) != (p >> 59) || k - p > md) ? 2u : 0u)) << (2 * u);
+  }
+  return f;
+}
+
+__device__ __forceinline__ uint64_t merge_counts(uint32_t f) {
+  uint64_t c = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) c += (static_cast<uint64_t>((f >> (2 * u + 1)) & 1u) << 32) | ((f >> (2 * u)) & 1u);
+  return c;
+}
+
+__global__ void __launch_bounds__(1024) k_bmerge_count(FilterArgs a, const uint32_t* big, const uint64_t* soff,
+                                                       SortClasses c, const uint32_t* perm, uint64_t* scratch,
+                                                       MergeTabs t) {
+  uint32_t b, ti, P;
+  if (!sort_tile(c, perm, &b, &ti, &P)) return;
+  const uint32_t rr = big[b];
+  const uint32_t f = merge_flags(scratch + soff[b], ti * kSortTile, a.actual[rr], a.merge_dist);
+  uint64_t tot = 0;
+  block_exscan(merge_counts(f), &tot);
+  if (threadIdx.x == 0) {
+    t.trs[blockIdx.x] = static_cast<uint32_t>(tot);
+    t.tws[blockIdx.x] = static_cast<uint32_t>(tot >> 32);
+  }
+}
+
+// PASS 0: run and window starts written (window bests cleared), the read's
+// ends and window count by its last tile; PASS 1: each run's offer to its window
+template <int PASS>
+__global__ void __launch_bounds__(1024) k_bmerge_pos(FilterArgs a, const uint32_t* big, const uint64_t* soff,
+                                                     SortClasses c, const uint32_t* perm, uint64_t* scratch,
+                                                     MergeTabs t) {
+  uint32_t b, ti, P;
+  if (!sort_tile(c, perm, &b, &ti, &P)) return;
+  const uint32_t rr = big[b], n = a.actual[rr];
+  uint64_t* K = scratch + soff[b];
+  unsigned long long* wbest = reinterpret_cast<unsigned long long*>(K + P);
+  uint32_t* pos_run = reinterpret_cast<uint32_t*>(K + 2 * P);
+  uint32_t* pos_win = pos_run + P + 1;
+  const uint32_t g0 = ti * kSortTile, t0 = blockIdx.x - ti;  // the read's tiles are consecutive
+  const uint32_t f = merge_flags(K, g0, n, a.merge_dist);
+  uint64_t tot = 0;
+  const uint64_t pre = block_exscan(merge_counts(f), &tot);
+  uint32_t rk = static_cast<uint32_t>(t.prs[blockIdx.x] - t.prs[t0]) + static_cast<uint32_t>(pre);
+  uint32_t wk = static_cast<uint32_t>(t.pws[blockIdx.x] - t.pws[t0]) + static_cast<uint32_t>(pre >> 32);
+  const uint32_t i0 = g0 + 4 * threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const bool rs = (f >> (2 * u)) & 1u, ws = (f >> (2 * u + 1)) & 1u;
+    const uint32_t i = i0 + u;
+    if (PASS == 0) {
+      if (rs) pos_run[rk++] = i;
+      if (ws) {
+        wbest[wk] = 0ull;
+        pos_win[wk++] = i;
+      }
+    } else {
+      wk += ws ? 1u : 0u;
+      if (rs) {
+        const uint32_t w = wk - 1;  // the window holding this run
+        const uint32_t len = pos_run[rk + 1] - i, at = i - pos_win[w];
+        atomicMax(&wbest[w], (static_cast<unsigned long long>(len) << 32) | (0xffffffffu - at));
+        ++rk;
+      }
+    }
+  }
+  if (PASS == 0 && threadIdx.x == 0 && ti == (P / kSortTile) - 1) {
+    const uint32_t te = t0 + P / kSortTile;
+    const uint32_t nruns = static_cast<uint32_t>(t.prs[te] - t.prs[t0]), nwin = static_cast<uint32_t>(t.pws[te] - t.pws[t0]);
+    pos_run[nruns] = n;
+    pos_win[nwin] = n;
+    a.nwin[rr] = nwin;
+  }
+}
+
+// each window's key (its most frequent CAL, the first of equally frequent) and
+// hits; clamped here unless the max_cands cut (k_cal_filter_big) still applies
+__global__ void __launch_bounds__(1024) k_bmerge_out(FilterArgs a, const uint32_t* big, const uint64_t* soff,
+                                                     SortClasses c, const uint32_t* perm, uint64_t* scratch) {
+  uint32_t b, ti, P;
+  if (!sort_tile(c, perm, &b, &ti, &P)) return;
+  const uint32_t rr = big[b], r = a.r0 + rr, nwin = a.nwin[rr];
+  const uint64_t* K = scratch + soff[b];
+  const unsigned long long* wbest = reinterpret_cast<const unsigned long long*>(K + P);
+  const uint32_t* pos_win = reinterpret_cast<const uint32_t*>(K + 2 * P) + P + 1;
+  const uint64_t base = a.off[rr];
+  const uint32_t m = static_cast<uint32_t>(a.read_off[r + 1] - a.read_off[r]);
+  const bool cut = a.max_cands && nwin > a.max_cands;
+  for (uint32_t j = ti * kSortTile + threadIdx.x; j < min(nwin, (ti + 1) * kSortTile); j += blockDim.x) {
+    const uint32_t at = 0xffffffffu - static_cast<uint32_t>(wbest[j] & 0xffffffffull);
+    a.wkey[base + j] = K[pos_win[j] + at];
+    a.whits[base + j] = pos_win[j + 1] - pos_win[j];
+    if (!cut) window_clamp(a, base, m, j);
+  }
+}
+
 int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
                       uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint32_t* actual,
                       const uint64_t* off, uint64_t* cals, uint32_t max_small, uint32_t max_mid, const uint32_t* big,
@@ -1165,8 +1297,20 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
       k_bsort_tail<<<grid, 1024, 0, st>>>(a, big, big_soff, c, perm, scratch, size);
       ++launched;
     }
+    // the merge by the same tiles, then the max_cands cut, one block per read that needs it
+    const uint32_t nt = static_cast<uint32_t>(tiles);
+    uint64_t* mt = scratch + scratch_words + kSortClasses + (n_big + 1) / 2 + 1;
+    MergeTabs t{reinterpret_cast<uint32_t*>(mt), reinterpret_cast<uint32_t*>(mt) + nt, mt + nt + 1, nullptr};
+    t.pws = t.prs + nt + 1;
+    uint64_t* sums = t.pws + nt + 1;
+    k_bmerge_count<<<nt, 1024, 0, st>>>(a, big, big_soff, c, perm, scratch, t);
+    if (launch_scan_u64(t.trs, nt, t.prs, sums, st) < 0 || launch_scan_u64(t.tws, nt, t.pws, sums, st) < 0)
+      return -1;
+    k_bmerge_pos<0><<<nt, 1024, 0, st>>>(a, big, big_soff, c, perm, scratch, t);
+    k_bmerge_pos<1><<<nt, 1024, 0, st>>>(a, big, big_soff, c, perm, scratch, t);
+    k_bmerge_out<<<nt, 1024, 0, st>>>(a, big, big_soff, c, perm, scratch);
     k_cal_filter_big<<<n_big, 1024, 0, st>>>(a, big, big_soff, scratch);
-    ++launched;
+    launched += 11;
   }
   return cudaPeekAtLastError() == cudaSuccess ? launched : -1;
 }
@@ -1325,6 +1469,10 @@ int preload_cal() {
   SR_TOUCH(k_cal_filter_big);
   SR_TOUCH(k_emit_count);
   SR_TOUCH(k_cal_emit_big);
+  SR_TOUCH(k_bmerge_count);
+  SR_TOUCH(k_bmerge_pos<0>);
+  SR_TOUCH(k_bmerge_pos<1>);
+  SR_TOUCH(k_bmerge_out);
   SR_TOUCH(k_bsort_hist);
   SR_TOUCH(k_bsort_order);
   SR_TOUCH(k_bsort_local);

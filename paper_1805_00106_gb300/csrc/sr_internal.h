@@ -341,11 +341,18 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
                       const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint64_t scratch_words,
                       uint32_t max_all, uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen,
                       cudaStream_t st);
-// words after a filter's scratch for the tables of the large-read emit (the
-// reads' chunk counts, their prefix and its block sums) and, later, of the
-// large-read sort (class counts and fills, the reads in class order)
-constexpr uint64_t cal_sort_words(uint64_t n_big) {
-  return (n_big + 1) / 2 + 1 + (n_big + 1) + n_big / 1024 + 2 + 24;
+// keys per tile of the large-read sort and merge
+constexpr uint32_t kCalSortTile = 4096;
+// words after a filter's scratch (scratch_words) for the tables of the
+// large-read emit (the reads' chunk counts, their prefix and its block sums)
+// and, later, of the large-read sort and merge (class counts and fills, the
+// reads in class order; run and window starts per tile, their prefixes and
+// block sums, for at most scratch_words / (3 kCalSortTile) + 1 tiles)
+constexpr uint64_t cal_sort_words(uint64_t n_big, uint64_t scratch_words) {
+  const uint64_t nt = scratch_words / (3ull * kCalSortTile) + 1;
+  const uint64_t emit = (n_big + 1) / 2 + 1 + (n_big + 1) + n_big / 1024 + 2;
+  const uint64_t merge = 20 + (n_big + 1) / 2 + 1 + nt + 2 * (nt + 1) + nt / 1024 + 2;
+  return (emit > merge ? emit : merge) + 8;
 }
 // out[i] = base + woff[i] for i = 0 .. nr (a chunk's window offsets in the whole list)
 int launch_cal_offsets(const uint32_t* woff, uint32_t nr, uint64_t base, uint64_t* out, cudaStream_t st);

@@ -1702,7 +1702,7 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
       e = cudaMemcpyAsync(&plan, d_plan, sizeof(CalPlan), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return done(SR_ECUDA, "sr_candidates_device route copy");
-      const uint64_t scratch_need = plan.scratch + (plan.n_big ? cal_sort_words(plan.n_big) : 0);
+      const uint64_t scratch_need = plan.scratch + (plan.n_big ? cal_sort_words(plan.n_big, plan.scratch) : 0);
       if (scratch_need > scratch_keys) {
         d_scratch = static_cast<uint64_t*>(cbuf(kCbScratch, scratch_need * 8));
         if (e != cudaSuccess) return done(SR_ENOMEM, "sr_candidates_device: device allocation failed");

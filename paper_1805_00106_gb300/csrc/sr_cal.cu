@@ -3,19 +3,22 @@
 // them on the host, Sec. 4.1-4.2).  Same windows, in the same order, as the host
 // stage sr_candidates.
 //
-//   count / emit  one warp per read: the read's 2-bit codes in shared memory,
-//                 each lane takes seeds o = lane*stride, (lane+32)*stride, ...;
-//                 per reference the hashed canonical seed picks a bucket of the
-//                 pointer table, a binary search finds its key among the
-//                 bucket's (key, position)-sorted entries, and every matching
-//                 entry gives a '+' and/or '-' CAL by its orientation bits.
-//                 CALs are packed keys ref << 60 | strand << 59 | (cal + 1024).
-//   filter        one block per read: bitonic sort of its CAL keys (shared
-//                 memory, or global scratch for very large reads), then the
-//                 merge of consecutive CALs <= merge_dist apart into windows
-//                 represented by their most frequent CAL (smallest on ties),
-//                 the max_cands cut by hit count, and the clamped window
-//                 [cal - pad, cal + m + pad).
+//   count / emit  one warp per read: the read's 2-bit codes packed in shared
+//                 memory (with its reverse complement), each lane takes seeds
+//                 o = lane*stride, (lane+32)*stride, ...; per reference the
+//                 hashed canonical seed picks a bucket, its key is found among
+//                 the bucket's (key, position)-sorted entries (or, with bucket
+//                 heads, in the bucket's 64-byte head), and every matching entry
+//                 gives a '+' and/or '-' CAL by its orientation bits.  The count
+//                 pass keeps each lookup for the emit pass.  CALs are packed keys
+//                 ref << 60 | strand << 59 | (cal + 1024).
+//   filter        per read: a sort of its CAL keys, then the merge of
+//                 consecutive CALs <= merge_dist apart into windows represented
+//                 by their most frequent CAL (smallest on ties), the max_cands
+//                 cut by hit count, and the clamped window [cal - pad, cal + m +
+//                 pad).  One warp per read up to 128 CALs, one block up to 8192
+//                 (shared memory); larger reads are emitted, sorted and merged by
+//                 many blocks each, in tiles of 4096 keys.
 //   compact       per-read windows to contiguous arrays.
 #include <cuda_runtime.h>
 #include <stdint.h>

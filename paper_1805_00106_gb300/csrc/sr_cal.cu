@@ -1211,8 +1211,7 @@ int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0,
                       uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint32_t* actual,
                       const uint64_t* off, uint64_t* cals, uint32_t max_small, uint32_t max_mid, const uint32_t* big,
                       const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint64_t scratch_words,
-                      uint32_t max_all, uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen,
-                      cudaStream_t st) {
+                      uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen, cudaStream_t st) {
   if (nr == 0) return 0;
   FilterArgs a{di, read_off, r0, nr, merge_dist, pad, max_cands, count, actual, off, cals, kCalSmemKeys,
                nwin, wkey, whits, wlen};

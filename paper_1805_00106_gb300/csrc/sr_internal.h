@@ -333,14 +333,13 @@ int launch_cal_slots(const uint64_t* read_off, uint32_t n, int k, uint32_t strid
 // kCalSmallKeys CALs (largest: max_small) and up to kCalSmemKeys (largest:
 // max_mid, 0 = none) sort in shared memory; the n_big others (device list big
 // of indices into the chunk) sort in scratch from slot big_soff[b] (pow2 of
-// their count each, scratch_words in all, max_all the largest count), followed
-// by cal_sort_words(n_big) words of the large-read sort's tile tables
+// their count each, scratch_words in all), followed by
+// cal_sort_words(n_big, scratch_words) words of the large-read tables
 int launch_cal_filter(const DevIndex& di, const uint64_t* read_off, uint32_t r0, uint32_t nr, uint32_t merge_dist,
                       uint32_t pad, uint32_t max_cands, const uint32_t* count, const uint32_t* actual,
                       const uint64_t* off, uint64_t* cals, uint32_t max_small, uint32_t max_mid, const uint32_t* big,
                       const uint64_t* big_soff, uint32_t n_big, uint64_t* scratch, uint64_t scratch_words,
-                      uint32_t max_all, uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen,
-                      cudaStream_t st);
+                      uint32_t* nwin, uint64_t* wkey, uint32_t* whits, uint32_t* wlen, cudaStream_t st);
 // keys per tile of the large-read sort and merge
 constexpr uint32_t kCalSortTile = 4096;
 // words after a filter's scratch (scratch_words) for the tables of the

@@ -1714,7 +1714,7 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
                               plan.n_big, d_scratch, plan.scratch, st) < 0 ||
           launch_cal_filter(s->didx, d_roff, r0, nr, cp.merge_dist, cp.pad, cp.max_cands, d_count + r0, d_actual,
                             d_off, d_cals, std::max(plan.max_small, 1u), plan.max_mid, d_big, d_bigoff, plan.n_big,
-                            d_scratch, plan.scratch, plan.max_all, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
+                            d_scratch, plan.scratch, d_nwin, d_wkey, d_whits, d_wlen, st) < 0 ||
           launch_scan_u32(d_nwin, nr, d_woff, d_wsums, st) < 0) {
         e = cudaGetLastError();
         return done(SR_ECUDA, "sr_candidates_device filter");

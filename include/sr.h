@@ -229,16 +229,17 @@ void sr_session_close(sr_session* s);
  * Sec. 4.1-4.2; here the index lives in HBM next to the references).
  * sr_session_attach_index uploads idx[r], the index of the session's reference
  * r (same length; all with one seed_len and address_bases), once; replacing an
- * attached set is allowed.  When the indexes share one hash_seed, each has
- * under 2^32 entries and at most 2^30 bases, and 2 * (seed_len -
- * address_bases) <= 16, the device copy is packed (bucket starts of all
- * references interleaved in 32 bits, 16-bit keys, position and orientation in
- * one word: 6 bytes per entry and 4 per bucket); otherwise each reference's
- * tables are copied as they are (9 bytes per entry and 8 per bucket).  A packed
- * copy of one or two references with at most 2^26 buckets and at most 13
- * entries per bucket on average also gets 64-byte bucket heads (both
- * references' starts and counts and up to 26 keys, built on the device; left
- * out if they cannot be allocated, or with SR_CAL_HEADS=0 in the environment).
+ * attached set is allowed.  When the indexes share one hash_seed and each has
+ * under 2^32 entries and at most 2^30 bases, the device copy is packed (bucket
+ * starts of all references interleaved in 32 bits, keys in 16 bits when 2 *
+ * (seed_len - address_bases) <= 16 and in 32 bits otherwise, position and
+ * orientation in one word: 6 or 8 bytes per entry and 4 per bucket); otherwise
+ * each reference's tables are copied as they are (9 bytes per entry and 8 per
+ * bucket).  A packed copy of one or two references with at most 2^26 buckets and
+ * at most 13 (16-bit keys) or 8 (32-bit keys) entries per bucket on average also
+ * gets 64-byte bucket heads (both references' starts and counts and up to 26 or
+ * 13 keys, built on the device; left out if they cannot be allocated, or with
+ * SR_CAL_HEADS=0 in the environment).
  * sr_candidates_device then returns exactly the list
  * sr_candidates returns for those indexes (same windows, order and hits): one
  * warp per read looks up its seeds, one block per read sorts and merges its

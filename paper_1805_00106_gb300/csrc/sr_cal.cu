@@ -53,11 +53,10 @@ __device__ __forceinline__ uint32_t code_of(char ch) {
   }
 }
 
-// packed index: entries [lo, hi) of reference r with key `key` in bucket b
-__device__ __forceinline__ void lookup_packed(const DevIndex& di, uint64_t b, uint32_t key, int r, uint64_t* lo,
-                                              uint64_t* hi) {
-  const uint64_t s0 = di.jptr[b * di.n_refs + r], s1 = di.jptr[(b + 1) * di.n_refs + r];
-  const uint16_t* K = di.key16[r];
+// entries [l, e) of the sorted keys K[s0 .. s1) equal to key
+template <typename KT>
+__device__ __forceinline__ void key_range(const KT* K, uint64_t s0, uint64_t s1, uint32_t key, uint64_t* lo,
+                                          uint64_t* hi) {
   uint64_t l = s0, u = s1;
   while (l < u) {
     const uint64_t mid = l + ((u - l) >> 1);
@@ -70,15 +69,43 @@ __device__ __forceinline__ void lookup_packed(const DevIndex& di, uint64_t b, ui
   *hi = e;
 }
 
+// packed index: entries [lo, hi) of reference r with key `key` in bucket b
+// (16-bit keys in key16, 32-bit ones in key)
+__device__ __forceinline__ void lookup_packed(const DevIndex& di, uint64_t b, uint32_t key, int r, uint64_t* lo,
+                                              uint64_t* hi) {
+  const uint64_t s0 = di.jptr[b * di.n_refs + r], s1 = di.jptr[(b + 1) * di.n_refs + r];
+  if (di.key_bits == 16) key_range(di.key16[r], s0, s1, key, lo, hi);
+  else key_range(di.key[r], s0, s1, key, lo, hi);
+}
+
+// 32-bit keys: the head holds up to kHeadKeys32, one per word
+__device__ __forceinline__ bool head_range32(const uint4 v0, const uint4 v1, const uint4 v2, const uint4 v3,
+                                             uint32_t key, uint32_t* lo0, uint32_t* hi0, uint32_t* lo1,
+                                             uint32_t* hi1) {
+  const uint32_t w[13] = {v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w, v3.x, v3.y, v3.z, v3.w};
+  uint32_t eq = 0;
+#pragma unroll
+  for (int j = 0; j < 13; ++j) eq |= (w[j] == key ? 1u : 0u) << j;
+  const uint32_t n0 = v0.z & 0xffffu, n1 = v0.z >> 16;
+  const uint32_t m0 = (1u << n0) - 1u, m1 = ((1u << (n0 + n1)) - 1u) & ~m0;
+  const uint32_t e0 = eq & m0, e1 = eq & m1;
+  *lo0 = v0.x + (e0 ? __ffs(e0) - 1u : 0u);
+  *hi0 = *lo0 + __popc(e0);
+  *lo1 = v0.y + (e1 ? __ffs(e1) - 1u - n0 : 0u);
+  *hi1 = *lo1 + __popc(e1);
+  return true;
+}
+
 // packed index with bucket heads: entries [lo0, hi0) of reference 0 and [lo1,
 // hi1) of reference 1 with key `key` in bucket b, from the bucket's head alone
 // (an empty range may start anywhere); false when the bucket spilled (its
 // entries are then looked up in jptr / key16)
-__device__ __forceinline__ bool lookup_head(const uint4* heads, uint64_t b, uint32_t key, uint32_t* lo0,
-                                            uint32_t* hi0, uint32_t* lo1, uint32_t* hi1) {
+__device__ __forceinline__ bool lookup_head(const uint4* heads, uint64_t b, uint32_t key, int key_bits,
+                                            uint32_t* lo0, uint32_t* hi0, uint32_t* lo1, uint32_t* hi1) {
   const uint4* h = heads + b * 4;
   const uint4 v0 = __ldg(h), v1 = __ldg(h + 1), v2 = __ldg(h + 2), v3 = __ldg(h + 3);
   if (v0.z == kHeadSpill) return false;
+  if (key_bits != 16) return head_range32(v0, v1, v2, v3, key, lo0, hi0, lo1, hi1);
   const uint32_t w[13] = {v0.w, v1.x, v1.y, v1.z, v1.w, v2.x, v2.y, v2.z, v2.w, v3.x, v3.y, v3.z, v3.w};
   // bit i: the head's key i equals the seed's, two keys per word: a 16-bit half
   // of w ^ (key, key) is zero exactly when adding 0x7fff to its low 15 bits
@@ -290,7 +317,8 @@ __global__ void __launch_bounds__(32 * kCalWarps, 12) k_cal_seeds(SeedArgs a) {
         // the count pass only (the emit pass reads the lookups it kept)
         uint32_t hl0 = 0, hh0 = 0, hl1 = 0, hh1 = 0;
         bool head = false;
-        if (!EMIT && a.di.heads && live) head = lookup_head(a.di.heads, pb, pkey, &hl0, &hh0, &hl1, &hh1);
+        if (!EMIT && a.di.heads && live)
+          head = lookup_head(a.di.heads, pb, pkey, a.di.key_bits, &hl0, &hh0, &hl1, &hh1);
         for (int r2 = 0; r2 < a.di.n_refs; ++r2) {
           uint64_t lo = 0, hi = 0;
           if (kept) {
@@ -955,7 +983,7 @@ int launch_cal_slots(const uint64_t* read_off, uint32_t n, int k, uint32_t strid
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-// one thread per bucket: its head from jptr and key16 (the layout at DevIndex)
+// one thread per bucket: its head from jptr and key16 / key (the layout at DevIndex)
 __global__ void k_cal_heads(DevIndex di, uint64_t nb, uint4* heads) {
   const uint64_t b = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
   if (b >= nb) return;
@@ -967,12 +995,15 @@ __global__ void k_cal_heads(DevIndex di, uint64_t nb, uint4* heads) {
   for (int i = 0; i < 16; ++i) w[i] = 0;
   w[0] = s0;
   w[1] = s1;
-  if (n0 + n1 <= static_cast<uint64_t>(kHeadKeys)) {
+  if (di.key_bits == 16 && n0 + n1 <= static_cast<uint64_t>(kHeadKeys)) {
     w[2] = static_cast<uint32_t>(n0 | (n1 << 16));
     for (uint32_t i = 0; i < n0 + n1; ++i) {
       const uint32_t kk = i < n0 ? di.key16[0][s0 + i] : di.key16[1][s1 + (i - n0)];
       w[3 + (i >> 1)] |= kk << (16 * (i & 1));
     }
+  } else if (di.key_bits != 16 && n0 + n1 <= static_cast<uint64_t>(kHeadKeys32)) {
+    w[2] = static_cast<uint32_t>(n0 | (n1 << 16));
+    for (uint32_t i = 0; i < n0 + n1; ++i) w[3 + i] = i < n0 ? di.key[0][s0 + i] : di.key[1][s1 + (i - n0)];
   } else {
     w[2] = kHeadSpill;
   }

@@ -269,22 +269,24 @@ struct DevIndex {
   const uint32_t* key[kMaxRefs];
   const uint32_t* pos[kMaxRefs];
   const uint8_t* orient[kMaxRefs];
-  // packed form (packed = 1, the arrays above unset): the bucket starts of all
-  // references interleaved as 32-bit values, jptr[b * n_refs + r], so that one
-  // sector holds a seed's bucket in every reference; 16-bit keys; each entry's
-  // position with its orientation bits in the top two (posor), one load per
-  // entry.  Used when the references share one hash seed, each has under 2^32
-  // entries and at most 2^30 bases, and keys fit 16 bits (2 (k - a) <= 16).
+  // packed form (packed = 1; ptr, pos and orient unset): the bucket starts of
+  // all references interleaved as 32-bit values, jptr[b * n_refs + r], so that
+  // one sector holds a seed's bucket in every reference; 16-bit keys in key16
+  // when they fit (2 (k - a) <= 16, key_bits 16), else 32-bit ones in key
+  // (key_bits 32); each entry's position with its orientation bits in the top
+  // two (posor), one load per entry.  Used when the references share one hash
+  // seed and each has under 2^32 entries and at most 2^30 bases.
   const uint32_t* jptr;
   const uint16_t* key16[kMaxRefs];
   const uint32_t* posor[kMaxRefs];
-  int packed;
+  int packed, key_bits;
   // bucket heads (packed form, one or two references; nullptr otherwise): 64
   // bytes per bucket, read with one access: its first entry in references 0 and
   // 1 (words 0, 1), their entry counts (word 2, 16 bits each) and up to
-  // kHeadKeys keys, reference 0's then reference 1's in entry order (words 3-15,
-  // two per word, low half first).  Word 2 is kHeadSpill where they do not fit:
-  // that bucket is looked up in jptr and key16.
+  // kHeadKeys 16-bit keys (two per word, low half first) or kHeadKeys32 32-bit
+  // ones, reference 0's then reference 1's in entry order (words 3-15).  Word 2
+  // is kHeadSpill where they do not fit: that bucket is looked up in jptr and
+  // the keys.
   const uint4* heads;
   uint64_t ref_len[kMaxRefs];
   uint64_t hash_seed[kMaxRefs];
@@ -310,6 +312,7 @@ struct CalRanges {
   uint32_t rbase = 0;
 };
 constexpr int kHeadKeys = 26;
+constexpr int kHeadKeys32 = 13;
 constexpr uint32_t kHeadSpill = 0xffffffffu;
 // the bucket heads of a packed index (nbuckets buckets, n_refs <= 2) into heads
 int launch_cal_heads(const DevIndex& di, uint64_t nbuckets, uint4* heads, cudaStream_t st);

@@ -1383,7 +1383,8 @@ extern "C" sr_status sr_session_attach_index(sr_session* s, const sr_index* cons
     return set_error(SR_ENOMEM, "sr_session_attach_index: device upload failed");
   };
   // the packed device form when the references allow it (see DevIndex)
-  bool packed = 2 * (static_cast<int>(t[0].seed_len) - static_cast<int>(t[0].address_bases)) <= 16;
+  const bool keys16 = 2 * (static_cast<int>(t[0].seed_len) - static_cast<int>(t[0].address_bases)) <= 16;
+  bool packed = true;
   for (uint32_t r = 0; r < n_refs && packed; ++r)
     packed = t[r].hash_seed == t[0].hash_seed && t[r].n_ptr == t[0].n_ptr && t[r].n_entries < (1ull << 32) &&
              t[r].ref_len <= (1ull << 30);
@@ -1396,20 +1397,23 @@ extern "C" sr_status sr_session_attach_index(sr_session* s, const sr_index* cons
     if (!up(jp.data(), jp.size() * 4, &pj)) return fail();
     s->didx.jptr = static_cast<const uint32_t*>(pj);
     for (uint32_t r = 0; r < n_refs; ++r) {
-      std::vector<uint16_t> k16(t[r].n_entries);
+      std::vector<uint16_t> k16(keys16 ? t[r].n_entries : 0);
       std::vector<uint32_t> po(t[r].n_entries);
       for (uint64_t i = 0; i < t[r].n_entries; ++i) {
-        k16[i] = static_cast<uint16_t>(t[r].key[i]);
+        if (keys16) k16[i] = static_cast<uint16_t>(t[r].key[i]);
         po[i] = t[r].pos[i] | (static_cast<uint32_t>(t[r].orient[i] & 3u) << 30);
       }
       void *pk, *pp;
-      if (!up(k16.data(), k16.size() * 2, &pk) || !up(po.data(), po.size() * 4, &pp)) return fail();
-      s->didx.key16[r] = static_cast<const uint16_t*>(pk);
+      if (keys16 ? !up(k16.data(), k16.size() * 2, &pk) : !up(t[r].key, t[r].n_entries * 4, &pk)) return fail();
+      if (!up(po.data(), po.size() * 4, &pp)) return fail();
+      if (keys16) s->didx.key16[r] = static_cast<const uint16_t*>(pk);
+      else s->didx.key[r] = static_cast<const uint32_t*>(pk);
       s->didx.posor[r] = static_cast<const uint32_t*>(pp);
       s->didx.ref_len[r] = t[r].ref_len;
       s->didx.hash_seed[r] = t[r].hash_seed;
     }
     s->didx.packed = 1;
+    s->didx.key_bits = keys16 ? 16 : 32;
   } else {
     for (uint32_t r = 0; r < n_refs; ++r) {
       void *pp, *pk, *ps, *po;
@@ -1428,13 +1432,14 @@ extern "C" sr_status sr_session_attach_index(sr_session* s, const sr_index* cons
   s->didx.k = static_cast<int>(t[0].seed_len);
   s->didx.a = static_cast<int>(t[0].address_bases);
   // bucket heads, built on the device from the packed tables: where buckets are
-  // small (at most half a head's keys on average) a seed's lookup in both
-  // references is one 64-byte access instead of three dependent ones
-  // (SR_CAL_HEADS=0 leaves them out)
+  // small (on average at most half a head's 16-bit keys, or 8 of its 13 32-bit
+  // ones, so that few spill) a seed's lookup in both references is one 64-byte
+  // access instead of three dependent ones (SR_CAL_HEADS=0 leaves them out)
   const uint64_t nbk = t[0].n_ptr ? t[0].n_ptr - 1 : 0;
   uint64_t entries = 0;
   for (uint32_t r = 0; r < n_refs; ++r) entries += t[r].n_entries;
-  if (packed && n_refs <= 2 && nbk && nbk <= (1ull << 26) && entries <= nbk * (kHeadKeys / 2) &&
+  const uint64_t per_bucket = keys16 ? kHeadKeys / 2 : 8;
+  if (packed && n_refs <= 2 && nbk && nbk <= (1ull << 26) && entries <= nbk * per_bucket &&
       env_u64("SR_CAL_HEADS", 1) != 0) {
     void* ph = nullptr;
     if (cudaMalloc(&ph, nbk * 64) == cudaSuccess) {

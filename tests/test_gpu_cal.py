@@ -24,9 +24,9 @@ def _same(a, b):
         assert np.array_equal(np.asarray(a[k], np.int64), np.asarray(b[k], np.int64)), k
 
 
-# (20, 12) with one hash seed and (16, 8) take the device index's packed form
-# (shared bucket starts, 16-bit keys); the others, and different hash seeds per
-# reference, the per-reference form
+# With one hash seed the device index takes its packed form (shared bucket
+# starts): 16-bit keys for (20, 12) and (16, 8), 32-bit ones for (20, 10) and
+# (22, 11); different hash seeds per reference take the per-reference form
 @pytest.mark.parametrize("k,addr,cal_limit,seeds", [(20, 10, 1024, (0, 0)), (22, 11, 0, (0, 0)), (16, 8, 64, (0, 0)),
                                                     (20, 12, 1024, (0, 0)), (20, 12, 1024, (5, 9))])
 def test_device_matches_host_xenograft(sr, k, addr, cal_limit, seeds):
@@ -50,7 +50,7 @@ def test_packed_index_with_and_without_bucket_heads(sr, monkeypatch, heads):
     list as the host stage; SR_CAL_HEADS=0 at attach time leaves the heads out."""
     monkeypatch.setenv("SR_CAL_HEADS", heads)
     w = S.workload("c3", scale=0.002, seed=23, rc_frac=0.5)
-    for k, addr in [(16, 8), (20, 12)]:
+    for k, addr in [(16, 8), (20, 12), (24, 12)]:  # 16-bit keys twice, then 32-bit ones
         idx = [sr.Index.build(bytes(r), seed_len=k, address_bases=addr, cal_limit=0) for r in w["refs"]]
         s = sr.Session.from_indexes(idx)
         s.attach_index(idx)

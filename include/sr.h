@@ -242,8 +242,9 @@ void sr_session_close(sr_session* s);
  * SR_CAL_HEADS=0 in the environment).
  * sr_candidates_device then returns exactly the list
  * sr_candidates returns for those indexes (same windows, order and hits): one
- * warp per read looks up its seeds, one block per read sorts and merges its
- * CALs.  The reads may be host memory or, flagged SR_FLAG_DEVICE, device
+ * warp per read looks up its seeds, one warp or block per read sorts and
+ * merges its CALs, and reads of more than 8192 CALs are emitted, sorted and
+ * merged by many blocks each.  The reads may be host memory or, flagged SR_FLAG_DEVICE, device
  * memory (read on the session's stream); params->flags = SR_FLAG_DEVICE leaves
  * the list in device memory (its arrays device pointers, the list flagged
  * SR_FLAG_DEVICE), so that reads, windows and the alignment stay on the device

@@ -1840,8 +1840,22 @@ extern "C" sr_status sr_candidates_device(sr_session* s, const sr_reads* reads, 
   uint64_t got = 0;
   char* blk = static_cast<char*>(pool_take(s, at[6], &got));
   if (!blk) {
-    sr_cand_list_free(h);
-    return done(SR_ENOMEM, "sr_candidates_device: pinned host allocation failed");
+    // no pinned block to be had: copy straight into the list's own arrays
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+      if (part_bytes[k]) e = cudaMemcpyAsync(dst[k], src[k], part_bytes[k], cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      sr_cand_list_free(h);
+      return done(SR_ECUDA, "sr_candidates_device list copy");
+    }
+    const sr_status stt = done(SR_OK, "");
+    sr_cand_list_free(l);
+    if (stt != SR_OK) {
+      sr_cand_list_free(h);
+      return stt;
+    }
+    *out = h;
+    return SR_OK;
   }
   for (int k = 0; k < 6 && e == cudaSuccess; ++k)
     if (part_bytes[k]) e = cudaMemcpyAsync(blk + at[k], src[k], part_bytes[k], cudaMemcpyDeviceToHost, st);

@@ -338,6 +338,23 @@ def cal_finder_bench(sr, scale):
             "index_build_s": round(t_index, 2)}
 
 
+def sweep_wanted(only, name, k=None, limit=None):
+    """Whether --sweep-only (comma-separated workload[:k[:limit]], limit 'inf' = 0)
+    selects this workload, seed length and CAL limit; everything when empty."""
+    sel = [x.split(":") for x in only.split(",") if x]
+    if not sel:
+        return True
+    for o in sel:
+        if o[0] != name:
+            continue
+        if k is not None and len(o) > 1 and int(o[1]) != k:
+            continue
+        if limit is not None and len(o) > 2 and (0 if o[2] == "inf" else int(o[2])) != limit:
+            continue
+        return True
+    return False
+
+
 def sweep(args):
     """The paper's seed length x CAL limit study (Table 5) on synthetic stand-ins:
     per setting, windows (CALs after the filter) per read, end-to-end reads/s of
@@ -355,20 +372,8 @@ def sweep(args):
                           "budget_s": args.sweep_seconds}), flush=True)
         return True
 
-    only = [x.split(":") for x in args.sweep_only.split(",") if x]
-
     def wanted(name, k=None, limit=None):
-        if not only:
-            return True
-        for o in only:
-            if o[0] != name:
-                continue
-            if k is not None and len(o) > 1 and int(o[1]) != k:
-                continue
-            if limit is not None and len(o) > 2 and (0 if o[2] == "inf" else int(o[2])) != limit:
-                continue
-            return True
-        return False
+        return sweep_wanted(args.sweep_only, name, k, limit)
 
     for name in ["c3", "c5"]:
         if not wanted(name):

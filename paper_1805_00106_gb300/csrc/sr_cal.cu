@@ -836,6 +836,7 @@ __device__ __forceinline__ uint32_t big_sort_len(const FilterArgs& a, uint32_t r
 // tiles: perm lists the reads (indices into big) class by class.
 constexpr int kSortLgMin = 12;    // log2 kSortTile
 constexpr int kSortClasses = 20;  // sort lengths 2^12 .. 2^31
+static_assert((1u << kSortLgMin) == kSortTile, "sort classes start at one tile");
 struct SortClasses {
   uint32_t n;                     // classes present
   uint32_t lg[kSortClasses];      // log2 of their sort length, decreasing
